@@ -1,0 +1,29 @@
+"""CPU oracle for basic ORBGRAND (arXiv 2202.13951).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may use it; the product path never does.
+It shares no code with the CUDA library.
+
+Functions and the passages they follow:
+  decode / decode_batch  Algorithm 1 with the basic ORBGRAND generator
+                         (Sec. III-A/B, Eq. lw, Eq. fractionation,
+                         Eq. intpart2, Eq. vu, Algorithm 2)
+  enumerate_patterns     the query order itself (Sec. III-B, Algorithm 2)
+  count_by_weight        patterns per (W, w) met by that order
+  landslide              Algorithm 2 with Build-mountain (Sec. III-C)
+  sort_reliability       the permutation pi (Sec. III-A)
+
+Parity pins: tests/test_oracle_pins.py (brute force on tiny codes, the
+first queries of Sec. III-B, the Fig. 3 / Fig. 5 examples, closed-form
+partition counts, decoder invariants) and tests/test_oracle_mutations.py
+(planted mistakes must fail a pin).
+"""
+from .oracle import (Oracle, OracleError, build_oracle, compile_oracle,
+                     count_by_weight, decode, decode_batch, default,
+                     enumerate_patterns, landslide, sort_reliability,
+                     ORACLE_LIB, ORACLE_SRC)
+
+__all__ = ["Oracle", "OracleError", "build_oracle", "compile_oracle",
+           "count_by_weight", "decode", "decode_batch", "default",
+           "enumerate_patterns", "landslide", "sort_reliability",
+           "ORACLE_LIB", "ORACLE_SRC"]

@@ -1,0 +1,446 @@
+/*
+ * orbg_oracle.c -- plain, single-threaded CPU oracle for basic ORBGRAND.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file: only the tests, the smoke check and the benchmark's CPU
+ * baseline do.  It shares no code, header, table or helper with the CUDA
+ * library; it is written straight from the paper:
+ *
+ *   Duffy, An, Medard, "Ordered Reliability Bits Guessing Random Additive
+ *   Noise Decoding", arXiv 2202.13951.
+ *
+ * What it computes, step by step, in the paper's order and notation:
+ *   1. Hard decision y_i = (sign(LLR_i)+1)/2 and reliability |LLR_i|
+ *      (Sec. III-A).  Reading: y_i = 1 iff LLR_i > 0, so +-0 give 0.
+ *   2. pi: bit positions sorted by increasing reliability (Sec. III-A);
+ *      ties broken by the lower received index.
+ *   3. GRAND loop (Algorithm 1): noise effects z are queried in increasing
+ *      logistic weight w_L(z) = sum_i i z_i (Eq. lw), Hamming weight
+ *      fractionated (Eq. fractionation), each (W, w) set enumerated as
+ *      partitions u of W' = W - w(w+1)/2 into w parts in [0, n'=n-w]
+ *      (Eq. intpart2) by the Landslide generator (Algorithm 2) with its
+ *      Build-mountain routine (Sec. III-C), mapped back by v_i = i + u_i
+ *      (Eq. vu) and through pi.  Reading of the arbitrary tie order: w
+ *      ascending within a logistic weight, Landslide order within (W, w).
+ *   4. Membership of y (+) z is tested by the syndrome H (y (+) z) = 0
+ *      (Sec. I: a linear code is checked by a matrix multiply and compare),
+ *      evaluated as H y (+) sum of the columns of H that z selects.
+ *   5. The first query in the code-book is the decoding; after `cap`
+ *      queries without one the decoder abandons (Sec. IV-A) and returns the
+ *      hard decision with the abandon flag set.
+ *
+ * Parity pins (tests): brute force over all 2^n patterns for tiny codes,
+ * the first queries listed in Sec. III-B, the Fig. 3 / Fig. 5 Landslide
+ * examples, closed-form partition counts and decoder invariants.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAX_N 1024
+#define ORC_MAX_WORDS 16 /* syndromes up to 1024 bits */
+
+enum {
+    ORC_OK = 0,
+    ORC_EINVAL = -1,
+    ORC_ENAN = -4,
+    ORC_STOP = 1 /* internal: the visitor asked to stop */
+};
+
+/* ------------------------------------------------------------------ */
+/* Landslide (Algorithm 2) with Build-mountain (Sec. III-C).            */
+/* u is 1-based: u[0] is the dummy part used for the initial partition. */
+/* ------------------------------------------------------------------ */
+
+typedef int (*orc_visit_fn)(const int *u, int w, void *ctx);
+
+/* Build-mountain from part k: fill u_{k+1..w} with u_k, then push the
+ * remaining cells of W' into the right-most parts, each capped at n'. */
+static void orc_build_mountain(int *u, int k, int w, int Wp, int np)
+{
+    int i, sum, Wpp, q, r, room;
+    for (i = k + 1; i <= w; i++)
+        u[i] = u[k];                      /* step 1 */
+    sum = 0;
+    for (i = 1; i <= w; i++)
+        sum += u[i];
+    Wpp = Wp - sum;                       /* step 2 */
+    if (Wpp == 0)
+        return;                           /* nothing left to place */
+    room = np - u[k];                     /* > 0 whenever Wpp > 0 */
+    q = Wpp / room;                       /* step 3 */
+    r = Wpp % room;
+    if (q != 0)
+        for (i = w - q + 1; i <= w; i++)
+            u[i] = np;                    /* step 4 */
+    u[w - q] += r;                        /* step 5 */
+}
+
+/* Accumulated drop D(i) = sum_{j=i}^{w} d(j) with d(w) = 0 and
+ * d(i) = u_{i+1} - u_i; it telescopes to u_w - u_i. */
+static int orc_drop(const int *u, int i, int w)
+{
+    int j, D = 0;
+    for (j = i; j < w; j++)
+        D += u[j + 1] - u[j];
+    return D;
+}
+
+/* Generate every partition of Wp into w non-decreasing parts in [0, np],
+ * in Landslide order, calling visit on each.  Requires w >= 1 and
+ * 0 <= Wp <= w * np. Returns ORC_STOP if the visitor stopped early. */
+int orc_landslide(int Wp, int w, int np, orc_visit_fn visit, void *ctx)
+{
+    int u[ORC_MAX_N + 1];
+    int k, rc;
+    if (w < 1 || w > ORC_MAX_N || np < 0 || Wp < 0 || Wp > w * np)
+        return ORC_EINVAL;
+    memset(u, 0, sizeof(u));
+    orc_build_mountain(u, 0, w, Wp, np);  /* dummy part u_0 = 0 */
+    rc = visit(u, w, ctx);
+    if (rc)
+        return rc;
+    while (orc_drop(u, 1, w) >= 2) {
+        for (k = w; k >= 1; k--)          /* largest k with D(k) >= 2 */
+            if (orc_drop(u, k, w) >= 2)
+                break;
+        u[k] += 1;
+        orc_build_mountain(u, k, w, Wp, np);
+        rc = visit(u, w, ctx);
+        if (rc)
+            return rc;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* The query order: W ascending; within W, Hamming weight w ascending   */
+/* (Eq. fractionation); within (W, w), Landslide order.                 */
+/* Patterns are reported as v (1-based positions in the sorted order).  */
+/* ------------------------------------------------------------------ */
+
+typedef int (*orc_pattern_fn)(const int *v, int w, void *ctx);
+
+typedef struct {
+    orc_pattern_fn fn;
+    void *ctx;
+} orc_map_ctx;
+
+static int orc_map_u_to_v(const int *u, int w, void *vctx)
+{
+    orc_map_ctx *m = (orc_map_ctx *)vctx;
+    int v[ORC_MAX_N + 1];
+    int i;
+    for (i = 1; i <= w; i++)
+        v[i] = i + u[i];                  /* Eq. vu */
+    return m->fn(v + 1, w, m->ctx);
+}
+
+/* Walk the patterns of a length-n word in query order, stopping when the
+ * visitor returns non-zero.  The zero pattern (w_L = 0) comes first. */
+static int orc_walk_patterns(int n, orc_pattern_fn fn, void *ctx)
+{
+    long Wmax = (long)n * (n + 1) / 2;   /* logistic weight of all-ones */
+    long W;
+    int w, rc;
+    orc_map_ctx m;
+    m.fn = fn;
+    m.ctx = ctx;
+    rc = fn(NULL, 0, ctx);               /* W = 0: nothing flipped */
+    if (rc)
+        return rc;
+    for (W = 1; W <= Wmax; W++) {
+        /* w up to floor((sqrt(1+8W)-1)/2): smallest w_L of weight w is
+         * w(w+1)/2 (Eq. fractionation). */
+        for (w = 1; (long)w * (w + 1) / 2 <= W && w <= n; w++) {
+            long Wp = W - (long)w * (w + 1) / 2;
+            int np = n - w;
+            if (Wp > (long)w * np)
+                continue;                 /* no partition fits */
+            rc = orc_landslide((int)Wp, w, np, orc_map_u_to_v, &m);
+            if (rc)
+                return rc;
+        }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Enumeration export, for pinning the order itself.                    */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int *out;        /* [count][n+1]: w, then v_1..v_w (rest zero) */
+    int stride;
+    long count, done;
+} orc_enum_ctx;
+
+static int orc_enum_visit(const int *v, int w, void *vctx)
+{
+    orc_enum_ctx *e = (orc_enum_ctx *)vctx;
+    int *row, i;
+    if (e->done >= e->count)
+        return ORC_STOP;
+    row = e->out + e->done * e->stride;
+    memset(row, 0, sizeof(int) * (size_t)e->stride);
+    row[0] = w;
+    for (i = 0; i < w; i++)
+        row[1 + i] = v[i];
+    e->done++;
+    return e->done >= e->count ? ORC_STOP : 0;
+}
+
+/* First `count` patterns for length n, rows of n+1 ints.  Returns the
+ * number written (less than count once the 2^n patterns run out). */
+long orbg_oracle_enumerate(int n, long count, int *out)
+{
+    orc_enum_ctx e;
+    if (n < 1 || n > ORC_MAX_N || count < 0 || (count > 0 && !out))
+        return ORC_EINVAL;
+    if (count == 0)
+        return 0;
+    e.out = out;
+    e.stride = n + 1;
+    e.count = count;
+    e.done = 0;
+    orc_walk_patterns(n, orc_enum_visit, &e);
+    return e.done;
+}
+
+typedef struct {
+    int *out;
+    int w;
+    long cap, done;
+} orc_ls_ctx;
+
+static int orc_ls_visit(const int *u, int w, void *vctx)
+{
+    orc_ls_ctx *c = (orc_ls_ctx *)vctx;
+    int i;
+    if (c->done >= c->cap)
+        return ORC_STOP;
+    for (i = 0; i < w; i++)
+        c->out[c->done * w + i] = u[i + 1];
+    c->done++;
+    return 0;
+}
+
+/* Landslide output for (W', w, n'), as rows of w parts u_1..u_w. */
+long orbg_oracle_landslide(int Wp, int w, int np, long cap, int *out)
+{
+    orc_ls_ctx c;
+    int rc;
+    c.out = out;
+    c.w = w;
+    c.cap = cap;
+    c.done = 0;
+    rc = orc_landslide(Wp, w, np, orc_ls_visit, &c);
+    if (rc < 0)
+        return rc;
+    return c.done;
+}
+
+typedef struct {
+    long *counts;    /* [(Wmax+1) * (n+1)], index W*(n+1) + w */
+    int n, Wmax;
+} orc_count_ctx;
+
+static int orc_count_visit(const int *v, int w, void *vctx)
+{
+    orc_count_ctx *c = (orc_count_ctx *)vctx;
+    long W = 0;
+    int i;
+    for (i = 0; i < w; i++)
+        W += v[i];                        /* w_L of the pattern (Eq. lw) */
+    if (W > c->Wmax)
+        return ORC_STOP;                  /* the order is by W: done */
+    c->counts[W * (c->n + 1) + w] += 1;
+    return 0;
+}
+
+/* Number of patterns of each (logistic weight W, Hamming weight w) met by
+ * the query order, for W <= Wmax. */
+int orbg_oracle_count_by_weight(int n, int Wmax, long *counts)
+{
+    orc_count_ctx c;
+    if (n < 1 || n > ORC_MAX_N || Wmax < 0 || !counts)
+        return ORC_EINVAL;
+    memset(counts, 0, sizeof(long) * (size_t)(Wmax + 1) * (n + 1));
+    c.counts = counts;
+    c.n = n;
+    c.Wmax = Wmax;
+    orc_walk_patterns(n, orc_count_visit, &c);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* The decoder (Algorithm 1 with the basic ORBGRAND generator).         */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int n, r, words;
+    const uint64_t *col;     /* col[j*words + x]: column j of H, bit i = H[i][j] */
+    const int *pi;           /* pi[p] = received index of the p-th least reliable bit */
+    uint64_t s0[ORC_MAX_WORDS];
+    uint64_t cap, t, sum_w;
+    int hit, hit_w;
+    int hit_v[ORC_MAX_N];
+} orc_dec_ctx;
+
+static int orc_dec_visit(const int *v, int w, void *vctx)
+{
+    orc_dec_ctx *d = (orc_dec_ctx *)vctx;
+    uint64_t s[ORC_MAX_WORDS];
+    int i, x, zero;
+    if (d->t >= d->cap)
+        return ORC_STOP;                  /* abandon: cap queries made */
+    d->t += 1;
+    d->sum_w += (uint64_t)w;
+    for (x = 0; x < d->words; x++)
+        s[x] = d->s0[x];
+    for (i = 0; i < w; i++) {
+        const uint64_t *c = d->col + (size_t)d->pi[v[i] - 1] * d->words;
+        for (x = 0; x < d->words; x++)
+            s[x] ^= c[x];
+    }
+    zero = 1;
+    for (x = 0; x < d->words; x++)
+        if (s[x])
+            zero = 0;
+    if (!zero)
+        return 0;
+    d->hit = 1;
+    d->hit_w = w;
+    for (i = 0; i < w; i++)
+        d->hit_v[i] = v[i];
+    return ORC_STOP;
+}
+
+/* Sort order of Sec. III-A: increasing reliability |LLR|, lower received
+ * index first among equal reliabilities.  A plain insertion sort. */
+static void orc_sort_by_reliability(const float *llr, int n, int *pi)
+{
+    int i, j;
+    for (i = 0; i < n; i++)
+        pi[i] = i;
+    for (i = 1; i < n; i++) {
+        int key = pi[i];
+        float rk = fabsf(llr[key]);
+        j = i - 1;
+        while (j >= 0) {
+            float rj = fabsf(llr[pi[j]]);
+            if (rj > rk || (rj == rk && pi[j] > key)) {
+                pi[j + 1] = pi[j];
+                j--;
+            } else {
+                break;
+            }
+        }
+        pi[j + 1] = key;
+    }
+}
+
+/*
+ * Decode one received block.
+ *   H       : r x n parity-check matrix, row-major bytes 0/1.
+ *   llr     : n log-likelihood ratios, LLR = log f(Y|1)/f(Y|0).
+ *   cap     : abandon after this many queries (>= 1).
+ *   c_out   : n bytes, the decoding (or the hard decision if abandoned).
+ *   q_out   : queries made: the index of the hit, or cap if abandoned.
+ *   abandon : 1 if no code-book member was met within cap queries.
+ *   sum_w   : sum over the queries made of their Hamming weights.
+ *   hit_w / hit_v (optional): the winning pattern, positions 1-based in
+ *             the sorted order.
+ * Returns 0, or ORC_ENAN if an LLR is NaN, ORC_EINVAL on bad sizes.
+ */
+int orbg_oracle_decode(const uint8_t *H, int n, int r, const float *llr,
+                       uint64_t cap, uint8_t *c_out, uint64_t *q_out,
+                       int *abandon, uint64_t *sum_w, int *hit_w, int *hit_v)
+{
+    static uint64_t col[ORC_MAX_N * ORC_MAX_WORDS];
+    int pi[ORC_MAX_N];
+    uint8_t y[ORC_MAX_N];
+    orc_dec_ctx d;
+    int i, j, words;
+
+    if (n < 1 || n > ORC_MAX_N || r < 1 || r > 64 * ORC_MAX_WORDS || cap < 1)
+        return ORC_EINVAL;
+    for (i = 0; i < n; i++)
+        if (isnan(llr[i]))
+            return ORC_ENAN;
+    words = (r + 63) / 64;
+    memset(col, 0, sizeof(uint64_t) * (size_t)n * words);
+    for (i = 0; i < r; i++)
+        for (j = 0; j < n; j++)
+            if (H[(size_t)i * n + j])
+                col[(size_t)j * words + i / 64] |= (uint64_t)1 << (i % 64);
+
+    for (i = 0; i < n; i++)
+        y[i] = llr[i] > 0.0f ? 1 : 0;     /* (sign(LLR)+1)/2, zero -> 0 */
+    orc_sort_by_reliability(llr, n, pi);
+
+    memset(&d, 0, sizeof(d));
+    d.n = n;
+    d.r = r;
+    d.words = words;
+    d.col = col;
+    d.pi = pi;
+    d.cap = cap;
+    for (i = 0; i < n; i++)               /* s0 = H y */
+        if (y[i])
+            for (j = 0; j < words; j++)
+                d.s0[j] ^= col[(size_t)i * words + j];
+
+    orc_walk_patterns(n, orc_dec_visit, &d);
+
+    for (i = 0; i < n; i++)
+        c_out[i] = y[i];
+    if (d.hit) {
+        for (i = 0; i < d.hit_w; i++)
+            c_out[pi[d.hit_v[i] - 1]] ^= 1;   /* y (-) z */
+        *q_out = d.t;
+        *abandon = 0;
+    } else {
+        *q_out = d.t;                      /* = cap, or 2^n if exhausted */
+        *abandon = 1;
+    }
+    if (sum_w)
+        *sum_w = d.sum_w;
+    if (hit_w)
+        *hit_w = d.hit ? d.hit_w : -1;
+    if (hit_v && d.hit)
+        for (i = 0; i < d.hit_w; i++)
+            hit_v[i] = d.hit_v[i];
+    return ORC_OK;
+}
+
+/* Batch form: blocks decoded one after another, same H. */
+int orbg_oracle_decode_batch(const uint8_t *H, int n, int r, const float *llr,
+                             long B, uint64_t cap, uint8_t *c_out,
+                             uint64_t *q_out, uint8_t *abandon, uint64_t *sum_w)
+{
+    long b;
+    for (b = 0; b < B; b++) {
+        int ab = 0, rc;
+        uint64_t sw = 0;
+        rc = orbg_oracle_decode(H, n, r, llr + (size_t)b * n, cap,
+                                c_out + (size_t)b * n, q_out + b, &ab, &sw,
+                                NULL, NULL);
+        if (rc)
+            return rc;
+        abandon[b] = (uint8_t)ab;
+        if (sum_w)
+            sum_w[b] = sw;
+    }
+    return ORC_OK;
+}
+
+/* The permutation of Sec. III-A alone, for tests. */
+int orbg_oracle_sort(const float *llr, int n, int *pi)
+{
+    if (n < 1 || n > ORC_MAX_N)
+        return ORC_EINVAL;
+    orc_sort_by_reliability(llr, n, pi);
+    return ORC_OK;
+}

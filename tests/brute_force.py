@@ -1,0 +1,48 @@
+"""Brute-force basic ORBGRAND for tiny codes (n <= 16): a third, independent
+implementation used to pin the oracle.
+
+It lists all 2^n noise patterns, sorts them by (logistic weight, Hamming
+weight, positions lexicographically) -- the canonical reading of the
+paper's arbitrary tie order -- and decodes by testing H c = 0 directly
+(the plain definition of code-book membership), with no syndrome
+bookkeeping and no partition generator.
+"""
+import functools
+
+import numpy as np
+
+
+@functools.lru_cache(maxsize=None)
+def query_order(n):
+    """All subsets of {1..n} in the canonical query order."""
+    pats = []
+    for mask in range(1 << n):
+        v = tuple(i + 1 for i in range(n) if (mask >> i) & 1)
+        pats.append((sum(v), len(v), v))
+    pats.sort()
+    return tuple(p[2] for p in pats)
+
+
+def reliability_order(llr):
+    """Received indices sorted by increasing |LLR| (FP32), lower index first
+    among equal reliabilities."""
+    rel = np.abs(np.asarray(llr, dtype=np.float32))
+    return sorted(range(len(rel)), key=lambda i: (float(rel[i]), i))
+
+
+def decode(H, llr, cap):
+    """Returns (codeword, queries, abandoned)."""
+    H = np.asarray(H, dtype=np.int64)
+    llr = np.asarray(llr, dtype=np.float32)
+    n = llr.shape[0]
+    y = (llr > 0).astype(np.uint8)
+    pi = reliability_order(llr)
+    for t, v in enumerate(query_order(n), start=1):
+        if t > cap:
+            return y.copy(), cap, 1
+        c = y.copy()
+        for p in v:
+            c[pi[p - 1]] ^= 1
+        if not ((H @ c.astype(np.int64)) % 2).any():
+            return c, t, 0
+    return y.copy(), len(query_order(n)), 1

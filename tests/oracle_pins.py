@@ -1,0 +1,271 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each function takes an ``oracle.Oracle`` and raises AssertionError on a
+mismatch.  tests/test_oracle_pins.py runs them on the real oracle;
+tests/test_oracle_mutations.py runs them on copies with planted mistakes,
+each of which must fail at least one pin.
+
+Sources of truth, none of them the oracle's own code:
+  * the paper's worked examples (tests/golden/, each line cited);
+  * closed forms: the generating function prod_i (1 + q^i) for the number
+    of patterns per logistic weight (Eq. znwl), the Gaussian binomial for
+    partitions into at most w parts <= n' (Eq. intpart2), textbook values
+    of the distinct-part partition numbers;
+  * brute force over all 2^n patterns (tests/brute_force.py);
+  * decoder invariants (noiseless input, H c = 0, basis, scaling,
+    permutation equivariance).
+"""
+import functools
+import itertools
+import os
+
+import numpy as np
+
+import brute_force
+from paper_2202_13951_gb300 import workloads
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def _golden(name):
+    rows = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split(":", 1)
+            rows[k.strip()] = v.strip()
+    return rows
+
+
+# ------------------------------------------------------------ closed forms
+
+def distinct_part_counts(n, Wmax):
+    """Coefficients of prod_{i=1}^{n} (1 + q^i) up to q^Wmax."""
+    poly = [1] + [0] * Wmax
+    for i in range(1, n + 1):
+        for W in range(Wmax, i - 1, -1):
+            poly[W] += poly[W - i]
+    return poly
+
+
+@functools.lru_cache(maxsize=None)
+def gaussian_binomial(m, k):
+    """Coefficients of the q-binomial [m choose k]_q (a polynomial in q)."""
+    if k < 0 or k > m:
+        return [0]
+    table = {}
+
+    def rec(mm, kk):
+        if kk == 0 or kk == mm:
+            return [1]
+        key = (mm, kk)
+        if key in table:
+            return table[key]
+        a = rec(mm - 1, kk - 1)
+        b = rec(mm - 1, kk)
+        out = [0] * max(len(a), len(b) + kk)
+        for i, x in enumerate(a):
+            out[i] += x
+        for i, x in enumerate(b):
+            out[i + kk] += x
+        table[key] = out
+        return out
+
+    return tuple(rec(m, k))
+
+
+# ------------------------------------------------------------------ pins
+
+def pin_first_queries(orc):
+    """Sec. III-B: queries 1..3 are {}, {1}, {2}; queries 4-5 are {3} and
+    {1,2} (tie arbitrary in the paper; this build's reading puts the lower
+    Hamming weight first)."""
+    g = _golden("sec3b_first_queries.txt")
+    for n in (3, 8, 64, 256):
+        got = orc.enumerate_patterns(n, 5)
+        assert got[0] == () and g["1"] == "-"
+        assert got[1] == tuple(int(x) for x in g["2"].split())
+        assert got[2] == tuple(int(x) for x in g["3"].split())
+        pair = [tuple(int(x) for x in p.split()) for p in g["4-5"].split("|")]
+        assert set(got[3:5]) == set(pair)
+        assert got[3] == (3,) and got[4] == (1, 2)   # w ascending reading
+
+
+def pin_fig3(orc):
+    """Fig. 3: Landslide(W'=8, w=4, n'=4) gives steps (a)..(h)."""
+    g = _golden("fig3_landslide.txt")
+    rows = orc.landslide(8, 4, 4)
+    assert len(rows) == int(g["count"])
+    assert rows[0] == tuple(int(x) for x in g["a"].split())
+    assert rows[4] == tuple(int(x) for x in g["e"].split())
+    assert rows[-1] == tuple(int(x) for x in g["h"].split())
+    # every partition of 8 into 4 non-decreasing parts <= 4, each once
+    brute = sorted(u for u in _nondecreasing(4, 8, 4))
+    assert sorted(rows) == brute
+
+
+def _nondecreasing(w, total, cap, lo=0):
+    if w == 0:
+        if total == 0:
+            yield ()
+        return
+    for x in range(lo, cap + 1):
+        if x * w > total:
+            break
+        for rest in _nondecreasing(w - 1, total - x, cap, x):
+            yield (x,) + rest
+
+
+def pin_fig5(orc):
+    """Fig. 5: (W=18, w=4, n=8) is (W'=8, w=4, n'=4) shifted by 1,2,3,4, and
+    it is exactly the 4-subsets of {1..8} summing to 18."""
+    g = _golden("fig5_mapping.txt")
+    W, w, n = int(g["W"]), int(g["w"]), int(g["n"])
+    off = [int(x) for x in g["offsets"].split()]
+    us = orc.landslide(W - w * (w + 1) // 2, w, n - w)
+    vs = [tuple(u[i] + off[i] for i in range(w)) for u in us]
+    brute = [c for c in itertools.combinations(range(1, n + 1), w)
+             if sum(c) == W]
+    assert sorted(vs) == sorted(brute)
+    # and the decoder's order visits exactly these, in this order
+    allp = orc.enumerate_patterns(n, 1 << n)
+    cls = [p for p in allp if len(p) == w and sum(p) == W]
+    assert cls == vs
+
+
+def pin_counts_closed_form(orc):
+    """Patterns per logistic weight = coefficients of prod (1+q^i) (Eq.
+    znwl); per (W, w) = Gaussian binomial [n'+w choose w]_q at q^W'
+    (Eq. intpart2); textbook distinct-part partition numbers."""
+    textbook = [1, 1, 1, 2, 2, 3, 4, 5, 6, 8, 10, 12]  # A000009, W = 0..11
+    cnt = orc.count_by_weight(40, 11)
+    assert list(cnt.sum(axis=1)) == textbook
+    for n, Wmax in ((7, 28), (16, 60), (64, 70), (128, 50), (256, 40)):
+        cnt = orc.count_by_weight(n, Wmax)
+        assert list(cnt.sum(axis=1)) == distinct_part_counts(n, Wmax)[:Wmax + 1]
+        for W in range(Wmax + 1):
+            for w in range(1, n + 1):
+                Wp = W - w * (w + 1) // 2
+                if Wp < 0:
+                    assert cnt[W, w] == 0
+                    continue
+                gb = gaussian_binomial(n, w)  # [(n-w)+w choose w]_q
+                expect = gb[Wp] if Wp < len(gb) else 0
+                assert cnt[W, w] == expect, (n, W, w, cnt[W, w], expect)
+
+
+def pin_cumulative_counts(orc):
+    """Patterns with W <= 82 (the depth a 1e6 query cap reaches)."""
+    for n in (64, 128):
+        cnt = orc.count_by_weight(n, 82)
+        assert int(cnt.sum()) == sum(distinct_part_counts(n, 82))
+
+
+def pin_order_brute(orc):
+    """The whole order for n <= 10 equals sorting all subsets by
+    (W, w, lexicographic)."""
+    for n in (1, 2, 5, 7, 10):
+        got = orc.enumerate_patterns(n, 1 << n)
+        assert got == list(brute_force.query_order(n))
+
+
+def _tiny_inputs(code, rng, blocks):
+    """Random LLRs with ties, signed zeros and infinities mixed in."""
+    out = []
+    for b in range(blocks):
+        llr = rng.normal(0.0, 2.0, code.n).astype(np.float32)
+        kind = b % 5
+        if kind == 1:   # quantised: many ties
+            llr = np.round(llr).astype(np.float32)
+        elif kind == 2:  # signed zeros and infinities
+            llr[rng.integers(0, code.n, 2)] = 0.0
+            llr[rng.integers(0, code.n, 1)] = -0.0
+            llr[rng.integers(0, code.n, 1)] = np.inf
+        elif kind == 3:  # all equal magnitude: hard GRAND order
+            llr = np.where(rng.random(code.n) < 0.5, -1.0, 1.0).astype(np.float32)
+        out.append(llr)
+    return out
+
+
+def pin_brute_decode(orc, blocks=60):
+    """Oracle = brute force on the (7,4) Hamming code and a seeded random
+    (16,11) code, at every cap for n=7 and at boundary caps for n=16."""
+    rng = np.random.default_rng(7)
+    ham = workloads.hamming74()
+    for llr in _tiny_inputs(ham, rng, blocks):
+        for cap in range(1, 129):
+            c0, q0, a0 = brute_force.decode(ham.H, llr, cap)
+            c1, q1, a1, _, _ = orc.decode(ham.H, llr, cap)
+            assert (c0 == c1).all() and q0 == q1 and a0 == a1, (llr, cap)
+    code = workloads.rlc(16, 11, seed=16)
+    for llr in _tiny_inputs(code, rng, blocks):
+        _, qh, _ = brute_force.decode(code.H, llr, 1 << 16)
+        for cap in sorted({1, 2, 3, max(1, qh - 1), qh, qh + 1, 1 << 16}):
+            c0, q0, a0 = brute_force.decode(code.H, llr, cap)
+            c1, q1, a1, _, _ = orc.decode(code.H, llr, cap)
+            assert (c0 == c1).all() and q0 == q1 and a0 == a1, (llr, cap)
+
+
+def pin_invariants(orc):
+    """Noiseless input decodes at query 1; H c = 0 whenever not abandoned;
+    decoding does not depend on the basis of H, on a positive scaling of the
+    LLRs, and commutes with a joint permutation of coordinates."""
+    rng = np.random.default_rng(11)
+    code = workloads.rlc(48, 38, seed=3)
+    llr, cw = workloads.awgn_llr(code, 40, 4.0, seed=5)
+    # noiseless: LLR signs agree with the codeword
+    clean = np.where(cw == 1, 3.0, -3.0).astype(np.float32)
+    clean *= rng.uniform(0.5, 2.0, clean.shape).astype(np.float32)
+    for b in range(10):
+        c, q, a, _, _ = orc.decode(code.H, clean[b], 1000)
+        assert q == 1 and a == 0 and (c == cw[b]).all()
+    # other basis: H' = A H with A invertible over GF(2)
+    while True:
+        A = rng.integers(0, 2, (code.r, code.r)).astype(np.uint8)
+        if workloads.gf2_rank(A) == code.r:
+            break
+    H2 = ((A.astype(np.int64) @ code.H.astype(np.int64)) % 2).astype(np.uint8)
+    perm = rng.permutation(code.n)
+    for b in range(llr.shape[0]):
+        c, q, a, _, _ = orc.decode(code.H, llr[b], 20000)
+        if not a:
+            assert not ((code.H.astype(np.int64) @ c) % 2).any()
+        c2, q2, a2, _, _ = orc.decode(H2, llr[b], 20000)
+        assert (c == c2).all() and q == q2 and a == a2
+        c3, q3, a3, _, _ = orc.decode(code.H, llr[b] * np.float32(4.0), 20000)
+        assert (c == c3).all() and q == q3 and a == a3
+        mags = np.abs(llr[b])
+        if np.unique(mags).shape[0] == code.n:
+            c4, q4, a4, _, _ = orc.decode(code.H[:, perm], llr[b][perm], 20000)
+            assert (c4 == c[perm]).all() and q4 == q and a4 == a
+
+
+def pin_cap_boundary(orc):
+    """A hit exactly at query cap is a decoding; one query less abandons and
+    returns the hard decision with q = cap."""
+    code = workloads.rlc(32, 24, seed=9)
+    llr, _ = workloads.awgn_llr(code, 30, 3.0, seed=10)
+    seen = 0
+    for b in range(llr.shape[0]):
+        c, q, a, _, _ = orc.decode(code.H, llr[b], 100000)
+        if a or q < 3:
+            continue
+        seen += 1
+        c1, q1, a1, _, _ = orc.decode(code.H, llr[b], q)
+        assert a1 == 0 and q1 == q and (c1 == c).all()
+        c2, q2, a2, _, _ = orc.decode(code.H, llr[b], q - 1)
+        assert a2 == 1 and q2 == q - 1
+        assert (c2 == (llr[b] > 0)).all()
+    assert seen > 5
+
+
+FAST_PINS = [pin_first_queries, pin_fig3, pin_fig5, pin_order_brute,
+             pin_counts_closed_form, pin_brute_decode, pin_invariants,
+             pin_cap_boundary]
+
+
+def run_all(orc, pins=None):
+    for p in pins or FAST_PINS:
+        p(orc)

@@ -1,0 +1,62 @@
+"""Plant plausible mistakes in copies of the oracle (on the CPU) and check
+that at least one pin fails for each: the pins are strong enough to catch a
+dropped term, a wrong sign or index, or a swapped order."""
+import os
+import subprocess
+import sys
+import textwrap
+
+import pytest
+
+import oracle
+
+# (name, text in orbg_oracle.c, replacement)
+MUTATIONS = [
+    ("tie_break_reversed", "(rj == rk && pi[j] > key)", "(rj == rk && pi[j] < key)"),
+    ("sort_descending", "if (rj > rk ||", "if (rj < rk ||"),
+    ("hard_decision_ge", "llr[i] > 0.0f ? 1 : 0", "llr[i] >= 0.0f ? 1 : 0"),
+    ("no_start_syndrome", "d.s0[j] ^= col[(size_t)i * words + j];", "(void)0;"),
+    ("zero_pattern_skipped", "rc = fn(NULL, 0, ctx);", "rc = 0;"),
+    ("build_mountain_step5_dropped", "u[w - q] += r;", "(void)r;"),
+    ("landslide_smallest_k", "for (k = w; k >= 1; k--)", "for (k = 1; k <= w; k++)"),
+    ("cap_off_by_one", "if (d->t >= d->cap)", "if (d->t > d->cap)"),
+    ("hamming_weight_descending",
+     "for (w = 1; (long)w * (w + 1) / 2 <= W && w <= n; w++) {",
+     "for (w = n; w >= 1; w--) { if ((long)w * (w + 1) / 2 > W) continue;"),
+    ("vu_map_transposed", "v[i] = i + u[i];", "v[i] = i + u[w + 1 - i];"),
+    ("flip_wrong_index", "c_out[pi[d.hit_v[i] - 1]] ^= 1;", "c_out[d.hit_v[i] - 1] ^= 1;"),
+]
+
+RUNNER = textwrap.dedent("""
+    import sys
+    sys.path[:0] = [{root!r}, {tests!r}]
+    import oracle, oracle_pins
+    orc = oracle.Oracle({lib!r})
+    failed = []
+    for p in oracle_pins.FAST_PINS:
+        try:
+            p(orc)
+        except AssertionError:
+            failed.append(p.__name__)
+    print("FAILED_PINS", failed)
+    sys.exit(1 if failed else 0)
+""")
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_mutation_is_caught(tmp_path, name, old, new):
+    src = open(oracle.ORACLE_SRC).read()
+    assert src.count(old) == 1, name
+    mutated = tmp_path / ("orbg_oracle_%s.c" % name)
+    mutated.write_text(src.replace(old, new))
+    lib = str(tmp_path / ("lib_%s.so" % name))
+    oracle.compile_oracle(str(mutated), lib)
+    tests_dir = os.path.dirname(os.path.abspath(__file__))
+    code = RUNNER.format(root=os.path.dirname(tests_dir), tests=tests_dir, lib=lib)
+    # a subprocess: a mutant may misbehave; it must not take pytest with it
+    try:
+        p = subprocess.run([sys.executable, "-c", code], capture_output=True,
+                           text=True, timeout=120)
+    except subprocess.TimeoutExpired:
+        return  # a mutant that never finishes is caught too
+    assert p.returncode != 0, "mutation %s passed every pin:\n%s" % (name, p.stdout)
