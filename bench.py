@@ -1,0 +1,502 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 basic-ORBGRAND decoder.
+
+One step = one batched persistent launch (orbg_decode_batched) over the
+whole BCH(127,113) workload: 4 x 100,000 blocks of FP32 LLRs at Eb/N0 =
+4, 5, 6, 7 dB, query cap 1e6 -- every block sorted, searched and written
+back.  Inputs (203 MB, larger than the 129 MB L2) are resident in HBM when
+the timed region starts; the code tables stay resident.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torchrun, one rank per GPU: each rank decodes its own
+400,000-block workload (seeds offset by rank), there is no data-path
+collective (blocks are independent), and the timing is the max over ranks
+(weak scaling).  ``--impl reference`` times the CPU oracle on the host
+cores instead, on a bounded sample of the same workload.
+
+Prints one JSON line (rank 0).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("decoded blocks/s and syndrome queries/s (bit-exact vs oracle) "
+          "+ p99 latency")
+WORKLOAD = "bch(127,113) 4x100000 blocks at Eb/N0 4,5,6,7 dB, query cap 1e6"
+POINTS = (4.0, 5.0, 6.0, 7.0)
+SEEDS = (201, 202, 203, 204)
+B_PER_POINT = 100_000
+CAP = 1_000_000
+SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+# ------------------------------------------------------------------ utils
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--ref-sample", type=int, default=8000,
+                   help="blocks per reference step (CPU oracle)")
+    return p.parse_args(argv)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def rank_seeds(rank):
+    """Each rank decodes its own workload: seeds offset by 1000 * rank."""
+    return tuple(s + 1000 * rank for s in SEEDS)
+
+
+def make_inputs(rank=0, b_per_point=B_PER_POINT):
+    from paper_2202_13951_gb300 import workloads
+    code = workloads.config2_code()
+    ls = []
+    for e, s in zip(POINTS, rank_seeds(rank)):
+        l, _ = workloads.awgn_llr(code, b_per_point, e, s)
+        ls.append(l)
+    return code, np.ascontiguousarray(np.concatenate(ls))
+
+
+def max_over_ranks(value, world, device=None):
+    """Max of a float over ranks (identity when world == 1)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value, world, device=None):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def class_weight_prefix(n, max_queries):
+    """Cumulative Hamming weight over the query order, by class: the order
+    visits logistic weights W = 0, 1, ... and within W Hamming weights w
+    ascending, a class (W, w) holding the partitions of W into w distinct
+    parts <= n.  Returns (class_end[], class_w[]) up to max_queries, so
+    sum_{t<=q} w_t follows from q alone."""
+    # N[w][W]: sets of w distinct parts in [1, n] summing to W (DP over parts)
+    Wmax = 1
+    while True:
+        Wmax *= 2
+        N = np.zeros((Wmax + 1, Wmax + 1), dtype=object)  # [w][W]
+        N[0][0] = 1
+        for part in range(1, min(n, Wmax) + 1):
+            for w in range(Wmax, 0, -1):
+                N[w][part:] = N[w][part:] + N[w - 1][:Wmax + 1 - part]
+        total = sum(int(N[w][W]) for w in range(Wmax + 1) for W in range(Wmax + 1))
+        if total >= max_queries or Wmax > 4096:
+            break
+    ends, ws = [], []
+    t = 0
+    for W in range(0, Wmax + 1):
+        for w in range(0, Wmax + 1):
+            c = int(N[w][W])
+            if c:
+                t += c
+                ends.append(t)
+                ws.append(w)
+        if t >= max_queries:
+            break
+    return np.array(ends, np.int64), np.array(ws, np.int64)
+
+
+def sum_weights(q, class_end, class_w):
+    """sum over blocks of sum_{t=1}^{q_b} w_t, from the class structure."""
+    q = np.asarray(q, np.int64)
+    full = np.concatenate([[0], np.cumsum((class_end - np.concatenate([[0], class_end[:-1]]))
+                                          * class_w)])
+    idx = np.searchsorted(class_end, q, side="left")  # class holding query q
+    start = np.concatenate([[0], class_end])[idx]
+    return int((full[idx] + (q - start) * class_w[idx]).sum())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled in the background."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index, period_ms=100):
+        self.gpu = gpu_index
+        self.period = period_ms
+        self.proc = None
+        self.lines = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", str(self.period)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+
+    def summary(self, t0, t1):
+        rows = []
+        for ts, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            rows.append((ts, parts))
+        inside = [p for ts, p in rows if t0 <= ts <= t1] or [p for _, p in rows]
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"],
+                    "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(p[1]) for p in inside if num(p[1]) is not None]
+        mx = [num(p[2]) for p in inside if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for p in inside:
+            for i, nm in enumerate(names):
+                if p[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(inside)}
+
+
+# ------------------------------------------------------------- CPU side
+
+def _oracle_worker(args):
+    H, llr, cap = args
+    import oracle
+    t = time.perf_counter()
+    _, q, ab, _ = oracle.decode_batch(H, llr, cap)
+    return time.perf_counter() - t, int(q.sum()), llr.shape[0]
+
+
+def cpu_sample(llr, per_point, step):
+    """Bounded sample: `per_point` blocks of each Eb/N0 point, the step-th
+    slice of each point's blocks (so steps see different blocks)."""
+    idx = []
+    for p in range(len(POINTS)):
+        base = p * B_PER_POINT
+        lo = (step * per_point) % max(1, B_PER_POINT - per_point)
+        idx.append(np.arange(base + lo, base + lo + per_point))
+    return llr[np.concatenate(idx)]
+
+
+def run_oracle(H, llr, cap, procs):
+    """Decode llr on `procs` spawned single-threaded oracle processes."""
+    if procs <= 1:
+        return _oracle_worker((H, llr, cap))
+    import multiprocessing as mp
+    chunks = np.array_split(llr, procs)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        res = pool.map(_oracle_worker, [(H, c, cap) for c in chunks])
+    return max(r[0] for r in res), sum(r[1] for r in res), sum(r[2] for r in res)
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    return "unknown"
+
+
+def bench_reference(args, rank, world):
+    """--impl reference: the CPU oracle as it stands, on the host cores, on
+    bounded samples of the same workload."""
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build_oracle()
+    code, llr = make_inputs(0)
+    cores = os.cpu_count() or 1
+    per_point = max(1, args.ref_sample // len(POINTS))
+    # the pool is started once, before any timing
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(cores)
+    times, blocks, queries = [], 0, 0
+    try:
+        for s in range(args.warmup + args.steps):
+            sample = cpu_sample(llr, per_point, s)
+            chunks = np.array_split(sample, cores)
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_worker, [(code.H, c, CAP) for c in chunks])
+            dt = time.perf_counter() - t0
+            if s >= args.warmup:
+                times.append(dt)
+                blocks += sample.shape[0]
+                queries += sum(r[1] for r in res)
+    finally:
+        pool.close()
+        pool.join()
+    total = sum(times)
+    value = blocks / total
+    line = {
+        "impl": "reference",
+        "metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-llr/u32-syndrome",
+        "data": "synthetic BPSK/AWGN, seeded",
+        "config": {"workload": WORKLOAD, "sample_blocks_per_step": sample.shape[0],
+                   "l2": "n/a (CPU)"},
+        "queries_per_s": queries / total,
+        "cpu_baseline": {"value": value, "unit": "blocks/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": "%d blocks per step (%d per Eb/N0 point), %d timed steps, "
+                                   "%d single-threaded oracle processes (%s)"
+                                   % (sample.shape[0], per_point, args.steps, cores,
+                                      cpu_model())},
+        "e2e": {"value": value, "unit": "blocks/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    return line
+
+
+# ------------------------------------------------------------- GPU side
+
+def bench_ours(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+    from paper_2202_13951_gb300 import build, orbg
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    orbg.load_library()
+
+    code, llr_np = make_inputs(rank)
+    B = llr_np.shape[0]
+    c = orbg.Code(code.H, max_query_cap=CAP)
+    cs = orbg.CodeSet([c])
+    llr = torch.from_numpy(llr_np).to(dev)
+    cw = torch.empty((B, code.n), dtype=torch.uint8, device=dev)
+    q = torch.empty((B,), dtype=torch.int32, device=dev)
+    ab = torch.empty((B,), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        orbg.orbg_decode_batched(cs.handle, None, None, llr, B, CAP, cw, None, q, ab, stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t_wall0 = time.time()
+    events[0].record(stream)
+    for i in range(args.steps):
+        step()
+        events[i + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    t_wall1 = time.time()
+    if world > 1:
+        dist.barrier()
+    sampler.stop()
+    per_step = [events[i].elapsed_time(events[i + 1]) for i in range(args.steps)]
+    local_ms = events[0].elapsed_time(events[-1])
+    total_ms = max_over_ranks(local_ms, world, dev)
+    blocks_total = sum_over_ranks(float(B * args.steps), world, dev)
+    value = blocks_total / (total_ms / 1000.0)
+
+    # work done per step, from this rank's last step
+    qh = q.cpu().numpy().astype(np.int64)
+    abh = ab.cpu().numpy()
+    q_step = int(qh.sum())
+    queries_total = sum_over_ranks(float(q_step * args.steps), world, dev)
+    ends, ws = class_weight_prefix(code.n, CAP)
+    sw = sum_weights(qh, ends, ws)
+    w32 = (code.r + 31) // 32
+    search_ops = w32 * (sw + q_step)            # w_t XORs + one zero test per word
+    sort_ops = B * code.n * math.ceil(math.log2(code.n))
+    alg_ops = search_ops + sort_ops
+    kernel_ms = statistics.mean(per_step)
+    achieved = alg_ops / (kernel_ms / 1000.0) / 1e12   # Tops/s
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    lanes = measured_int_lanes(orbg)
+    peak = lanes * SMS * SM_MAX_MHZ * 1e6 / 1e12 if lanes else None
+
+    clocks = sampler.summary(t_wall0, t_wall1)
+
+    # end to end: host (pinned) buffers through the same C call
+    e2e = None
+    if not args.no_e2e:
+        e2e = bench_e2e(orbg, cs, code, llr_np, B, args, world, dev)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup),
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-llr/u32-syndrome",
+        "data": "synthetic BPSK/AWGN, seeded (numpy PCG64); each rank its own seeds",
+        "config": {"workload": WORKLOAD, "blocks_per_step": B, "query_cap": CAP,
+                   "form": "batched persistent launch (orbg_decode_batched)",
+                   "l2": "inputs 203 MB > 129 MB L2, no flush",
+                   "launch_shape": list(orbg.orbg_get_launch_shape()),
+                   "parallelism": "replicas x%d (blocks sharded by rank, no collective)" % world},
+        "queries_per_s": queries_total / (total_ms / 1000.0),
+        "latency_ms": {"step_p50": statistics.median(per_step),
+                       "step_p99": float(np.percentile(per_step, 99)),
+                       "what": "one 400,000-block batch, launch to completion"},
+        "abandon_rate": float(abh.mean()),
+        "mean_queries": float(qh.mean()),
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "Tops/s", "frac": (achieved / peak) if peak else None,
+                     "traffic": None,
+                     "what": ("orbg_batched_kernel; algorithmic 32-bit integer ops per "
+                              "launch = sum_t W32 (w_t + 1) + B n ceil(log2 n) = %d; "
+                              "peak = measured LOP3 lanes/clk/SM (%s) x 152 SMs x "
+                              "2070 MHz" % (alg_ops, lanes))},
+        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
+                   "reasons": clocks["reasons"], "samples": clocks["samples"]},
+        "hbm_peak_gbs": peaks.get("hbm_gbs"),
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(code, llr_np)
+    if world > 1:
+        dist.destroy_process_group()
+    return line if rank == 0 else None
+
+
+def measured_int_lanes(orbg):
+    """LOP3 lanes per clock per SM, from the library's probe kernel."""
+    try:
+        return orbg.orbg_probe_int_lanes()
+    except Exception:
+        return None
+
+
+def bench_e2e(orbg, cs, code, llr_np, B, args, world, dev):
+    import torch
+    pin_llr = torch.empty(llr_np.shape, dtype=torch.float32, pin_memory=True)
+    pin_llr.numpy()[...] = llr_np
+    h_cw = torch.empty((B, code.n), dtype=torch.uint8, pin_memory=True)
+    h_q = torch.empty((B,), dtype=torch.int32, pin_memory=True)
+    h_ab = torch.empty((B,), dtype=torch.uint8, pin_memory=True)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        orbg.orbg_decode_batched(cs.handle, None, None, pin_llr, B, CAP, h_cw, None, h_q,
+                                 h_ab, stream)
+
+    for _ in range(2):
+        step()
+    steps = max(3, min(args.steps, 20))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()  # host-buffer calls synchronise before returning
+    dt = time.perf_counter() - t0
+    dt = max_over_ranks(dt, world, dev)
+    blocks = sum_over_ranks(float(B * steps), world, dev)
+    return {"value": blocks / dt, "unit": "blocks/s",
+            "h2d_bytes_per_step": int(B * code.n * 4),
+            "d2h_bytes_per_step": int(B * code.n + B * 4 + B),
+            "steps": steps,
+            "what": "orbg_decode_batched on pinned host buffers: H2D, kernel, D2H, sync"}
+
+
+def cpu_baseline(code, llr_np):
+    """The oracle as it stands, one process, on a bounded sample (~10 s)."""
+    import oracle
+    oracle.build_oracle()
+    per_point = 25_000
+    sample = cpu_sample(llr_np, per_point, 0)
+    dt, qsum, nb = run_oracle(code.H, sample, CAP, 1)
+    return {"value": nb / dt, "unit": "blocks/s", "cores": 1, "kind": "oracle",
+            "queries_per_s": qsum / dt,
+            "sample": "first %d blocks of each of the 4 Eb/N0 points (%d blocks), one "
+                      "single-threaded process on %s" % (per_point, nb, cpu_model())}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        line = bench_reference(args, rank, world)
+    else:
+        line = bench_ours(args, rank, world, local)
+    if line is not None and rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * orbg.h -- C ABI of the GB300 basic-ORBGRAND decoder.
+ *
+ * Basic ORBGRAND (Duffy, An, Medard, arXiv 2202.13951): for each received
+ * block, sort the bit positions by reliability |LLR| (Sec. III-A), query
+ * noise patterns z in increasing logistic weight w_L(z) = sum_i i z_i
+ * (Eq. lw, Eq. fractionation, Eq. intpart2), and return the first y (+) z
+ * that is a code-book member, i.e. whose syndrome H (y (+) z) is zero
+ * (Algorithm 1; membership of a linear code by a matrix multiply and
+ * compare, Sec. I), or abandon after the query cap (Sec. IV-A).
+ *
+ * Query order fixed by this library where the paper leaves ties arbitrary:
+ *   - bits with equal |LLR| are ordered by their received index;
+ *   - within one logistic weight W, patterns of lower Hamming weight come
+ *     first; within (W, w), flipped positions in lexicographic order (the
+ *     order the Landslide generator, Algorithm 2, produces);
+ *   - the zero pattern is query 1; hard decision y_i = 1 iff LLR_i > 0
+ *     (+0 and -0 give 0); +-Inf is allowed (most reliable).
+ *
+ * Conventions for every function:
+ *   - returns ORBG_OK (0) or a negative orbg_status; nothing is thrown;
+ *   - on error, output buffers are unspecified;
+ *   - abandonment is a per-block result, not an error;
+ *   - buffers are owned by the caller.  Each may be a device pointer or a
+ *     host pointer (detected per pointer).  With all buffers on the device
+ *     the call is asynchronous on `cuda_stream` (NULL = the legacy default
+ *     stream) and the buffers must stay valid until the stream reaches the
+ *     call's end.  With any host buffer the library stages the data through
+ *     device memory, copies results back and synchronises the stream before
+ *     returning.
+ */
+#ifndef ORBG_H
+#define ORBG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ORBG_API __attribute__((visibility("default")))
+#else
+#define ORBG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum orbg_status {
+    ORBG_OK = 0,
+    ORBG_EINVAL = -1,   /* null pointer, bad size, entry not 0/1, bad kind */
+    ORBG_ERANK = -2,    /* matrix rank differs from what n, k require */
+    ORBG_ELIMIT = -3,   /* n > 256, n-k > 128, or cap beyond the handle's reserve */
+    ORBG_ENAN = -4,     /* a NaN LLR was seen (reported by host-buffer calls) */
+    ORBG_ENOMEM = -5,   /* host or device allocation failed */
+    ORBG_ECUDA = -6,    /* a CUDA call failed; see orbg_last_cuda_error() */
+    ORBG_ETIMEOUT = -7  /* a bounded device wait ran out */
+} orbg_status;
+
+enum { ORBG_MAT_H = 0, ORBG_MAT_G = 1 };
+
+/* Limits of this version. */
+#define ORBG_MAX_N 256
+#define ORBG_MAX_R 128
+#define ORBG_MAX_QUERY_CAP (1u << 25)
+#define ORBG_DEFAULT_QUERY_CAP (1u << 20)
+
+/* Per-block values written to abandoned[b]. */
+#define ORBG_BLOCK_DECODED 0
+#define ORBG_BLOCK_ABANDONED 1
+#define ORBG_BLOCK_NAN 2       /* block had a NaN LLR: codeword = hard decision, queries = 0 */
+
+typedef struct orbg_code orbg_code;       /* opaque, library-owned */
+typedef struct orbg_codeset orbg_codeset; /* opaque, library-owned */
+
+/*
+ * Load a binary linear code of length n and dimension k.
+ *   mat   : host memory, row-major bytes, each 0 or 1; copied.
+ *           kind ORBG_MAT_H: (n-k) x n parity-check matrix, rank n-k.
+ *           kind ORBG_MAT_G: k x n generator matrix, rank k; the library
+ *           derives a parity-check matrix spanning its null space.
+ *   n     : 1..256;  n-k : 1..128.
+ *   max_query_cap : the largest query cap later decode calls may use
+ *           (0 = ORBG_DEFAULT_QUERY_CAP, at most ORBG_MAX_QUERY_CAP).  The
+ *           handle holds the query-order tables up to that depth.
+ *   out   : receives the handle.  It owns device copies of H and of the
+ *           tables on the device current at load time, until
+ *           orbg_free_code.  The load synchronises that device.
+ * Errors: EINVAL, ERANK, ELIMIT, ENOMEM, ECUDA.
+ * Paper: Algorithm 1's code-book membership function (Sec. I: matrix
+ * multiply and compare for a linear code).
+ */
+ORBG_API int orbg_load_code(const uint8_t *mat, int kind, int n, int k,
+                   uint32_t max_query_cap, orbg_code **out);
+
+/* Release a handle (NULL is allowed).  Not stream-ordered: no decode call
+ * using it may still be in flight. */
+ORBG_API int orbg_free_code(orbg_code *code);
+
+/* Copy of the handle's parity-check matrix, (n-k) x n row-major bytes, and
+ * its sizes; any output pointer may be NULL.  Host only, no CUDA call. */
+ORBG_API int orbg_code_info(const orbg_code *code, int *n, int *k,
+                   uint32_t *max_query_cap, uint8_t *H_out);
+
+/*
+ * Plain form: one launch, one warp per block, blocks in a static grid.
+ *   llr       : [B][n] FP32 LLRs, row-major, LLR = log f(Y|1)/f(Y|0).
+ *   B         : number of blocks (0 is a no-op).
+ *   query_cap : 1..max_query_cap of the handle; abandon after this many
+ *               queries (Sec. IV-A).  A hit at exactly query_cap decodes.
+ *   codeword  : [B][n] bytes 0/1: y (+) z* for the first hit z*, or the hard
+ *               decision y if abandoned.
+ *   queries   : [B] the 1-based index of the hit in the query order, or
+ *               query_cap if abandoned (0 for a NaN block).
+ *   abandoned : [B] ORBG_BLOCK_DECODED / _ABANDONED / _NAN.
+ * Errors: EINVAL, ELIMIT, ENOMEM, ECUDA; ENAN only for host-buffer calls
+ * (device-buffer calls report NaN blocks through abandoned[b] alone).
+ * Paper: Algorithm 1 with the basic ORBGRAND generator (Sec. III-B).
+ */
+ORBG_API int orbg_decode(const orbg_code *code, const float *llr, int64_t B,
+                uint32_t query_cap, uint8_t *codeword, uint32_t *queries,
+                uint8_t *abandoned, void *cuda_stream);
+
+/*
+ * A set of loaded codes that one batched launch may mix.  The codes must
+ * stay loaded while the set is used; the set holds a device copy of their
+ * descriptors (made synchronously here).  ncodes: 1..1024.
+ */
+ORBG_API int orbg_codeset_create(const orbg_code *const *codes, int ncodes,
+                        orbg_codeset **out);
+ORBG_API int orbg_codeset_free(orbg_codeset *set);
+
+/*
+ * Batched form: one persistent launch (about one CTA per SM and a few per
+ * SM more) whose warps pull blocks from an atomic work queue, so blocks with
+ * very different query counts, and blocks of different codes, balance.
+ *   code_id    : [B] index into the set per block, or NULL (all code 0).
+ *   llr_offset : [B] element offset of block b in llr, or NULL
+ *                (dense: b * n of code 0).
+ *   cw_offset  : [B] byte offset of block b in codeword, or NULL (dense).
+ *   Other arguments as orbg_decode; query_cap must be within every code's
+ *   max_query_cap.
+ * The call uses 64 bytes of stream-ordered device scratch (the work
+ * queue head), allocated and freed on cuda_stream.
+ * Results are identical to orbg_decode's block by block.
+ * Paper: Algorithm 1 per block; the batching is this library's.
+ */
+ORBG_API int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
+                        const int64_t *llr_offset, const float *llr,
+                        int64_t B, uint32_t query_cap, uint8_t *codeword,
+                        const int64_t *cw_offset, uint32_t *queries,
+                        uint8_t *abandoned, void *cuda_stream);
+
+/* Launch shape of the batched form: warps per CTA (1..16, 0 = default) and
+ * resident CTAs per SM (0 = as many as fit).  Process-wide. */
+ORBG_API int orbg_set_launch_shape(int warps_per_cta, int ctas_per_sm);
+ORBG_API int orbg_get_launch_shape(int *warps_per_cta, int *ctas_per_sm);
+
+/*
+ * The query order this library decodes in, for inspection and tests: the
+ * first `count` noise patterns for length n (1..256), expanded from the
+ * same tables the kernels read.  out: host memory, [count][n+1] int32 rows
+ * holding w, then the w flipped positions (1-based, in increasing
+ * reliability order, ascending), then zeros.  Returns the number of rows
+ * written (fewer than count once the 2^n patterns run out), or a negative
+ * status.  Host only, no CUDA call.  Paper: Sec. III-B (Eq. lw, Eq.
+ * fractionation, Eq. intpart), ties as read at the top of this header.
+ */
+ORBG_API int64_t orbg_query_order(int n, uint32_t count, int32_t *out);
+
+/* Static description of a status code (never NULL). */
+ORBG_API const char *orbg_status_string(int status);
+
+/* The last CUDA error code seen by this thread (0 if none). */
+ORBG_API int orbg_last_cuda_error(void);
+
+/* Library version, e.g. 100 for 0.1.0. */
+ORBG_API int orbg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ORBG_H */

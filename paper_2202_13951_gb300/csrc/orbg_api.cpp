@@ -1,0 +1,506 @@
+/*
+ * orbg_api.cpp -- the C ABI of include/orbg.h: code loading (validation,
+ * GF(2) rank / null space, column packing, query-order tables, upload),
+ * argument checking, host-buffer staging and kernel launches.
+ */
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/orbg.h"
+#include "orbg_internal.h"
+
+struct orbg_code {
+    int n, k, r, w32;
+    uint32_t max_cap;
+    int device;
+    std::vector<uint8_t> H;      /* r x n as used */
+    uint32_t *d_hcol = nullptr;
+    OrbgRun *d_runs = nullptr;
+    uint32_t *d_floor = nullptr;
+    OrbgDeviceCode dev;
+};
+
+struct orbg_codeset {
+    int ncodes, n_max, w32_max;
+    std::vector<int> n_of;       /* n of each code, host copy */
+    uint32_t cap_min;
+    int device;
+    OrbgDeviceCode *d_codes = nullptr;
+};
+
+namespace {
+
+thread_local int g_last_cuda = 0;
+std::mutex g_shape_mu;
+int g_wpc = 8;
+int g_ctas_per_sm = 0;
+
+int cuda_fail(cudaError_t e)
+{
+    g_last_cuda = (int)e;
+    return e == cudaErrorMemoryAllocation ? ORBG_ENOMEM : ORBG_ECUDA;
+}
+
+
+/* Is p device-accessible memory the kernels may use directly? */
+bool is_device_ptr(const void *p)
+{
+    if (!p)
+        return true;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError(); /* clear: plain host pointers on old runtimes */
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+/* A device mirror of a caller buffer that lives on the host. */
+struct Staged {
+    void *host = nullptr;
+    void *dev = nullptr;
+    size_t bytes = 0;
+    bool copy_in = false, copy_out = false;
+};
+
+struct Stager {
+    std::vector<Staged> items;
+    cudaStream_t st;
+    explicit Stager(cudaStream_t s) : st(s) {}
+    /* returns device pointer to use for p */
+    template <typename T>
+    int add(T *p, size_t bytes, bool in, bool out, T **dev_out)
+    {
+        if (!p || bytes == 0 || is_device_ptr(p)) {
+            *dev_out = p;
+            return ORBG_OK;
+        }
+        Staged s;
+        s.host = (void *)p;
+        s.bytes = bytes;
+        s.copy_in = in;
+        s.copy_out = out;
+        cudaError_t e = cudaMallocAsync(&s.dev, bytes, st);
+        if (e != cudaSuccess)
+            return cuda_fail(e);
+        items.push_back(s);
+        if (in) {
+            e = cudaMemcpyAsync(s.dev, s.host, bytes, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess)
+                return cuda_fail(e);
+        }
+        *dev_out = (T *)s.dev;
+        return ORBG_OK;
+    }
+    bool any() const { return !items.empty(); }
+    int finish(bool ok)
+    {
+        int rc = ORBG_OK;
+        for (auto &s : items) {
+            if (ok && s.copy_out) {
+                cudaError_t e = cudaMemcpyAsync(s.host, s.dev, s.bytes, cudaMemcpyDeviceToHost, st);
+                if (e != cudaSuccess && rc == ORBG_OK)
+                    rc = cuda_fail(e);
+            }
+        }
+        for (auto &s : items)
+            cudaFreeAsync(s.dev, st);
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess && rc == ORBG_OK)
+            rc = cuda_fail(e);
+        items.clear();
+        return rc;
+    }
+};
+
+void free_code_device(orbg_code *c)
+{
+    if (c->d_hcol) cudaFree(c->d_hcol);
+    if (c->d_runs) cudaFree(c->d_runs);
+    if (c->d_floor) cudaFree(c->d_floor);
+    c->d_hcol = nullptr;
+    c->d_runs = nullptr;
+    c->d_floor = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *orbg_status_string(int status)
+{
+    switch (status) {
+    case ORBG_OK: return "ok";
+    case ORBG_EINVAL: return "invalid argument";
+    case ORBG_ERANK: return "matrix rank does not match n and k";
+    case ORBG_ELIMIT: return "size or query cap beyond this library's limits";
+    case ORBG_ENAN: return "NaN log-likelihood ratio";
+    case ORBG_ENOMEM: return "out of memory";
+    case ORBG_ECUDA: return "CUDA error";
+    case ORBG_ETIMEOUT: return "bounded device wait ran out";
+    default: return "unknown status";
+    }
+}
+
+int orbg_last_cuda_error(void) { return g_last_cuda; }
+
+int orbg_version(void) { return 100; }
+
+int64_t orbg_query_order(int n, uint32_t count, int32_t *out)
+{
+    if (n < 1 || n > ORBG_MAX_N || (count > 0 && !out))
+        return ORBG_EINVAL;
+    if (count == 0)
+        return 0;
+    OrbgTables tb;
+    if (orbg_build_tables(n, count, &tb) != 0)
+        return ORBG_ELIMIT;
+    const size_t stride = (size_t)n + 1;
+    uint64_t total = std::min<uint64_t>(tb.patterns, count);
+    std::memset(out, 0, sizeof(int32_t) * stride * (size_t)total);
+    for (const OrbgRun &r : tb.runs) {
+        for (int j = 0; j < r.len; j++) {
+            uint64_t t = (uint64_t)r.tstart + (uint64_t)j;
+            if (t > total)
+                break;
+            int32_t *row = out + (t - 1) * stride;
+            int w = 0;
+            for (int i = 0; i < r.npre; i++)
+                row[1 + w++] = (int32_t)r.pre[i] + 1;
+            int a = (int)r.a0 + j;
+            if (a < n) {
+                row[1 + w++] = a + 1;
+                row[1 + w++] = (int)r.pair_sum - a + 1;
+            }
+            row[0] = w;
+        }
+    }
+    return (int64_t)total;
+}
+
+int orbg_set_launch_shape(int warps_per_cta, int ctas_per_sm)
+{
+    if (warps_per_cta < 0 || warps_per_cta > 16 || ctas_per_sm < 0 || ctas_per_sm > 64)
+        return ORBG_EINVAL;
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    g_wpc = warps_per_cta ? warps_per_cta : 8;
+    g_ctas_per_sm = ctas_per_sm;
+    return ORBG_OK;
+}
+
+int orbg_get_launch_shape(int *warps_per_cta, int *ctas_per_sm)
+{
+    std::lock_guard<std::mutex> lk(g_shape_mu);
+    if (warps_per_cta) *warps_per_cta = g_wpc;
+    if (ctas_per_sm) *ctas_per_sm = g_ctas_per_sm;
+    return ORBG_OK;
+}
+
+int orbg_load_code(const uint8_t *mat, int kind, int n, int k, uint32_t max_query_cap,
+                   orbg_code **out)
+{
+    if (!out)
+        return ORBG_EINVAL;
+    *out = nullptr;
+    if (!mat || (kind != ORBG_MAT_H && kind != ORBG_MAT_G) || n < 1 || k < 0 || k >= n)
+        return ORBG_EINVAL;
+    if (n > ORBG_MAX_N || n - k > ORBG_MAX_R)
+        return ORBG_ELIMIT;
+    uint32_t cap = max_query_cap ? max_query_cap : ORBG_DEFAULT_QUERY_CAP;
+    if (cap > ORBG_MAX_QUERY_CAP)
+        return ORBG_ELIMIT;
+    const int r = n - k;
+    const int rows = kind == ORBG_MAT_H ? r : k;
+    for (size_t i = 0; i < (size_t)rows * n; i++)
+        if (mat[i] > 1)
+            return ORBG_EINVAL;
+
+    orbg_code *c = new (std::nothrow) orbg_code();
+    if (!c)
+        return ORBG_ENOMEM;
+    c->n = n;
+    c->k = k;
+    c->r = r;
+    c->w32 = r <= 32 ? 1 : r <= 64 ? 2 : 4;
+    c->max_cap = cap;
+    if (kind == ORBG_MAT_H) {
+        if (orbg_gf2_rank(mat, r, n) != r) {
+            delete c;
+            return ORBG_ERANK;
+        }
+        c->H.assign(mat, mat + (size_t)r * n);
+    } else {
+        if (k > 0 && orbg_gf2_rank(mat, k, n) != k) {
+            delete c;
+            return ORBG_ERANK;
+        }
+        int dim = 0;
+        if (k == 0) {
+            c->H.assign((size_t)n * n, 0);
+            for (int i = 0; i < n; i++)
+                c->H[(size_t)i * n + i] = 1;
+            dim = n;
+        } else {
+            orbg_gf2_nullspace(mat, k, n, &c->H, &dim);
+        }
+        if (dim != r) {
+            delete c;
+            return ORBG_ERANK;
+        }
+    }
+    /* columns, bit-packed: word x of column j holds rows 32x .. 32x+31 */
+    std::vector<uint32_t> hcol((size_t)n * c->w32, 0);
+    for (int i = 0; i < r; i++)
+        for (int j = 0; j < n; j++)
+            if (c->H[(size_t)i * n + j])
+                hcol[(size_t)j * c->w32 + i / 32] |= 1u << (i % 32);
+    OrbgTables tb;
+    int trc = orbg_build_tables(n, cap, &tb);
+    if (trc != 0) {
+        delete c;
+        return ORBG_ELIMIT;
+    }
+    cudaError_t e;
+    if ((e = cudaGetDevice(&c->device)) != cudaSuccess) {
+        delete c;
+        return cuda_fail(e);
+    }
+    size_t hb = hcol.size() * sizeof(uint32_t);
+    size_t rb = tb.runs.size() * sizeof(OrbgRun);
+    size_t fb = tb.group_floor.size() * sizeof(uint32_t);
+    if ((e = cudaMalloc(&c->d_hcol, hb)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_runs, rb)) != cudaSuccess ||
+        (e = cudaMalloc(&c->d_floor, fb)) != cudaSuccess ||
+        (e = cudaMemcpy(c->d_hcol, hcol.data(), hb, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c->d_runs, tb.runs.data(), rb, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(c->d_floor, tb.group_floor.data(), fb, cudaMemcpyHostToDevice)) !=
+            cudaSuccess) {
+        free_code_device(c);
+        delete c;
+        return cuda_fail(e);
+    }
+    c->dev.hcol = c->d_hcol;
+    c->dev.runs = c->d_runs;
+    c->dev.group_floor = c->d_floor;
+    c->dev.nruns = (uint32_t)tb.runs.size();
+    c->dev.ngroups = (uint32_t)tb.group_floor.size();
+    c->dev.max_cap = cap;
+    c->dev.n = n;
+    c->dev.r = r;
+    c->dev.w32 = c->w32;
+    *out = c;
+    return ORBG_OK;
+}
+
+int orbg_free_code(orbg_code *code)
+{
+    if (!code)
+        return ORBG_OK;
+    free_code_device(code);
+    delete code;
+    return ORBG_OK;
+}
+
+int orbg_code_info(const orbg_code *code, int *n, int *k, uint32_t *max_query_cap,
+                   uint8_t *H_out)
+{
+    if (!code)
+        return ORBG_EINVAL;
+    if (n) *n = code->n;
+    if (k) *k = code->k;
+    if (max_query_cap) *max_query_cap = code->max_cap;
+    if (H_out) std::memcpy(H_out, code->H.data(), code->H.size());
+    return ORBG_OK;
+}
+
+int orbg_decode(const orbg_code *code, const float *llr, int64_t B, uint32_t query_cap,
+                uint8_t *codeword, uint32_t *queries, uint8_t *abandoned, void *cuda_stream)
+{
+    if (!code || B < 0)
+        return ORBG_EINVAL;
+    if (query_cap < 1)
+        return ORBG_EINVAL;
+    if (query_cap > code->max_cap)
+        return ORBG_ELIMIT;
+    if (B == 0)
+        return ORBG_OK;
+    if (!llr || !codeword || !queries || !abandoned)
+        return ORBG_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const size_t nb = (size_t)B * code->n;
+    Stager sg(st);
+    const float *d_llr;
+    uint8_t *d_cw, *d_ab;
+    uint32_t *d_q;
+    int rc;
+    if ((rc = sg.add(llr, nb * sizeof(float), true, false, &d_llr)) ||
+        (rc = sg.add(codeword, nb, false, true, &d_cw)) ||
+        (rc = sg.add(queries, (size_t)B * sizeof(uint32_t), false, true, &d_q)) ||
+        (rc = sg.add(abandoned, (size_t)B, false, true, &d_ab))) {
+        sg.finish(false);
+        return rc;
+    }
+    int e = orbg_launch_plain(code->dev, d_llr, B, query_cap, d_cw, d_q, d_ab, st);
+    if (e != 0) {
+        sg.finish(false);
+        return cuda_fail((cudaError_t)e);
+    }
+    if (!sg.any())
+        return ORBG_OK;
+    rc = sg.finish(true);
+    if (rc)
+        return rc;
+    if (!is_device_ptr(abandoned))
+        for (int64_t b = 0; b < B; b++)
+            if (abandoned[b] == ORBG_BLOCK_NAN)
+                return ORBG_ENAN;
+    return ORBG_OK;
+}
+
+int orbg_codeset_create(const orbg_code *const *codes, int ncodes, orbg_codeset **out)
+{
+    if (!out)
+        return ORBG_EINVAL;
+    *out = nullptr;
+    if (!codes || ncodes < 1 || ncodes > 1024)
+        return ORBG_EINVAL;
+    std::vector<OrbgDeviceCode> descs((size_t)ncodes);
+    orbg_codeset *s = new (std::nothrow) orbg_codeset();
+    if (!s)
+        return ORBG_ENOMEM;
+    s->ncodes = ncodes;
+    s->n_max = 0;
+    s->w32_max = 1;
+    s->cap_min = 0xFFFFFFFFu;
+    for (int i = 0; i < ncodes; i++) {
+        if (!codes[i]) {
+            delete s;
+            return ORBG_EINVAL;
+        }
+        descs[i] = codes[i]->dev;
+        s->n_of.push_back(codes[i]->n);
+        s->n_max = std::max(s->n_max, codes[i]->n);
+        s->w32_max = std::max(s->w32_max, codes[i]->w32);
+        s->cap_min = std::min(s->cap_min, codes[i]->max_cap);
+    }
+    cudaError_t e;
+    if ((e = cudaGetDevice(&s->device)) != cudaSuccess ||
+        (e = cudaMalloc(&s->d_codes, descs.size() * sizeof(OrbgDeviceCode))) != cudaSuccess ||
+        (e = cudaMemcpy(s->d_codes, descs.data(), descs.size() * sizeof(OrbgDeviceCode),
+                        cudaMemcpyHostToDevice)) != cudaSuccess) {
+        if (s->d_codes) cudaFree(s->d_codes);
+        delete s;
+        return cuda_fail(e);
+    }
+    *out = s;
+    return ORBG_OK;
+}
+
+int orbg_codeset_free(orbg_codeset *set)
+{
+    if (!set)
+        return ORBG_OK;
+    if (set->d_codes)
+        cudaFree(set->d_codes);
+    delete set;
+    return ORBG_OK;
+}
+
+int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
+                        const int64_t *llr_offset, const float *llr, int64_t B,
+                        uint32_t query_cap, uint8_t *codeword, const int64_t *cw_offset,
+                        uint32_t *queries, uint8_t *abandoned, void *cuda_stream)
+{
+    if (!set || B < 0 || query_cap < 1)
+        return ORBG_EINVAL;
+    if (query_cap > set->cap_min)
+        return ORBG_ELIMIT;
+    if (B == 0)
+        return ORBG_OK;
+    if (!llr || !codeword || !queries || !abandoned)
+        return ORBG_EINVAL;
+    if ((llr_offset == nullptr) != (cw_offset == nullptr))
+        return ORBG_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    /* element counts: dense layout, or as far as the largest offset reaches */
+    size_t n_llr, n_cw;
+    if (!llr_offset) {
+        n_llr = n_cw = (size_t)B * set->n_of[0];
+    } else {
+        if (!is_device_ptr(llr_offset) || !is_device_ptr(cw_offset) ||
+            (code_id && !is_device_ptr(code_id))) {
+            /* host-side layout arrays: find extents for staging */
+            if (is_device_ptr(llr_offset) || is_device_ptr(cw_offset) ||
+                (code_id && is_device_ptr(code_id)))
+                return ORBG_EINVAL;
+            int64_t hi_l = 0, hi_c = 0;
+            for (int64_t b = 0; b < B; b++) {
+                int cid = code_id ? code_id[b] : 0;
+                if (cid < 0 || cid >= set->ncodes || llr_offset[b] < 0 || cw_offset[b] < 0)
+                    return ORBG_EINVAL;
+                hi_l = std::max(hi_l, llr_offset[b] + set->n_of[cid]);
+                hi_c = std::max(hi_c, cw_offset[b] + set->n_of[cid]);
+            }
+            n_llr = (size_t)hi_l;
+            n_cw = (size_t)hi_c;
+        } else {
+            if (!is_device_ptr(llr) || !is_device_ptr(codeword))
+                return ORBG_EINVAL; /* device layout arrays need device data */
+            n_llr = n_cw = 0;
+        }
+    }
+    Stager sg(st);
+    const float *d_llr;
+    uint8_t *d_cw, *d_ab;
+    uint32_t *d_q;
+    const int32_t *d_cid;
+    const int64_t *d_lo, *d_co;
+    int rc;
+    if ((rc = sg.add(code_id, code_id ? (size_t)B * sizeof(int32_t) : 0, true, false, &d_cid)) ||
+        (rc = sg.add(llr_offset, llr_offset ? (size_t)B * sizeof(int64_t) : 0, true, false,
+                     &d_lo)) ||
+        (rc = sg.add(cw_offset, cw_offset ? (size_t)B * sizeof(int64_t) : 0, true, false,
+                     &d_co)) ||
+        (rc = sg.add(llr, n_llr * sizeof(float), true, false, &d_llr)) ||
+        (rc = sg.add(codeword, n_cw, false, true, &d_cw)) ||
+        (rc = sg.add(queries, (size_t)B * sizeof(uint32_t), false, true, &d_q)) ||
+        (rc = sg.add(abandoned, (size_t)B, false, true, &d_ab))) {
+        sg.finish(false);
+        return rc;
+    }
+    unsigned long long *counter = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&counter, 64, st);
+    if (e != cudaSuccess) {
+        sg.finish(false);
+        return cuda_fail(e);
+    }
+    int wpc, cps;
+    orbg_get_launch_shape(&wpc, &cps);
+    int le = orbg_launch_batched(set->d_codes, set->ncodes, set->n_max, set->w32_max, d_cid,
+                                 d_lo, d_llr, B, query_cap, d_cw, d_co, d_q, d_ab, counter, wpc,
+                                 cps, st);
+    cudaFreeAsync(counter, st);
+    if (le != 0) {
+        sg.finish(false);
+        return cuda_fail((cudaError_t)le);
+    }
+    if (!sg.any())
+        return ORBG_OK;
+    rc = sg.finish(true);
+    if (rc)
+        return rc;
+    if (!is_device_ptr(abandoned))
+        for (int64_t b = 0; b < B; b++)
+            if (abandoned[b] == ORBG_BLOCK_NAN)
+                return ORBG_ENAN;
+    return ORBG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,297 @@
+"""Python binding of the C ABI in include/orbg.h (ctypes).
+
+Argument marshalling only: every step of the decode runs in the CUDA
+library.  Names match the C functions.  Array arguments may be torch
+tensors (CUDA or CPU) or NumPy arrays; they must be contiguous with the C
+type's dtype.  There is no fallback: if liborbg.so is missing or a CUDA
+call fails, these functions raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ORBG_OK = 0
+ORBG_EINVAL = -1
+ORBG_ERANK = -2
+ORBG_ELIMIT = -3
+ORBG_ENAN = -4
+ORBG_ENOMEM = -5
+ORBG_ECUDA = -6
+ORBG_ETIMEOUT = -7
+ORBG_MAT_H = 0
+ORBG_MAT_G = 1
+ORBG_MAX_N = 256
+ORBG_MAX_R = 128
+ORBG_MAX_QUERY_CAP = 1 << 25
+ORBG_DEFAULT_QUERY_CAP = 1 << 20
+ORBG_BLOCK_DECODED = 0
+ORBG_BLOCK_ABANDONED = 1
+ORBG_BLOCK_NAN = 2
+
+LIB_PATH = _build.LIB
+_lib = None
+
+
+class OrbgError(RuntimeError):
+    def __init__(self, status, what=""):
+        self.status = status
+        msg = "%s: %s (%d)" % (what, _status_string(status), status)
+        if status == ORBG_ECUDA and _lib is not None:
+            msg += " [cuda error %d]" % _lib.orbg_last_cuda_error()
+        super().__init__(msg)
+
+
+def _status_string(s):
+    if _lib is None:
+        return "status"
+    return _lib.orbg_status_string(s).decode()
+
+
+def load_library(path=None):
+    """Load liborbg.so (built by paper_2202_13951_gb300.build)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("CUDA library %s is not built; run "
+                           "paper_2202_13951_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    u32 = ctypes.c_uint32
+    i32 = ctypes.c_int
+    i64 = ctypes.c_int64
+    lib.orbg_load_code.argtypes = [vp, i32, i32, i32, u32, ctypes.POINTER(vp)]
+    lib.orbg_free_code.argtypes = [vp]
+    lib.orbg_code_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                   ctypes.POINTER(u32), vp]
+    lib.orbg_decode.argtypes = [vp, vp, i64, u32, vp, vp, vp, vp]
+    lib.orbg_codeset_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
+    lib.orbg_codeset_free.argtypes = [vp]
+    lib.orbg_decode_batched.argtypes = [vp, vp, vp, vp, i64, u32, vp, vp, vp, vp, vp]
+    lib.orbg_set_launch_shape.argtypes = [i32, i32]
+    lib.orbg_get_launch_shape.argtypes = [ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.orbg_status_string.argtypes = [i32]
+    lib.orbg_status_string.restype = ctypes.c_char_p
+    lib.orbg_last_cuda_error.argtypes = []
+    lib.orbg_version.argtypes = []
+    lib.orbg_query_order.argtypes = [i32, u32, vp]
+    lib.orbg_query_order.restype = i64
+    for f in ("orbg_load_code", "orbg_free_code", "orbg_code_info", "orbg_decode",
+              "orbg_codeset_create", "orbg_codeset_free", "orbg_decode_batched",
+              "orbg_set_launch_shape", "orbg_get_launch_shape",
+              "orbg_last_cuda_error", "orbg_version"):
+        getattr(lib, f).restype = i32
+    if path == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+def _check(rc, what):
+    if rc != ORBG_OK:
+        raise OrbgError(rc, what)
+
+
+def _ok(dtype):
+    # query counts are below 2^31, so an int32 buffer holds them bit-exactly
+    return ("uint32", "int32") if dtype == "uint32" else (dtype,)
+
+
+def _ptr(a, dtype=None):
+    """Address of a torch tensor / NumPy array (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):  # torch
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if dtype is not None and str(a.dtype).replace("torch.", "") not in _ok(dtype):
+            raise TypeError("expected dtype %s, got %s" % (dtype, a.dtype))
+        return a.data_ptr() or None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        if dtype is not None and str(a.dtype) not in _ok(dtype):
+            raise TypeError("expected dtype %s, got %s" % (dtype, a.dtype))
+        return a.ctypes.data or None
+    if isinstance(a, int):
+        return a
+    raise TypeError("unsupported buffer type %r" % type(a))
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream or None
+    return int(s) or None
+
+
+# ------------------------------------------------------------- the C names
+
+def orbg_load_code(mat, kind, n, k, max_query_cap=0):
+    lib = load_library()
+    m = np.ascontiguousarray(mat, dtype=np.uint8)
+    h = ctypes.c_void_p()
+    _check(lib.orbg_load_code(m.ctypes.data, int(kind), int(n), int(k),
+                              int(max_query_cap), ctypes.byref(h)), "orbg_load_code")
+    return h
+
+
+def orbg_free_code(code):
+    _check(load_library().orbg_free_code(code), "orbg_free_code")
+
+
+def orbg_code_info(code):
+    lib = load_library()
+    n = ctypes.c_int()
+    k = ctypes.c_int()
+    cap = ctypes.c_uint32()
+    _check(lib.orbg_code_info(code, ctypes.byref(n), ctypes.byref(k),
+                              ctypes.byref(cap), None), "orbg_code_info")
+    H = np.zeros((n.value - k.value, n.value), np.uint8)
+    _check(lib.orbg_code_info(code, None, None, None, H.ctypes.data), "orbg_code_info")
+    return n.value, k.value, cap.value, H
+
+
+def orbg_decode(code, llr, B, query_cap, codeword, queries, abandoned, cuda_stream=None):
+    rc = load_library().orbg_decode(code, _ptr(llr, "float32"), int(B), int(query_cap),
+                                    _ptr(codeword, "uint8"), _ptr(queries, "uint32"),
+                                    _ptr(abandoned, "uint8"), _stream(cuda_stream))
+    _check(rc, "orbg_decode")
+
+
+def orbg_codeset_create(codes):
+    lib = load_library()
+    arr = (ctypes.c_void_p * len(codes))(*[c.value if hasattr(c, "value") else c
+                                           for c in codes])
+    h = ctypes.c_void_p()
+    _check(lib.orbg_codeset_create(arr, len(codes), ctypes.byref(h)), "orbg_codeset_create")
+    return h
+
+
+def orbg_codeset_free(cs):
+    _check(load_library().orbg_codeset_free(cs), "orbg_codeset_free")
+
+
+def orbg_decode_batched(cs, code_id, llr_offset, llr, B, query_cap, codeword, cw_offset,
+                        queries, abandoned, cuda_stream=None):
+    rc = load_library().orbg_decode_batched(
+        cs, _ptr(code_id, "int32"), _ptr(llr_offset, "int64"), _ptr(llr, "float32"), int(B),
+        int(query_cap), _ptr(codeword, "uint8"), _ptr(cw_offset, "int64"),
+        _ptr(queries, "uint32"), _ptr(abandoned, "uint8"), _stream(cuda_stream))
+    _check(rc, "orbg_decode_batched")
+
+
+def orbg_set_launch_shape(warps_per_cta=0, ctas_per_sm=0):
+    _check(load_library().orbg_set_launch_shape(int(warps_per_cta), int(ctas_per_sm)),
+           "orbg_set_launch_shape")
+
+
+def orbg_get_launch_shape():
+    a = ctypes.c_int()
+    b = ctypes.c_int()
+    _check(load_library().orbg_get_launch_shape(ctypes.byref(a), ctypes.byref(b)),
+           "orbg_get_launch_shape")
+    return a.value, b.value
+
+
+def orbg_status_string(status):
+    return load_library().orbg_status_string(int(status)).decode()
+
+
+def orbg_last_cuda_error():
+    return load_library().orbg_last_cuda_error()
+
+
+def orbg_version():
+    return load_library().orbg_version()
+
+
+def orbg_query_order(n, count):
+    """First `count` patterns of the decoder's query order for length n, as
+    tuples of 1-based sorted-order positions."""
+    lib = load_library()
+    out = np.zeros((count, n + 1), np.int32)
+    got = lib.orbg_query_order(int(n), int(count), out.ctypes.data)
+    if got < 0:
+        raise OrbgError(int(got), "orbg_query_order")
+    return [tuple(int(x) for x in row[1:1 + row[0]]) for row in out[:got]]
+
+
+# ------------------------------------------------------- convenience layer
+
+class Code:
+    """Owning wrapper of an orbg_code handle."""
+
+    def __init__(self, mat, kind=ORBG_MAT_H, n=None, k=None, max_query_cap=0):
+        mat = np.asarray(mat, dtype=np.uint8)
+        n = mat.shape[1] if n is None else n
+        if k is None:
+            k = n - mat.shape[0] if kind == ORBG_MAT_H else mat.shape[0]
+        self.n, self.k = int(n), int(k)
+        self.handle = orbg_load_code(mat, kind, n, k, max_query_cap)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            orbg_free_code(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class CodeSet:
+    def __init__(self, codes):
+        self.codes = list(codes)
+        self.handle = orbg_codeset_create([c.handle for c in self.codes])
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            orbg_codeset_free(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def decode(code, llr, query_cap, stream=None):
+    """Plain form on a torch tensor llr[B][n] (CUDA): returns (codeword u8,
+    queries int32, abandoned u8) tensors on the same device."""
+    import torch
+    B = llr.shape[0]
+    cw = torch.empty((B, code.n), dtype=torch.uint8, device=llr.device)
+    q = torch.empty((B,), dtype=torch.int32, device=llr.device)
+    ab = torch.empty((B,), dtype=torch.uint8, device=llr.device)
+    orbg_decode(code.handle, llr, B, query_cap, cw, q, ab,
+                stream if stream is not None else torch.cuda.current_stream(llr.device))
+    return cw, q, ab
+
+
+def decode_batched(codeset, llr, query_cap, code_id=None, llr_offset=None,
+                   cw_offset=None, n_total=None, stream=None):
+    """Batched persistent form.  Dense single-code layout when the offsets
+    are None; otherwise n_total is the codeword buffer length."""
+    import torch
+    dev = llr.device
+    if llr_offset is None:
+        n = codeset.codes[0].n
+        B = llr.numel() // n
+        cw = torch.empty((B, n), dtype=torch.uint8, device=dev)
+    else:
+        B = llr_offset.shape[0]
+        cw = torch.empty((n_total,), dtype=torch.uint8, device=dev)
+    q = torch.empty((B,), dtype=torch.int32, device=dev)
+    ab = torch.empty((B,), dtype=torch.uint8, device=dev)
+    orbg_decode_batched(codeset.handle, code_id, llr_offset, llr, B, query_cap, cw,
+                        cw_offset, q, ab,
+                        stream if stream is not None else torch.cuda.current_stream(dev))
+    return cw, q, ab

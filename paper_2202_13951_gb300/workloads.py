@@ -269,7 +269,10 @@ def sigma_for(ebn0_db, rate):
 
 
 def encode(G, info):
-    return ((info.astype(np.int64) @ G.astype(np.int64)) % 2).astype(np.uint8)
+    """c = m G over GF(2).  The product is taken in float32, which is exact
+    here (every sum is an integer <= k <= 256), then reduced mod 2."""
+    prod = info.astype(np.float32) @ G.astype(np.float32)
+    return (prod.astype(np.int64) % 2).astype(np.uint8)
 
 
 def awgn_llr(code: Code, B: int, ebn0_db, seed: int, zero_info=False):

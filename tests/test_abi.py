@@ -1,0 +1,113 @@
+"""The C-ABI library builds, loads and exports every symbol include/orbg.h
+declares; host-only entry points behave (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_13951_gb300 import build, orbg, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "orbg.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return orbg.load_library()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(orbg_\w+)\s*\(", src)))
+
+
+def test_header_compiles_as_c_and_cxx():
+    for lang, std in (("c", "-std=c99"), ("c++", "-std=c++17")):
+        subprocess.check_call(["gcc", "-x", lang, std, "-fsyntax-only", "-Wall",
+                               "-Werror", HEADER])
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 13
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings_and_version(lib):
+    for s in range(-7, 1):
+        assert orbg.orbg_status_string(s) not in ("", "unknown status")
+    assert orbg.orbg_status_string(-99) == "unknown status"
+    assert orbg.orbg_version() == 100
+
+
+def test_launch_shape_roundtrip(lib):
+    old = orbg.orbg_get_launch_shape()
+    orbg.orbg_set_launch_shape(4, 2)
+    assert orbg.orbg_get_launch_shape() == (4, 2)
+    with pytest.raises(orbg.OrbgError):
+        orbg.orbg_set_launch_shape(17, 0)
+    orbg.orbg_set_launch_shape(*old)
+
+
+def test_load_code_rejects_bad_input_before_any_cuda_call(lib):
+    H = workloads.hamming74().H
+    cases = [
+        (H, 7, 7, 4, orbg.ORBG_EINVAL),          # kind
+        (H, orbg.ORBG_MAT_H, 0, 0, orbg.ORBG_EINVAL),
+        (H, orbg.ORBG_MAT_H, 7, 7, orbg.ORBG_EINVAL),  # k >= n
+        (np.full_like(H, 2), orbg.ORBG_MAT_H, 7, 4, orbg.ORBG_EINVAL),
+        (np.zeros((3, 300), np.uint8), orbg.ORBG_MAT_H, 300, 297, orbg.ORBG_ELIMIT),
+        (np.zeros((129, 200), np.uint8), orbg.ORBG_MAT_H, 200, 71, orbg.ORBG_ELIMIT),
+        (np.vstack([H[:2], H[:1]]), orbg.ORBG_MAT_H, 7, 4, orbg.ORBG_ERANK),
+    ]
+    for mat, kind, n, k, want in cases:
+        with pytest.raises(orbg.OrbgError) as ei:
+            orbg.orbg_load_code(mat, kind, n, k)
+        assert ei.value.status == want, (kind, n, k)
+    with pytest.raises(orbg.OrbgError) as ei:
+        orbg.orbg_load_code(H, orbg.ORBG_MAT_H, 7, 4, orbg.ORBG_MAX_QUERY_CAP + 1)
+    assert ei.value.status == orbg.ORBG_ELIMIT
+    # null output pointer
+    rc = lib.orbg_load_code(H.ctypes.data, 0, 7, 4, 0, None)
+    assert rc == orbg.ORBG_EINVAL
+
+
+def test_decode_argument_checks_without_gpu(lib):
+    # NULL code handle and negative sizes fail before any CUDA call
+    assert lib.orbg_decode(None, None, 1, 10, None, None, None, None) == orbg.ORBG_EINVAL
+    assert lib.orbg_decode_batched(None, None, None, None, 1, 10, None, None, None, None,
+                                   None) == orbg.ORBG_EINVAL
+    assert lib.orbg_code_info(None, None, None, None, None) == orbg.ORBG_EINVAL
+    assert lib.orbg_free_code(None) == orbg.ORBG_OK
+    assert lib.orbg_codeset_free(None) == orbg.ORBG_OK
+
+
+@pytest.mark.parametrize("n,count", [(1, 2), (3, 8), (7, 128), (12, 4096),
+                                     (16, 65536), (64, 150000), (127, 150000),
+                                     (128, 150000), (256, 40000)])
+def test_query_order_tables_match_oracle(lib, n, count):
+    """The tables the kernels walk expand to exactly the oracle's order."""
+    assert orbg.orbg_query_order(n, count) == oracle.enumerate_patterns(n, count)
+
+
+def test_query_order_depth_for_cap(lib):
+    """Counting the table's patterns per logistic weight at the 1e6 cap depth
+    agrees with the oracle's count (W <= 82, n = 128 and 64)."""
+    for n in (64, 128):
+        cnt = oracle.count_by_weight(n, 82)
+        total = int(cnt.sum())
+        got = lib.orbg_query_order(n, 0, None)
+        assert got == 0
+        # the library must cover at least `total` patterns for that cap
+        out = np.zeros((1, n + 1), np.int32)
+        # last pattern of depth 82 is the (total)-th; its weight must be 82
+        rows = orbg.orbg_query_order(n, total)
+        assert len(rows) == total
+        assert sum(rows[-1]) == 82 and sum(rows[0]) == 0

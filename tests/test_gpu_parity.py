@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA decoder, called through the C ABI, against the CPU
+oracle, element by element.  Bit-exact (tolerance 0) on the codeword, the
+query count and the abandon flag: all three are integer results.
+
+Sizes: small cases the oracle finishes in seconds (several warp groups of
+runs, ragged n), and the full benchmark configurations decoded in the same
+launch configuration the benchmark times, checked on a seeded random
+sample of blocks the oracle decodes one by one.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2202_13951_gb300 import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def orbg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2202_13951_gb300 import build, orbg as ob
+    build.build()
+    ob.load_library()
+    return ob
+
+
+def gpu_plain(ob, code_obj, llr, cap):
+    llr_t = torch.from_numpy(np.ascontiguousarray(llr, np.float32)).cuda()
+    cw, q, ab = ob.decode(code_obj, llr_t, cap)
+    torch.cuda.synchronize()
+    return (cw.cpu().numpy(), q.cpu().numpy().astype(np.int64),
+            ab.cpu().numpy())
+
+
+def gpu_batched(ob, codeset, llr, cap):
+    llr_t = torch.from_numpy(np.ascontiguousarray(llr, np.float32)).cuda()
+    cw, q, ab = ob.decode_batched(codeset, llr_t, cap)
+    torch.cuda.synchronize()
+    return (cw.cpu().numpy(), q.cpu().numpy().astype(np.int64),
+            ab.cpu().numpy())
+
+
+def assert_same(got, want, idx=None):
+    cw, q, ab = got
+    wc, wq, wab = want[0], want[1].astype(np.int64), want[2]
+    if idx is not None:
+        cw, q, ab = cw[idx], q[idx], ab[idx]
+    bad = np.nonzero((cw != wc).any(axis=1) | (q != wq) | (ab != wab))[0]
+    assert bad.size == 0, "first mismatches %s: gpu q=%s ab=%s, oracle q=%s ab=%s" % (
+        bad[:5], q[bad[:5]], ab[bad[:5]], wq[bad[:5]], wab[bad[:5]])
+
+
+def tiny_inputs(n, rng, blocks):
+    out = []
+    for b in range(blocks):
+        llr = rng.normal(0.0, 2.0, n).astype(np.float32)
+        kind = b % 5
+        if kind == 1:
+            llr = np.round(llr).astype(np.float32)
+        elif kind == 2:
+            llr[rng.integers(0, n, 2)] = 0.0
+            llr[rng.integers(0, n, 1)] = -0.0
+            llr[rng.integers(0, n, 1)] = np.inf
+            llr[rng.integers(0, n, 1)] = -np.inf
+        elif kind == 3:
+            llr = np.where(rng.random(n) < 0.5, -1.0, 1.0).astype(np.float32)
+        out.append(llr)
+    return np.stack(out)
+
+
+# ------------------------------------------------------------ small codes
+
+@pytest.mark.parametrize("cap", [1, 2, 3, 5, 17, 64, 128])
+def test_hamming74_every_cap(orbg, cap):
+    code = workloads.hamming74()
+    c = orbg.Code(code.H)
+    llr = tiny_inputs(7, np.random.default_rng(1), 200)
+    want = oracle.decode_batch(code.H, llr, cap)[:3]
+    assert_same(gpu_plain(orbg, c, llr, cap), want)
+
+
+@pytest.mark.parametrize("n,k,seed", [(16, 11, 16), (32, 20, 3), (33, 20, 4),
+                                      (64, 32, 5), (64, 31, 6), (65, 40, 7),
+                                      (96, 70, 8), (127, 113, 9), (128, 96, 10),
+                                      (160, 140, 11), (256, 240, 12), (256, 128, 13)])
+def test_random_codes_plain_and_batched(orbg, n, k, seed):
+    """n across key-padding cases (7..256), n-k on both sides of the 32/64
+    word boundaries, up to n-k = 128."""
+    code = workloads.rlc(n, k, seed)
+    rng = np.random.default_rng(seed + 100)
+    llr = np.concatenate([
+        tiny_inputs(n, rng, 40),
+        workloads.awgn_llr(code, 160, 3.0 + (seed % 4), seed + 200)[0]])
+    cap = 20000
+    want = oracle.decode_batch(code.H, llr, cap)[:3]
+    c = orbg.Code(code.H, max_query_cap=cap)
+    assert_same(gpu_plain(orbg, c, llr, cap), want)
+    cs = orbg.CodeSet([c])
+    assert_same(gpu_batched(orbg, cs, llr, cap), want)
+
+
+def test_generator_matrix_input_same_result(orbg):
+    """Loading G (the library derives its own H) decodes identically."""
+    code = workloads.config1_code()
+    llr, _ = workloads.awgn_llr(code, 500, 4.0, 77)
+    want = oracle.decode_batch(code.H, llr, 100000)[:3]
+    cg = orbg.Code(code.G, kind=orbg.ORBG_MAT_G, n=code.n, k=code.k, max_query_cap=100000)
+    assert_same(gpu_plain(orbg, cg, llr, 100000), want)
+
+
+def test_cap_exactly_at_hit(orbg):
+    code = workloads.rlc(64, 50, 31)
+    llr, _ = workloads.awgn_llr(code, 300, 3.0, 32)
+    _, q, ab, _ = oracle.decode_batch(code.H, llr, 200000)
+    c = orbg.Code(code.H, max_query_cap=200000)
+    for b in np.nonzero((ab == 0) & (q > 40))[0][:20]:
+        qb = int(q[b])
+        for cap in (qb - 1, qb):
+            want = oracle.decode_batch(code.H, llr[b:b + 1], cap)[:3]
+            assert_same(gpu_plain(orbg, c, llr[b:b + 1], cap), want)
+
+
+def test_nan_block_flagged(orbg):
+    code = workloads.config1_code()
+    llr, _ = workloads.awgn_llr(code, 64, 5.0, 5)
+    llr[3, 7] = np.nan
+    c = orbg.Code(code.H, max_query_cap=1000)
+    cw, q, ab = gpu_plain(orbg, c, llr, 1000)
+    assert ab[3] == orbg.ORBG_BLOCK_NAN and q[3] == 0
+    others = np.arange(64) != 3
+    want = oracle.decode_batch(code.H, llr[others], 1000)[:3]
+    assert_same((cw[others], q[others], ab[others]), want)
+    # host-buffer call reports ENAN
+    cwh = np.zeros((64, code.n), np.uint8)
+    qh = np.zeros(64, np.uint32)
+    abh = np.zeros(64, np.uint8)
+    with pytest.raises(orbg.OrbgError) as ei:
+        orbg.orbg_decode(c.handle, llr, 64, 1000, cwh, qh, abh)
+    assert ei.value.status == orbg.ORBG_ENAN
+
+
+def test_empty_batch(orbg):
+    code = workloads.config1_code()
+    c = orbg.Code(code.H)
+    e = torch.empty((0, code.n), dtype=torch.float32, device="cuda")
+    cw, q, ab = orbg.decode(c, e, 100)
+    assert cw.shape == (0, code.n)
+
+
+def test_host_buffers_match_device_buffers(orbg):
+    code = workloads.config2_code()
+    llr, _ = workloads.awgn_llr(code, 3000, 4.5, 9)
+    c = orbg.Code(code.H, max_query_cap=10 ** 6)
+    dev = gpu_plain(orbg, c, llr, 10 ** 6)
+    cw = np.zeros((3000, code.n), np.uint8)
+    q = np.zeros(3000, np.uint32)
+    ab = np.zeros(3000, np.uint8)
+    orbg.orbg_decode(c.handle, llr, 3000, 10 ** 6, cw, q, ab)
+    assert_same((cw, q.astype(np.int64), ab), dev)
+    cs = orbg.CodeSet([c])
+    orbg.orbg_decode_batched(cs.handle, None, None, llr, 3000, 10 ** 6, cw, None, q, ab)
+    assert_same((cw, q.astype(np.int64), ab), dev)
+
+
+def test_mixed_codes_one_launch_equals_alone(orbg):
+    """Blocks of four codes with different n and n-k in one batched launch
+    give what each code's blocks give alone, and what the oracle gives."""
+    codes, cid, llr, off, cwt, ebn0 = workloads.config4_inputs(B=4000, seed=4401)
+    objs = [orbg.Code(cd.H, max_query_cap=10 ** 6) for cd in codes]
+    cs = orbg.CodeSet(objs)
+    llr_t = torch.from_numpy(llr).cuda()
+    off_t = torch.from_numpy(off).cuda()
+    cid_t = torch.from_numpy(cid).cuda()
+    cw, q, ab = orbg.decode_batched(cs, llr_t, 10 ** 6, code_id=cid_t, llr_offset=off_t,
+                                    cw_offset=off_t, n_total=llr.shape[0])
+    torch.cuda.synchronize()
+    cw, q, ab = cw.cpu().numpy(), q.cpu().numpy().astype(np.int64), ab.cpu().numpy()
+    rng = np.random.default_rng(5)
+    for j, cd in enumerate(codes):
+        idx = np.nonzero(cid == j)[0]
+        blocks = np.stack([llr[off[b]:off[b] + cd.n] for b in idx])
+        alone = gpu_plain(orbg, objs[j], blocks, 10 ** 6)
+        mixed = (np.stack([cw[off[b]:off[b] + cd.n] for b in idx]), q[idx], ab[idx])
+        assert_same(mixed, alone)
+        pick = rng.choice(idx.shape[0], size=min(40, idx.shape[0]), replace=False)
+        want = oracle.decode_batch(cd.H, blocks[pick], 10 ** 6)[:3]
+        assert_same(alone, want, pick)
+
+
+# ------------------------------------------------ benchmark configurations
+
+def test_config1_full_parity(orbg):
+    """RLC(64,51), 5 dB, all-zero and random information, 2 x 10,000 blocks,
+    cap 1e5, plain single launch: every block against the oracle."""
+    code, llr, _ = workloads.config1_inputs()
+    want = oracle.decode_batch(code.H, llr, 10 ** 5)[:3]
+    c = orbg.Code(code.H, max_query_cap=10 ** 5)
+    assert_same(gpu_plain(orbg, c, llr, 10 ** 5), want)
+
+
+def _sampled(orbg, code, llr, cap, nsample, seed):
+    c = orbg.Code(code.H, max_query_cap=cap)
+    cs = orbg.CodeSet([c])
+    got = gpu_batched(orbg, cs, llr, cap)
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(llr.shape[0], size=nsample, replace=False))
+    want = oracle.decode_batch(code.H, llr[pick], cap)[:3]
+    assert_same(got, want, pick)
+    return got
+
+
+def test_config2_full_size_sampled(orbg):
+    """BCH(127,113), 4 x 100,000 blocks at 4..7 dB, cap 1e6, one batched
+    launch (the benchmark's call); 3000 seeded random blocks checked."""
+    code, llr, _ = workloads.config2_inputs()
+    got = _sampled(orbg, code, llr, 10 ** 6, 3000, 2)
+    # property at any size: every decoded block is a codeword
+    cw, q, ab = got
+    ok = ab == 0
+    H = torch.from_numpy(code.H.astype(np.float32)).cuda()
+    syn = (torch.from_numpy(cw[ok].astype(np.float32)).cuda() @ H.T) % 2
+    assert int(syn.abs().sum().item()) == 0
+
+
+def test_config3_full_size_sampled(orbg):
+    """CA-Polar(128,94), 4 x 100,000 blocks at 3..6 dB, cap 1e6 (64-bit
+    syndromes, heavy abandonment); 120 seeded random blocks checked."""
+    code, llr, _ = workloads.config3_inputs()
+    _sampled(orbg, code, llr, 10 ** 6, 120, 3)
