@@ -35,10 +35,17 @@ if ROOT not in sys.path:
 
 METRIC = ("decoded blocks/s and syndrome queries/s (bit-exact vs oracle) "
           "+ p99 latency")
-WORKLOAD = "bch(127,113) 4x100000 blocks at Eb/N0 4,5,6,7 dB, query cap 1e6"
+# name -> (description, code constructor name, Eb/N0 points, seeds)
+WORKLOADS = {
+    "bch": ("bch(127,113) 4x%d blocks at Eb/N0 4,5,6,7 dB, query cap 1e6",
+            "config2_code", (4.0, 5.0, 6.0, 7.0), (201, 202, 203, 204)),
+    "capolar": ("ca-polar(128,94[K=105]) 4x%d blocks at Eb/N0 3,4,5,6 dB, query cap 1e6",
+                "config3_code", (3.0, 4.0, 5.0, 6.0), (301, 302, 303, 304)),
+}
 POINTS = (4.0, 5.0, 6.0, 7.0)
 SEEDS = (201, 202, 203, 204)
 B_PER_POINT = 100_000
+WORKLOAD = WORKLOADS["bch"][0] % B_PER_POINT
 CAP = 1_000_000
 SMS = 152
 SM_MAX_MHZ = 2070.0
@@ -49,14 +56,33 @@ SM_MAX_MHZ = 2070.0
 def parse_args(argv=None):
     p = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=50)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--ref-sample", type=int, default=8000,
                    help="blocks per reference step (CPU oracle)")
-    return p.parse_args(argv)
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="bch",
+                   help="bch: the headline configuration; capolar: the search-heavy "
+                        "CA-Polar configuration (profiling)")
+    p.add_argument("--blocks-per-point", type=int, default=B_PER_POINT)
+    p.add_argument("--shape", default="",
+                   help="warps_per_cta,ctas_per_sm,blocks_per_grab,warp_budget,heavy_warps "
+                        "for the batched launch (orbg_tuning)")
+    args = p.parse_args(argv)
+    select_workload(args.workload, args.blocks_per_point)
+    return args
+
+
+def select_workload(name, b_per_point):
+    global WORKLOAD, POINTS, SEEDS, B_PER_POINT, CODE_FN
+    desc, CODE_FN, POINTS, SEEDS = WORKLOADS[name]
+    B_PER_POINT = b_per_point
+    WORKLOAD = desc % b_per_point
+
+
+CODE_FN = "config2_code"
 
 
 def dist_env():
@@ -71,12 +97,12 @@ def rank_seeds(rank):
     return tuple(s + 1000 * rank for s in SEEDS)
 
 
-def make_inputs(rank=0, b_per_point=B_PER_POINT):
+def make_inputs(rank=0):
     from paper_2202_13951_gb300 import workloads
-    code = workloads.config2_code()
+    code = getattr(workloads, CODE_FN)()
     ls = []
     for e, s in zip(POINTS, rank_seeds(rank)):
-        l, _ = workloads.awgn_llr(code, b_per_point, e, s)
+        l, _ = workloads.awgn_llr(code, B_PER_POINT, e, s)
         ls.append(l)
     return code, np.ascontiguousarray(np.concatenate(ls))
 
@@ -150,7 +176,7 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index, period_ms=100):
+    def __init__(self, gpu_index, period_ms=50):
         self.gpu = gpu_index
         self.period = period_ms
         self.proc = None
@@ -192,7 +218,11 @@ class ClockSampler:
             if len(parts) < 9:
                 continue
             rows.append((ts, parts))
-        inside = [p for ts, p in rows if t0 <= ts <= t1] or [p for _, p in rows]
+        inside = [p for ts, p in rows if t0 <= ts <= t1]
+        window = "timed"
+        if not inside:
+            inside = [p for _, p in rows]
+            window = "whole run (timed region shorter than the sampling period)"
         if not inside:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"],
                     "samples": 0}
@@ -213,7 +243,7 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(inside)}
+                "reasons": sorted(reasons), "samples": len(inside), "window": window}
 
 
 # ------------------------------------------------------------- CPU side
@@ -232,7 +262,7 @@ def cpu_sample(llr, per_point, step):
     idx = []
     for p in range(len(POINTS)):
         base = p * B_PER_POINT
-        lo = (step * per_point) % max(1, B_PER_POINT - per_point)
+        lo = (step * per_point) % max(1, B_PER_POINT - per_point + 1)
         idx.append(np.arange(base + lo, base + lo + per_point))
     return llr[np.concatenate(idx)]
 
@@ -334,6 +364,9 @@ def bench_ours(args, rank, world, local):
     B = llr_np.shape[0]
     c = orbg.Code(code.H, max_query_cap=CAP)
     cs = orbg.CodeSet([c])
+    if args.shape:
+        f = [int(x) for x in args.shape.split(",")]
+        orbg.orbg_codeset_set_tuning(cs.handle, orbg.OrbgTuning(*f))
     llr = torch.from_numpy(llr_np).to(dev)
     cw = torch.empty((B, code.n), dtype=torch.uint8, device=dev)
     q = torch.empty((B,), dtype=torch.int32, device=dev)
@@ -405,9 +438,11 @@ def bench_ours(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32-llr/u32-syndrome",
         "data": "synthetic BPSK/AWGN, seeded (numpy PCG64); each rank its own seeds",
         "config": {"workload": WORKLOAD, "blocks_per_step": B, "query_cap": CAP,
+                   "input_mb": round(llr_np.nbytes / 1e6, 1),
                    "form": "batched persistent launch (orbg_decode_batched)",
-                   "l2": "inputs 203 MB > 129 MB L2, no flush",
-                   "launch_shape": list(orbg.orbg_get_launch_shape()),
+                   "l2": ("inputs %.0f MB %s 129 MB L2, no flush"
+                          % (llr_np.nbytes / 1e6, ">" if llr_np.nbytes > 129e6 else "<=")),
+                   "tuning": orbg.orbg_codeset_get_tuning(cs.handle).as_dict(),
                    "parallelism": "replicas x%d (blocks sharded by rank, no collective)" % world},
         "queries_per_s": queries_total / (total_ms / 1000.0),
         "latency_ms": {"step_p50": statistics.median(per_step),
@@ -415,16 +450,15 @@ def bench_ours(args, rank, world, local):
                        "what": "one 400,000-block batch, launch to completion"},
         "abandon_rate": float(abh.mean()),
         "mean_queries": float(qh.mean()),
-        "gpu_launches": args.steps,
+        "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "Tops/s", "frac": (achieved / peak) if peak else None,
                      "traffic": None,
-                     "what": ("orbg_batched_kernel; algorithmic 32-bit integer ops per "
+                     "what": ("orbg_batched_kernel + orbg_heavy_kernel (one step); algorithmic 32-bit integer ops per "
                               "launch = sum_t W32 (w_t + 1) + B n ceil(log2 n) = %d; "
                               "peak = measured LOP3 lanes/clk/SM (%s) x 152 SMs x "
                               "2070 MHz" % (alg_ops, lanes))},
-        "clocks": {"sm_mhz": clocks["sm_mhz"], "sm_max_mhz": clocks["sm_max_mhz"],
-                   "reasons": clocks["reasons"], "samples": clocks["samples"]},
+        "clocks": clocks,
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
     }
     if e2e:
@@ -478,13 +512,14 @@ def cpu_baseline(code, llr_np):
     """The oracle as it stands, one process, on a bounded sample (~10 s)."""
     import oracle
     oracle.build_oracle()
-    per_point = 25_000
+    per_point = B_PER_POINT
     sample = cpu_sample(llr_np, per_point, 0)
     dt, qsum, nb = run_oracle(code.H, sample, CAP, 1)
     return {"value": nb / dt, "unit": "blocks/s", "cores": 1, "kind": "oracle",
             "queries_per_s": qsum / dt,
-            "sample": "first %d blocks of each of the 4 Eb/N0 points (%d blocks), one "
-                      "single-threaded process on %s" % (per_point, nb, cpu_model())}
+            "sample": "%d blocks of each of the 4 Eb/N0 points (%d blocks, the whole "
+                      "workload), one single-threaded process on %s"
+                      % (per_point, nb, cpu_model())}
 
 
 def main(argv=None):

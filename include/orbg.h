@@ -130,17 +130,20 @@ ORBG_API int orbg_codeset_create(const orbg_code *const *codes, int ncodes,
 ORBG_API int orbg_codeset_free(orbg_codeset *set);
 
 /*
- * Batched form: one persistent launch (about one CTA per SM and a few per
- * SM more) whose warps pull blocks from an atomic work queue, so blocks with
- * very different query counts, and blocks of different codes, balance.
+ * Batched form: two persistent launches.  In the first, warps pull blocks
+ * from an atomic work queue and decode each alone up to a query budget; in
+ * the second, every CTA takes one still-open block at a time and searches it
+ * with all its warps.  Blocks with very different query counts, and blocks
+ * of different codes, balance across the GPU.
  *   code_id    : [B] index into the set per block, or NULL (all code 0).
  *   llr_offset : [B] element offset of block b in llr, or NULL
  *                (dense: b * n of code 0).
  *   cw_offset  : [B] byte offset of block b in codeword, or NULL (dense).
  *   Other arguments as orbg_decode; query_cap must be within every code's
  *   max_query_cap.
- * The call uses 64 bytes of stream-ordered device scratch (the work
- * queue head), allocated and freed on cuda_stream.
+ * The call uses 64 + 8 B bytes of stream-ordered device scratch (queue
+ * counters and the list of still-open blocks), allocated and freed on
+ * cuda_stream.
  * Results are identical to orbg_decode's block by block.
  * Paper: Algorithm 1 per block; the batching is this library's.
  */
@@ -150,10 +153,38 @@ ORBG_API int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id
                         const int64_t *cw_offset, uint32_t *queries,
                         uint8_t *abandoned, void *cuda_stream);
 
-/* Launch shape of the batched form: warps per CTA (1..16, 0 = default) and
- * resident CTAs per SM (0 = as many as fit).  Process-wide. */
-ORBG_API int orbg_set_launch_shape(int warps_per_cta, int ctas_per_sm);
-ORBG_API int orbg_get_launch_shape(int *warps_per_cta, int *ctas_per_sm);
+/*
+ * Tuning of the batched form, per code set (the autotuner writes these):
+ *   warps_per_cta   phase 1: warps per CTA, one block per warp (1..16; 0 = 8)
+ *   ctas_per_sm     phase 1: resident CTAs per SM (0 = as many as fit)
+ *   blocks_per_grab phase 1: blocks a warp takes per work-queue atomic
+ *                   (1..1024; 0 = 8)
+ *   warp_budget     phase 1: queries of a block's order a single warp walks
+ *                   before handing the block to phase 2 (0 = 4096; a value
+ *                   >= the call's query cap disables phase 2)
+ *   heavy_warps     phase 2: warps per CTA sharing one block (1..16; 0 = 16)
+ * None of these change any result.
+ */
+typedef struct orbg_tuning {
+    int warps_per_cta;
+    int ctas_per_sm;
+    int blocks_per_grab;
+    uint32_t warp_budget;
+    int heavy_warps;
+} orbg_tuning;
+
+/* t = NULL restores the defaults.  Not stream-ordered: set it while no
+ * batched call on this set is being enqueued. */
+ORBG_API int orbg_codeset_set_tuning(orbg_codeset *set, const orbg_tuning *t);
+ORBG_API int orbg_codeset_get_tuning(const orbg_codeset *set, orbg_tuning *t);
+
+/*
+ * Roofline probe: issue rate of independent 32-bit 3-input logic ops
+ * (lop3.b32, the instruction a syndrome XOR compiles to) per SM per clock,
+ * in lanes (threads x instructions), measured with clock64 on every SM of
+ * the current device.  Synchronous; allocates and frees a small buffer.
+ */
+ORBG_API int orbg_probe_int_lanes(double *lanes_per_clk_per_sm);
 
 /*
  * The query order this library decodes in, for inspection and tests: the

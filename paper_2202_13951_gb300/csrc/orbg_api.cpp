@@ -28,6 +28,7 @@ struct orbg_code {
 
 struct orbg_codeset {
     int ncodes, n_max, w32_max;
+    orbg_tuning tuning;
     std::vector<int> n_of;       /* n of each code, host copy */
     uint32_t cap_min;
     int device;
@@ -37,9 +38,7 @@ struct orbg_codeset {
 namespace {
 
 thread_local int g_last_cuda = 0;
-std::mutex g_shape_mu;
-int g_wpc = 8;
-int g_ctas_per_sm = 0;
+const orbg_tuning kDefaultTuning = {8, 0, 8, 4096u, 16};
 
 int cuda_fail(cudaError_t e)
 {
@@ -185,22 +184,41 @@ int64_t orbg_query_order(int n, uint32_t count, int32_t *out)
     return (int64_t)total;
 }
 
-int orbg_set_launch_shape(int warps_per_cta, int ctas_per_sm)
+int orbg_codeset_set_tuning(orbg_codeset *set, const orbg_tuning *t)
 {
-    if (warps_per_cta < 0 || warps_per_cta > 16 || ctas_per_sm < 0 || ctas_per_sm > 64)
+    if (!set)
         return ORBG_EINVAL;
-    std::lock_guard<std::mutex> lk(g_shape_mu);
-    g_wpc = warps_per_cta ? warps_per_cta : 8;
-    g_ctas_per_sm = ctas_per_sm;
+    if (!t) {
+        set->tuning = kDefaultTuning;
+        return ORBG_OK;
+    }
+    if (t->warps_per_cta < 0 || t->warps_per_cta > 16 || t->ctas_per_sm < 0 ||
+        t->ctas_per_sm > 64 || t->blocks_per_grab < 0 || t->blocks_per_grab > 1024 ||
+        t->heavy_warps < 0 || t->heavy_warps > 16)
+        return ORBG_EINVAL;
+    orbg_tuning v = *t;
+    if (!v.warps_per_cta) v.warps_per_cta = kDefaultTuning.warps_per_cta;
+    if (!v.blocks_per_grab) v.blocks_per_grab = kDefaultTuning.blocks_per_grab;
+    if (!v.warp_budget) v.warp_budget = kDefaultTuning.warp_budget;
+    if (!v.heavy_warps) v.heavy_warps = kDefaultTuning.heavy_warps;
+    set->tuning = v;
     return ORBG_OK;
 }
 
-int orbg_get_launch_shape(int *warps_per_cta, int *ctas_per_sm)
+int orbg_codeset_get_tuning(const orbg_codeset *set, orbg_tuning *t)
 {
-    std::lock_guard<std::mutex> lk(g_shape_mu);
-    if (warps_per_cta) *warps_per_cta = g_wpc;
-    if (ctas_per_sm) *ctas_per_sm = g_ctas_per_sm;
+    if (!set || !t)
+        return ORBG_EINVAL;
+    *t = set->tuning;
     return ORBG_OK;
+}
+
+int orbg_probe_int_lanes(double *lanes_per_clk_per_sm)
+{
+    if (!lanes_per_clk_per_sm)
+        return ORBG_EINVAL;
+    int e = orbg_launch_int_probe(lanes_per_clk_per_sm);
+    return e ? cuda_fail((cudaError_t)e) : ORBG_OK;
 }
 
 int orbg_load_code(const uint8_t *mat, int kind, int n, int k, uint32_t max_query_cap,
@@ -379,6 +397,7 @@ int orbg_codeset_create(const orbg_code *const *codes, int ncodes, orbg_codeset 
     s->n_max = 0;
     s->w32_max = 1;
     s->cap_min = 0xFFFFFFFFu;
+    s->tuning = kDefaultTuning;
     for (int i = 0; i < ncodes; i++) {
         if (!codes[i]) {
             delete s;
@@ -475,18 +494,19 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
         sg.finish(false);
         return rc;
     }
-    unsigned long long *counter = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&counter, 64, st);
+    unsigned long long *scratch = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&scratch, orbg_batched_scratch_bytes(B), st);
     if (e != cudaSuccess) {
         sg.finish(false);
         return cuda_fail(e);
     }
-    int wpc, cps;
-    orbg_get_launch_shape(&wpc, &cps);
+    const orbg_tuning &t = set->tuning;
+    const uint32_t budget = t.warp_budget < query_cap ? t.warp_budget : query_cap;
     int le = orbg_launch_batched(set->d_codes, set->ncodes, set->n_max, set->w32_max, d_cid,
-                                 d_lo, d_llr, B, query_cap, d_cw, d_co, d_q, d_ab, counter, wpc,
-                                 cps, st);
-    cudaFreeAsync(counter, st);
+                                 d_lo, d_llr, B, query_cap, budget, d_cw, d_co, d_q, d_ab,
+                                 scratch, t.warps_per_cta, t.ctas_per_sm, t.blocks_per_grab,
+                                 t.heavy_warps, st);
+    cudaFreeAsync(scratch, st);
     if (le != 0) {
         sg.finish(false);
         return cuda_fail((cudaError_t)le);

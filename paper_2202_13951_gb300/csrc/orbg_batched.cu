@@ -1,6 +1,18 @@
 /*
- * orbg_batched.cu -- the batched form: a persistent launch whose warps pull
- * blocks, possibly of different codes, from an atomic work queue.
+ * orbg_batched.cu -- the batched form: two persistent launches over blocks
+ * that may belong to different codes.
+ *
+ * Phase 1 (orbg_batched_kernel): each warp pulls `grab` blocks at a time
+ * from an atomic work queue and decodes each with decode_block_warp, giving
+ * it a query budget.  Most blocks finish inside the budget (at high SNR
+ * query 1 already decodes).  A block still open when its warp reaches the
+ * budget is appended to a heavy list.
+ * Phase 2 (orbg_heavy_kernel, orbg_heavy.cu): each CTA pulls heavy blocks
+ * one at a time and decodes each with all its warps (decode_block_cta), so a
+ * block that needs up to 1e6 queries is searched by a whole SM instead of a
+ * single warp.
+ * Both phases compute the exact first hit of the same query order, so the
+ * result equals the plain form's block for block.
  */
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -11,93 +23,133 @@ using namespace orbg_dev;
 
 namespace {
 
+constexpr int kCounters = ORBG_BATCHED_COUNTERS;
+
 template <int KMAX, int WMAX>
-__global__ void __launch_bounds__(512) orbg_batched_kernel(
+__global__ void __launch_bounds__(256, 4) orbg_batched_kernel(
     const OrbgDeviceCode *__restrict__ codes, int ncodes, const int32_t *__restrict__ code_id,
     const int64_t *__restrict__ llr_off, const float *__restrict__ llr, int64_t B, uint32_t cap,
-    uint8_t *__restrict__ cw, const int64_t *__restrict__ cw_off, uint32_t *__restrict__ q,
-    uint8_t *__restrict__ ab, unsigned long long *__restrict__ counter, uint32_t wstride)
+    uint32_t budget, uint8_t *__restrict__ cw, const int64_t *__restrict__ cw_off,
+    uint32_t *__restrict__ q, uint8_t *__restrict__ ab, unsigned long long *__restrict__ counters,
+    unsigned long long *__restrict__ heavy, uint32_t bstride, int grab)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    unsigned char *wsm = smem + warp * wstride;
+    unsigned char *bsm = smem + warp * bstride;
     const int64_t n0 = codes[0].n;
     for (;;) {
-        unsigned long long b = 0;
+        /* one atomic per `grab` consecutive blocks */
+        unsigned long long b0 = 0;
         if (lane == 0)
-            b = atomicAdd(counter, 1ull);
-        b = __shfl_sync(FULL_MASK, b, 0);
-        if ((int64_t)b >= B)
+            b0 = atomicAdd(&counters[0], (unsigned long long)grab);
+        b0 = __shfl_sync(FULL_MASK, b0, 0);
+        if ((int64_t)b0 >= B)
             break;
-        int cid = code_id ? code_id[b] : 0;
-        if (cid < 0 || cid >= ncodes) {
-            if (lane == 0) {
-                q[b] = 0u;
-                ab[b] = 2;
+        const int64_t bend = min((int64_t)b0 + grab, B);
+        for (int64_t b = (int64_t)b0; b < bend; b++) {
+            const int cid = code_id ? code_id[b] : 0;
+            if (cid < 0 || cid >= ncodes) {
+                if (lane == 0) {
+                    q[b] = 0u;
+                    ab[b] = 2;
+                }
+                continue;
             }
-            continue;
+            const OrbgDeviceCode code = codes[cid];
+            const int64_t lo = llr_off ? llr_off[b] : b * n0;
+            const int64_t co = cw_off ? cw_off[b] : b * n0;
+#define ORBG_CALL_WARP(KK, WW)                                                            \
+    decode_block_warp<KK, WW>(code, llr + lo, cw + co, q + b, ab + b, cap, budget, bsm, lane, \
+                              heavy, &counters[1], (unsigned long long)b)
+            ORBG_DISPATCH(KMAX, WMAX, ORBG_CALL_WARP);
+#undef ORBG_CALL_WARP
         }
-        const OrbgDeviceCode code = codes[cid];
-        const int64_t lo = llr_off ? llr_off[b] : (int64_t)b * n0;
-        const int64_t co = cw_off ? cw_off[b] : (int64_t)b * n0;
-        decode_any<KMAX, WMAX>(code, llr + lo, cw + co, q + b, ab + b, cap, wsm, lane);
     }
 }
 
 }  // namespace
+
+int orbg_grid_for(const void *kern, int threads, size_t smem, int ctas_per_sm, int *grid_out)
+{
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return (int)e;
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return (int)e;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem);
+    if (e != cudaSuccess) return (int)e;
+    if (occ < 1) return (int)cudaErrorInvalidConfiguration;
+    int per_sm = ctas_per_sm > 0 && ctas_per_sm < occ ? ctas_per_sm : occ;
+    *grid_out = sms * per_sm;
+    return 0;
+}
 
 namespace {
 
 template <int KMAX, int WMAX>
 cudaError_t launch_batched_t(const OrbgDeviceCode *d_codes, int ncodes, int n_max, int w32_max,
                              const int32_t *code_id, const int64_t *llr_off, const float *llr,
-                             int64_t B, uint32_t cap, uint8_t *cw, const int64_t *cw_off,
-                             uint32_t *q, uint8_t *ab, unsigned long long *counter,
-                             int warps_per_cta, int ctas_per_sm, cudaStream_t st)
+                             int64_t B, uint32_t cap, uint32_t budget, uint8_t *cw,
+                             const int64_t *cw_off, uint32_t *q, uint8_t *ab,
+                             unsigned long long *scratch, int warps_per_cta, int ctas_per_sm,
+                             int grab, int heavy_warps, cudaStream_t st)
 {
-    auto kern = orbg_batched_kernel<KMAX, WMAX>;
-    int wpc = warps_per_cta > 0 ? warps_per_cta : 8;
-    uint32_t wstride = warp_smem_bytes(n_max, w32_max);
-    size_t smem = (size_t)wstride * wpc;
+    const int wpc = warps_per_cta > 0 ? (warps_per_cta > 8 ? 8 : warps_per_cta) : 8;
+    const int g = grab < 1 ? 1 : grab;
+    const uint32_t bstride = block_smem_bytes(n_max, w32_max);
+    unsigned long long *counters = scratch;
+    unsigned long long *heavy = scratch + kCounters;
     cudaError_t e;
-    int dev = 0, sms = 0, occ = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    int grid = 0, rc;
+    if ((e = cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * kCounters, st)) !=
+        cudaSuccess)
         return e;
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, wpc * 32, smem);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) return cudaErrorInvalidConfiguration;
-    int per_sm = ctas_per_sm > 0 && ctas_per_sm < occ ? ctas_per_sm : occ;
-    int64_t grid = (int64_t)sms * per_sm;
-    int64_t need = (B + wpc - 1) / wpc;
-    if (grid > need) grid = need > 0 ? need : 1;
-    if ((e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st)) != cudaSuccess)
+    /* phase 1 */
+    auto k1 = orbg_batched_kernel<KMAX, WMAX>;
+    size_t smem1 = (size_t)bstride * wpc;
+    if ((rc = orbg_grid_for((const void *)k1, wpc * 32, smem1, ctas_per_sm, &grid)) != 0)
+        return (cudaError_t)rc;
+    int64_t units = (B + g - 1) / g;
+    int64_t need = (units + wpc - 1) / wpc;
+    if (grid > need) grid = (int)(need > 0 ? need : 1);
+    k1<<<grid, wpc * 32, smem1, st>>>(d_codes, ncodes, code_id, llr_off, llr, B, cap, budget, cw,
+                                      cw_off, q, ab, counters, heavy, bstride, g);
+    if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
-    kern<<<(unsigned)grid, wpc * 32, smem, st>>>(d_codes, ncodes, code_id, llr_off, llr, B, cap,
-                                                 cw, cw_off, q, ab, counter, wstride);
-    return cudaGetLastError();
+    if (budget >= cap)
+        return cudaSuccess; /* every block finished in phase 1 */
+    /* phase 2 */
+    return (cudaError_t)orbg_launch_heavy(d_codes, ncodes, n_max, w32_max, code_id, llr_off, llr,
+                                          cap, cw, cw_off, q, ab, counters, heavy, heavy_warps,
+                                          st);
 }
 
 }  // namespace
 
+size_t orbg_batched_scratch_bytes(int64_t B)
+{
+    return sizeof(unsigned long long) * ((size_t)kCounters + (size_t)(B > 0 ? B : 0));
+}
+
 int orbg_launch_batched(const OrbgDeviceCode *d_codes, int ncodes, int n_max, int w32_max,
                         const int32_t *code_id, const int64_t *llr_off, const float *llr,
-                        int64_t B, uint32_t cap, uint8_t *cw, const int64_t *cw_off,
-                        uint32_t *q, uint8_t *ab, unsigned long long *counter,
-                        int warps_per_cta, int ctas_per_sm, void *stream)
+                        int64_t B, uint32_t cap, uint32_t budget, uint8_t *cw,
+                        const int64_t *cw_off, uint32_t *q, uint8_t *ab,
+                        unsigned long long *scratch, int warps_per_cta, int ctas_per_sm, int grab,
+                        int heavy_warps, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
 #define ORBG_B(KM, WM)                                                                       \
     return (int)launch_batched_t<KM, WM>(d_codes, ncodes, n_max, w32_max, code_id, llr_off, \
-                                         llr, B, cap, cw, cw_off, q, ab, counter,            \
-                                         warps_per_cta, ctas_per_sm, st);
-#define ORBG_BW(KM)                 \
-    if (w32_max <= 1) { ORBG_B(KM, 1) } \
+                                         llr, B, cap, budget, cw, cw_off, q, ab, scratch,     \
+                                         warps_per_cta, ctas_per_sm, grab, heavy_warps, st);
+#define ORBG_BW(KM)                          \
+    if (w32_max <= 1) { ORBG_B(KM, 1) }      \
     else if (w32_max <= 2) { ORBG_B(KM, 2) } \
     else { ORBG_B(KM, 4) }
     if (n_max <= 32) {

@@ -2,22 +2,29 @@
  * orbg_decode_block.cuh -- per-block device code of the basic-ORBGRAND
  * decoder, shared by the plain and the batched kernels.
  *
- * One warp decodes one received block (Algorithm 1 with the basic ORBGRAND
+ * Decoding one received block (Algorithm 1 with the basic ORBGRAND
  * generator, Sec. III-B):
  *   1. coalesced load of the n FP32 LLRs; hard decision y_i = [L_i > 0];
- *      reliability key (FP32 bits of |L_i|, i) (Sec. III-A);
+ *      reliability key (FP32 bits of |L_i|, i) (Sec. III-A); starting
+ *      syndrome s0 = H y (Sec. I).  If s0 = 0, y is a codeword and query 1
+ *      (the zero pattern) decodes: no sort is needed;
  *   2. warp bitonic sort of the keys in registers -> pi (Sec. III-A; the
  *      paper names bitonic sorting networks as one option, Sec. IV-B);
  *   3. permuted columns hperm[p] = H[:, pi_p] into shared memory, plus a
- *      zero column at p = n; starting syndrome s0 = H y (Sec. I);
+ *      zero column at p = n;
  *   4. the query order as runs (orbg_internal.h): lane l of a warp step
  *      takes run l of a group of 32, XORs its prefix columns into s0 and
  *      walks the run, testing s0 (+) prefix (+) hperm[a] (+) hperm[b] == 0;
- *      the warp keeps the smallest hit index (__reduce_min_sync) and stops
- *      once no later group can hold a smaller one, or the cap is passed;
+ *      the smallest hit index is kept and the search stops once no later
+ *      group can hold a smaller one, or the cap is passed;
  *   5. codeword y (+) z* (or y if abandoned), query count, abandon flag.
- * Every loop is bounded by the table size or the run length; no kernel
- * waits on another thread's progress.
+ *
+ * Two ways to run step 4: one warp walks all groups of its block
+ * (decode_block_warp), or all warps of a CTA share one block and take its
+ * groups in turn, with the best index in shared memory (decode_block_cta).
+ * The second keeps a block that needs 1e6 queries from running on a single
+ * warp.  Every loop is bounded by the table size or the run length; no
+ * thread waits on another's progress beyond __syncthreads.
  */
 #pragma once
 #include <cuda_runtime.h>
@@ -26,6 +33,7 @@
 #include "orbg_internal.h"
 
 #define FULL_MASK 0xFFFFFFFFu
+#define ORBG_NONE 0xFFFFFFFFu
 
 namespace orbg_dev {
 
@@ -75,30 +83,40 @@ __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m)
     return ((uint64_t)hi << 32) | lo;
 }
 
-/* Shared memory of one warp: hperm[n+1] syndromes, then pi[256], cw[256]. */
-__host__ __device__ __forceinline__ uint32_t warp_smem_bytes(int n, int w32)
+/* Shared memory of one block in flight: hperm[n+1] syndromes, then pi[256]
+ * and the staged codeword cw[256]. */
+__host__ __device__ __forceinline__ uint32_t block_smem_bytes(int n, int w32)
 {
     uint32_t h = (uint32_t)(n + 1) * 4u * (uint32_t)w32;
     h = (h + 15u) & ~15u;
     return h + 256u + 256u;
 }
 
-/* ------------------------------------------------------------ one block */
+template <int W> struct BlockSmem {
+    typedef typename Syn<W>::T T;
+    T *h;
+    uint8_t *pi;
+    uint8_t *cw;
+    __device__ __forceinline__ BlockSmem(unsigned char *base, int n)
+    {
+        h = reinterpret_cast<T *>(base);
+        pi = base + (((uint32_t)(n + 1) * sizeof(T) + 15u) & ~15u);
+        cw = pi + 256;
+    }
+};
 
+/* ------------------------------------------------------- step 1: load */
+
+/* Loads the block, writes y into cw, builds the K keys per lane and returns
+ * s0 (identical in every lane).  *nan is warp-uniform. */
 template <int K, int W>
-__device__ void decode_block(const OrbgDeviceCode &code, const float *__restrict__ llr,
-                             uint8_t *__restrict__ cw_out, uint32_t *__restrict__ q_out,
-                             uint8_t *__restrict__ ab_out, uint32_t cap,
-                             unsigned char *__restrict__ wsm, int lane)
+__device__ __forceinline__ typename Syn<W>::T load_block(const OrbgDeviceCode &code,
+                                                         const float *__restrict__ llr,
+                                                         uint64_t (&key)[K], uint8_t *cw,
+                                                         int lane, bool *nan_out)
 {
     typedef typename Syn<W>::T T;
     const int n = code.n;
-    T *h = reinterpret_cast<T *>(wsm);
-    uint8_t *pi = wsm + (((uint32_t)(n + 1) * sizeof(T) + 15u) & ~15u);
-    uint8_t *cw = pi + 256;
-
-    /* 1. load, hard decision, keys, s0 */
-    uint64_t key[K];
     T s0 = szero<T>();
     bool nan = false;
 #pragma unroll
@@ -120,22 +138,17 @@ __device__ void decode_block(const OrbgDeviceCode &code, const float *__restrict
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1)
         s0 = sx(s0, shfl_xor_all(s0, m));
-    if (__any_sync(FULL_MASK, nan)) {
-        __syncwarp();
-#pragma unroll
-        for (int k = 0; k < K; k++) {
-            int i = k * 32 + lane;
-            if (i < n)
-                cw_out[i] = cw[i];
-        }
-        if (lane == 0) {
-            *q_out = 0u;
-            *ab_out = 2;
-        }
-        return;
-    }
+    *nan_out = __any_sync(FULL_MASK, nan);
+    return s0;
+}
 
-    /* 2. bitonic sort; position e = lane*K + k after the sort */
+/* ------------------------------------------------------- step 2: sort */
+
+/* Bitonic sort of 32*K unique keys held K per lane; afterwards position
+ * e = lane*K + k holds the e-th smallest. */
+template <int K>
+__device__ __forceinline__ void sort_keys(uint64_t (&key)[K], int lane)
+{
 #pragma unroll
     for (int size = 2; size <= 32 * K; size <<= 1) {
 #pragma unroll
@@ -168,150 +181,409 @@ __device__ void decode_block(const OrbgDeviceCode &code, const float *__restrict
             }
         }
     }
+}
 
-    /* 3. pi and permuted columns; zero column at n */
+/*
+ * Cheaper sort: one 32-bit key per element, (|L| bits truncated) << IB | i,
+ * with IB index bits (n <= 2^IB) and the low IB-1 mantissa bits of |L|
+ * dropped so the key fits 32 bits.  The truncation merges reliabilities
+ * that differ only in those bits; inside such a tie the key orders by
+ * index, which is the exact order unless the full bits disagree.  That is
+ * checked on every adjacent pair afterwards; any disagreement sends the
+ * block to the exact 64-bit sort.
+ */
+template <int K>
+__device__ __forceinline__ void bitonic32(uint32_t (&key)[K], int lane)
+{
+#pragma unroll
+    for (int size = 2; size <= 32 * K; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= K) {
+                const int lm = stride / K;
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    const int e = lane * K + k;
+                    const uint32_t o = __shfl_xor_sync(FULL_MASK, key[k], lm);
+                    const bool takemin = ((e & size) == 0) == ((e & stride) == 0);
+                    key[k] = takemin ? min(key[k], o) : max(key[k], o);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    if ((k & stride) == 0) {
+                        const int k2 = k | stride;
+                        const int e = lane * K + k;
+                        const bool asc = (e & size) == 0;
+                        const uint32_t lo = min(key[k], key[k2]), hi = max(key[k], key[k2]);
+                        key[k] = asc ? lo : hi;
+                        key[k2] = asc ? hi : lo;
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int K> struct KeyBits {
+    static constexpr int IB = K == 1 ? 5 : K == 2 ? 6 : K == 4 ? 7 : 8; /* 32*K <= 2^IB */
+    static constexpr int DROP = IB - 1;                                  /* 31 + IB - DROP = 32 */
+    static constexpr uint32_t IMASK = (1u << IB) - 1u;
+};
+
+/* Sort 64-bit keys (bits << 32 | i) through 32-bit keys; returns false if
+ * the truncated order may differ from the exact one. On true, key[] holds
+ * the exact sorted keys (positions e = lane*K + k). */
+template <int K>
+__device__ __forceinline__ bool sort_keys_fast(uint64_t (&key)[K], const float *__restrict__ llr,
+                                               int n, int lane)
+{
+    typedef KeyBits<K> KB;
+    uint32_t k32[K];
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const uint32_t bits = (uint32_t)(key[k] >> 32);
+        const uint32_t idx = (uint32_t)key[k];
+        k32[k] = ((bits >> KB::DROP) << KB::IB) | (idx & KB::IMASK);
+        /* padding (bits = 0xFFFFFFFF) keeps all-ones above the index */
+    }
+    bitonic32<K>(k32, lane);
+    /* adjacent pairs with equal truncated reliabilities: check exact order */
+    bool bad = false;
+    const uint32_t next_first = __shfl_down_sync(FULL_MASK, k32[0], 1);
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const int e = lane * K + k;
+        const uint32_t nxt = (k + 1 < K) ? k32[k + 1 < K ? k + 1 : k] : next_first;
+        if (e + 1 < n && (k32[k] >> KB::IB) == (nxt >> KB::IB)) {
+            const uint32_t ba = __float_as_uint(__ldg(llr + (k32[k] & KB::IMASK))) & 0x7FFFFFFFu;
+            const uint32_t bb = __float_as_uint(__ldg(llr + (nxt & KB::IMASK))) & 0x7FFFFFFFu;
+            bad |= ba > bb;
+        }
+    }
+    if (__any_sync(FULL_MASK, bad))
+        return false;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const uint32_t idx = k32[k] & KB::IMASK;
+        key[k] = (uint64_t)idx; /* only the index is used after the sort */
+    }
+    return true;
+}
+
+/* Sort with the fast path and the exact fallback (the fast path leaves
+ * key[] untouched when it gives up). */
+template <int K>
+__device__ __forceinline__ void sort_block(uint64_t (&key)[K], const float *__restrict__ llr,
+                                           int n, int lane)
+{
+    if (!sort_keys_fast<K>(key, llr, n, lane))
+        sort_keys<K>(key, lane);
+}
+
+/* ------------------------------------------------- step 3: permutation */
+
+template <int K, int W>
+__device__ __forceinline__ void build_perm(const OrbgDeviceCode &code, const uint64_t (&key)[K],
+                                           const BlockSmem<W> &sm, int lane)
+{
+    const int n = code.n;
 #pragma unroll
     for (int k = 0; k < K; k++) {
         const int e = lane * K + k;
         if (e < n) {
             int idx = (int)(uint32_t)key[k];
-            pi[e] = (uint8_t)idx;
-            h[e] = load_col<W>(code.hcol, idx);
+            sm.pi[e] = (uint8_t)idx;
+            sm.h[e] = load_col<W>(code.hcol, idx);
         }
     }
     if (lane == 0)
-        h[n] = szero<T>();
-    __syncwarp();
+        sm.h[n] = szero<typename Syn<W>::T>();
+}
 
-    /* 4. runs in groups of 32 */
-    const uint32_t limit = cap;          /* hits above the cap do not count */
-    uint32_t best = 0xFFFFFFFFu;
-    uint32_t my_t = 0xFFFFFFFFu;         /* hit this lane found and kept */
-    uint32_t my_run = 0, my_j = 0;
-    const uint4 *runs4 = reinterpret_cast<const uint4 *>(code.runs);
-    for (uint32_t g = 0; g < code.ngroups; g++) {
-        uint32_t floor = __ldg(code.group_floor + g);
-        if (floor >= best || floor > limit)
-            break;
-        uint32_t e = g * ORBG_GROUP + (uint32_t)lane;
-        uint32_t mine = 0xFFFFFFFFu, mj = 0;
-        if (e < code.nruns) {
-            uint4 v0 = __ldg(runs4 + 2 * e);
-            uint4 v1 = __ldg(runs4 + 2 * e + 1);
-            const uint32_t tstart = v0.x;
-            const int pair_sum = (int)(v0.y & 0xFFFFu);
-            int a = (int)(v0.y >> 16);
-            const int len = (int)(v0.z & 0xFFu);
-            const int npre = (int)((v0.z >> 8) & 0xFFu);
-            if (tstart < best && tstart <= limit) {
-                T P = s0;
+/* -------------------------------------------------- step 4: one run */
+
+/* Walk one run (two 16-byte halves v0, v1) unless it cannot beat `best`.
+ * Returns the run's first hit index (or ORBG_NONE) and its offset j.
+ * h[] has n+1 entries, the last one zero: prefix slots past npre read it,
+ * so the first eight prefix loads are issued without waiting on npre. */
+template <int W>
+__device__ __forceinline__ uint32_t search_run(const uint4 &v0, const uint4 &v1,
+                                               const typename Syn<W>::T *__restrict__ h,
+                                               const typename Syn<W>::T s0, uint32_t best,
+                                               uint32_t cap, int n, uint32_t *mj)
+{
+    typedef typename Syn<W>::T T;
+    const uint32_t tstart = v0.x;
+    if (!(tstart < best && tstart <= cap))
+        return ORBG_NONE;
+    const int pair_sum = (int)(v0.y & 0xFFFFu);
+    int a = (int)(v0.y >> 16);
+    const int len = (int)(v0.z & 0xFFu);
+    const int npre = (int)((v0.z >> 8) & 0xFFu);
+    /* prefix positions 0..7, independent loads (zero column past npre) */
+    T p[8];
 #pragma unroll
-                for (int i = 0; i < ORBG_RUN_MAX_PRE; i++) {
-                    if (i >= npre)
-                        break;
-                    uint32_t wd = (i < 4) ? v0.w : (i < 8) ? v1.x : (i < 12) ? v1.y
-                                : (i < 16) ? v1.z : v1.w;
-                    P = sx(P, h[(wd >> (8 * (i & 3))) & 0xFFu]);
-                }
-                int b = pair_sum - a;
-                for (int j = 0; j < len; j++, a++, b--) {
-                    T s = sx(sx(P, h[a]), h[b]);
-                    if (sz(s)) {
-                        mine = tstart + (uint32_t)j;
-                        mj = (uint32_t)j;
-                        break;
-                    }
-                }
-            }
-        }
-        uint32_t gbest = __reduce_min_sync(FULL_MASK, mine);
-        if (gbest < best) {
-            best = gbest;
-            if (mine == gbest) {
-                my_t = mine;
-                my_run = e;
-                my_j = mj;
-            }
+    for (int i = 0; i < 8; i++) {
+        const uint32_t wd = i < 4 ? v0.w : v1.x;
+        const int pos = i < npre ? (int)((wd >> (8 * (i & 3))) & 0xFFu) : n;
+        p[i] = h[pos];
+    }
+    T P = sx(sx(sx(s0, p[0]), sx(p[1], p[2])), sx(sx(p[3], p[4]), sx(p[5], sx(p[6], p[7]))));
+    if (npre > 8) {
+#pragma unroll
+        for (int i = 8; i < ORBG_RUN_MAX_PRE; i++) {
+            if (i >= npre)
+                break;
+            const uint32_t wd = (i < 12) ? v1.y : (i < 16) ? v1.z : v1.w;
+            P = sx(P, h[(wd >> (8 * (i & 3))) & 0xFFu]);
         }
     }
+    /* the run, two queries per step; the second slot is clamped into the
+     * table and masked when it lies past the run */
+    int b = pair_sum - a;
+    for (int j = 0; j < len; j += 2, a += 2, b -= 2) {
+        const int a1 = min(a + 1, n), b1 = max(b - 1, 0);
+        const T s_0 = sx(sx(P, h[a]), h[b]);
+        const T s_1 = sx(sx(P, h[a1]), h[b1]);
+        const bool z0 = sz(s_0);
+        const bool z1 = sz(s_1) && (j + 1 < len);
+        if (z0 || z1) {
+            const uint32_t jj = (uint32_t)j + (z0 ? 0u : 1u);
+            *mj = jj;
+            return tstart + jj;
+        }
+    }
+    return ORBG_NONE;
+}
 
-    /* 5. output */
-    const bool hit = best <= limit;
-    if (hit && my_t == best) {
-        /* the lane that owns the winning run applies the flips */
-        const OrbgRun *rp = code.runs + my_run;
-        int npre = rp->npre;
-        for (int i = 0; i < npre; i++)
-            cw[pi[rp->pre[i]]] ^= 1;
-        int a = (int)rp->a0 + (int)my_j;
-        if (a < n) {
-            int b = (int)rp->pair_sum - a;
-            cw[pi[a]] ^= 1;
-            cw[pi[b]] ^= 1;
-        }
+__device__ __forceinline__ void load_run(const OrbgDeviceCode &code, uint32_t e, uint4 *v0,
+                                         uint4 *v1)
+{
+    if (e < code.nruns) {
+        const uint4 *runs4 = reinterpret_cast<const uint4 *>(code.runs);
+        *v0 = __ldg(runs4 + 2 * e);
+        *v1 = __ldg(runs4 + 2 * e + 1);
+    } else {
+        *v0 = make_uint4(ORBG_NONE, 0u, 0u, 0u); /* tstart = NONE: never searched */
+        *v1 = make_uint4(0u, 0u, 0u, 0u);
     }
+}
+
+/* ----------------------------------------------------- step 5: output */
+
+/* The owner of the winning run applies its flips to the staged codeword. */
+__device__ __forceinline__ void apply_flips(const OrbgDeviceCode &code, uint32_t run, uint32_t j,
+                                            const uint8_t *pi, uint8_t *cw)
+{
+    const OrbgRun *rp = code.runs + run;
+    const int npre = rp->npre;
+    for (int i = 0; i < npre; i++)
+        cw[pi[rp->pre[i]]] ^= 1;
+    const int a = (int)rp->a0 + (int)j;
+    if (a < code.n) {
+        const int b = (int)rp->pair_sum - a;
+        cw[pi[a]] ^= 1;
+        cw[pi[b]] ^= 1;
+    }
+}
+
+/* ------------------------------------------------ one warp, one block */
+
+/*
+ * Decode one block with one warp.  Groups are walked from 0 while their
+ * floor (the smallest first index of any later run) is below the best hit,
+ * at most `cap`, and at most `budget`.  If the walk stops on the budget
+ * with the result still open, the block is not written: its index is
+ * appended to heavy[] (when heavy != NULL) for decode_block_cta.  With
+ * budget >= cap every block finishes here.
+ */
+template <int K, int W>
+__device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__restrict__ llr,
+                                  uint8_t *__restrict__ cw_out, uint32_t *__restrict__ q_out,
+                                  uint8_t *__restrict__ ab_out, uint32_t cap, uint32_t budget,
+                                  unsigned char *__restrict__ bsm, int lane,
+                                  unsigned long long *heavy, unsigned long long *heavy_count,
+                                  unsigned long long block_index)
+{
+    typedef typename Syn<W>::T T;
+    const int n = code.n;
+    BlockSmem<W> sm(bsm, n);
+    uint64_t key[K];
+    bool nan;
+    const T s0 = load_block<K, W>(code, llr, key, sm.cw, lane, &nan);
+    uint32_t best = ORBG_NONE, my_t = ORBG_NONE, my_run = 0, my_j = 0;
+    bool done = true;
+    if (nan) {
+        best = ORBG_NONE - 1; /* marker: NaN block */
+    } else if (sz(s0)) {
+        best = 1u;            /* query 1, the zero pattern, is a codeword */
+    } else {
+        sort_block<K>(key, llr, n, lane);
+        build_perm<K, W>(code, key, sm, lane);
+        __syncwarp();
+        uint32_t stop = ORBG_NONE;
+        uint4 n0, n1;
+        load_run(code, (uint32_t)lane, &n0, &n1);
+        for (uint32_t g = 0; g < code.ngroups; g++) {
+            const uint32_t floor = __ldg(code.group_floor + g);
+            if (floor >= best || floor > cap || floor > budget) {
+                stop = floor;
+                break;
+            }
+            const uint4 v0 = n0, v1 = n1;
+            load_run(code, (g + 1) * ORBG_GROUP + (uint32_t)lane, &n0, &n1); /* prefetch */
+            uint32_t mj = 0;
+            const uint32_t mine = search_run<W>(v0, v1, sm.h, s0, best, cap, n, &mj);
+            const uint32_t gbest = __reduce_min_sync(FULL_MASK, mine);
+            if (gbest < best) {
+                best = gbest;
+                if (mine == gbest) {
+                    my_t = mine;
+                    my_run = g * ORBG_GROUP + (uint32_t)lane;
+                    my_j = mj;
+                }
+            }
+        }
+        done = stop >= best || stop > cap; /* exhausted tables give stop = NONE */
+    }
+    if (!done) {
+        if (heavy != nullptr && lane == 0) {
+            unsigned long long slot = atomicAdd(heavy_count, 1ull);
+            heavy[slot] = block_index;
+        }
+        __syncwarp();
+        return;
+    }
+    const bool is_nan = best == ORBG_NONE - 1;
+    const bool hit = !is_nan && best <= cap;
+    if (hit && my_t == best)
+        apply_flips(code, my_run, my_j, sm.pi, sm.cw);
     __syncwarp();
 #pragma unroll
     for (int k = 0; k < K; k++) {
         int i = k * 32 + lane;
         if (i < n)
-            cw_out[i] = cw[i];
+            cw_out[i] = sm.cw[i];
     }
     if (lane == 0) {
-        *q_out = hit ? best : cap;
-        *ab_out = hit ? 0 : 1;
+        *q_out = is_nan ? 0u : hit ? best : cap;
+        *ab_out = is_nan ? 2 : hit ? 0 : 1;
     }
     __syncwarp();
 }
 
-/* Runtime dispatch on (n, syndrome width), warp-uniform; only variants up to
- * (KMAX keys per lane, WMAX syndrome words) are instantiated. */
-template <int K, int WMAX>
-__device__ __forceinline__ void decode_w(const OrbgDeviceCode &code, const float *llr, uint8_t *cw,
-                                         uint32_t *q, uint8_t *ab, uint32_t cap,
-                                         unsigned char *wsm, int lane)
+/* ------------------------------------------------ one CTA, one block */
+
+/*
+ * All warps of the CTA decode one block.  Warp 0 loads and sorts; then warp
+ * w walks groups w, w + nw, w + 2 nw, ...  Each warp stops at its first
+ * group whose floor is at least the shared best (or above the cap): floors
+ * never decrease with the group index and the best never increases, so no
+ * group that could hold the final best is skipped.  s_best must be set to
+ * ORBG_NONE and s_s0 written by the caller's protocol below.
+ */
+template <int K, int W>
+__device__ void decode_block_cta(const OrbgDeviceCode &code, const float *__restrict__ llr,
+                                 uint8_t *__restrict__ cw_out, uint32_t *__restrict__ q_out,
+                                 uint8_t *__restrict__ ab_out, uint32_t cap,
+                                 unsigned char *__restrict__ bsm, uint32_t *s_best,
+                                 typename Syn<W>::T *s_s0, int warp, int lane, int nwarps)
 {
-    const int w = code.w32;
-    if constexpr (WMAX >= 4) {
-        if (w > 2) {
-            decode_block<K, 4>(code, llr, cw, q, ab, cap, wsm, lane);
-            return;
+    typedef typename Syn<W>::T T;
+    const int n = code.n;
+    BlockSmem<W> sm(bsm, n);
+    if (warp == 0) {
+        uint64_t key[K];
+        bool nan;
+        const T s0 = load_block<K, W>(code, llr, key, sm.cw, lane, &nan);
+        if (nan || sz(s0)) {
+            /* not expected here (the warp pass finishes these), but exact */
+            if (lane == 0)
+                *s_best = nan ? ORBG_NONE - 1 : 1u;
+        } else {
+            sort_block<K>(key, llr, n, lane);
+            build_perm<K, W>(code, key, sm, lane);
+            if (lane == 0) {
+                *s_best = ORBG_NONE;
+                *s_s0 = s0;
+            }
         }
     }
-    if constexpr (WMAX >= 2) {
-        if (w == 2) {
-            decode_block<K, 2>(code, llr, cw, q, ab, cap, wsm, lane);
-            return;
+    __syncthreads();
+    uint32_t my_t = ORBG_NONE, my_run = 0, my_j = 0;
+    const uint32_t start = *s_best;
+    if (start == ORBG_NONE) {
+        const T s0 = *s_s0;
+        uint4 n0, n1;
+        uint32_t g = (uint32_t)warp;
+        load_run(code, g * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
+        for (; g < code.ngroups; g += (uint32_t)nwarps) {
+            const uint32_t floor = __ldg(code.group_floor + g);
+            const uint32_t best = *((volatile uint32_t *)s_best);
+            if (floor >= best || floor > cap)
+                break;
+            const uint4 v0 = n0, v1 = n1;
+            load_run(code, (g + nwarps) * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
+            uint32_t mj = 0;
+            const uint32_t mine = search_run<W>(v0, v1, sm.h, s0, best, cap, n, &mj);
+            const uint32_t gbest = __reduce_min_sync(FULL_MASK, mine);
+            if (gbest != ORBG_NONE) {
+                if (mine == gbest) {
+                    my_t = mine;
+                    my_run = g * ORBG_GROUP + (uint32_t)lane;
+                    my_j = mj;
+                    atomicMin(s_best, mine);
+                }
+            }
         }
     }
-    decode_block<K, 1>(code, llr, cw, q, ab, cap, wsm, lane);
+    __syncthreads();
+    const uint32_t best = *s_best;
+    const bool is_nan = best == ORBG_NONE - 1;
+    const bool hit = !is_nan && best <= cap;
+    if (start == ORBG_NONE && hit && my_t == best)
+        apply_flips(code, my_run, my_j, sm.pi, sm.cw);
+    __syncthreads();
+    for (int i = warp * 32 + lane; i < n; i += nwarps * 32)
+        cw_out[i] = sm.cw[i];
+    if (warp == 0 && lane == 0) {
+        *q_out = is_nan ? 0u : hit ? best : cap;
+        *ab_out = is_nan ? 2 : hit ? 0 : 1;
+    }
+    __syncthreads();
 }
 
-template <int KMAX, int WMAX>
-__device__ __forceinline__ void decode_any(const OrbgDeviceCode &code, const float *llr,
-                                           uint8_t *cw, uint32_t *q, uint8_t *ab, uint32_t cap,
-                                           unsigned char *wsm, int lane)
-{
-    const int n = code.n;
-    if constexpr (KMAX >= 8) {
-        if (n > 128) {
-            decode_w<8, WMAX>(code, llr, cw, q, ab, cap, wsm, lane);
-            return;
-        }
-    }
-    if constexpr (KMAX >= 4) {
-        if (n > 64) {
-            decode_w<4, WMAX>(code, llr, cw, q, ab, cap, wsm, lane);
-            return;
-        }
-    }
-    if constexpr (KMAX >= 2) {
-        if (n > 32) {
-            decode_w<2, WMAX>(code, llr, cw, q, ab, cap, wsm, lane);
-            return;
-        }
-    }
-    decode_w<1, WMAX>(code, llr, cw, q, ab, cap, wsm, lane);
-}
+/* ----------------------------------------------------------- dispatch */
+
+/* Runtime dispatch on (n, syndrome width), warp-uniform; only variants up to
+ * (KMAX keys per lane, WMAX syndrome words) are instantiated. */
+#define ORBG_DISPATCH(KMAX, WMAX, CALL)                                   \
+    do {                                                                  \
+        const int n_ = code.n, w_ = code.w32;                             \
+        bool done_ = false;                                               \
+        if constexpr (KMAX >= 8) {                                        \
+            if (!done_ && n_ > 128) { ORBG_DISPATCH_W(8, WMAX, CALL); done_ = true; } \
+        }                                                                 \
+        if constexpr (KMAX >= 4) {                                        \
+            if (!done_ && n_ > 64) { ORBG_DISPATCH_W(4, WMAX, CALL); done_ = true; } \
+        }                                                                 \
+        if constexpr (KMAX >= 2) {                                        \
+            if (!done_ && n_ > 32) { ORBG_DISPATCH_W(2, WMAX, CALL); done_ = true; } \
+        }                                                                 \
+        if (!done_) { ORBG_DISPATCH_W(1, WMAX, CALL); }                  \
+    } while (0)
+
+#define ORBG_DISPATCH_W(KK, WMAX, CALL)                                   \
+    do {                                                                  \
+        bool dw_ = false;                                                 \
+        if constexpr (WMAX >= 4) {                                        \
+            if (w_ > 2) { CALL(KK, 4); dw_ = true; }                      \
+        }                                                                 \
+        if constexpr (WMAX >= 2) {                                        \
+            if (!dw_ && w_ == 2) { CALL(KK, 2); dw_ = true; }             \
+        }                                                                 \
+        if (!dw_) { CALL(KK, 1); }                                        \
+    } while (0)
 
 }  // namespace orbg_dev

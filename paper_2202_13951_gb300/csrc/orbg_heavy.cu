@@ -1,0 +1,101 @@
+/*
+ * orbg_heavy.cu -- phase 2 of the batched form: every CTA takes one block
+ * left open by phase 1 at a time and searches it with all its warps
+ * (decode_block_cta in orbg_decode_block.cuh).
+ */
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "orbg_decode_block.cuh"
+
+using namespace orbg_dev;
+
+namespace {
+
+template <int KMAX, int WMAX>
+__global__ void __launch_bounds__(512, 2) orbg_heavy_kernel(
+    const OrbgDeviceCode *__restrict__ codes, int ncodes, const int32_t *__restrict__ code_id,
+    const int64_t *__restrict__ llr_off, const float *__restrict__ llr, uint32_t cap,
+    uint8_t *__restrict__ cw, const int64_t *__restrict__ cw_off, uint32_t *__restrict__ q,
+    uint8_t *__restrict__ ab, unsigned long long *__restrict__ counters,
+    const unsigned long long *__restrict__ heavy)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long s_block;
+    __shared__ uint32_t s_best;
+    __shared__ uint4 s_s0;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    const int64_t n0 = codes[0].n;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const unsigned long long nheavy = *((volatile unsigned long long *)&counters[1]);
+            const unsigned long long slot = atomicAdd(&counters[2], 1ull);
+            s_block = slot < nheavy ? heavy[slot] : ~0ull;
+        }
+        __syncthreads();
+        const unsigned long long bb = s_block;
+        if (bb == ~0ull)
+            break; /* uniform: every thread read the same s_block */
+        const int64_t b = (int64_t)bb;
+        const int cid = code_id ? code_id[b] : 0; /* checked in phase 1 */
+        const OrbgDeviceCode code = codes[cid];
+        const int64_t lo = llr_off ? llr_off[b] : b * n0;
+        const int64_t co = cw_off ? cw_off[b] : b * n0;
+#define ORBG_CALL_CTA(KK, WW)                                                               \
+    decode_block_cta<KK, WW>(code, llr + lo, cw + co, q + b, ab + b, cap, smem, &s_best,     \
+                             reinterpret_cast<typename Syn<WW>::T *>(&s_s0), warp, lane, nwarps)
+        ORBG_DISPATCH(KMAX, WMAX, ORBG_CALL_CTA);
+#undef ORBG_CALL_CTA
+    }
+    (void)ncodes;
+}
+
+template <int KMAX, int WMAX>
+cudaError_t launch_heavy_t(const OrbgDeviceCode *d_codes, int ncodes, int n_max, int w32_max,
+                           const int32_t *code_id, const int64_t *llr_off, const float *llr,
+                           uint32_t cap, uint8_t *cw, const int64_t *cw_off, uint32_t *q,
+                           uint8_t *ab, unsigned long long *counters,
+                           const unsigned long long *heavy, int heavy_warps, cudaStream_t st)
+{
+    auto k2 = orbg_heavy_kernel<KMAX, WMAX>;
+    const int hw = heavy_warps > 0 ? heavy_warps : 16;
+    const uint32_t bstride = block_smem_bytes(n_max, w32_max);
+    int grid = 0;
+    int rc = orbg_grid_for((const void *)k2, hw * 32, bstride, 0, &grid);
+    if (rc != 0)
+        return (cudaError_t)rc;
+    k2<<<grid, hw * 32, bstride, st>>>(d_codes, ncodes, code_id, llr_off, llr, cap, cw, cw_off, q,
+                                       ab, counters, heavy);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int orbg_launch_heavy(const OrbgDeviceCode *d_codes, int ncodes, int n_max, int w32_max,
+                      const int32_t *code_id, const int64_t *llr_off, const float *llr,
+                      uint32_t cap, uint8_t *cw, const int64_t *cw_off, uint32_t *q, uint8_t *ab,
+                      unsigned long long *counters, const unsigned long long *heavy,
+                      int heavy_warps, void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+#define ORBG_H(KM, WM)                                                                         \
+    return (int)launch_heavy_t<KM, WM>(d_codes, ncodes, n_max, w32_max, code_id, llr_off, llr, \
+                                       cap, cw, cw_off, q, ab, counters, heavy, heavy_warps, st);
+#define ORBG_HW(KM)                          \
+    if (w32_max <= 1) { ORBG_H(KM, 1) }      \
+    else if (w32_max <= 2) { ORBG_H(KM, 2) } \
+    else { ORBG_H(KM, 4) }
+    if (n_max <= 32) {
+        ORBG_HW(1)
+    } else if (n_max <= 64) {
+        ORBG_HW(2)
+    } else if (n_max <= 128) {
+        ORBG_HW(4)
+    } else {
+        ORBG_HW(8)
+    }
+#undef ORBG_HW
+#undef ORBG_H
+}

@@ -77,9 +77,21 @@ int orbg_launch_plain(const OrbgDeviceCode &code, const float *llr, int64_t B,
 int orbg_launch_batched(const OrbgDeviceCode *d_codes, int ncodes, int n_max,
                         int w32_max, const int32_t *code_id,
                         const int64_t *llr_off, const float *llr, int64_t B,
-                        uint32_t cap, uint8_t *cw, const int64_t *cw_off,
-                        uint32_t *q, uint8_t *ab, unsigned long long *counter,
-                        int warps_per_cta, int ctas_per_sm, void *stream);
+                        uint32_t cap, uint32_t budget, uint8_t *cw,
+                        const int64_t *cw_off, uint32_t *q, uint8_t *ab,
+                        unsigned long long *scratch, int warps_per_cta,
+                        int ctas_per_sm, int grab, int heavy_warps, void *stream);
+/* device scratch the batched form needs for B blocks: counters (queue head,
+ * open-block count, phase-2 cursor) and the list of open blocks */
+#define ORBG_BATCHED_COUNTERS 8
+size_t orbg_batched_scratch_bytes(int64_t B);
+int orbg_launch_heavy(const OrbgDeviceCode *d_codes, int ncodes, int n_max, int w32_max,
+                      const int32_t *code_id, const int64_t *llr_off, const float *llr,
+                      uint32_t cap, uint8_t *cw, const int64_t *cw_off, uint32_t *q, uint8_t *ab,
+                      unsigned long long *counters, const unsigned long long *heavy,
+                      int heavy_warps, void *stream);
+int orbg_grid_for(const void *kern, int threads, size_t smem, int ctas_per_sm, int *grid_out);
+int orbg_launch_int_probe(double *lanes_per_clk_per_sm);
 #endif
 
 #endif /* ORBG_INTERNAL_H */

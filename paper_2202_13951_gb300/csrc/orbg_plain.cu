@@ -27,8 +27,8 @@ __global__ void __launch_bounds__(256) orbg_plain_kernel(OrbgDeviceCode code,
     if (b >= B)
         return; /* whole warp */
     const int64_t off = b * (int64_t)code.n;
-    decode_block<K, W>(code, llr + off, cw + off, q + b, ab + b, cap, smem + warp * wstride,
-                       lane);
+    decode_block_warp<K, W>(code, llr + off, cw + off, q + b, ab + b, cap, cap,
+                            smem + warp * wstride, lane, nullptr, nullptr, 0ull);
 }
 
 template <int K, int W>
@@ -36,7 +36,7 @@ cudaError_t launch_plain_t(const OrbgDeviceCode &code, const float *llr, int64_t
                            uint8_t *cw, uint32_t *q, uint8_t *ab, cudaStream_t st)
 {
     const int wpc = 8;
-    uint32_t wstride = warp_smem_bytes(code.n, W);
+    uint32_t wstride = block_smem_bytes(code.n, W);
     size_t smem = (size_t)wstride * wpc;
     int64_t grid = (B + wpc - 1) / wpc;
     if (grid > 0x7FFFFFFF)

@@ -35,6 +35,16 @@ LIB_PATH = _build.LIB
 _lib = None
 
 
+class OrbgTuning(ctypes.Structure):
+    """struct orbg_tuning of include/orbg.h."""
+    _fields_ = [("warps_per_cta", ctypes.c_int), ("ctas_per_sm", ctypes.c_int),
+                ("blocks_per_grab", ctypes.c_int), ("warp_budget", ctypes.c_uint32),
+                ("heavy_warps", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class OrbgError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
@@ -72,8 +82,9 @@ def load_library(path=None):
     lib.orbg_codeset_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
     lib.orbg_codeset_free.argtypes = [vp]
     lib.orbg_decode_batched.argtypes = [vp, vp, vp, vp, i64, u32, vp, vp, vp, vp, vp]
-    lib.orbg_set_launch_shape.argtypes = [i32, i32]
-    lib.orbg_get_launch_shape.argtypes = [ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.orbg_codeset_set_tuning.argtypes = [vp, ctypes.POINTER(OrbgTuning)]
+    lib.orbg_codeset_get_tuning.argtypes = [vp, ctypes.POINTER(OrbgTuning)]
+    lib.orbg_probe_int_lanes.argtypes = [ctypes.POINTER(ctypes.c_double)]
     lib.orbg_status_string.argtypes = [i32]
     lib.orbg_status_string.restype = ctypes.c_char_p
     lib.orbg_last_cuda_error.argtypes = []
@@ -82,7 +93,7 @@ def load_library(path=None):
     lib.orbg_query_order.restype = i64
     for f in ("orbg_load_code", "orbg_free_code", "orbg_code_info", "orbg_decode",
               "orbg_codeset_create", "orbg_codeset_free", "orbg_decode_batched",
-              "orbg_set_launch_shape", "orbg_get_launch_shape",
+              "orbg_codeset_set_tuning", "orbg_codeset_get_tuning", "orbg_probe_int_lanes",
               "orbg_last_cuda_error", "orbg_version"):
         getattr(lib, f).restype = i32
     if path == LIB_PATH:
@@ -185,17 +196,28 @@ def orbg_decode_batched(cs, code_id, llr_offset, llr, B, query_cap, codeword, cw
     _check(rc, "orbg_decode_batched")
 
 
-def orbg_set_launch_shape(warps_per_cta=0, ctas_per_sm=0):
-    _check(load_library().orbg_set_launch_shape(int(warps_per_cta), int(ctas_per_sm)),
-           "orbg_set_launch_shape")
+def orbg_codeset_set_tuning(cs, tuning=None):
+    """tuning: OrbgTuning, a dict of its fields, or None for the defaults."""
+    t = None
+    if tuning is not None:
+        if isinstance(tuning, dict):
+            tuning = OrbgTuning(**tuning)
+        t = ctypes.byref(tuning)
+    _check(load_library().orbg_codeset_set_tuning(cs, t), "orbg_codeset_set_tuning")
 
 
-def orbg_get_launch_shape():
-    a = ctypes.c_int()
-    b = ctypes.c_int()
-    _check(load_library().orbg_get_launch_shape(ctypes.byref(a), ctypes.byref(b)),
-           "orbg_get_launch_shape")
-    return a.value, b.value
+def orbg_codeset_get_tuning(cs):
+    t = OrbgTuning()
+    _check(load_library().orbg_codeset_get_tuning(cs, ctypes.byref(t)),
+           "orbg_codeset_get_tuning")
+    return t
+
+
+def orbg_probe_int_lanes():
+    """lop3.b32 lanes retired per SM per clock on the current device."""
+    x = ctypes.c_double()
+    _check(load_library().orbg_probe_int_lanes(ctypes.byref(x)), "orbg_probe_int_lanes")
+    return x.value
 
 
 def orbg_status_string(status):

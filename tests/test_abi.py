@@ -47,13 +47,10 @@ def test_status_strings_and_version(lib):
     assert orbg.orbg_version() == 100
 
 
-def test_launch_shape_roundtrip(lib):
-    old = orbg.orbg_get_launch_shape()
-    orbg.orbg_set_launch_shape(4, 2)
-    assert orbg.orbg_get_launch_shape() == (4, 2)
-    with pytest.raises(orbg.OrbgError):
-        orbg.orbg_set_launch_shape(17, 0)
-    orbg.orbg_set_launch_shape(*old)
+def test_tuning_argument_checks(lib):
+    t = orbg.OrbgTuning(8, 0, 8, 4096, 16)
+    assert lib.orbg_codeset_set_tuning(None, ctypes.byref(t)) == orbg.ORBG_EINVAL
+    assert lib.orbg_codeset_get_tuning(None, ctypes.byref(t)) == orbg.ORBG_EINVAL
 
 
 def test_load_code_rejects_bad_input_before_any_cuda_call(lib):
@@ -87,6 +84,7 @@ def test_decode_argument_checks_without_gpu(lib):
     assert lib.orbg_code_info(None, None, None, None, None) == orbg.ORBG_EINVAL
     assert lib.orbg_free_code(None) == orbg.ORBG_OK
     assert lib.orbg_codeset_free(None) == orbg.ORBG_OK
+    assert lib.orbg_probe_int_lanes(None) == orbg.ORBG_EINVAL
 
 
 @pytest.mark.parametrize("n,count", [(1, 2), (3, 8), (7, 128), (12, 4096),

@@ -1,0 +1,61 @@
+"""bench.py's multi-GPU host logic on CPU with gloo, world size 2: every rank
+decodes its own seeded workload (replicas, no data-path collective) and the
+timing / work totals are reduced over ranks (max / sum)."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    os.environ["RANK"] = str(rank)
+    os.environ["WORLD_SIZE"] = str(world)
+    os.environ["LOCAL_RANK"] = str(rank)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    bench.select_workload("bch", 50)
+    r, w, lr = bench.dist_env()
+    assert (r, w, lr) == (rank, world, rank)
+    code, llr = bench.make_inputs(rank)
+    t = bench.max_over_ranks(1.0 + rank, world)
+    s = bench.sum_over_ranks(float(llr.shape[0]), world)
+    out[rank] = (t, s, float(llr[0, 0]), bench.rank_seeds(rank)[0])
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_rank_reductions_and_sharding():
+    world = 2
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
+    (t0, s0, x0, seed0), (t1, s1, x1, seed1) = out[0], out[1]
+    assert t0 == t1 == 2.0            # max over ranks
+    assert s0 == s1 == 2 * 4 * 50     # total blocks of both replicas
+    assert seed0 != seed1 and x0 != x1  # each rank its own seeded data
+
+
+def test_class_weight_prefix_matches_oracle():
+    import bench
+    import oracle
+    from paper_2202_13951_gb300 import workloads
+    code = workloads.rlc(64, 48, 5)
+    llr, _ = workloads.awgn_llr(code, 200, 3.0, 6)
+    _, q, _, sw = oracle.decode_batch(code.H, llr, 10 ** 5)
+    ends, ws = bench.class_weight_prefix(code.n, 10 ** 5)
+    assert bench.sum_weights(q, ends, ws) == int(sw.sum())

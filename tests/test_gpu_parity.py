@@ -230,3 +230,45 @@ def test_config3_full_size_sampled(orbg):
     syndromes, heavy abandonment); 120 seeded random blocks checked."""
     code, llr, _ = workloads.config3_inputs()
     _sampled(orbg, code, llr, 10 ** 6, 120, 3)
+
+
+@pytest.mark.parametrize("tuning", [(8, 0, 8, 1, 16), (4, 0, 1, 64, 4), (16, 0, 32, 4096, 1),
+                                    (2, 1, 3, 100, 7), (8, 0, 8, 10 ** 6, 16)],
+                         ids=lambda t: "wpc%d_cps%d_grab%d_budget%d_hw%d" % t)
+def test_batched_tuning_does_not_change_results(orbg, tuning):
+    """Phase-1 budget down to one group (nearly every block goes to the CTA
+    phase), one to sixteen warps per open block, any grab size: the batched
+    form still returns the oracle's first hit, abandons included."""
+    code = workloads.rlc(64, 44, 61)
+    llr, _ = workloads.awgn_llr(code, 600, 2.5, 62)
+    cap = 100000
+    want = oracle.decode_batch(code.H, llr, cap)[:3]
+    assert want[2].any() and not want[2].all()  # some blocks abandon
+    c = orbg.Code(code.H, max_query_cap=cap)
+    cs = orbg.CodeSet([c])
+    orbg.orbg_codeset_set_tuning(cs.handle, orbg.OrbgTuning(*tuning))
+    assert_same(gpu_batched(orbg, cs, llr, cap), want)
+
+
+def test_mixed_codes_phase2(orbg):
+    """Mixed n and n-k in one batched call with a small phase-1 budget, so
+    the CTA phase sees blocks of every code."""
+    codes, cid, llr, off, cwt, ebn0 = workloads.config4_inputs(B=3000, seed=4402)
+    objs = [orbg.Code(cd.H, max_query_cap=2 * 10 ** 5) for cd in codes]
+    cs = orbg.CodeSet(objs)
+    orbg.orbg_codeset_set_tuning(cs.handle, orbg.OrbgTuning(8, 0, 4, 32, 8))
+    llr_t = torch.from_numpy(llr).cuda()
+    off_t = torch.from_numpy(off).cuda()
+    cid_t = torch.from_numpy(cid).cuda()
+    cw, q, ab = orbg.decode_batched(cs, llr_t, 2 * 10 ** 5, code_id=cid_t, llr_offset=off_t,
+                                    cw_offset=off_t, n_total=llr.shape[0])
+    torch.cuda.synchronize()
+    cw, q, ab = cw.cpu().numpy(), q.cpu().numpy().astype(np.int64), ab.cpu().numpy()
+    rng = np.random.default_rng(6)
+    for j, cd in enumerate(codes):
+        idx = np.nonzero(cid == j)[0]
+        pick = np.sort(rng.choice(idx, size=min(60, idx.shape[0]), replace=False))
+        blocks = np.stack([llr[off[b]:off[b] + cd.n] for b in pick])
+        want = oracle.decode_batch(cd.H, blocks, 2 * 10 ** 5)[:3]
+        got = (np.stack([cw[off[b]:off[b] + cd.n] for b in pick]), q[pick], ab[pick])
+        assert_same(got, want)
