@@ -154,6 +154,43 @@ ORBG_API int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id
                         uint8_t *abandoned, void *cuda_stream);
 
 /*
+ * Batched decode that allocates nothing (the paper has no counterpart; this
+ * is a deployment variant of orbg_decode_batched).
+ *
+ * For callers that must not allocate device memory while decoding, e.g. a
+ * receiver that reserves all its GPU memory at start-up and treats a later
+ * allocation as a failure, or code that cannot let an allocation block
+ * behind other device work inside its latency budget.  orbg_decode_batched
+ * allocates its scratch on the stream on every call; this variant uses a
+ * fixed array compiled into the library instead, and calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   - Same arguments, layout and results as orbg_decode_batched, except
+ *     that every buffer must be device memory (host buffers would need
+ *     staging): EINVAL otherwise.
+ *   - B <= ORBG_NOALLOC_MAX_BLOCKS (524,288), else ELIMIT.  Larger batches
+ *     can be split into several calls.
+ *   - The array is 8 * (8 + ORBG_NOALLOC_MAX_BLOCKS) bytes (4 MiB + 64 B)
+ *     of device memory per GPU that loads the library, held until the
+ *     process exits.
+ *   - The first call on each device looks up the array's device address
+ *     (with that device current) and keeps it; make that first call before
+ *     any stream capture.
+ *   - All calls on a device share the one array; the counters that must
+ *     start at zero are cleared on cuda_stream at the start of each call.
+ *     Calls whose work overlaps on the GPU (other streams, or other host
+ *     threads) race on the array and give wrong results: serialise them.
+ */
+#define ORBG_NOALLOC_MAX_BLOCKS (1 << 19)
+ORBG_API int orbg_decode_batched_noalloc(const orbg_codeset *set,
+                                         const int32_t *code_id,
+                                         const int64_t *llr_offset,
+                                         const float *llr, int64_t B,
+                                         uint32_t query_cap, uint8_t *codeword,
+                                         const int64_t *cw_offset,
+                                         uint32_t *queries, uint8_t *abandoned,
+                                         void *cuda_stream);
+
+/*
  * Tuning of the batched form, per code set (the autotuner writes these):
  *   warps_per_cta   phase 1: warps per CTA, one block per warp (1..16; 0 = 8)
  *   ctas_per_sm     phase 1: resident CTAs per SM (0 = as many as fit)

@@ -14,7 +14,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liborbg.so")
-SOURCES = ["orbg_plain.cu", "orbg_batched.cu", "orbg_heavy.cu", "orbg_probe.cu", "orbg_api.cpp",
+SOURCES = ["orbg_plain.cu", "orbg_batched.cu", "orbg_heavy.cu", "orbg_noalloc.cu",
+           "orbg_probe.cu", "orbg_api.cpp",
            "orbg_tables.cpp"]
 HEADERS = ["orbg_internal.h", "orbg_decode_block.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

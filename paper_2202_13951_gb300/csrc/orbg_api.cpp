@@ -131,6 +131,24 @@ void free_code_device(orbg_code *c)
 
 }  // namespace
 
+int orbg_codeset_view(const orbg_codeset *set, OrbgSetView *out)
+{
+    if (!set || !out)
+        return -1;
+    out->d_codes = set->d_codes;
+    out->ncodes = set->ncodes;
+    out->n_max = set->n_max;
+    out->w32_max = set->w32_max;
+    out->cap_min = set->cap_min;
+    out->tuning = set->tuning;
+    return 0;
+}
+
+int orbg_note_cuda_error(int cuda_error)
+{
+    return cuda_fail((cudaError_t)cuda_error);
+}
+
 extern "C" {
 
 const char *orbg_status_string(int status)

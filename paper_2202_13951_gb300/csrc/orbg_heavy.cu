@@ -80,13 +80,13 @@ int orbg_launch_heavy(const OrbgDeviceCode *d_codes, int ncodes, int n_max, int 
                       int heavy_warps, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
-#define ORBG_H(KM, WM)                                                                         \
+#define ORBG_LH(KM, WM)                                                                         \
     return (int)launch_heavy_t<KM, WM>(d_codes, ncodes, n_max, w32_max, code_id, llr_off, llr, \
                                        cap, cw, cw_off, q, ab, counters, heavy, heavy_warps, st);
 #define ORBG_HW(KM)                          \
-    if (w32_max <= 1) { ORBG_H(KM, 1) }      \
-    else if (w32_max <= 2) { ORBG_H(KM, 2) } \
-    else { ORBG_H(KM, 4) }
+    if (w32_max <= 1) { ORBG_LH(KM, 1) }      \
+    else if (w32_max <= 2) { ORBG_LH(KM, 2) } \
+    else { ORBG_LH(KM, 4) }
     if (n_max <= 32) {
         ORBG_HW(1)
     } else if (n_max <= 64) {
@@ -97,5 +97,5 @@ int orbg_launch_heavy(const OrbgDeviceCode *d_codes, int ncodes, int n_max, int 
         ORBG_HW(8)
     }
 #undef ORBG_HW
-#undef ORBG_H
+#undef ORBG_LH
 }

@@ -91,6 +91,18 @@ int orbg_launch_heavy(const OrbgDeviceCode *d_codes, int ncodes, int n_max, int 
                       unsigned long long *counters, const unsigned long long *heavy,
                       int heavy_warps, void *stream);
 int orbg_grid_for(const void *kern, int threads, size_t smem, int ctas_per_sm, int *grid_out);
+
+/* What a launch needs of a code set (orbg_api.cpp owns the struct). */
+#include "../../include/orbg.h"
+struct OrbgSetView {
+    const OrbgDeviceCode *d_codes;
+    int ncodes, n_max, w32_max;
+    uint32_t cap_min;
+    orbg_tuning tuning;
+};
+int orbg_codeset_view(const orbg_codeset *set, OrbgSetView *out);
+/* Records a cudaError_t for orbg_last_cuda_error; returns the orbg status. */
+int orbg_note_cuda_error(int cuda_error);
 int orbg_launch_int_probe(double *lanes_per_clk_per_sm);
 #endif
 

@@ -1,0 +1,108 @@
+/*
+ * orbg_noalloc.cu -- a batched decode entry point that allocates nothing.
+ *
+ * Some callers cannot allocate device memory once they are running: a
+ * receiver that reserves all of its GPU memory at start-up and treats any
+ * later allocation as a fault, or code that must not risk an allocation
+ * blocking behind other work on the device while it holds a latency budget.
+ * orbg_decode_batched allocates its scratch (queue counters and the list of
+ * blocks left open by phase 1) on the stream for every call, so it is not
+ * usable there.  orbg_decode_batched_noalloc runs the same two launches with
+ * that scratch in a fixed array compiled into this library instead.
+ *
+ * The array is a file-scope __device__ variable: every GPU that loads the
+ * library holds it (8 * (8 + ORBG_NOALLOC_MAX_BLOCKS) bytes, 4 MiB + 64 B)
+ * until the process exits.  Host code cannot use the variable's name as a
+ * device address, so the first call on each device, with that device
+ * current, asks the runtime for the address (cudaGetSymbolAddress) and keeps
+ * it; later calls on that device reuse it.
+ */
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "../../include/orbg.h"
+#include "orbg_internal.h"
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+/* Scratch shared by every no-alloc call on a device: counters, then one
+ * slot per block for the open-block list. */
+static __device__ __align__(256) unsigned long long
+    g_orbg_noalloc_scratch[ORBG_BATCHED_COUNTERS + ORBG_NOALLOC_MAX_BLOCKS];
+
+std::mutex g_mu;
+unsigned long long *g_scratch_addr[kMaxDevices];
+
+/* Device address of the scratch array on the current device, looked up once
+ * per device. Returns a cudaError_t value. */
+int scratch_on_current_device(unsigned long long **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return (int)e;
+    if (dev < 0 || dev >= kMaxDevices)
+        return (int)cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_orbg_noalloc_scratch);
+        if (e != cudaSuccess)
+            return (int)e;
+        g_scratch_addr[dev] = (unsigned long long *)p;
+    }
+    *out = g_scratch_addr[dev];
+    return 0;
+}
+
+bool on_device(const void *p)
+{
+    if (!p)
+        return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" int orbg_decode_batched_noalloc(const orbg_codeset *set, const int32_t *code_id,
+                                           const int64_t *llr_offset, const float *llr,
+                                           int64_t B, uint32_t query_cap, uint8_t *codeword,
+                                           const int64_t *cw_offset, uint32_t *queries,
+                                           uint8_t *abandoned, void *cuda_stream)
+{
+    OrbgSetView v;
+    if (!set || B < 0 || query_cap < 1 || orbg_codeset_view(set, &v) != 0)
+        return ORBG_EINVAL;
+    if (B > ORBG_NOALLOC_MAX_BLOCKS || query_cap > v.cap_min)
+        return ORBG_ELIMIT;
+    if (B == 0)
+        return ORBG_OK;
+    if (!llr || !codeword || !queries || !abandoned ||
+        (llr_offset == nullptr) != (cw_offset == nullptr))
+        return ORBG_EINVAL;
+    /* staging host buffers would need an allocation: device buffers only */
+    if (!on_device(llr) || !on_device(codeword) || !on_device(queries) ||
+        !on_device(abandoned) || !on_device(code_id) || !on_device(llr_offset) ||
+        !on_device(cw_offset))
+        return ORBG_EINVAL;
+    unsigned long long *scratch = nullptr;
+    int e = scratch_on_current_device(&scratch);
+    if (e != 0)
+        return orbg_note_cuda_error(e);
+    const uint32_t budget = v.tuning.warp_budget < query_cap ? v.tuning.warp_budget : query_cap;
+    /* the launcher zeroes the counters on the stream before phase 1 */
+    e = orbg_launch_batched(v.d_codes, v.ncodes, v.n_max, v.w32_max, code_id, llr_offset, llr, B,
+                            query_cap, budget, codeword, cw_offset, queries, abandoned, scratch,
+                            v.tuning.warps_per_cta, v.tuning.ctas_per_sm,
+                            v.tuning.blocks_per_grab, v.tuning.heavy_warps, cuda_stream);
+    return e != 0 ? orbg_note_cuda_error(e) : ORBG_OK;
+}

@@ -30,6 +30,7 @@ ORBG_DEFAULT_QUERY_CAP = 1 << 20
 ORBG_BLOCK_DECODED = 0
 ORBG_BLOCK_ABANDONED = 1
 ORBG_BLOCK_NAN = 2
+ORBG_NOALLOC_MAX_BLOCKS = 1 << 19
 
 LIB_PATH = _build.LIB
 _lib = None
@@ -82,6 +83,7 @@ def load_library(path=None):
     lib.orbg_codeset_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.POINTER(vp)]
     lib.orbg_codeset_free.argtypes = [vp]
     lib.orbg_decode_batched.argtypes = [vp, vp, vp, vp, i64, u32, vp, vp, vp, vp, vp]
+    lib.orbg_decode_batched_noalloc.argtypes = [vp, vp, vp, vp, i64, u32, vp, vp, vp, vp, vp]
     lib.orbg_codeset_set_tuning.argtypes = [vp, ctypes.POINTER(OrbgTuning)]
     lib.orbg_codeset_get_tuning.argtypes = [vp, ctypes.POINTER(OrbgTuning)]
     lib.orbg_probe_int_lanes.argtypes = [ctypes.POINTER(ctypes.c_double)]
@@ -93,6 +95,7 @@ def load_library(path=None):
     lib.orbg_query_order.restype = i64
     for f in ("orbg_load_code", "orbg_free_code", "orbg_code_info", "orbg_decode",
               "orbg_codeset_create", "orbg_codeset_free", "orbg_decode_batched",
+              "orbg_decode_batched_noalloc",
               "orbg_codeset_set_tuning", "orbg_codeset_get_tuning", "orbg_probe_int_lanes",
               "orbg_last_cuda_error", "orbg_version"):
         getattr(lib, f).restype = i32
@@ -194,6 +197,19 @@ def orbg_decode_batched(cs, code_id, llr_offset, llr, B, query_cap, codeword, cw
         int(query_cap), _ptr(codeword, "uint8"), _ptr(cw_offset, "int64"),
         _ptr(queries, "uint32"), _ptr(abandoned, "uint8"), _stream(cuda_stream))
     _check(rc, "orbg_decode_batched")
+
+
+def orbg_decode_batched_noalloc(cs, code_id, llr_offset, llr, B, query_cap, codeword,
+                                cw_offset, queries, abandoned, cuda_stream=None):
+    """orbg_decode_batched without any device allocation: its scratch lives
+    in a fixed array inside the library.  Device buffers only; at most
+    ORBG_NOALLOC_MAX_BLOCKS blocks per call; calls that overlap on the GPU
+    race on the shared array."""
+    rc = load_library().orbg_decode_batched_noalloc(
+        cs, _ptr(code_id, "int32"), _ptr(llr_offset, "int64"), _ptr(llr, "float32"), int(B),
+        int(query_cap), _ptr(codeword, "uint8"), _ptr(cw_offset, "int64"),
+        _ptr(queries, "uint32"), _ptr(abandoned, "uint8"), _stream(cuda_stream))
+    _check(rc, "orbg_decode_batched_noalloc")
 
 
 def orbg_codeset_set_tuning(cs, tuning=None):
