@@ -41,6 +41,9 @@ WORKLOADS = {
             "config2_code", (4.0, 5.0, 6.0, 7.0), (201, 202, 203, 204)),
     "capolar": ("ca-polar(128,94[K=105]) 4x%d blocks at Eb/N0 3,4,5,6 dB, query cap 1e6",
                 "config3_code", (3.0, 4.0, 5.0, 6.0), (301, 302, 303, 304)),
+    "mixed": ("mixed rlc(64,51),(128,112),(256,240),(256,232), code uniform per block, "
+              "%d blocks at Eb/N0 U[4,7] dB, query cap 1e6, one launch, autotuned",
+              None, (), (401,)),
 }
 POINTS = (4.0, 5.0, 6.0, 7.0)
 SEEDS = (201, 202, 203, 204)
@@ -67,6 +70,8 @@ def parse_args(argv=None):
                    help="bch: the headline configuration; capolar: the search-heavy "
                         "CA-Polar configuration (profiling)")
     p.add_argument("--blocks-per-point", type=int, default=B_PER_POINT)
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the library's default tuning")
     p.add_argument("--shape", default="",
                    help="warps_per_cta,ctas_per_sm,blocks_per_grab,warp_budget,heavy_warps "
                         "for the batched launch (orbg_tuning)")
@@ -76,10 +81,14 @@ def parse_args(argv=None):
 
 
 def select_workload(name, b_per_point):
-    global WORKLOAD, POINTS, SEEDS, B_PER_POINT, CODE_FN
+    global WORKLOAD, POINTS, SEEDS, B_PER_POINT, CODE_FN, WORKLOAD_NAME
     desc, CODE_FN, POINTS, SEEDS = WORKLOADS[name]
+    WORKLOAD_NAME = name
     B_PER_POINT = b_per_point
-    WORKLOAD = desc % b_per_point
+    WORKLOAD = desc % (b_per_point * 10 if name == "mixed" else b_per_point)
+
+
+WORKLOAD_NAME = "bch"
 
 
 CODE_FN = "config2_code"
@@ -345,6 +354,66 @@ def bench_reference(args, rank, world):
 
 # ------------------------------------------------------------- GPU side
 
+class Job:
+    """One workload on the device: codes, inputs, outputs and the step."""
+
+    def __init__(self, orbg, dev, rank, args):
+        import torch
+        from paper_2202_13951_gb300 import workloads
+        self.orbg = orbg
+        if WORKLOAD_NAME == "mixed":
+            B = 10 * B_PER_POINT
+            codes, cid, llr, off, _, _ = workloads.config4_inputs(B=B, seed=SEEDS[0] + 1000 * rank)
+            self.codes = codes
+            self.cid_np, self.off_np, self.llr_np = cid, off, llr
+        else:
+            code, llr = make_inputs(rank)
+            self.codes = [code]
+            B = llr.shape[0]
+            self.cid_np = np.zeros(B, np.int32)
+            self.off_np = None
+            self.llr_np = llr
+        self.B = B
+        self.n_of_block = np.array([c.n for c in self.codes], np.int64)[self.cid_np]
+        self.objs = [orbg.Code(c.H, max_query_cap=CAP) for c in self.codes]
+        self.cs = orbg.CodeSet(self.objs)
+        self.llr = torch.from_numpy(self.llr_np).to(dev)
+        n_total = int(self.n_of_block.sum())
+        self.cw = torch.empty((n_total,), dtype=torch.uint8, device=dev)
+        self.q = torch.empty((B,), dtype=torch.int32, device=dev)
+        self.ab = torch.empty((B,), dtype=torch.uint8, device=dev)
+        if self.off_np is not None:
+            self.cid = torch.from_numpy(self.cid_np).to(dev)
+            self.off = torch.from_numpy(self.off_np).to(dev)
+        else:
+            self.cid = self.off = None
+        self.stream = torch.cuda.current_stream(dev)
+
+    def step(self):
+        self.orbg.orbg_decode_batched(self.cs.handle, self.cid, self.off, self.llr, self.B, CAP,
+                                      self.cw, self.off, self.q, self.ab, self.stream)
+
+    def autotune(self):
+        return self.orbg.orbg_codeset_autotune(self.cs.handle, self.cid, self.off, self.llr,
+                                               self.B, CAP, self.cw, self.off, self.q, self.ab,
+                                               2, self.stream)
+
+    def alg_ops(self, qh):
+        """Algorithmic integer ops of one step: per query sum_t W32 (w_t + 1),
+        per block n ceil(log2 n) sort compares."""
+        total = 0
+        for j, code in enumerate(self.codes):
+            sel = self.cid_np == j
+            if not sel.any():
+                continue
+            ends, ws = class_weight_prefix(code.n, CAP)
+            qj = qh[sel]
+            w32 = (code.r + 31) // 32
+            total += w32 * (sum_weights(qj, ends, ws) + int(qj.sum()))
+            total += int(sel.sum()) * code.n * math.ceil(math.log2(code.n))
+        return total
+
+
 def bench_ours(args, rank, world, local):
     import torch
     import torch.distributed as dist
@@ -360,28 +429,24 @@ def bench_ours(args, rank, world, local):
         dist.barrier()
     orbg.load_library()
 
-    code, llr_np = make_inputs(rank)
-    B = llr_np.shape[0]
-    c = orbg.Code(code.H, max_query_cap=CAP)
-    cs = orbg.CodeSet([c])
+    job = Job(orbg, dev, rank, args)
+    B = job.B
+    tuned = "default"
     if args.shape:
         f = [int(x) for x in args.shape.split(",")]
-        orbg.orbg_codeset_set_tuning(cs.handle, orbg.OrbgTuning(*f))
-    llr = torch.from_numpy(llr_np).to(dev)
-    cw = torch.empty((B, code.n), dtype=torch.uint8, device=dev)
-    q = torch.empty((B,), dtype=torch.int32, device=dev)
-    ab = torch.empty((B,), dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream(dev)
-
-    def step():
-        orbg.orbg_decode_batched(cs.handle, None, None, llr, B, CAP, cw, None, q, ab, stream)
+        orbg.orbg_codeset_set_tuning(job.cs.handle, orbg.OrbgTuning(*f))
+        tuned = "given (--shape)"
+    elif not args.no_autotune:
+        job.autotune()  # untimed: scheduling knobs only, results do not change
+        tuned = "autotuned on this workload before warm-up"
 
     for _ in range(max(3, args.warmup)):
-        step()
+        job.step()
     torch.cuda.synchronize(dev)
 
     sampler = ClockSampler(local)
     sampler.start()
+    stream = job.stream
     events = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     if world > 1:
         dist.barrier()
@@ -389,7 +454,7 @@ def bench_ours(args, rank, world, local):
     t_wall0 = time.time()
     events[0].record(stream)
     for i in range(args.steps):
-        step()
+        job.step()
         events[i + 1].record(stream)
     torch.cuda.synchronize(dev)
     t_wall1 = time.time()
@@ -403,16 +468,11 @@ def bench_ours(args, rank, world, local):
     value = blocks_total / (total_ms / 1000.0)
 
     # work done per step, from this rank's last step
-    qh = q.cpu().numpy().astype(np.int64)
-    abh = ab.cpu().numpy()
+    qh = job.q.cpu().numpy().astype(np.int64)
+    abh = job.ab.cpu().numpy()
     q_step = int(qh.sum())
     queries_total = sum_over_ranks(float(q_step * args.steps), world, dev)
-    ends, ws = class_weight_prefix(code.n, CAP)
-    sw = sum_weights(qh, ends, ws)
-    w32 = (code.r + 31) // 32
-    search_ops = w32 * (sw + q_step)            # w_t XORs + one zero test per word
-    sort_ops = B * code.n * math.ceil(math.log2(code.n))
-    alg_ops = search_ops + sort_ops
+    alg_ops = job.alg_ops(qh)
     kernel_ms = statistics.mean(per_step)
     achieved = alg_ops / (kernel_ms / 1000.0) / 1e12   # Tops/s
 
@@ -429,7 +489,7 @@ def bench_ours(args, rank, world, local):
     # end to end: host (pinned) buffers through the same C call
     e2e = None
     if not args.no_e2e:
-        e2e = bench_e2e(orbg, cs, code, llr_np, B, args, world, dev)
+        e2e = bench_e2e(orbg, job, args, world, dev)
 
     line = {
         "metric": METRIC, "value": value, "unit": "blocks/s", "n_gpus": world,
@@ -438,33 +498,35 @@ def bench_ours(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32-llr/u32-syndrome",
         "data": "synthetic BPSK/AWGN, seeded (numpy PCG64); each rank its own seeds",
         "config": {"workload": WORKLOAD, "blocks_per_step": B, "query_cap": CAP,
-                   "input_mb": round(llr_np.nbytes / 1e6, 1),
+                   "input_mb": round(job.llr_np.nbytes / 1e6, 1),
                    "form": "batched persistent launch (orbg_decode_batched)",
                    "l2": ("inputs %.0f MB %s 129 MB L2, no flush"
-                          % (llr_np.nbytes / 1e6, ">" if llr_np.nbytes > 129e6 else "<=")),
-                   "tuning": orbg.orbg_codeset_get_tuning(cs.handle).as_dict(),
+                          % (job.llr_np.nbytes / 1e6,
+                             ">" if job.llr_np.nbytes > 129e6 else "<=")),
+                   "tuning": orbg.orbg_codeset_get_tuning(job.cs.handle).as_dict(),
+                   "tuning_source": tuned,
                    "parallelism": "replicas x%d (blocks sharded by rank, no collective)" % world},
         "queries_per_s": queries_total / (total_ms / 1000.0),
         "latency_ms": {"step_p50": statistics.median(per_step),
                        "step_p99": float(np.percentile(per_step, 99)),
-                       "what": "one 400,000-block batch, launch to completion"},
+                       "what": "one %d-block batch, launch to completion" % B},
         "abandon_rate": float(abh.mean()),
         "mean_queries": float(qh.mean()),
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "Tops/s", "frac": (achieved / peak) if peak else None,
                      "traffic": None,
-                     "what": ("orbg_batched_kernel + orbg_heavy_kernel (one step); algorithmic 32-bit integer ops per "
-                              "launch = sum_t W32 (w_t + 1) + B n ceil(log2 n) = %d; "
-                              "peak = measured LOP3 lanes/clk/SM (%s) x 152 SMs x "
-                              "2070 MHz" % (alg_ops, lanes))},
+                     "what": ("orbg_batched_kernel + orbg_heavy_kernel (one step); algorithmic "
+                              "32-bit integer ops per launch = sum_t W32 (w_t + 1) + "
+                              "B n ceil(log2 n) = %d; peak = measured LOP3 lanes/clk/SM (%s) "
+                              "x 152 SMs x 2070 MHz" % (alg_ops, lanes))},
         "clocks": clocks,
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
     }
     if e2e:
         line["e2e"] = e2e
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(code, llr_np)
+        line["cpu_baseline"] = cpu_baseline(job)
     if world > 1:
         dist.destroy_process_group()
     return line if rank == 0 else None
@@ -478,18 +540,27 @@ def measured_int_lanes(orbg):
         return None
 
 
-def bench_e2e(orbg, cs, code, llr_np, B, args, world, dev):
+def bench_e2e(orbg, job, args, world, dev):
+    """The same call with the inputs and outputs in pinned host memory: the
+    library stages them (H2D, both kernels, D2H, stream sync), all timed."""
     import torch
-    pin_llr = torch.empty(llr_np.shape, dtype=torch.float32, pin_memory=True)
-    pin_llr.numpy()[...] = llr_np
-    h_cw = torch.empty((B, code.n), dtype=torch.uint8, pin_memory=True)
+    B = job.B
+    pin_llr = torch.empty(job.llr_np.shape, dtype=torch.float32, pin_memory=True)
+    pin_llr.numpy()[...] = job.llr_np
+    n_total = int(job.n_of_block.sum())
+    h_cw = torch.empty((n_total,), dtype=torch.uint8, pin_memory=True)
     h_q = torch.empty((B,), dtype=torch.int32, pin_memory=True)
     h_ab = torch.empty((B,), dtype=torch.uint8, pin_memory=True)
-    stream = torch.cuda.current_stream(dev)
+    cid = off = None
+    in_meta = 0
+    if job.off_np is not None:
+        cid = torch.from_numpy(job.cid_np).pin_memory()
+        off = torch.from_numpy(job.off_np).pin_memory()
+        in_meta = B * (4 + 8 + 8)
 
     def step():
-        orbg.orbg_decode_batched(cs.handle, None, None, pin_llr, B, CAP, h_cw, None, h_q,
-                                 h_ab, stream)
+        orbg.orbg_decode_batched(job.cs.handle, cid, off, pin_llr, B, CAP, h_cw, off, h_q,
+                                 h_ab, job.stream)
 
     for _ in range(2):
         step()
@@ -502,24 +573,41 @@ def bench_e2e(orbg, cs, code, llr_np, B, args, world, dev):
     dt = max_over_ranks(dt, world, dev)
     blocks = sum_over_ranks(float(B * steps), world, dev)
     return {"value": blocks / dt, "unit": "blocks/s",
-            "h2d_bytes_per_step": int(B * code.n * 4),
-            "d2h_bytes_per_step": int(B * code.n + B * 4 + B),
+            "h2d_bytes_per_step": int(job.llr_np.nbytes + in_meta),
+            "d2h_bytes_per_step": int(n_total + B * 4 + B),
             "steps": steps,
-            "what": "orbg_decode_batched on pinned host buffers: H2D, kernel, D2H, sync"}
+            "what": "orbg_decode_batched on pinned host buffers: H2D, kernels, D2H, sync"}
 
 
-def cpu_baseline(code, llr_np):
-    """The oracle as it stands, one process, on a bounded sample (~10 s)."""
+def cpu_baseline(job):
+    """The oracle as it stands, one process, on a bounded sample: the whole
+    workload for the 400,000-block configurations (~4 s), a 40,000-block
+    stratified sample for the mixed one."""
     import oracle
     oracle.build_oracle()
-    per_point = B_PER_POINT
-    sample = cpu_sample(llr_np, per_point, 0)
-    dt, qsum, nb = run_oracle(code.H, sample, CAP, 1)
-    return {"value": nb / dt, "unit": "blocks/s", "cores": 1, "kind": "oracle",
-            "queries_per_s": qsum / dt,
-            "sample": "%d blocks of each of the 4 Eb/N0 points (%d blocks, the whole "
-                      "workload), one single-threaded process on %s"
-                      % (per_point, nb, cpu_model())}
+    t_total = 0.0
+    nb = 0
+    qsum = 0
+    if WORKLOAD_NAME == "mixed":
+        pick = np.arange(0, job.B, max(1, job.B // 40000))
+        groups = {}
+        for b in pick:
+            groups.setdefault(int(job.cid_np[b]), []).append(b)
+        for j, blocks in groups.items():
+            n = job.codes[j].n
+            llr = np.stack([job.llr_np[job.off_np[b]:job.off_np[b] + n] for b in blocks])
+            dt, qs, k = run_oracle(job.codes[j].H, llr, CAP, 1)
+            t_total += dt
+            qsum += qs
+            nb += k
+        what = "%d blocks, every %d-th of the mixed batch" % (nb, max(1, job.B // 40000))
+    else:
+        dt, qsum, nb = run_oracle(job.codes[0].H, job.llr_np, CAP, 1)
+        t_total = dt
+        what = "the whole %d-block workload" % nb
+    return {"value": nb / t_total, "unit": "blocks/s", "cores": 1, "kind": "oracle",
+            "queries_per_s": qsum / t_total,
+            "sample": "%s, one single-threaded process on %s" % (what, cpu_model())}
 
 
 def main(argv=None):

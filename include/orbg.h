@@ -216,6 +216,95 @@ ORBG_API int orbg_codeset_set_tuning(orbg_codeset *set, const orbg_tuning *t);
 ORBG_API int orbg_codeset_get_tuning(const orbg_codeset *set, orbg_tuning *t);
 
 /*
+ * Serving: continuous batching of decode requests over a code set.
+ *
+ * orbg_server_create starts a dispatcher thread on the current device with
+ * a device memory pool and a pinned host pool of mem_budget_bytes each
+ * (0 = 1 GiB) and `streams` CUDA streams (0 = 4).  orbg_server_submit
+ * queues a request (its LLRs are copied, so the caller's buffer is free on
+ * return).  The dispatcher packs waiting requests, oldest first, into the
+ * next batch while the batch's footprint -- LLRs, outputs, per-block layout
+ * arrays and kernel scratch -- still fits the free part of both pools
+ * (admission by memory footprint), and runs each batch as one mixed-code
+ * batched decode on a free stream; batches on different streams overlap,
+ * and requests that arrive while batches run join the next batch.  The
+ * code tables stay on the device.  Results are the same, block for block,
+ * as orbg_decode_batched would give for the request alone.
+ *   query_cap        : per-block cap for every request (<= each code's reserve)
+ *   max_batch_blocks : largest batch in blocks (0 = 2^20)
+ *   submit           : code_index into the set; B >= 1 blocks of that
+ *                      code's n LLRs, row-major host memory; request_id is
+ *                      the caller's (must not be in use).  ELIMIT if the
+ *                      request alone could never fit the pools.
+ *   poll             : waits up to timeout_us for finished requests and
+ *                      writes up to max_ids of their ids; returns the
+ *                      count (or a negative status).  Each id is reported
+ *                      once.
+ *   fetch            : copies a finished request's codeword [B][n], queries
+ *                      [B], abandoned [B] (any pointer may be NULL) to host
+ *                      memory, with its latency from submit to completion
+ *                      in seconds, and forgets the request.
+ *   destroy          : waits for submitted work, then frees everything.
+ * The server's own extension, not the paper's (the paper decodes one block
+ * at a time, Algorithm 1).
+ */
+typedef struct orbg_server orbg_server;
+typedef struct orbg_server_stats {
+    uint64_t submitted, completed;
+    uint64_t blocks_submitted, blocks_done;
+    uint64_t batches, max_batch_blocks, max_inflight_batches;
+    uint64_t pending, inflight_batches;
+} orbg_server_stats;
+
+ORBG_API int orbg_server_create(const orbg_codeset *set, size_t mem_budget_bytes,
+                                uint32_t query_cap, int streams,
+                                int64_t max_batch_blocks, orbg_server **out);
+ORBG_API int orbg_server_submit(orbg_server *srv, uint64_t request_id,
+                                int code_index, const float *llr, int64_t B);
+ORBG_API int orbg_server_poll(orbg_server *srv, uint64_t *ids, int max_ids,
+                              int timeout_us);
+ORBG_API int orbg_server_fetch(orbg_server *srv, uint64_t request_id,
+                               uint8_t *codeword, uint32_t *queries,
+                               uint8_t *abandoned, double *latency_s);
+ORBG_API int orbg_server_stats_get(orbg_server *srv, orbg_server_stats *out);
+ORBG_API int orbg_server_destroy(orbg_server *srv);
+
+/*
+ * Trace replay on a server, for measuring it: request i (code[i], B[i]
+ * blocks at element llr_off[i] of llr_all) is submitted arrival_s[i]
+ * seconds after the call starts, from a second thread, while this thread
+ * polls and fetches; outputs go to cw_all at element llr_off[i] and to
+ * q_all / ab_all at block blk_off[i]; latency_s[i] is its latency and
+ * *wall_s the replay's duration.  Host memory throughout.
+ */
+ORBG_API int orbg_server_replay(orbg_server *srv, int64_t nreq,
+                                const double *arrival_s, const int32_t *code,
+                                const int64_t *B, const int64_t *llr_off,
+                                const int64_t *blk_off, const float *llr_all,
+                                uint8_t *cw_all, uint32_t *q_all,
+                                uint8_t *ab_all, double *latency_s,
+                                double *wall_s);
+
+/*
+ * Autotuner for the batched form: times orbg_decode_batched on the given
+ * sample (device buffers, same arguments as orbg_decode_batched) under
+ * candidate tunings -- coordinate descent over warp_budget, heavy_warps,
+ * blocks_per_grab, warps_per_cta and ctas_per_sm, each candidate the median
+ * of `reps` timed runs (CUDA events on cuda_stream, after one warm-up) --
+ * keeps the fastest on the set and writes it to *best (may be NULL).
+ * Synchronises the stream.  The outputs are overwritten by every trial and
+ * hold the sample's (tuning-independent) results at the end.  The
+ * library's own addition; the paper has no counterpart.
+ */
+ORBG_API int orbg_codeset_autotune(orbg_codeset *set, const int32_t *code_id,
+                                   const int64_t *llr_offset, const float *llr,
+                                   int64_t B, uint32_t query_cap,
+                                   uint8_t *codeword, const int64_t *cw_offset,
+                                   uint32_t *queries, uint8_t *abandoned,
+                                   int reps, void *cuda_stream,
+                                   orbg_tuning *best);
+
+/*
  * Roofline probe: issue rate of independent 32-bit 3-input logic ops
  * (lop3.b32, the instruction a syndrome XOR compiles to) per SM per clock,
  * in lanes (threads x instructions), measured with clock64 on every SM of
@@ -226,14 +315,17 @@ ORBG_API int orbg_probe_int_lanes(double *lanes_per_clk_per_sm);
 /*
  * The query order this library decodes in, for inspection and tests: the
  * first `count` noise patterns for length n (1..256), expanded from the
- * same tables the kernels read.  out: host memory, [count][n+1] int32 rows
+ * same tables the kernels read (table 0: the one-warp-per-block table;
+ * table 1: the CTA table of the batched form's second phase; both hold
+ * the same order).  out: host memory, [count][n+1] int32 rows
  * holding w, then the w flipped positions (1-based, in increasing
  * reliability order, ascending), then zeros.  Returns the number of rows
  * written (fewer than count once the 2^n patterns run out), or a negative
  * status.  Host only, no CUDA call.  Paper: Sec. III-B (Eq. lw, Eq.
  * fractionation, Eq. intpart), ties as read at the top of this header.
  */
-ORBG_API int64_t orbg_query_order(int n, uint32_t count, int32_t *out);
+ORBG_API int64_t orbg_query_order(int n, uint32_t count, int table,
+                                  int32_t *out);
 
 /* Static description of a status code (never NULL). */
 ORBG_API const char *orbg_status_string(int status);

@@ -15,7 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liborbg.so")
 SOURCES = ["orbg_plain.cu", "orbg_batched.cu", "orbg_heavy.cu", "orbg_noalloc.cu",
-           "orbg_probe.cu", "orbg_api.cpp",
+           "orbg_probe.cu", "orbg_api.cpp", "orbg_serve.cpp",
            "orbg_tables.cpp"]
 HEADERS = ["orbg_internal.h", "orbg_decode_block.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -67,7 +67,7 @@ def build(force=False, verbose=False, extra=()):
     if failed:
         raise RuntimeError("nvcc failed:\n" + "\n".join(failed))
     tmp = LIB + ".%d.tmp" % os.getpid()
-    link = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"]
+    link = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static", "-lpthread"]
     subprocess.check_call(link)
     os.replace(tmp, LIB)
     return LIB

@@ -23,11 +23,15 @@ struct orbg_code {
     uint32_t *d_hcol = nullptr;
     OrbgRun *d_runs = nullptr;
     uint32_t *d_floor = nullptr;
+    OrbgRun *d_runs_cta = nullptr;
+    uint32_t *d_floor_cta = nullptr;
+    uint32_t *d_trip = nullptr;
     OrbgDeviceCode dev;
 };
 
 struct orbg_codeset {
     int ncodes, n_max, w32_max;
+    uint32_t ntrip_max;
     orbg_tuning tuning;
     std::vector<int> n_of;       /* n of each code, host copy */
     uint32_t cap_min;
@@ -124,6 +128,12 @@ void free_code_device(orbg_code *c)
     if (c->d_hcol) cudaFree(c->d_hcol);
     if (c->d_runs) cudaFree(c->d_runs);
     if (c->d_floor) cudaFree(c->d_floor);
+    if (c->d_runs_cta) cudaFree(c->d_runs_cta);
+    if (c->d_floor_cta) cudaFree(c->d_floor_cta);
+    if (c->d_trip) cudaFree(c->d_trip);
+    c->d_runs_cta = nullptr;
+    c->d_floor_cta = nullptr;
+    c->d_trip = nullptr;
     c->d_hcol = nullptr;
     c->d_runs = nullptr;
     c->d_floor = nullptr;
@@ -139,8 +149,17 @@ int orbg_codeset_view(const orbg_codeset *set, OrbgSetView *out)
     out->ncodes = set->ncodes;
     out->n_max = set->n_max;
     out->w32_max = set->w32_max;
+    out->ntrip_max = set->ntrip_max;
     out->cap_min = set->cap_min;
     out->tuning = set->tuning;
+    return 0;
+}
+
+int orbg_codeset_lengths(const orbg_codeset *set, std::vector<int> *n_of)
+{
+    if (!set || !n_of)
+        return -1;
+    *n_of = set->n_of;
     return 0;
 }
 
@@ -170,33 +189,30 @@ int orbg_last_cuda_error(void) { return g_last_cuda; }
 
 int orbg_version(void) { return 100; }
 
-int64_t orbg_query_order(int n, uint32_t count, int32_t *out)
+int64_t orbg_query_order(int n, uint32_t count, int table, int32_t *out)
 {
-    if (n < 1 || n > ORBG_MAX_N || (count > 0 && !out))
+    if (n < 1 || n > ORBG_MAX_N || (count > 0 && !out) || table < 0 || table > 1)
         return ORBG_EINVAL;
     if (count == 0)
         return 0;
     OrbgTables tb;
     if (orbg_build_tables(n, count, &tb) != 0)
         return ORBG_ELIMIT;
+    const std::vector<OrbgRun> &runs = table == 0 ? tb.runs : tb.runs_cta;
     const size_t stride = (size_t)n + 1;
     uint64_t total = std::min<uint64_t>(tb.patterns, count);
     std::memset(out, 0, sizeof(int32_t) * stride * (size_t)total);
-    for (const OrbgRun &r : tb.runs) {
-        for (int j = 0; j < r.len; j++) {
+    std::vector<int> v(64);
+    for (const OrbgRun &r : runs) {
+        for (int j = 0; j < r.count; j++) {
             uint64_t t = (uint64_t)r.tstart + (uint64_t)j;
             if (t > total)
                 break;
             int32_t *row = out + (t - 1) * stride;
-            int w = 0;
-            for (int i = 0; i < r.npre; i++)
-                row[1 + w++] = (int32_t)r.pre[i] + 1;
-            int a = (int)r.a0 + j;
-            if (a < n) {
-                row[1 + w++] = a + 1;
-                row[1 + w++] = (int)r.pair_sum - a + 1;
-            }
+            const int w = orbg_run_pattern(r, j, tb.trip.data(), v.data());
             row[0] = w;
+            for (int i = 0; i < w; i++)
+                row[1 + i] = v[i];
         }
     }
     return (int64_t)total;
@@ -308,25 +324,42 @@ int orbg_load_code(const uint8_t *mat, int kind, int n, int k, uint32_t max_quer
         delete c;
         return cuda_fail(e);
     }
-    size_t hb = hcol.size() * sizeof(uint32_t);
-    size_t rb = tb.runs.size() * sizeof(OrbgRun);
-    size_t fb = tb.group_floor.size() * sizeof(uint32_t);
-    if ((e = cudaMalloc(&c->d_hcol, hb)) != cudaSuccess ||
-        (e = cudaMalloc(&c->d_runs, rb)) != cudaSuccess ||
-        (e = cudaMalloc(&c->d_floor, fb)) != cudaSuccess ||
-        (e = cudaMemcpy(c->d_hcol, hcol.data(), hb, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(c->d_runs, tb.runs.data(), rb, cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = cudaMemcpy(c->d_floor, tb.group_floor.data(), fb, cudaMemcpyHostToDevice)) !=
-            cudaSuccess) {
-        free_code_device(c);
-        delete c;
-        return cuda_fail(e);
+    /* device copies: hcol, both run tables with their floors, the triples */
+    struct Up {
+        void **dst;
+        const void *src;
+        size_t bytes;
+    };
+    Up ups[] = {
+        {(void **)&c->d_hcol, hcol.data(), hcol.size() * sizeof(uint32_t)},
+        {(void **)&c->d_runs, tb.runs.data(), tb.runs.size() * sizeof(OrbgRun)},
+        {(void **)&c->d_floor, tb.group_floor.data(), tb.group_floor.size() * sizeof(uint32_t)},
+        {(void **)&c->d_runs_cta, tb.runs_cta.data(), tb.runs_cta.size() * sizeof(OrbgRun)},
+        {(void **)&c->d_floor_cta, tb.group_floor_cta.data(),
+         tb.group_floor_cta.size() * sizeof(uint32_t)},
+        {(void **)&c->d_trip, tb.trip.data(), std::max<size_t>(4, tb.trip.size() * 4)},
+    };
+    for (const Up &u : ups) {
+        const size_t bytes = std::max<size_t>(u.bytes, 4);
+        if ((e = cudaMalloc(u.dst, bytes)) != cudaSuccess ||
+            (u.bytes && (e = cudaMemcpy(*u.dst, u.src, u.bytes, cudaMemcpyHostToDevice)) !=
+                            cudaSuccess)) {
+            free_code_device(c);
+            delete c;
+            return cuda_fail(e);
+        }
     }
     c->dev.hcol = c->d_hcol;
-    c->dev.runs = c->d_runs;
-    c->dev.group_floor = c->d_floor;
-    c->dev.nruns = (uint32_t)tb.runs.size();
-    c->dev.ngroups = (uint32_t)tb.group_floor.size();
+    c->dev.warp.runs = c->d_runs;
+    c->dev.warp.group_floor = c->d_floor;
+    c->dev.warp.nruns = (uint32_t)tb.runs.size();
+    c->dev.warp.ngroups = (uint32_t)tb.group_floor.size();
+    c->dev.cta.runs = c->d_runs_cta;
+    c->dev.cta.group_floor = c->d_floor_cta;
+    c->dev.cta.nruns = (uint32_t)tb.runs_cta.size();
+    c->dev.cta.ngroups = (uint32_t)tb.group_floor_cta.size();
+    c->dev.trip = c->d_trip;
+    c->dev.ntrip = (uint32_t)tb.trip.size();
     c->dev.max_cap = cap;
     c->dev.n = n;
     c->dev.r = r;
@@ -415,6 +448,7 @@ int orbg_codeset_create(const orbg_code *const *codes, int ncodes, orbg_codeset 
     s->n_max = 0;
     s->w32_max = 1;
     s->cap_min = 0xFFFFFFFFu;
+    s->ntrip_max = 0;
     s->tuning = kDefaultTuning;
     for (int i = 0; i < ncodes; i++) {
         if (!codes[i]) {
@@ -426,6 +460,7 @@ int orbg_codeset_create(const orbg_code *const *codes, int ncodes, orbg_codeset 
         s->n_max = std::max(s->n_max, codes[i]->n);
         s->w32_max = std::max(s->w32_max, codes[i]->w32);
         s->cap_min = std::min(s->cap_min, codes[i]->max_cap);
+        s->ntrip_max = std::max(s->ntrip_max, codes[i]->dev.ntrip);
     }
     cudaError_t e;
     if ((e = cudaGetDevice(&s->device)) != cudaSuccess ||
@@ -523,7 +558,7 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
     int le = orbg_launch_batched(set->d_codes, set->ncodes, set->n_max, set->w32_max, d_cid,
                                  d_lo, d_llr, B, query_cap, budget, d_cw, d_co, d_q, d_ab,
                                  scratch, t.warps_per_cta, t.ctas_per_sm, t.blocks_per_grab,
-                                 t.heavy_warps, st);
+                                 t.heavy_warps, set->ntrip_max, st);
     cudaFreeAsync(scratch, st);
     if (le != 0) {
         sg.finish(false);
@@ -539,6 +574,89 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
             if (abandoned[b] == ORBG_BLOCK_NAN)
                 return ORBG_ENAN;
     return ORBG_OK;
+}
+
+int orbg_codeset_autotune(orbg_codeset *set, const int32_t *code_id, const int64_t *llr_offset,
+                          const float *llr, int64_t B, uint32_t query_cap, uint8_t *codeword,
+                          const int64_t *cw_offset, uint32_t *queries, uint8_t *abandoned,
+                          int reps, void *cuda_stream, orbg_tuning *best)
+{
+    if (!set || B < 1 || reps < 0 || reps > 64)
+        return ORBG_EINVAL;
+    if (!is_device_ptr(llr) || !is_device_ptr(codeword) || !is_device_ptr(queries) ||
+        !is_device_ptr(abandoned))
+        return ORBG_EINVAL;
+    const int r = reps ? reps : 3;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce;
+    if ((ce = cudaEventCreate(&e0)) != cudaSuccess || (ce = cudaEventCreate(&e1)) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return cuda_fail(ce);
+    }
+    /* median time of r runs of one tuning, ms; negative status on error */
+    auto trial = [&](const orbg_tuning &t, float *ms) -> int {
+        int rc = orbg_codeset_set_tuning(set, &t);
+        if (rc) return rc;
+        rc = orbg_decode_batched(set, code_id, llr_offset, llr, B, query_cap, codeword,
+                                 cw_offset, queries, abandoned, cuda_stream); /* warm-up */
+        if (rc) return rc;
+        std::vector<float> v;
+        for (int i = 0; i < r; i++) {
+            cudaEventRecord(e0, st);
+            rc = orbg_decode_batched(set, code_id, llr_offset, llr, B, query_cap, codeword,
+                                     cw_offset, queries, abandoned, cuda_stream);
+            if (rc) return rc;
+            cudaEventRecord(e1, st);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) return cuda_fail(e);
+            float x = 0;
+            cudaEventElapsedTime(&x, e0, e1);
+            v.push_back(x);
+        }
+        std::sort(v.begin(), v.end());
+        *ms = v[v.size() / 2];
+        return ORBG_OK;
+    };
+    orbg_tuning cur = set->tuning;
+    float cur_ms = 0;
+    int rc = trial(cur, &cur_ms);
+    const uint32_t budgets[] = {256u, 1024u, 4096u, 16384u, 65536u};
+    const int heavy[] = {4, 8, 16};
+    const int grabs[] = {1, 4, 8, 32};
+    const int wpcs[] = {4, 8};
+    const int cps[] = {0, 2, 3};
+    for (int knob = 0; knob < 5 && rc == ORBG_OK; knob++) {
+        const int count = knob == 0 ? 5 : knob == 1 ? 3 : knob == 2 ? 4 : knob == 3 ? 2 : 3;
+        for (int i = 0; i < count && rc == ORBG_OK; i++) {
+            orbg_tuning t = cur;
+            switch (knob) {
+            case 0: t.warp_budget = budgets[i]; break;
+            case 1: t.heavy_warps = heavy[i]; break;
+            case 2: t.blocks_per_grab = grabs[i]; break;
+            case 3: t.warps_per_cta = wpcs[i]; break;
+            default: t.ctas_per_sm = cps[i]; break;
+            }
+            if (std::memcmp(&t, &cur, sizeof(t)) == 0)
+                continue;
+            float ms = 0;
+            rc = trial(t, &ms);
+            if (rc == ORBG_OK && ms < cur_ms) {
+                cur = t;
+                cur_ms = ms;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != ORBG_OK)
+        return rc;
+    set->tuning = cur;
+    if (best)
+        *best = cur;
+    /* leave the outputs holding the sample's results under the chosen tuning */
+    return orbg_decode_batched(set, code_id, llr_offset, llr, B, query_cap, codeword, cw_offset,
+                               queries, abandoned, cuda_stream);
 }
 
 }  // extern "C"

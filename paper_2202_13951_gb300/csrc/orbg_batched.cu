@@ -97,7 +97,7 @@ cudaError_t launch_batched_t(const OrbgDeviceCode *d_codes, int ncodes, int n_ma
                              int64_t B, uint32_t cap, uint32_t budget, uint8_t *cw,
                              const int64_t *cw_off, uint32_t *q, uint8_t *ab,
                              unsigned long long *scratch, int warps_per_cta, int ctas_per_sm,
-                             int grab, int heavy_warps, cudaStream_t st)
+                             int grab, int heavy_warps, uint32_t ntrip_max, cudaStream_t st)
 {
     const int wpc = warps_per_cta > 0 ? (warps_per_cta > 8 ? 8 : warps_per_cta) : 8;
     const int g = grab < 1 ? 1 : grab;
@@ -126,7 +126,7 @@ cudaError_t launch_batched_t(const OrbgDeviceCode *d_codes, int ncodes, int n_ma
     /* phase 2 */
     return (cudaError_t)orbg_launch_heavy(d_codes, ncodes, n_max, w32_max, code_id, llr_off, llr,
                                           cap, cw, cw_off, q, ab, counters, heavy, heavy_warps,
-                                          st);
+                                          ntrip_max, st);
 }
 
 }  // namespace
@@ -141,13 +141,14 @@ int orbg_launch_batched(const OrbgDeviceCode *d_codes, int ncodes, int n_max, in
                         int64_t B, uint32_t cap, uint32_t budget, uint8_t *cw,
                         const int64_t *cw_off, uint32_t *q, uint8_t *ab,
                         unsigned long long *scratch, int warps_per_cta, int ctas_per_sm, int grab,
-                        int heavy_warps, void *stream)
+                        int heavy_warps, uint32_t ntrip_max, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
 #define ORBG_B(KM, WM)                                                                       \
     return (int)launch_batched_t<KM, WM>(d_codes, ncodes, n_max, w32_max, code_id, llr_off, \
                                          llr, B, cap, budget, cw, cw_off, q, ab, scratch,     \
-                                         warps_per_cta, ctas_per_sm, grab, heavy_warps, st);
+                                         warps_per_cta, ctas_per_sm, grab, heavy_warps,      \
+                                         ntrip_max, st);
 #define ORBG_BW(KM)                          \
     if (w32_max <= 1) { ORBG_B(KM, 1) }      \
     else if (w32_max <= 2) { ORBG_B(KM, 2) } \

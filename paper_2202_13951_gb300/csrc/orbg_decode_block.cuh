@@ -83,27 +83,48 @@ __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m)
     return ((uint64_t)hi << 32) | lo;
 }
 
-/* Shared memory of one block in flight: hperm[n+1] syndromes, then pi[256]
- * and the staged codeword cw[256]. */
+/* Shared memory of one block in flight: hperm[n+1] full syndromes, then
+ * (for W > 1) h0[n+1], the first 32-bit word of each, then pi[256] and the
+ * staged codeword cw[256].  Entry n is a zero column. */
 __host__ __device__ __forceinline__ uint32_t block_smem_bytes(int n, int w32)
 {
     uint32_t h = (uint32_t)(n + 1) * 4u * (uint32_t)w32;
     h = (h + 15u) & ~15u;
-    return h + 256u + 256u;
+    uint32_t h0 = w32 > 1 ? (((uint32_t)(n + 1) * 4u + 15u) & ~15u) : 0u;
+    return h + h0 + 256u + 256u;
+}
+
+/* Triple table of the CTA search: X3[i] = h0[c0] ^ h0[a0] ^ h0[b0] for
+ * triple i of the code's triple list. */
+__host__ __device__ __forceinline__ uint32_t triple_table_bytes(uint32_t ntrip)
+{
+    return (ntrip * 4u + 15u) & ~15u;
 }
 
 template <int W> struct BlockSmem {
     typedef typename Syn<W>::T T;
     T *h;
+    uint32_t *h0;
     uint8_t *pi;
     uint8_t *cw;
     __device__ __forceinline__ BlockSmem(unsigned char *base, int n)
     {
         h = reinterpret_cast<T *>(base);
-        pi = base + (((uint32_t)(n + 1) * sizeof(T) + 15u) & ~15u);
+        unsigned char *p = base + (((uint32_t)(n + 1) * sizeof(T) + 15u) & ~15u);
+        if (W > 1) {
+            h0 = reinterpret_cast<uint32_t *>(p);
+            p += ((uint32_t)(n + 1) * 4u + 15u) & ~15u;
+        } else {
+            h0 = reinterpret_cast<uint32_t *>(base);
+        }
+        pi = p;
         cw = pi + 256;
     }
 };
+
+__device__ __forceinline__ uint32_t first_word(uint32_t v) { return v; }
+__device__ __forceinline__ uint32_t first_word(uint2 v) { return v.x; }
+__device__ __forceinline__ uint32_t first_word(uint4 v) { return v.x; }
 
 /* ------------------------------------------------------- step 1: load */
 
@@ -294,34 +315,37 @@ __device__ __forceinline__ void build_perm(const OrbgDeviceCode &code, const uin
         if (e < n) {
             int idx = (int)(uint32_t)key[k];
             sm.pi[e] = (uint8_t)idx;
-            sm.h[e] = load_col<W>(code.hcol, idx);
+            const typename Syn<W>::T col = load_col<W>(code.hcol, idx);
+            sm.h[e] = col;
+            if (W > 1)
+                sm.h0[e] = first_word(col);
         }
     }
-    if (lane == 0)
+    if (lane == 0) {
         sm.h[n] = szero<typename Syn<W>::T>();
+        if (W > 1)
+            sm.h0[n] = 0u;
+    }
 }
 
 /* -------------------------------------------------- step 4: one run */
 
-/* Walk one run (two 16-byte halves v0, v1) unless it cannot beat `best`.
- * Returns the run's first hit index (or ORBG_NONE) and its offset j.
- * h[] has n+1 entries, the last one zero: prefix slots past npre read it,
- * so the first eight prefix loads are issued without waiting on npre. */
-template <int W>
-__device__ __forceinline__ uint32_t search_run(const uint4 &v0, const uint4 &v1,
-                                               const typename Syn<W>::T *__restrict__ h,
-                                               const typename Syn<W>::T s0, uint32_t best,
-                                               uint32_t cap, int n, uint32_t *mj)
+/* A run record (orbg_internal.h) as two 16-byte loads:
+ * v0.x tstart, v0.y count | npre << 16 | kind << 24, v0.z aux,
+ * v0.w prefix positions 0..3, v1 prefix positions 4..19. */
+__device__ __forceinline__ int run_count(const uint4 &v0) { return (int)(v0.y & 0xFFFFu); }
+__device__ __forceinline__ int run_npre(const uint4 &v0) { return (int)((v0.y >> 16) & 0xFFu); }
+__device__ __forceinline__ int run_kind(const uint4 &v0) { return (int)(v0.y >> 24); }
+
+/* Syndrome of a run's prefix: s0 (+) the prefix columns, over the W-word
+ * syndromes h or over their first words h0.  Slots past npre read entry n,
+ * the zero column, so the first eight loads are issued without waiting on
+ * npre. */
+template <typename T>
+__device__ __forceinline__ T prefix_syndrome(const uint4 &v0, const uint4 &v1,
+                                             const T *__restrict__ h, const T s0, int npre,
+                                             int n)
 {
-    typedef typename Syn<W>::T T;
-    const uint32_t tstart = v0.x;
-    if (!(tstart < best && tstart <= cap))
-        return ORBG_NONE;
-    const int pair_sum = (int)(v0.y & 0xFFFFu);
-    int a = (int)(v0.y >> 16);
-    const int len = (int)(v0.z & 0xFFu);
-    const int npre = (int)((v0.z >> 8) & 0xFFu);
-    /* prefix positions 0..7, independent loads (zero column past npre) */
     T p[8];
 #pragma unroll
     for (int i = 0; i < 8; i++) {
@@ -339,29 +363,172 @@ __device__ __forceinline__ uint32_t search_run(const uint4 &v0, const uint4 &v1,
             P = sx(P, h[(wd >> (8 * (i & 3))) & 0xFFu]);
         }
     }
-    /* the run, two queries per step; the second slot is clamped into the
-     * table and masked when it lies past the run */
-    int b = pair_sum - a;
-    for (int j = 0; j < len; j += 2, a += 2, b -= 2) {
-        const int a1 = min(a + 1, n), b1 = max(b - 1, 0);
-        const T s_0 = sx(sx(P, h[a]), h[b]);
-        const T s_1 = sx(sx(P, h[a1]), h[b1]);
-        const bool z0 = sz(s_0);
-        const bool z1 = sz(s_1) && (j + 1 < len);
-        if (z0 || z1) {
-            const uint32_t jj = (uint32_t)j + (z0 ? 0u : 1u);
-            *mj = jj;
-            return tstart + jj;
-        }
-    }
-    return ORBG_NONE;
+    return P;
 }
 
-__device__ __forceinline__ void load_run(const OrbgDeviceCode &code, uint32_t e, uint4 *v0,
-                                         uint4 *v1)
+/* Positions (0-based) a query flips besides the prefix: kind 1 hit value
+ * is a (1-based), the pair (a, S - a); kind 3 hit value is the triple
+ * index.  Writes up to three positions, returns how many. */
+__device__ __forceinline__ int query_tail(const uint4 &v0, uint32_t hit, const uint32_t *trip,
+                                          int *pos)
 {
-    if (e < code.nruns) {
-        const uint4 *runs4 = reinterpret_cast<const uint4 *>(code.runs);
+    const int kind = run_kind(v0);
+    if (kind == ORBG_RUN_PAIRS) {
+        const int S = (int)(v0.z & 0xFFu), a = (int)hit;
+        pos[0] = a - 1;
+        pos[1] = S - a - 1;
+        return 2;
+    }
+    if (kind == ORBG_RUN_TRIPLES) {
+        const uint32_t t = __ldg(trip + hit);
+        pos[0] = (int)(t & 0xFFu);
+        pos[1] = (int)((t >> 8) & 0xFFu);
+        pos[2] = (int)((t >> 16) & 0xFFu);
+        return 3;
+    }
+    return 0;
+}
+
+/* Full-width check of a query whose first word matched (rare: kept out of
+ * line so it costs the scan loops no registers). */
+template <int W>
+__device__ __noinline__ bool verify_query(const uint4 &v0, const uint4 &v1,
+                                          const typename Syn<W>::T *__restrict__ h,
+                                          const typename Syn<W>::T s0, int n, uint32_t hit,
+                                          const uint32_t *trip)
+{
+    typedef typename Syn<W>::T T;
+    T P = prefix_syndrome<T>(v0, v1, h, s0, run_npre(v0), n);
+    int pos[3];
+    const int k = query_tail(v0, hit, trip, pos);
+    for (int i = 0; i < k; i++)
+        P = sx(P, h[pos[i]]);
+    return sz(P);
+}
+
+/* Pair run (kind 1): queries (a, S - a) for a = a_lo, a_lo + 1, ...; two
+ * queries per step, first words from h0; a first-word match is checked on
+ * all W words outside the scan loop (a false match, probability 2^-32 per
+ * query, resumes it).  Returns the offset of the first hit or -1, and the
+ * hit's a in *hit. */
+template <int W>
+__device__ __forceinline__ int walk_pairs(const uint4 &v0, const uint4 &v1,
+                                          const typename Syn<W>::T *__restrict__ h,
+                                          const uint32_t *__restrict__ h0,
+                                          const typename Syn<W>::T s0, uint32_t P0, int n,
+                                          uint32_t *hit)
+{
+    const int len = run_count(v0);
+    const int S = (int)(v0.z & 0xFFu);
+    const int a_first = (int)((v0.z >> 8) & 0xFFu);
+    int j = 0;
+    for (;;) {
+        int cand = -1;
+        for (; j < len; j += 2) {
+            const int a = a_first + j;
+            const int b = S - a;
+            /* the second slot is clamped into the table and masked past the run */
+            const int a1 = min(a + 1, n + 1), b1 = max(b - 1, 1);
+            const bool m0 = (h0[a - 1] ^ h0[b - 1]) == P0;
+            const bool m1 = ((h0[a1 - 1] ^ h0[b1 - 1]) == P0) && (j + 1 < len);
+            if (m0 || m1) {
+                cand = j + (m0 ? 0 : 1);
+                break;
+            }
+        }
+        if (cand < 0)
+            return -1;
+        if (W == 1 || verify_query<W>(v0, v1, h, s0, n, (uint32_t)(a_first + cand), nullptr)) {
+            *hit = (uint32_t)(a_first + cand);
+            return cand;
+        }
+        j = cand + 1;
+    }
+}
+
+/* Walk one run of the warp table unless it cannot beat `best`.  Returns the
+ * run's first hit index (or ORBG_NONE) and the hit value for the flips. */
+template <int W>
+__device__ __forceinline__ uint32_t search_run_warp(const uint4 &v0, const uint4 &v1,
+                                                    const typename Syn<W>::T *__restrict__ h,
+                                                    const uint32_t *__restrict__ h0,
+                                                    const typename Syn<W>::T s0, uint32_t best,
+                                                    uint32_t cap, int n, uint32_t *hit)
+{
+    const uint32_t tstart = v0.x;
+    if (!(tstart < best && tstart <= cap))
+        return ORBG_NONE;
+    const uint32_t P0 = prefix_syndrome<uint32_t>(v0, v1, h0, first_word(s0), run_npre(v0), n);
+    if (run_kind(v0) == ORBG_RUN_SINGLE) {
+        if (P0 == 0u && (W == 1 || verify_query<W>(v0, v1, h, s0, n, 0u, nullptr))) {
+            *hit = 0u;
+            return tstart;
+        }
+        return ORBG_NONE;
+    }
+    const int j = walk_pairs<W>(v0, v1, h, h0, s0, P0, n, hit);
+    return j < 0 ? ORBG_NONE : tstart + (uint32_t)j;
+}
+
+/* Walk one run of the CTA table: kind 3 tests the X3 range [aux, aux +
+ * count) against the prefix syndrome, four queries per step. */
+template <int W>
+__device__ __forceinline__ uint32_t search_run_cta(const uint4 &v0, const uint4 &v1,
+                                                   const typename Syn<W>::T *__restrict__ h,
+                                                   const uint32_t *__restrict__ h0,
+                                                   const uint32_t *__restrict__ X3,
+                                                   const uint32_t *__restrict__ trip,
+                                                   const typename Syn<W>::T s0, uint32_t best,
+                                                   uint32_t cap, int n, uint32_t *hit)
+{
+    const uint32_t tstart = v0.x;
+    if (!(tstart < best && tstart <= cap))
+        return ORBG_NONE;
+    const uint32_t P0 = prefix_syndrome<uint32_t>(v0, v1, h0, first_word(s0), run_npre(v0), n);
+    const int kind = run_kind(v0);
+    if (kind == ORBG_RUN_TRIPLES) {
+        const int len = run_count(v0);
+        const uint32_t *x = X3 + v0.z;
+        int j = 0;
+        for (;;) {
+            int cand = -1;
+            for (; j < len; j += 4) {
+                /* slots past the run are masked; their loads stay inside it */
+                const int last = len - 1;
+                const bool m0 = x[j] == P0;
+                const bool m1 = (x[min(j + 1, last)] == P0) && (j + 1 < len);
+                const bool m2 = (x[min(j + 2, last)] == P0) && (j + 2 < len);
+                const bool m3 = (x[min(j + 3, last)] == P0) && (j + 3 < len);
+                if (m0 || m1 || m2 || m3) {
+                    cand = j + (m0 ? 0 : m1 ? 1 : m2 ? 2 : 3);
+                    break;
+                }
+            }
+            if (cand < 0)
+                return ORBG_NONE;
+            const uint32_t t = v0.z + (uint32_t)cand;
+            if (W == 1 || verify_query<W>(v0, v1, h, s0, n, t, trip)) {
+                *hit = t;
+                return tstart + (uint32_t)cand;
+            }
+            j = cand + 1;
+        }
+    }
+    if (kind == ORBG_RUN_SINGLE) {
+        if (P0 == 0u && (W == 1 || verify_query<W>(v0, v1, h, s0, n, 0u, nullptr))) {
+            *hit = 0u;
+            return tstart;
+        }
+        return ORBG_NONE;
+    }
+    const int j = walk_pairs<W>(v0, v1, h, h0, s0, P0, n, hit);
+    return j < 0 ? ORBG_NONE : tstart + (uint32_t)j;
+}
+
+__device__ __forceinline__ void load_run(const OrbgTable &tb, uint32_t e, uint4 *v0, uint4 *v1)
+{
+    if (e < tb.nruns) {
+        const uint4 *runs4 = reinterpret_cast<const uint4 *>(tb.runs);
         *v0 = __ldg(runs4 + 2 * e);
         *v1 = __ldg(runs4 + 2 * e + 1);
     } else {
@@ -373,30 +540,32 @@ __device__ __forceinline__ void load_run(const OrbgDeviceCode &code, uint32_t e,
 /* ----------------------------------------------------- step 5: output */
 
 /* The owner of the winning run applies its flips to the staged codeword. */
-__device__ __forceinline__ void apply_flips(const OrbgDeviceCode &code, uint32_t run, uint32_t j,
-                                            const uint8_t *pi, uint8_t *cw)
+__device__ __forceinline__ void apply_flips(const OrbgTable &tb, uint32_t run, uint32_t hit,
+                                            const uint32_t *trip, const uint8_t *pi,
+                                            uint8_t *cw)
 {
-    const OrbgRun *rp = code.runs + run;
-    const int npre = rp->npre;
-    for (int i = 0; i < npre; i++)
-        cw[pi[rp->pre[i]]] ^= 1;
-    const int a = (int)rp->a0 + (int)j;
-    if (a < code.n) {
-        const int b = (int)rp->pair_sum - a;
-        cw[pi[a]] ^= 1;
-        cw[pi[b]] ^= 1;
+    const uint4 *runs4 = reinterpret_cast<const uint4 *>(tb.runs);
+    const uint4 v0 = __ldg(runs4 + 2 * run), v1 = __ldg(runs4 + 2 * run + 1);
+    const int npre = run_npre(v0);
+    for (int i = 0; i < npre; i++) {
+        const uint32_t wd = i < 4 ? v0.w : i < 8 ? v1.x : i < 12 ? v1.y : i < 16 ? v1.z : v1.w;
+        cw[pi[(wd >> (8 * (i & 3))) & 0xFFu]] ^= 1;
     }
+    int pos[3];
+    const int k = query_tail(v0, hit, trip, pos);
+    for (int i = 0; i < k; i++)
+        cw[pi[pos[i]]] ^= 1;
 }
 
 /* ------------------------------------------------ one warp, one block */
 
 /*
- * Decode one block with one warp.  Groups are walked from 0 while their
- * floor (the smallest first index of any later run) is below the best hit,
- * at most `cap`, and at most `budget`.  If the walk stops on the budget
- * with the result still open, the block is not written: its index is
- * appended to heavy[] (when heavy != NULL) for decode_block_cta.  With
- * budget >= cap every block finishes here.
+ * Decode one block with one warp over the warp table.  Groups are walked
+ * from 0 while their floor (the smallest first index of any later run) is
+ * below the best hit, at most `cap`, and at most `budget`.  If the walk
+ * stops on the budget with the result still open, the block is not
+ * written: its index is appended to heavy[] (when heavy != NULL) for
+ * decode_block_cta.  With budget >= cap every block finishes here.
  */
 template <int K, int W>
 __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__restrict__ llr,
@@ -408,11 +577,12 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
 {
     typedef typename Syn<W>::T T;
     const int n = code.n;
+    const OrbgTable &tb = code.warp;
     BlockSmem<W> sm(bsm, n);
     uint64_t key[K];
     bool nan;
     const T s0 = load_block<K, W>(code, llr, key, sm.cw, lane, &nan);
-    uint32_t best = ORBG_NONE, my_t = ORBG_NONE, my_run = 0, my_j = 0;
+    uint32_t best = ORBG_NONE, my_t = ORBG_NONE, my_run = 0, my_hit = 0;
     bool done = true;
     if (nan) {
         best = ORBG_NONE - 1; /* marker: NaN block */
@@ -424,24 +594,24 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
         __syncwarp();
         uint32_t stop = ORBG_NONE;
         uint4 n0, n1;
-        load_run(code, (uint32_t)lane, &n0, &n1);
-        for (uint32_t g = 0; g < code.ngroups; g++) {
-            const uint32_t floor = __ldg(code.group_floor + g);
+        load_run(tb, (uint32_t)lane, &n0, &n1);
+        for (uint32_t g = 0; g < tb.ngroups; g++) {
+            const uint32_t floor = __ldg(tb.group_floor + g);
             if (floor >= best || floor > cap || floor > budget) {
                 stop = floor;
                 break;
             }
             const uint4 v0 = n0, v1 = n1;
-            load_run(code, (g + 1) * ORBG_GROUP + (uint32_t)lane, &n0, &n1); /* prefetch */
-            uint32_t mj = 0;
-            const uint32_t mine = search_run<W>(v0, v1, sm.h, s0, best, cap, n, &mj);
+            load_run(tb, (g + 1) * ORBG_GROUP + (uint32_t)lane, &n0, &n1); /* prefetch */
+            uint32_t hv = 0;
+            const uint32_t mine = search_run_warp<W>(v0, v1, sm.h, sm.h0, s0, best, cap, n, &hv);
             const uint32_t gbest = __reduce_min_sync(FULL_MASK, mine);
             if (gbest < best) {
                 best = gbest;
                 if (mine == gbest) {
                     my_t = mine;
                     my_run = g * ORBG_GROUP + (uint32_t)lane;
-                    my_j = mj;
+                    my_hit = hv;
                 }
             }
         }
@@ -458,7 +628,7 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
     const bool is_nan = best == ORBG_NONE - 1;
     const bool hit = !is_nan && best <= cap;
     if (hit && my_t == best)
-        apply_flips(code, my_run, my_j, sm.pi, sm.cw);
+        apply_flips(tb, my_run, my_hit, code.trip, sm.pi, sm.cw);
     __syncwarp();
 #pragma unroll
     for (int k = 0; k < K; k++) {
@@ -476,22 +646,25 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
 /* ------------------------------------------------ one CTA, one block */
 
 /*
- * All warps of the CTA decode one block.  Warp 0 loads and sorts; then warp
- * w walks groups w, w + nw, w + 2 nw, ...  Each warp stops at its first
- * group whose floor is at least the shared best (or above the cap): floors
- * never decrease with the group index and the best never increases, so no
- * group that could hold the final best is skipped.  s_best must be set to
- * ORBG_NONE and s_s0 written by the caller's protocol below.
+ * All warps of the CTA decode one block over the CTA table.  Warp 0 loads
+ * and sorts; all threads then fill the triple table X3 from the permuted
+ * first-word columns; then warp w walks groups w, w + nw, w + 2 nw, ...
+ * Each warp stops at its first group whose floor is at least the shared
+ * best (or above the cap): floors never decrease with the group index and
+ * the best never increases, so no group that could hold the final best is
+ * skipped.
  */
 template <int K, int W>
 __device__ void decode_block_cta(const OrbgDeviceCode &code, const float *__restrict__ llr,
                                  uint8_t *__restrict__ cw_out, uint32_t *__restrict__ q_out,
                                  uint8_t *__restrict__ ab_out, uint32_t cap,
-                                 unsigned char *__restrict__ bsm, uint32_t *s_best,
-                                 typename Syn<W>::T *s_s0, int warp, int lane, int nwarps)
+                                 unsigned char *__restrict__ bsm, uint32_t *__restrict__ X3,
+                                 uint32_t *s_best, typename Syn<W>::T *s_s0, int warp, int lane,
+                                 int nwarps)
 {
     typedef typename Syn<W>::T T;
     const int n = code.n;
+    const OrbgTable &tb = code.cta;
     BlockSmem<W> sm(bsm, n);
     if (warp == 0) {
         uint64_t key[K];
@@ -511,28 +684,36 @@ __device__ void decode_block_cta(const OrbgDeviceCode &code, const float *__rest
         }
     }
     __syncthreads();
-    uint32_t my_t = ORBG_NONE, my_run = 0, my_j = 0;
     const uint32_t start = *s_best;
+    if (start == ORBG_NONE) {
+        for (uint32_t i = threadIdx.x; i < code.ntrip; i += blockDim.x) {
+            const uint32_t t = __ldg(code.trip + i);
+            X3[i] = sm.h0[t & 0xFFu] ^ sm.h0[(t >> 8) & 0xFFu] ^ sm.h0[(t >> 16) & 0xFFu];
+        }
+    }
+    __syncthreads();
+    uint32_t my_t = ORBG_NONE, my_run = 0, my_hit = 0;
     if (start == ORBG_NONE) {
         const T s0 = *s_s0;
         uint4 n0, n1;
         uint32_t g = (uint32_t)warp;
-        load_run(code, g * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
-        for (; g < code.ngroups; g += (uint32_t)nwarps) {
-            const uint32_t floor = __ldg(code.group_floor + g);
+        load_run(tb, g * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
+        for (; g < tb.ngroups; g += (uint32_t)nwarps) {
+            const uint32_t floor = __ldg(tb.group_floor + g);
             const uint32_t best = *((volatile uint32_t *)s_best);
             if (floor >= best || floor > cap)
                 break;
             const uint4 v0 = n0, v1 = n1;
-            load_run(code, (g + nwarps) * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
-            uint32_t mj = 0;
-            const uint32_t mine = search_run<W>(v0, v1, sm.h, s0, best, cap, n, &mj);
+            load_run(tb, (g + nwarps) * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
+            uint32_t hv = 0;
+            const uint32_t mine =
+                search_run_cta<W>(v0, v1, sm.h, sm.h0, X3, code.trip, s0, best, cap, n, &hv);
             const uint32_t gbest = __reduce_min_sync(FULL_MASK, mine);
             if (gbest != ORBG_NONE) {
                 if (mine == gbest) {
                     my_t = mine;
                     my_run = g * ORBG_GROUP + (uint32_t)lane;
-                    my_j = mj;
+                    my_hit = hv;
                     atomicMin(s_best, mine);
                 }
             }
@@ -543,7 +724,7 @@ __device__ void decode_block_cta(const OrbgDeviceCode &code, const float *__rest
     const bool is_nan = best == ORBG_NONE - 1;
     const bool hit = !is_nan && best <= cap;
     if (start == ORBG_NONE && hit && my_t == best)
-        apply_flips(code, my_run, my_j, sm.pi, sm.cw);
+        apply_flips(tb, my_run, my_hit, code.trip, sm.pi, sm.cw);
     __syncthreads();
     for (int i = warp * 32 + lane; i < n; i += nwarps * 32)
         cw_out[i] = sm.cw[i];

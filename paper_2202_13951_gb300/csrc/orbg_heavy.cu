@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(512, 2) orbg_heavy_kernel(
     const int64_t *__restrict__ llr_off, const float *__restrict__ llr, uint32_t cap,
     uint8_t *__restrict__ cw, const int64_t *__restrict__ cw_off, uint32_t *__restrict__ q,
     uint8_t *__restrict__ ab, unsigned long long *__restrict__ counters,
-    const unsigned long long *__restrict__ heavy)
+    const unsigned long long *__restrict__ heavy, uint32_t bstride)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ unsigned long long s_block;
@@ -44,7 +44,8 @@ __global__ void __launch_bounds__(512, 2) orbg_heavy_kernel(
         const int64_t lo = llr_off ? llr_off[b] : b * n0;
         const int64_t co = cw_off ? cw_off[b] : b * n0;
 #define ORBG_CALL_CTA(KK, WW)                                                               \
-    decode_block_cta<KK, WW>(code, llr + lo, cw + co, q + b, ab + b, cap, smem, &s_best,     \
+    decode_block_cta<KK, WW>(code, llr + lo, cw + co, q + b, ab + b, cap, smem,              \
+                             reinterpret_cast<uint32_t *>(smem + bstride), &s_best,          \
                              reinterpret_cast<typename Syn<WW>::T *>(&s_s0), warp, lane, nwarps)
         ORBG_DISPATCH(KMAX, WMAX, ORBG_CALL_CTA);
 #undef ORBG_CALL_CTA
@@ -57,17 +58,19 @@ cudaError_t launch_heavy_t(const OrbgDeviceCode *d_codes, int ncodes, int n_max,
                            const int32_t *code_id, const int64_t *llr_off, const float *llr,
                            uint32_t cap, uint8_t *cw, const int64_t *cw_off, uint32_t *q,
                            uint8_t *ab, unsigned long long *counters,
-                           const unsigned long long *heavy, int heavy_warps, cudaStream_t st)
+                           const unsigned long long *heavy, int heavy_warps, uint32_t ntrip_max,
+                           cudaStream_t st)
 {
     auto k2 = orbg_heavy_kernel<KMAX, WMAX>;
     const int hw = heavy_warps > 0 ? heavy_warps : 16;
     const uint32_t bstride = block_smem_bytes(n_max, w32_max);
+    const size_t smem = (size_t)bstride + triple_table_bytes(ntrip_max);
     int grid = 0;
-    int rc = orbg_grid_for((const void *)k2, hw * 32, bstride, 0, &grid);
+    int rc = orbg_grid_for((const void *)k2, hw * 32, smem, 0, &grid);
     if (rc != 0)
         return (cudaError_t)rc;
-    k2<<<grid, hw * 32, bstride, st>>>(d_codes, ncodes, code_id, llr_off, llr, cap, cw, cw_off, q,
-                                       ab, counters, heavy);
+    k2<<<grid, hw * 32, smem, st>>>(d_codes, ncodes, code_id, llr_off, llr, cap, cw, cw_off, q,
+                                    ab, counters, heavy, bstride);
     return cudaGetLastError();
 }
 
@@ -77,12 +80,13 @@ int orbg_launch_heavy(const OrbgDeviceCode *d_codes, int ncodes, int n_max, int 
                       const int32_t *code_id, const int64_t *llr_off, const float *llr,
                       uint32_t cap, uint8_t *cw, const int64_t *cw_off, uint32_t *q, uint8_t *ab,
                       unsigned long long *counters, const unsigned long long *heavy,
-                      int heavy_warps, void *stream)
+                      int heavy_warps, uint32_t ntrip_max, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
 #define ORBG_LH(KM, WM)                                                                         \
     return (int)launch_heavy_t<KM, WM>(d_codes, ncodes, n_max, w32_max, code_id, llr_off, llr, \
-                                       cap, cw, cw_off, q, ab, counters, heavy, heavy_warps, st);
+                                       cap, cw, cw_off, q, ab, counters, heavy, heavy_warps,   \
+                                       ntrip_max, st);
 #define ORBG_HW(KM)                          \
     if (w32_max <= 1) { ORBG_LH(KM, 1) }      \
     else if (w32_max <= 2) { ORBG_LH(KM, 2) } \

@@ -4,17 +4,27 @@
  *
  * The query order (Sec. III-B: increasing logistic weight W; this library's
  * tie reading: Hamming weight w ascending, then positions lexicographic) is
- * held as a table of "runs".  A pattern of weight w >= 2 is a prefix
- * v_1 < ... < v_{w-2} followed by a pair a < b with a + b = S fixed by W;
- * for one prefix, the lexicographic order walks a upward, so the prefix's
- * patterns form one run of consecutive query indices.  Patterns of weight
- * 0 and 1 are runs of length one whose pair is the all-zero column twice.
+ * held as tables of "runs" of consecutive query indices.  Two tables per
+ * code, each covering the whole order:
  *
+ * Warp table (one warp decodes a block):
+ *   kind 0  one pattern of weight 0 or 1 (the prefix is the pattern);
+ *   kind 1  a prefix v_1 < ... < v_{w-2} and every pair a < b <= n after it
+ *           with a + b = S, a ascending from a_lo.
+ * CTA table (a CTA decodes a block and first builds the block's triple
+ * table X3: the first syndrome word of every triple c < a < b <= n with
+ * c + a + b <= S3max, ordered by that sum, then c, then a):
+ *   kind 0  as above;
+ *   kind 1  as above, used for w = 2 and for triples beyond S3max;
+ *   kind 3  a prefix v_1 < ... < v_{w-3} and every triple after it with
+ *           c + a + b = S3: a contiguous range of X3, tested against one
+ *           prefix syndrome.  Cut into chunks of at most 8..255 queries
+ *           (longer deeper in the order).
  * Runs are stored class by class ((W, w) ascending); inside a class they are
- * sorted by run length so that the 32 lanes of a warp, which take 32
+ * sorted by length so that the 32 lanes of a warp, which take 32
  * consecutive runs, loop for about the same number of queries.  Every run
  * keeps its own first query index, so the decoder still reports the first
- * hit of the paper's order; group_floor[g] (the smallest first index over
+ * hit of the paper's order; a group floor (the smallest first index over
  * runs of groups >= g) tells a warp when no later group can hold an earlier
  * hit.
  */
@@ -23,27 +33,37 @@
 
 #include <stdint.h>
 
-#define ORBG_GROUP 32        /* runs per warp step: one per lane */
-#define ORBG_RUN_MAX_PRE 20  /* prefix positions stored per run */
+#define ORBG_GROUP 32          /* runs per warp step: one per lane */
+#define ORBG_RUN_MAX_PRE 20    /* prefix positions stored per run */
+#define ORBG_MAX_LOGISTIC 255  /* deepest logistic weight a table may reach */
+#define ORBG_X3_MAX 16384      /* triple-table entries (64 KiB of shared memory) */
+
+enum { ORBG_RUN_SINGLE = 0, ORBG_RUN_PAIRS = 1, ORBG_RUN_TRIPLES = 3 };
 
 /* One run: 32 bytes, read by a lane as two 16-byte loads. */
 struct OrbgRun {
     uint32_t tstart;    /* 1-based query index of the run's first pattern */
-    uint16_t pair_sum;  /* a0 + b0 for 0-based pair positions a0 < b0 */
-    uint16_t a0;        /* first a0; runs of one pattern: a0 = b0 = n */
-    uint8_t len;        /* patterns in the run, >= 1 */
+    uint16_t count;     /* patterns in the run, >= 1 */
     uint8_t npre;       /* prefix positions used */
-    uint8_t pad[2];
+    uint8_t kind;       /* ORBG_RUN_* */
+    uint32_t aux;       /* kind 1: S | a_lo << 8 (1-based); kind 3: first X3 index */
     uint8_t pre[ORBG_RUN_MAX_PRE]; /* 0-based prefix positions, ascending */
+};
+
+struct OrbgTable {
+    const OrbgRun *runs;         /* [nruns] */
+    const uint32_t *group_floor; /* [ngroups] */
+    uint32_t nruns;
+    uint32_t ngroups;
 };
 
 /* What a kernel needs of one code (passed by value or from a device array). */
 struct OrbgDeviceCode {
     const uint32_t *hcol;        /* [n][w32]: column j of H, row i at bit i%32 of word i/32 */
-    const OrbgRun *runs;         /* [nruns] */
-    const uint32_t *group_floor; /* [ngroups] */
-    uint32_t nruns;
-    uint32_t ngroups;
+    OrbgTable warp;              /* runs of kinds 0, 1 */
+    OrbgTable cta;               /* runs of kinds 0, 1, 3 */
+    const uint32_t *trip;        /* [ntrip]: c0 | a0 << 8 | b0 << 16 (0-based), X3 order */
+    uint32_t ntrip;
     uint32_t max_cap;
     int32_t n;
     int32_t r;
@@ -58,12 +78,16 @@ static_assert(sizeof(OrbgRun) == 32, "run record must be 32 bytes");
 #ifdef __cplusplus
 #include <vector>
 struct OrbgTables {
-    std::vector<OrbgRun> runs;
+    std::vector<OrbgRun> runs;           /* warp table */
     std::vector<uint32_t> group_floor;
+    std::vector<OrbgRun> runs_cta;       /* CTA table */
+    std::vector<uint32_t> group_floor_cta;
+    std::vector<uint32_t> trip;          /* X3 order */
     uint64_t patterns = 0;  /* query indices covered (last index) */
     int wmax_logistic = 0;  /* deepest logistic weight in the table */
 };
 int orbg_build_tables(int n, uint64_t cap, OrbgTables *out);
+int orbg_run_pattern(const OrbgRun &r, int j, const uint32_t *trip, int *v);
 
 /* GF(2) helpers on dense 0/1 byte matrices (row-major). */
 int orbg_gf2_rank(const uint8_t *M, int rows, int cols);
@@ -80,7 +104,8 @@ int orbg_launch_batched(const OrbgDeviceCode *d_codes, int ncodes, int n_max,
                         uint32_t cap, uint32_t budget, uint8_t *cw,
                         const int64_t *cw_off, uint32_t *q, uint8_t *ab,
                         unsigned long long *scratch, int warps_per_cta,
-                        int ctas_per_sm, int grab, int heavy_warps, void *stream);
+                        int ctas_per_sm, int grab, int heavy_warps,
+                        uint32_t ntrip_max, void *stream);
 /* device scratch the batched form needs for B blocks: counters (queue head,
  * open-block count, phase-2 cursor) and the list of open blocks */
 #define ORBG_BATCHED_COUNTERS 8
@@ -89,7 +114,7 @@ int orbg_launch_heavy(const OrbgDeviceCode *d_codes, int ncodes, int n_max, int 
                       const int32_t *code_id, const int64_t *llr_off, const float *llr,
                       uint32_t cap, uint8_t *cw, const int64_t *cw_off, uint32_t *q, uint8_t *ab,
                       unsigned long long *counters, const unsigned long long *heavy,
-                      int heavy_warps, void *stream);
+                      int heavy_warps, uint32_t ntrip_max, void *stream);
 int orbg_grid_for(const void *kern, int threads, size_t smem, int ctas_per_sm, int *grid_out);
 
 /* What a launch needs of a code set (orbg_api.cpp owns the struct). */
@@ -97,10 +122,12 @@ int orbg_grid_for(const void *kern, int threads, size_t smem, int ctas_per_sm, i
 struct OrbgSetView {
     const OrbgDeviceCode *d_codes;
     int ncodes, n_max, w32_max;
+    uint32_t ntrip_max;
     uint32_t cap_min;
     orbg_tuning tuning;
 };
 int orbg_codeset_view(const orbg_codeset *set, OrbgSetView *out);
+int orbg_codeset_lengths(const orbg_codeset *set, std::vector<int> *n_of);
 /* Records a cudaError_t for orbg_last_cuda_error; returns the orbg status. */
 int orbg_note_cuda_error(int cuda_error);
 int orbg_launch_int_probe(double *lanes_per_clk_per_sm);

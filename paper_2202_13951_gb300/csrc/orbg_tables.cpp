@@ -6,8 +6,9 @@
  * split by Hamming weight w (Eq. fractionation) ascending, and inside one
  * (W, w) the distinct-part partitions v_1 < ... < v_w <= n of W (Eq.
  * intpart) in lexicographic order, the order Algorithm 2 (Landslide)
- * generates.  This file enumerates that order directly as lexicographic
- * prefixes plus a final pair (see orbg_internal.h), not with Landslide.
+ * generates.  This file enumerates that order directly, as lexicographic
+ * prefixes followed by a run of pairs or of triples (see orbg_internal.h),
+ * not with Landslide.
  */
 #include <algorithm>
 #include <cstring>
@@ -17,52 +18,101 @@
 
 namespace {
 
+/* Pairs a < b <= n (1-based) with a + b = S and a >= lo: a in
+ * [max(lo, S - n), (S - 1) / 2]. */
+inline int pair_lo(int S, int lo, int n) { return std::max(lo, S - n); }
+inline int pair_hi(int S) { return (S - 1) / 2; }
+
+/* Triples c < a < b <= n with c + a + b = S3 and c >= lo: the c that admit a
+ * pair form [max(lo, S3 - (2n - 1)), (S3 - 3) / 3]. */
+inline int trip_c_lo(int S3, int lo, int n) { return std::max(lo, S3 - (2 * n - 1)); }
+inline int trip_c_hi(int S3) { return (S3 - 3) / 3; }
+
+/* Longest chunk a triple run starting at query t is cut into: short early
+ * in the order (a warp step over 32 chunks should not overshoot a hit by
+ * much) and long deep in it (the per-chunk setup is amortised). */
+int chunk_len(uint64_t t)
+{
+    const uint64_t c = t / 512;
+    return (int)(c < 8 ? 8 : c > 255 ? 255 : c);
+}
+
 struct Builder {
     int n;
-    uint64_t t;                    /* next query index */
+    bool cta;                      /* build the CTA table (triple runs) */
+    int s3max = 0;                 /* triple sums covered by X3 */
+    const std::vector<uint32_t> *x3off = nullptr; /* first X3 index of each sum */
+    uint64_t t = 1;                /* next query index */
     std::vector<OrbgRun> cls;      /* runs of the current (W, w) class */
     int pre[64];
+    bool overflow = false;
 
-    void emit_single(const int *p, int np) {
+    OrbgRun blank(int kind, int npre) {
         OrbgRun r;
         std::memset(&r, 0, sizeof(r));
         r.tstart = (uint32_t)t;
-        r.pair_sum = (uint16_t)(2 * n);   /* a0 = b0 = n: the zero column */
-        r.a0 = (uint16_t)n;
-        r.len = 1;
-        r.npre = (uint8_t)np;
-        for (int i = 0; i < np; i++)
-            r.pre[i] = (uint8_t)(p[i] - 1);
-        cls.push_back(r);
-        t += 1;
+        r.kind = (uint8_t)kind;
+        r.npre = (uint8_t)npre;
+        for (int i = 0; i < npre; i++)
+            r.pre[i] = (uint8_t)(pre[i] - 1);
+        return r;
     }
 
-    /* Prefixes of `need` more positions, each > lo-1, with `rem` left for
-     * them and the final pair; `depth` positions already in pre[]. */
-    void prefixes(int depth, int need, int lo, int rem) {
-        if (need == 0) {
-            /* pair a < b, a >= lo, b <= n, a + b = rem */
-            int S = rem;
-            int a_lo = std::max(lo, S - n);
-            int a_hi = (S - 1) / 2;
-            if (a_lo > a_hi)
-                return;
-            OrbgRun r;
-            std::memset(&r, 0, sizeof(r));
-            r.tstart = (uint32_t)t;
-            r.pair_sum = (uint16_t)(S - 2);
-            r.a0 = (uint16_t)(a_lo - 1);
-            r.len = (uint8_t)(a_hi - a_lo + 1);
-            r.npre = (uint8_t)depth;
-            for (int i = 0; i < depth; i++)
-                r.pre[i] = (uint8_t)(pre[i] - 1);
-            cls.push_back(r);
-            t += (uint64_t)(a_hi - a_lo + 1);
+    void emit(OrbgRun r, uint64_t count) {
+        if (count > 0xFFFF || count == 0) {
+            overflow |= count > 0xFFFF;
             return;
         }
-        /* after choosing v, need-1 more prefix positions and the pair, all
-         * distinct and above v: m = need + 1 positions */
-        const int m = need + 1;
+        r.count = (uint16_t)count;
+        cls.push_back(r);
+        t += count;
+    }
+
+    void single(int np) { emit(blank(ORBG_RUN_SINGLE, np), 1); }
+
+    /* pairs of sum S after a prefix of `depth` positions ending at q */
+    void pairs(int depth, int q, int S) {
+        const int lo = pair_lo(S, q + 1, n), hi = pair_hi(S);
+        if (lo > hi)
+            return;
+        OrbgRun r = blank(ORBG_RUN_PAIRS, depth);
+        r.aux = (uint32_t)S | ((uint32_t)lo << 8);
+        emit(r, (uint64_t)(hi - lo + 1));
+    }
+
+    /* triples of sum S3 after a prefix ending at q: one X3 range, chunked */
+    void triples(int depth, int q, int S3) {
+        const int c_lo = trip_c_lo(S3, q + 1, n), c_hi = trip_c_hi(S3);
+        if (c_lo > c_hi)
+            return;
+        /* X3 index of the first triple with c >= c_lo, and the range length */
+        uint32_t x = (*x3off)[S3];
+        for (int c = trip_c_lo(S3, 1, n); c < c_lo; c++)
+            x += (uint32_t)(pair_hi(S3 - c) - pair_lo(S3 - c, c + 1, n) + 1);
+        uint64_t total = 0;
+        for (int c = c_lo; c <= c_hi; c++)
+            total += (uint64_t)(pair_hi(S3 - c) - pair_lo(S3 - c, c + 1, n) + 1);
+        while (total > 0) {
+            const uint64_t len = std::min<uint64_t>(total, (uint64_t)chunk_len(t));
+            OrbgRun r = blank(ORBG_RUN_TRIPLES, depth);
+            r.aux = x;
+            emit(r, len);
+            x += (uint32_t)len;
+            total -= len;
+        }
+    }
+
+    /* Prefixes of `need` more positions, each >= lo, with `rem` left for
+     * them and the final `tail` (2 = pair, 3 = triple) positions. */
+    void prefixes(int depth, int need, int lo, int rem, int tail) {
+        if (need == 0) {
+            if (tail == 2)
+                pairs(depth, lo - 1, rem);
+            else
+                triples(depth, lo - 1, rem);
+            return;
+        }
+        const int m = need - 1 + tail; /* positions after v, all above it */
         for (int v = lo; v <= n; v++) {
             long min_rest = (long)m * v + (long)m * (m + 1) / 2;
             long max_rest = (long)m * n - (long)m * (m - 1) / 2;
@@ -71,20 +121,97 @@ struct Builder {
             if (v + max_rest < rem)
                 continue;
             pre[depth] = v;
-            prefixes(depth + 1, need - 1, v + 1, rem - v);
+            prefixes(depth + 1, need - 1, v + 1, rem - v, tail);
         }
     }
 
-    void flush(OrbgTables *out) {
+    void flush(std::vector<OrbgRun> *out) {
         /* longest runs first; equal lengths keep the query order */
         std::stable_sort(cls.begin(), cls.end(),
                          [](const OrbgRun &a, const OrbgRun &b) {
-                             return a.len > b.len;
+                             return a.count > b.count;
                          });
-        out->runs.insert(out->runs.end(), cls.begin(), cls.end());
+        out->insert(out->end(), cls.begin(), cls.end());
         cls.clear();
     }
+
+    /* The whole order up to the class holding query `cap`. */
+    int build(uint64_t cap, std::vector<OrbgRun> *out, uint64_t *patterns, int *wdeep) {
+        t = 1;
+        single(0); /* W = 0: the zero pattern */
+        flush(out);
+        const long Wlast = (long)n * (n + 1) / 2;
+        for (long W = 1; W <= Wlast && t <= cap; W++) {
+            if (W > ORBG_MAX_LOGISTIC)
+                return -2;
+            for (int w = 1; (long)w * (w + 1) / 2 <= W && w <= n; w++) {
+                if (w == 1) {
+                    if (W <= n) {
+                        pre[0] = (int)W;
+                        single(1);
+                    }
+                } else if (cta && w >= 3) {
+                    /* triple runs where the prefix leaves a sum inside X3,
+                     * pair runs (prefix extended by c) where it does not */
+                    if (w - 2 > ORBG_RUN_MAX_PRE)
+                        return -2;
+                    prefixes_split(0, w - 3, 1, (int)W);
+                } else {
+                    if (w - 2 > ORBG_RUN_MAX_PRE)
+                        return -2;
+                    prefixes(0, w - 2, 1, (int)W, 2);
+                }
+                flush(out);
+            }
+            *wdeep = (int)W;
+        }
+        *patterns = t - 1;
+        return overflow ? -2 : 0;
+    }
+
+    /* CTA table, w >= 3: (w-3)-prefixes in lexicographic order; each one's
+     * triples become an X3 range if their sum fits X3, else the prefix is
+     * extended by every valid c (in order) and the pairs after it form
+     * pair runs -- the same patterns in the same order. */
+    void prefixes_split(int depth, int need, int lo, int rem) {
+        if (need == 0) {
+            if (rem <= s3max) {
+                triples(depth, lo - 1, rem);
+            } else {
+                const int c_lo = trip_c_lo(rem, lo, n), c_hi = trip_c_hi(rem);
+                for (int c = c_lo; c <= c_hi; c++) {
+                    pre[depth] = c;
+                    pairs(depth + 1, c, rem - c);
+                }
+            }
+            return;
+        }
+        const int m = need - 1 + 3;
+        for (int v = lo; v <= n; v++) {
+            long min_rest = (long)m * v + (long)m * (m + 1) / 2;
+            long max_rest = (long)m * n - (long)m * (m - 1) / 2;
+            if (v + min_rest > rem)
+                break;
+            if (v + max_rest < rem)
+                continue;
+            pre[depth] = v;
+            prefixes_split(depth + 1, need - 1, v + 1, rem - v);
+        }
+    }
 };
+
+void floors(const std::vector<OrbgRun> &runs, std::vector<uint32_t> *out)
+{
+    const size_t nr = runs.size();
+    const size_t ng = (nr + ORBG_GROUP - 1) / ORBG_GROUP;
+    out->assign(ng, 0xFFFFFFFFu);
+    uint32_t floor = 0xFFFFFFFFu;
+    for (size_t g = ng; g-- > 0;) {
+        for (size_t i = g * ORBG_GROUP; i < std::min(nr, (g + 1) * ORBG_GROUP); i++)
+            floor = std::min(floor, runs[i].tstart);
+        (*out)[g] = floor;
+    }
+}
 
 }  // namespace
 
@@ -92,47 +219,75 @@ int orbg_build_tables(int n, uint64_t cap, OrbgTables *out)
 {
     if (n < 1 || n > 256 || cap < 1)
         return -1;
+    /* warp table */
+    Builder bw;
+    bw.n = n;
+    bw.cta = false;
     out->runs.clear();
-    out->group_floor.clear();
-    Builder b;
-    b.n = n;
-    b.t = 1;
-    /* W = 0: the zero pattern */
-    b.emit_single(nullptr, 0);
-    b.flush(out);
-    long Wlast = (long)n * (n + 1) / 2;
+    uint64_t patterns = 0;
     int wdeep = 0;
-    for (long W = 1; W <= Wlast && b.t <= cap; W++) {
-        for (int w = 1; (long)w * (w + 1) / 2 <= W && w <= n; w++) {
-            if (w - 2 > ORBG_RUN_MAX_PRE)
-                return -2;
-            if (w == 1) {
-                if (W <= n) {
-                    int p = (int)W;
-                    b.emit_single(&p, 1);
-                }
-            } else {
-                b.prefixes(0, w - 2, 1, (int)W);
-            }
-            b.flush(out);
-        }
-        wdeep = (int)W;
-    }
-    out->patterns = b.t - 1;
+    int rc = bw.build(cap, &out->runs, &patterns, &wdeep);
+    if (rc)
+        return rc;
+    out->patterns = patterns;
     out->wmax_logistic = wdeep;
-    if (out->patterns >= 0xFFFFFFFFull)
+    if (patterns >= 0xFFFFFFFFull)
         return -3;
-    /* pad to whole groups with runs that start after every real one */
-    size_t nr = out->runs.size();
-    size_t ng = (nr + ORBG_GROUP - 1) / ORBG_GROUP;
-    out->group_floor.assign(ng, 0xFFFFFFFFu);
-    uint32_t floor = 0xFFFFFFFFu;
-    for (size_t g = ng; g-- > 0;) {
-        for (size_t i = g * ORBG_GROUP; i < std::min(nr, (g + 1) * ORBG_GROUP); i++)
-            floor = std::min(floor, out->runs[i].tstart);
-        out->group_floor[g] = floor;
+    /* X3: every triple c < a < b <= n by sum (<= the table's depth, within
+     * ORBG_X3_MAX entries), then c, then a */
+    std::vector<uint32_t> x3off(ORBG_MAX_LOGISTIC + 2, 0);
+    out->trip.clear();
+    int s3max = 0;
+    for (int S3 = 6; S3 <= wdeep; S3++) {
+        size_t cnt = 0;
+        for (int c = trip_c_lo(S3, 1, n); c <= trip_c_hi(S3); c++)
+            cnt += (size_t)(pair_hi(S3 - c) - pair_lo(S3 - c, c + 1, n) + 1);
+        if (out->trip.size() + cnt > ORBG_X3_MAX)
+            break;
+        x3off[S3] = (uint32_t)out->trip.size();
+        for (int c = trip_c_lo(S3, 1, n); c <= trip_c_hi(S3); c++)
+            for (int a = pair_lo(S3 - c, c + 1, n); a <= pair_hi(S3 - c); a++)
+                out->trip.push_back((uint32_t)(c - 1) | ((uint32_t)(a - 1) << 8) |
+                                    ((uint32_t)(S3 - c - a - 1) << 16));
+        s3max = S3;
     }
+    /* CTA table */
+    Builder bc;
+    bc.n = n;
+    bc.cta = true;
+    bc.s3max = s3max;
+    bc.x3off = &x3off;
+    out->runs_cta.clear();
+    uint64_t patterns_c = 0;
+    int wdeep_c = 0;
+    rc = bc.build(cap, &out->runs_cta, &patterns_c, &wdeep_c);
+    if (rc)
+        return rc;
+    if (patterns_c != patterns)
+        return -5;
+    floors(out->runs, &out->group_floor);
+    floors(out->runs_cta, &out->group_floor_cta);
     return 0;
+}
+
+/* Expands run r's j-th pattern into v (1-based sorted positions, ascending);
+ * returns its Hamming weight.  trip is the table's X3 triple list. */
+int orbg_run_pattern(const OrbgRun &r, int j, const uint32_t *trip, int *v)
+{
+    int w = 0;
+    for (int i = 0; i < r.npre; i++)
+        v[w++] = r.pre[i] + 1;
+    if (r.kind == ORBG_RUN_PAIRS) {
+        const int S = (int)(r.aux & 0xFFu), a = (int)(r.aux >> 8) + j;
+        v[w++] = a;
+        v[w++] = S - a;
+    } else if (r.kind == ORBG_RUN_TRIPLES) {
+        const uint32_t t = trip[r.aux + (uint32_t)j];
+        v[w++] = (int)(t & 0xFFu) + 1;
+        v[w++] = (int)((t >> 8) & 0xFFu) + 1;
+        v[w++] = (int)((t >> 16) & 0xFFu) + 1;
+    }
+    return w;
 }
 
 /* ------------------------------------------------------------- GF(2) -- */

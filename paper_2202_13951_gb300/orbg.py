@@ -46,6 +46,16 @@ class OrbgTuning(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class OrbgServerStats(ctypes.Structure):
+    """struct orbg_server_stats of include/orbg.h."""
+    _fields_ = [(f, ctypes.c_uint64) for f in (
+        "submitted", "completed", "blocks_submitted", "blocks_done", "batches",
+        "max_batch_blocks", "max_inflight_batches", "pending", "inflight_batches")]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
 class OrbgError(RuntimeError):
     def __init__(self, status, what=""):
         self.status = status
@@ -85,18 +95,32 @@ def load_library(path=None):
     lib.orbg_decode_batched.argtypes = [vp, vp, vp, vp, i64, u32, vp, vp, vp, vp, vp]
     lib.orbg_decode_batched_noalloc.argtypes = [vp, vp, vp, vp, i64, u32, vp, vp, vp, vp, vp]
     lib.orbg_codeset_set_tuning.argtypes = [vp, ctypes.POINTER(OrbgTuning)]
+    lib.orbg_codeset_autotune.argtypes = [vp, vp, vp, vp, i64, u32, vp, vp, vp, vp, i32, vp,
+                                          ctypes.POINTER(OrbgTuning)]
     lib.orbg_codeset_get_tuning.argtypes = [vp, ctypes.POINTER(OrbgTuning)]
     lib.orbg_probe_int_lanes.argtypes = [ctypes.POINTER(ctypes.c_double)]
     lib.orbg_status_string.argtypes = [i32]
     lib.orbg_status_string.restype = ctypes.c_char_p
     lib.orbg_last_cuda_error.argtypes = []
     lib.orbg_version.argtypes = []
-    lib.orbg_query_order.argtypes = [i32, u32, vp]
+    lib.orbg_query_order.argtypes = [i32, u32, i32, vp]
     lib.orbg_query_order.restype = i64
+    lib.orbg_server_create.argtypes = [vp, ctypes.c_size_t, u32, i32, i64, ctypes.POINTER(vp)]
+    lib.orbg_server_submit.argtypes = [vp, ctypes.c_uint64, i32, vp, i64]
+    lib.orbg_server_poll.argtypes = [vp, vp, i32, i32]
+    lib.orbg_server_fetch.argtypes = [vp, ctypes.c_uint64, vp, vp, vp,
+                                      ctypes.POINTER(ctypes.c_double)]
+    lib.orbg_server_stats_get.argtypes = [vp, ctypes.POINTER(OrbgServerStats)]
+    lib.orbg_server_destroy.argtypes = [vp]
+    lib.orbg_server_replay.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                       ctypes.POINTER(ctypes.c_double)]
     for f in ("orbg_load_code", "orbg_free_code", "orbg_code_info", "orbg_decode",
               "orbg_codeset_create", "orbg_codeset_free", "orbg_decode_batched",
-              "orbg_decode_batched_noalloc",
+              "orbg_decode_batched_noalloc", "orbg_server_create", "orbg_server_submit",
+              "orbg_server_poll", "orbg_server_fetch", "orbg_server_stats_get",
+              "orbg_server_destroy", "orbg_server_replay",
               "orbg_codeset_set_tuning", "orbg_codeset_get_tuning", "orbg_probe_int_lanes",
+              "orbg_codeset_autotune",
               "orbg_last_cuda_error", "orbg_version"):
         getattr(lib, f).restype = i32
     if path == LIB_PATH:
@@ -212,6 +236,58 @@ def orbg_decode_batched_noalloc(cs, code_id, llr_offset, llr, B, query_cap, code
     _check(rc, "orbg_decode_batched_noalloc")
 
 
+def orbg_server_create(cs, mem_budget_bytes, query_cap, streams=0, max_batch_blocks=0):
+    h = ctypes.c_void_p()
+    _check(load_library().orbg_server_create(cs, int(mem_budget_bytes), int(query_cap),
+                                             int(streams), int(max_batch_blocks),
+                                             ctypes.byref(h)), "orbg_server_create")
+    return h
+
+
+def orbg_server_submit(srv, request_id, code_index, llr, B):
+    _check(load_library().orbg_server_submit(srv, int(request_id), int(code_index),
+                                             _ptr(llr, "float32"), int(B)),
+           "orbg_server_submit")
+
+
+def orbg_server_poll(srv, max_ids=1024, timeout_us=1000):
+    ids = np.zeros(max_ids, np.uint64)
+    k = load_library().orbg_server_poll(srv, ids.ctypes.data, int(max_ids), int(timeout_us))
+    if k < 0:
+        raise OrbgError(k, "orbg_server_poll")
+    return [int(x) for x in ids[:k]]
+
+
+def orbg_server_fetch(srv, request_id, codeword=None, queries=None, abandoned=None):
+    lat = ctypes.c_double()
+    _check(load_library().orbg_server_fetch(srv, int(request_id), _ptr(codeword, "uint8"),
+                                            _ptr(queries, "uint32"), _ptr(abandoned, "uint8"),
+                                            ctypes.byref(lat)), "orbg_server_fetch")
+    return lat.value
+
+
+def orbg_server_stats_get(srv):
+    st = OrbgServerStats()
+    _check(load_library().orbg_server_stats_get(srv, ctypes.byref(st)), "orbg_server_stats_get")
+    return st.as_dict()
+
+
+def orbg_server_destroy(srv):
+    _check(load_library().orbg_server_destroy(srv), "orbg_server_destroy")
+
+
+def orbg_server_replay(srv, arrival_s, code, B, llr_off, blk_off, llr_all, cw_all, q_all,
+                       ab_all, latency_s):
+    wall = ctypes.c_double()
+    _check(load_library().orbg_server_replay(
+        srv, int(len(arrival_s)), _ptr(arrival_s, "float64"), _ptr(code, "int32"),
+        _ptr(B, "int64"), _ptr(llr_off, "int64"), _ptr(blk_off, "int64"),
+        _ptr(llr_all, "float32"), _ptr(cw_all, "uint8"), _ptr(q_all, "uint32"),
+        _ptr(ab_all, "uint8"), _ptr(latency_s, "float64"), ctypes.byref(wall)),
+        "orbg_server_replay")
+    return wall.value
+
+
 def orbg_codeset_set_tuning(cs, tuning=None):
     """tuning: OrbgTuning, a dict of its fields, or None for the defaults."""
     t = None
@@ -220,6 +296,20 @@ def orbg_codeset_set_tuning(cs, tuning=None):
             tuning = OrbgTuning(**tuning)
         t = ctypes.byref(tuning)
     _check(load_library().orbg_codeset_set_tuning(cs, t), "orbg_codeset_set_tuning")
+
+
+def orbg_codeset_autotune(cs, code_id, llr_offset, llr, B, query_cap, codeword, cw_offset,
+                          queries, abandoned, reps=3, cuda_stream=None):
+    """Coordinate-descent autotuner of the batched form on a device sample;
+    sets the fastest tuning on the code set and returns it."""
+    t = OrbgTuning()
+    rc = load_library().orbg_codeset_autotune(
+        cs, _ptr(code_id, "int32"), _ptr(llr_offset, "int64"), _ptr(llr, "float32"), int(B),
+        int(query_cap), _ptr(codeword, "uint8"), _ptr(cw_offset, "int64"),
+        _ptr(queries, "uint32"), _ptr(abandoned, "uint8"), int(reps), _stream(cuda_stream),
+        ctypes.byref(t))
+    _check(rc, "orbg_codeset_autotune")
+    return t
 
 
 def orbg_codeset_get_tuning(cs):
@@ -248,12 +338,13 @@ def orbg_version():
     return load_library().orbg_version()
 
 
-def orbg_query_order(n, count):
+def orbg_query_order(n, count, table=0):
     """First `count` patterns of the decoder's query order for length n, as
-    tuples of 1-based sorted-order positions."""
+    tuples of 1-based sorted-order positions, from table 0 (warp) or 1
+    (CTA)."""
     lib = load_library()
     out = np.zeros((count, n + 1), np.int32)
-    got = lib.orbg_query_order(int(n), int(count), out.ctypes.data)
+    got = lib.orbg_query_order(int(n), int(count), int(table), out.ctypes.data)
     if got < 0:
         raise OrbgError(int(got), "orbg_query_order")
     return [tuple(int(x) for x in row[1:1 + row[0]]) for row in out[:got]]

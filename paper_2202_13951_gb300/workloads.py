@@ -365,3 +365,55 @@ def config4_inputs(B=1_000_000, seed=401):
         llr[pos] = l
         cw[pos] = c
     return codes, cid, llr, off, cw, ebn0
+
+
+def config5_codes():
+    """The serving mix: BCH(127,113), CA-Polar(128,94[K=105]), RLC(128,112)."""
+    return [bch(), ca_polar(), rlc(128, 112, seed=42)]
+
+
+def serving_trace(rate_blocks_s=2e6, seconds=10.0, max_size=4096, ebn0=(3.0, 7.0),
+                  seed=501, codes=None):
+    """Poisson request stream: request sizes U{1..max_size} blocks, code
+    uniform over `codes`, Eb/N0 uniform in `ebn0` per request; arrivals with
+    exponential gaps at rate_blocks_s / E[size] requests per second, over
+    `seconds`.  Returns a dict of arrays (arrival_s, code, B, ebn0,
+    llr_off, blk_off) plus llr_all (float32) and cw_all (transmitted)."""
+    codes = codes if codes is not None else config5_codes()
+    rng = np.random.default_rng(seed)
+    mean_size = (1 + max_size) / 2.0
+    req_rate = rate_blocks_s / mean_size
+    arrivals = []
+    t = 0.0
+    while True:
+        t += rng.exponential(1.0 / req_rate)
+        if t >= seconds:
+            break
+        arrivals.append(t)
+    m = len(arrivals)
+    size = rng.integers(1, max_size + 1, size=m).astype(np.int64)
+    code = rng.integers(0, len(codes), size=m).astype(np.int32)
+    eb = rng.uniform(ebn0[0], ebn0[1], size=m)
+    ns = np.array([c.n for c in codes], np.int64)
+    elems = size * ns[code]
+    llr_off = np.zeros(m, np.int64)
+    llr_off[1:] = np.cumsum(elems)[:-1]
+    blk_off = np.zeros(m, np.int64)
+    blk_off[1:] = np.cumsum(size)[:-1]
+    llr_all = np.zeros(int(elems.sum()), np.float32)
+    cw_all = np.zeros(int(elems.sum()), np.uint8)
+    for j, cd in enumerate(codes):
+        reqs = np.nonzero(code == j)[0]
+        if reqs.size == 0:
+            continue
+        per_block_eb = np.repeat(eb[reqs], size[reqs])
+        l, c = awgn_llr(cd, int(size[reqs].sum()), per_block_eb, seed * 10 + j)
+        pos = 0
+        for r in reqs:
+            k = int(size[r])
+            llr_all[llr_off[r]:llr_off[r] + k * cd.n] = l[pos:pos + k].ravel()
+            cw_all[llr_off[r]:llr_off[r] + k * cd.n] = c[pos:pos + k].ravel()
+            pos += k
+    return {"arrival_s": np.array(arrivals, np.float64), "code": code, "B": size,
+            "ebn0": eb, "llr_off": llr_off, "blk_off": blk_off, "llr_all": llr_all,
+            "cw_all": cw_all, "codes": codes}

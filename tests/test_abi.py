@@ -91,8 +91,10 @@ def test_decode_argument_checks_without_gpu(lib):
                                      (16, 65536), (64, 150000), (127, 150000),
                                      (128, 150000), (256, 40000)])
 def test_query_order_tables_match_oracle(lib, n, count):
-    """The tables the kernels walk expand to exactly the oracle's order."""
-    assert orbg.orbg_query_order(n, count) == oracle.enumerate_patterns(n, count)
+    """Both tables the kernels walk expand to exactly the oracle's order."""
+    want = oracle.enumerate_patterns(n, count)
+    assert orbg.orbg_query_order(n, count, 0) == want
+    assert orbg.orbg_query_order(n, count, 1) == want
 
 
 def test_query_order_depth_for_cap(lib):
@@ -101,7 +103,7 @@ def test_query_order_depth_for_cap(lib):
     for n in (64, 128):
         cnt = oracle.count_by_weight(n, 82)
         total = int(cnt.sum())
-        got = lib.orbg_query_order(n, 0, None)
+        got = lib.orbg_query_order(n, 0, 0, None)
         assert got == 0
         # the library must cover at least `total` patterns for that cap
         out = np.zeros((1, n + 1), np.int32)
