@@ -317,7 +317,8 @@ ORBG_API int orbg_probe_int_lanes(double *lanes_per_clk_per_sm);
  * first `count` noise patterns for length n (1..256), expanded from the
  * same tables the kernels read (table 0: the one-warp-per-block table;
  * table 1: the CTA table of the batched form's second phase; both hold
- * the same order).  out: host memory, [count][n+1] int32 rows
+ * the same order; table 2: the flat table of the leading patterns both
+ * start with, which stops after at most 1024 patterns).  out: host memory, [count][n+1] int32 rows
  * holding w, then the w flipped positions (1-based, in increasing
  * reliability order, ascending), then zeros.  Returns the number of rows
  * written (fewer than count once the 2^n patterns run out), or a negative

@@ -26,6 +26,9 @@ struct orbg_code {
     OrbgRun *d_runs_cta = nullptr;
     uint32_t *d_floor_cta = nullptr;
     uint32_t *d_trip = nullptr;
+    uint32_t *d_reach = nullptr;
+    uint32_t *d_reach_cta = nullptr;
+    uint8_t *d_flat = nullptr;
     OrbgDeviceCode dev;
 };
 
@@ -131,9 +134,15 @@ void free_code_device(orbg_code *c)
     if (c->d_runs_cta) cudaFree(c->d_runs_cta);
     if (c->d_floor_cta) cudaFree(c->d_floor_cta);
     if (c->d_trip) cudaFree(c->d_trip);
+    if (c->d_reach) cudaFree(c->d_reach);
+    if (c->d_reach_cta) cudaFree(c->d_reach_cta);
+    if (c->d_flat) cudaFree(c->d_flat);
     c->d_runs_cta = nullptr;
     c->d_floor_cta = nullptr;
     c->d_trip = nullptr;
+    c->d_reach = nullptr;
+    c->d_reach_cta = nullptr;
+    c->d_flat = nullptr;
     c->d_hcol = nullptr;
     c->d_runs = nullptr;
     c->d_floor = nullptr;
@@ -191,7 +200,7 @@ int orbg_version(void) { return 100; }
 
 int64_t orbg_query_order(int n, uint32_t count, int table, int32_t *out)
 {
-    if (n < 1 || n > ORBG_MAX_N || (count > 0 && !out) || table < 0 || table > 1)
+    if (n < 1 || n > ORBG_MAX_N || (count > 0 && !out) || table < 0 || table > 2)
         return ORBG_EINVAL;
     if (count == 0)
         return 0;
@@ -201,6 +210,19 @@ int64_t orbg_query_order(int n, uint32_t count, int table, int32_t *out)
     const std::vector<OrbgRun> &runs = table == 0 ? tb.runs : tb.runs_cta;
     const size_t stride = (size_t)n + 1;
     uint64_t total = std::min<uint64_t>(tb.patterns, count);
+    if (table == 2) {
+        /* the flat table: its leading patterns only */
+        total = std::min<uint64_t>(total, tb.nflat);
+        std::memset(out, 0, sizeof(int32_t) * stride * (size_t)total);
+        for (uint64_t t = 0; t < total; t++) {
+            const uint8_t *e = &tb.flat[t * 8];
+            int32_t *row = out + t * stride;
+            row[0] = e[7];
+            for (int i = 0; i < e[7]; i++)
+                row[1 + i] = e[i];
+        }
+        return (int64_t)total;
+    }
     std::memset(out, 0, sizeof(int32_t) * stride * (size_t)total);
     std::vector<int> v(64);
     for (const OrbgRun &r : runs) {
@@ -337,7 +359,10 @@ int orbg_load_code(const uint8_t *mat, int kind, int n, int k, uint32_t max_quer
         {(void **)&c->d_runs_cta, tb.runs_cta.data(), tb.runs_cta.size() * sizeof(OrbgRun)},
         {(void **)&c->d_floor_cta, tb.group_floor_cta.data(),
          tb.group_floor_cta.size() * sizeof(uint32_t)},
-        {(void **)&c->d_trip, tb.trip.data(), std::max<size_t>(4, tb.trip.size() * 4)},
+        {(void **)&c->d_trip, tb.trip.data(), tb.trip.size() * 4},
+        {(void **)&c->d_reach, tb.reach.data(), tb.reach.size() * 4},
+        {(void **)&c->d_reach_cta, tb.reach_cta.data(), tb.reach_cta.size() * 4},
+        {(void **)&c->d_flat, tb.flat.data(), tb.flat.size()},
     };
     for (const Up &u : ups) {
         const size_t bytes = std::max<size_t>(u.bytes, 4);
@@ -354,10 +379,16 @@ int orbg_load_code(const uint8_t *mat, int kind, int n, int k, uint32_t max_quer
     c->dev.warp.group_floor = c->d_floor;
     c->dev.warp.nruns = (uint32_t)tb.runs.size();
     c->dev.warp.ngroups = (uint32_t)tb.group_floor.size();
+    c->dev.warp.group_reach = c->d_reach;
+    c->dev.warp.flat_group = tb.flat_group;
     c->dev.cta.runs = c->d_runs_cta;
     c->dev.cta.group_floor = c->d_floor_cta;
     c->dev.cta.nruns = (uint32_t)tb.runs_cta.size();
     c->dev.cta.ngroups = (uint32_t)tb.group_floor_cta.size();
+    c->dev.cta.group_reach = c->d_reach_cta;
+    c->dev.cta.flat_group = tb.flat_group_cta;
+    c->dev.flat = reinterpret_cast<const uint32_t *>(c->d_flat);
+    c->dev.nflat = tb.nflat;
     c->dev.trip = c->d_trip;
     c->dev.ntrip = (uint32_t)tb.trip.size();
     c->dev.max_cap = cap;
@@ -492,7 +523,7 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
 {
     if (!set || B < 0 || query_cap < 1)
         return ORBG_EINVAL;
-    if (query_cap > set->cap_min)
+    if (query_cap > set->cap_min || B >= ((int64_t)1 << 32))
         return ORBG_ELIMIT;
     if (B == 0)
         return ORBG_OK;

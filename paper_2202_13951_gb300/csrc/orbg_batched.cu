@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cuda_pipeline.h>
+
 #include "orbg_decode_block.cuh"
 
 using namespace orbg_dev;
@@ -36,36 +38,76 @@ __global__ void __launch_bounds__(256, 4) orbg_batched_kernel(
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
     unsigned char *bsm = smem + warp * bstride;
+    /* two LLR slots per warp: the block being decoded and the next one,
+     * copied in asynchronously while the current one is decoded */
+    constexpr int kSlot = 32 * KMAX;
+    float *ring = reinterpret_cast<float *>(smem + nwarps * bstride) + warp * 2 * kSlot;
     const int64_t n0 = codes[0].n;
-    for (;;) {
-        /* one atomic per `grab` consecutive blocks */
-        unsigned long long b0 = 0;
-        if (lane == 0)
-            b0 = atomicAdd(&counters[0], (unsigned long long)grab);
-        b0 = __shfl_sync(FULL_MASK, b0, 0);
-        if ((int64_t)b0 >= B)
-            break;
-        const int64_t bend = min((int64_t)b0 + grab, B);
-        for (int64_t b = (int64_t)b0; b < bend; b++) {
+
+    /* the warp's block sequence: `grab` consecutive blocks per atomic */
+    int64_t pos = 0, end = 0;
+    auto next_block = [&]() -> int64_t {
+        if (pos >= end) {
+            unsigned long long c = 0;
+            if (lane == 0)
+                c = atomicAdd(&counters[0], (unsigned long long)grab);
+            c = __shfl_sync(FULL_MASK, c, 0);
+            pos = (int64_t)c;
+            end = min(pos + (int64_t)grab, B);
+            if (pos >= B)
+                return B;
+        }
+        return pos++;
+    };
+    auto stage = [&](int64_t b, int slot) {
+        if (b < B) {
             const int cid = code_id ? code_id[b] : 0;
-            if (cid < 0 || cid >= ncodes) {
-                if (lane == 0) {
-                    q[b] = 0u;
-                    ab[b] = 2;
+            if (cid >= 0 && cid < ncodes) {
+                const int n = codes[cid].n;
+                const int64_t lo = llr_off ? llr_off[b] : b * n0;
+#pragma unroll
+                for (int k = 0; k < KMAX; k++) {
+                    const int i = k * 32 + lane;
+                    if (i < n)
+                        __pipeline_memcpy_async(ring + slot * kSlot + i, llr + lo + i, 4);
                 }
-                continue;
             }
+        }
+        __pipeline_commit();
+    };
+
+    int64_t b = next_block();
+    int slot = 0;
+    stage(b, slot);
+    int64_t bn = next_block();
+    while (b < B) {
+        stage(bn, slot ^ 1);
+        __pipeline_wait_prior(1); /* block b's copies have landed */
+        __syncwarp();
+        const int cid = code_id ? code_id[b] : 0;
+        if (cid < 0 || cid >= ncodes) {
+            if (lane == 0) {
+                q[b] = 0u;
+                ab[b] = 2;
+            }
+        } else {
             const OrbgDeviceCode code = codes[cid];
-            const int64_t lo = llr_off ? llr_off[b] : b * n0;
             const int64_t co = cw_off ? cw_off[b] : b * n0;
-#define ORBG_CALL_WARP(KK, WW)                                                            \
-    decode_block_warp<KK, WW>(code, llr + lo, cw + co, q + b, ab + b, cap, budget, bsm, lane, \
-                              heavy, &counters[1], (unsigned long long)b)
+            const float *l = ring + slot * kSlot;
+#define ORBG_CALL_WARP(KK, WW)                                                                 \
+    decode_block_warp<KK, WW, true>(code, l, cw + co, q + b, ab + b, cap, budget, bsm, lane, \
+                                    heavy, &counters[1], (unsigned long long)b)
             ORBG_DISPATCH(KMAX, WMAX, ORBG_CALL_WARP);
 #undef ORBG_CALL_WARP
         }
+        __syncwarp(); /* slot is free before it is refilled */
+        b = bn;
+        bn = next_block();
+        slot ^= 1;
     }
+    __pipeline_wait_prior(0);
 }
 
 }  // namespace
@@ -109,9 +151,9 @@ cudaError_t launch_batched_t(const OrbgDeviceCode *d_codes, int ncodes, int n_ma
     if ((e = cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * kCounters, st)) !=
         cudaSuccess)
         return e;
-    /* phase 1 */
+    /* phase 1: per warp, one block's working set and two LLR slots */
     auto k1 = orbg_batched_kernel<KMAX, WMAX>;
-    size_t smem1 = (size_t)bstride * wpc;
+    size_t smem1 = ((size_t)bstride + 2u * 32u * KMAX * sizeof(float)) * wpc;
     if ((rc = orbg_grid_for((const void *)k1, wpc * 32, smem1, ctas_per_sm, &grid)) != 0)
         return (cudaError_t)rc;
     int64_t units = (B + g - 1) / g;

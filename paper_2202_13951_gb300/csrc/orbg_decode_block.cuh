@@ -126,11 +126,21 @@ __device__ __forceinline__ uint32_t first_word(uint32_t v) { return v; }
 __device__ __forceinline__ uint32_t first_word(uint2 v) { return v.x; }
 __device__ __forceinline__ uint32_t first_word(uint4 v) { return v.x; }
 
+/* LLR reads: from shared memory (LS, staged ahead by the batched kernel)
+ * or from global memory through the read-only path. */
+template <bool LS>
+__device__ __forceinline__ float llr_at(const float *__restrict__ llr, int i)
+{
+    if (LS)
+        return llr[i];
+    return __ldg(llr + i);
+}
+
 /* ------------------------------------------------------- step 1: load */
 
 /* Loads the block, writes y into cw, builds the K keys per lane and returns
  * s0 (identical in every lane).  *nan is warp-uniform. */
-template <int K, int W>
+template <int K, int W, bool LS = false>
 __device__ __forceinline__ typename Syn<W>::T load_block(const OrbgDeviceCode &code,
                                                          const float *__restrict__ llr,
                                                          uint64_t (&key)[K], uint8_t *cw,
@@ -144,7 +154,7 @@ __device__ __forceinline__ typename Syn<W>::T load_block(const OrbgDeviceCode &c
     for (int k = 0; k < K; k++) {
         int i = k * 32 + lane;
         if (i < n) {
-            float L = __ldg(llr + i);
+            float L = llr_at<LS>(llr, i);
             nan |= (L != L);
             uint32_t bits = __float_as_uint(L) & 0x7FFFFFFFu;
             key[k] = ((uint64_t)bits << 32) | (uint32_t)i;
@@ -255,7 +265,7 @@ template <int K> struct KeyBits {
 /* Sort 64-bit keys (bits << 32 | i) through 32-bit keys; returns false if
  * the truncated order may differ from the exact one. On true, key[] holds
  * the exact sorted keys (positions e = lane*K + k). */
-template <int K>
+template <int K, bool LS = false>
 __device__ __forceinline__ bool sort_keys_fast(uint64_t (&key)[K], const float *__restrict__ llr,
                                                int n, int lane)
 {
@@ -277,8 +287,8 @@ __device__ __forceinline__ bool sort_keys_fast(uint64_t (&key)[K], const float *
         const int e = lane * K + k;
         const uint32_t nxt = (k + 1 < K) ? k32[k + 1 < K ? k + 1 : k] : next_first;
         if (e + 1 < n && (k32[k] >> KB::IB) == (nxt >> KB::IB)) {
-            const uint32_t ba = __float_as_uint(__ldg(llr + (k32[k] & KB::IMASK))) & 0x7FFFFFFFu;
-            const uint32_t bb = __float_as_uint(__ldg(llr + (nxt & KB::IMASK))) & 0x7FFFFFFFu;
+            const uint32_t ba = __float_as_uint(llr_at<LS>(llr, (int)(k32[k] & KB::IMASK))) & 0x7FFFFFFFu;
+            const uint32_t bb = __float_as_uint(llr_at<LS>(llr, (int)(nxt & KB::IMASK))) & 0x7FFFFFFFu;
             bad |= ba > bb;
         }
     }
@@ -294,11 +304,11 @@ __device__ __forceinline__ bool sort_keys_fast(uint64_t (&key)[K], const float *
 
 /* Sort with the fast path and the exact fallback (the fast path leaves
  * key[] untouched when it gives up). */
-template <int K>
+template <int K, bool LS = false>
 __device__ __forceinline__ void sort_block(uint64_t (&key)[K], const float *__restrict__ llr,
                                            int n, int lane)
 {
-    if (!sort_keys_fast<K>(key, llr, n, lane))
+    if (!sort_keys_fast<K, LS>(key, llr, n, lane))
         sort_keys<K>(key, lane);
 }
 
@@ -557,6 +567,77 @@ __device__ __forceinline__ void apply_flips(const OrbgTable &tb, uint32_t run, u
         cw[pi[pos[i]]] ^= 1;
 }
 
+/* ---------------------------------------------------- the flat table */
+
+/* Flat-table pattern t (1-based): up to ORBG_FLAT_POS positions. */
+__device__ __forceinline__ int flat_pos(const uint2 &e, int i)
+{
+    return (int)(((i < 4 ? e.x : e.y) >> (8 * (i & 3))) & 0xFFu); /* 1-based, 0 = none */
+}
+
+/* Lane's query of flat step `base` (queries base+1 .. base+32): returns its
+ * index if it is a hit, else ORBG_NONE. */
+template <int W>
+__device__ __forceinline__ uint32_t flat_query(const OrbgDeviceCode &code,
+                                               const typename Syn<W>::T *__restrict__ h,
+                                               const uint32_t *__restrict__ h0,
+                                               const typename Syn<W>::T s0, uint32_t base,
+                                               uint32_t cap, int lane)
+{
+    typedef typename Syn<W>::T T;
+    const uint32_t t = base + (uint32_t)lane + 1u;
+    if (t > code.nflat || t > cap)
+        return ORBG_NONE;
+    const uint2 e = __ldg(reinterpret_cast<const uint2 *>(code.flat) + (t - 1));
+    const int n = code.n;
+    uint32_t p[ORBG_FLAT_POS];
+#pragma unroll
+    for (int i = 0; i < ORBG_FLAT_POS; i++) {
+        const int q = flat_pos(e, i);
+        p[i] = h0[q ? q - 1 : n];
+    }
+    const uint32_t P0 = first_word(s0) ^ p[0] ^ p[1] ^ p[2] ^ p[3] ^ p[4] ^ p[5] ^ p[6];
+    if (P0 != 0u)
+        return ORBG_NONE;
+    if (W > 1) {
+        T P = s0;
+        for (int i = 0; i < ORBG_FLAT_POS; i++) {
+            const int q = flat_pos(e, i);
+            if (q)
+                P = sx(P, h[q - 1]);
+        }
+        if (!sz(P))
+            return ORBG_NONE;
+    }
+    return t;
+}
+
+/* Flips of flat pattern t into the staged codeword. */
+__device__ __forceinline__ void apply_flat_flips(const OrbgDeviceCode &code, uint32_t t,
+                                                 const uint8_t *pi, uint8_t *cw)
+{
+    const uint2 e = __ldg(reinterpret_cast<const uint2 *>(code.flat) + (t - 1));
+    for (int i = 0; i < ORBG_FLAT_POS; i++) {
+        const int q = flat_pos(e, i);
+        if (q)
+            cw[pi[q - 1]] ^= 1;
+    }
+}
+
+/* First group of `tb` holding a query >= q (reach is non-decreasing). */
+__device__ __forceinline__ uint32_t group_reaching(const OrbgTable &tb, uint32_t q)
+{
+    uint32_t lo = 0, hi = tb.ngroups;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(tb.group_reach + mid) >= q)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
 /* ------------------------------------------------ one warp, one block */
 
 /*
@@ -565,9 +646,10 @@ __device__ __forceinline__ void apply_flips(const OrbgTable &tb, uint32_t run, u
  * below the best hit, at most `cap`, and at most `budget`.  If the walk
  * stops on the budget with the result still open, the block is not
  * written: its index is appended to heavy[] (when heavy != NULL) for
- * decode_block_cta.  With budget >= cap every block finishes here.
+ * decode_block_cta.  With budget >= cap every block finishes here.  LS:
+ * llr points into shared memory (the batched kernel stages it there).
  */
-template <int K, int W>
+template <int K, int W, bool LS = false>
 __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__restrict__ llr,
                                   uint8_t *__restrict__ cw_out, uint32_t *__restrict__ q_out,
                                   uint8_t *__restrict__ ab_out, uint32_t cap, uint32_t budget,
@@ -581,54 +663,105 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
     BlockSmem<W> sm(bsm, n);
     uint64_t key[K];
     bool nan;
-    const T s0 = load_block<K, W>(code, llr, key, sm.cw, lane, &nan);
+    const T s0 = load_block<K, W, LS>(code, llr, key, sm.cw, lane, &nan);
     uint32_t best = ORBG_NONE, my_t = ORBG_NONE, my_run = 0, my_hit = 0;
+    uint32_t handover = 0;
     bool done = true;
     if (nan) {
         best = ORBG_NONE - 1; /* marker: NaN block */
     } else if (sz(s0)) {
         best = 1u;            /* query 1, the zero pattern, is a codeword */
     } else {
-        sort_block<K>(key, llr, n, lane);
+        sort_block<K, LS>(key, llr, n, lane);
         build_perm<K, W>(code, key, sm, lane);
         __syncwarp();
-        uint32_t stop = ORBG_NONE;
-        uint4 n0, n1;
-        load_run(tb, (uint32_t)lane, &n0, &n1);
-        for (uint32_t g = 0; g < tb.ngroups; g++) {
-            const uint32_t floor = __ldg(tb.group_floor + g);
-            if (floor >= best || floor > cap || floor > budget) {
-                stop = floor;
-                break;
-            }
-            const uint4 v0 = n0, v1 = n1;
-            load_run(tb, (g + 1) * ORBG_GROUP + (uint32_t)lane, &n0, &n1); /* prefetch */
-            uint32_t hv = 0;
-            const uint32_t mine = search_run_warp<W>(v0, v1, sm.h, sm.h0, s0, best, cap, n, &hv);
+        /* the flat table: 32 consecutive queries per step, in query order,
+         * so the first step with a hit holds the answer */
+        for (uint32_t base = 0; base < code.nflat && base < cap; base += 32u) {
+            const uint32_t mine = flat_query<W>(code, sm.h, sm.h0, s0, base, cap, lane);
             const uint32_t gbest = __reduce_min_sync(FULL_MASK, mine);
-            if (gbest < best) {
+            if (gbest != ORBG_NONE) {
                 best = gbest;
                 if (mine == gbest) {
                     my_t = mine;
-                    my_run = g * ORBG_GROUP + (uint32_t)lane;
-                    my_hit = hv;
+                    my_run = ORBG_NONE; /* a flat-table hit */
+                }
+                break;
+            }
+        }
+        uint32_t stop = ORBG_NONE;
+        if (best == ORBG_NONE) {
+            /* then the runs, from the first group past the flat table */
+            uint4 n0, n1;
+            const uint32_t g0 = tb.flat_group;
+            load_run(tb, g0 * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
+            for (uint32_t g = g0; g < tb.ngroups; g++) {
+                const uint32_t floor = __ldg(tb.group_floor + g);
+                if (floor >= best || floor > cap || floor > budget) {
+                    stop = floor;
+                    break;
+                }
+                const uint4 v0 = n0, v1 = n1;
+                load_run(tb, (g + 1) * ORBG_GROUP + (uint32_t)lane, &n0, &n1); /* prefetch */
+                uint32_t hv = 0;
+                const uint32_t mine =
+                    search_run_warp<W>(v0, v1, sm.h, sm.h0, s0, best, cap, n, &hv);
+                const uint32_t gbest = __reduce_min_sync(FULL_MASK, mine);
+                if (gbest < best) {
+                    best = gbest;
+                    if (mine == gbest) {
+                        my_t = mine;
+                        my_run = g * ORBG_GROUP + (uint32_t)lane;
+                        my_hit = hv;
+                    }
                 }
             }
         }
         done = stop >= best || stop > cap; /* exhausted tables give stop = NONE */
+        if (!done && best != ORBG_NONE) {
+            /* a hit inside the budget whose class runs past it: finish here */
+            for (uint32_t g = 0; g < tb.ngroups; g++) {
+                const uint32_t floor = __ldg(tb.group_floor + g);
+                if (floor < stop)
+                    continue; /* walked already */
+                if (floor >= best || floor > cap)
+                    break;
+                uint4 v0, v1;
+                load_run(tb, g * ORBG_GROUP + (uint32_t)lane, &v0, &v1);
+                uint32_t hv = 0;
+                const uint32_t mine =
+                    search_run_warp<W>(v0, v1, sm.h, sm.h0, s0, best, cap, n, &hv);
+                const uint32_t gbest = __reduce_min_sync(FULL_MASK, mine);
+                if (gbest < best) {
+                    best = gbest;
+                    if (mine == gbest) {
+                        my_t = mine;
+                        my_run = g * ORBG_GROUP + (uint32_t)lane;
+                        my_hit = hv;
+                    }
+                }
+            }
+            done = true;
+        }
+        handover = stop;
     }
     if (!done) {
+        /* every query below `handover` was tested without a hit */
         if (heavy != nullptr && lane == 0) {
             unsigned long long slot = atomicAdd(heavy_count, 1ull);
-            heavy[slot] = block_index;
+            heavy[slot] = block_index | ((unsigned long long)handover << 32);
         }
         __syncwarp();
         return;
     }
     const bool is_nan = best == ORBG_NONE - 1;
     const bool hit = !is_nan && best <= cap;
-    if (hit && my_t == best)
-        apply_flips(tb, my_run, my_hit, code.trip, sm.pi, sm.cw);
+    if (hit && my_t == best) {
+        if (my_run == ORBG_NONE)
+            apply_flat_flips(code, my_t, sm.pi, sm.cw);
+        else
+            apply_flips(tb, my_run, my_hit, code.trip, sm.pi, sm.cw);
+    }
     __syncwarp();
 #pragma unroll
     for (int k = 0; k < K; k++) {
@@ -659,8 +792,8 @@ __device__ void decode_block_cta(const OrbgDeviceCode &code, const float *__rest
                                  uint8_t *__restrict__ cw_out, uint32_t *__restrict__ q_out,
                                  uint8_t *__restrict__ ab_out, uint32_t cap,
                                  unsigned char *__restrict__ bsm, uint32_t *__restrict__ X3,
-                                 uint32_t *s_best, typename Syn<W>::T *s_s0, int warp, int lane,
-                                 int nwarps)
+                                 uint32_t *s_best, typename Syn<W>::T *s_s0, uint32_t from,
+                                 int warp, int lane, int nwarps)
 {
     typedef typename Syn<W>::T T;
     const int n = code.n;
@@ -695,26 +828,56 @@ __device__ void decode_block_cta(const OrbgDeviceCode &code, const float *__rest
     uint32_t my_t = ORBG_NONE, my_run = 0, my_hit = 0;
     if (start == ORBG_NONE) {
         const T s0 = *s_s0;
-        uint4 n0, n1;
+        bool stopped = false;
         uint32_t g = (uint32_t)warp;
-        load_run(tb, g * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
-        for (; g < tb.ngroups; g += (uint32_t)nwarps) {
-            const uint32_t floor = __ldg(tb.group_floor + g);
-            const uint32_t best = *((volatile uint32_t *)s_best);
-            if (floor >= best || floor > cap)
-                break;
-            const uint4 v0 = n0, v1 = n1;
-            load_run(tb, (g + nwarps) * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
-            uint32_t hv = 0;
-            const uint32_t mine =
-                search_run_cta<W>(v0, v1, sm.h, sm.h0, X3, code.trip, s0, best, cap, n, &hv);
-            const uint32_t gbest = __reduce_min_sync(FULL_MASK, mine);
-            if (gbest != ORBG_NONE) {
-                if (mine == gbest) {
-                    my_t = mine;
-                    my_run = g * ORBG_GROUP + (uint32_t)lane;
-                    my_hit = hv;
-                    atomicMin(s_best, mine);
+        if (from <= code.nflat) {
+            /* flat table, steps interleaved over the warps: a warp that sees
+             * a hit, or a step at or past the best, has nothing left to do
+             * below the best (every query <= nflat is some warp's step) */
+            for (uint32_t base = 32u * (uint32_t)warp; base < code.nflat && base < cap;
+                 base += 32u * (uint32_t)nwarps) {
+                if (base + 1u >= *((volatile uint32_t *)s_best)) {
+                    stopped = true;
+                    break;
+                }
+                const uint32_t mine = flat_query<W>(code, sm.h, sm.h0, s0, base, cap, lane);
+                const uint32_t gbest = __reduce_min_sync(FULL_MASK, mine);
+                if (gbest != ORBG_NONE) {
+                    if (mine == gbest) {
+                        my_t = mine;
+                        my_run = ORBG_NONE;
+                        atomicMin(s_best, mine);
+                    }
+                    stopped = true;
+                    break;
+                }
+            }
+            g += tb.flat_group;
+        } else {
+            /* every query below `from` was tested by the warp pass */
+            g += group_reaching(tb, from);
+        }
+        if (!stopped) {
+            uint4 n0, n1;
+            load_run(tb, g * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
+            for (; g < tb.ngroups; g += (uint32_t)nwarps) {
+                const uint32_t floor = __ldg(tb.group_floor + g);
+                const uint32_t best = *((volatile uint32_t *)s_best);
+                if (floor >= best || floor > cap)
+                    break;
+                const uint4 v0 = n0, v1 = n1;
+                load_run(tb, (g + nwarps) * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
+                uint32_t hv = 0;
+                const uint32_t mine = search_run_cta<W>(v0, v1, sm.h, sm.h0, X3, code.trip, s0,
+                                                        best, cap, n, &hv);
+                const uint32_t gbest = __reduce_min_sync(FULL_MASK, mine);
+                if (gbest != ORBG_NONE) {
+                    if (mine == gbest) {
+                        my_t = mine;
+                        my_run = g * ORBG_GROUP + (uint32_t)lane;
+                        my_hit = hv;
+                        atomicMin(s_best, mine);
+                    }
                 }
             }
         }
@@ -723,8 +886,12 @@ __device__ void decode_block_cta(const OrbgDeviceCode &code, const float *__rest
     const uint32_t best = *s_best;
     const bool is_nan = best == ORBG_NONE - 1;
     const bool hit = !is_nan && best <= cap;
-    if (start == ORBG_NONE && hit && my_t == best)
-        apply_flips(tb, my_run, my_hit, code.trip, sm.pi, sm.cw);
+    if (start == ORBG_NONE && hit && my_t == best) {
+        if (my_run == ORBG_NONE)
+            apply_flat_flips(code, my_t, sm.pi, sm.cw);
+        else
+            apply_flips(tb, my_run, my_hit, code.trip, sm.pi, sm.cw);
+    }
     __syncthreads();
     for (int i = warp * 32 + lane; i < n; i += nwarps * 32)
         cw_out[i] = sm.cw[i];

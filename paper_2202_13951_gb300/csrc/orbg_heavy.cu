@@ -32,13 +32,14 @@ __global__ void __launch_bounds__(512, 2) orbg_heavy_kernel(
         if (threadIdx.x == 0) {
             const unsigned long long nheavy = *((volatile unsigned long long *)&counters[1]);
             const unsigned long long slot = atomicAdd(&counters[2], 1ull);
-            s_block = slot < nheavy ? heavy[slot] : ~0ull;
+            s_block = slot < nheavy ? heavy[slot] : ~0ull; /* block | tested-below << 32 */
         }
         __syncthreads();
         const unsigned long long bb = s_block;
         if (bb == ~0ull)
             break; /* uniform: every thread read the same s_block */
-        const int64_t b = (int64_t)bb;
+        const int64_t b = (int64_t)(bb & 0xFFFFFFFFull);
+        const uint32_t from = (uint32_t)(bb >> 32);
         const int cid = code_id ? code_id[b] : 0; /* checked in phase 1 */
         const OrbgDeviceCode code = codes[cid];
         const int64_t lo = llr_off ? llr_off[b] : b * n0;
@@ -46,7 +47,8 @@ __global__ void __launch_bounds__(512, 2) orbg_heavy_kernel(
 #define ORBG_CALL_CTA(KK, WW)                                                               \
     decode_block_cta<KK, WW>(code, llr + lo, cw + co, q + b, ab + b, cap, smem,              \
                              reinterpret_cast<uint32_t *>(smem + bstride), &s_best,          \
-                             reinterpret_cast<typename Syn<WW>::T *>(&s_s0), warp, lane, nwarps)
+                             reinterpret_cast<typename Syn<WW>::T *>(&s_s0), from, warp, lane,  \
+                             nwarps)
         ORBG_DISPATCH(KMAX, WMAX, ORBG_CALL_CTA);
 #undef ORBG_CALL_CTA
     }

@@ -53,9 +53,17 @@ struct OrbgRun {
 struct OrbgTable {
     const OrbgRun *runs;         /* [nruns] */
     const uint32_t *group_floor; /* [ngroups] */
+    const uint32_t *group_reach; /* [ngroups]: largest query index in groups <= g */
     uint32_t nruns;
     uint32_t ngroups;
+    uint32_t flat_group;         /* first group holding a query beyond the flat table */
 };
+
+/* The flat table: the first `nflat` patterns of the order, 8 bytes each:
+ * up to 7 positions, 1-based (0 = unused), then the Hamming weight.  A
+ * warp tests 32 consecutive patterns per step before it turns to runs. */
+#define ORBG_FLAT_MAX 1024
+#define ORBG_FLAT_POS 7
 
 /* What a kernel needs of one code (passed by value or from a device array). */
 struct OrbgDeviceCode {
@@ -64,6 +72,8 @@ struct OrbgDeviceCode {
     OrbgTable cta;               /* runs of kinds 0, 1, 3 */
     const uint32_t *trip;        /* [ntrip]: c0 | a0 << 8 | b0 << 16 (0-based), X3 order */
     uint32_t ntrip;
+    const uint32_t *flat;        /* [2 * nflat] flat-table patterns, 8 bytes each */
+    uint32_t nflat;
     uint32_t max_cap;
     int32_t n;
     int32_t r;
@@ -83,6 +93,9 @@ struct OrbgTables {
     std::vector<OrbgRun> runs_cta;       /* CTA table */
     std::vector<uint32_t> group_floor_cta;
     std::vector<uint32_t> trip;          /* X3 order */
+    std::vector<uint8_t> flat;           /* 8 bytes per pattern */
+    std::vector<uint32_t> reach, reach_cta;
+    uint32_t nflat = 0, flat_group = 0, flat_group_cta = 0;
     uint64_t patterns = 0;  /* query indices covered (last index) */
     int wmax_logistic = 0;  /* deepest logistic weight in the table */
 };

@@ -200,6 +200,29 @@ struct Builder {
     }
 };
 
+/* reach[g]: the largest query index in groups 0..g; and the first group
+ * holding a query beyond `nflat` */
+void reaches(const std::vector<OrbgRun> &runs, uint32_t nflat, std::vector<uint32_t> *out,
+             uint32_t *flat_group)
+{
+    const size_t nr = runs.size();
+    const size_t ng = (nr + ORBG_GROUP - 1) / ORBG_GROUP;
+    out->assign(ng, 0u);
+    uint32_t reach = 0;
+    *flat_group = (uint32_t)ng;
+    for (size_t g = 0; g < ng; g++) {
+        bool beyond = false;
+        for (size_t i = g * ORBG_GROUP; i < std::min(nr, (g + 1) * ORBG_GROUP); i++) {
+            const uint32_t last = runs[i].tstart + runs[i].count - 1u;
+            reach = std::max(reach, last);
+            beyond |= last > nflat;
+        }
+        (*out)[g] = reach;
+        if (beyond && *flat_group == ng)
+            *flat_group = (uint32_t)g;
+    }
+}
+
 void floors(const std::vector<OrbgRun> &runs, std::vector<uint32_t> *out)
 {
     const size_t nr = runs.size();
@@ -267,6 +290,31 @@ int orbg_build_tables(int n, uint64_t cap, OrbgTables *out)
         return -5;
     floors(out->runs, &out->group_floor);
     floors(out->runs_cta, &out->group_floor_cta);
+    /* flat table: the leading patterns of weight <= ORBG_FLAT_POS, at most
+     * ORBG_FLAT_MAX of them, in query order */
+    std::vector<std::vector<int>> first((size_t)std::min<uint64_t>(patterns, ORBG_FLAT_MAX));
+    std::vector<int> v(64);
+    for (const OrbgRun &r : out->runs)
+        for (int j = 0; j < r.count; j++) {
+            const uint64_t t = (uint64_t)r.tstart + (uint64_t)j;
+            if (t <= first.size()) {
+                const int w = orbg_run_pattern(r, j, out->trip.data(), v.data());
+                first[t - 1].assign(v.begin(), v.begin() + w);
+            }
+        }
+    uint32_t nflat = 0;
+    while (nflat < first.size() && first[nflat].size() <= ORBG_FLAT_POS)
+        nflat++;
+    out->nflat = nflat;
+    out->flat.assign((size_t)std::max<uint32_t>(nflat, 1) * 8, 0);
+    for (uint32_t t = 0; t < nflat; t++) {
+        uint8_t *e = &out->flat[(size_t)t * 8];
+        for (size_t i = 0; i < first[t].size(); i++)
+            e[i] = (uint8_t)first[t][i];
+        e[7] = (uint8_t)first[t].size();
+    }
+    reaches(out->runs, nflat, &out->reach, &out->flat_group);
+    reaches(out->runs_cta, nflat, &out->reach_cta, &out->flat_group_cta);
     return 0;
 }
 

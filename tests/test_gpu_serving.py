@@ -75,27 +75,26 @@ def test_each_request_same_alone_and_in_the_mix(orbg, budget_mb, streams):
 
 
 def test_overlapping_batches_and_admission(orbg):
-    """A burst of requests: several batches are in flight at once, and a
-    request that can never fit the pools is refused up front."""
-    cap = 100000
+    """Requests submitted back to back, each heavy enough (CA-Polar at 2.5 dB,
+    about half its blocks run to the 1e6 cap) to keep a batch on the GPU
+    for a while: several batches are in flight at once; and a request that
+    can never fit the pools is refused up front."""
+    cap = 10 ** 6
     codes_w = workloads.config5_codes()
     codes = [orbg.Code(c.H, max_query_cap=cap) for c in codes_w]
     cs = orbg.CodeSet(codes)
     srv = orbg.orbg_server_create(cs.handle, 64 << 20, cap, 4, 2048)
     try:
-        rng = np.random.default_rng(5)
-        ids = []
-        for i in range(40):
-            j = i % 3
-            llr, _ = workloads.awgn_llr(codes_w[j], 1500, 3.5, 1000 + i)
-            orbg.orbg_server_submit(srv, i, j, llr, 1500)
-            ids.append(i)
+        reqs = [workloads.awgn_llr(codes_w[1], 1500, 2.5, 1000 + i)[0] for i in range(12)]
+        for i, llr in enumerate(reqs):  # code 1: CA-Polar
+            orbg.orbg_server_submit(srv, i, 1, llr, llr.shape[0])
         got = set()
-        while len(got) < len(ids):
+        while len(got) < len(reqs):
             got.update(orbg.orbg_server_poll(srv, 64, 100000))
-        for i in ids:
+        for i in range(len(reqs)):
             orbg.orbg_server_fetch(srv, i)
         st = orbg.orbg_server_stats_get(srv)
+        assert st["batches"] == len(reqs)  # max_batch_blocks 2048: one request each
         assert st["max_inflight_batches"] >= 2
         big = np.zeros((1 << 17, 128), np.float32)
         with pytest.raises(orbg.OrbgError) as ei:
