@@ -41,6 +41,8 @@ WORKLOADS = {
             "config2_code", (4.0, 5.0, 6.0, 7.0), (201, 202, 203, 204)),
     "capolar": ("ca-polar(128,94[K=105]) 4x%d blocks at Eb/N0 3,4,5,6 dB, query cap 1e6",
                 "config3_code", (3.0, 4.0, 5.0, 6.0), (301, 302, 303, 304)),
+    "rlc64": ("rlc(64,51) 2x%d blocks at Eb/N0 5 dB (all-zero and random information), "
+              "query cap 1e5", "config1_code", (5.0, 5.0), (101, 102)),
     "mixed": ("mixed rlc(64,51),(128,112),(256,240),(256,232), code uniform per block, "
               "%d blocks at Eb/N0 U[4,7] dB, query cap 1e6, one launch, autotuned",
               None, (), (401,)),
@@ -50,6 +52,7 @@ SEEDS = (201, 202, 203, 204)
 B_PER_POINT = 100_000
 WORKLOAD = WORKLOADS["bch"][0] % B_PER_POINT
 CAP = 1_000_000
+CAPS = {"rlc64": 100_000}
 SMS = 152
 SM_MAX_MHZ = 2070.0
 
@@ -70,6 +73,9 @@ def parse_args(argv=None):
                    help="bch: the headline configuration; capolar: the search-heavy "
                         "CA-Polar configuration (profiling)")
     p.add_argument("--blocks-per-point", type=int, default=B_PER_POINT)
+    p.add_argument("--form", choices=("batched", "plain"), default="batched",
+                   help="batched: orbg_decode_batched (two persistent launches); plain: "
+                        "orbg_decode (one warp per block, one launch)")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the library's default tuning")
     p.add_argument("--shape", default="",
@@ -81,9 +87,12 @@ def parse_args(argv=None):
 
 
 def select_workload(name, b_per_point):
-    global WORKLOAD, POINTS, SEEDS, B_PER_POINT, CODE_FN, WORKLOAD_NAME
+    global WORKLOAD, POINTS, SEEDS, B_PER_POINT, CODE_FN, WORKLOAD_NAME, CAP
     desc, CODE_FN, POINTS, SEEDS = WORKLOADS[name]
     WORKLOAD_NAME = name
+    CAP = CAPS.get(name, 1_000_000)
+    if name == "rlc64" and b_per_point == 100_000:
+        b_per_point = 10_000  # the configuration's 2 x 10,000 blocks
     B_PER_POINT = b_per_point
     WORKLOAD = desc % (b_per_point * 10 if name == "mixed" else b_per_point)
 
@@ -106,14 +115,19 @@ def rank_seeds(rank):
     return tuple(s + 1000 * rank for s in SEEDS)
 
 
-def make_inputs(rank=0):
+def make_inputs(rank=0, with_codewords=False):
     from paper_2202_13951_gb300 import workloads
     code = getattr(workloads, CODE_FN)()
-    ls = []
-    for e, s in zip(POINTS, rank_seeds(rank)):
-        l, _ = workloads.awgn_llr(code, B_PER_POINT, e, s)
+    ls, cs = [], []
+    for i, (e, s) in enumerate(zip(POINTS, rank_seeds(rank))):
+        zero = WORKLOAD_NAME == "rlc64" and i == 0  # config 1: all-zero information half
+        l, c = workloads.awgn_llr(code, B_PER_POINT, e, s, zero_info=zero)
         ls.append(l)
-    return code, np.ascontiguousarray(np.concatenate(ls))
+        cs.append(c)
+    llr = np.ascontiguousarray(np.concatenate(ls))
+    if with_codewords:
+        return code, llr, np.concatenate(cs)
+    return code, llr
 
 
 def max_over_ranks(value, world, device=None):
@@ -361,18 +375,24 @@ class Job:
         import torch
         from paper_2202_13951_gb300 import workloads
         self.orbg = orbg
+        self.form = args.form
         if WORKLOAD_NAME == "mixed":
             B = 10 * B_PER_POINT
-            codes, cid, llr, off, _, _ = workloads.config4_inputs(B=B, seed=SEEDS[0] + 1000 * rank)
+            codes, cid, llr, off, cwt, _ = workloads.config4_inputs(B=B,
+                                                                     seed=SEEDS[0] + 1000 * rank)
             self.codes = codes
             self.cid_np, self.off_np, self.llr_np = cid, off, llr
+            self.sent = cwt
         else:
-            code, llr = make_inputs(rank)
+            code, llr, cwt = make_inputs(rank, with_codewords=True)
             self.codes = [code]
             B = llr.shape[0]
             self.cid_np = np.zeros(B, np.int32)
             self.off_np = None
             self.llr_np = llr
+            self.sent = cwt.reshape(-1)
+        if self.form == "plain" and len(self.codes) != 1:
+            raise SystemExit("--form plain needs a single-code workload")
         self.B = B
         self.n_of_block = np.array([c.n for c in self.codes], np.int64)[self.cid_np]
         self.objs = [orbg.Code(c.H, max_query_cap=CAP) for c in self.codes]
@@ -390,8 +410,20 @@ class Job:
         self.stream = torch.cuda.current_stream(dev)
 
     def step(self):
+        if self.form == "plain":
+            self.orbg.orbg_decode(self.objs[0].handle, self.llr, self.B, CAP, self.cw, self.q,
+                                  self.ab, self.stream)
+            return
         self.orbg.orbg_decode_batched(self.cs.handle, self.cid, self.off, self.llr, self.B, CAP,
                                       self.cw, self.off, self.q, self.ab, self.stream)
+
+    def bler(self):
+        """Fraction of blocks whose decoding differs from the sent codeword."""
+        got = self.cw.cpu().numpy()
+        diff = got != self.sent
+        starts = (np.concatenate([[0], np.cumsum(self.n_of_block)[:-1]])
+                  if self.off_np is None else self.off_np)
+        return float(np.logical_or.reduceat(diff, starts).mean())
 
     def autotune(self):
         return self.orbg.orbg_codeset_autotune(self.cs.handle, self.cid, self.off, self.llr,
@@ -436,7 +468,7 @@ def bench_ours(args, rank, world, local):
         f = [int(x) for x in args.shape.split(",")]
         orbg.orbg_codeset_set_tuning(job.cs.handle, orbg.OrbgTuning(*f))
         tuned = "given (--shape)"
-    elif not args.no_autotune:
+    elif not args.no_autotune and args.form == "batched":
         job.autotune()  # untimed: scheduling knobs only, results do not change
         tuned = "autotuned on this workload before warm-up"
 
@@ -499,7 +531,8 @@ def bench_ours(args, rank, world, local):
         "data": "synthetic BPSK/AWGN, seeded (numpy PCG64); each rank its own seeds",
         "config": {"workload": WORKLOAD, "blocks_per_step": B, "query_cap": CAP,
                    "input_mb": round(job.llr_np.nbytes / 1e6, 1),
-                   "form": "batched persistent launch (orbg_decode_batched)",
+                   "form": ("plain single launch (orbg_decode)" if args.form == "plain" else
+                            "batched persistent launch (orbg_decode_batched)"),
                    "l2": ("inputs %.0f MB %s 129 MB L2, no flush"
                           % (job.llr_np.nbytes / 1e6,
                              ">" if job.llr_np.nbytes > 129e6 else "<=")),
@@ -512,11 +545,13 @@ def bench_ours(args, rank, world, local):
                        "what": "one %d-block batch, launch to completion" % B},
         "abandon_rate": float(abh.mean()),
         "mean_queries": float(qh.mean()),
-        "gpu_launches": 2 * args.steps,
+        "bler": job.bler(),
+        "gpu_launches": (1 if args.form == "plain" else 2) * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "Tops/s", "frac": (achieved / peak) if peak else None,
                      "traffic": None,
-                     "what": ("orbg_batched_kernel + orbg_heavy_kernel (one step); algorithmic "
+                     "what": ("the step's kernels (batched: orbg_batched_kernel + "
+                              "orbg_heavy_kernel; plain: orbg_plain_kernel); algorithmic "
                               "32-bit integer ops per launch = sum_t W32 (w_t + 1) + "
                               "B n ceil(log2 n) = %d; peak = measured LOP3 lanes/clk/SM (%s) "
                               "x 152 SMs x 2070 MHz" % (alg_ops, lanes))},
@@ -559,8 +594,11 @@ def bench_e2e(orbg, job, args, world, dev):
         in_meta = B * (4 + 8 + 8)
 
     def step():
-        orbg.orbg_decode_batched(job.cs.handle, cid, off, pin_llr, B, CAP, h_cw, off, h_q,
-                                 h_ab, job.stream)
+        if job.form == "plain":
+            orbg.orbg_decode(job.objs[0].handle, pin_llr, B, CAP, h_cw, h_q, h_ab, job.stream)
+        else:
+            orbg.orbg_decode_batched(job.cs.handle, cid, off, pin_llr, B, CAP, h_cw, off, h_q,
+                                     h_ab, job.stream)
 
     for _ in range(2):
         step()
@@ -576,35 +614,41 @@ def bench_e2e(orbg, job, args, world, dev):
             "h2d_bytes_per_step": int(job.llr_np.nbytes + in_meta),
             "d2h_bytes_per_step": int(n_total + B * 4 + B),
             "steps": steps,
-            "what": "orbg_decode_batched on pinned host buffers: H2D, kernels, D2H, sync"}
+            "what": "the same call on pinned host buffers: H2D, kernels, D2H, sync"}
 
 
-def cpu_baseline(job):
-    """The oracle as it stands, one process, on a bounded sample: the whole
-    workload for the 400,000-block configurations (~4 s), a 40,000-block
-    stratified sample for the mixed one."""
+def cpu_baseline(job, budget_s=15.0):
+    """The oracle as it stands, one process, on a bounded sample of the same
+    workload: blocks taken in a stratified order (every stride-th block,
+    then the next residue, ...) in chunks, until about budget_s seconds of
+    CPU work; the whole workload if it finishes sooner."""
     import oracle
     oracle.build_oracle()
+    B = job.B
+    stride = 97
+    order = np.concatenate([np.arange(r, B, stride) for r in range(stride)])
     t_total = 0.0
     nb = 0
     qsum = 0
-    if WORKLOAD_NAME == "mixed":
-        pick = np.arange(0, job.B, max(1, job.B // 40000))
-        groups = {}
-        for b in pick:
-            groups.setdefault(int(job.cid_np[b]), []).append(b)
-        for j, blocks in groups.items():
+    chunk = 1000
+    for c0 in range(0, B, chunk):
+        idx = order[c0:c0 + chunk]
+        for j in np.unique(job.cid_np[idx]):
+            sel = idx[job.cid_np[idx] == j]
             n = job.codes[j].n
-            llr = np.stack([job.llr_np[job.off_np[b]:job.off_np[b] + n] for b in blocks])
+            if job.off_np is None:
+                llr = job.llr_np[sel]
+            else:
+                llr = np.stack([job.llr_np[job.off_np[b]:job.off_np[b] + n] for b in sel])
             dt, qs, k = run_oracle(job.codes[j].H, llr, CAP, 1)
             t_total += dt
             qsum += qs
             nb += k
-        what = "%d blocks, every %d-th of the mixed batch" % (nb, max(1, job.B // 40000))
-    else:
-        dt, qsum, nb = run_oracle(job.codes[0].H, job.llr_np, CAP, 1)
-        t_total = dt
-        what = "the whole %d-block workload" % nb
+        if t_total > budget_s:
+            break
+    what = ("the whole %d-block workload" % nb if nb == B else
+            "%d of the %d blocks (stratified: every %d-th block, residues in turn; ~%.0f s)"
+            % (nb, B, stride, budget_s))
     return {"value": nb / t_total, "unit": "blocks/s", "cores": 1, "kind": "oracle",
             "queries_per_s": qsum / t_total,
             "sample": "%s, one single-threaded process on %s" % (what, cpu_model())}
