@@ -29,12 +29,15 @@ struct orbg_code {
     uint32_t *d_reach = nullptr;
     uint32_t *d_reach_cta = nullptr;
     uint8_t *d_flat = nullptr;
+    uint8_t *d_s3 = nullptr;
+    uint32_t *d_x3off = nullptr;
     OrbgDeviceCode dev;
 };
 
 struct orbg_codeset {
     int ncodes, n_max, w32_max;
     uint32_t ntrip_max;
+    uint32_t x3w_max;
     orbg_tuning tuning;
     std::vector<int> n_of;       /* n of each code, host copy */
     uint32_t cap_min;
@@ -137,6 +140,10 @@ void free_code_device(orbg_code *c)
     if (c->d_reach) cudaFree(c->d_reach);
     if (c->d_reach_cta) cudaFree(c->d_reach_cta);
     if (c->d_flat) cudaFree(c->d_flat);
+    if (c->d_s3) cudaFree(c->d_s3);
+    if (c->d_x3off) cudaFree(c->d_x3off);
+    c->d_s3 = nullptr;
+    c->d_x3off = nullptr;
     c->d_runs_cta = nullptr;
     c->d_floor_cta = nullptr;
     c->d_trip = nullptr;
@@ -159,6 +166,7 @@ int orbg_codeset_view(const orbg_codeset *set, OrbgSetView *out)
     out->n_max = set->n_max;
     out->w32_max = set->w32_max;
     out->ntrip_max = set->ntrip_max;
+    out->x3w_max = set->x3w_max;
     out->cap_min = set->cap_min;
     out->tuning = set->tuning;
     return 0;
@@ -363,6 +371,8 @@ int orbg_load_code(const uint8_t *mat, int kind, int n, int k, uint32_t max_quer
         {(void **)&c->d_reach, tb.reach.data(), tb.reach.size() * 4},
         {(void **)&c->d_reach_cta, tb.reach_cta.data(), tb.reach_cta.size() * 4},
         {(void **)&c->d_flat, tb.flat.data(), tb.flat.size()},
+        {(void **)&c->d_s3, tb.s3_cta.data(), tb.s3_cta.size()},
+        {(void **)&c->d_x3off, tb.x3off.data(), tb.x3off.size() * 4},
     };
     for (const Up &u : ups) {
         const size_t bytes = std::max<size_t>(u.bytes, 4);
@@ -386,6 +396,11 @@ int orbg_load_code(const uint8_t *mat, int kind, int n, int k, uint32_t max_quer
     c->dev.cta.nruns = (uint32_t)tb.runs_cta.size();
     c->dev.cta.ngroups = (uint32_t)tb.group_floor_cta.size();
     c->dev.cta.group_reach = c->d_reach_cta;
+    c->dev.cta.group_s3 = c->d_s3;
+    c->dev.x3off = c->d_x3off;
+    c->dev.s3max = tb.s3max;
+    c->dev.exact16 = r <= 16 ? 1 : 0;
+    c->dev.x3w = tb.x3off[std::min(ORBG_X3_WARP_S3, tb.s3max) + 1];
     c->dev.cta.flat_group = tb.flat_group_cta;
     c->dev.flat = reinterpret_cast<const uint32_t *>(c->d_flat);
     c->dev.nflat = tb.nflat;
@@ -480,6 +495,7 @@ int orbg_codeset_create(const orbg_code *const *codes, int ncodes, orbg_codeset 
     s->w32_max = 1;
     s->cap_min = 0xFFFFFFFFu;
     s->ntrip_max = 0;
+    s->x3w_max = 0;
     s->tuning = kDefaultTuning;
     for (int i = 0; i < ncodes; i++) {
         if (!codes[i]) {
@@ -492,6 +508,7 @@ int orbg_codeset_create(const orbg_code *const *codes, int ncodes, orbg_codeset 
         s->w32_max = std::max(s->w32_max, codes[i]->w32);
         s->cap_min = std::min(s->cap_min, codes[i]->max_cap);
         s->ntrip_max = std::max(s->ntrip_max, codes[i]->dev.ntrip);
+        s->x3w_max = std::max(s->x3w_max, codes[i]->dev.x3w);
     }
     cudaError_t e;
     if ((e = cudaGetDevice(&s->device)) != cudaSuccess ||
@@ -589,7 +606,7 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
     int le = orbg_launch_batched(set->d_codes, set->ncodes, set->n_max, set->w32_max, d_cid,
                                  d_lo, d_llr, B, query_cap, budget, d_cw, d_co, d_q, d_ab,
                                  scratch, t.warps_per_cta, t.ctas_per_sm, t.blocks_per_grab,
-                                 t.heavy_warps, set->ntrip_max, st);
+                                 t.heavy_warps, set->ntrip_max, set->x3w_max, st);
     cudaFreeAsync(scratch, st);
     if (le != 0) {
         sg.finish(false);

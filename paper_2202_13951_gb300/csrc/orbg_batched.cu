@@ -27,13 +27,18 @@ namespace {
 
 constexpr int kCounters = ORBG_BATCHED_COUNTERS;
 
+/* resident phase-1 CTAs per SM the register allocation is sized for */
+#ifndef ORBG_PHASE1_MIN_CTAS
+#define ORBG_PHASE1_MIN_CTAS 3
+#endif
+
 template <int KMAX, int WMAX>
-__global__ void __launch_bounds__(256, 4) orbg_batched_kernel(
+__global__ void __launch_bounds__(256, ORBG_PHASE1_MIN_CTAS) orbg_batched_kernel(
     const OrbgDeviceCode *__restrict__ codes, int ncodes, const int32_t *__restrict__ code_id,
     const int64_t *__restrict__ llr_off, const float *__restrict__ llr, int64_t B, uint32_t cap,
     uint32_t budget, uint8_t *__restrict__ cw, const int64_t *__restrict__ cw_off,
     uint32_t *__restrict__ q, uint8_t *__restrict__ ab, unsigned long long *__restrict__ counters,
-    unsigned long long *__restrict__ heavy, uint32_t bstride, int grab)
+    unsigned long long *__restrict__ heavy, uint32_t bstride, uint32_t x3w_bytes, int grab)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
@@ -44,6 +49,9 @@ __global__ void __launch_bounds__(256, 4) orbg_batched_kernel(
      * copied in asynchronously while the current one is decoded */
     constexpr int kSlot = 32 * KMAX;
     float *ring = reinterpret_cast<float *>(smem + nwarps * bstride) + warp * 2 * kSlot;
+    /* the warp's own triple table (sums <= ORBG_X3_WARP_S3), filled lazily */
+    uint16_t *X3w = reinterpret_cast<uint16_t *>(smem + nwarps * (bstride + 2 * kSlot * 4) +
+                                                 warp * x3w_bytes);
     const int64_t n0 = codes[0].n;
 
     /* the warp's block sequence: `grab` consecutive blocks per atomic */
@@ -97,8 +105,9 @@ __global__ void __launch_bounds__(256, 4) orbg_batched_kernel(
             const int64_t co = cw_off ? cw_off[b] : b * n0;
             const float *l = ring + slot * kSlot;
 #define ORBG_CALL_WARP(KK, WW)                                                                 \
-    decode_block_warp<KK, WW, true>(code, l, cw + co, q + b, ab + b, cap, budget, bsm, lane, \
-                                    heavy, &counters[1], (unsigned long long)b)
+    decode_block_warp<KK, WW, true, true>(code, l, cw + co, q + b, ab + b, cap, budget, bsm,  \
+                                          lane, heavy, &counters[1], (unsigned long long)b,  \
+                                          X3w)
             ORBG_DISPATCH(KMAX, WMAX, ORBG_CALL_WARP);
 #undef ORBG_CALL_WARP
         }
@@ -139,7 +148,8 @@ cudaError_t launch_batched_t(const OrbgDeviceCode *d_codes, int ncodes, int n_ma
                              int64_t B, uint32_t cap, uint32_t budget, uint8_t *cw,
                              const int64_t *cw_off, uint32_t *q, uint8_t *ab,
                              unsigned long long *scratch, int warps_per_cta, int ctas_per_sm,
-                             int grab, int heavy_warps, uint32_t ntrip_max, cudaStream_t st)
+                             int grab, int heavy_warps, uint32_t ntrip_max, uint32_t x3w_max,
+                             cudaStream_t st)
 {
     const int wpc = warps_per_cta > 0 ? (warps_per_cta > 8 ? 8 : warps_per_cta) : 8;
     const int g = grab < 1 ? 1 : grab;
@@ -153,14 +163,15 @@ cudaError_t launch_batched_t(const OrbgDeviceCode *d_codes, int ncodes, int n_ma
         return e;
     /* phase 1: per warp, one block's working set and two LLR slots */
     auto k1 = orbg_batched_kernel<KMAX, WMAX>;
-    size_t smem1 = ((size_t)bstride + 2u * 32u * KMAX * sizeof(float)) * wpc;
+    const uint32_t x3w_bytes = triple_table_bytes(x3w_max);
+    size_t smem1 = ((size_t)bstride + 2u * 32u * KMAX * sizeof(float) + x3w_bytes) * wpc;
     if ((rc = orbg_grid_for((const void *)k1, wpc * 32, smem1, ctas_per_sm, &grid)) != 0)
         return (cudaError_t)rc;
     int64_t units = (B + g - 1) / g;
     int64_t need = (units + wpc - 1) / wpc;
     if (grid > need) grid = (int)(need > 0 ? need : 1);
     k1<<<grid, wpc * 32, smem1, st>>>(d_codes, ncodes, code_id, llr_off, llr, B, cap, budget, cw,
-                                      cw_off, q, ab, counters, heavy, bstride, g);
+                                      cw_off, q, ab, counters, heavy, bstride, x3w_bytes, g);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     if (budget >= cap)
@@ -183,14 +194,14 @@ int orbg_launch_batched(const OrbgDeviceCode *d_codes, int ncodes, int n_max, in
                         int64_t B, uint32_t cap, uint32_t budget, uint8_t *cw,
                         const int64_t *cw_off, uint32_t *q, uint8_t *ab,
                         unsigned long long *scratch, int warps_per_cta, int ctas_per_sm, int grab,
-                        int heavy_warps, uint32_t ntrip_max, void *stream)
+                        int heavy_warps, uint32_t ntrip_max, uint32_t x3w_max, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
 #define ORBG_B(KM, WM)                                                                       \
     return (int)launch_batched_t<KM, WM>(d_codes, ncodes, n_max, w32_max, code_id, llr_off, \
                                          llr, B, cap, budget, cw, cw_off, q, ab, scratch,     \
                                          warps_per_cta, ctas_per_sm, grab, heavy_warps,      \
-                                         ntrip_max, st);
+                                         ntrip_max, x3w_max, st);
 #define ORBG_BW(KM)                          \
     if (w32_max <= 1) { ORBG_B(KM, 1) }      \
     else if (w32_max <= 2) { ORBG_B(KM, 2) } \

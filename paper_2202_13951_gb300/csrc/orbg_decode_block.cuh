@@ -94,11 +94,23 @@ __host__ __device__ __forceinline__ uint32_t block_smem_bytes(int n, int w32)
     return h + h0 + 256u + 256u;
 }
 
-/* Triple table of the CTA search: X3[i] = h0[c0] ^ h0[a0] ^ h0[b0] for
- * triple i of the code's triple list. */
+/* Triple table: X3[i] = low 16 bits of h0[c0] ^ h0[a0] ^ h0[b0] for triple
+ * i of the code's triple list (a match is verified on the whole syndrome
+ * unless n - k <= 16, where 16 bits are the whole syndrome). */
 __host__ __device__ __forceinline__ uint32_t triple_table_bytes(uint32_t ntrip)
 {
-    return (ntrip * 4u + 15u) & ~15u;
+    return (ntrip * 2u + 15u) & ~15u;
+}
+
+/* Fills X3[lo, hi) from the triple list; `stride` threads starting at `t`. */
+__device__ __forceinline__ void build_x3(const OrbgDeviceCode &code, const uint32_t *h0,
+                                         uint16_t *X3, uint32_t lo, uint32_t hi, uint32_t t,
+                                         uint32_t stride)
+{
+    for (uint32_t i = lo + t; i < hi; i += stride) {
+        const uint32_t c = __ldg(code.trip + i);
+        X3[i] = (uint16_t)(h0[c & 0xFFu] ^ h0[(c >> 8) & 0xFFu] ^ h0[(c >> 16) & 0xFFu]);
+    }
 }
 
 template <int W> struct BlockSmem {
@@ -136,35 +148,46 @@ __device__ __forceinline__ float llr_at(const float *__restrict__ llr, int i)
     return __ldg(llr + i);
 }
 
+/* Sort keys are 32 bits: (|L| bits with the low DROP bits dropped) << IB | i,
+ * with IB index bits (32 K <= 2^IB).  The truncation merges reliabilities
+ * that differ only in the dropped bits; inside such a tie the key orders by
+ * index, which is the exact order unless the full bits disagree -- checked
+ * after the sort (sort_block). */
+template <int K> struct KeyBits {
+    static constexpr int IB = K == 1 ? 5 : K == 2 ? 6 : K == 4 ? 7 : 8; /* 32*K <= 2^IB */
+    static constexpr int DROP = IB - 1;                                  /* 31 + IB - DROP = 32 */
+    static constexpr uint32_t IMASK = (1u << IB) - 1u;
+};
+
 /* ------------------------------------------------------- step 1: load */
 
-/* Loads the block, writes y into cw, builds the K keys per lane and returns
- * s0 (identical in every lane).  *nan is warp-uniform. */
+/* Loads the block, writes y into cw, builds the K 32-bit sort keys per lane
+ * and returns s0 (identical in every lane).  *nan is warp-uniform. */
 template <int K, int W, bool LS = false>
 __device__ __forceinline__ typename Syn<W>::T load_block(const OrbgDeviceCode &code,
                                                          const float *__restrict__ llr,
-                                                         uint64_t (&key)[K], uint8_t *cw,
+                                                         uint32_t (&key)[K], uint8_t *cw,
                                                          int lane, bool *nan_out)
 {
     typedef typename Syn<W>::T T;
+    typedef KeyBits<K> KB;
     const int n = code.n;
     T s0 = szero<T>();
     bool nan = false;
 #pragma unroll
     for (int k = 0; k < K; k++) {
         int i = k * 32 + lane;
+        uint32_t bits = 0xFFFFFFFFu; /* padding sorts last */
         if (i < n) {
             float L = llr_at<LS>(llr, i);
             nan |= (L != L);
-            uint32_t bits = __float_as_uint(L) & 0x7FFFFFFFu;
-            key[k] = ((uint64_t)bits << 32) | (uint32_t)i;
+            bits = __float_as_uint(L) & 0x7FFFFFFFu;
             uint8_t y = L > 0.0f ? 1 : 0;
             cw[i] = y;
             if (y)
                 s0 = sx(s0, load_col<W>(code.hcol, i));
-        } else {
-            key[k] = 0xFFFFFFFF00000000ull | (uint32_t)i; /* padding sorts last */
         }
+        key[k] = ((bits >> KB::DROP) << KB::IB) | ((uint32_t)i & KB::IMASK);
     }
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1)
@@ -214,15 +237,7 @@ __device__ __forceinline__ void sort_keys(uint64_t (&key)[K], int lane)
     }
 }
 
-/*
- * Cheaper sort: one 32-bit key per element, (|L| bits truncated) << IB | i,
- * with IB index bits (n <= 2^IB) and the low IB-1 mantissa bits of |L|
- * dropped so the key fits 32 bits.  The truncation merges reliabilities
- * that differ only in those bits; inside such a tie the key orders by
- * index, which is the exact order unless the full bits disagree.  That is
- * checked on every adjacent pair afterwards; any disagreement sends the
- * block to the exact 64-bit sort.
- */
+/* Bitonic sort of 32*K unique 32-bit keys held K per lane. */
 template <int K>
 __device__ __forceinline__ void bitonic32(uint32_t (&key)[K], int lane)
 {
@@ -256,66 +271,56 @@ __device__ __forceinline__ void bitonic32(uint32_t (&key)[K], int lane)
     }
 }
 
-template <int K> struct KeyBits {
-    static constexpr int IB = K == 1 ? 5 : K == 2 ? 6 : K == 4 ? 7 : 8; /* 32*K <= 2^IB */
-    static constexpr int DROP = IB - 1;                                  /* 31 + IB - DROP = 32 */
-    static constexpr uint32_t IMASK = (1u << IB) - 1u;
-};
-
-/* Sort 64-bit keys (bits << 32 | i) through 32-bit keys; returns false if
- * the truncated order may differ from the exact one. On true, key[] holds
- * the exact sorted keys (positions e = lane*K + k). */
+/*
+ * Sort the 32-bit keys, then check every adjacent pair whose truncated
+ * reliabilities are equal against the full bits; if any is out of order,
+ * sort exact 64-bit keys (bits << 32 | i) rebuilt from the LLRs instead.
+ * Afterwards key[k] holds the received index of sorted position lane*K + k.
+ */
 template <int K, bool LS = false>
-__device__ __forceinline__ bool sort_keys_fast(uint64_t (&key)[K], const float *__restrict__ llr,
-                                               int n, int lane)
+__device__ __forceinline__ void sort_block(uint32_t (&key)[K], const float *__restrict__ llr,
+                                           int n, int lane)
 {
     typedef KeyBits<K> KB;
-    uint32_t k32[K];
-#pragma unroll
-    for (int k = 0; k < K; k++) {
-        const uint32_t bits = (uint32_t)(key[k] >> 32);
-        const uint32_t idx = (uint32_t)key[k];
-        k32[k] = ((bits >> KB::DROP) << KB::IB) | (idx & KB::IMASK);
-        /* padding (bits = 0xFFFFFFFF) keeps all-ones above the index */
-    }
-    bitonic32<K>(k32, lane);
-    /* adjacent pairs with equal truncated reliabilities: check exact order */
+    bitonic32<K>(key, lane);
     bool bad = false;
-    const uint32_t next_first = __shfl_down_sync(FULL_MASK, k32[0], 1);
+    const uint32_t next_first = __shfl_down_sync(FULL_MASK, key[0], 1);
 #pragma unroll
     for (int k = 0; k < K; k++) {
         const int e = lane * K + k;
-        const uint32_t nxt = (k + 1 < K) ? k32[k + 1 < K ? k + 1 : k] : next_first;
-        if (e + 1 < n && (k32[k] >> KB::IB) == (nxt >> KB::IB)) {
-            const uint32_t ba = __float_as_uint(llr_at<LS>(llr, (int)(k32[k] & KB::IMASK))) & 0x7FFFFFFFu;
-            const uint32_t bb = __float_as_uint(llr_at<LS>(llr, (int)(nxt & KB::IMASK))) & 0x7FFFFFFFu;
+        const uint32_t nxt = (k + 1 < K) ? key[k + 1 < K ? k + 1 : k] : next_first;
+        if (e + 1 < n && (key[k] >> KB::IB) == (nxt >> KB::IB)) {
+            const uint32_t ba =
+                __float_as_uint(llr_at<LS>(llr, (int)(key[k] & KB::IMASK))) & 0x7FFFFFFFu;
+            const uint32_t bb =
+                __float_as_uint(llr_at<LS>(llr, (int)(nxt & KB::IMASK))) & 0x7FFFFFFFu;
             bad |= ba > bb;
         }
     }
-    if (__any_sync(FULL_MASK, bad))
-        return false;
+    if (__any_sync(FULL_MASK, bad)) {
+        uint64_t k64[K];
 #pragma unroll
-    for (int k = 0; k < K; k++) {
-        const uint32_t idx = k32[k] & KB::IMASK;
-        key[k] = (uint64_t)idx; /* only the index is used after the sort */
+        for (int k = 0; k < K; k++) {
+            const int i = k * 32 + lane;
+            const uint32_t bits =
+                i < n ? (__float_as_uint(llr_at<LS>(llr, i)) & 0x7FFFFFFFu) : 0xFFFFFFFFu;
+            k64[k] = ((uint64_t)bits << 32) | (uint32_t)i;
+        }
+        sort_keys<K>(k64, lane);
+#pragma unroll
+        for (int k = 0; k < K; k++)
+            key[k] = (uint32_t)k64[k];
+        return;
     }
-    return true;
-}
-
-/* Sort with the fast path and the exact fallback (the fast path leaves
- * key[] untouched when it gives up). */
-template <int K, bool LS = false>
-__device__ __forceinline__ void sort_block(uint64_t (&key)[K], const float *__restrict__ llr,
-                                           int n, int lane)
-{
-    if (!sort_keys_fast<K, LS>(key, llr, n, lane))
-        sort_keys<K>(key, lane);
+#pragma unroll
+    for (int k = 0; k < K; k++)
+        key[k] &= KB::IMASK;
 }
 
 /* ------------------------------------------------- step 3: permutation */
 
 template <int K, int W>
-__device__ __forceinline__ void build_perm(const OrbgDeviceCode &code, const uint64_t (&key)[K],
+__device__ __forceinline__ void build_perm(const OrbgDeviceCode &code, const uint32_t (&key)[K],
                                            const BlockSmem<W> &sm, int lane)
 {
     const int n = code.n;
@@ -323,7 +328,7 @@ __device__ __forceinline__ void build_perm(const OrbgDeviceCode &code, const uin
     for (int k = 0; k < K; k++) {
         const int e = lane * K + k;
         if (e < n) {
-            int idx = (int)(uint32_t)key[k];
+            const int idx = (int)key[k];
             sm.pi[e] = (uint8_t)idx;
             const typename Syn<W>::T col = load_col<W>(code.hcol, idx);
             sm.h[e] = col;
@@ -481,15 +486,20 @@ __device__ __forceinline__ uint32_t search_run_warp(const uint4 &v0, const uint4
 }
 
 /* Walk one run of the CTA table: kind 3 tests the X3 range [aux, aux +
- * count) against the prefix syndrome, four queries per step. */
+ * count) against the low 16 bits of the prefix syndrome, four queries per
+ * step.  Entries at or past x3lim are not built: those queries are formed
+ * from the triple list instead (slower, used only near the end of a warp's
+ * own table). */
 template <int W>
 __device__ __forceinline__ uint32_t search_run_cta(const uint4 &v0, const uint4 &v1,
                                                    const typename Syn<W>::T *__restrict__ h,
                                                    const uint32_t *__restrict__ h0,
-                                                   const uint32_t *__restrict__ X3,
+                                                   const uint16_t *__restrict__ X3,
+                                                   uint32_t x3lim,
                                                    const uint32_t *__restrict__ trip,
                                                    const typename Syn<W>::T s0, uint32_t best,
-                                                   uint32_t cap, int n, uint32_t *hit)
+                                                   uint32_t cap, int n, bool exact16,
+                                                   uint32_t *hit)
 {
     const uint32_t tstart = v0.x;
     if (!(tstart < best && tstart <= cap))
@@ -498,31 +508,49 @@ __device__ __forceinline__ uint32_t search_run_cta(const uint4 &v0, const uint4 
     const int kind = run_kind(v0);
     if (kind == ORBG_RUN_TRIPLES) {
         const int len = run_count(v0);
-        const uint32_t *x = X3 + v0.z;
+        const uint32_t x0 = v0.z;
+        const uint16_t p16 = (uint16_t)P0;
+        const bool exact = W == 1 && exact16;
         int j = 0;
-        for (;;) {
-            int cand = -1;
-            for (; j < len; j += 4) {
-                /* slots past the run are masked; their loads stay inside it */
-                const int last = len - 1;
-                const bool m0 = x[j] == P0;
-                const bool m1 = (x[min(j + 1, last)] == P0) && (j + 1 < len);
-                const bool m2 = (x[min(j + 2, last)] == P0) && (j + 2 < len);
-                const bool m3 = (x[min(j + 3, last)] == P0) && (j + 3 < len);
-                if (m0 || m1 || m2 || m3) {
-                    cand = j + (m0 ? 0 : m1 ? 1 : m2 ? 2 : 3);
-                    break;
+        if (x0 + (uint32_t)len <= x3lim) {
+            const uint16_t *x = X3 + x0;
+            for (;;) {
+                int cand = -1;
+                for (; j + 3 < len; j += 4) {
+                    const bool m0 = x[j] == p16, m1 = x[j + 1] == p16;
+                    const bool m2 = x[j + 2] == p16, m3 = x[j + 3] == p16;
+                    if (m0 || m1 || m2 || m3) {
+                        cand = j + (m0 ? 0 : m1 ? 1 : m2 ? 2 : 3);
+                        break;
+                    }
                 }
+                if (cand < 0) {
+                    for (; j < len; j++)
+                        if (x[j] == p16) {
+                            cand = j;
+                            break;
+                        }
+                }
+                if (cand < 0)
+                    return ORBG_NONE;
+                const uint32_t t = x0 + (uint32_t)cand;
+                if (exact || verify_query<W>(v0, v1, h, s0, n, t, trip)) {
+                    *hit = t;
+                    return tstart + (uint32_t)cand;
+                }
+                j = cand + 1;
             }
-            if (cand < 0)
-                return ORBG_NONE;
-            const uint32_t t = v0.z + (uint32_t)cand;
-            if (W == 1 || verify_query<W>(v0, v1, h, s0, n, t, trip)) {
-                *hit = t;
-                return tstart + (uint32_t)cand;
-            }
-            j = cand + 1;
         }
+        for (; j < len; j++) { /* entries not built: form each triple */
+            const uint32_t t = x0 + (uint32_t)j;
+            const uint32_t c = __ldg(trip + t);
+            const uint32_t v = h0[c & 0xFFu] ^ h0[(c >> 8) & 0xFFu] ^ h0[(c >> 16) & 0xFFu];
+            if (v == P0 && (W == 1 || verify_query<W>(v0, v1, h, s0, n, t, trip))) {
+                *hit = t;
+                return tstart + (uint32_t)j;
+            }
+        }
+        return ORBG_NONE;
     }
     if (kind == ORBG_RUN_SINGLE) {
         if (P0 == 0u && (W == 1 || verify_query<W>(v0, v1, h, s0, n, 0u, nullptr))) {
@@ -649,19 +677,19 @@ __device__ __forceinline__ uint32_t group_reaching(const OrbgTable &tb, uint32_t
  * decode_block_cta.  With budget >= cap every block finishes here.  LS:
  * llr points into shared memory (the batched kernel stages it there).
  */
-template <int K, int W, bool LS = false>
+template <int K, int W, bool LS = false, bool TRIP = false>
 __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__restrict__ llr,
                                   uint8_t *__restrict__ cw_out, uint32_t *__restrict__ q_out,
                                   uint8_t *__restrict__ ab_out, uint32_t cap, uint32_t budget,
                                   unsigned char *__restrict__ bsm, int lane,
                                   unsigned long long *heavy, unsigned long long *heavy_count,
-                                  unsigned long long block_index)
+                                  unsigned long long block_index, uint16_t *X3w = nullptr)
 {
     typedef typename Syn<W>::T T;
     const int n = code.n;
-    const OrbgTable &tb = code.warp;
+    const OrbgTable &tb = TRIP ? code.cta : code.warp;
     BlockSmem<W> sm(bsm, n);
-    uint64_t key[K];
+    uint32_t key[K];
     bool nan;
     const T s0 = load_block<K, W, LS>(code, llr, key, sm.cw, lane, &nan);
     uint32_t best = ORBG_NONE, my_t = ORBG_NONE, my_run = 0, my_hit = 0;
@@ -691,21 +719,44 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
         }
         uint32_t stop = ORBG_NONE;
         if (best == ORBG_NONE) {
-            /* then the runs, from the first group past the flat table */
-            uint4 n0, n1;
+            /* then the runs, from the first group past the flat table; the
+             * budget (and, on the CTA table, the warp's own triple table)
+             * only ends the walk while no hit is known */
             const uint32_t g0 = tb.flat_group;
-            load_run(tb, g0 * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
+            int built = 5;         /* triple sums whose X3 entries exist */
+            uint32_t x3lim = 0;    /* X3 entries built */
             for (uint32_t g = g0; g < tb.ngroups; g++) {
                 const uint32_t floor = __ldg(tb.group_floor + g);
-                if (floor >= best || floor > cap || floor > budget) {
+                if (floor >= best || floor > cap || (best == ORBG_NONE && floor > budget)) {
                     stop = floor;
                     break;
                 }
-                const uint4 v0 = n0, v1 = n1;
-                load_run(tb, (g + 1) * ORBG_GROUP + (uint32_t)lane, &n0, &n1); /* prefetch */
+                if (TRIP) {
+                    const int need = (int)__ldg(tb.group_s3 + g);
+                    if (need > built) {
+                        if (best == ORBG_NONE && need > ORBG_X3_WARP_S3) {
+                            stop = floor;
+                            break;
+                        }
+                        const int upto = min(need, ORBG_X3_WARP_S3);
+                        if (upto > built) {
+                            const uint32_t lo = __ldg(code.x3off + built + 1);
+                            x3lim = __ldg(code.x3off + upto + 1);
+                            build_x3(code, sm.h0, X3w, lo, x3lim, (uint32_t)lane, 32u);
+                            __syncwarp();
+                            built = upto;
+                        }
+                    }
+                }
+                uint4 v0, v1;
+                load_run(tb, g * ORBG_GROUP + (uint32_t)lane, &v0, &v1);
                 uint32_t hv = 0;
-                const uint32_t mine =
-                    search_run_warp<W>(v0, v1, sm.h, sm.h0, s0, best, cap, n, &hv);
+                uint32_t mine;
+                if (TRIP)
+                    mine = search_run_cta<W>(v0, v1, sm.h, sm.h0, X3w, x3lim, code.trip, s0,
+                                             best, cap, n, code.exact16 != 0, &hv);
+                else
+                    mine = search_run_warp<W>(v0, v1, sm.h, sm.h0, s0, best, cap, n, &hv);
                 const uint32_t gbest = __reduce_min_sync(FULL_MASK, mine);
                 if (gbest < best) {
                     best = gbest;
@@ -718,31 +769,6 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
             }
         }
         done = stop >= best || stop > cap; /* exhausted tables give stop = NONE */
-        if (!done && best != ORBG_NONE) {
-            /* a hit inside the budget whose class runs past it: finish here */
-            for (uint32_t g = 0; g < tb.ngroups; g++) {
-                const uint32_t floor = __ldg(tb.group_floor + g);
-                if (floor < stop)
-                    continue; /* walked already */
-                if (floor >= best || floor > cap)
-                    break;
-                uint4 v0, v1;
-                load_run(tb, g * ORBG_GROUP + (uint32_t)lane, &v0, &v1);
-                uint32_t hv = 0;
-                const uint32_t mine =
-                    search_run_warp<W>(v0, v1, sm.h, sm.h0, s0, best, cap, n, &hv);
-                const uint32_t gbest = __reduce_min_sync(FULL_MASK, mine);
-                if (gbest < best) {
-                    best = gbest;
-                    if (mine == gbest) {
-                        my_t = mine;
-                        my_run = g * ORBG_GROUP + (uint32_t)lane;
-                        my_hit = hv;
-                    }
-                }
-            }
-            done = true;
-        }
         handover = stop;
     }
     if (!done) {
@@ -791,7 +817,7 @@ template <int K, int W>
 __device__ void decode_block_cta(const OrbgDeviceCode &code, const float *__restrict__ llr,
                                  uint8_t *__restrict__ cw_out, uint32_t *__restrict__ q_out,
                                  uint8_t *__restrict__ ab_out, uint32_t cap,
-                                 unsigned char *__restrict__ bsm, uint32_t *__restrict__ X3,
+                                 unsigned char *__restrict__ bsm, uint16_t *__restrict__ X3,
                                  uint32_t *s_best, typename Syn<W>::T *s_s0, uint32_t from,
                                  int warp, int lane, int nwarps)
 {
@@ -800,7 +826,7 @@ __device__ void decode_block_cta(const OrbgDeviceCode &code, const float *__rest
     const OrbgTable &tb = code.cta;
     BlockSmem<W> sm(bsm, n);
     if (warp == 0) {
-        uint64_t key[K];
+        uint32_t key[K];
         bool nan;
         const T s0 = load_block<K, W>(code, llr, key, sm.cw, lane, &nan);
         if (nan || sz(s0)) {
@@ -818,12 +844,8 @@ __device__ void decode_block_cta(const OrbgDeviceCode &code, const float *__rest
     }
     __syncthreads();
     const uint32_t start = *s_best;
-    if (start == ORBG_NONE) {
-        for (uint32_t i = threadIdx.x; i < code.ntrip; i += blockDim.x) {
-            const uint32_t t = __ldg(code.trip + i);
-            X3[i] = sm.h0[t & 0xFFu] ^ sm.h0[(t >> 8) & 0xFFu] ^ sm.h0[(t >> 16) & 0xFFu];
-        }
-    }
+    if (start == ORBG_NONE)
+        build_x3(code, sm.h0, X3, 0u, code.ntrip, threadIdx.x, blockDim.x);
     __syncthreads();
     uint32_t my_t = ORBG_NONE, my_run = 0, my_hit = 0;
     if (start == ORBG_NONE) {
@@ -868,8 +890,9 @@ __device__ void decode_block_cta(const OrbgDeviceCode &code, const float *__rest
                 const uint4 v0 = n0, v1 = n1;
                 load_run(tb, (g + nwarps) * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
                 uint32_t hv = 0;
-                const uint32_t mine = search_run_cta<W>(v0, v1, sm.h, sm.h0, X3, code.trip, s0,
-                                                        best, cap, n, &hv);
+                const uint32_t mine =
+                    search_run_cta<W>(v0, v1, sm.h, sm.h0, X3, code.ntrip, code.trip, s0, best,
+                                      cap, n, code.exact16 != 0, &hv);
                 const uint32_t gbest = __reduce_min_sync(FULL_MASK, mine);
                 if (gbest != ORBG_NONE) {
                     if (mine == gbest) {

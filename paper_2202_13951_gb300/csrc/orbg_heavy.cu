@@ -12,8 +12,13 @@ using namespace orbg_dev;
 
 namespace {
 
+/* resident 512-thread phase-2 CTAs per SM the register allocation is sized for */
+#ifndef ORBG_PHASE2_MIN_CTAS
+#define ORBG_PHASE2_MIN_CTAS 2
+#endif
+
 template <int KMAX, int WMAX>
-__global__ void __launch_bounds__(512, 2) orbg_heavy_kernel(
+__global__ void __launch_bounds__(512, ORBG_PHASE2_MIN_CTAS) orbg_heavy_kernel(
     const OrbgDeviceCode *__restrict__ codes, int ncodes, const int32_t *__restrict__ code_id,
     const int64_t *__restrict__ llr_off, const float *__restrict__ llr, uint32_t cap,
     uint8_t *__restrict__ cw, const int64_t *__restrict__ cw_off, uint32_t *__restrict__ q,
@@ -46,7 +51,7 @@ __global__ void __launch_bounds__(512, 2) orbg_heavy_kernel(
         const int64_t co = cw_off ? cw_off[b] : b * n0;
 #define ORBG_CALL_CTA(KK, WW)                                                               \
     decode_block_cta<KK, WW>(code, llr + lo, cw + co, q + b, ab + b, cap, smem,              \
-                             reinterpret_cast<uint32_t *>(smem + bstride), &s_best,          \
+                             reinterpret_cast<uint16_t *>(smem + bstride), &s_best,          \
                              reinterpret_cast<typename Syn<WW>::T *>(&s_s0), from, warp, lane,  \
                              nwarps)
         ORBG_DISPATCH(KMAX, WMAX, ORBG_CALL_CTA);

@@ -36,7 +36,8 @@
 #define ORBG_GROUP 32          /* runs per warp step: one per lane */
 #define ORBG_RUN_MAX_PRE 20    /* prefix positions stored per run */
 #define ORBG_MAX_LOGISTIC 255  /* deepest logistic weight a table may reach */
-#define ORBG_X3_MAX 16384      /* triple-table entries (64 KiB of shared memory) */
+#define ORBG_X3_MAX 16384      /* triple-table entries (32 KiB of shared memory, 16 bits each) */
+#define ORBG_X3_WARP_S3 44     /* triple sums a phase-1 warp keeps in its own table */
 
 enum { ORBG_RUN_SINGLE = 0, ORBG_RUN_PAIRS = 1, ORBG_RUN_TRIPLES = 3 };
 
@@ -54,6 +55,7 @@ struct OrbgTable {
     const OrbgRun *runs;         /* [nruns] */
     const uint32_t *group_floor; /* [ngroups] */
     const uint32_t *group_reach; /* [ngroups]: largest query index in groups <= g */
+    const uint8_t *group_s3;     /* [ngroups]: largest triple sum any run in groups <= g reads */
     uint32_t nruns;
     uint32_t ngroups;
     uint32_t flat_group;         /* first group holding a query beyond the flat table */
@@ -71,7 +73,11 @@ struct OrbgDeviceCode {
     OrbgTable warp;              /* runs of kinds 0, 1 */
     OrbgTable cta;               /* runs of kinds 0, 1, 3 */
     const uint32_t *trip;        /* [ntrip]: c0 | a0 << 8 | b0 << 16 (0-based), X3 order */
+    const uint32_t *x3off;       /* [s3max + 2]: first X3 index of each triple sum */
     uint32_t ntrip;
+    int32_t s3max;               /* largest triple sum in X3 */
+    uint32_t x3w;                /* X3 entries of sums <= ORBG_X3_WARP_S3 (a warp's own table) */
+    int32_t exact16;             /* n - k <= 16: 16-bit X3 entries are whole syndromes */
     const uint32_t *flat;        /* [2 * nflat] flat-table patterns, 8 bytes each */
     uint32_t nflat;
     uint32_t max_cap;
@@ -95,6 +101,9 @@ struct OrbgTables {
     std::vector<uint32_t> trip;          /* X3 order */
     std::vector<uint8_t> flat;           /* 8 bytes per pattern */
     std::vector<uint32_t> reach, reach_cta;
+    std::vector<uint8_t> s3_cta;         /* group_s3 of the CTA table */
+    std::vector<uint32_t> x3off;
+    int s3max = 0;
     uint32_t nflat = 0, flat_group = 0, flat_group_cta = 0;
     uint64_t patterns = 0;  /* query indices covered (last index) */
     int wmax_logistic = 0;  /* deepest logistic weight in the table */
@@ -118,7 +127,7 @@ int orbg_launch_batched(const OrbgDeviceCode *d_codes, int ncodes, int n_max,
                         const int64_t *cw_off, uint32_t *q, uint8_t *ab,
                         unsigned long long *scratch, int warps_per_cta,
                         int ctas_per_sm, int grab, int heavy_warps,
-                        uint32_t ntrip_max, void *stream);
+                        uint32_t ntrip_max, uint32_t x3w_max, void *stream);
 /* device scratch the batched form needs for B blocks: counters (queue head,
  * open-block count, phase-2 cursor) and the list of open blocks */
 #define ORBG_BATCHED_COUNTERS 8
@@ -136,6 +145,7 @@ struct OrbgSetView {
     const OrbgDeviceCode *d_codes;
     int ncodes, n_max, w32_max;
     uint32_t ntrip_max;
+    uint32_t x3w_max;
     uint32_t cap_min;
     orbg_tuning tuning;
 };

@@ -103,7 +103,7 @@ extern "C" int orbg_decode_batched_noalloc(const orbg_codeset *set, const int32_
     e = orbg_launch_batched(v.d_codes, v.ncodes, v.n_max, v.w32_max, code_id, llr_offset, llr, B,
                             query_cap, budget, codeword, cw_offset, queries, abandoned, scratch,
                             v.tuning.warps_per_cta, v.tuning.ctas_per_sm,
-                            v.tuning.blocks_per_grab, v.tuning.heavy_warps, v.ntrip_max,
+                            v.tuning.blocks_per_grab, v.tuning.heavy_warps, v.ntrip_max, v.x3w_max,
                             cuda_stream);
     return e != 0 ? orbg_note_cuda_error(e) : ORBG_OK;
 }

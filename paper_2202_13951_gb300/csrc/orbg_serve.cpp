@@ -313,7 +313,8 @@ bool dispatch_one(orbg_server *s)
             reinterpret_cast<uint32_t *>(d + bt.L.q), d + bt.L.ab,
             reinterpret_cast<unsigned long long *>(d + bt.L.scratch),
             s->view.tuning.warps_per_cta, s->view.tuning.ctas_per_sm,
-            s->view.tuning.blocks_per_grab, s->view.tuning.heavy_warps, s->view.ntrip_max, st);
+            s->view.tuning.blocks_per_grab, s->view.tuning.heavy_warps, s->view.ntrip_max,
+            s->view.x3w_max, st);
     if (e == cudaSuccess && le != 0)
         e = (cudaError_t)le;
     if (e == cudaSuccess)

@@ -274,6 +274,9 @@ int orbg_build_tables(int n, uint64_t cap, OrbgTables *out)
                                     ((uint32_t)(S3 - c - a - 1) << 16));
         s3max = S3;
     }
+    out->s3max = s3max;
+    out->x3off.assign(x3off.begin(), x3off.begin() + (s3max + 2));
+    out->x3off[s3max + 1] = (uint32_t)out->trip.size();
     /* CTA table */
     Builder bc;
     bc.n = n;
@@ -315,6 +318,27 @@ int orbg_build_tables(int n, uint64_t cap, OrbgTables *out)
     }
     reaches(out->runs, nflat, &out->reach, &out->flat_group);
     reaches(out->runs_cta, nflat, &out->reach_cta, &out->flat_group_cta);
+    /* largest triple sum read by the runs of groups <= g: an X3 index falls
+     * in the sum whose range holds it */
+    {
+        const size_t nr = out->runs_cta.size();
+        const size_t ng = (nr + ORBG_GROUP - 1) / ORBG_GROUP;
+        out->s3_cta.assign(ng, 0);
+        int s3 = 0;
+        for (size_t g = 0; g < ng; g++) {
+            for (size_t i = g * ORBG_GROUP; i < std::min(nr, (g + 1) * ORBG_GROUP); i++) {
+                const OrbgRun &r = out->runs_cta[i];
+                if (r.kind != ORBG_RUN_TRIPLES)
+                    continue;
+                const uint32_t last = r.aux + r.count - 1u;
+                int S = 6;
+                while (S < s3max && out->x3off[S + 1] <= last)
+                    S++;
+                s3 = std::max(s3, S);
+            }
+            out->s3_cta[g] = (uint8_t)s3;
+        }
+    }
     return 0;
 }
 
