@@ -225,8 +225,11 @@ int64_t orbg_query_order(int n, uint32_t count, int table, int32_t *out)
         for (uint64_t t = 0; t < total; t++) {
             const uint8_t *e = &tb.flat[t * 8];
             int32_t *row = out + t * stride;
-            row[0] = e[7];
-            for (int i = 0; i < e[7]; i++)
+            int w = 0;
+            while (w < ORBG_FLAT_POS && e[w] != 0)
+                w++;
+            row[0] = w;
+            for (int i = 0; i < w; i++)
                 row[1 + i] = e[i];
         }
         return (int64_t)total;

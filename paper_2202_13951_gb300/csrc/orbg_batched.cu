@@ -128,7 +128,9 @@ int orbg_grid_for(const void *kern, int threads, size_t smem, int ctas_per_sm, i
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return (int)e;
-    if (smem > 48 * 1024) {
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return (int)e;
+    if (smem + fa.sharedSizeBytes > 48 * 1024) { /* static + dynamic past 48 KB: opt in */
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return (int)e;
     }

@@ -343,6 +343,89 @@ __device__ __forceinline__ void build_perm(const OrbgDeviceCode &code, const uin
     }
 }
 
+/* ------------------------------------- step 2': the leading ranks only */
+
+/*
+ * Most blocks finish inside the flat table, whose patterns flip only the
+ * ORBG_FLAT_RANKS least reliable positions.  For those the full sort is
+ * replaced by extracting the smallest keys one at a time (a warp minimum
+ * per rank) until the ranks a flat step needs are known; the full sort runs
+ * only when the walk leaves the flat table.  Each lane first sorts its own
+ * K keys, so its smallest is key[0].
+ */
+template <int K>
+__device__ __forceinline__ void sort_lane(uint32_t (&key)[K])
+{
+#pragma unroll
+    for (int i = 0; i < K; i++)
+#pragma unroll
+        for (int j = 0; j + 1 < K - i; j++) {
+            const uint32_t lo = min(key[j], key[j + 1]), hi = max(key[j], key[j + 1]);
+            key[j] = lo;
+            key[j + 1] = hi;
+        }
+}
+
+/* Extracts ranks have .. upto-1 (upto <= 32): lane r keeps rank r's key in
+ * *mine.  Returns true if two consecutive ranks (this call's or the last
+ * earlier one, in *prev) have equal truncated reliabilities: then the
+ * truncated order may differ from the exact one and the caller sorts
+ * exactly instead. */
+template <int K>
+__device__ __forceinline__ bool extract_ranks(uint32_t (&key)[K], int have, int upto,
+                                              uint32_t *prev, uint32_t *mine, int lane)
+{
+    typedef KeyBits<K> KB;
+    bool tie = false;
+    uint32_t pv = *prev, mn = *mine;
+    for (int r = have; r < upto; r++) {
+        const uint32_t g = __reduce_min_sync(FULL_MASK, key[0]);
+        tie |= (g >> KB::IB) == (pv >> KB::IB);
+        if (key[0] == g) {
+#pragma unroll
+            for (int k = 0; k + 1 < K; k++)
+                key[k] = key[k + 1];
+            key[K - 1] = 0xFFFFFFFFu;
+        }
+        if (lane == r)
+            mn = g;
+        pv = g;
+    }
+    *prev = pv;
+    *mine = mn;
+    return tie;
+}
+
+/* Permuted columns of ranks lo .. hi-1 from the lanes holding them. */
+template <int K, int W>
+__device__ __forceinline__ void perm_ranks(const OrbgDeviceCode &code, uint32_t mine, int lo,
+                                           int hi, const BlockSmem<W> &sm, int lane)
+{
+    if (lane >= lo && lane < hi) {
+        const int idx = (int)(mine & KeyBits<K>::IMASK);
+        sm.pi[lane] = (uint8_t)idx;
+        const typename Syn<W>::T col = load_col<W>(code.hcol, idx);
+        sm.h[lane] = col;
+        if (W > 1)
+            sm.h0[lane] = first_word(col);
+    }
+}
+
+/* The K truncated keys of a lane, in load order (as load_block makes them). */
+template <int K, bool LS>
+__device__ __forceinline__ void make_keys(const float *__restrict__ llr, int n, int lane,
+                                          uint32_t (&key)[K])
+{
+    typedef KeyBits<K> KB;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const int i = k * 32 + lane;
+        const uint32_t bits =
+            i < n ? (__float_as_uint(llr_at<LS>(llr, i)) & 0x7FFFFFFFu) : 0xFFFFFFFFu;
+        key[k] = ((bits >> KB::DROP) << KB::IB) | ((uint32_t)i & KB::IMASK);
+    }
+}
+
 /* -------------------------------------------------- step 4: one run */
 
 /* A run record (orbg_internal.h) as two 16-byte loads:
@@ -603,6 +686,52 @@ __device__ __forceinline__ int flat_pos(const uint2 &e, int i)
     return (int)(((i < 4 ? e.x : e.y) >> (8 * (i & 3))) & 0xFFu); /* 1-based, 0 = none */
 }
 
+/* Flat-table entry t (1-based) or, past the table or the cap, an entry with
+ * no positions whose rank count is 0. */
+__device__ __forceinline__ uint2 flat_entry(const OrbgDeviceCode &code, uint32_t t, uint32_t cap)
+{
+    if (t > code.nflat || t > cap)
+        return make_uint2(0u, 0u);
+    return __ldg(reinterpret_cast<const uint2 *>(code.flat) + (t - 1));
+}
+
+/* The step byte of entry e: ranks needed (bits 0-4), largest weight
+ * (bits 5-7). */
+__device__ __forceinline__ uint32_t flat_step(const uint2 &e) { return e.y >> 24; }
+
+/* Is flat pattern e a hit?  wmax (warp-uniform) bounds its weight.  (An
+ * entry with no positions is tested as the zero pattern: callers pass only
+ * entries of real queries past query 1.) */
+template <int W>
+__device__ __forceinline__ bool flat_test(const typename Syn<W>::T *__restrict__ h,
+                                          const uint32_t *__restrict__ h0,
+                                          const typename Syn<W>::T s0, const uint2 &e, int n,
+                                          int wmax = ORBG_FLAT_POS)
+{
+    typedef typename Syn<W>::T T;
+    uint32_t P0 = first_word(s0);
+#pragma unroll
+    for (int i = 0; i < ORBG_FLAT_POS; i++) {
+        if (i >= wmax)
+            break;
+        const int q = flat_pos(e, i);
+        P0 ^= h0[q ? q - 1 : n];
+    }
+    if (P0 != 0u)
+        return false;
+    if (W > 1) {
+        T P = s0;
+        for (int i = 0; i < ORBG_FLAT_POS; i++) {
+            const int q = flat_pos(e, i);
+            if (q)
+                P = sx(P, h[q - 1]);
+        }
+        if (!sz(P))
+            return false;
+    }
+    return true;
+}
+
 /* Lane's query of flat step `base` (queries base+1 .. base+32): returns its
  * index if it is a hit, else ORBG_NONE. */
 template <int W>
@@ -612,32 +741,11 @@ __device__ __forceinline__ uint32_t flat_query(const OrbgDeviceCode &code,
                                                const typename Syn<W>::T s0, uint32_t base,
                                                uint32_t cap, int lane)
 {
-    typedef typename Syn<W>::T T;
     const uint32_t t = base + (uint32_t)lane + 1u;
     if (t > code.nflat || t > cap)
         return ORBG_NONE;
-    const uint2 e = __ldg(reinterpret_cast<const uint2 *>(code.flat) + (t - 1));
-    const int n = code.n;
-    uint32_t p[ORBG_FLAT_POS];
-#pragma unroll
-    for (int i = 0; i < ORBG_FLAT_POS; i++) {
-        const int q = flat_pos(e, i);
-        p[i] = h0[q ? q - 1 : n];
-    }
-    const uint32_t P0 = first_word(s0) ^ p[0] ^ p[1] ^ p[2] ^ p[3] ^ p[4] ^ p[5] ^ p[6];
-    if (P0 != 0u)
-        return ORBG_NONE;
-    if (W > 1) {
-        T P = s0;
-        for (int i = 0; i < ORBG_FLAT_POS; i++) {
-            const int q = flat_pos(e, i);
-            if (q)
-                P = sx(P, h[q - 1]);
-        }
-        if (!sz(P))
-            return ORBG_NONE;
-    }
-    return t;
+    const uint2 e = flat_entry(code, t, cap);
+    return flat_test<W>(h, h0, s0, e, code.n) ? t : ORBG_NONE;
 }
 
 /* Flips of flat pattern t into the staged codeword. */
@@ -700,13 +808,44 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
     } else if (sz(s0)) {
         best = 1u;            /* query 1, the zero pattern, is a codeword */
     } else {
-        sort_block<K, LS>(key, llr, n, lane);
-        build_perm<K, W>(code, key, sm, lane);
-        __syncwarp();
         /* the flat table: 32 consecutive queries per step, in query order,
-         * so the first step with a hit holds the answer */
+         * so the first step with a hit holds the answer.  Ranks are
+         * extracted as the steps need them (one more than needed, so that a
+         * tie across the boundary is seen); a tie sorts everything exactly. */
+        sort_lane<K>(key);
+        if (lane == 0) {
+            sm.h[n] = szero<T>();
+            if (W > 1)
+                sm.h0[n] = 0u;
+        }
+        bool sorted = false;
+        int have = 0;
+        uint32_t prev = 0xFFFFFFFFu, mine_key = 0xFFFFFFFFu;
         for (uint32_t base = 0; base < code.nflat && base < cap; base += 32u) {
-            const uint32_t mine = flat_query<W>(code, sm.h, sm.h0, s0, base, cap, lane);
+            const uint32_t t = base + (uint32_t)lane + 1u;
+            const uint2 e = flat_entry(code, t, cap);
+            /* every entry of a step carries the step byte; entries past the
+             * table are zero */
+            const uint32_t step = __reduce_max_sync(FULL_MASK, flat_step(e));
+            if (!sorted) {
+                const int upto = min((int)(step & 31u) + 1, n);
+                if (upto > have) {
+                    if (extract_ranks<K>(key, have, upto, &prev, &mine_key, lane)) {
+                        make_keys<K, LS>(llr, n, lane, key);
+                        sort_block<K, LS>(key, llr, n, lane);
+                        build_perm<K, W>(code, key, sm, lane);
+                        sorted = true;
+                    } else {
+                        perm_ranks<K, W>(code, mine_key, have, upto, sm, lane);
+                        have = upto;
+                    }
+                    __syncwarp();
+                }
+            }
+            const uint32_t mine =
+                (e.x | e.y << 8) != 0u && flat_test<W>(sm.h, sm.h0, s0, e, n, (int)(step >> 5))
+                    ? t
+                    : ORBG_NONE;
             const uint32_t gbest = __reduce_min_sync(FULL_MASK, mine);
             if (gbest != ORBG_NONE) {
                 best = gbest;
@@ -716,6 +855,13 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
                 }
                 break;
             }
+        }
+        if (best == ORBG_NONE && !sorted) {
+            /* leaving the flat table: every rank is needed */
+            make_keys<K, LS>(llr, n, lane, key);
+            sort_block<K, LS>(key, llr, n, lane);
+            build_perm<K, W>(code, key, sm, lane);
+            __syncwarp();
         }
         uint32_t stop = ORBG_NONE;
         if (best == ORBG_NONE) {

@@ -62,10 +62,14 @@ struct OrbgTable {
 };
 
 /* The flat table: the first `nflat` patterns of the order, 8 bytes each:
- * up to 7 positions, 1-based (0 = unused), then the Hamming weight.  A
- * warp tests 32 consecutive patterns per step before it turns to runs. */
+ * up to 7 positions, 1-based (0 = unused), then a byte describing the
+ * pattern's step of 32: bits 0-4 the number of sorted ranks the step needs
+ * (the largest position of that step or an earlier one, at most
+ * ORBG_FLAT_RANKS), bits 5-7 the step's largest Hamming weight.  A warp
+ * tests 32 consecutive patterns per step before it turns to runs. */
 #define ORBG_FLAT_MAX 1024
 #define ORBG_FLAT_POS 7
+#define ORBG_FLAT_RANKS 31
 
 /* What a kernel needs of one code (passed by value or from a device array). */
 struct OrbgDeviceCode {

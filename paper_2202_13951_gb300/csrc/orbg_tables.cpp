@@ -308,13 +308,36 @@ int orbg_build_tables(int n, uint64_t cap, OrbgTables *out)
     uint32_t nflat = 0;
     while (nflat < first.size() && first[nflat].size() <= ORBG_FLAT_POS)
         nflat++;
+    /* per step of 32 patterns: the ranks it needs in sorted order (its
+     * largest position, non-decreasing over the steps; the table ends before
+     * the first step needing more than ORBG_FLAT_RANKS) and its largest
+     * Hamming weight */
+    std::vector<uint8_t> need;
+    {
+        int mx = 0;
+        uint32_t keep = 0;
+        for (uint32_t base = 0; base < nflat; base += 32) {
+            const uint32_t end = std::min<uint32_t>(nflat, base + 32);
+            int wmax = 0;
+            for (uint32_t t = base; t < end; t++) {
+                wmax = std::max(wmax, (int)first[t].size());
+                for (int p : first[t])
+                    mx = std::max(mx, p);
+            }
+            if (mx > ORBG_FLAT_RANKS)
+                break;
+            need.push_back((uint8_t)(mx | wmax << 5));
+            keep = end;
+        }
+        nflat = keep;
+    }
     out->nflat = nflat;
     out->flat.assign((size_t)std::max<uint32_t>(nflat, 1) * 8, 0);
     for (uint32_t t = 0; t < nflat; t++) {
         uint8_t *e = &out->flat[(size_t)t * 8];
         for (size_t i = 0; i < first[t].size(); i++)
             e[i] = (uint8_t)first[t][i];
-        e[7] = (uint8_t)first[t].size();
+        e[7] = need[t / 32];
     }
     reaches(out->runs, nflat, &out->reach, &out->flat_group);
     reaches(out->runs_cta, nflat, &out->reach_cta, &out->flat_group_cta);

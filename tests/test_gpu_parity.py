@@ -102,6 +102,46 @@ def test_random_codes_plain_and_batched(orbg, n, k, seed):
     assert_same(gpu_batched(orbg, cs, llr, cap), want)
 
 
+def near_tie_inputs(code, blocks, ebn0, seed):
+    """AWGN blocks in which pairs of reliabilities differ only in the lowest
+    mantissa bits, the more reliable of each pair at the lower index: the
+    decoder's sort keys keep only the high bits of |L| and must fall back to
+    the exact order (Section II: ties in |L| are broken by index, not by
+    value).  Pairs sit among the least reliable positions (read by the first
+    queries) and deeper (read only by long searches)."""
+    llr, _ = workloads.awgn_llr(code, blocks, ebn0, seed)
+    rng = np.random.default_rng(seed + 1)
+    bits = llr.view(np.uint32)
+    for b in range(blocks):
+        order = np.argsort(np.abs(llr[b]), kind="stable")
+        ranks = [(0, 1), (2, 3 + int(rng.integers(0, 3))),
+                 tuple(sorted(rng.choice(np.arange(6, min(40, code.n)), 2, replace=False)))]
+        for r0, r1 in ranks[: 1 + b % 3]:
+            i, j = sorted((int(order[r0]), int(order[r1])))
+            base = bits[b, i] & np.uint32(0xFFFFFF00)
+            sign_i = bits[b, i] & np.uint32(0x80000000)
+            sign_j = bits[b, j] & np.uint32(0x80000000)
+            mag = base & np.uint32(0x7FFFFFFF)
+            bits[b, i] = sign_i | mag | np.uint32(0x05)   # lower index, larger |L|
+            bits[b, j] = sign_j | mag | np.uint32(0x02)   # same high bits
+    return llr
+
+
+@pytest.mark.parametrize("n,k,seed", [(31, 20, 71), (64, 45, 72), (127, 113, 73),
+                                      (200, 180, 74), (255, 239, 75)])
+def test_near_ties_exact_order(orbg, n, k, seed):
+    code = workloads.rlc(n, k, seed)
+    llr = near_tie_inputs(code, 300, 3.5, seed + 10)
+    cap = 20000
+    want = oracle.decode_batch(code.H, llr, cap)[:3]
+    c = orbg.Code(code.H, max_query_cap=cap)
+    assert_same(gpu_plain(orbg, c, llr, cap), want)
+    cs = orbg.CodeSet([c])
+    assert_same(gpu_batched(orbg, cs, llr, cap), want)
+    orbg.orbg_codeset_set_tuning(cs.handle, orbg.OrbgTuning(8, 0, 1, 1, 8))
+    assert_same(gpu_batched(orbg, cs, llr, cap), want)
+
+
 def test_generator_matrix_input_same_result(orbg):
     """Loading G (the library derives its own H) decodes identically."""
     code = workloads.config1_code()
