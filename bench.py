@@ -428,7 +428,7 @@ class Job:
     def autotune(self):
         return self.orbg.orbg_codeset_autotune(self.cs.handle, self.cid, self.off, self.llr,
                                                self.B, CAP, self.cw, self.off, self.q, self.ab,
-                                               2, self.stream)
+                                               3, self.stream)
 
     def alg_ops(self, qh):
         """Algorithmic integer ops of one step: per query sum_t W32 (w_t + 1),

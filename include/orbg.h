@@ -195,11 +195,11 @@ ORBG_API int orbg_decode_batched_noalloc(const orbg_codeset *set,
  *   warps_per_cta   phase 1: warps per CTA, one block per warp (1..16; 0 = 8)
  *   ctas_per_sm     phase 1: resident CTAs per SM (0 = as many as fit)
  *   blocks_per_grab phase 1: blocks a warp takes per work-queue atomic
- *                   (1..1024; 0 = 8)
+ *                   (1..1024; 0 = 4)
  *   warp_budget     phase 1: queries of a block's order a single warp walks
- *                   before handing the block to phase 2 (0 = 4096; a value
+ *                   before handing the block to phase 2 (0 = 16384; a value
  *                   >= the call's query cap disables phase 2)
- *   heavy_warps     phase 2: warps per CTA sharing one block (1..16; 0 = 16)
+ *   heavy_warps     phase 2: warps per CTA sharing one block (1..16; 0 = 8)
  * None of these change any result.
  */
 typedef struct orbg_tuning {
@@ -289,8 +289,9 @@ ORBG_API int orbg_server_replay(orbg_server *srv, int64_t nreq,
  * Autotuner for the batched form: times orbg_decode_batched on the given
  * sample (device buffers, same arguments as orbg_decode_batched) under
  * candidate tunings -- coordinate descent over warp_budget, heavy_warps,
- * blocks_per_grab, warps_per_cta and ctas_per_sm, each candidate the median
- * of `reps` timed runs (CUDA events on cuda_stream, after one warm-up) --
+ * blocks_per_grab, warps_per_cta and ctas_per_sm, repeated (at most three
+ * passes) while a pass changes the tuning, each candidate the median of
+ * `reps` timed runs (CUDA events on cuda_stream, after one warm-up) --
  * keeps the fastest on the set and writes it to *best (may be NULL).
  * Synchronises the stream.  The outputs are overwritten by every trial and
  * hold the sample's (tuning-independent) results at the end.  The

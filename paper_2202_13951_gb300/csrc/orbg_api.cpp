@@ -48,7 +48,7 @@ struct orbg_codeset {
 namespace {
 
 thread_local int g_last_cuda = 0;
-const orbg_tuning kDefaultTuning = {8, 0, 8, 4096u, 16};
+const orbg_tuning kDefaultTuning = {8, 0, 4, 16384u, 8};
 
 int cuda_fail(cudaError_t e)
 {
@@ -677,7 +677,12 @@ int orbg_codeset_autotune(orbg_codeset *set, const int32_t *code_id, const int64
     const int grabs[] = {1, 4, 8, 32};
     const int wpcs[] = {4, 8};
     const int cps[] = {0, 2, 3};
-    for (int knob = 0; knob < 5 && rc == ORBG_OK; knob++) {
+    /* coordinate descent, repeated while a pass still changes something
+     * (the budget and the phase-2 width interact: one pass can stop at a
+     * budget that only suited the starting width) */
+    for (int pass = 0; pass < 3 && rc == ORBG_OK; pass++) {
+      const orbg_tuning before = cur;
+      for (int knob = 0; knob < 5 && rc == ORBG_OK; knob++) {
         const int count = knob == 0 ? 5 : knob == 1 ? 3 : knob == 2 ? 4 : knob == 3 ? 2 : 3;
         for (int i = 0; i < count && rc == ORBG_OK; i++) {
             orbg_tuning t = cur;
@@ -697,6 +702,9 @@ int orbg_codeset_autotune(orbg_codeset *set, const int32_t *code_id, const int64
                 cur_ms = ms;
             }
         }
+      }
+      if (std::memcmp(&before, &cur, sizeof(cur)) == 0)
+          break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
