@@ -568,6 +568,13 @@ __device__ __forceinline__ uint32_t search_run_warp(const uint4 &v0, const uint4
     return j < 0 ? ORBG_NONE : tstart + (uint32_t)j;
 }
 
+/* Nonzero iff one of the two 16-bit halves of t is zero (the lowest zero
+ * half always sets its flag; a borrow can only add flags above it). */
+__device__ __forceinline__ uint32_t zero16(uint32_t t)
+{
+    return (t - 0x00010001u) & ~t & 0x80008000u;
+}
+
 /* Walk one run of the CTA table: kind 3 tests the X3 range [aux, aux +
  * count) against the low 16 bits of the prefix syndrome, four queries per
  * step.  Entries at or past x3lim are not built: those queries are formed
@@ -596,33 +603,27 @@ __device__ __forceinline__ uint32_t search_run_cta(const uint4 &v0, const uint4 
         const bool exact = W == 1 && exact16;
         int j = 0;
         if (x0 + (uint32_t)len <= x3lim) {
-            const uint16_t *x = X3 + x0;
-            for (;;) {
-                int cand = -1;
-                for (; j + 3 < len; j += 4) {
-                    const bool m0 = x[j] == p16, m1 = x[j + 1] == p16;
-                    const bool m2 = x[j + 2] == p16, m3 = x[j + 3] == p16;
-                    if (m0 || m1 || m2 || m3) {
-                        cand = j + (m0 ? 0 : m1 ? 1 : m2 ? 2 : 3);
-                        break;
+            /* aligned 16-byte chunks of eight entries (the table starts on
+             * a 16-byte boundary and its allocation is a whole number of
+             * chunks), each tested at once for an entry equal to p16; a
+             * chunk with one is re-read entry by entry, skipping the
+             * entries outside the run */
+            const uint32_t end = x0 + (uint32_t)len;
+            const uint32_t pp = (uint32_t)p16 * 0x00010001u;
+            const uint4 *X4 = reinterpret_cast<const uint4 *>(X3);
+            for (uint32_t c = x0 & ~7u; c < end; c += 8u) {
+                const uint4 v = X4[c >> 3];
+                if (zero16(v.x ^ pp) | zero16(v.y ^ pp) | zero16(v.z ^ pp) | zero16(v.w ^ pp)) {
+                    for (uint32_t e = max(c, x0); e < min(c + 8u, end); e++) {
+                        if (X3[e] == p16 &&
+                            (exact || verify_query<W>(v0, v1, h, s0, n, e, trip))) {
+                            *hit = e;
+                            return tstart + (e - x0);
+                        }
                     }
                 }
-                if (cand < 0) {
-                    for (; j < len; j++)
-                        if (x[j] == p16) {
-                            cand = j;
-                            break;
-                        }
-                }
-                if (cand < 0)
-                    return ORBG_NONE;
-                const uint32_t t = x0 + (uint32_t)cand;
-                if (exact || verify_query<W>(v0, v1, h, s0, n, t, trip)) {
-                    *hit = t;
-                    return tstart + (uint32_t)cand;
-                }
-                j = cand + 1;
             }
+            return ORBG_NONE;
         }
         for (; j < len; j++) { /* entries not built: form each triple */
             const uint32_t t = x0 + (uint32_t)j;
