@@ -14,10 +14,13 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liborbg.so")
-SOURCES = ["orbg_plain.cu", "orbg_batched.cu", "orbg_heavy.cu", "orbg_noalloc.cu",
+SOURCES = ["orbg_plain.cu", "orbg_batched.cu", "orbg_noalloc.cu",
            "orbg_probe.cu", "orbg_api.cpp", "orbg_serve.cpp",
            "orbg_tables.cpp"]
-HEADERS = ["orbg_internal.h", "orbg_decode_block.cuh"]
+# the batched kernels: one object per (keys per lane, syndrome words) pair
+INST = "orbg_batched_inst.cu"
+INST_KW = [(k, w) for k in (1, 2, 4, 8) for w in (1, 2, 4)]
+HEADERS = ["orbg_internal.h", "orbg_decode_block.cuh", "orbg_batched.cuh", "orbg_heavy.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -32,7 +35,7 @@ def _stale():
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS]
+    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS + [INST]]
     deps.append(os.path.join(ROOT, "include", "orbg.h"))
     deps.append(os.path.abspath(__file__))
     return any(os.path.getmtime(d) > t for d in deps)
@@ -47,13 +50,16 @@ def build(force=False, verbose=False, extra=()):
               os.path.join(ROOT, "include"), "-I", CSRC]
     procs = []
     objs = []
-    for s in SOURCES:
-        obj = os.path.join(OBJDIR, s + ".o")
-        cmd = [cc, "-c", os.path.join(CSRC, s), "-o", obj] + common
+    # the largest instantiations first, so the slowest compiles start at once
+    units = [(INST, "orbg_batched_k%dw%d.o" % (k, w),
+              ["-DORBG_INST_K=%d" % k, "-DORBG_INST_W=%d" % w])
+             for k, w in sorted(INST_KW, key=lambda kw: -kw[0] * kw[1])]
+    units += [(s, s + ".o", []) for s in SOURCES]
+    for s, o, defs in units:
+        obj = os.path.join(OBJDIR, o)
+        cmd = [cc, "-c", os.path.join(CSRC, s), "-o", obj] + common + defs
         if s.endswith(".cu"):
             cmd += ARCH + ["-lineinfo"] + list(extra)
-        else:
-            pass
         procs.append((cmd, subprocess.Popen(cmd, stdout=subprocess.PIPE,
                                             stderr=subprocess.STDOUT)))
         objs.append(obj)

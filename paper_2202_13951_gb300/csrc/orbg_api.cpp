@@ -40,6 +40,7 @@ struct orbg_codeset {
     uint32_t x3w_max;
     orbg_tuning tuning;
     std::vector<int> n_of;       /* n of each code, host copy */
+    OrbgDeviceCode code0;        /* host copy of code 0's descriptor */
     uint32_t cap_min;
     int device;
     OrbgDeviceCode *d_codes = nullptr;
@@ -162,6 +163,7 @@ int orbg_codeset_view(const orbg_codeset *set, OrbgSetView *out)
     if (!set || !out)
         return -1;
     out->d_codes = set->d_codes;
+    out->code0 = set->code0;
     out->ncodes = set->ncodes;
     out->n_max = set->n_max;
     out->w32_max = set->w32_max;
@@ -506,6 +508,8 @@ int orbg_codeset_create(const orbg_code *const *codes, int ncodes, orbg_codeset 
             return ORBG_EINVAL;
         }
         descs[i] = codes[i]->dev;
+        if (i == 0)
+            s->code0 = codes[i]->dev;
         s->n_of.push_back(codes[i]->n);
         s->n_max = std::max(s->n_max, codes[i]->n);
         s->w32_max = std::max(s->w32_max, codes[i]->w32);
@@ -606,10 +610,31 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
     }
     const orbg_tuning &t = set->tuning;
     const uint32_t budget = t.warp_budget < query_cap ? t.warp_budget : query_cap;
-    int le = orbg_launch_batched(set->d_codes, set->ncodes, set->n_max, set->w32_max, d_cid,
-                                 d_lo, d_llr, B, query_cap, budget, d_cw, d_co, d_q, d_ab,
-                                 scratch, t.warps_per_cta, t.ctas_per_sm, t.blocks_per_grab,
-                                 t.heavy_warps, set->ntrip_max, set->x3w_max, st);
+    OrbgBatchedArgs a{};
+    a.d_codes = set->d_codes;
+    a.code0 = &set->code0;
+    a.ncodes = set->ncodes;
+    a.n_max = set->n_max;
+    a.w32_max = set->w32_max;
+    a.code_id = d_cid;
+    a.llr_off = d_lo;
+    a.llr = d_llr;
+    a.B = B;
+    a.cap = query_cap;
+    a.budget = budget;
+    a.cw = d_cw;
+    a.cw_off = d_co;
+    a.q = d_q;
+    a.ab = d_ab;
+    a.scratch = scratch;
+    a.warps_per_cta = t.warps_per_cta;
+    a.ctas_per_sm = t.ctas_per_sm;
+    a.grab = t.blocks_per_grab;
+    a.heavy_warps = t.heavy_warps;
+    a.ntrip_max = set->ntrip_max;
+    a.x3w_max = set->x3w_max;
+    a.stream = st;
+    int le = orbg_launch_batched(a);
     cudaFreeAsync(scratch, st);
     if (le != 0) {
         sg.finish(false);

@@ -1,0 +1,181 @@
+/*
+ * orbg_batched.cuh -- phase 1 of the batched form.  orbg_batched_inst.cu
+ * instantiates it once per (keys per lane, syndrome width) pair; the build
+ * compiles those twelve objects in parallel.
+ *
+ * Phase 1 (orbg_batched_kernel): each warp pulls `grab` blocks at a time
+ * from an atomic work queue and decodes each with decode_block_warp, giving
+ * it a query budget.  Most blocks finish inside the budget (at high SNR
+ * query 1 already decodes).  A block still open when its warp reaches the
+ * budget is appended to a heavy list.
+ * Phase 2 (orbg_heavy_kernel, orbg_heavy.cuh): each CTA pulls heavy blocks
+ * one at a time and decodes each with all its warps (decode_block_cta), so a
+ * block that needs up to 1e6 queries is searched by a whole SM instead of a
+ * single warp.
+ * Both phases compute the exact first hit of the same query order, so the
+ * result equals the plain form's block for block.
+ *
+ * ONE: every block belongs to one code, passed by value as a kernel
+ * parameter (constant bank) and decoded with its exact keys-per-lane K and
+ * syndrome width W; otherwise each block's code comes from the device array
+ * and K, W are dispatched per block up to KMAX, WMAX.
+ */
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cuda_pipeline.h>
+
+#include "orbg_decode_block.cuh"
+#include "orbg_heavy.cuh"
+
+namespace orbg_batched_impl {
+
+using namespace orbg_dev;
+
+constexpr int kCounters = ORBG_BATCHED_COUNTERS;
+
+/* resident phase-1 CTAs per SM the register allocation is sized for */
+#ifndef ORBG_PHASE1_MIN_CTAS
+#define ORBG_PHASE1_MIN_CTAS 3
+#endif
+
+template <int KMAX, int WMAX, bool ONE>
+__global__ void __launch_bounds__(256, ORBG_PHASE1_MIN_CTAS) orbg_batched_kernel(
+    const OrbgDeviceCode *__restrict__ codes, int ncodes, const int32_t *__restrict__ code_id,
+    const int64_t *__restrict__ llr_off, const float *__restrict__ llr, int64_t B, uint32_t cap,
+    uint32_t budget, uint8_t *__restrict__ cw, const int64_t *__restrict__ cw_off,
+    uint32_t *__restrict__ q, uint8_t *__restrict__ ab, unsigned long long *__restrict__ counters,
+    unsigned long long *__restrict__ heavy, uint32_t bstride, uint32_t x3w_bytes, int grab,
+    const __grid_constant__ OrbgDeviceCode code0)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+    unsigned char *bsm = smem + warp * bstride;
+    /* two LLR slots per warp: the block being decoded and the next one,
+     * copied in asynchronously while the current one is decoded */
+    constexpr int kSlot = 32 * KMAX;
+    float *ring = reinterpret_cast<float *>(smem + nwarps * bstride) + warp * 2 * kSlot;
+    /* the warp's own triple table (sums <= ORBG_X3_WARP_S3), filled lazily */
+    uint16_t *X3w = reinterpret_cast<uint16_t *>(smem + nwarps * (bstride + 2 * kSlot * 4) +
+                                                 warp * x3w_bytes);
+    const int64_t n0 = ONE ? code0.n : codes[0].n;
+
+    /* the warp's block sequence: `grab` consecutive blocks per atomic */
+    int64_t pos = 0, end = 0;
+    auto next_block = [&]() -> int64_t {
+        if (pos >= end) {
+            unsigned long long c = 0;
+            if (lane == 0)
+                c = atomicAdd(&counters[0], (unsigned long long)grab);
+            c = __shfl_sync(FULL_MASK, c, 0);
+            pos = (int64_t)c;
+            end = min(pos + (int64_t)grab, B);
+            if (pos >= B)
+                return B;
+        }
+        return pos++;
+    };
+    auto stage = [&](int64_t b, int slot) {
+        if (b < B) {
+            const int cid = ONE ? 0 : code_id ? code_id[b] : 0;
+            if (cid >= 0 && cid < ncodes) {
+                const int n = ONE ? code0.n : codes[cid].n;
+                const int64_t lo = llr_off ? llr_off[b] : b * n0;
+#pragma unroll
+                for (int k = 0; k < KMAX; k++) {
+                    const int i = k * 32 + lane;
+                    if (i < n)
+                        __pipeline_memcpy_async(ring + slot * kSlot + i, llr + lo + i, 4);
+                }
+            }
+        }
+        __pipeline_commit();
+    };
+
+    int64_t b = next_block();
+    int slot = 0;
+    stage(b, slot);
+    int64_t bn = next_block();
+    while (b < B) {
+        stage(bn, slot ^ 1);
+        __pipeline_wait_prior(1); /* block b's copies have landed */
+        __syncwarp();
+        const int cid = ONE ? 0 : code_id ? code_id[b] : 0;
+        const int64_t co = cw_off ? cw_off[b] : b * n0;
+        const float *l = ring + slot * kSlot;
+        if (ONE) {
+            /* one code, read from the kernel's parameters: K and W are exact */
+            decode_block_warp<KMAX, WMAX, true, true>(code0, l, cw + co, q + b, ab + b, cap,
+                                                      budget, bsm, lane, heavy, &counters[1],
+                                                      (unsigned long long)b, X3w);
+        } else if (cid < 0 || cid >= ncodes) {
+            if (lane == 0) {
+                q[b] = 0u;
+                ab[b] = 2;
+            }
+        } else {
+            const OrbgDeviceCode code = codes[cid];
+#define ORBG_CALL_WARP(KK, WW)                                                                 \
+    decode_block_warp<KK, WW, true, true>(code, l, cw + co, q + b, ab + b, cap, budget, bsm,  \
+                                          lane, heavy, &counters[1], (unsigned long long)b,  \
+                                          X3w)
+            ORBG_DISPATCH(KMAX, WMAX, ORBG_CALL_WARP);
+#undef ORBG_CALL_WARP
+        }
+        __syncwarp(); /* slot is free before it is refilled */
+        b = bn;
+        bn = next_block();
+        slot ^= 1;
+    }
+    __pipeline_wait_prior(0);
+}
+
+
+template <int KMAX, int WMAX, bool ONE>
+cudaError_t launch_t(const OrbgBatchedArgs &a)
+{
+    const int wpc = a.warps_per_cta > 0 ? (a.warps_per_cta > 8 ? 8 : a.warps_per_cta) : 8;
+    const int g = a.grab < 1 ? 1 : a.grab;
+    const uint32_t bstride = block_smem_bytes(a.n_max, a.w32_max);
+    unsigned long long *counters = a.scratch;
+    unsigned long long *heavy = a.scratch + kCounters;
+    cudaStream_t st = (cudaStream_t)a.stream;
+    cudaError_t e;
+    int grid = 0, rc;
+    if ((e = cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * kCounters, st)) !=
+        cudaSuccess)
+        return e;
+    /* phase 1: per warp, one block's working set, two LLR slots and its own
+     * triple table */
+    auto k1 = orbg_batched_kernel<KMAX, WMAX, ONE>;
+    const uint32_t x3w_bytes = triple_table_bytes(a.x3w_max);
+    size_t smem1 = ((size_t)bstride + 2u * 32u * KMAX * sizeof(float) + x3w_bytes) * wpc;
+    if ((rc = orbg_grid_for((const void *)k1, wpc * 32, smem1, a.ctas_per_sm, &grid)) != 0)
+        return (cudaError_t)rc;
+    int64_t units = (a.B + g - 1) / g;
+    int64_t need = (units + wpc - 1) / wpc;
+    if (grid > need) grid = (int)(need > 0 ? need : 1);
+    OrbgDeviceCode c0{};
+    if (ONE)
+        c0 = *a.code0;
+    k1<<<grid, wpc * 32, smem1, st>>>(a.d_codes, a.ncodes, a.code_id, a.llr_off, a.llr, a.B,
+                                      a.cap, a.budget, a.cw, a.cw_off, a.q, a.ab, counters,
+                                      heavy, bstride, x3w_bytes, g, c0);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    if (a.budget >= a.cap)
+        return cudaSuccess; /* every block finished in phase 1 */
+    return launch_heavy_t<KMAX, WMAX, ONE>(a, counters, heavy);
+}
+
+/* Phases 1 and 2 for keys-per-lane bound KMAX and syndrome width WMAX. */
+template <int KMAX, int WMAX>
+int launch_kw(const OrbgBatchedArgs &a)
+{
+    return a.code0 ? (int)launch_t<KMAX, WMAX, true>(a) : (int)launch_t<KMAX, WMAX, false>(a);
+}
+
+}  // namespace orbg_batched_impl

@@ -1,0 +1,22 @@
+/*
+ * orbg_batched_inst.cu -- one instantiation of the batched form's kernels
+ * (orbg_batched.cuh) for codes of n <= 32 ORBG_INST_K and ORBG_INST_W
+ * syndrome words.  The build compiles this file once per pair (K in
+ * 1, 2, 4, 8; W in 1, 2, 4), defining the two macros.
+ */
+#include "orbg_batched.cuh"
+
+#ifndef ORBG_INST_K
+#define ORBG_INST_K 1
+#endif
+#ifndef ORBG_INST_W
+#define ORBG_INST_W 1
+#endif
+
+#define ORBG_INST_CAT(kk, ww) orbg_launch_batched_k##kk##w##ww
+#define ORBG_INST_NAME(k, w) ORBG_INST_CAT(k, w)
+
+int ORBG_INST_NAME(ORBG_INST_K, ORBG_INST_W)(const OrbgBatchedArgs &a)
+{
+    return orbg_batched_impl::launch_kw<ORBG_INST_K, ORBG_INST_W>(a);
+}

@@ -124,29 +124,46 @@ int orbg_gf2_nullspace(const uint8_t *M, int rows, int cols,
 int orbg_launch_plain(const OrbgDeviceCode &code, const float *llr, int64_t B,
                       uint32_t cap, uint8_t *cw, uint32_t *q, uint8_t *ab,
                       void *stream);
-int orbg_launch_batched(const OrbgDeviceCode *d_codes, int ncodes, int n_max,
-                        int w32_max, const int32_t *code_id,
-                        const int64_t *llr_off, const float *llr, int64_t B,
-                        uint32_t cap, uint32_t budget, uint8_t *cw,
-                        const int64_t *cw_off, uint32_t *q, uint8_t *ab,
-                        unsigned long long *scratch, int warps_per_cta,
-                        int ctas_per_sm, int grab, int heavy_warps,
-                        uint32_t ntrip_max, uint32_t x3w_max, void *stream);
+/* One batched call (orbg_batched.cu); buffers on the device.  code0: host
+ * copy of code 0's descriptor, or NULL; with code_id == NULL every block is
+ * code 0 and the kernels take it from their parameters. */
+struct OrbgBatchedArgs {
+    const OrbgDeviceCode *d_codes;
+    const OrbgDeviceCode *code0;
+    int ncodes, n_max, w32_max;
+    const int32_t *code_id;
+    const int64_t *llr_off;
+    const float *llr;
+    int64_t B;
+    uint32_t cap, budget;
+    uint8_t *cw;
+    const int64_t *cw_off;
+    uint32_t *q;
+    uint8_t *ab;
+    unsigned long long *scratch;
+    int warps_per_cta, ctas_per_sm, grab, heavy_warps;
+    uint32_t ntrip_max, x3w_max;
+    void *stream;
+};
+int orbg_launch_batched(const OrbgBatchedArgs &args);
+/* orbg_batched_inst.cu, one per (keys per lane K, syndrome words W) */
+#define ORBG_DECLARE_BATCHED(K, W) int orbg_launch_batched_k##K##w##W(const OrbgBatchedArgs &a);
+ORBG_DECLARE_BATCHED(1, 1) ORBG_DECLARE_BATCHED(1, 2) ORBG_DECLARE_BATCHED(1, 4)
+ORBG_DECLARE_BATCHED(2, 1) ORBG_DECLARE_BATCHED(2, 2) ORBG_DECLARE_BATCHED(2, 4)
+ORBG_DECLARE_BATCHED(4, 1) ORBG_DECLARE_BATCHED(4, 2) ORBG_DECLARE_BATCHED(4, 4)
+ORBG_DECLARE_BATCHED(8, 1) ORBG_DECLARE_BATCHED(8, 2) ORBG_DECLARE_BATCHED(8, 4)
+#undef ORBG_DECLARE_BATCHED
 /* device scratch the batched form needs for B blocks: counters (queue head,
  * open-block count, phase-2 cursor) and the list of open blocks */
 #define ORBG_BATCHED_COUNTERS 8
 size_t orbg_batched_scratch_bytes(int64_t B);
-int orbg_launch_heavy(const OrbgDeviceCode *d_codes, int ncodes, int n_max, int w32_max,
-                      const int32_t *code_id, const int64_t *llr_off, const float *llr,
-                      uint32_t cap, uint8_t *cw, const int64_t *cw_off, uint32_t *q, uint8_t *ab,
-                      unsigned long long *counters, const unsigned long long *heavy,
-                      int heavy_warps, uint32_t ntrip_max, void *stream);
 int orbg_grid_for(const void *kern, int threads, size_t smem, int ctas_per_sm, int *grid_out);
 
 /* What a launch needs of a code set (orbg_api.cpp owns the struct). */
 #include "../../include/orbg.h"
 struct OrbgSetView {
     const OrbgDeviceCode *d_codes;
+    OrbgDeviceCode code0;        /* host copy of code 0's descriptor */
     int ncodes, n_max, w32_max;
     uint32_t ntrip_max;
     uint32_t x3w_max;

@@ -100,10 +100,30 @@ extern "C" int orbg_decode_batched_noalloc(const orbg_codeset *set, const int32_
         return orbg_note_cuda_error(e);
     const uint32_t budget = v.tuning.warp_budget < query_cap ? v.tuning.warp_budget : query_cap;
     /* the launcher zeroes the counters on the stream before phase 1 */
-    e = orbg_launch_batched(v.d_codes, v.ncodes, v.n_max, v.w32_max, code_id, llr_offset, llr, B,
-                            query_cap, budget, codeword, cw_offset, queries, abandoned, scratch,
-                            v.tuning.warps_per_cta, v.tuning.ctas_per_sm,
-                            v.tuning.blocks_per_grab, v.tuning.heavy_warps, v.ntrip_max, v.x3w_max,
-                            cuda_stream);
+    OrbgBatchedArgs a{};
+    a.d_codes = v.d_codes;
+    a.code0 = &v.code0;
+    a.ncodes = v.ncodes;
+    a.n_max = v.n_max;
+    a.w32_max = v.w32_max;
+    a.code_id = code_id;
+    a.llr_off = llr_offset;
+    a.llr = llr;
+    a.B = B;
+    a.cap = query_cap;
+    a.budget = budget;
+    a.cw = codeword;
+    a.cw_off = cw_offset;
+    a.q = queries;
+    a.ab = abandoned;
+    a.scratch = scratch;
+    a.warps_per_cta = v.tuning.warps_per_cta;
+    a.ctas_per_sm = v.tuning.ctas_per_sm;
+    a.grab = v.tuning.blocks_per_grab;
+    a.heavy_warps = v.tuning.heavy_warps;
+    a.ntrip_max = v.ntrip_max;
+    a.x3w_max = v.x3w_max;
+    a.stream = cuda_stream;
+    e = orbg_launch_batched(a);
     return e != 0 ? orbg_note_cuda_error(e) : ORBG_OK;
 }

@@ -303,18 +303,33 @@ bool dispatch_one(orbg_server *s)
     const uint32_t budget = s->view.tuning.warp_budget < s->cap ? s->view.tuning.warp_budget
                                                                 : s->cap;
     int le = 0;
-    if (e == cudaSuccess)
-        le = orbg_launch_batched(
-            s->view.d_codes, s->view.ncodes, s->view.n_max, s->view.w32_max,
-            reinterpret_cast<const int32_t *>(d + bt.L.code_id),
-            reinterpret_cast<const int64_t *>(d + bt.L.llr_off),
-            reinterpret_cast<const float *>(d + bt.L.llr), bt.B, s->cap, budget, d + bt.L.cw,
-            reinterpret_cast<const int64_t *>(d + bt.L.cw_off),
-            reinterpret_cast<uint32_t *>(d + bt.L.q), d + bt.L.ab,
-            reinterpret_cast<unsigned long long *>(d + bt.L.scratch),
-            s->view.tuning.warps_per_cta, s->view.tuning.ctas_per_sm,
-            s->view.tuning.blocks_per_grab, s->view.tuning.heavy_warps, s->view.ntrip_max,
-            s->view.x3w_max, st);
+    if (e == cudaSuccess) {
+        OrbgBatchedArgs a{};
+        a.d_codes = s->view.d_codes;
+        a.code0 = nullptr; /* requests mix codes: per-block code ids */
+        a.ncodes = s->view.ncodes;
+        a.n_max = s->view.n_max;
+        a.w32_max = s->view.w32_max;
+        a.code_id = reinterpret_cast<const int32_t *>(d + bt.L.code_id);
+        a.llr_off = reinterpret_cast<const int64_t *>(d + bt.L.llr_off);
+        a.llr = reinterpret_cast<const float *>(d + bt.L.llr);
+        a.B = bt.B;
+        a.cap = s->cap;
+        a.budget = budget;
+        a.cw = d + bt.L.cw;
+        a.cw_off = reinterpret_cast<const int64_t *>(d + bt.L.cw_off);
+        a.q = reinterpret_cast<uint32_t *>(d + bt.L.q);
+        a.ab = d + bt.L.ab;
+        a.scratch = reinterpret_cast<unsigned long long *>(d + bt.L.scratch);
+        a.warps_per_cta = s->view.tuning.warps_per_cta;
+        a.ctas_per_sm = s->view.tuning.ctas_per_sm;
+        a.grab = s->view.tuning.blocks_per_grab;
+        a.heavy_warps = s->view.tuning.heavy_warps;
+        a.ntrip_max = s->view.ntrip_max;
+        a.x3w_max = s->view.x3w_max;
+        a.stream = st;
+        le = orbg_launch_batched(a);
+    }
     if (e == cudaSuccess && le != 0)
         e = (cudaError_t)le;
     if (e == cudaSuccess)
