@@ -605,16 +605,22 @@ __device__ __forceinline__ uint32_t search_run_cta(const uint4 &v0, const uint4 
         if (x0 + (uint32_t)len <= x3lim) {
             /* aligned 16-byte chunks of eight entries (the table starts on
              * a 16-byte boundary and its allocation is a whole number of
-             * chunks), each tested at once for an entry equal to p16; a
-             * chunk with one is re-read entry by entry, skipping the
-             * entries outside the run */
+             * chunks), tested at once for an entry equal to p16; a step
+             * with one is re-read entry by entry, skipping the entries
+             * outside the run */
             const uint32_t end = x0 + (uint32_t)len;
             const uint32_t pp = (uint32_t)p16 * 0x00010001u;
             const uint4 *X4 = reinterpret_cast<const uint4 *>(X3);
-            for (uint32_t c = x0 & ~7u; c < end; c += 8u) {
-                const uint4 v = X4[c >> 3];
-                if (zero16(v.x ^ pp) | zero16(v.y ^ pp) | zero16(v.z ^ pp) | zero16(v.w ^ pp)) {
-                    for (uint32_t e = max(c, x0); e < min(c + 8u, end); e++) {
+            /* two chunks per step; the second is read only inside the run
+             * (past its end the table may end) */
+            for (uint32_t c = x0 & ~7u; c < end; c += 16u) {
+                const uint4 va = X4[c >> 3];
+                const bool two = c + 8u < end;
+                const uint4 vb = two ? X4[(c >> 3) + 1u] : va;
+                if (zero16(va.x ^ pp) | zero16(va.y ^ pp) | zero16(va.z ^ pp) |
+                    zero16(va.w ^ pp) | zero16(vb.x ^ pp) | zero16(vb.y ^ pp) |
+                    zero16(vb.z ^ pp) | zero16(vb.w ^ pp)) {
+                    for (uint32_t e = max(c, x0); e < min(c + 16u, end); e++) {
                         if (X3[e] == p16 &&
                             (exact || verify_query<W>(v0, v1, h, s0, n, e, trip))) {
                             *hit = e;
@@ -1029,13 +1035,17 @@ __device__ void decode_block_cta(const OrbgDeviceCode &code, const float *__rest
         if (!stopped) {
             uint4 n0, n1;
             load_run(tb, g * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
+            uint32_t nfloor = g < tb.ngroups ? __ldg(tb.group_floor + g) : ORBG_NONE;
             for (; g < tb.ngroups; g += (uint32_t)nwarps) {
-                const uint32_t floor = __ldg(tb.group_floor + g);
+                const uint32_t floor = nfloor;
                 const uint32_t best = *((volatile uint32_t *)s_best);
                 if (floor >= best || floor > cap)
                     break;
                 const uint4 v0 = n0, v1 = n1;
-                load_run(tb, (g + nwarps) * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
+                /* the warp's next group, loaded while this one is searched */
+                const uint32_t gn = g + (uint32_t)nwarps;
+                load_run(tb, gn * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
+                nfloor = gn < tb.ngroups ? __ldg(tb.group_floor + gn) : ORBG_NONE;
                 uint32_t hv = 0;
                 const uint32_t mine =
                     search_run_cta<W>(v0, v1, sm.h, sm.h0, X3, code.ntrip, code.trip, s0, best,
