@@ -108,9 +108,10 @@ __global__ void __launch_bounds__(256, ORBG_PHASE1_MIN_CTAS) orbg_batched_kernel
         const float *l = ring + slot * kSlot;
         if (ONE) {
             /* one code, read from the kernel's parameters: K and W are exact */
-            decode_block_warp<KMAX, WMAX, true, true>(code0, l, cw + co, q + b, ab + b, cap,
-                                                      budget, bsm, lane, heavy, &counters[1],
-                                                      (unsigned long long)b, X3w);
+            decode_block_warp<KMAX, WMAX, true, true, (KMAX <= 4)>(code0, l, cw + co, q + b, ab + b,
+                                                            cap, budget, bsm, lane, heavy,
+                                                            &counters[1], (unsigned long long)b,
+                                                            X3w);
         } else if (cid < 0 || cid >= ncodes) {
             if (lane == 0) {
                 q[b] = 0u;
@@ -119,9 +120,9 @@ __global__ void __launch_bounds__(256, ORBG_PHASE1_MIN_CTAS) orbg_batched_kernel
         } else {
             const OrbgDeviceCode code = codes[cid];
 #define ORBG_CALL_WARP(KK, WW)                                                                 \
-    decode_block_warp<KK, WW, true, true>(code, l, cw + co, q + b, ab + b, cap, budget, bsm,  \
-                                          lane, heavy, &counters[1], (unsigned long long)b,  \
-                                          X3w)
+    decode_block_warp<KK, WW, true, true, false>(code, l, cw + co, q + b, ab + b, cap,       \
+                                                 budget, bsm, lane, heavy, &counters[1],    \
+                                                 (unsigned long long)b, X3w)
             ORBG_DISPATCH(KMAX, WMAX, ORBG_CALL_WARP);
 #undef ORBG_CALL_WARP
         }

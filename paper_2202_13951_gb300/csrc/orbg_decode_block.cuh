@@ -792,7 +792,7 @@ __device__ __forceinline__ uint32_t group_reaching(const OrbgTable &tb, uint32_t
  * decode_block_cta.  With budget >= cap every block finishes here.  LS:
  * llr points into shared memory (the batched kernel stages it there).
  */
-template <int K, int W, bool LS = false, bool TRIP = false>
+template <int K, int W, bool LS = false, bool TRIP = false, bool PF = true>
 __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__restrict__ llr,
                                   uint8_t *__restrict__ cw_out, uint32_t *__restrict__ q_out,
                                   uint8_t *__restrict__ ab_out, uint32_t cap, uint32_t budget,
@@ -878,14 +878,40 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
             const uint32_t g0 = tb.flat_group;
             int built = 5;         /* triple sums whose X3 entries exist */
             uint32_t x3lim = 0;    /* X3 entries built */
+            /* PF: group g + 1's runs, floor and triple need are loaded while
+             * g is searched (costs registers: off where they are short) */
+            uint4 n0, n1;
+            uint32_t nfloor = 0;
+            int nneed = 0;
+            if (PF) {
+                load_run(tb, g0 * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
+                nfloor = g0 < tb.ngroups ? __ldg(tb.group_floor + g0) : ORBG_NONE;
+                nneed = TRIP && g0 < tb.ngroups ? (int)__ldg(tb.group_s3 + g0) : 0;
+            }
             for (uint32_t g = g0; g < tb.ngroups; g++) {
-                const uint32_t floor = __ldg(tb.group_floor + g);
+                uint4 v0, v1;
+                uint32_t floor;
+                int need_g = 0;
+                if (PF) {
+                    floor = nfloor;
+                    need_g = nneed;
+                    v0 = n0;
+                    v1 = n1;
+                } else {
+                    floor = __ldg(tb.group_floor + g);
+                }
                 if (floor >= best || floor > cap || (best == ORBG_NONE && floor > budget)) {
                     stop = floor;
                     break;
                 }
+                if (PF && g + 1u < tb.ngroups) {
+                    load_run(tb, (g + 1u) * ORBG_GROUP + (uint32_t)lane, &n0, &n1);
+                    nfloor = __ldg(tb.group_floor + g + 1u);
+                    if (TRIP)
+                        nneed = (int)__ldg(tb.group_s3 + g + 1u);
+                }
                 if (TRIP) {
-                    const int need = (int)__ldg(tb.group_s3 + g);
+                    const int need = PF ? need_g : (int)__ldg(tb.group_s3 + g);
                     if (need > built) {
                         if (best == ORBG_NONE && need > ORBG_X3_WARP_S3) {
                             stop = floor;
@@ -901,8 +927,8 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
                         }
                     }
                 }
-                uint4 v0, v1;
-                load_run(tb, g * ORBG_GROUP + (uint32_t)lane, &v0, &v1);
+                if (!PF)
+                    load_run(tb, g * ORBG_GROUP + (uint32_t)lane, &v0, &v1);
                 uint32_t hv = 0;
                 uint32_t mine;
                 if (TRIP)
