@@ -113,6 +113,9 @@ __device__ __forceinline__ void build_x3(const OrbgDeviceCode &code, const uint3
     }
 }
 
+/* h[r] (and h0[r]) is the column of sorted position r, 0 <= r < n; the
+ * entry before it, h[-1], is the zero column, so a 1-based position p (0 =
+ * none) reads h[p - 1] with no test. */
 template <int W> struct BlockSmem {
     typedef typename Syn<W>::T T;
     T *h;
@@ -121,13 +124,13 @@ template <int W> struct BlockSmem {
     uint8_t *cw;
     __device__ __forceinline__ BlockSmem(unsigned char *base, int n)
     {
-        h = reinterpret_cast<T *>(base);
+        h = reinterpret_cast<T *>(base) + 1;
         unsigned char *p = base + (((uint32_t)(n + 1) * sizeof(T) + 15u) & ~15u);
         if (W > 1) {
-            h0 = reinterpret_cast<uint32_t *>(p);
+            h0 = reinterpret_cast<uint32_t *>(p) + 1;
             p += ((uint32_t)(n + 1) * 4u + 15u) & ~15u;
         } else {
-            h0 = reinterpret_cast<uint32_t *>(base);
+            h0 = reinterpret_cast<uint32_t *>(base) + 1;
         }
         pi = p;
         cw = pi + 256;
@@ -337,9 +340,9 @@ __device__ __forceinline__ void build_perm(const OrbgDeviceCode &code, const uin
         }
     }
     if (lane == 0) {
-        sm.h[n] = szero<typename Syn<W>::T>();
+        sm.h[-1] = szero<typename Syn<W>::T>();
         if (W > 1)
-            sm.h0[n] = 0u;
+            sm.h0[-1] = 0u;
     }
 }
 
@@ -436,20 +439,18 @@ __device__ __forceinline__ int run_npre(const uint4 &v0) { return (int)((v0.y >>
 __device__ __forceinline__ int run_kind(const uint4 &v0) { return (int)(v0.y >> 24); }
 
 /* Syndrome of a run's prefix: s0 (+) the prefix columns, over the W-word
- * syndromes h or over their first words h0.  Slots past npre read entry n,
- * the zero column, so the first eight loads are issued without waiting on
- * npre. */
+ * syndromes h or over their first words h0.  Prefix positions are stored
+ * 1-based with 0 in the unused slots, which read the zero column h[-1]:
+ * the first eight loads need no test of npre. */
 template <typename T>
 __device__ __forceinline__ T prefix_syndrome(const uint4 &v0, const uint4 &v1,
-                                             const T *__restrict__ h, const T s0, int npre,
-                                             int n)
+                                             const T *__restrict__ h, const T s0, int npre)
 {
     T p[8];
 #pragma unroll
     for (int i = 0; i < 8; i++) {
         const uint32_t wd = i < 4 ? v0.w : v1.x;
-        const int pos = i < npre ? (int)((wd >> (8 * (i & 3))) & 0xFFu) : n;
-        p[i] = h[pos];
+        p[i] = h[(int)((wd >> (8 * (i & 3))) & 0xFFu) - 1];
     }
     T P = sx(sx(sx(s0, p[0]), sx(p[1], p[2])), sx(sx(p[3], p[4]), sx(p[5], sx(p[6], p[7]))));
     if (npre > 8) {
@@ -458,7 +459,7 @@ __device__ __forceinline__ T prefix_syndrome(const uint4 &v0, const uint4 &v1,
             if (i >= npre)
                 break;
             const uint32_t wd = (i < 12) ? v1.y : (i < 16) ? v1.z : v1.w;
-            P = sx(P, h[(wd >> (8 * (i & 3))) & 0xFFu]);
+            P = sx(P, h[(int)((wd >> (8 * (i & 3))) & 0xFFu) - 1]);
         }
     }
     return P;
@@ -496,7 +497,7 @@ __device__ __noinline__ bool verify_query(const uint4 &v0, const uint4 &v1,
                                           const uint32_t *trip)
 {
     typedef typename Syn<W>::T T;
-    T P = prefix_syndrome<T>(v0, v1, h, s0, run_npre(v0), n);
+    T P = prefix_syndrome<T>(v0, v1, h, s0, run_npre(v0));
     int pos[3];
     const int k = query_tail(v0, hit, trip, pos);
     for (int i = 0; i < k; i++)
@@ -526,7 +527,7 @@ __device__ __forceinline__ int walk_pairs(const uint4 &v0, const uint4 &v1,
             const int a = a_first + j;
             const int b = S - a;
             /* the second slot is clamped into the table and masked past the run */
-            const int a1 = min(a + 1, n + 1), b1 = max(b - 1, 1);
+            const int a1 = min(a + 1, n), b1 = max(b - 1, 1);
             const bool m0 = (h0[a - 1] ^ h0[b - 1]) == P0;
             const bool m1 = ((h0[a1 - 1] ^ h0[b1 - 1]) == P0) && (j + 1 < len);
             if (m0 || m1) {
@@ -556,7 +557,7 @@ __device__ __forceinline__ uint32_t search_run_warp(const uint4 &v0, const uint4
     const uint32_t tstart = v0.x;
     if (!(tstart < best && tstart <= cap))
         return ORBG_NONE;
-    const uint32_t P0 = prefix_syndrome<uint32_t>(v0, v1, h0, first_word(s0), run_npre(v0), n);
+    const uint32_t P0 = prefix_syndrome<uint32_t>(v0, v1, h0, first_word(s0), run_npre(v0));
     if (run_kind(v0) == ORBG_RUN_SINGLE) {
         if (P0 == 0u && (W == 1 || verify_query<W>(v0, v1, h, s0, n, 0u, nullptr))) {
             *hit = 0u;
@@ -594,7 +595,7 @@ __device__ __forceinline__ uint32_t search_run_cta(const uint4 &v0, const uint4 
     const uint32_t tstart = v0.x;
     if (!(tstart < best && tstart <= cap))
         return ORBG_NONE;
-    const uint32_t P0 = prefix_syndrome<uint32_t>(v0, v1, h0, first_word(s0), run_npre(v0), n);
+    const uint32_t P0 = prefix_syndrome<uint32_t>(v0, v1, h0, first_word(s0), run_npre(v0));
     const int kind = run_kind(v0);
     if (kind == ORBG_RUN_TRIPLES) {
         const int len = run_count(v0);
@@ -677,7 +678,7 @@ __device__ __forceinline__ void apply_flips(const OrbgTable &tb, uint32_t run, u
     const int npre = run_npre(v0);
     for (int i = 0; i < npre; i++) {
         const uint32_t wd = i < 4 ? v0.w : i < 8 ? v1.x : i < 12 ? v1.y : i < 16 ? v1.z : v1.w;
-        cw[pi[(wd >> (8 * (i & 3))) & 0xFFu]] ^= 1;
+        cw[pi[(int)((wd >> (8 * (i & 3))) & 0xFFu) - 1]] ^= 1;
     }
     int pos[3];
     const int k = query_tail(v0, hit, trip, pos);
@@ -722,7 +723,7 @@ __device__ __forceinline__ bool flat_test(const typename Syn<W>::T *__restrict__
         if (i >= wmax)
             break;
         const int q = flat_pos(e, i);
-        P0 ^= h0[q ? q - 1 : n];
+        P0 ^= h0[q - 1];
     }
     if (P0 != 0u)
         return false;
@@ -821,9 +822,9 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
          * tie across the boundary is seen); a tie sorts everything exactly. */
         sort_lane<K>(key);
         if (lane == 0) {
-            sm.h[n] = szero<T>();
+            sm.h[-1] = szero<T>();
             if (W > 1)
-                sm.h0[n] = 0u;
+                sm.h0[-1] = 0u;
         }
         bool sorted = false;
         int have = 0;

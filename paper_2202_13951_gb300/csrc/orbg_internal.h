@@ -48,7 +48,7 @@ struct OrbgRun {
     uint8_t npre;       /* prefix positions used */
     uint8_t kind;       /* ORBG_RUN_* */
     uint32_t aux;       /* kind 1: S | a_lo << 8 (1-based); kind 3: first X3 index */
-    uint8_t pre[ORBG_RUN_MAX_PRE]; /* 0-based prefix positions, ascending */
+    uint8_t pre[ORBG_RUN_MAX_PRE]; /* 1-based prefix positions, ascending; 0 = unused */
 };
 
 struct OrbgTable {

@@ -53,8 +53,10 @@ struct Builder {
         r.tstart = (uint32_t)t;
         r.kind = (uint8_t)kind;
         r.npre = (uint8_t)npre;
-        for (int i = 0; i < npre; i++)
-            r.pre[i] = (uint8_t)(pre[i] - 1);
+        for (int i = 0; i < npre; i++) {
+            overflow |= pre[i] > 255; /* a byte holds positions 1..255 */
+            r.pre[i] = (uint8_t)pre[i]; /* 1-based; 0 marks an unused slot */
+        }
         return r;
     }
 
@@ -371,7 +373,7 @@ int orbg_run_pattern(const OrbgRun &r, int j, const uint32_t *trip, int *v)
 {
     int w = 0;
     for (int i = 0; i < r.npre; i++)
-        v[w++] = r.pre[i] + 1;
+        v[w++] = r.pre[i];
     if (r.kind == ORBG_RUN_PAIRS) {
         const int S = (int)(r.aux & 0xFFu), a = (int)(r.aux >> 8) + j;
         v[w++] = a;

@@ -205,6 +205,39 @@ def test_host_buffers_match_device_buffers(orbg):
     assert_same((cw, q.astype(np.int64), ab), dev)
 
 
+def test_single_code_with_offsets(orbg):
+    """One code, no code ids, but a custom layout: blocks stored out of order
+    with gaps (per-block LLR and codeword offsets).  Same results as the
+    oracle, block by block, in both phases."""
+    code = workloads.rlc(127, 106, 81)
+    llr, _ = workloads.awgn_llr(code, 700, 3.5, 82)
+    B, n = llr.shape
+    rng = np.random.default_rng(83)
+    order = rng.permutation(B)
+    stride = n + 9
+    flat = np.full(B * stride + 5, np.nan, np.float32)   # gaps hold NaN: never read
+    off = np.empty(B, np.int64)
+    for pos, b in enumerate(order):
+        off[b] = 5 + pos * stride
+        flat[off[b]:off[b] + n] = llr[b]
+    cap = 30000
+    want = oracle.decode_batch(code.H, llr, cap)[:3]
+    c = orbg.Code(code.H, max_query_cap=cap)
+    cs = orbg.CodeSet([c])
+    for tuning in (None, (8, 0, 1, 64, 8)):
+        if tuning:
+            orbg.orbg_codeset_set_tuning(cs.handle, orbg.OrbgTuning(*tuning))
+        off_t = torch.from_numpy(off).cuda()
+        cw, q, ab = orbg.decode_batched(cs, torch.from_numpy(flat).cuda(), cap,
+                                        llr_offset=off_t, cw_offset=off_t,
+                                        n_total=flat.shape[0])
+        torch.cuda.synchronize()
+        cw = cw.cpu().numpy()
+        got = (np.stack([cw[o:o + n] for o in off]), q.cpu().numpy().astype(np.int64),
+               ab.cpu().numpy())
+        assert_same(got, want)
+
+
 def test_mixed_codes_one_launch_equals_alone(orbg):
     """Blocks of four codes with different n and n-k in one batched launch
     give what each code's blocks give alone, and what the oracle gives."""
