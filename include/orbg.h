@@ -144,6 +144,12 @@ ORBG_API int orbg_codeset_free(orbg_codeset *set);
  * The call uses 64 + 8 B bytes of stream-ordered device scratch (queue
  * counters and the list of still-open blocks), allocated and freed on
  * cuda_stream.
+ * Host buffers (staged through stream-ordered device copies): a call with
+ * code_id, llr_offset and cw_offset NULL, every buffer on the host and
+ * B >= 131072 is cut into up to eight chunks whose copies in, decodes and
+ * copies out overlap on three library-owned streams (created on the set's
+ * first such call); cuda_stream waits for them and is synchronised before
+ * the call returns, as for any host-buffer call.
  * Results are identical to orbg_decode's block by block.
  * Paper: Algorithm 1 per block; the batching is this library's.
  */

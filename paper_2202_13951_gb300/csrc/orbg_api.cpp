@@ -44,11 +44,17 @@ struct orbg_codeset {
     uint32_t cap_min;
     int device;
     OrbgDeviceCode *d_codes = nullptr;
+    /* streams of the pipelined host-buffer path (copy in, decode, copy
+     * out), created on first use */
+    mutable std::mutex pipe_mu;
+    mutable cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace {
 
 thread_local int g_last_cuda = 0;
+/* smallest chunk of the pipelined host-buffer path (blocks) */
+constexpr int64_t kPipeChunkMin = 65536;
 const orbg_tuning kDefaultTuning = {8, 0, 4, 16384u, 8};
 
 int cuda_fail(cudaError_t e)
@@ -536,9 +542,137 @@ int orbg_codeset_free(orbg_codeset *set)
         return ORBG_OK;
     if (set->d_codes)
         cudaFree(set->d_codes);
+    for (cudaStream_t s : set->pipe)
+        if (s)
+            cudaStreamDestroy(s);
     delete set;
     return ORBG_OK;
 }
+
+namespace {
+
+/*
+ * Host buffers, one code, dense layout, a large batch: the batch is cut
+ * into chunks whose host-to-device copy, decode and device-to-host copy
+ * run on three streams, so chunk i's copy in overlaps chunk i-1's decode
+ * and chunk i-2's copy out.  Each chunk is an ordinary batched call, so
+ * the results equal the unchunked call's.  Synchronises `st`.
+ */
+int decode_batched_pipelined(const orbg_codeset *set, const float *llr, int64_t B,
+                             uint32_t query_cap, uint8_t *codeword, uint32_t *queries,
+                             uint8_t *abandoned, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    {
+        std::lock_guard<std::mutex> lk(set->pipe_mu);
+        for (int i = 0; i < 3 && e == cudaSuccess; i++)
+            if (!set->pipe[i])
+                e = cudaStreamCreateWithFlags(&set->pipe[i], cudaStreamNonBlocking);
+    }
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    cudaStream_t s_in = set->pipe[0], s_dec = set->pipe[1], s_out = set->pipe[2];
+    const int64_t n = set->n_of[0];
+    const int64_t nch = std::min<int64_t>(8, B / kPipeChunkMin);
+    const int64_t per = (B + nch - 1) / nch;
+    float *d_llr = nullptr;
+    uint8_t *d_cw = nullptr, *d_ab = nullptr;
+    uint32_t *d_q = nullptr;
+    unsigned long long *scratch = nullptr;
+    std::vector<cudaEvent_t> ev;
+    auto event = [&](cudaEvent_t *out) -> cudaError_t {
+        cudaError_t r = cudaEventCreateWithFlags(out, cudaEventDisableTiming);
+        if (r == cudaSuccess)
+            ev.push_back(*out);
+        return r;
+    };
+    cudaEvent_t start = nullptr, done = nullptr;
+    if ((e = cudaMallocAsync((void **)&d_llr, (size_t)(B * n) * sizeof(float), st)) ||
+        (e = cudaMallocAsync((void **)&d_cw, (size_t)(B * n), st)) ||
+        (e = cudaMallocAsync((void **)&d_q, (size_t)B * sizeof(uint32_t), st)) ||
+        (e = cudaMallocAsync((void **)&d_ab, (size_t)B, st)) ||
+        (e = cudaMallocAsync((void **)&scratch, orbg_batched_scratch_bytes(per), st)) ||
+        (e = event(&start)) || (e = cudaEventRecord(start, st)) ||
+        (e = cudaStreamWaitEvent(s_in, start, 0)) || (e = cudaStreamWaitEvent(s_dec, start, 0)) ||
+        (e = cudaStreamWaitEvent(s_out, start, 0))) {
+        /* fall through to clean-up */
+    }
+    const orbg_tuning &t = set->tuning;
+    int le = 0;
+    for (int64_t i = 0; i < nch && e == cudaSuccess && le == 0; i++) {
+        const int64_t b0 = i * per, bc = std::min(per, B - b0);
+        if (bc <= 0)
+            break;
+        cudaEvent_t in_done = nullptr, dec_done = nullptr;
+        if ((e = event(&in_done)) || (e = event(&dec_done)))
+            break;
+        if ((e = cudaMemcpyAsync(d_llr + b0 * n, llr + b0 * n, (size_t)(bc * n) * sizeof(float),
+                                 cudaMemcpyHostToDevice, s_in)) ||
+            (e = cudaEventRecord(in_done, s_in)) || (e = cudaStreamWaitEvent(s_dec, in_done, 0)))
+            break;
+        OrbgBatchedArgs a{};
+        a.d_codes = set->d_codes;
+        a.code0 = &set->code0;
+        a.ncodes = set->ncodes;
+        a.n_max = set->n_max;
+        a.w32_max = set->w32_max;
+        a.llr = d_llr + b0 * n;
+        a.B = bc;
+        a.cap = query_cap;
+        a.budget = t.warp_budget < query_cap ? t.warp_budget : query_cap;
+        a.cw = d_cw + b0 * n;
+        a.q = d_q + b0;
+        a.ab = d_ab + b0;
+        a.scratch = scratch;
+        a.warps_per_cta = t.warps_per_cta;
+        a.ctas_per_sm = t.ctas_per_sm;
+        a.grab = t.blocks_per_grab;
+        a.heavy_warps = t.heavy_warps;
+        a.ntrip_max = set->ntrip_max;
+        a.x3w_max = set->x3w_max;
+        a.stream = s_dec;
+        if ((le = orbg_launch_batched(a)) != 0)
+            break;
+        if ((e = cudaEventRecord(dec_done, s_dec)) ||
+            (e = cudaStreamWaitEvent(s_out, dec_done, 0)) ||
+            (e = cudaMemcpyAsync(codeword + b0 * n, d_cw + b0 * n, (size_t)(bc * n),
+                                 cudaMemcpyDeviceToHost, s_out)) ||
+            (e = cudaMemcpyAsync(queries + b0, d_q + b0, (size_t)bc * sizeof(uint32_t),
+                                 cudaMemcpyDeviceToHost, s_out)) ||
+            (e = cudaMemcpyAsync(abandoned + b0, d_ab + b0, (size_t)bc, cudaMemcpyDeviceToHost,
+                                 s_out)))
+            break;
+    }
+    /* join: the caller's stream waits for all three before the buffers go */
+    cudaError_t je = cudaSuccess;
+    for (cudaStream_t sx : {s_in, s_dec, s_out}) {
+        if (je == cudaSuccess && (je = event(&done)) == cudaSuccess &&
+            (je = cudaEventRecord(done, sx)) == cudaSuccess)
+            je = cudaStreamWaitEvent(st, done, 0);
+    }
+    if (d_llr) cudaFreeAsync(d_llr, st);
+    if (d_cw) cudaFreeAsync(d_cw, st);
+    if (d_q) cudaFreeAsync(d_q, st);
+    if (d_ab) cudaFreeAsync(d_ab, st);
+    if (scratch) cudaFreeAsync(scratch, st);
+    cudaError_t se = cudaStreamSynchronize(st);
+    for (cudaEvent_t x : ev)
+        cudaEventDestroy(x);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    if (le != 0)
+        return cuda_fail((cudaError_t)le);
+    if (je != cudaSuccess)
+        return cuda_fail(je);
+    if (se != cudaSuccess)
+        return cuda_fail(se);
+    for (int64_t b = 0; b < B; b++)
+        if (abandoned[b] == ORBG_BLOCK_NAN)
+            return ORBG_ENAN;
+    return ORBG_OK;
+}
+
+}  // namespace
 
 int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
                         const int64_t *llr_offset, const float *llr, int64_t B,
@@ -556,6 +690,10 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
     if ((llr_offset == nullptr) != (cw_offset == nullptr))
         return ORBG_EINVAL;
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (!code_id && !llr_offset && B >= 2 * kPipeChunkMin && !is_device_ptr(llr) &&
+        !is_device_ptr(codeword) && !is_device_ptr(queries) && !is_device_ptr(abandoned))
+        return decode_batched_pipelined(set, llr, B, query_cap, codeword, queries, abandoned,
+                                        st);
     /* element counts: dense layout, or as far as the largest offset reaches */
     size_t n_llr, n_cw;
     if (!llr_offset) {

@@ -238,6 +238,31 @@ def test_single_code_with_offsets(orbg):
         assert_same(got, want)
 
 
+def test_pipelined_host_buffers(orbg):
+    """A large single-code call on host buffers is cut into chunks whose
+    copies and decodes overlap on three streams: every block equals the
+    device-buffer call, and a NaN block in a late chunk is still reported."""
+    code, llr, _ = workloads.config2_inputs(B_per_point=50_000)
+    B, n = llr.shape
+    c = orbg.Code(code.H, max_query_cap=10 ** 6)
+    cs = orbg.CodeSet([c])
+    dev = gpu_batched(orbg, cs, llr, 10 ** 6)
+    cw = np.zeros((B, n), np.uint8)
+    q = np.zeros(B, np.uint32)
+    ab = np.zeros(B, np.uint8)
+    orbg.orbg_decode_batched(cs.handle, None, None, llr, B, 10 ** 6, cw, None, q, ab)
+    assert_same((cw, q.astype(np.int64), ab), dev)
+    llr2 = llr.copy()
+    llr2[B - 5, 3] = np.nan
+    with pytest.raises(orbg.OrbgError) as ei:
+        orbg.orbg_decode_batched(cs.handle, None, None, llr2, B, 10 ** 6, cw, None, q, ab)
+    assert ei.value.status == orbg.ORBG_ENAN
+    assert ab[B - 5] == orbg.ORBG_BLOCK_NAN and q[B - 5] == 0
+    keep = np.arange(B) != B - 5
+    assert_same((cw[keep], q[keep].astype(np.int64), ab[keep]),
+                (dev[0][keep], dev[1][keep], dev[2][keep]))
+
+
 def test_mixed_codes_one_launch_equals_alone(orbg):
     """Blocks of four codes with different n and n-k in one batched launch
     give what each code's blocks give alone, and what the oracle gives."""
