@@ -8,10 +8,12 @@
  *      reliability key (FP32 bits of |L_i|, i) (Sec. III-A); starting
  *      syndrome s0 = H y (Sec. I).  If s0 = 0, y is a codeword and query 1
  *      (the zero pattern) decodes: no sort is needed;
- *   2. warp bitonic sort of the keys in registers -> pi (Sec. III-A; the
- *      paper names bitonic sorting networks as one option, Sec. IV-B);
- *   3. permuted columns hperm[p] = H[:, pi_p] into shared memory, plus a
- *      zero column at p = n;
+ *   2. the reliability order pi (Sec. III-A): for blocks decided inside the
+ *      flat table only its leading ranks, extracted as warp minima; else a
+ *      warp bitonic sort of the keys in registers (the paper names bitonic
+ *      sorting networks as one option, Sec. IV-B);
+ *   3. permuted columns hperm[p] = H[:, pi_p] into shared memory, after a
+ *      zero column read by unused prefix slots;
  *   4. the query order as runs (orbg_internal.h): lane l of a warp step
  *      takes run l of a group of 32, XORs its prefix columns into s0 and
  *      walks the run, testing s0 (+) prefix (+) hperm[a] (+) hperm[b] == 0;
@@ -85,7 +87,8 @@ __device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m)
 
 /* Shared memory of one block in flight: hperm[n+1] full syndromes, then
  * (for W > 1) h0[n+1], the first 32-bit word of each, then pi[256] and the
- * staged codeword cw[256].  Entry n is a zero column. */
+ * staged codeword cw[256].  Entry 0 of hperm and h0 is a zero column
+ * (BlockSmem). */
 __host__ __device__ __forceinline__ uint32_t block_smem_bytes(int n, int w32)
 {
     uint32_t h = (uint32_t)(n + 1) * 4u * (uint32_t)w32;
