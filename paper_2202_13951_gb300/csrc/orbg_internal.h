@@ -120,7 +120,7 @@ int orbg_gf2_rank(const uint8_t *M, int rows, int cols);
 int orbg_gf2_nullspace(const uint8_t *M, int rows, int cols,
                        std::vector<uint8_t> *basis, int *dim);
 
-/* Kernel launchers (orbg_kernels.cu).  Return a cudaError_t value. */
+/* Kernel launchers (orbg_plain.cu, orbg_batched.cu).  Return a cudaError_t value. */
 int orbg_launch_plain(const OrbgDeviceCode &code, const float *llr, int64_t B,
                       uint32_t cap, uint8_t *cw, uint32_t *q, uint8_t *ab,
                       void *stream);
