@@ -145,11 +145,13 @@ ORBG_API int orbg_codeset_free(orbg_codeset *set);
  * counters and the list of still-open blocks), allocated and freed on
  * cuda_stream.
  * Host buffers (staged through stream-ordered device copies): a call with
- * code_id, llr_offset and cw_offset NULL, every buffer on the host and
- * B >= 131072 is cut into up to eight chunks whose copies in, decodes and
- * copies out overlap on three library-owned streams (created on the set's
- * first such call); cuda_stream waits for them and is synchronised before
- * the call returns, as for any host-buffer call.
+ * every buffer on the host, B >= 131072 and a layout that places the
+ * blocks in order without overlap (dense, or offsets that never go back)
+ * is cut into up to eight chunks whose copies in, decodes and copies out
+ * overlap on three library-owned streams (created on the set's first such
+ * call); cuda_stream waits for them and is synchronised before the call
+ * returns, as for any host-buffer call.  With host buffers and offsets,
+ * codeword bytes between blocks are unspecified afterwards.
  * Results are identical to orbg_decode's block by block.
  * Paper: Algorithm 1 per block; the batching is this library's.
  */

@@ -551,16 +551,38 @@ int orbg_codeset_free(orbg_codeset *set)
 
 namespace {
 
+/* Host layout arrays that place block b + 1 at or after the end of block b
+ * (in both buffers), so consecutive blocks occupy one contiguous range.
+ * The dense layout (no offsets) qualifies. */
+bool ordered_layout(const orbg_codeset *set, const int32_t *code_id,
+                    const int64_t *llr_offset, const int64_t *cw_offset, int64_t B)
+{
+    if (!llr_offset)
+        return !code_id;
+    for (int64_t b = 0; b + 1 < B; b++) {
+        const int n = set->n_of[code_id ? code_id[b] : 0];
+        if (llr_offset[b + 1] < llr_offset[b] + n || cw_offset[b + 1] < cw_offset[b] + n)
+            return false;
+    }
+    return true;
+}
+
 /*
- * Host buffers, one code, dense layout, a large batch: the batch is cut
- * into chunks whose host-to-device copy, decode and device-to-host copy
- * run on three streams, so chunk i's copy in overlaps chunk i-1's decode
- * and chunk i-2's copy out.  Each chunk is an ordinary batched call, so
- * the results equal the unchunked call's.  Synchronises `st`.
+ * Host buffers and a large batch: the batch is cut into chunks of
+ * consecutive blocks whose host-to-device copy, decode and device-to-host
+ * copy run on three streams, so chunk i's copy in overlaps chunk i-1's
+ * decode and chunk i-2's copy out.  The layout is dense (one code, no
+ * offsets) or given per block by offsets that place the blocks in order
+ * without overlap (ordered_layout), so each chunk's LLRs and codewords are
+ * one contiguous range.  Each chunk is an ordinary batched call on its
+ * blocks, so the results equal the unchunked call's.  n_llr, n_cw: element
+ * counts of the whole buffers.  Synchronises `st`.
  */
-int decode_batched_pipelined(const orbg_codeset *set, const float *llr, int64_t B,
-                             uint32_t query_cap, uint8_t *codeword, uint32_t *queries,
-                             uint8_t *abandoned, cudaStream_t st)
+int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
+                             const int64_t *llr_offset, const float *llr, int64_t B,
+                             uint32_t query_cap, uint8_t *codeword, const int64_t *cw_offset,
+                             uint32_t *queries, uint8_t *abandoned, size_t n_llr, size_t n_cw,
+                             cudaStream_t st)
 {
     cudaError_t e = cudaSuccess;
     {
@@ -572,12 +594,21 @@ int decode_batched_pipelined(const orbg_codeset *set, const float *llr, int64_t 
     if (e != cudaSuccess)
         return cuda_fail(e);
     cudaStream_t s_in = set->pipe[0], s_dec = set->pipe[1], s_out = set->pipe[2];
-    const int64_t n = set->n_of[0];
+    const int64_t n0 = set->n_of[0];
     const int64_t nch = std::min<int64_t>(8, B / kPipeChunkMin);
     const int64_t per = (B + nch - 1) / nch;
+    /* first element of block b in each buffer; block B marks the end */
+    auto llr_at = [&](int64_t b) -> int64_t {
+        return b >= B ? (int64_t)n_llr : llr_offset ? llr_offset[b] : b * n0;
+    };
+    auto cw_at = [&](int64_t b) -> int64_t {
+        return b >= B ? (int64_t)n_cw : cw_offset ? cw_offset[b] : b * n0;
+    };
     float *d_llr = nullptr;
     uint8_t *d_cw = nullptr, *d_ab = nullptr;
     uint32_t *d_q = nullptr;
+    int32_t *d_cid = nullptr;
+    int64_t *d_lo = nullptr, *d_co = nullptr;
     unsigned long long *scratch = nullptr;
     std::vector<cudaEvent_t> ev;
     auto event = [&](cudaEvent_t *out) -> cudaError_t {
@@ -587,28 +618,48 @@ int decode_batched_pipelined(const orbg_codeset *set, const float *llr, int64_t 
         return r;
     };
     cudaEvent_t start = nullptr, done = nullptr;
-    if ((e = cudaMallocAsync((void **)&d_llr, (size_t)(B * n) * sizeof(float), st)) ||
-        (e = cudaMallocAsync((void **)&d_cw, (size_t)(B * n), st)) ||
-        (e = cudaMallocAsync((void **)&d_q, (size_t)B * sizeof(uint32_t), st)) ||
-        (e = cudaMallocAsync((void **)&d_ab, (size_t)B, st)) ||
-        (e = cudaMallocAsync((void **)&scratch, orbg_batched_scratch_bytes(per), st)) ||
-        (e = event(&start)) || (e = cudaEventRecord(start, st)) ||
-        (e = cudaStreamWaitEvent(s_in, start, 0)) || (e = cudaStreamWaitEvent(s_dec, start, 0)) ||
-        (e = cudaStreamWaitEvent(s_out, start, 0))) {
+    if ((e = cudaMallocAsync((void **)&d_llr, n_llr * sizeof(float), st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&d_cw, n_cw, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&d_q, (size_t)B * sizeof(uint32_t), st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&d_ab, (size_t)B, st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&scratch, orbg_batched_scratch_bytes(per), st)) !=
+            cudaSuccess ||
+        (code_id && (e = cudaMallocAsync((void **)&d_cid, (size_t)B * sizeof(int32_t), st)) !=
+                        cudaSuccess) ||
+        (llr_offset && (e = cudaMallocAsync((void **)&d_lo, (size_t)B * sizeof(int64_t), st)) !=
+                           cudaSuccess) ||
+        (cw_offset && (e = cudaMallocAsync((void **)&d_co, (size_t)B * sizeof(int64_t), st)) !=
+                          cudaSuccess) ||
+        (e = event(&start)) != cudaSuccess || (e = cudaEventRecord(start, st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(s_in, start, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(s_dec, start, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(s_out, start, 0)) != cudaSuccess) {
         /* fall through to clean-up */
     }
+    /* the per-block layout arrays go first, whole (12 bytes a block) */
+    if (e == cudaSuccess && code_id)
+        e = cudaMemcpyAsync(d_cid, code_id, (size_t)B * sizeof(int32_t), cudaMemcpyHostToDevice,
+                            s_in);
+    if (e == cudaSuccess && llr_offset)
+        e = cudaMemcpyAsync(d_lo, llr_offset, (size_t)B * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, s_in);
+    if (e == cudaSuccess && cw_offset)
+        e = cudaMemcpyAsync(d_co, cw_offset, (size_t)B * sizeof(int64_t), cudaMemcpyHostToDevice,
+                            s_in);
     const orbg_tuning &t = set->tuning;
     int le = 0;
     for (int64_t i = 0; i < nch && e == cudaSuccess && le == 0; i++) {
-        const int64_t b0 = i * per, bc = std::min(per, B - b0);
-        if (bc <= 0)
+        const int64_t b0 = i * per, b1 = std::min(B, b0 + per);
+        if (b1 <= b0)
             break;
+        const int64_t l0 = llr_at(b0), l1 = llr_at(b1), c0 = cw_at(b0), c1 = cw_at(b1);
         cudaEvent_t in_done = nullptr, dec_done = nullptr;
-        if ((e = event(&in_done)) || (e = event(&dec_done)))
+        if ((e = event(&in_done)) != cudaSuccess || (e = event(&dec_done)) != cudaSuccess)
             break;
-        if ((e = cudaMemcpyAsync(d_llr + b0 * n, llr + b0 * n, (size_t)(bc * n) * sizeof(float),
-                                 cudaMemcpyHostToDevice, s_in)) ||
-            (e = cudaEventRecord(in_done, s_in)) || (e = cudaStreamWaitEvent(s_dec, in_done, 0)))
+        if ((e = cudaMemcpyAsync(d_llr + l0, llr + l0, (size_t)(l1 - l0) * sizeof(float),
+                                 cudaMemcpyHostToDevice, s_in)) != cudaSuccess ||
+            (e = cudaEventRecord(in_done, s_in)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s_dec, in_done, 0)) != cudaSuccess)
             break;
         OrbgBatchedArgs a{};
         a.d_codes = set->d_codes;
@@ -616,11 +667,16 @@ int decode_batched_pipelined(const orbg_codeset *set, const float *llr, int64_t 
         a.ncodes = set->ncodes;
         a.n_max = set->n_max;
         a.w32_max = set->w32_max;
-        a.llr = d_llr + b0 * n;
-        a.B = bc;
+        a.code_id = d_cid ? d_cid + b0 : nullptr;
+        a.llr_off = d_lo ? d_lo + b0 : nullptr;
+        a.cw_off = d_co ? d_co + b0 : nullptr;
+        /* dense chunks index from their own first block; offsets are
+         * absolute in the whole buffers */
+        a.llr = d_lo ? d_llr : d_llr + l0;
+        a.cw = d_co ? d_cw : d_cw + c0;
+        a.B = b1 - b0;
         a.cap = query_cap;
         a.budget = t.warp_budget < query_cap ? t.warp_budget : query_cap;
-        a.cw = d_cw + b0 * n;
         a.q = d_q + b0;
         a.ab = d_ab + b0;
         a.scratch = scratch;
@@ -633,14 +689,15 @@ int decode_batched_pipelined(const orbg_codeset *set, const float *llr, int64_t 
         a.stream = s_dec;
         if ((le = orbg_launch_batched(a)) != 0)
             break;
-        if ((e = cudaEventRecord(dec_done, s_dec)) ||
-            (e = cudaStreamWaitEvent(s_out, dec_done, 0)) ||
-            (e = cudaMemcpyAsync(codeword + b0 * n, d_cw + b0 * n, (size_t)(bc * n),
-                                 cudaMemcpyDeviceToHost, s_out)) ||
-            (e = cudaMemcpyAsync(queries + b0, d_q + b0, (size_t)bc * sizeof(uint32_t),
-                                 cudaMemcpyDeviceToHost, s_out)) ||
-            (e = cudaMemcpyAsync(abandoned + b0, d_ab + b0, (size_t)bc, cudaMemcpyDeviceToHost,
-                                 s_out)))
+        if ((e = cudaEventRecord(dec_done, s_dec)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s_out, dec_done, 0)) != cudaSuccess ||
+            (c1 > c0 &&
+             (e = cudaMemcpyAsync(codeword + c0, d_cw + c0, (size_t)(c1 - c0),
+                                  cudaMemcpyDeviceToHost, s_out)) != cudaSuccess) ||
+            (e = cudaMemcpyAsync(queries + b0, d_q + b0, (size_t)(b1 - b0) * sizeof(uint32_t),
+                                 cudaMemcpyDeviceToHost, s_out)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(abandoned + b0, d_ab + b0, (size_t)(b1 - b0),
+                                 cudaMemcpyDeviceToHost, s_out)) != cudaSuccess)
             break;
     }
     /* join: the caller's stream waits for all three before the buffers go */
@@ -650,11 +707,10 @@ int decode_batched_pipelined(const orbg_codeset *set, const float *llr, int64_t 
             (je = cudaEventRecord(done, sx)) == cudaSuccess)
             je = cudaStreamWaitEvent(st, done, 0);
     }
-    if (d_llr) cudaFreeAsync(d_llr, st);
-    if (d_cw) cudaFreeAsync(d_cw, st);
-    if (d_q) cudaFreeAsync(d_q, st);
-    if (d_ab) cudaFreeAsync(d_ab, st);
-    if (scratch) cudaFreeAsync(scratch, st);
+    for (void *ptr : {(void *)d_llr, (void *)d_cw, (void *)d_q, (void *)d_ab, (void *)scratch,
+                      (void *)d_cid, (void *)d_lo, (void *)d_co})
+        if (ptr)
+            cudaFreeAsync(ptr, st);
     cudaError_t se = cudaStreamSynchronize(st);
     for (cudaEvent_t x : ev)
         cudaEventDestroy(x);
@@ -690,10 +746,6 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
     if ((llr_offset == nullptr) != (cw_offset == nullptr))
         return ORBG_EINVAL;
     cudaStream_t st = (cudaStream_t)cuda_stream;
-    if (!code_id && !llr_offset && B >= 2 * kPipeChunkMin && !is_device_ptr(llr) &&
-        !is_device_ptr(codeword) && !is_device_ptr(queries) && !is_device_ptr(abandoned))
-        return decode_batched_pipelined(set, llr, B, query_cap, codeword, queries, abandoned,
-                                        st);
     /* element counts: dense layout, or as far as the largest offset reaches */
     size_t n_llr, n_cw;
     if (!llr_offset) {
@@ -721,6 +773,15 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
             n_llr = n_cw = 0;
         }
     }
+    /* large batches on host buffers: chunked, copies overlapping decodes,
+     * when every layout array is on the host and places blocks in order */
+    if (B >= 2 * kPipeChunkMin && !is_device_ptr(llr) && !is_device_ptr(codeword) &&
+        !is_device_ptr(queries) && !is_device_ptr(abandoned) &&
+        (!code_id || !is_device_ptr(code_id)) && (!llr_offset || !is_device_ptr(llr_offset)) &&
+        (!cw_offset || !is_device_ptr(cw_offset)) &&
+        ordered_layout(set, code_id, llr_offset, cw_offset, B))
+        return decode_batched_pipelined(set, code_id, llr_offset, llr, B, query_cap, codeword,
+                                        cw_offset, queries, abandoned, n_llr, n_cw, st);
     Stager sg(st);
     const float *d_llr;
     uint8_t *d_cw, *d_ab;

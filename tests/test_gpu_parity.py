@@ -263,6 +263,30 @@ def test_pipelined_host_buffers(orbg):
                 (dev[0][keep], dev[1][keep], dev[2][keep]))
 
 
+def test_pipelined_host_buffers_mixed_codes(orbg):
+    """The chunked host-buffer path with code ids and per-block offsets
+    (blocks in order, no overlap): equal to the same call on device
+    buffers, block by block."""
+    codes, cid, llr, off, cwt, ebn0 = workloads.config4_inputs(B=160_000, seed=4403)
+    objs = [orbg.Code(cd.H, max_query_cap=10 ** 5) for cd in codes]
+    cs = orbg.CodeSet(objs)
+    B = cid.shape[0]
+    n_total = llr.shape[0]
+    cw_d, q_d, ab_d = orbg.decode_batched(cs, torch.from_numpy(llr).cuda(), 10 ** 5,
+                                          code_id=torch.from_numpy(cid).cuda(),
+                                          llr_offset=torch.from_numpy(off).cuda(),
+                                          cw_offset=torch.from_numpy(off).cuda(),
+                                          n_total=n_total)
+    torch.cuda.synchronize()
+    cw = np.zeros(n_total, np.uint8)
+    q = np.zeros(B, np.uint32)
+    ab = np.zeros(B, np.uint8)
+    orbg.orbg_decode_batched(cs.handle, cid, off, llr, B, 10 ** 5, cw, off, q, ab)
+    assert np.array_equal(cw, cw_d.cpu().numpy())
+    assert np.array_equal(q, q_d.cpu().numpy().astype(np.uint32))
+    assert np.array_equal(ab, ab_d.cpu().numpy())
+
+
 def test_mixed_codes_one_launch_equals_alone(orbg):
     """Blocks of four codes with different n and n-k in one batched launch
     give what each code's blocks give alone, and what the oracle gives."""
