@@ -67,6 +67,8 @@ def parse_args(argv=None):
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-graph", action="store_true",
+                   help="time direct calls instead of replays of a captured CUDA graph")
     p.add_argument("--ref-sample", type=int, default=8000,
                    help="blocks per reference step (CPU oracle)")
     p.add_argument("--workload", choices=sorted(WORKLOADS), default="bch",
@@ -409,13 +411,28 @@ class Job:
             self.cid = self.off = None
         self.stream = torch.cuda.current_stream(dev)
 
+    def capture(self):
+        """Capture one step (its scratch allocation, counter reset and both
+        launches) into a CUDA graph; later steps replay it."""
+        import torch
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.call(torch.cuda.current_stream())
+        self.graph = g
+
     def step(self):
+        if getattr(self, "graph", None) is not None:
+            self.graph.replay()
+            return
+        self.call(self.stream)
+
+    def call(self, stream):
         if self.form == "plain":
             self.orbg.orbg_decode(self.objs[0].handle, self.llr, self.B, CAP, self.cw, self.q,
-                                  self.ab, self.stream)
+                                  self.ab, stream)
             return
         self.orbg.orbg_decode_batched(self.cs.handle, self.cid, self.off, self.llr, self.B, CAP,
-                                      self.cw, self.off, self.q, self.ab, self.stream)
+                                      self.cw, self.off, self.q, self.ab, stream)
 
     def bler(self):
         """Fraction of blocks whose decoding differs from the sent codeword."""
@@ -475,6 +492,18 @@ def bench_ours(args, rank, world, local):
     for _ in range(max(3, args.warmup)):
         job.step()
     torch.cuda.synchronize(dev)
+    graph = "direct calls (--no-graph)"
+    if not args.no_graph:
+        try:
+            job.capture()
+            for _ in range(3):  # warm-up replays
+                job.step()
+            torch.cuda.synchronize(dev)
+            graph = "replays of a captured CUDA graph of one call"
+        except Exception as exc:  # capture refused: time the direct calls
+            job.graph = None
+            torch.cuda.synchronize(dev)
+            graph = "direct calls (capture failed: %s)" % str(exc).splitlines()[0][:120]
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -515,6 +544,7 @@ def bench_ours(args, rank, world, local):
         pass
     lanes = measured_int_lanes(orbg)
     peak = lanes * SMS * SM_MAX_MHZ * 1e6 / 1e12 if lanes else None
+    smem_bpc = measured_smem_bytes(orbg)
 
     clocks = sampler.summary(t_wall0, t_wall1)
 
@@ -537,7 +567,7 @@ def bench_ours(args, rank, world, local):
                           % (job.llr_np.nbytes / 1e6,
                              ">" if job.llr_np.nbytes > 129e6 else "<=")),
                    "tuning": orbg.orbg_codeset_get_tuning(job.cs.handle).as_dict(),
-                   "tuning_source": tuned,
+                   "tuning_source": tuned, "timed": graph,
                    "parallelism": "replicas x%d (blocks sharded by rank, no collective)" % world},
         "queries_per_s": queries_total / (total_ms / 1000.0),
         "latency_ms": {"step_p50": statistics.median(per_step),
@@ -557,6 +587,10 @@ def bench_ours(args, rank, world, local):
                               "x 152 SMs x 2070 MHz" % (alg_ops, lanes))},
         "clocks": clocks,
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
+        "smem_peak": {"bytes_per_clk_per_sm": smem_bpc,
+                      "tb_s": (smem_bpc * SMS * SM_MAX_MHZ * 1e6 / 1e12) if smem_bpc else None,
+                      "what": "measured 64-bit conflict-free shared loads (the search's "
+                              "column and triple-table reads are shared loads)"},
     }
     if e2e:
         line["e2e"] = e2e
@@ -571,6 +605,14 @@ def measured_int_lanes(orbg):
     """LOP3 lanes per clock per SM, from the library's probe kernel."""
     try:
         return orbg.orbg_probe_int_lanes()
+    except Exception:
+        return None
+
+
+def measured_smem_bytes(orbg):
+    """Shared-memory bytes per clock per SM, from the library's probe kernel."""
+    try:
+        return orbg.orbg_probe_smem_bytes()
     except Exception:
         return None
 

@@ -322,6 +322,16 @@ ORBG_API int orbg_codeset_autotune(orbg_codeset *set, const int32_t *code_id,
 ORBG_API int orbg_probe_int_lanes(double *lanes_per_clk_per_sm);
 
 /*
+ * Roofline probe for shared memory: bytes per SM per clock that 64-bit
+ * shared loads deliver (a warp reads 32 consecutive 8-byte words, so no
+ * bank conflicts), measured with clock64 on every SM of the current
+ * device.  The column and triple-table reads of the search are shared
+ * loads.  Synchronous; allocates and frees a small buffer.  The library's
+ * own addition; the paper has no counterpart.
+ */
+ORBG_API int orbg_probe_smem_bytes(double *bytes_per_clk_per_sm);
+
+/*
  * The query order this library decodes in, for inspection and tests: the
  * first `count` noise patterns for length n (1..256), expanded from the
  * same tables the kernels read (table 0: the one-warp-per-block table;

@@ -296,6 +296,14 @@ int orbg_probe_int_lanes(double *lanes_per_clk_per_sm)
     return e ? cuda_fail((cudaError_t)e) : ORBG_OK;
 }
 
+int orbg_probe_smem_bytes(double *bytes_per_clk_per_sm)
+{
+    if (!bytes_per_clk_per_sm)
+        return ORBG_EINVAL;
+    int e = orbg_launch_smem_probe(bytes_per_clk_per_sm);
+    return e ? cuda_fail((cudaError_t)e) : ORBG_OK;
+}
+
 int orbg_load_code(const uint8_t *mat, int kind, int n, int k, uint32_t max_query_cap,
                    orbg_code **out)
 {

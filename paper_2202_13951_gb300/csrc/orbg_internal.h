@@ -175,6 +175,7 @@ int orbg_codeset_lengths(const orbg_codeset *set, std::vector<int> *n_of);
 /* Records a cudaError_t for orbg_last_cuda_error; returns the orbg status. */
 int orbg_note_cuda_error(int cuda_error);
 int orbg_launch_int_probe(double *lanes_per_clk_per_sm);
+int orbg_launch_smem_probe(double *bytes_per_clk_per_sm);
 #endif
 
 #endif /* ORBG_INTERNAL_H */

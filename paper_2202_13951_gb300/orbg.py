@@ -99,6 +99,7 @@ def load_library(path=None):
                                           ctypes.POINTER(OrbgTuning)]
     lib.orbg_codeset_get_tuning.argtypes = [vp, ctypes.POINTER(OrbgTuning)]
     lib.orbg_probe_int_lanes.argtypes = [ctypes.POINTER(ctypes.c_double)]
+    lib.orbg_probe_smem_bytes.argtypes = [ctypes.POINTER(ctypes.c_double)]
     lib.orbg_status_string.argtypes = [i32]
     lib.orbg_status_string.restype = ctypes.c_char_p
     lib.orbg_last_cuda_error.argtypes = []
@@ -120,7 +121,7 @@ def load_library(path=None):
               "orbg_server_poll", "orbg_server_fetch", "orbg_server_stats_get",
               "orbg_server_destroy", "orbg_server_replay",
               "orbg_codeset_set_tuning", "orbg_codeset_get_tuning", "orbg_probe_int_lanes",
-              "orbg_codeset_autotune",
+              "orbg_probe_smem_bytes", "orbg_codeset_autotune",
               "orbg_last_cuda_error", "orbg_version"):
         getattr(lib, f).restype = i32
     if path == LIB_PATH:
@@ -323,6 +324,13 @@ def orbg_probe_int_lanes():
     """lop3.b32 lanes retired per SM per clock on the current device."""
     x = ctypes.c_double()
     _check(load_library().orbg_probe_int_lanes(ctypes.byref(x)), "orbg_probe_int_lanes")
+    return x.value
+
+
+def orbg_probe_smem_bytes():
+    """Shared-memory bytes per SM per clock (64-bit loads, no conflicts)."""
+    x = ctypes.c_double(0)
+    _check(load_library().orbg_probe_smem_bytes(ctypes.byref(x)), "orbg_probe_smem_bytes")
     return x.value
 
 

@@ -85,6 +85,7 @@ def test_decode_argument_checks_without_gpu(lib):
     assert lib.orbg_free_code(None) == orbg.ORBG_OK
     assert lib.orbg_codeset_free(None) == orbg.ORBG_OK
     assert lib.orbg_probe_int_lanes(None) == orbg.ORBG_EINVAL
+    assert lib.orbg_probe_smem_bytes(None) == orbg.ORBG_EINVAL
 
 
 @pytest.mark.parametrize("n,count", [(1, 2), (3, 8), (7, 128), (12, 4096),

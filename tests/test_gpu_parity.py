@@ -287,6 +287,32 @@ def test_pipelined_host_buffers_mixed_codes(orbg):
     assert np.array_equal(ab, ab_d.cpu().numpy())
 
 
+def test_batched_call_in_cuda_graph(orbg):
+    """A batched call on device buffers (stream-ordered scratch allocation,
+    counter reset, both launches) captures into a CUDA graph; every replay
+    equals the direct call."""
+    code, llr, _ = workloads.config2_inputs(B_per_point=5000)
+    B, n = llr.shape
+    c = orbg.Code(code.H, max_query_cap=10 ** 6)
+    cs = orbg.CodeSet([c])
+    x = torch.from_numpy(llr).cuda()
+    want = gpu_batched(orbg, cs, llr, 10 ** 6)
+    cw = torch.empty((B, n), dtype=torch.uint8, device="cuda")
+    q = torch.empty(B, dtype=torch.int32, device="cuda")
+    ab = torch.empty(B, dtype=torch.uint8, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        orbg.orbg_decode_batched(cs.handle, None, None, x, B, 10 ** 6, cw, None, q, ab,
+                                 torch.cuda.current_stream())
+    for _ in range(2):
+        cw.zero_()
+        q.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert_same((cw.cpu().numpy(), q.cpu().numpy().astype(np.int64), ab.cpu().numpy()),
+                    want)
+
+
 def test_mixed_codes_one_launch_equals_alone(orbg):
     """Blocks of four codes with different n and n-k in one batched launch
     give what each code's blocks give alone, and what the oracle gives."""
