@@ -67,7 +67,7 @@ struct OrbgTable {
  * (the largest position of that step or an earlier one, at most
  * ORBG_FLAT_RANKS), bits 5-7 the step's largest Hamming weight.  A warp
  * tests 32 consecutive patterns per step before it turns to runs. */
-#define ORBG_FLAT_MAX 1024
+#define ORBG_FLAT_MAX 256
 #define ORBG_FLAT_POS 7
 #define ORBG_FLAT_RANKS 31
 

@@ -97,7 +97,7 @@ def test_query_order_tables_match_oracle(lib, n, count):
     assert orbg.orbg_query_order(n, count, 0) == want
     assert orbg.orbg_query_order(n, count, 1) == want
     flat = orbg.orbg_query_order(n, count, 2)
-    assert len(flat) == min(count, 1024) or n <= 10
+    assert len(flat) == min(count, 256) or n <= 10
     assert flat == want[:len(flat)]
 
 
