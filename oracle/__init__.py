@@ -1,4 +1,4 @@
-"""CPU oracle for basic ORBGRAND (arXiv 2202.13951).
+"""CPU oracle for basic and one-line full ORBGRAND (arXiv 2202.13951).
 
 TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
 benchmark's CPU-baseline leg may use it; the product path never does.
@@ -12,18 +12,26 @@ Functions and the passages they follow:
   count_by_weight        patterns per (W, w) met by that order
   landslide              Algorithm 2 with Build-mountain (Sec. III-C)
   sort_reliability       the permutation pi (Sec. III-A)
+  decode_1line / decode_batch_1line / enumerate_patterns_1line
+                         one-line full ORBGRAND (Sec. III-D, Eq. relest_seg
+                         with m = 1, Eq. wu_i): the order of increasing
+                         reliability weight J0 w_H + beta w_L
 
 Parity pins: tests/test_oracle_pins.py (brute force on tiny codes, the
 first queries of Sec. III-B, the Fig. 3 / Fig. 5 examples, closed-form
-partition counts, decoder invariants) and tests/test_oracle_mutations.py
-(planted mistakes must fail a pin).
+partition counts, decoder invariants), tests/test_oracle_1line.py (the
+one-line order against brute force and its generating function; J0 = 0,
+beta = 1 is basic ORBGRAND) and tests/test_oracle_mutations.py (planted
+mistakes must fail a pin).
 """
 from .oracle import (Oracle, OracleError, build_oracle, compile_oracle,
-                     count_by_weight, decode, decode_batch, default,
-                     enumerate_patterns, landslide, sort_reliability,
+                     count_by_weight, decode, decode_1line, decode_batch,
+                     decode_batch_1line, default, enumerate_patterns,
+                     enumerate_patterns_1line, landslide, sort_reliability,
                      ORACLE_LIB, ORACLE_SRC)
 
 __all__ = ["Oracle", "OracleError", "build_oracle", "compile_oracle",
-           "count_by_weight", "decode", "decode_batch", "default",
-           "enumerate_patterns", "landslide", "sort_reliability",
+           "count_by_weight", "decode", "decode_1line", "decode_batch",
+           "decode_batch_1line", "default", "enumerate_patterns",
+           "enumerate_patterns_1line", "landslide", "sort_reliability",
            "ORACLE_LIB", "ORACLE_SRC"]

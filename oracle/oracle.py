@@ -74,6 +74,19 @@ class Oracle:
         lib.orbg_oracle_count_by_weight.argtypes = [ctypes.c_int,
                                                     ctypes.c_int, i64p]
         lib.orbg_oracle_count_by_weight.restype = ctypes.c_int
+        lib.orbg_oracle_enumerate_1line.argtypes = [ctypes.c_int, ctypes.c_long,
+                                                    ctypes.c_long, ctypes.c_long, i32p]
+        lib.orbg_oracle_enumerate_1line.restype = ctypes.c_long
+        lib.orbg_oracle_decode_1line.argtypes = [u8p, ctypes.c_int, ctypes.c_int, f32p,
+                                                 ctypes.c_uint64, ctypes.c_long,
+                                                 ctypes.c_long, u8p, u64p, i32p, u64p,
+                                                 i32p, i32p]
+        lib.orbg_oracle_decode_1line.restype = ctypes.c_int
+        lib.orbg_oracle_decode_batch_1line.argtypes = [u8p, ctypes.c_int, ctypes.c_int,
+                                                       f32p, ctypes.c_long, ctypes.c_uint64,
+                                                       ctypes.c_long, ctypes.c_long, u8p,
+                                                       u64p, u8p, u64p]
+        lib.orbg_oracle_decode_batch_1line.restype = ctypes.c_int
         self.lib = lib
         self.path = path
 
@@ -119,6 +132,56 @@ class Oracle:
         if rc != 0:
             raise OracleError("oracle batch decode failed: %d" % rc)
         return c, q, ab, sw
+
+    def decode_1line(self, H, llr, cap, J0, beta):
+        """decode() for one-line full ORBGRAND (Sec. III-D): queries in
+        increasing J0 w_H + beta w_L."""
+        H = np.ascontiguousarray(H, dtype=np.uint8)
+        r, n = H.shape
+        llr = np.ascontiguousarray(llr, dtype=np.float32)
+        assert llr.shape == (n,)
+        c = np.zeros(n, np.uint8)
+        q = ctypes.c_uint64(0)
+        ab = ctypes.c_int(0)
+        sw = ctypes.c_uint64(0)
+        hw = ctypes.c_int(0)
+        hv = np.zeros(n, np.int32)
+        rc = self.lib.orbg_oracle_decode_1line(
+            _ptr(H, ctypes.c_uint8), n, r, _ptr(llr, ctypes.c_float), int(cap), int(J0),
+            int(beta), _ptr(c, ctypes.c_uint8), ctypes.byref(q), ctypes.byref(ab),
+            ctypes.byref(sw), ctypes.byref(hw), _ptr(hv, ctypes.c_int))
+        if rc != 0:
+            raise OracleError("oracle 1-line decode failed: %d" % rc)
+        hit = None if hw.value < 0 else [int(x) for x in hv[:hw.value]]
+        return c, int(q.value), int(ab.value), int(sw.value), hit
+
+    def decode_batch_1line(self, H, llr, cap, J0, beta):
+        """decode_batch() for one-line full ORBGRAND."""
+        H = np.ascontiguousarray(H, dtype=np.uint8)
+        r, n = H.shape
+        llr = np.ascontiguousarray(llr, dtype=np.float32).reshape(-1, n)
+        B = llr.shape[0]
+        c = np.zeros((B, n), np.uint8)
+        q = np.zeros(B, np.uint64)
+        ab = np.zeros(B, np.uint8)
+        sw = np.zeros(B, np.uint64)
+        rc = self.lib.orbg_oracle_decode_batch_1line(
+            _ptr(H, ctypes.c_uint8), n, r, _ptr(llr, ctypes.c_float), B, int(cap), int(J0),
+            int(beta), _ptr(c, ctypes.c_uint8), _ptr(q, ctypes.c_uint64),
+            _ptr(ab, ctypes.c_uint8), _ptr(sw, ctypes.c_uint64))
+        if rc != 0:
+            raise OracleError("oracle 1-line batch decode failed: %d" % rc)
+        return c, q, ab, sw
+
+    def enumerate_patterns_1line(self, n, count, J0, beta):
+        """First `count` patterns of the one-line order (increasing
+        J0 w_H + beta w_L), as tuples of 1-based sorted-order positions."""
+        out = np.zeros((count, n + 1), np.int32)
+        got = self.lib.orbg_oracle_enumerate_1line(n, int(J0), int(beta), count,
+                                                   _ptr(out, ctypes.c_int))
+        if got < 0:
+            raise OracleError("enumerate failed: %d" % got)
+        return [tuple(int(x) for x in row[1:1 + row[0]]) for row in out[:got]]
 
     def enumerate_patterns(self, n, count):
         """First `count` patterns of the query order for length n, as tuples
@@ -190,3 +253,15 @@ def sort_reliability(llr):
 
 def count_by_weight(n, Wmax):
     return default().count_by_weight(n, Wmax)
+
+
+def decode_1line(H, llr, cap, J0, beta):
+    return default().decode_1line(H, llr, cap, J0, beta)
+
+
+def decode_batch_1line(H, llr, cap, J0, beta):
+    return default().decode_batch_1line(H, llr, cap, J0, beta)
+
+
+def enumerate_patterns_1line(n, count, J0, beta):
+    return default().enumerate_patterns_1line(n, count, J0, beta)

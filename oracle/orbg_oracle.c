@@ -29,9 +29,22 @@
  *      queries without one the decoder abandons (Sec. IV-A) and returns the
  *      hard decision with the abandon flag set.
  *
+ * Full ORBGRAND with one line (Sec. III-D, Eq. relest_seg with m = 1,
+ * I_1 = n): the sorted position j gets the integer reliability
+ * J_0 + beta j, so pattern z has reliability weight
+ * J_0 w_H(z) + beta w_L(z), and queries go in increasing reliability weight.
+ * For a weight R and a Hamming weight w the logistic weight is fixed,
+ * w_L = (R - J_0 w) / beta (Eq. wu_i), and the patterns are the same
+ * Landslide sets as above.  Readings: J_0 >= 0 and beta >= 1 (the model's
+ * values increase with the position); ties within a reliability weight in
+ * the same canonical order as the basic decoder (w ascending, then the
+ * Landslide order).  Basic ORBGRAND is the case J_0 = 0, beta = 1 (the
+ * paper notes it is the special case of Eq. relest_seg).
+ *
  * Parity pins (tests): brute force over all 2^n patterns for tiny codes,
  * the first queries listed in Sec. III-B, the Fig. 3 / Fig. 5 Landslide
- * examples, closed-form partition counts and decoder invariants.
+ * examples, closed-form partition counts (for the reliability weight, the
+ * coefficients of prod_i (1 + x^(J_0 + beta i))) and decoder invariants.
  */
 #include <math.h>
 #include <stdint.h>
@@ -137,33 +150,51 @@ static int orc_map_u_to_v(const int *u, int w, void *vctx)
     return m->fn(v + 1, w, m->ctx);
 }
 
-/* Walk the patterns of a length-n word in query order, stopping when the
- * visitor returns non-zero.  The zero pattern (w_L = 0) comes first. */
-static int orc_walk_patterns(int n, orc_pattern_fn fn, void *ctx)
+/* Walk the patterns of a length-n word in the order of increasing
+ * reliability weight R = J0 w_H + beta w_L (Sec. III-D; basic ORBGRAND:
+ * J0 = 0, beta = 1, where R is the logistic weight), stopping when the
+ * visitor returns non-zero.  The zero pattern (R = 0) comes first. */
+static int orc_walk_rw(int n, long J0, long beta, orc_pattern_fn fn, void *ctx)
 {
-    long Wmax = (long)n * (n + 1) / 2;   /* logistic weight of all-ones */
-    long W;
+    /* reliability weight of the all-ones pattern */
+    long Rmax = J0 * n + beta * ((long)n * (n + 1) / 2);
+    long R, L;
     int w, rc;
     orc_map_ctx m;
     m.fn = fn;
     m.ctx = ctx;
-    rc = fn(NULL, 0, ctx);               /* W = 0: nothing flipped */
+    rc = fn(NULL, 0, ctx);               /* R = 0: nothing flipped */
     if (rc)
         return rc;
-    for (W = 1; W <= Wmax; W++) {
-        /* w up to floor((sqrt(1+8W)-1)/2): smallest w_L of weight w is
-         * w(w+1)/2 (Eq. fractionation). */
-        for (w = 1; (long)w * (w + 1) / 2 <= W && w <= n; w++) {
-            long Wp = W - (long)w * (w + 1) / 2;
-            int np = n - w;
-            if (Wp > (long)w * np)
-                continue;                 /* no partition fits */
-            rc = orc_landslide((int)Wp, w, np, orc_map_u_to_v, &m);
-            if (rc)
-                return rc;
+    for (R = 1; R <= Rmax; R++) {
+        for (w = 1; w <= n; w++) {
+            if (R - J0 * w < 0)
+                break;                    /* larger w only weigh more */
+            if ((R - J0 * w) % beta)
+                continue;                 /* no integer logistic weight */
+            L = (R - J0 * w) / beta;      /* Eq. wu_i with m = 1 */
+            /* smallest w_L of weight w is w(w+1)/2 (Eq. fractionation);
+             * it grows with w while L shrinks */
+            if (L < (long)w * (w + 1) / 2)
+                break;
+            {
+                long Wp = L - (long)w * (w + 1) / 2;
+                int np = n - w;
+                if (Wp > (long)w * np)
+                    continue;             /* no partition fits */
+                rc = orc_landslide((int)Wp, w, np, orc_map_u_to_v, &m);
+                if (rc)
+                    return rc;
+            }
         }
     }
     return ORC_OK;
+}
+
+/* The basic order: increasing logistic weight. */
+static int orc_walk_patterns(int n, orc_pattern_fn fn, void *ctx)
+{
+    return orc_walk_rw(n, 0, 1, fn, ctx);
 }
 
 /* ------------------------------------------------------------------ */
@@ -205,6 +236,22 @@ long orbg_oracle_enumerate(int n, long count, int *out)
     e.count = count;
     e.done = 0;
     orc_walk_patterns(n, orc_enum_visit, &e);
+    return e.done;
+}
+
+/* The same for the one-line order of reliability weight J0 w_H + beta w_L. */
+long orbg_oracle_enumerate_1line(int n, long J0, long beta, long count, int *out)
+{
+    orc_enum_ctx e;
+    if (n < 1 || n > ORC_MAX_N || J0 < 0 || beta < 1 || count < 0 || (count > 0 && !out))
+        return ORC_EINVAL;
+    if (count == 0)
+        return 0;
+    e.out = out;
+    e.stride = n + 1;
+    e.count = count;
+    e.done = 0;
+    orc_walk_rw(n, J0, beta, orc_enum_visit, &e);
     return e.done;
 }
 
@@ -354,9 +401,9 @@ static void orc_sort_by_reliability(const float *llr, int n, int *pi)
  *             the sorted order.
  * Returns 0, or ORC_ENAN if an LLR is NaN, ORC_EINVAL on bad sizes.
  */
-int orbg_oracle_decode(const uint8_t *H, int n, int r, const float *llr,
-                       uint64_t cap, uint8_t *c_out, uint64_t *q_out,
-                       int *abandon, uint64_t *sum_w, int *hit_w, int *hit_v)
+static int orc_decode_rw(const uint8_t *H, int n, int r, const float *llr, uint64_t cap,
+                         long J0, long beta, uint8_t *c_out, uint64_t *q_out, int *abandon,
+                         uint64_t *sum_w, int *hit_w, int *hit_v)
 {
     static uint64_t col[ORC_MAX_N * ORC_MAX_WORDS];
     int pi[ORC_MAX_N];
@@ -364,7 +411,8 @@ int orbg_oracle_decode(const uint8_t *H, int n, int r, const float *llr,
     orc_dec_ctx d;
     int i, j, words;
 
-    if (n < 1 || n > ORC_MAX_N || r < 1 || r > 64 * ORC_MAX_WORDS || cap < 1)
+    if (n < 1 || n > ORC_MAX_N || r < 1 || r > 64 * ORC_MAX_WORDS || cap < 1 || J0 < 0 ||
+        beta < 1)
         return ORC_EINVAL;
     for (i = 0; i < n; i++)
         if (isnan(llr[i]))
@@ -392,7 +440,7 @@ int orbg_oracle_decode(const uint8_t *H, int n, int r, const float *llr,
             for (j = 0; j < words; j++)
                 d.s0[j] ^= col[(size_t)i * words + j];
 
-    orc_walk_patterns(n, orc_dec_visit, &d);
+    orc_walk_rw(n, J0, beta, orc_dec_visit, &d);
 
     for (i = 0; i < n; i++)
         c_out[i] = y[i];
@@ -415,18 +463,34 @@ int orbg_oracle_decode(const uint8_t *H, int n, int r, const float *llr,
     return ORC_OK;
 }
 
-/* Batch form: blocks decoded one after another, same H. */
-int orbg_oracle_decode_batch(const uint8_t *H, int n, int r, const float *llr,
-                             long B, uint64_t cap, uint8_t *c_out,
-                             uint64_t *q_out, uint8_t *abandon, uint64_t *sum_w)
+/* Basic ORBGRAND (the order of increasing logistic weight). */
+int orbg_oracle_decode(const uint8_t *H, int n, int r, const float *llr,
+                       uint64_t cap, uint8_t *c_out, uint64_t *q_out,
+                       int *abandon, uint64_t *sum_w, int *hit_w, int *hit_v)
+{
+    return orc_decode_rw(H, n, r, llr, cap, 0, 1, c_out, q_out, abandon, sum_w, hit_w, hit_v);
+}
+
+/* One-line full ORBGRAND with integer J0 >= 0, beta >= 1 (Sec. III-D). */
+int orbg_oracle_decode_1line(const uint8_t *H, int n, int r, const float *llr, uint64_t cap,
+                             long J0, long beta, uint8_t *c_out, uint64_t *q_out,
+                             int *abandon, uint64_t *sum_w, int *hit_w, int *hit_v)
+{
+    return orc_decode_rw(H, n, r, llr, cap, J0, beta, c_out, q_out, abandon, sum_w, hit_w,
+                         hit_v);
+}
+
+/* Batch forms: blocks decoded one after another, same H. */
+int orbg_oracle_decode_batch_1line(const uint8_t *H, int n, int r, const float *llr, long B,
+                                   uint64_t cap, long J0, long beta, uint8_t *c_out,
+                                   uint64_t *q_out, uint8_t *abandon, uint64_t *sum_w)
 {
     long b;
     for (b = 0; b < B; b++) {
         int ab = 0, rc;
         uint64_t sw = 0;
-        rc = orbg_oracle_decode(H, n, r, llr + (size_t)b * n, cap,
-                                c_out + (size_t)b * n, q_out + b, &ab, &sw,
-                                NULL, NULL);
+        rc = orc_decode_rw(H, n, r, llr + (size_t)b * n, cap, J0, beta,
+                           c_out + (size_t)b * n, q_out + b, &ab, &sw, NULL, NULL);
         if (rc)
             return rc;
         abandon[b] = (uint8_t)ab;
@@ -434,6 +498,14 @@ int orbg_oracle_decode_batch(const uint8_t *H, int n, int r, const float *llr,
             sum_w[b] = sw;
     }
     return ORC_OK;
+}
+
+int orbg_oracle_decode_batch(const uint8_t *H, int n, int r, const float *llr,
+                             long B, uint64_t cap, uint8_t *c_out,
+                             uint64_t *q_out, uint8_t *abandon, uint64_t *sum_w)
+{
+    return orbg_oracle_decode_batch_1line(H, n, r, llr, B, cap, 0, 1, c_out, q_out, abandon,
+                                          sum_w);
 }
 
 /* The permutation of Sec. III-A alone, for tests. */

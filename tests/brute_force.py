@@ -1,5 +1,5 @@
-"""Brute-force basic ORBGRAND for tiny codes (n <= 16): a third, independent
-implementation used to pin the oracle.
+"""Brute-force basic and one-line full ORBGRAND for tiny codes (n <= 16): a
+third, independent implementation used to pin the oracle.
 
 It lists all 2^n noise patterns, sorts them by (logistic weight, Hamming
 weight, positions lexicographically) -- the canonical reading of the
@@ -46,3 +46,36 @@ def decode(H, llr, cap):
         if not ((H @ c.astype(np.int64)) % 2).any():
             return c, t, 0
     return y.copy(), len(query_order(n)), 1
+
+
+@functools.lru_cache(maxsize=None)
+def query_order_1line(n, J0, beta):
+    """All subsets of {1..n} sorted by (reliability weight J0 |v| + beta sum(v),
+    Hamming weight, positions lexicographically): one-line full ORBGRAND
+    (Sec. III-D: sorted position j is worth J0 + beta j) with the same
+    canonical tie order."""
+    pats = []
+    for mask in range(1 << n):
+        v = tuple(i + 1 for i in range(n) if (mask >> i) & 1)
+        pats.append((J0 * len(v) + beta * sum(v), len(v), v))
+    pats.sort()
+    return tuple(p[2] for p in pats)
+
+
+def decode_1line(H, llr, cap, J0, beta):
+    """decode() in the one-line order.  Returns (codeword, queries, abandoned)."""
+    H = np.asarray(H, dtype=np.int64)
+    llr = np.asarray(llr, dtype=np.float32)
+    n = llr.shape[0]
+    y = (llr > 0).astype(np.uint8)
+    pi = reliability_order(llr)
+    order = query_order_1line(n, J0, beta)
+    for t, v in enumerate(order, start=1):
+        if t > cap:
+            return y.copy(), cap, 1
+        c = y.copy()
+        for p in v:
+            c[pi[p - 1]] ^= 1
+        if not ((H @ c.astype(np.int64)) % 2).any():
+            return c, t, 0
+    return y.copy(), len(order), 1

@@ -261,9 +261,106 @@ def pin_cap_boundary(orc):
     assert seen > 5
 
 
+# ---------------------------------------------- one-line full ORBGRAND
+
+# (J0, beta) pairs: basic, intercepts below, at and far above one slope,
+# slopes above one, and intercepts not divisible by the slope
+LINES = [(0, 1), (1, 1), (3, 1), (20, 1), (0, 2), (5, 2), (2, 3), (7, 4)]
+
+
+def pin_1line_order_brute(orc):
+    """The whole one-line order for n <= 10 equals sorting all subsets by
+    (J0 w + beta w_L, w, lexicographic) (Sec. III-D, Eq. relest_seg, m = 1)."""
+    for n in (1, 3, 6, 9, 10):
+        for J0, beta in LINES:
+            got = orc.enumerate_patterns_1line(n, 1 << n, J0, beta)
+            assert got == list(brute_force.query_order_1line(n, J0, beta)), (n, J0, beta)
+
+
+def _rw_series(n, J0, beta, Rmax):
+    """Coefficients of prod_{i=1}^{n} (1 + x^(J0 + beta i)) up to x^Rmax: the
+    number of patterns of each reliability weight."""
+    c = [0] * (Rmax + 1)
+    c[0] = 1
+    for i in range(1, n + 1):
+        e = J0 + beta * i
+        for R in range(Rmax, e - 1, -1):
+            c[R] += c[R - e]
+    return c
+
+
+def pin_1line_generating_function(orc):
+    """For n = 40 and 64, the oracle's first patterns carry non-decreasing
+    reliability weights whose counts per weight are the coefficients of
+    prod_i (1 + x^(J0 + beta i))."""
+    for n, J0, beta, Rmax in ((40, 4, 2, 90), (64, 0, 1, 40), (64, 3, 1, 60),
+                              (40, 2, 3, 80)):
+        want = _rw_series(n, J0, beta, Rmax)
+        total = sum(want)
+        pats = orc.enumerate_patterns_1line(n, total, J0, beta)
+        assert len(pats) == total
+        rw = [J0 * len(v) + beta * sum(v) for v in pats]
+        assert rw == sorted(rw) and rw[-1] <= Rmax
+        hist = [0] * (Rmax + 1)
+        for R in rw:
+            hist[R] += 1
+        assert hist == want, (n, J0, beta)
+
+
+def pin_1line_is_basic_at_origin(orc):
+    """J0 = 0, beta = 1 is basic ORBGRAND (the paper's special case of
+    Eq. relest_seg): same order, same decodings."""
+    assert orc.enumerate_patterns_1line(64, 20000, 0, 1) == orc.enumerate_patterns(64, 20000)
+    code = workloads.rlc(48, 38, seed=3)
+    llr, _ = workloads.awgn_llr(code, 60, 3.0, seed=6)
+    a = orc.decode_batch(code.H, llr, 20000)
+    b = orc.decode_batch_1line(code.H, llr, 20000, 0, 1)
+    for x, y in zip(a, b):
+        assert (x == y).all()
+
+
+def pin_1line_brute_decode(orc, blocks=40):
+    """One-line oracle = brute force on the (7,4) Hamming code at every cap
+    and on a seeded random (12,8) code at boundary caps, for every line."""
+    rng = np.random.default_rng(17)
+    ham = workloads.hamming74()
+    code = workloads.rlc(12, 8, seed=12)
+    for J0, beta in LINES:
+        for llr in _tiny_inputs(ham, rng, blocks // 4):
+            for cap in range(1, 129, 7):
+                c0, q0, a0 = brute_force.decode_1line(ham.H, llr, cap, J0, beta)
+                c1, q1, a1, _, _ = orc.decode_1line(ham.H, llr, cap, J0, beta)
+                assert (c0 == c1).all() and q0 == q1 and a0 == a1, (J0, beta, llr, cap)
+        for llr in _tiny_inputs(code, rng, blocks // 4):
+            _, qh, _ = brute_force.decode_1line(code.H, llr, 1 << 12, J0, beta)
+            for cap in sorted({1, 2, max(1, qh - 1), qh, qh + 1, 1 << 12}):
+                c0, q0, a0 = brute_force.decode_1line(code.H, llr, cap, J0, beta)
+                c1, q1, a1, _, _ = orc.decode_1line(code.H, llr, cap, J0, beta)
+                assert (c0 == c1).all() and q0 == q1 and a0 == a1, (J0, beta, llr, cap)
+
+
+def pin_1line_invariants(orc):
+    """Noiseless input decodes at query 1 for any line; H c = 0 whenever not
+    abandoned."""
+    rng = np.random.default_rng(19)
+    code = workloads.rlc(40, 30, seed=4)
+    llr, cw = workloads.awgn_llr(code, 20, 3.5, seed=8)
+    clean = np.where(cw == 1, 2.0, -2.0).astype(np.float32)
+    clean *= rng.uniform(0.5, 2.0, clean.shape).astype(np.float32)
+    for J0, beta in ((3, 1), (5, 2)):
+        for b in range(5):
+            c, q, a, _, _ = orc.decode_1line(code.H, clean[b], 1000, J0, beta)
+            assert q == 1 and a == 0 and (c == cw[b]).all()
+        for b in range(llr.shape[0]):
+            c, q, a, _, _ = orc.decode_1line(code.H, llr[b], 20000, J0, beta)
+            if not a:
+                assert not ((code.H.astype(np.int64) @ c) % 2).any()
+
+
 FAST_PINS = [pin_first_queries, pin_fig3, pin_fig5, pin_order_brute,
              pin_counts_closed_form, pin_brute_decode, pin_invariants,
-             pin_cap_boundary]
+             pin_cap_boundary, pin_1line_order_brute, pin_1line_generating_function,
+             pin_1line_is_basic_at_origin, pin_1line_brute_decode, pin_1line_invariants]
 
 
 def run_all(orc, pins=None):

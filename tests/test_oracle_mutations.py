@@ -20,9 +20,10 @@ MUTATIONS = [
     ("build_mountain_step5_dropped", "u[w - q] += r;", "(void)r;"),
     ("landslide_smallest_k", "for (k = w; k >= 1; k--)", "for (k = 1; k <= w; k++)"),
     ("cap_off_by_one", "if (d->t >= d->cap)", "if (d->t > d->cap)"),
-    ("hamming_weight_descending",
-     "for (w = 1; (long)w * (w + 1) / 2 <= W && w <= n; w++) {",
-     "for (w = n; w >= 1; w--) { if ((long)w * (w + 1) / 2 > W) continue;"),
+    ("hamming_weight_descending", "for (w = 1; w <= n; w++) {", "for (w = n; w >= 1; w--) {"),
+    ("rw_divisibility_dropped", "if ((R - J0 * w) % beta)", "if (0)"),
+    ("rw_hamming_term_dropped", "L = (R - J0 * w) / beta;", "L = R / beta;"),
+    ("rw_slope_on_hamming", "L = (R - J0 * w) / beta;", "L = (R - beta * w) / beta;"),
     ("vu_map_transposed", "v[i] = i + u[i];", "v[i] = i + u[w + 1 - i];"),
     ("flip_wrong_index", "c_out[pi[d.hit_v[i] - 1]] ^= 1;", "c_out[d.hit_v[i] - 1] ^= 1;"),
 ]
