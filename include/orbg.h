@@ -92,6 +92,20 @@ typedef struct orbg_codeset orbg_codeset; /* opaque, library-owned */
 ORBG_API int orbg_load_code(const uint8_t *mat, int kind, int n, int k,
                    uint32_t max_query_cap, orbg_code **out);
 
+/*
+ * One-line full ORBGRAND (Sec. III-D, Eq. relest_seg with one segment):
+ * as orbg_load_code, but the handle's query order sorts noise patterns by
+ * increasing reliability weight J0 w_H + beta w_L, the sorted position j
+ * counting J0 + beta j (Eq. wu_i), ties as for basic ORBGRAND (Hamming
+ * weight ascending, then lexicographic).  J0: 0..1024, beta: 1..1024;
+ * J0 = 0, beta = 1 is orbg_load_code.  Every decode entry point decodes
+ * in the handle's order.  Errors as orbg_load_code; EINVAL for J0 or beta
+ * out of range.
+ */
+ORBG_API int orbg_load_code_line(const uint8_t *mat, int kind, int n, int k,
+                                 uint32_t max_query_cap, int32_t J0, int32_t beta,
+                                 orbg_code **out);
+
 /* Release a handle (NULL is allowed).  Not stream-ordered: no decode call
  * using it may still be in flight. */
 ORBG_API int orbg_free_code(orbg_code *code);
@@ -337,7 +351,7 @@ ORBG_API int orbg_probe_smem_bytes(double *bytes_per_clk_per_sm);
  * same tables the kernels read (table 0: the one-warp-per-block table;
  * table 1: the CTA table of the batched form's second phase; both hold
  * the same order; table 2: the flat table of the leading patterns both
- * start with, which stops after at most 1024 patterns).  out: host memory, [count][n+1] int32 rows
+ * start with, which stops after at most 256 patterns).  out: host memory, [count][n+1] int32 rows
  * holding w, then the w flipped positions (1-based, in increasing
  * reliability order, ascending), then zeros.  Returns the number of rows
  * written (fewer than count once the 2^n patterns run out), or a negative
@@ -346,6 +360,10 @@ ORBG_API int orbg_probe_smem_bytes(double *bytes_per_clk_per_sm);
  */
 ORBG_API int64_t orbg_query_order(int n, uint32_t count, int table,
                                   int32_t *out);
+
+/* The same for the one-line order of orbg_load_code_line (Sec. III-D). */
+ORBG_API int64_t orbg_query_order_line(int n, uint32_t count, int table, int32_t J0,
+                                       int32_t beta, int32_t *out);
 
 /* Static description of a status code (never NULL). */
 ORBG_API const char *orbg_status_string(int status);

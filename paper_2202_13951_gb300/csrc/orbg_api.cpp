@@ -216,12 +216,19 @@ int orbg_version(void) { return 100; }
 
 int64_t orbg_query_order(int n, uint32_t count, int table, int32_t *out)
 {
-    if (n < 1 || n > ORBG_MAX_N || (count > 0 && !out) || table < 0 || table > 2)
+    return orbg_query_order_line(n, count, table, 0, 1, out);
+}
+
+int64_t orbg_query_order_line(int n, uint32_t count, int table, int32_t J0, int32_t beta,
+                              int32_t *out)
+{
+    if (n < 1 || n > ORBG_MAX_N || (count > 0 && !out) || table < 0 || table > 2 || J0 < 0 ||
+        beta < 1 || J0 > ORBG_MAX_LINE || beta > ORBG_MAX_LINE)
         return ORBG_EINVAL;
     if (count == 0)
         return 0;
     OrbgTables tb;
-    if (orbg_build_tables(n, count, &tb) != 0)
+    if (orbg_build_tables(n, count, &tb, J0, beta) != 0)
         return ORBG_ELIMIT;
     const std::vector<OrbgRun> &runs = table == 0 ? tb.runs : tb.runs_cta;
     const size_t stride = (size_t)n + 1;
@@ -307,9 +314,17 @@ int orbg_probe_smem_bytes(double *bytes_per_clk_per_sm)
 int orbg_load_code(const uint8_t *mat, int kind, int n, int k, uint32_t max_query_cap,
                    orbg_code **out)
 {
+    return orbg_load_code_line(mat, kind, n, k, max_query_cap, 0, 1, out);
+}
+
+int orbg_load_code_line(const uint8_t *mat, int kind, int n, int k, uint32_t max_query_cap,
+                        int32_t J0, int32_t beta, orbg_code **out)
+{
     if (!out)
         return ORBG_EINVAL;
     *out = nullptr;
+    if (J0 < 0 || beta < 1 || J0 > ORBG_MAX_LINE || beta > ORBG_MAX_LINE)
+        return ORBG_EINVAL;
     if (!mat || (kind != ORBG_MAT_H && kind != ORBG_MAT_G) || n < 1 || k < 0 || k >= n)
         return ORBG_EINVAL;
     if (n > ORBG_MAX_N || n - k > ORBG_MAX_R)
@@ -363,7 +378,7 @@ int orbg_load_code(const uint8_t *mat, int kind, int n, int k, uint32_t max_quer
             if (c->H[(size_t)i * n + j])
                 hcol[(size_t)j * c->w32 + i / 32] |= 1u << (i % 32);
     OrbgTables tb;
-    int trc = orbg_build_tables(n, cap, &tb);
+    int trc = orbg_build_tables(n, cap, &tb, J0, beta);
     if (trc != 0) {
         delete c;
         return ORBG_ELIMIT;

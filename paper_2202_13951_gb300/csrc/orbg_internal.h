@@ -112,7 +112,10 @@ struct OrbgTables {
     uint64_t patterns = 0;  /* query indices covered (last index) */
     int wmax_logistic = 0;  /* deepest logistic weight in the table */
 };
-int orbg_build_tables(int n, uint64_t cap, OrbgTables *out);
+/* The tables for the order of increasing reliability weight J0 w + beta W
+ * (one-line full ORBGRAND; J0 = 0, beta = 1 is basic ORBGRAND). */
+#define ORBG_MAX_LINE 1024
+int orbg_build_tables(int n, uint64_t cap, OrbgTables *out, long J0 = 0, long beta = 1);
 int orbg_run_pattern(const OrbgRun &r, int j, const uint32_t *trip, int *v);
 
 /* GF(2) helpers on dense 0/1 byte matrices (row-major). */

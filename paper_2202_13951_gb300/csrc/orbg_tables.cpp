@@ -46,6 +46,7 @@ struct Builder {
     std::vector<OrbgRun> cls;      /* runs of the current (W, w) class */
     int pre[64];
     bool overflow = false;
+    long J0 = 0, beta = 1;         /* the line: reliability J0 + beta j */
 
     OrbgRun blank(int kind, int npre) {
         OrbgRun r;
@@ -137,16 +138,29 @@ struct Builder {
         cls.clear();
     }
 
-    /* The whole order up to the class holding query `cap`. */
+    /* The whole order up to the class holding query `cap`: classes (W, w)
+     * of logistic weight W and Hamming weight w in increasing reliability
+     * weight R = J0 w + beta W (one-line full ORBGRAND, Sec. III-D; basic
+     * ORBGRAND is J0 = 0, beta = 1, R = W), w ascending within R. */
     int build(uint64_t cap, std::vector<OrbgRun> *out, uint64_t *patterns, int *wdeep) {
         t = 1;
-        single(0); /* W = 0: the zero pattern */
+        single(0); /* R = 0: the zero pattern */
         flush(out);
-        const long Wlast = (long)n * (n + 1) / 2;
-        for (long W = 1; W <= Wlast && t <= cap; W++) {
-            if (W > ORBG_MAX_LOGISTIC)
-                return -2;
-            for (int w = 1; (long)w * (w + 1) / 2 <= W && w <= n; w++) {
+        *wdeep = 0;
+        const long Rlast = J0 * n + beta * ((long)n * (n + 1) / 2);
+        for (long R = 1; R <= Rlast && t <= cap; R++) {
+            for (int w = 1; w <= n; w++) {
+                if (R - J0 * w < 0)
+                    break;                 /* larger w only weigh more */
+                if ((R - J0 * w) % beta)
+                    continue;              /* no integer logistic weight */
+                const long W = (R - J0 * w) / beta;
+                if (W < (long)w * (w + 1) / 2)
+                    break;                 /* below the lightest w-subset */
+                if (W > (long)w * (w + 1) / 2 + (long)w * (n - w))
+                    continue;              /* above the heaviest w-subset */
+                if (W > ORBG_MAX_LOGISTIC)
+                    return -2;
                 if (w == 1) {
                     if (W <= n) {
                         pre[0] = (int)W;
@@ -164,8 +178,8 @@ struct Builder {
                     prefixes(0, w - 2, 1, (int)W, 2);
                 }
                 flush(out);
+                *wdeep = std::max(*wdeep, (int)W);
             }
-            *wdeep = (int)W;
         }
         *patterns = t - 1;
         return overflow ? -2 : 0;
@@ -240,14 +254,17 @@ void floors(const std::vector<OrbgRun> &runs, std::vector<uint32_t> *out)
 
 }  // namespace
 
-int orbg_build_tables(int n, uint64_t cap, OrbgTables *out)
+int orbg_build_tables(int n, uint64_t cap, OrbgTables *out, long J0, long beta)
 {
-    if (n < 1 || n > 256 || cap < 1)
+    if (n < 1 || n > 256 || cap < 1 || J0 < 0 || beta < 1 || J0 > ORBG_MAX_LINE ||
+        beta > ORBG_MAX_LINE)
         return -1;
     /* warp table */
     Builder bw;
     bw.n = n;
     bw.cta = false;
+    bw.J0 = J0;
+    bw.beta = beta;
     out->runs.clear();
     uint64_t patterns = 0;
     int wdeep = 0;
@@ -283,6 +300,8 @@ int orbg_build_tables(int n, uint64_t cap, OrbgTables *out)
     Builder bc;
     bc.n = n;
     bc.cta = true;
+    bc.J0 = J0;
+    bc.beta = beta;
     bc.s3max = s3max;
     bc.x3off = &x3off;
     out->runs_cta.clear();

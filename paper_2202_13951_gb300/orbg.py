@@ -86,6 +86,7 @@ def load_library(path=None):
     i32 = ctypes.c_int
     i64 = ctypes.c_int64
     lib.orbg_load_code.argtypes = [vp, i32, i32, i32, u32, ctypes.POINTER(vp)]
+    lib.orbg_load_code_line.argtypes = [vp, i32, i32, i32, u32, i32, i32, ctypes.POINTER(vp)]
     lib.orbg_free_code.argtypes = [vp]
     lib.orbg_code_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(u32), vp]
@@ -106,6 +107,8 @@ def load_library(path=None):
     lib.orbg_version.argtypes = []
     lib.orbg_query_order.argtypes = [i32, u32, i32, vp]
     lib.orbg_query_order.restype = i64
+    lib.orbg_query_order_line.argtypes = [i32, u32, i32, i32, i32, vp]
+    lib.orbg_query_order_line.restype = i64
     lib.orbg_server_create.argtypes = [vp, ctypes.c_size_t, u32, i32, i64, ctypes.POINTER(vp)]
     lib.orbg_server_submit.argtypes = [vp, ctypes.c_uint64, i32, vp, i64]
     lib.orbg_server_poll.argtypes = [vp, vp, i32, i32]
@@ -115,7 +118,7 @@ def load_library(path=None):
     lib.orbg_server_destroy.argtypes = [vp]
     lib.orbg_server_replay.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                        ctypes.POINTER(ctypes.c_double)]
-    for f in ("orbg_load_code", "orbg_free_code", "orbg_code_info", "orbg_decode",
+    for f in ("orbg_load_code", "orbg_load_code_line", "orbg_free_code", "orbg_code_info", "orbg_decode",
               "orbg_codeset_create", "orbg_codeset_free", "orbg_decode_batched",
               "orbg_decode_batched_noalloc", "orbg_server_create", "orbg_server_submit",
               "orbg_server_poll", "orbg_server_fetch", "orbg_server_stats_get",
@@ -176,6 +179,16 @@ def orbg_load_code(mat, kind, n, k, max_query_cap=0):
     h = ctypes.c_void_p()
     _check(lib.orbg_load_code(m.ctypes.data, int(kind), int(n), int(k),
                               int(max_query_cap), ctypes.byref(h)), "orbg_load_code")
+    return h
+
+
+def orbg_load_code_line(mat, kind, n, k, max_query_cap, J0, beta):
+    lib = load_library()
+    m = np.ascontiguousarray(mat, dtype=np.uint8)
+    h = ctypes.c_void_p()
+    _check(lib.orbg_load_code_line(m.ctypes.data, int(kind), int(n), int(k),
+                                   int(max_query_cap), int(J0), int(beta), ctypes.byref(h)),
+           "orbg_load_code_line")
     return h
 
 
@@ -358,18 +371,34 @@ def orbg_query_order(n, count, table=0):
     return [tuple(int(x) for x in row[1:1 + row[0]]) for row in out[:got]]
 
 
+def orbg_query_order_line(n, count, table, J0, beta):
+    """orbg_query_order for the one-line order of reliability weight
+    J0 w_H + beta w_L."""
+    lib = load_library()
+    out = np.zeros((count, n + 1), np.int32)
+    got = lib.orbg_query_order_line(int(n), int(count), int(table), int(J0), int(beta),
+                                    out.ctypes.data)
+    if got < 0:
+        raise OrbgError(int(got), "orbg_query_order_line")
+    return [tuple(int(x) for x in row[1:1 + row[0]]) for row in out[:got]]
+
+
 # ------------------------------------------------------- convenience layer
 
 class Code:
     """Owning wrapper of an orbg_code handle."""
 
-    def __init__(self, mat, kind=ORBG_MAT_H, n=None, k=None, max_query_cap=0):
+    def __init__(self, mat, kind=ORBG_MAT_H, n=None, k=None, max_query_cap=0, line=None):
+        """line: (J0, beta) for one-line full ORBGRAND, None for basic."""
         mat = np.asarray(mat, dtype=np.uint8)
         n = mat.shape[1] if n is None else n
         if k is None:
             k = n - mat.shape[0] if kind == ORBG_MAT_H else mat.shape[0]
         self.n, self.k = int(n), int(k)
-        self.handle = orbg_load_code(mat, kind, n, k, max_query_cap)
+        if line is None:
+            self.handle = orbg_load_code(mat, kind, n, k, max_query_cap)
+        else:
+            self.handle = orbg_load_code_line(mat, kind, n, k, max_query_cap, *line)
 
     def close(self):
         if self.handle is not None and self.handle.value:

@@ -86,6 +86,10 @@ def test_decode_argument_checks_without_gpu(lib):
     assert lib.orbg_codeset_free(None) == orbg.ORBG_OK
     assert lib.orbg_probe_int_lanes(None) == orbg.ORBG_EINVAL
     assert lib.orbg_probe_smem_bytes(None) == orbg.ORBG_EINVAL
+    out = np.zeros((4, 8), np.int32)
+    for J0, beta in ((-1, 1), (0, 0), (2000, 1), (0, 2000)):
+        assert lib.orbg_query_order_line(7, 4, 0, J0, beta, out.ctypes.data) == orbg.ORBG_EINVAL
+        assert lib.orbg_load_code_line(None, 0, 7, 4, 0, J0, beta, None) == orbg.ORBG_EINVAL
 
 
 @pytest.mark.parametrize("n,count", [(1, 2), (3, 8), (7, 128), (12, 4096),
@@ -115,3 +119,18 @@ def test_query_order_depth_for_cap(lib):
         rows = orbg.orbg_query_order(n, total)
         assert len(rows) == total
         assert sum(rows[-1]) == 82 and sum(rows[0]) == 0
+
+
+@pytest.mark.parametrize("n,count", [(3, 8), (7, 128), (12, 4096), (40, 60000), (127, 60000),
+                                     (256, 20000)])
+@pytest.mark.parametrize("line", [(0, 1), (1, 1), (3, 1), (20, 1), (5, 2), (2, 3)],
+                         ids=lambda l: "J%d_b%d" % l)
+def test_query_order_line_tables_match_oracle(lib, n, count, line):
+    """The one-line tables (Sec. III-D) expand to exactly the one-line
+    oracle's order, in all three tables the kernels read."""
+    want = oracle.enumerate_patterns_1line(n, count, *line)
+    assert orbg.orbg_query_order_line(n, count, 0, *line) == want
+    assert orbg.orbg_query_order_line(n, count, 1, *line) == want
+    flat = orbg.orbg_query_order_line(n, count, 2, *line)
+    assert 0 < len(flat) <= 256
+    assert flat == want[:len(flat)]

@@ -313,6 +313,25 @@ def test_batched_call_in_cuda_graph(orbg):
                     want)
 
 
+@pytest.mark.parametrize("line", [(3, 1), (5, 2), (20, 1)], ids=lambda l: "J%d_b%d" % l)
+def test_one_line_orbgrand(orbg, line):
+    """One-line full ORBGRAND (Sec. III-D): codes loaded with a line decode,
+    in both forms, exactly as the one-line oracle."""
+    cap = 20000
+    for n, k, seed, ebn0 in ((64, 51, 91, 3.5), (127, 113, 92, 4.0)):
+        code = workloads.rlc(n, k, seed)
+        rng = np.random.default_rng(seed + 1)
+        llr = np.concatenate([tiny_inputs(n, rng, 20),
+                              workloads.awgn_llr(code, 180, ebn0, seed + 2)[0]])
+        want = oracle.decode_batch_1line(code.H, llr, cap, *line)[:3]
+        c = orbg.Code(code.H, max_query_cap=cap, line=line)
+        assert_same(gpu_plain(orbg, c, llr, cap), want)
+        cs = orbg.CodeSet([c])
+        assert_same(gpu_batched(orbg, cs, llr, cap), want)
+        orbg.orbg_codeset_set_tuning(cs.handle, orbg.OrbgTuning(8, 0, 1, 64, 8))
+        assert_same(gpu_batched(orbg, cs, llr, cap), want)
+
+
 def test_mixed_codes_one_launch_equals_alone(orbg):
     """Blocks of four codes with different n and n-k in one batched launch
     give what each code's blocks give alone, and what the oracle gives."""
