@@ -67,6 +67,8 @@ def parse_args(argv=None):
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--line", default="",
+                   help="J0,beta: decode one-line full ORBGRAND (Sec. III-D) instead of basic")
     p.add_argument("--no-graph", action="store_true",
                    help="time direct calls instead of replays of a captured CUDA graph")
     p.add_argument("--ref-sample", type=int, default=8000,
@@ -85,6 +87,10 @@ def parse_args(argv=None):
                         "for the batched launch (orbg_tuning)")
     args = p.parse_args(argv)
     select_workload(args.workload, args.blocks_per_point)
+    if args.line:
+        global LINE, WORKLOAD
+        LINE = tuple(int(x) for x in args.line.split(","))
+        WORKLOAD += ", one-line full ORBGRAND J0=%d beta=%d" % LINE
     return args
 
 
@@ -100,6 +106,7 @@ def select_workload(name, b_per_point):
 
 
 WORKLOAD_NAME = "bch"
+LINE = None  # (J0, beta) for one-line full ORBGRAND, None for basic
 
 
 CODE_FN = "config2_code"
@@ -153,12 +160,14 @@ def sum_over_ranks(value, world, device=None):
     return float(t.item())
 
 
-def class_weight_prefix(n, max_queries):
+def class_weight_prefix(n, max_queries, line=None):
     """Cumulative Hamming weight over the query order, by class: the order
-    visits logistic weights W = 0, 1, ... and within W Hamming weights w
-    ascending, a class (W, w) holding the partitions of W into w distinct
-    parts <= n.  Returns (class_end[], class_w[]) up to max_queries, so
-    sum_{t<=q} w_t follows from q alone."""
+    visits classes (W, w) -- the partitions of W into w distinct parts <= n
+    -- in increasing J0 w + beta W, w ascending within it (basic ORBGRAND:
+    J0 = 0, beta = 1, so logistic weights W = 0, 1, ...).  Returns
+    (class_end[], class_w[]) up to max_queries, so sum_{t<=q} w_t follows
+    from q alone."""
+    J0, beta = line if line else (0, 1)
     # N[w][W]: sets of w distinct parts in [1, n] summing to W (DP over parts)
     Wmax = 1
     while True:
@@ -168,18 +177,19 @@ def class_weight_prefix(n, max_queries):
         for part in range(1, min(n, Wmax) + 1):
             for w in range(Wmax, 0, -1):
                 N[w][part:] = N[w][part:] + N[w - 1][:Wmax + 1 - part]
-        total = sum(int(N[w][W]) for w in range(Wmax + 1) for W in range(Wmax + 1))
+        # classes of reliability weight <= beta Wmax are all within W <= Wmax
+        classes = sorted((J0 * w + beta * W, w, int(N[w][W]))
+                         for w in range(Wmax + 1) for W in range(Wmax + 1)
+                         if N[w][W] and J0 * w + beta * W <= beta * Wmax)
+        total = sum(c for _, _, c in classes)
         if total >= max_queries or Wmax > 4096:
             break
     ends, ws = [], []
     t = 0
-    for W in range(0, Wmax + 1):
-        for w in range(0, Wmax + 1):
-            c = int(N[w][W])
-            if c:
-                t += c
-                ends.append(t)
-                ws.append(w)
+    for _, w, c in classes:
+        t += c
+        ends.append(t)
+        ws.append(w)
         if t >= max_queries:
             break
     return np.array(ends, np.int64), np.array(ws, np.int64)
@@ -274,10 +284,13 @@ class ClockSampler:
 # ------------------------------------------------------------- CPU side
 
 def _oracle_worker(args):
-    H, llr, cap = args
+    H, llr, cap, line = args
     import oracle
     t = time.perf_counter()
-    _, q, ab, _ = oracle.decode_batch(H, llr, cap)
+    if line:
+        _, q, ab, _ = oracle.decode_batch_1line(H, llr, cap, *line)
+    else:
+        _, q, ab, _ = oracle.decode_batch(H, llr, cap)
     return time.perf_counter() - t, int(q.sum()), llr.shape[0]
 
 
@@ -295,12 +308,12 @@ def cpu_sample(llr, per_point, step):
 def run_oracle(H, llr, cap, procs):
     """Decode llr on `procs` spawned single-threaded oracle processes."""
     if procs <= 1:
-        return _oracle_worker((H, llr, cap))
+        return _oracle_worker((H, llr, cap, LINE))
     import multiprocessing as mp
     chunks = np.array_split(llr, procs)
     ctx = mp.get_context("spawn")
     with ctx.Pool(procs) as pool:
-        res = pool.map(_oracle_worker, [(H, c, cap) for c in chunks])
+        res = pool.map(_oracle_worker, [(H, c, cap, LINE) for c in chunks])
     return max(r[0] for r in res), sum(r[1] for r in res), sum(r[2] for r in res)
 
 
@@ -335,7 +348,7 @@ def bench_reference(args, rank, world):
             sample = cpu_sample(llr, per_point, s)
             chunks = np.array_split(sample, cores)
             t0 = time.perf_counter()
-            res = pool.map(_oracle_worker, [(code.H, c, CAP) for c in chunks])
+            res = pool.map(_oracle_worker, [(code.H, c, CAP, LINE) for c in chunks])
             dt = time.perf_counter() - t0
             if s >= args.warmup:
                 times.append(dt)
@@ -397,7 +410,7 @@ class Job:
             raise SystemExit("--form plain needs a single-code workload")
         self.B = B
         self.n_of_block = np.array([c.n for c in self.codes], np.int64)[self.cid_np]
-        self.objs = [orbg.Code(c.H, max_query_cap=CAP) for c in self.codes]
+        self.objs = [orbg.Code(c.H, max_query_cap=CAP, line=LINE) for c in self.codes]
         self.cs = orbg.CodeSet(self.objs)
         self.llr = torch.from_numpy(self.llr_np).to(dev)
         n_total = int(self.n_of_block.sum())
@@ -455,7 +468,7 @@ class Job:
             sel = self.cid_np == j
             if not sel.any():
                 continue
-            ends, ws = class_weight_prefix(code.n, CAP)
+            ends, ws = class_weight_prefix(code.n, CAP, LINE)
             qj = qh[sel]
             w32 = (code.r + 31) // 32
             total += w32 * (sum_weights(qj, ends, ws) + int(qj.sum()))
@@ -568,6 +581,8 @@ def bench_ours(args, rank, world, local):
                              ">" if job.llr_np.nbytes > 129e6 else "<=")),
                    "tuning": orbg.orbg_codeset_get_tuning(job.cs.handle).as_dict(),
                    "tuning_source": tuned, "timed": graph,
+                   "order": ("one-line full ORBGRAND, J0=%d beta=%d" % LINE) if LINE
+                   else "basic ORBGRAND",
                    "parallelism": "replicas x%d (blocks sharded by rank, no collective)" % world},
         "queries_per_s": queries_total / (total_ms / 1000.0),
         "latency_ms": {"step_p50": statistics.median(per_step),

@@ -59,3 +59,18 @@ def test_class_weight_prefix_matches_oracle():
     _, q, _, sw = oracle.decode_batch(code.H, llr, 10 ** 5)
     ends, ws = bench.class_weight_prefix(code.n, 10 ** 5)
     assert bench.sum_weights(q, ends, ws) == int(sw.sum())
+
+
+
+@pytest.mark.parametrize("line", [(3, 1), (5, 2), (20, 1)])
+def test_class_weight_prefix_one_line_matches_oracle(line):
+    """The bench's per-query Hamming-weight sums in the one-line order
+    (Sec. III-D) equal the one-line oracle's own count."""
+    import bench
+    import oracle
+    from paper_2202_13951_gb300 import workloads
+    code = workloads.rlc(64, 48, 5)
+    llr, _ = workloads.awgn_llr(code, 150, 3.0, 7)
+    _, q, _, sw = oracle.decode_batch_1line(code.H, llr, 10 ** 5, *line)
+    ends, ws = bench.class_weight_prefix(code.n, 10 ** 5, line)
+    assert bench.sum_weights(q, ends, ws) == int(sw.sum())
