@@ -16,6 +16,11 @@ Functions and the passages they follow:
                          one-line full ORBGRAND (Sec. III-D, Eq. relest_seg
                          with m = 1, Eq. wu_i): the order of increasing
                          reliability weight J0 w_H + beta w_L
+  decode_batch_mline / enumerate_patterns_mline
+                         m-segment full ORBGRAND (Sec. III-D: Eq.
+                         relest_seg, Algorithm 3 splits checked by
+                         Algorithm 4 / Eq. wi_cond, Landslide per segment,
+                         the Cartesian product of Eq. cartP)
 
 Parity pins: tests/test_oracle_pins.py (brute force on tiny codes, the
 first queries of Sec. III-B, the Fig. 3 / Fig. 5 examples, closed-form
@@ -26,12 +31,14 @@ mistakes must fail a pin).
 """
 from .oracle import (Oracle, OracleError, build_oracle, compile_oracle,
                      count_by_weight, decode, decode_1line, decode_batch,
-                     decode_batch_1line, default, enumerate_patterns,
-                     enumerate_patterns_1line, landslide, sort_reliability,
+                     decode_batch_1line, decode_batch_mline, default,
+                     enumerate_patterns, enumerate_patterns_1line,
+                     enumerate_patterns_mline, landslide, sort_reliability,
                      ORACLE_LIB, ORACLE_SRC)
 
 __all__ = ["Oracle", "OracleError", "build_oracle", "compile_oracle",
            "count_by_weight", "decode", "decode_1line", "decode_batch",
-           "decode_batch_1line", "default", "enumerate_patterns",
-           "enumerate_patterns_1line", "landslide", "sort_reliability",
+           "decode_batch_1line", "decode_batch_mline", "default",
+           "enumerate_patterns", "enumerate_patterns_1line",
+           "enumerate_patterns_mline", "landslide", "sort_reliability",
            "ORACLE_LIB", "ORACLE_SRC"]

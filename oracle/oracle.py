@@ -87,6 +87,14 @@ class Oracle:
                                                        ctypes.c_long, ctypes.c_long, u8p,
                                                        u64p, u8p, u64p]
         lib.orbg_oracle_decode_batch_1line.restype = ctypes.c_int
+        lib.orbg_oracle_enumerate_mline.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i64p,
+                                                    i64p, ctypes.c_long, i32p]
+        lib.orbg_oracle_enumerate_mline.restype = ctypes.c_long
+        lib.orbg_oracle_decode_batch_mline.argtypes = [u8p, ctypes.c_int, ctypes.c_int, f32p,
+                                                       ctypes.c_long, ctypes.c_uint64,
+                                                       ctypes.c_int, i32p, i64p, i64p, u8p,
+                                                       u64p, u8p, u64p]
+        lib.orbg_oracle_decode_batch_mline.restype = ctypes.c_int
         self.lib = lib
         self.path = path
 
@@ -183,6 +191,47 @@ class Oracle:
             raise OracleError("enumerate failed: %d" % got)
         return [tuple(int(x) for x in row[1:1 + row[0]]) for row in out[:got]]
 
+    @staticmethod
+    def _model(model):
+        """(anchors I_1..I_{m-1}, J_0..J_{m-1}, beta_1..beta_m) as C arrays."""
+        anchors, J, beta = model
+        m = len(J)
+        assert len(beta) == m and len(anchors) == m - 1
+        a = np.array(list(anchors) + [0], np.int32)
+        return m, a, np.array(J, np.int64), np.array(beta, np.int64)
+
+    def enumerate_patterns_mline(self, n, count, model):
+        """First `count` patterns of the m-segment order (Sec. III-D), as
+        tuples of 1-based sorted-order positions.  model = (anchors, J, beta)."""
+        m, a, J, beta = self._model(model)
+        out = np.zeros((count, n + 1), np.int32)
+        got = self.lib.orbg_oracle_enumerate_mline(
+            n, m, _ptr(a, ctypes.c_int), J.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+            beta.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), count, _ptr(out, ctypes.c_int))
+        if got < 0:
+            raise OracleError("enumerate failed: %d" % got)
+        return [tuple(int(x) for x in row[1:1 + row[0]]) for row in out[:got]]
+
+    def decode_batch_mline(self, H, llr, cap, model):
+        """decode_batch() for m-segment full ORBGRAND."""
+        m, a, J, beta = self._model(model)
+        H = np.ascontiguousarray(H, dtype=np.uint8)
+        r, n = H.shape
+        llr = np.ascontiguousarray(llr, dtype=np.float32).reshape(-1, n)
+        B = llr.shape[0]
+        c = np.zeros((B, n), np.uint8)
+        q = np.zeros(B, np.uint64)
+        ab = np.zeros(B, np.uint8)
+        sw = np.zeros(B, np.uint64)
+        rc = self.lib.orbg_oracle_decode_batch_mline(
+            _ptr(H, ctypes.c_uint8), n, r, _ptr(llr, ctypes.c_float), B, int(cap), m,
+            _ptr(a, ctypes.c_int), J.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+            beta.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), _ptr(c, ctypes.c_uint8),
+            _ptr(q, ctypes.c_uint64), _ptr(ab, ctypes.c_uint8), _ptr(sw, ctypes.c_uint64))
+        if rc != 0:
+            raise OracleError("oracle m-line batch decode failed: %d" % rc)
+        return c, q, ab, sw
+
     def enumerate_patterns(self, n, count):
         """First `count` patterns of the query order for length n, as tuples
         of 1-based sorted-order positions (the zero pattern is ())."""
@@ -265,3 +314,11 @@ def decode_batch_1line(H, llr, cap, J0, beta):
 
 def enumerate_patterns_1line(n, count, J0, beta):
     return default().enumerate_patterns_1line(n, count, J0, beta)
+
+
+def enumerate_patterns_mline(n, count, model):
+    return default().enumerate_patterns_mline(n, count, model)
+
+
+def decode_batch_mline(H, llr, cap, model):
+    return default().decode_batch_mline(H, llr, cap, model)

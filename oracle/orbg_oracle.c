@@ -401,9 +401,23 @@ static void orc_sort_by_reliability(const float *llr, int n, int *pi)
  *             the sorted order.
  * Returns 0, or ORC_ENAN if an LLR is NaN, ORC_EINVAL on bad sizes.
  */
-static int orc_decode_rw(const uint8_t *H, int n, int r, const float *llr, uint64_t cap,
-                         long J0, long beta, uint8_t *c_out, uint64_t *q_out, int *abandon,
-                         uint64_t *sum_w, int *hit_w, int *hit_v)
+/* A query order: walks the patterns of length n, calling fn on each. */
+typedef int (*orc_walker)(int n, const void *order, orc_pattern_fn fn, void *ctx);
+
+typedef struct {
+    long J0, beta;
+} orc_line;
+
+static int orc_walk_line(int n, const void *order, orc_pattern_fn fn, void *ctx)
+{
+    const orc_line *l = (const orc_line *)order;
+    return orc_walk_rw(n, l->J0, l->beta, fn, ctx);
+}
+
+static int orc_decode_walk(const uint8_t *H, int n, int r, const float *llr, uint64_t cap,
+                           orc_walker walk, const void *order, uint8_t *c_out,
+                           uint64_t *q_out, int *abandon, uint64_t *sum_w, int *hit_w,
+                           int *hit_v)
 {
     static uint64_t col[ORC_MAX_N * ORC_MAX_WORDS];
     int pi[ORC_MAX_N];
@@ -411,8 +425,7 @@ static int orc_decode_rw(const uint8_t *H, int n, int r, const float *llr, uint6
     orc_dec_ctx d;
     int i, j, words;
 
-    if (n < 1 || n > ORC_MAX_N || r < 1 || r > 64 * ORC_MAX_WORDS || cap < 1 || J0 < 0 ||
-        beta < 1)
+    if (n < 1 || n > ORC_MAX_N || r < 1 || r > 64 * ORC_MAX_WORDS || cap < 1)
         return ORC_EINVAL;
     for (i = 0; i < n; i++)
         if (isnan(llr[i]))
@@ -440,7 +453,7 @@ static int orc_decode_rw(const uint8_t *H, int n, int r, const float *llr, uint6
             for (j = 0; j < words; j++)
                 d.s0[j] ^= col[(size_t)i * words + j];
 
-    orc_walk_rw(n, J0, beta, orc_dec_visit, &d);
+    walk(n, order, orc_dec_visit, &d);
 
     for (i = 0; i < n; i++)
         c_out[i] = y[i];
@@ -461,6 +474,20 @@ static int orc_decode_rw(const uint8_t *H, int n, int r, const float *llr, uint6
         for (i = 0; i < d.hit_w; i++)
             hit_v[i] = d.hit_v[i];
     return ORC_OK;
+}
+
+/* One block in the one-line order (J0 >= 0, beta >= 1). */
+static int orc_decode_rw(const uint8_t *H, int n, int r, const float *llr, uint64_t cap,
+                         long J0, long beta, uint8_t *c_out, uint64_t *q_out, int *abandon,
+                         uint64_t *sum_w, int *hit_w, int *hit_v)
+{
+    orc_line l;
+    if (J0 < 0 || beta < 1)
+        return ORC_EINVAL;
+    l.J0 = J0;
+    l.beta = beta;
+    return orc_decode_walk(H, n, r, llr, cap, orc_walk_line, &l, c_out, q_out, abandon, sum_w,
+                           hit_w, hit_v);
 }
 
 /* Basic ORBGRAND (the order of increasing logistic weight). */
@@ -506,6 +533,349 @@ int orbg_oracle_decode_batch(const uint8_t *H, int n, int r, const float *llr,
 {
     return orbg_oracle_decode_batch_1line(H, n, r, llr, B, cap, 0, 1, c_out, q_out, abandon,
                                           sum_w);
+}
+
+/* ------------------------------------------------------------------ */
+/* Full ORBGRAND with m segments (Sec. III-D).                          */
+/* ------------------------------------------------------------------ */
+
+/*
+ * The piece-wise linear model (Eq. relest_seg): anchors 0 = I_0 < I_1 <
+ * ... < I_m = n; sorted position j in segment i (I_{i-1} < j <= I_i) counts
+ * J_{i-1} + beta_i (j - I_{i-1}).  A pattern's reliability weight is the
+ * sum over its flipped positions; queries go in increasing weight.  For a
+ * weight R (the paper's W) the oracle follows the paper's construction:
+ * every split R = W_1 + ... + W_m (Algorithm 3, nested sweeps of W_1 ..
+ * W_{m-1}), each W_i checked against its valid partial Hamming weights
+ * (Algorithm 4 with Eq. wi_cond, the bounds applying to the partial
+ * logistic weight (W_i - w_i J_{i-1}) / beta_i, Eq. wu_i), each segment's
+ * partial patterns from Landslide, and their Cartesian product
+ * (Eq. cartP).  Readings: J_{i-1} >= 0 and beta_i >= 1; the patterns of
+ * one weight are visited in the canonical order of the other decoders
+ * (Hamming weight ascending, then positions lexicographically), since the
+ * paper leaves the order inside a weight free.
+ */
+#define ORC_MAX_SEG 8
+
+typedef struct {
+    int m;
+    int I[ORC_MAX_SEG + 1];    /* anchors, I[0] = 0, I[m] = n */
+    long J[ORC_MAX_SEG];       /* J_{i-1} of segment i, at index i-1 */
+    long beta[ORC_MAX_SEG];    /* beta_i of segment i, at index i-1 */
+} orc_model;
+
+/* Patterns of one reliability weight, collected before they are ordered. */
+typedef struct {
+    int *pos;                  /* all positions, pattern after pattern */
+    long *start;               /* start[k]: offset of pattern k in pos */
+    int *len;                  /* Hamming weight of pattern k */
+    long npat, cap_pat, npos, cap_pos;
+} orc_bucket;
+
+static int orc_bucket_add(orc_bucket *b, const int *v, int w)
+{
+    if (b->npat == b->cap_pat) {
+        long c = b->cap_pat ? 2 * b->cap_pat : 1024;
+        long *s2 = (long *)realloc(b->start, sizeof(long) * (size_t)c);
+        int *l2 = (int *)realloc(b->len, sizeof(int) * (size_t)c);
+        if (!s2 || !l2) {
+            if (s2) b->start = s2;
+            if (l2) b->len = l2;
+            return ORC_EINVAL;
+        }
+        b->start = s2;
+        b->len = l2;
+        b->cap_pat = c;
+    }
+    if (b->npos + w > b->cap_pos) {
+        long c = b->cap_pos ? 2 * b->cap_pos : 4096;
+        int *p2;
+        while (c < b->npos + w)
+            c *= 2;
+        p2 = (int *)realloc(b->pos, sizeof(int) * (size_t)c);
+        if (!p2)
+            return ORC_EINVAL;
+        b->pos = p2;
+        b->cap_pos = c;
+    }
+    b->start[b->npat] = b->npos;
+    b->len[b->npat] = w;
+    memcpy(b->pos + b->npos, v, sizeof(int) * (size_t)w);
+    b->npos += w;
+    b->npat += 1;
+    return ORC_OK;
+}
+
+/* State of one weight's construction: the split, chosen Hamming weights,
+ * and the partial patterns fixed so far (absolute positions, ascending). */
+typedef struct {
+    const orc_model *md;
+    int n;
+    long W[ORC_MAX_SEG];
+    int w[ORC_MAX_SEG];
+    int v[ORC_MAX_N];
+    int nv;
+    int seg;                   /* segment being filled */
+    orc_bucket *bucket;
+    int err;
+} orc_seg_ctx;
+
+static int orc_fill_segment(orc_seg_ctx *c);
+
+/* Landslide visitor for segment c->seg: append its partial pattern and
+ * go on with the next segment. */
+static int orc_seg_visit(const int *u, int w, void *vctx)
+{
+    orc_seg_ctx *c = (orc_seg_ctx *)vctx;
+    const int i = c->seg, base = c->md->I[i];
+    int k, keep = c->nv, rc;
+    for (k = 1; k <= w; k++)
+        c->v[c->nv++] = base + k + u[k];     /* Eq. vu, shifted into segment i */
+    c->seg = i + 1;
+    rc = orc_fill_segment(c);
+    c->seg = i;
+    c->nv = keep;
+    return rc;
+}
+
+/* Cartesian product over segments seg .. m-1 (Eq. cartP). */
+static int orc_fill_segment(orc_seg_ctx *c)
+{
+    const orc_model *md = c->md;
+    const int i = c->seg;
+    long L;
+    int ni, w;
+    if (i == md->m)
+        return orc_bucket_add(c->bucket, c->v, c->nv) ? (c->err = 1, ORC_STOP) : 0;
+    w = c->w[i];
+    if (w == 0)                              /* W_i = 0: nothing flipped here */
+    {
+        int rc;
+        c->seg = i + 1;
+        rc = orc_fill_segment(c);
+        c->seg = i;
+        return rc;
+    }
+    ni = md->I[i + 1] - md->I[i];
+    L = (c->W[i] - (long)w * md->J[i]) / md->beta[i];   /* Eq. wu_i */
+    return orc_landslide((int)(L - (long)w * (w + 1) / 2), w, ni - w, orc_seg_visit, c);
+}
+
+/* Algorithm 4: is w a valid partial Hamming weight for W_i in segment i
+ * (Eq. wi_cond, bounds on the partial logistic weight)? */
+static int orc_valid_w(const orc_model *md, int i, long Wi, int w)
+{
+    const int ni = md->I[i + 1] - md->I[i];
+    long rem, L;
+    if (w > ni)
+        return 0;
+    rem = Wi - (long)w * md->J[i];
+    if (rem < 0 || rem % md->beta[i])
+        return 0;
+    L = rem / md->beta[i];
+    return L >= (long)w * (w + 1) / 2 && L <= (long)(ni + 1) * w - (long)w * (w + 1) / 2;
+}
+
+/* For a complete split: every choice of valid partial Hamming weights. */
+static int orc_choose_w(orc_seg_ctx *c, int i)
+{
+    const orc_model *md = c->md;
+    int w, rc;
+    if (i == md->m) {
+        c->seg = 0;
+        c->nv = 0;
+        return orc_fill_segment(c);
+    }
+    if (c->W[i] == 0) {
+        c->w[i] = 0;
+        return orc_choose_w(c, i + 1);
+    }
+    for (w = 1; w <= md->I[i + 1] - md->I[i]; w++) {
+        if (!orc_valid_w(md, i, c->W[i], w))
+            continue;
+        c->w[i] = w;
+        rc = orc_choose_w(c, i + 1);
+        if (rc)
+            return rc;
+    }
+    return 0;
+}
+
+/* Algorithm 3: sweep W_1 .. W_{m-1} (W_m is the rest); a non-zero W_i
+ * without a valid partial Hamming weight is skipped (Algorithm 4). */
+static int orc_split(orc_seg_ctx *c, int i, long left)
+{
+    const orc_model *md = c->md;
+    long Wi;
+    int w, ok, rc;
+    if (i == md->m - 1) {
+        c->W[i] = left;
+        Wi = left;
+        ok = Wi == 0;
+        for (w = 1; !ok && w <= md->I[i + 1] - md->I[i]; w++)
+            ok = orc_valid_w(md, i, Wi, w);
+        return ok ? orc_choose_w(c, 0) : 0;
+    }
+    for (Wi = 0; Wi <= left; Wi++) {
+        ok = Wi == 0;
+        for (w = 1; !ok && w <= md->I[i + 1] - md->I[i]; w++)
+            ok = orc_valid_w(md, i, Wi, w);
+        if (!ok)
+            continue;
+        c->W[i] = Wi;
+        rc = orc_split(c, i + 1, left - Wi);
+        if (rc)
+            return rc;
+    }
+    return 0;
+}
+
+/* Canonical order inside one weight: Hamming weight, then positions. */
+static const orc_bucket *orc_sort_bucket;
+static int orc_cmp_pattern(const void *a, const void *b)
+{
+    const long ka = *(const long *)a, kb = *(const long *)b;
+    const orc_bucket *bk = orc_sort_bucket;
+    const int la = bk->len[ka], lb = bk->len[kb];
+    const int *pa = bk->pos + bk->start[ka], *pb = bk->pos + bk->start[kb];
+    int i;
+    if (la != lb)
+        return la < lb ? -1 : 1;
+    for (i = 0; i < la; i++)
+        if (pa[i] != pb[i])
+            return pa[i] < pb[i] ? -1 : 1;
+    return 0;
+}
+
+static int orc_check_model(const orc_model *md, int n)
+{
+    int i;
+    if (md->m < 1 || md->m > ORC_MAX_SEG || md->I[0] != 0 || md->I[md->m] != n)
+        return 0;
+    for (i = 0; i < md->m; i++)
+        if (md->I[i + 1] <= md->I[i] || md->J[i] < 0 || md->beta[i] < 1)
+            return 0;
+    return 1;
+}
+
+/* Walk every pattern in increasing reliability weight under model md. */
+static int orc_walk_model(int n, const orc_model *md, orc_pattern_fn fn, void *ctx)
+{
+    long Rmax = 0, R, k;
+    int i, j, rc = 0;
+    orc_bucket b;
+    orc_seg_ctx c;
+    long *order = NULL;
+    for (i = 0; i < md->m; i++)
+        for (j = md->I[i] + 1; j <= md->I[i + 1]; j++)
+            Rmax += md->J[i] + md->beta[i] * (j - md->I[i]);
+    memset(&b, 0, sizeof(b));
+    rc = fn(NULL, 0, ctx);                   /* R = 0: nothing flipped */
+    for (R = 1; R <= Rmax && !rc; R++) {
+        memset(&c, 0, sizeof(c));
+        c.md = md;
+        c.n = n;
+        c.bucket = &b;
+        b.npat = 0;
+        b.npos = 0;
+        orc_split(&c, 0, R);
+        if (c.err) {
+            rc = ORC_EINVAL;
+            break;
+        }
+        if (b.npat == 0)
+            continue;
+        order = (long *)realloc(order, sizeof(long) * (size_t)b.npat);
+        if (!order) {
+            rc = ORC_EINVAL;
+            break;
+        }
+        for (k = 0; k < b.npat; k++)
+            order[k] = k;
+        orc_sort_bucket = &b;
+        qsort(order, (size_t)b.npat, sizeof(long), orc_cmp_pattern);
+        for (k = 0; k < b.npat && !rc; k++)
+            rc = fn(b.pos + b.start[order[k]], b.len[order[k]], ctx);
+    }
+    free(order);
+    free(b.pos);
+    free(b.start);
+    free(b.len);
+    return rc < 0 ? rc : ORC_OK;
+}
+
+static void orc_fill_model(orc_model *md, int m, const int *anchors, const long *J,
+                           const long *beta, int n)
+{
+    int i;
+    memset(md, 0, sizeof(*md));
+    md->m = m;
+    md->I[0] = 0;
+    for (i = 1; i < m && i < ORC_MAX_SEG; i++)
+        md->I[i] = anchors[i - 1];
+    if (m >= 1 && m <= ORC_MAX_SEG)
+        md->I[m] = n;
+    for (i = 0; i < m && i < ORC_MAX_SEG; i++) {
+        md->J[i] = J[i];
+        md->beta[i] = beta[i];
+    }
+}
+
+/*
+ * m-segment full ORBGRAND (Sec. III-D).
+ *   anchors: I_1 .. I_{m-1} (I_0 = 0 and I_m = n implied), increasing;
+ *   J:       J_0 .. J_{m-1};  beta: beta_1 .. beta_m.
+ * Other arguments as orbg_oracle_decode_batch / _enumerate.
+ */
+long orbg_oracle_enumerate_mline(int n, int m, const int *anchors, const long *J,
+                                 const long *beta, long count, int *out)
+{
+    orc_model md;
+    orc_enum_ctx e;
+    if (n < 1 || n > ORC_MAX_N || count < 0 || (count > 0 && !out))
+        return ORC_EINVAL;
+    orc_fill_model(&md, m, anchors, J, beta, n);
+    if (!orc_check_model(&md, n))
+        return ORC_EINVAL;
+    if (count == 0)
+        return 0;
+    e.out = out;
+    e.stride = n + 1;
+    e.count = count;
+    e.done = 0;
+    orc_walk_model(n, &md, orc_enum_visit, &e);
+    return e.done;
+}
+
+static int orc_walk_model_fn(int n, const void *order, orc_pattern_fn fn, void *ctx)
+{
+    return orc_walk_model(n, (const orc_model *)order, fn, ctx);
+}
+
+int orbg_oracle_decode_batch_mline(const uint8_t *H, int n, int r, const float *llr, long B,
+                                   uint64_t cap, int m, const int *anchors, const long *J,
+                                   const long *beta, uint8_t *c_out, uint64_t *q_out,
+                                   uint8_t *abandon, uint64_t *sum_w)
+{
+    orc_model md;
+    long b;
+    if (n < 1 || n > ORC_MAX_N)
+        return ORC_EINVAL;
+    orc_fill_model(&md, m, anchors, J, beta, n);
+    if (!orc_check_model(&md, n))
+        return ORC_EINVAL;
+    for (b = 0; b < B; b++) {
+        int ab = 0, rc;
+        uint64_t sw = 0;
+        rc = orc_decode_walk(H, n, r, llr + (size_t)b * n, cap, orc_walk_model_fn, &md,
+                             c_out + (size_t)b * n, q_out + b, &ab, &sw, NULL, NULL);
+        if (rc)
+            return rc;
+        abandon[b] = (uint8_t)ab;
+        if (sum_w)
+            sum_w[b] = sw;
+    }
+    return ORC_OK;
 }
 
 /* The permutation of Sec. III-A alone, for tests. */

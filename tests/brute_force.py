@@ -79,3 +79,47 @@ def decode_1line(H, llr, cap, J0, beta):
         if not ((H @ c.astype(np.int64)) % 2).any():
             return c, t, 0
     return y.copy(), len(order), 1
+
+
+def model_weights(n, model):
+    """rho_j for sorted positions j = 1..n under the piece-wise linear model
+    (anchors I_1..I_{m-1}, J_0..J_{m-1}, beta_1..beta_m) of Eq. relest_seg."""
+    anchors, J, beta = model
+    I = [0] + list(anchors) + [n]
+    rho = []
+    for i in range(len(J)):
+        for j in range(I[i] + 1, I[i + 1] + 1):
+            rho.append(J[i] + beta[i] * (j - I[i]))
+    return rho
+
+
+def query_order_model(n, model):
+    """All subsets of {1..n} sorted by (sum of rho over the subset, Hamming
+    weight, positions lexicographically): m-segment full ORBGRAND with the
+    canonical tie order."""
+    rho = model_weights(n, model)
+    pats = []
+    for mask in range(1 << n):
+        v = tuple(i + 1 for i in range(n) if (mask >> i) & 1)
+        pats.append((sum(rho[p - 1] for p in v), len(v), v))
+    pats.sort()
+    return [p[2] for p in pats]
+
+
+def decode_model(H, llr, cap, model):
+    """decode() in the m-segment order.  Returns (codeword, queries, abandoned)."""
+    H = np.asarray(H, dtype=np.int64)
+    llr = np.asarray(llr, dtype=np.float32)
+    n = llr.shape[0]
+    y = (llr > 0).astype(np.uint8)
+    pi = reliability_order(llr)
+    order = query_order_model(n, model)
+    for t, v in enumerate(order, start=1):
+        if t > cap:
+            return y.copy(), cap, 1
+        c = y.copy()
+        for p in v:
+            c[pi[p - 1]] ^= 1
+        if not ((H @ c.astype(np.int64)) % 2).any():
+            return c, t, 0
+    return y.copy(), len(order), 1

@@ -357,10 +357,77 @@ def pin_1line_invariants(orc):
                 assert not ((code.H.astype(np.int64) @ c) % 2).any()
 
 
+# ------------------------------------------- m-segment full ORBGRAND
+
+# (anchors, J, beta) for n = 10 (anchors inside 1..9); includes one
+# segment, zero intercepts, J divisible and not divisible by beta
+MODELS10 = [((), (0,), (1,)), ((), (4,), (3,)), ((3,), (0, 4), (1, 2)),
+            ((2, 6), (0, 3, 6), (1, 1, 2)), ((4, 7), (1, 6, 9), (2, 3, 1)),
+            ((1, 2, 5), (0, 2, 5, 9), (1, 2, 1, 3))]
+
+
+def pin_mline_order_brute(orc):
+    """The whole m-segment order for n = 10 equals sorting all subsets by
+    (sum of the model's reliabilities, w, lexicographic) (Sec. III-D)."""
+    for model in MODELS10:
+        got = orc.enumerate_patterns_mline(10, 1 << 10, model)
+        assert got == brute_force.query_order_model(10, model), model
+
+
+def pin_mline_generating_function(orc):
+    """For n = 30, the first patterns' reliability weights are
+    non-decreasing and their counts per weight are the coefficients of
+    prod_j (1 + x^rho_j)."""
+    n, Rmax = 30, 45
+    for model in (((10, 20), (0, 4, 9), (1, 1, 2)), ((12,), (2, 7), (1, 3))):
+        rho = brute_force.model_weights(n, model)
+        c = [0] * (Rmax + 1)
+        c[0] = 1
+        for e in rho:
+            for R in range(Rmax, e - 1, -1):
+                c[R] += c[R - e]
+        total = sum(c)
+        pats = orc.enumerate_patterns_mline(n, total, model)
+        rw = [sum(rho[p - 1] for p in v) for v in pats]
+        assert len(pats) == total and rw == sorted(rw) and rw[-1] <= Rmax
+        hist = [0] * (Rmax + 1)
+        for R in rw:
+            hist[R] += 1
+        assert hist == c, model
+
+
+def pin_mline_one_segment_is_one_line(orc):
+    """One segment is the one-line order (Eq. relest_seg with m = 1)."""
+    for J0, beta in ((0, 1), (3, 1), (5, 2)):
+        assert (orc.enumerate_patterns_mline(40, 5000, ((), (J0,), (beta,))) ==
+                orc.enumerate_patterns_1line(40, 5000, J0, beta))
+    code = workloads.rlc(24, 16, seed=5)
+    llr, _ = workloads.awgn_llr(code, 30, 2.5, seed=9)
+    a = orc.decode_batch_1line(code.H, llr, 3000, 3, 1)
+    b = orc.decode_batch_mline(code.H, llr, 3000, ((), (3,), (1,)))
+    for x, y in zip(a, b):
+        assert (x == y).all()
+
+
+def pin_mline_brute_decode(orc, blocks=30):
+    """m-segment oracle = brute force on a seeded random (10,6) code."""
+    rng = np.random.default_rng(23)
+    code = workloads.rlc(10, 6, seed=10)
+    for model in MODELS10[2:]:
+        llrs = np.stack(_tiny_inputs(code, rng, blocks))
+        for cap in (1, 3, 17, 1 << 10):
+            c1, q1, a1, _ = orc.decode_batch_mline(code.H, llrs, cap, model)
+            for b in range(blocks):
+                c0, q0, a0 = brute_force.decode_model(code.H, llrs[b], cap, model)
+                assert (c0 == c1[b]).all() and q0 == q1[b] and a0 == a1[b], (model, cap)
+
+
 FAST_PINS = [pin_first_queries, pin_fig3, pin_fig5, pin_order_brute,
              pin_counts_closed_form, pin_brute_decode, pin_invariants,
              pin_cap_boundary, pin_1line_order_brute, pin_1line_generating_function,
-             pin_1line_is_basic_at_origin, pin_1line_brute_decode, pin_1line_invariants]
+             pin_1line_is_basic_at_origin, pin_1line_brute_decode, pin_1line_invariants,
+             pin_mline_order_brute, pin_mline_generating_function,
+             pin_mline_one_segment_is_one_line, pin_mline_brute_decode]
 
 
 def run_all(orc, pins=None):

@@ -16,7 +16,10 @@ MUTATIONS = [
     ("sort_descending", "if (rj > rk ||", "if (rj < rk ||"),
     ("hard_decision_ge", "llr[i] > 0.0f ? 1 : 0", "llr[i] >= 0.0f ? 1 : 0"),
     ("no_start_syndrome", "d.s0[j] ^= col[(size_t)i * words + j];", "(void)0;"),
-    ("zero_pattern_skipped", "rc = fn(NULL, 0, ctx);", "rc = 0;"),
+    ("zero_pattern_skipped", "rc = fn(NULL, 0, ctx);               /* R = 0",
+     "rc = 0;               /* R = 0"),
+    ("segments_zero_pattern_skipped", "rc = fn(NULL, 0, ctx);                   /* R = 0",
+     "rc = 0;                   /* R = 0"),
     ("build_mountain_step5_dropped", "u[w - q] += r;", "(void)r;"),
     ("landslide_smallest_k", "for (k = w; k >= 1; k--)", "for (k = 1; k <= w; k++)"),
     ("cap_off_by_one", "if (d->t >= d->cap)", "if (d->t > d->cap)"),
@@ -24,6 +27,11 @@ MUTATIONS = [
     ("rw_divisibility_dropped", "if ((R - J0 * w) % beta)", "if (0)"),
     ("rw_hamming_term_dropped", "L = (R - J0 * w) / beta;", "L = R / beta;"),
     ("rw_slope_on_hamming", "L = (R - J0 * w) / beta;", "L = (R - beta * w) / beta;"),
+    ("segment_shift_dropped", "c->v[c->nv++] = base + k + u[k];",
+     "c->v[c->nv++] = k + u[k];"),
+    ("segment_upper_bound_off", "L <= (long)(ni + 1) * w - (long)w * (w + 1) / 2;",
+     "L <= (long)(ni + 2) * w - (long)w * (w + 1) / 2;"),
+    ("segment_intercept_ignored", "rem = Wi - (long)w * md->J[i];", "rem = Wi;"),
     ("vu_map_transposed", "v[i] = i + u[i];", "v[i] = i + u[w + 1 - i];"),
     ("flip_wrong_index", "c_out[pi[d.hit_v[i] - 1]] ^= 1;", "c_out[d.hit_v[i] - 1] ^= 1;"),
 ]
