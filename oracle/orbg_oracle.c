@@ -550,10 +550,12 @@ int orbg_oracle_decode_batch(const uint8_t *H, int n, int r, const float *llr,
  * (Algorithm 4 with Eq. wi_cond, the bounds applying to the partial
  * logistic weight (W_i - w_i J_{i-1}) / beta_i, Eq. wu_i), each segment's
  * partial patterns from Landslide, and their Cartesian product
- * (Eq. cartP).  Readings: J_{i-1} >= 0 and beta_i >= 1; the patterns of
- * one weight are visited in the canonical order of the other decoders
- * (Hamming weight ascending, then positions lexicographically), since the
- * paper leaves the order inside a weight free.
+ * (Eq. cartP).  Readings: beta_i >= 1 and J_{i-1} >= -beta_i, so every
+ * position weighs at least 0 (the fitted J_0 of Eq. quant can be as low as
+ * -beta_1); the patterns of one weight are visited in the canonical order
+ * of the other decoders (Hamming weight ascending, then positions
+ * lexicographically), since the paper leaves the order inside a weight
+ * free.
  */
 #define ORC_MAX_SEG 8
 
@@ -686,9 +688,11 @@ static int orc_choose_w(orc_seg_ctx *c, int i)
         c->nv = 0;
         return orc_fill_segment(c);
     }
-    if (c->W[i] == 0) {
+    if (c->W[i] == 0) {                      /* nothing flipped in segment i */
         c->w[i] = 0;
-        return orc_choose_w(c, i + 1);
+        rc = orc_choose_w(c, i + 1);
+        if (rc)
+            return rc;
     }
     for (w = 1; w <= md->I[i + 1] - md->I[i]; w++) {
         if (!orc_valid_w(md, i, c->W[i], w))
@@ -753,8 +757,8 @@ static int orc_check_model(const orc_model *md, int n)
     if (md->m < 1 || md->m > ORC_MAX_SEG || md->I[0] != 0 || md->I[md->m] != n)
         return 0;
     for (i = 0; i < md->m; i++)
-        if (md->I[i + 1] <= md->I[i] || md->J[i] < 0 || md->beta[i] < 1)
-            return 0;
+        if (md->I[i + 1] <= md->I[i] || md->beta[i] < 1 || md->J[i] < -md->beta[i])
+            return 0;                        /* every position weight >= 0 */
     return 1;
 }
 
@@ -770,8 +774,9 @@ static int orc_walk_model(int n, const orc_model *md, orc_pattern_fn fn, void *c
         for (j = md->I[i] + 1; j <= md->I[i + 1]; j++)
             Rmax += md->J[i] + md->beta[i] * (j - md->I[i]);
     memset(&b, 0, sizeof(b));
-    rc = fn(NULL, 0, ctx);                   /* R = 0: nothing flipped */
-    for (R = 1; R <= Rmax && !rc; R++) {
+    /* R = 0 holds the empty pattern (all W_i = 0, nothing flipped) and,
+     * when a segment starts at weight 0, the patterns of zero weight */
+    for (R = 0; R <= Rmax && !rc; R++) {
         memset(&c, 0, sizeof(c));
         c.md = md;
         c.n = n;

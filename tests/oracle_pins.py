@@ -363,7 +363,10 @@ def pin_1line_invariants(orc):
 # segment, zero intercepts, J divisible and not divisible by beta
 MODELS10 = [((), (0,), (1,)), ((), (4,), (3,)), ((3,), (0, 4), (1, 2)),
             ((2, 6), (0, 3, 6), (1, 1, 2)), ((4, 7), (1, 6, 9), (2, 3, 1)),
-            ((1, 2, 5), (0, 2, 5, 9), (1, 2, 1, 3))]
+            ((1, 2, 5), (0, 2, 5, 9), (1, 2, 1, 3)),
+            # a first segment starting at weight 0 (J_0 = -beta_1, as Eq. quant
+            # gives when the least reliable bit rounds to 0)
+            ((3,), (-2, 3), (2, 1)), ((), (-1,), (1,))]
 
 
 def pin_mline_order_brute(orc):

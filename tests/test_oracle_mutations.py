@@ -18,8 +18,8 @@ MUTATIONS = [
     ("no_start_syndrome", "d.s0[j] ^= col[(size_t)i * words + j];", "(void)0;"),
     ("zero_pattern_skipped", "rc = fn(NULL, 0, ctx);               /* R = 0",
      "rc = 0;               /* R = 0"),
-    ("segments_zero_pattern_skipped", "rc = fn(NULL, 0, ctx);                   /* R = 0",
-     "rc = 0;                   /* R = 0"),
+    ("segments_weight_zero_skipped", "for (R = 0; R <= Rmax && !rc; R++) {",
+     "for (R = 1; R <= Rmax && !rc; R++) {"),
     ("build_mountain_step5_dropped", "u[w - q] += r;", "(void)r;"),
     ("landslide_smallest_k", "for (k = w; k >= 1; k--)", "for (k = 1; k <= w; k++)"),
     ("cap_off_by_one", "if (d->t >= d->cap)", "if (d->t > d->cap)"),
