@@ -21,6 +21,11 @@ Functions and the passages they follow:
                          relest_seg, Algorithm 3 splits checked by
                          Algorithm 4 / Eq. wi_cond, Landslide per segment,
                          the Cartesian product of Eq. cartP)
+  fit                    piece-wise linear fitting and quantisation of a
+                         block's ordered reliabilities (Sec. III-E, Eq. Q,
+                         Eq. quant)
+  decode_batch_fit       full ORBGRAND per block: fit, then the m-segment
+                         order
 
 Parity pins: tests/test_oracle_pins.py (brute force on tiny codes, the
 first queries of Sec. III-B, the Fig. 3 / Fig. 5 examples, closed-form
@@ -33,12 +38,12 @@ from .oracle import (Oracle, OracleError, build_oracle, compile_oracle,
                      count_by_weight, decode, decode_1line, decode_batch,
                      decode_batch_1line, decode_batch_mline, default,
                      enumerate_patterns, enumerate_patterns_1line,
-                     enumerate_patterns_mline, landslide, sort_reliability,
-                     ORACLE_LIB, ORACLE_SRC)
+                     enumerate_patterns_mline, fit, decode_batch_fit, landslide,
+                     sort_reliability, ORACLE_LIB, ORACLE_SRC)
 
 __all__ = ["Oracle", "OracleError", "build_oracle", "compile_oracle",
            "count_by_weight", "decode", "decode_1line", "decode_batch",
            "decode_batch_1line", "decode_batch_mline", "default",
            "enumerate_patterns", "enumerate_patterns_1line",
-           "enumerate_patterns_mline", "landslide", "sort_reliability",
-           "ORACLE_LIB", "ORACLE_SRC"]
+           "enumerate_patterns_mline", "fit", "decode_batch_fit", "landslide",
+           "sort_reliability", "ORACLE_LIB", "ORACLE_SRC"]

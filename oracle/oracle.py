@@ -95,6 +95,14 @@ class Oracle:
                                                        ctypes.c_int, i32p, i64p, i64p, u8p,
                                                        u64p, u8p, u64p]
         lib.orbg_oracle_decode_batch_mline.restype = ctypes.c_int
+        lib.orbg_oracle_fit.argtypes = [f32p, ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p,
+                                        i32p, i64p, i64p]
+        lib.orbg_oracle_fit.restype = ctypes.c_int
+        lib.orbg_oracle_decode_batch_fit.argtypes = [u8p, ctypes.c_int, ctypes.c_int, f32p,
+                                                     ctypes.c_long, ctypes.c_uint64,
+                                                     ctypes.c_int, ctypes.c_int, u8p, u64p,
+                                                     u8p, u64p]
+        lib.orbg_oracle_decode_batch_fit.restype = ctypes.c_int
         self.lib = lib
         self.path = path
 
@@ -232,6 +240,44 @@ class Oracle:
             raise OracleError("oracle m-line batch decode failed: %d" % rc)
         return c, q, ab, sw
 
+    def fit(self, llr, lines, divisible=False):
+        """Piece-wise linear fit and quantisation of one block's ordered
+        reliabilities (Sec. III-E): the model (anchors, J, beta)."""
+        llr = np.ascontiguousarray(llr, dtype=np.float32)
+        m = ctypes.c_int(0)
+        a = np.zeros(8, np.int32)
+        J = np.zeros(8, np.int64)
+        beta = np.zeros(8, np.int64)
+        rc = self.lib.orbg_oracle_fit(_ptr(llr, ctypes.c_float), llr.shape[0], int(lines),
+                                      int(bool(divisible)), ctypes.byref(m),
+                                      _ptr(a, ctypes.c_int),
+                                      J.ctypes.data_as(ctypes.POINTER(ctypes.c_long)),
+                                      beta.ctypes.data_as(ctypes.POINTER(ctypes.c_long)))
+        if rc != 0:
+            raise OracleError("fit failed: %d" % rc)
+        k = m.value
+        return (tuple(int(x) for x in a[:k - 1]), tuple(int(x) for x in J[:k]),
+                tuple(int(x) for x in beta[:k]))
+
+    def decode_batch_fit(self, H, llr, cap, lines, divisible=False):
+        """decode_batch() for full ORBGRAND with each block's own fitted
+        model (fit(), then the m-segment order)."""
+        H = np.ascontiguousarray(H, dtype=np.uint8)
+        r, n = H.shape
+        llr = np.ascontiguousarray(llr, dtype=np.float32).reshape(-1, n)
+        B = llr.shape[0]
+        c = np.zeros((B, n), np.uint8)
+        q = np.zeros(B, np.uint64)
+        ab = np.zeros(B, np.uint8)
+        sw = np.zeros(B, np.uint64)
+        rc = self.lib.orbg_oracle_decode_batch_fit(
+            _ptr(H, ctypes.c_uint8), n, r, _ptr(llr, ctypes.c_float), B, int(cap), int(lines),
+            int(bool(divisible)), _ptr(c, ctypes.c_uint8), _ptr(q, ctypes.c_uint64),
+            _ptr(ab, ctypes.c_uint8), _ptr(sw, ctypes.c_uint64))
+        if rc != 0:
+            raise OracleError("oracle fitted batch decode failed: %d" % rc)
+        return c, q, ab, sw
+
     def enumerate_patterns(self, n, count):
         """First `count` patterns of the query order for length n, as tuples
         of 1-based sorted-order positions (the zero pattern is ())."""
@@ -322,3 +368,11 @@ def enumerate_patterns_mline(n, count, model):
 
 def decode_batch_mline(H, llr, cap, model):
     return default().decode_batch_mline(H, llr, cap, model)
+
+
+def fit(llr, lines, divisible=False):
+    return default().fit(llr, lines, divisible)
+
+
+def decode_batch_fit(H, llr, cap, lines, divisible=False):
+    return default().decode_batch_fit(H, llr, cap, lines, divisible)

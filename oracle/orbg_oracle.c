@@ -41,6 +41,10 @@
  * Landslide order).  Basic ORBGRAND is the case J_0 = 0, beta = 1 (the
  * paper notes it is the special case of Eq. relest_seg).
  *
+ * Piece-wise linear fitting and quantisation (Sec. III-E, Eq. Q and
+ * Eq. quant) turn a block's ordered reliabilities into such a model:
+ * orbg_oracle_fit, with the readings stated there.
+ *
  * Parity pins (tests): brute force over all 2^n patterns for tiny codes,
  * the first queries listed in Sec. III-B, the Fig. 3 / Fig. 5 Landslide
  * examples, closed-form partition counts (for the reliability weight, the
@@ -874,6 +878,143 @@ int orbg_oracle_decode_batch_mline(const uint8_t *H, int n, int r, const float *
         uint64_t sw = 0;
         rc = orc_decode_walk(H, n, r, llr + (size_t)b * n, cap, orc_walk_model_fn, &md,
                              c_out + (size_t)b * n, q_out + b, &ab, &sw, NULL, NULL);
+        if (rc)
+            return rc;
+        abandon[b] = (uint8_t)ab;
+        if (sum_w)
+            sum_w[b] = sw;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Piece-wise linear fitting and quantisation (Sec. III-E).             */
+/* ------------------------------------------------------------------ */
+
+#define ORC_FIT_MAX 16777216.0 /* 2^24: largest quantised slope or offset */
+
+static long orc_round(double x)              /* [ ]: half away from zero */
+{
+    return (long)(x < 0 ? -floor(-x + 0.5) : floor(x + 0.5));
+}
+
+/*
+ * Fit `lines` (1..ORC_MAX_SEG) lines to the block's ordered reliability
+ * curve L_1 <= ... <= L_n (|LLR| sorted as in Sec. III-A) and quantise
+ * them (Eq. Q, Eq. quant).  Anchors start at the edge index 1 and the
+ * centre floor(n/2); each further anchor goes into the first interval
+ * (the high-curvature edge), at the largest vertical gap between that
+ * interval's chord and the curve (smallest index on ties); the search
+ * stops early when the interval has no inner index or no gap.  The line
+ * ending at the centre is extended to n.  With the anchors a_0 = 1 < a_1
+ * < ... < a_m = centre: I_i = a_i for 0 < i < m, I_m = n; slope s_1 =
+ * (L_{a_1} - L_1)/(a_1 - 1), s_i = (L_{a_i} - L_{a_{i-1}})/(a_i - a_{i-1});
+ * Q = min s_i; beta_i = [s_i / Q]; J_0 = [L_1 / Q] - beta_1;
+ * J_i = [L_{I_i} / Q].  divisible != 0: J_{i-1} <- [J_{i-1} / beta_i] beta_i.
+ * n < 4, Q <= 0 (a flat stretch), or a ratio s_i / Q or L_{I_i} / Q
+ * (i < m) that is not finite or exceeds 2^24: the basic model, one line
+ * with J_0 = 0, beta_1 = 1.  Outputs: *m, anchors I_1 .. I_{m-1}, J_0 ..
+ * J_{m-1}, beta_1 .. beta_m.
+ */
+int orbg_oracle_fit(const float *llr, int n, int lines, int divisible, int *m_out,
+                    int *anchors, long *J, long *beta)
+{
+    int pi[ORC_MAX_N];
+    double L[ORC_MAX_N + 1];
+    int a[ORC_MAX_SEG + 1], na, i, j, k;
+    double s[ORC_MAX_SEG], Q;
+    if (n < 1 || n > ORC_MAX_N || lines < 1 || lines > ORC_MAX_SEG || !m_out || !J || !beta)
+        return ORC_EINVAL;
+    for (i = 0; i < n; i++)
+        if (isnan(llr[i]))
+            return ORC_ENAN;
+    orc_sort_by_reliability(llr, n, pi);
+    for (j = 1; j <= n; j++)
+        L[j] = fabs((double)llr[pi[j - 1]]);
+    *m_out = 1;
+    J[0] = 0;
+    beta[0] = 1;
+    if (n < 4)
+        return ORC_OK;
+    a[0] = 1;
+    a[1] = n / 2;
+    na = 2;
+    while (na - 1 < lines) {                  /* one more line: split [a_0, a_1] */
+        const int lo = a[0], hi = a[1];
+        int best = -1;
+        double gap = 0.0;
+        for (j = lo + 1; j < hi; j++) {
+            const double chord = L[lo] + (L[hi] - L[lo]) * (double)(j - lo) / (double)(hi - lo);
+            const double g = fabs(chord - L[j]);
+            if (g > gap) {
+                gap = g;
+                best = j;
+            }
+        }
+        if (best < 0)
+            break;                            /* no inner index or no gap */
+        for (k = na; k > 1; k--)
+            a[k] = a[k - 1];
+        a[1] = best;
+        na++;
+    }
+    {
+        const int m = na - 1;
+        s[0] = (L[a[1]] - L[1]) / (double)(a[1] - 1);
+        for (i = 2; i <= m; i++)
+            s[i - 1] = (L[a[i]] - L[a[i - 1]]) / (double)(a[i] - a[i - 1]);
+        Q = s[0];
+        for (i = 1; i < m; i++)
+            if (s[i] < Q)
+                Q = s[i];                     /* Eq. Q */
+        if (!(Q > 0.0))
+            return ORC_OK;                    /* a flat stretch: basic model */
+        for (i = 0; i < m; i++)
+            if (!(s[i] / Q <= ORC_FIT_MAX) || !(L[a[i]] / Q <= ORC_FIT_MAX))
+                return ORC_OK;                /* out of range: basic model */
+        for (i = 0; i < m; i++)
+            beta[i] = orc_round(s[i] / Q);    /* Eq. quant */
+        J[0] = orc_round(L[1] / Q) - beta[0];
+        for (i = 1; i < m; i++)
+            J[i] = orc_round(L[a[i]] / Q);
+        if (divisible)
+            for (i = 0; i < m; i++)
+                J[i] = orc_round((double)J[i] / (double)beta[i]) * beta[i];
+        for (i = 1; i < m; i++)
+            if (anchors)
+                anchors[i - 1] = a[i];
+        *m_out = m;
+    }
+    return ORC_OK;
+}
+
+/*
+ * Full ORBGRAND per block (the flow of Fig. flow_char): fit and quantise
+ * each block's own model (orbg_oracle_fit), then query in increasing
+ * reliability weight under it (orbg_oracle_decode_batch_mline's walk).
+ * Outputs as orbg_oracle_decode_batch_1line.
+ */
+int orbg_oracle_decode_batch_fit(const uint8_t *H, int n, int r, const float *llr, long B,
+                                 uint64_t cap, int lines, int divisible, uint8_t *c_out,
+                                 uint64_t *q_out, uint8_t *abandon, uint64_t *sum_w)
+{
+    long b;
+    if (n < 1 || n > ORC_MAX_N || lines < 1 || lines > ORC_MAX_SEG)
+        return ORC_EINVAL;
+    for (b = 0; b < B; b++) {
+        const float *x = llr + (size_t)b * n;
+        int m = 1, anchors[ORC_MAX_SEG], ab = 0, rc;
+        long J[ORC_MAX_SEG], beta[ORC_MAX_SEG];
+        uint64_t sw = 0;
+        orc_model md;
+        rc = orbg_oracle_fit(x, n, lines, divisible, &m, anchors, J, beta);
+        if (rc)
+            return rc;
+        orc_fill_model(&md, m, anchors, J, beta, n);
+        if (!orc_check_model(&md, n))
+            return ORC_EINVAL;
+        rc = orc_decode_walk(H, n, r, x, cap, orc_walk_model_fn, &md, c_out + (size_t)b * n,
+                             q_out + b, &ab, &sw, NULL, NULL);
         if (rc)
             return rc;
         abandon[b] = (uint8_t)ab;

@@ -93,6 +93,7 @@ def model_weights(n, model):
     return rho
 
 
+@functools.lru_cache(maxsize=None)
 def query_order_model(n, model):
     """All subsets of {1..n} sorted by (sum of rho over the subset, Hamming
     weight, positions lexicographically): m-segment full ORBGRAND with the
@@ -103,7 +104,7 @@ def query_order_model(n, model):
         v = tuple(i + 1 for i in range(n) if (mask >> i) & 1)
         pats.append((sum(rho[p - 1] for p in v), len(v), v))
     pats.sort()
-    return [p[2] for p in pats]
+    return tuple(p[2] for p in pats)
 
 
 def decode_model(H, llr, cap, model):

@@ -374,7 +374,7 @@ def pin_mline_order_brute(orc):
     (sum of the model's reliabilities, w, lexicographic) (Sec. III-D)."""
     for model in MODELS10:
         got = orc.enumerate_patterns_mline(10, 1 << 10, model)
-        assert got == brute_force.query_order_model(10, model), model
+        assert got == list(brute_force.query_order_model(10, model)), model
 
 
 def pin_mline_generating_function(orc):
@@ -425,12 +425,152 @@ def pin_mline_brute_decode(orc, blocks=30):
                 assert (c0 == c1[b]).all() and q0 == q1[b] and a0 == a1[b], (model, cap)
 
 
+# ------------------------------------------- piece-wise fitting (Sec. III-E)
+
+# Closed forms for the ordered reliabilities L_j = j^2 (Eq. Q, Eq. quant),
+# worked by hand.  The vertical gap between the chord over [lo, hi] and the
+# parabola is (j - lo)(hi - j), largest at the midpoint; an odd lo + hi ties
+# two indices and the smaller is taken.  Keys (n, lines); values are the
+# models (anchors, J, beta) without and with J_{i-1} divisible by beta_i.
+#   n = 64, centre 32: anchors 16 (tie 16/17), then 8 (tie 8/9), 4 (tie
+#   4/5), 2 (tie 2/3), then [1, 2] has no inner index.  Four lines: slopes
+#   15/3, 48/4, 192/8, 768/16 = 5, 12, 24, 48, Q = 5, beta = [1, 2.4, 4.8,
+#   9.6] = (1, 2, 5, 10), J_0 = [1/5] - 1, J = [16/5], [64/5], [256/5];
+#   divisible: [3/2]*2 = 4, [13/5]*5 = 15, [51/10]*10 = 50.
+#   n = 12, centre 6: anchors 3 (tie 3/4), 2.  Three lines: slopes 3, 5, 9,
+#   Q = 3, beta = (1, [5/3], 3), J = ([1/3] - 1, [4/3], [9/3]); divisible
+#   J_1 = [1/2]*2 = 2 (half away from zero).
+#   n = 13: the centre is floor(13/2) = 6, so the fit equals n = 12's.
+PARABOLA_FITS = {
+    (64, 1): (((), (-1,), (1,)), ((), (-1,), (1,))),
+    (64, 2): (((16,), (-1, 15), (1, 3)), ((16,), (-1, 15), (1, 3))),
+    (64, 3): (((8, 16), (-1, 7, 28), (1, 3, 5)), ((8, 16), (-1, 6, 30), (1, 3, 5))),
+    (64, 4): (((4, 8, 16), (-1, 3, 13, 51), (1, 2, 5, 10)),
+              ((4, 8, 16), (-1, 4, 15, 50), (1, 2, 5, 10))),
+    (64, 5): (((2, 4, 8, 16), (-1, 1, 5, 21, 85), (1, 2, 4, 8, 16)),
+              ((2, 4, 8, 16), (-1, 2, 4, 24, 80), (1, 2, 4, 8, 16))),
+    (64, 6): (((2, 4, 8, 16), (-1, 1, 5, 21, 85), (1, 2, 4, 8, 16)),
+              ((2, 4, 8, 16), (-1, 2, 4, 24, 80), (1, 2, 4, 8, 16))),
+    (12, 1): (((), (-1,), (1,)), ((), (-1,), (1,))),
+    (12, 2): (((3,), (-1, 2), (1, 2)), ((3,), (-1, 2), (1, 2))),
+    (12, 3): (((2, 3), (-1, 1, 3), (1, 2, 3)), ((2, 3), (-1, 2, 3), (1, 2, 3))),
+    (12, 4): (((2, 3), (-1, 1, 3), (1, 2, 3)), ((2, 3), (-1, 2, 3), (1, 2, 3))),
+    (13, 2): (((3,), (-1, 2), (1, 2)), ((3,), (-1, 2), (1, 2))),
+}
+
+
+def _disguise(L, rng, scale=1.0):
+    """Received LLRs whose sorted magnitudes are L * scale: a random order
+    and random signs (the fit sees only the ordered reliabilities)."""
+    x = np.asarray(L, np.float64) * scale
+    x = x[rng.permutation(len(x))] * rng.choice((-1.0, 1.0), len(x))
+    return x.astype(np.float32)
+
+
+def pin_fit_parabola(orc):
+    """Anchor search, Eq. Q and Eq. quant on L_j = j^2 against the hand-worked
+    closed forms, in any received order and sign, at power-of-two scales."""
+    rng = np.random.default_rng(29)
+    for (n, lines), (plain, div) in PARABOLA_FITS.items():
+        L = [j * j for j in range(1, n + 1)]
+        for scale in (1.0, 0.125, 32.0):
+            llr = _disguise(L, rng, scale)
+            assert orc.fit(llr, lines) == plain, (n, lines, scale)
+            assert orc.fit(llr, lines, divisible=True) == div, (n, lines, scale)
+
+
+def pin_fit_piecewise_exact(orc):
+    """A convex piece-wise linear curve with its kinks below the centre and
+    a straight tail is fitted exactly: the anchors are the kinks and
+    Q * rho_j = L_j at every j (Eq. relest_seg, Eq. quant with no rounding)."""
+    rng = np.random.default_rng(31)
+    # (n, lines, kinks, slopes, L_1, expected model), slopes a multiple of 2
+    cases = [(40, 2, (6,), (2, 6), 6, ((6,), (2, 8), (1, 3))),
+             (40, 3, (6,), (2, 6), 6, ((6,), (2, 8), (1, 3))),
+             (40, 3, (3, 10), (2, 4, 8), 2, ((3, 10), (0, 3, 17), (1, 2, 4))),
+             (64, 4, (3, 10), (2, 4, 8), 2, ((3, 10), (0, 3, 17), (1, 2, 4)))]
+    for n, lines, kinks, slopes, L1, want in cases:
+        L, seg = [L1], 0
+        for j in range(2, n + 1):
+            if seg < len(kinks) and j > kinks[seg]:
+                seg += 1
+            L.append(L[-1] + slopes[seg])
+        model = orc.fit(_disguise(L, rng), lines)
+        assert model == want, (n, lines, model)
+        Q = min(slopes)
+        assert [Q * r for r in brute_force.model_weights(n, model)] == L
+    # the three-line case with J_{i-1} divisible by beta_i: [3/2]*2, [17/4]*4
+    L = [2 * j if j <= 3 else 6 + 4 * (j - 3) if j <= 10 else 34 + 8 * (j - 10)
+         for j in range(1, 41)]
+    assert orc.fit(_disguise(L, rng), 3, divisible=True) == ((3, 10), (0, 4, 16), (1, 2, 4))
+
+
+def pin_fit_invariants(orc):
+    """On AWGN blocks: at most `lines` segments, anchors strictly inside
+    (1, floor(n/2)) and nested as lines grow, beta >= 1 with the smallest
+    slope quantised to 1 (Eq. Q), every position weight >= 0, J_{i-1} a
+    multiple of beta_i in the divisible variant within beta_i / 2 of the
+    plain J, the same model for any order, sign or power-of-two scale of
+    the LLRs, and a model the m-segment order accepts."""
+    rng = np.random.default_rng(37)
+    code = workloads.rlc(64, 48, seed=6)
+    for snr in (1.0, 4.0, 7.0):
+        llr, _ = workloads.awgn_llr(code, 12, snr, seed=int(snr) + 40)
+        for b in range(llr.shape[0]):
+            x = llr[b]
+            prev = ()
+            for lines in range(1, 7):
+                anchors, J, beta = model = orc.fit(x, lines)
+                m = len(J)
+                assert 1 <= m <= lines and len(beta) == m and len(anchors) == m - 1
+                assert all(1 < a < 32 for a in anchors)
+                assert list(anchors) == sorted(set(anchors))
+                assert set(prev) <= set(anchors)
+                prev = anchors
+                assert min(beta) == 1 and all(bb >= 1 for bb in beta)
+                assert min(brute_force.model_weights(64, model)) >= 0
+                _, Jd, bd = orc.fit(x, lines, divisible=True)
+                assert bd == beta
+                assert all(Jd[i] % beta[i] == 0 and 2 * abs(Jd[i] - J[i]) <= beta[i]
+                           for i in range(m))
+                y = (x * np.float32(4.0))[rng.permutation(64)]
+                y *= rng.choice((-1.0, 1.0), 64).astype(np.float32)
+                assert orc.fit(y, lines) == model
+                assert len(orc.enumerate_patterns_mline(64, 50, model)) == 50
+
+
+def pin_fit_brute_decode(orc, blocks=24):
+    """Full ORBGRAND with per-block fitting (Sec. III-E, then the m-segment
+    order) = brute force under the closed-form model, on blocks whose
+    ordered reliabilities are j^2 (n = 12, seeded random (12, 6) code)."""
+    rng = np.random.default_rng(41)
+    code = workloads.rlc(12, 6, seed=11)
+    L = [j * j for j in range(1, 13)]
+    llrs = np.stack([_disguise(L, rng, 0.25) for _ in range(blocks)])
+    for lines in (1, 2, 3):
+        for divisible in (False, True):
+            model = PARABOLA_FITS[(12, lines)][int(divisible)]
+            for cap in (1, 5, 40, 1 << 12):
+                c1, q1, a1, _ = orc.decode_batch_fit(code.H, llrs, cap, lines, divisible)
+                for b in range(blocks):
+                    c0, q0, a0 = brute_force.decode_model(code.H, llrs[b], cap, model)
+                    assert (c0 == c1[b]).all() and q0 == q1[b] and a0 == a1[b], (lines, cap)
+    # AWGN blocks: each block is decoded under its own fitted model
+    code = workloads.rlc(24, 16, seed=5)
+    llr, _ = workloads.awgn_llr(code, 16, 4.0, seed=12)
+    c1, q1, a1, _ = orc.decode_batch_fit(code.H, llr, 3000, 3)
+    for b in range(llr.shape[0]):
+        c0, q0, a0, _ = orc.decode_batch_mline(code.H, llr[b:b + 1], 3000, orc.fit(llr[b], 3))
+        assert (c0[0] == c1[b]).all() and q0[0] == q1[b] and a0[0] == a1[b]
+
+
 FAST_PINS = [pin_first_queries, pin_fig3, pin_fig5, pin_order_brute,
              pin_counts_closed_form, pin_brute_decode, pin_invariants,
              pin_cap_boundary, pin_1line_order_brute, pin_1line_generating_function,
              pin_1line_is_basic_at_origin, pin_1line_brute_decode, pin_1line_invariants,
              pin_mline_order_brute, pin_mline_generating_function,
-             pin_mline_one_segment_is_one_line, pin_mline_brute_decode]
+             pin_mline_one_segment_is_one_line, pin_mline_brute_decode, pin_fit_parabola,
+             pin_fit_piecewise_exact, pin_fit_invariants, pin_fit_brute_decode]
 
 
 def run_all(orc, pins=None):

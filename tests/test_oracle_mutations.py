@@ -34,6 +34,21 @@ MUTATIONS = [
     ("segment_intercept_ignored", "rem = Wi - (long)w * md->J[i];", "rem = Wi;"),
     ("vu_map_transposed", "v[i] = i + u[i];", "v[i] = i + u[w + 1 - i];"),
     ("flip_wrong_index", "c_out[pi[d.hit_v[i] - 1]] ^= 1;", "c_out[d.hit_v[i] - 1] ^= 1;"),
+    ("fit_gap_tie_to_larger_index", "if (g > gap) {", "if (g >= gap && g > 0.0) {"),
+    ("fit_split_last_interval", "const int lo = a[0], hi = a[1];",
+     "const int lo = a[na - 2], hi = a[na - 1];"),
+    ("fit_centre_rounded_up", "a[1] = n / 2;", "a[1] = (n + 1) / 2;"),
+    ("fit_Q_largest_slope", "if (s[i] < Q)", "if (s[i] > Q)"),
+    ("fit_first_slope_from_origin", "s[0] = (L[a[1]] - L[1]) / (double)(a[1] - 1);",
+     "s[0] = L[a[1]] / (double)a[1];"),
+    ("fit_J0_unshifted", "J[0] = orc_round(L[1] / Q) - beta[0];", "J[0] = orc_round(L[1] / Q);"),
+    ("fit_J_at_segment_start", "J[i] = orc_round(L[a[i]] / Q);",
+     "J[i] = orc_round(L[a[i] + 1] / Q);"),
+    ("fit_divisible_floor", "J[i] = orc_round((double)J[i] / (double)beta[i]) * beta[i];",
+     "J[i] = (long)floor((double)J[i] / (double)beta[i]) * beta[i];"),
+    ("fit_divisible_next_slope", "J[i] = orc_round((double)J[i] / (double)beta[i]) * beta[i];",
+     "J[i] = orc_round((double)J[i] / (double)beta[i < m - 1 ? i + 1 : i]) *"
+     " beta[i < m - 1 ? i + 1 : i];"),
 ]
 
 RUNNER = textwrap.dedent("""
