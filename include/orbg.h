@@ -106,6 +106,29 @@ ORBG_API int orbg_load_code_line(const uint8_t *mat, int kind, int n, int k,
                                  uint32_t max_query_cap, int32_t J0, int32_t beta,
                                  orbg_code **out);
 
+/*
+ * m-segment full ORBGRAND (Sec. III-D, Eq. relest_seg): as orbg_load_code,
+ * but the handle's query order sorts noise patterns by increasing
+ * reliability weight under a piece-wise linear model of m segments
+ * (1..8): with I_0 = 0, I_m = n and the anchors I_1 < ... < I_{m-1}
+ * (host array `anchors`, m - 1 entries, inside 1..n-1), sorted position j
+ * of segment i, I_{i-1} < j <= I_i, counts J_{i-1} + beta_i (j - I_{i-1}).
+ * J: host array J_0..J_{m-1}; beta: host array beta_1..beta_m.  beta_i:
+ * 1..2^20; J_{i-1}: -beta_i..2^20, so that no position counts below 0
+ * (Eq. quant gives J_0 = -beta_1 when the least reliable bit rounds to
+ * zero).  Ties: Hamming weight ascending, then positions lexicographically;
+ * the empty pattern is query 1.  The orders of orbg_load_code and
+ * orbg_load_code_line are the one-segment cases (J_0 = J0, beta_1 =
+ * beta), built here without triple runs.  Every decode entry point decodes
+ * in the handle's order.  Arrays are read during the call only.  Errors as
+ * orbg_load_code; EINVAL for a model out of range; ELIMIT when the order
+ * up to max_query_cap needs a position above 255 in a pattern's leading
+ * positions or more than 22 flipped positions.
+ */
+ORBG_API int orbg_load_code_model(const uint8_t *mat, int kind, int n, int k,
+                                  uint32_t max_query_cap, int m, const int32_t *anchors,
+                                  const int32_t *J, const int32_t *beta, orbg_code **out);
+
 /* Release a handle (NULL is allowed).  Not stream-ordered: no decode call
  * using it may still be in flight. */
 ORBG_API int orbg_free_code(orbg_code *code);
@@ -364,6 +387,13 @@ ORBG_API int64_t orbg_query_order(int n, uint32_t count, int table,
 /* The same for the one-line order of orbg_load_code_line (Sec. III-D). */
 ORBG_API int64_t orbg_query_order_line(int n, uint32_t count, int table, int32_t J0,
                                        int32_t beta, int32_t *out);
+
+/* The same for the m-segment order of orbg_load_code_model (Sec. III-D,
+ * Eq. relest_seg); the model's arguments as there.  Tables 0 and 1 are the
+ * same run list. */
+ORBG_API int64_t orbg_query_order_model(int n, uint32_t count, int table, int m,
+                                        const int32_t *anchors, const int32_t *J,
+                                        const int32_t *beta, int32_t *out);
 
 /* Static description of a status code (never NULL). */
 ORBG_API const char *orbg_status_string(int status);

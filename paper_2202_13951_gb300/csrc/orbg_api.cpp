@@ -219,17 +219,11 @@ int64_t orbg_query_order(int n, uint32_t count, int table, int32_t *out)
     return orbg_query_order_line(n, count, table, 0, 1, out);
 }
 
-int64_t orbg_query_order_line(int n, uint32_t count, int table, int32_t J0, int32_t beta,
-                              int32_t *out)
+namespace {
+
+/* The first `count` patterns of table `table` of tb (orbg_query_order). */
+int64_t expand_tables(const OrbgTables &tb, int n, uint32_t count, int table, int32_t *out)
 {
-    if (n < 1 || n > ORBG_MAX_N || (count > 0 && !out) || table < 0 || table > 2 || J0 < 0 ||
-        beta < 1 || J0 > ORBG_MAX_LINE || beta > ORBG_MAX_LINE)
-        return ORBG_EINVAL;
-    if (count == 0)
-        return 0;
-    OrbgTables tb;
-    if (orbg_build_tables(n, count, &tb, J0, beta) != 0)
-        return ORBG_ELIMIT;
     const std::vector<OrbgRun> &runs = table == 0 ? tb.runs : tb.runs_cta;
     const size_t stride = (size_t)n + 1;
     uint64_t total = std::min<uint64_t>(tb.patterns, count);
@@ -264,6 +258,59 @@ int64_t orbg_query_order_line(int n, uint32_t count, int table, int32_t J0, int3
         }
     }
     return (int64_t)total;
+}
+
+/* Checks a model given through the C ABI and fills m: anchors I_1..I_{m-1},
+ * J_0..J_{m-1}, beta_1..beta_m. */
+bool make_model(int n, int m, const int32_t *anchors, const int32_t *J, const int32_t *beta,
+                OrbgModel *md)
+{
+    if (m < 1 || m > ORBG_MAX_SEG || !J || !beta || (m > 1 && !anchors))
+        return false;
+    md->m = m;
+    md->I[0] = 0;
+    md->I[m] = n;
+    for (int i = 1; i < m; i++)
+        md->I[i] = anchors[i - 1];
+    for (int i = 0; i < m; i++) {
+        md->J[i] = J[i];
+        md->beta[i] = beta[i];
+        if (md->I[i + 1] <= md->I[i] || beta[i] < 1 || beta[i] > ORBG_MAX_MODEL ||
+            J[i] < -beta[i] || J[i] > ORBG_MAX_MODEL)
+            return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+int64_t orbg_query_order_line(int n, uint32_t count, int table, int32_t J0, int32_t beta,
+                              int32_t *out)
+{
+    if (n < 1 || n > ORBG_MAX_N || (count > 0 && !out) || table < 0 || table > 2 || J0 < 0 ||
+        beta < 1 || J0 > ORBG_MAX_LINE || beta > ORBG_MAX_LINE)
+        return ORBG_EINVAL;
+    if (count == 0)
+        return 0;
+    OrbgTables tb;
+    if (orbg_build_tables(n, count, &tb, J0, beta) != 0)
+        return ORBG_ELIMIT;
+    return expand_tables(tb, n, count, table, out);
+}
+
+int64_t orbg_query_order_model(int n, uint32_t count, int table, int m, const int32_t *anchors,
+                               const int32_t *J, const int32_t *beta, int32_t *out)
+{
+    OrbgModel md;
+    if (n < 1 || n > ORBG_MAX_N || (count > 0 && !out) || table < 0 || table > 2 ||
+        !make_model(n, m, anchors, J, beta, &md))
+        return ORBG_EINVAL;
+    if (count == 0)
+        return 0;
+    OrbgTables tb;
+    if (orbg_build_tables_model(n, count, md, &tb) != 0)
+        return ORBG_ELIMIT;
+    return expand_tables(tb, n, count, table, out);
 }
 
 int orbg_codeset_set_tuning(orbg_codeset *set, const orbg_tuning *t)
@@ -317,14 +364,13 @@ int orbg_load_code(const uint8_t *mat, int kind, int n, int k, uint32_t max_quer
     return orbg_load_code_line(mat, kind, n, k, max_query_cap, 0, 1, out);
 }
 
-int orbg_load_code_line(const uint8_t *mat, int kind, int n, int k, uint32_t max_query_cap,
-                        int32_t J0, int32_t beta, orbg_code **out)
+namespace {
+
+/* orbg_load_code for the order of model md (m-segment), or of the line
+ * (J0, beta) when md is NULL. */
+int load_code(const uint8_t *mat, int kind, int n, int k, uint32_t max_query_cap,
+              const OrbgModel *md, int32_t J0, int32_t beta, orbg_code **out)
 {
-    if (!out)
-        return ORBG_EINVAL;
-    *out = nullptr;
-    if (J0 < 0 || beta < 1 || J0 > ORBG_MAX_LINE || beta > ORBG_MAX_LINE)
-        return ORBG_EINVAL;
     if (!mat || (kind != ORBG_MAT_H && kind != ORBG_MAT_G) || n < 1 || k < 0 || k >= n)
         return ORBG_EINVAL;
     if (n > ORBG_MAX_N || n - k > ORBG_MAX_R)
@@ -378,7 +424,8 @@ int orbg_load_code_line(const uint8_t *mat, int kind, int n, int k, uint32_t max
             if (c->H[(size_t)i * n + j])
                 hcol[(size_t)j * c->w32 + i / 32] |= 1u << (i % 32);
     OrbgTables tb;
-    int trc = orbg_build_tables(n, cap, &tb, J0, beta);
+    int trc = md ? orbg_build_tables_model(n, cap, *md, &tb)
+                 : orbg_build_tables(n, cap, &tb, J0, beta);
     if (trc != 0) {
         delete c;
         return ORBG_ELIMIT;
@@ -446,6 +493,32 @@ int orbg_load_code_line(const uint8_t *mat, int kind, int n, int k, uint32_t max
     c->dev.w32 = c->w32;
     *out = c;
     return ORBG_OK;
+}
+
+}  // namespace
+
+int orbg_load_code_line(const uint8_t *mat, int kind, int n, int k, uint32_t max_query_cap,
+                        int32_t J0, int32_t beta, orbg_code **out)
+{
+    if (!out)
+        return ORBG_EINVAL;
+    *out = nullptr;
+    if (J0 < 0 || beta < 1 || J0 > ORBG_MAX_LINE || beta > ORBG_MAX_LINE)
+        return ORBG_EINVAL;
+    return load_code(mat, kind, n, k, max_query_cap, nullptr, J0, beta, out);
+}
+
+int orbg_load_code_model(const uint8_t *mat, int kind, int n, int k, uint32_t max_query_cap,
+                         int m, const int32_t *anchors, const int32_t *J, const int32_t *beta,
+                         orbg_code **out)
+{
+    if (!out)
+        return ORBG_EINVAL;
+    *out = nullptr;
+    OrbgModel md;
+    if (n < 1 || !make_model(n, m, anchors, J, beta, &md))
+        return ORBG_EINVAL;
+    return load_code(mat, kind, n, k, max_query_cap, &md, 0, 1, out);
 }
 
 int orbg_free_code(orbg_code *code)

@@ -116,6 +116,20 @@ struct OrbgTables {
  * (one-line full ORBGRAND; J0 = 0, beta = 1 is basic ORBGRAND). */
 #define ORBG_MAX_LINE 1024
 int orbg_build_tables(int n, uint64_t cap, OrbgTables *out, long J0 = 0, long beta = 1);
+/* The m-segment model of Eq. relest_seg: segment i = 1..m covers the
+ * sorted positions I[i-1] < j <= I[i] (I[0] = 0, I[m] = n) and position j
+ * weighs J[i-1] + beta[i-1] (j - I[i-1]); beta >= 1, J[i-1] >= -beta[i-1]. */
+#define ORBG_MAX_SEG 8
+#define ORBG_MAX_MODEL (1L << 20) /* largest J or beta of a model */
+struct OrbgModel {
+    int m;
+    int I[ORBG_MAX_SEG + 1];
+    long J[ORBG_MAX_SEG];
+    long beta[ORBG_MAX_SEG];
+};
+/* The tables for the m-segment order (reliability weight, then Hamming
+ * weight, then positions lexicographically), single and pair runs only. */
+int orbg_build_tables_model(int n, uint64_t cap, const OrbgModel &md, OrbgTables *out);
 int orbg_run_pattern(const OrbgRun &r, int j, const uint32_t *trip, int *v);
 
 /* GF(2) helpers on dense 0/1 byte matrices (row-major). */

@@ -8,10 +8,13 @@
  * intpart) in lexicographic order, the order Algorithm 2 (Landslide)
  * generates.  This file enumerates that order directly, as lexicographic
  * prefixes followed by a run of pairs or of triples (see orbg_internal.h),
- * not with Landslide.
+ * not with Landslide.  The one-line order of full ORBGRAND (Sec. III-D)
+ * reorders the same (W, w) classes; the m-segment order (Eq. relest_seg)
+ * is built pattern by pattern (orbg_build_tables_model).
  */
 #include <algorithm>
 #include <cstring>
+#include <queue>
 #include <vector>
 
 #include "orbg_internal.h"
@@ -252,66 +255,12 @@ void floors(const std::vector<OrbgRun> &runs, std::vector<uint32_t> *out)
     }
 }
 
-}  // namespace
-
-int orbg_build_tables(int n, uint64_t cap, OrbgTables *out, long J0, long beta)
+/* Group floors and reaches, the flat table and the CTA table's triple
+ * needs, from the two run tables (and X3) of `out`. */
+void finish_tables(OrbgTables *out)
 {
-    if (n < 1 || n > 256 || cap < 1 || J0 < 0 || beta < 1 || J0 > ORBG_MAX_LINE ||
-        beta > ORBG_MAX_LINE)
-        return -1;
-    /* warp table */
-    Builder bw;
-    bw.n = n;
-    bw.cta = false;
-    bw.J0 = J0;
-    bw.beta = beta;
-    out->runs.clear();
-    uint64_t patterns = 0;
-    int wdeep = 0;
-    int rc = bw.build(cap, &out->runs, &patterns, &wdeep);
-    if (rc)
-        return rc;
-    out->patterns = patterns;
-    out->wmax_logistic = wdeep;
-    if (patterns >= 0xFFFFFFFFull)
-        return -3;
-    /* X3: every triple c < a < b <= n by sum (<= the table's depth, within
-     * ORBG_X3_MAX entries), then c, then a */
-    std::vector<uint32_t> x3off(ORBG_MAX_LOGISTIC + 2, 0);
-    out->trip.clear();
-    int s3max = 0;
-    for (int S3 = 6; S3 <= wdeep; S3++) {
-        size_t cnt = 0;
-        for (int c = trip_c_lo(S3, 1, n); c <= trip_c_hi(S3); c++)
-            cnt += (size_t)(pair_hi(S3 - c) - pair_lo(S3 - c, c + 1, n) + 1);
-        if (out->trip.size() + cnt > ORBG_X3_MAX)
-            break;
-        x3off[S3] = (uint32_t)out->trip.size();
-        for (int c = trip_c_lo(S3, 1, n); c <= trip_c_hi(S3); c++)
-            for (int a = pair_lo(S3 - c, c + 1, n); a <= pair_hi(S3 - c); a++)
-                out->trip.push_back((uint32_t)(c - 1) | ((uint32_t)(a - 1) << 8) |
-                                    ((uint32_t)(S3 - c - a - 1) << 16));
-        s3max = S3;
-    }
-    out->s3max = s3max;
-    out->x3off.assign(x3off.begin(), x3off.begin() + (s3max + 2));
-    out->x3off[s3max + 1] = (uint32_t)out->trip.size();
-    /* CTA table */
-    Builder bc;
-    bc.n = n;
-    bc.cta = true;
-    bc.J0 = J0;
-    bc.beta = beta;
-    bc.s3max = s3max;
-    bc.x3off = &x3off;
-    out->runs_cta.clear();
-    uint64_t patterns_c = 0;
-    int wdeep_c = 0;
-    rc = bc.build(cap, &out->runs_cta, &patterns_c, &wdeep_c);
-    if (rc)
-        return rc;
-    if (patterns_c != patterns)
-        return -5;
+    const uint64_t patterns = out->patterns;
+    const int s3max = out->s3max;
     floors(out->runs, &out->group_floor);
     floors(out->runs_cta, &out->group_floor_cta);
     /* flat table: the leading patterns of weight <= ORBG_FLAT_POS, at most
@@ -383,6 +332,231 @@ int orbg_build_tables(int n, uint64_t cap, OrbgTables *out, long J0, long beta)
             out->s3_cta[g] = (uint8_t)s3;
         }
     }
+}
+
+}  // namespace
+
+int orbg_build_tables(int n, uint64_t cap, OrbgTables *out, long J0, long beta)
+{
+    if (n < 1 || n > 256 || cap < 1 || J0 < 0 || beta < 1 || J0 > ORBG_MAX_LINE ||
+        beta > ORBG_MAX_LINE)
+        return -1;
+    /* warp table */
+    Builder bw;
+    bw.n = n;
+    bw.cta = false;
+    bw.J0 = J0;
+    bw.beta = beta;
+    out->runs.clear();
+    uint64_t patterns = 0;
+    int wdeep = 0;
+    int rc = bw.build(cap, &out->runs, &patterns, &wdeep);
+    if (rc)
+        return rc;
+    out->patterns = patterns;
+    out->wmax_logistic = wdeep;
+    if (patterns >= 0xFFFFFFFFull)
+        return -3;
+    /* X3: every triple c < a < b <= n by sum (<= the table's depth, within
+     * ORBG_X3_MAX entries), then c, then a */
+    std::vector<uint32_t> x3off(ORBG_MAX_LOGISTIC + 2, 0);
+    out->trip.clear();
+    int s3max = 0;
+    for (int S3 = 6; S3 <= wdeep; S3++) {
+        size_t cnt = 0;
+        for (int c = trip_c_lo(S3, 1, n); c <= trip_c_hi(S3); c++)
+            cnt += (size_t)(pair_hi(S3 - c) - pair_lo(S3 - c, c + 1, n) + 1);
+        if (out->trip.size() + cnt > ORBG_X3_MAX)
+            break;
+        x3off[S3] = (uint32_t)out->trip.size();
+        for (int c = trip_c_lo(S3, 1, n); c <= trip_c_hi(S3); c++)
+            for (int a = pair_lo(S3 - c, c + 1, n); a <= pair_hi(S3 - c); a++)
+                out->trip.push_back((uint32_t)(c - 1) | ((uint32_t)(a - 1) << 8) |
+                                    ((uint32_t)(S3 - c - a - 1) << 16));
+        s3max = S3;
+    }
+    out->s3max = s3max;
+    out->x3off.assign(x3off.begin(), x3off.begin() + (s3max + 2));
+    out->x3off[s3max + 1] = (uint32_t)out->trip.size();
+    /* CTA table */
+    Builder bc;
+    bc.n = n;
+    bc.cta = true;
+    bc.J0 = J0;
+    bc.beta = beta;
+    bc.s3max = s3max;
+    bc.x3off = &x3off;
+    out->runs_cta.clear();
+    uint64_t patterns_c = 0;
+    int wdeep_c = 0;
+    rc = bc.build(cap, &out->runs_cta, &patterns_c, &wdeep_c);
+    if (rc)
+        return rc;
+    if (patterns_c != patterns)
+        return -5;
+    finish_tables(out);
+    return 0;
+}
+
+namespace {
+
+/*
+ * m-segment full ORBGRAND (Sec. III-D, Eq. relest_seg): position j of
+ * segment i, I_{i-1} < j <= I_i, weighs rho_j = J_{i-1} + beta_i (j -
+ * I_{i-1}) >= 0, and patterns come in increasing reliability weight (the
+ * sum of rho over the flipped positions), then Hamming weight, then
+ * positions lexicographically.
+ *
+ * Patterns of increasing weight come from a best-first walk over subsets
+ * of the positions ranked by weight, x_0 <= x_1 <= ...: a subset whose
+ * highest rank is k leads to the subset with rank k + 1 added and to the
+ * one with rank k replaced by k + 1.  Every non-empty subset is reached
+ * exactly once, from {0}, and never weighs less than the subset it comes
+ * from, so a min-heap pops weights in order.  All subsets of one weight R
+ * are collected, ordered by (w, positions) and cut into runs: consecutive
+ * patterns (p, a, b), (p, a + 1, b - 1), ... with one prefix p become one
+ * pair run; the rest are single runs.
+ */
+struct ModelBuilder {
+    Builder b;                           /* run records and class flush */
+    std::vector<long> x;                 /* weights by rank, lightest first */
+    std::vector<int> pos;                /* 1-based position of each rank */
+    struct Node {
+        int parent;                      /* the subset without `rank`, -1 = empty */
+        int rank;
+    };
+    std::vector<Node> nodes;
+
+    int build(uint64_t cap, std::vector<OrbgRun> *out, uint64_t *patterns) {
+        const int n = b.n;
+        typedef std::pair<long, int> Item;   /* (weight, node) */
+        std::priority_queue<Item, std::vector<Item>, std::greater<Item>> heap;
+        nodes.clear();
+        nodes.push_back(Node{-1, 0});
+        heap.push(Item(x[0], 0));
+        b.t = 1;
+        std::vector<std::vector<int>> bucket;
+        long R = 0;
+        bool first = true;
+        while (b.t <= cap && (first || !heap.empty())) {
+            bucket.clear();
+            if (first)
+                bucket.push_back(std::vector<int>()); /* the empty pattern, weight 0 */
+            else
+                R = heap.top().first;
+            first = false;
+            while (!heap.empty() && heap.top().first == R) {
+                const int id = heap.top().second;
+                heap.pop();
+                const int k = nodes[id].rank;
+                if (k + 1 < n) {
+                    const int par = nodes[id].parent;
+                    nodes.push_back(Node{id, k + 1});
+                    heap.push(Item(R + x[k + 1], (int)nodes.size() - 1));
+                    nodes.push_back(Node{par, k + 1});
+                    heap.push(Item(R - x[k] + x[k + 1], (int)nodes.size() - 1));
+                }
+                std::vector<int> v;
+                for (int q = id; q >= 0; q = nodes[q].parent)
+                    v.push_back(pos[nodes[q].rank]);
+                std::sort(v.begin(), v.end());
+                bucket.push_back(v);
+            }
+            if (nodes.size() > (size_t)1 << 30)
+                return -2;
+            std::sort(bucket.begin(), bucket.end(),
+                      [](const std::vector<int> &p, const std::vector<int> &q) {
+                          return p.size() != q.size() ? p.size() < q.size() : p < q;
+                      });
+            if (emit_bucket(bucket, out))
+                return -2;
+        }
+        *patterns = b.t - 1;
+        return b.overflow ? -2 : 0;
+    }
+
+    /* Runs of one weight's patterns, class by class (one class per w). */
+    int emit_bucket(const std::vector<std::vector<int>> &P, std::vector<OrbgRun> *out) {
+        size_t i = 0;
+        while (i < P.size()) {
+            const int w = (int)P[i].size();
+            size_t end = i;
+            while (end < P.size() && (int)P[end].size() == w)
+                end++;
+            if (w - 2 > ORBG_RUN_MAX_PRE)
+                return -2;
+            for (size_t s = i; s < end;) {
+                const std::vector<int> &v = P[s];
+                size_t e = s + 1;
+                if (w >= 2) {
+                    const int a = v[w - 2], bb = v[w - 1];
+                    while (e < end && std::equal(v.begin(), v.end() - 2, P[e].begin()) &&
+                           P[e][w - 2] == a + (int)(e - s) && P[e][w - 1] == bb - (int)(e - s))
+                        e++;
+                    if (a + bb <= 255) {
+                        for (int q = 0; q < w - 2; q++)
+                            b.pre[q] = v[q];
+                        OrbgRun r = b.blank(ORBG_RUN_PAIRS, w - 2);
+                        r.aux = (uint32_t)(a + bb) | ((uint32_t)a << 8);
+                        b.emit(r, (uint64_t)(e - s));
+                        s = e;
+                        continue;
+                    }
+                }
+                if (w > ORBG_RUN_MAX_PRE)
+                    return -2;
+                for (size_t q = s; q < e; q++) {
+                    for (int z = 0; z < w; z++)
+                        b.pre[z] = P[q][z];
+                    b.single(w);
+                }
+                s = e;
+            }
+            b.flush(out);
+            i = end;
+        }
+        return 0;
+    }
+};
+
+}  // namespace
+
+int orbg_build_tables_model(int n, uint64_t cap, const OrbgModel &md, OrbgTables *out)
+{
+    if (n < 1 || n > 256 || cap < 1 || md.m < 1 || md.m > ORBG_MAX_SEG || md.I[0] != 0 ||
+        md.I[md.m] != n)
+        return -1;
+    for (int i = 0; i < md.m; i++)
+        if (md.I[i + 1] <= md.I[i] || md.beta[i] < 1 || md.beta[i] > ORBG_MAX_MODEL ||
+            md.J[i] < -md.beta[i] || md.J[i] > ORBG_MAX_MODEL)
+            return -1;
+    ModelBuilder mb;
+    mb.b.n = n;
+    mb.b.cta = false;
+    std::vector<std::pair<long, int>> w;
+    for (int i = 0; i < md.m; i++)
+        for (int j = md.I[i] + 1; j <= md.I[i + 1]; j++)
+            w.push_back(std::make_pair(md.J[i] + md.beta[i] * (long)(j - md.I[i]), j));
+    std::sort(w.begin(), w.end());
+    for (const auto &e : w) {
+        mb.x.push_back(e.first);
+        mb.pos.push_back(e.second);
+    }
+    out->runs.clear();
+    uint64_t patterns = 0;
+    const int rc = mb.build(cap, &out->runs, &patterns);
+    if (rc)
+        return rc;
+    if (patterns >= 0xFFFFFFFFull)
+        return -3;
+    out->patterns = patterns;
+    out->wmax_logistic = 0;
+    /* no triple runs: the CTA table is the warp table, X3 is empty */
+    out->runs_cta = out->runs;
+    out->trip.clear();
+    out->s3max = 0;
+    out->x3off.assign(2, 0u);
+    finish_tables(out);
     return 0;
 }
 

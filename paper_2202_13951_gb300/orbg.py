@@ -87,6 +87,8 @@ def load_library(path=None):
     i64 = ctypes.c_int64
     lib.orbg_load_code.argtypes = [vp, i32, i32, i32, u32, ctypes.POINTER(vp)]
     lib.orbg_load_code_line.argtypes = [vp, i32, i32, i32, u32, i32, i32, ctypes.POINTER(vp)]
+    lib.orbg_load_code_model.argtypes = [vp, i32, i32, i32, u32, i32, vp, vp, vp,
+                                         ctypes.POINTER(vp)]
     lib.orbg_free_code.argtypes = [vp]
     lib.orbg_code_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(u32), vp]
@@ -109,6 +111,8 @@ def load_library(path=None):
     lib.orbg_query_order.restype = i64
     lib.orbg_query_order_line.argtypes = [i32, u32, i32, i32, i32, vp]
     lib.orbg_query_order_line.restype = i64
+    lib.orbg_query_order_model.argtypes = [i32, u32, i32, i32, vp, vp, vp, vp]
+    lib.orbg_query_order_model.restype = i64
     lib.orbg_server_create.argtypes = [vp, ctypes.c_size_t, u32, i32, i64, ctypes.POINTER(vp)]
     lib.orbg_server_submit.argtypes = [vp, ctypes.c_uint64, i32, vp, i64]
     lib.orbg_server_poll.argtypes = [vp, vp, i32, i32]
@@ -118,7 +122,8 @@ def load_library(path=None):
     lib.orbg_server_destroy.argtypes = [vp]
     lib.orbg_server_replay.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                        ctypes.POINTER(ctypes.c_double)]
-    for f in ("orbg_load_code", "orbg_load_code_line", "orbg_free_code", "orbg_code_info", "orbg_decode",
+    for f in ("orbg_load_code", "orbg_load_code_line", "orbg_load_code_model",
+              "orbg_free_code", "orbg_code_info", "orbg_decode",
               "orbg_codeset_create", "orbg_codeset_free", "orbg_decode_batched",
               "orbg_decode_batched_noalloc", "orbg_server_create", "orbg_server_submit",
               "orbg_server_poll", "orbg_server_fetch", "orbg_server_stats_get",
@@ -189,6 +194,28 @@ def orbg_load_code_line(mat, kind, n, k, max_query_cap, J0, beta):
     _check(lib.orbg_load_code_line(m.ctypes.data, int(kind), int(n), int(k),
                                    int(max_query_cap), int(J0), int(beta), ctypes.byref(h)),
            "orbg_load_code_line")
+    return h
+
+
+def _model_arrays(model):
+    """(anchors, J, beta) -> m and int32 arrays (kept alive by the caller)."""
+    anchors, J, beta = model
+    m = len(J)
+    a = np.ascontiguousarray(list(anchors) or [0], dtype=np.int32)
+    return (m, a, np.ascontiguousarray(J, dtype=np.int32),
+            np.ascontiguousarray(beta, dtype=np.int32))
+
+
+def orbg_load_code_model(mat, kind, n, k, max_query_cap, model):
+    """model: (anchors I_1..I_{m-1}, J_0..J_{m-1}, beta_1..beta_m)."""
+    lib = load_library()
+    m = np.ascontiguousarray(mat, dtype=np.uint8)
+    h = ctypes.c_void_p()
+    segs, a, J, beta = _model_arrays(model)
+    _check(lib.orbg_load_code_model(m.ctypes.data, int(kind), int(n), int(k),
+                                    int(max_query_cap), segs, a.ctypes.data, J.ctypes.data,
+                                    beta.ctypes.data, ctypes.byref(h)),
+           "orbg_load_code_model")
     return h
 
 
@@ -383,22 +410,40 @@ def orbg_query_order_line(n, count, table, J0, beta):
     return [tuple(int(x) for x in row[1:1 + row[0]]) for row in out[:got]]
 
 
+def orbg_query_order_model(n, count, table, model):
+    """orbg_query_order for the m-segment order of model (anchors, J, beta)."""
+    lib = load_library()
+    out = np.zeros((count, n + 1), np.int32)
+    segs, a, J, beta = _model_arrays(model)
+    got = lib.orbg_query_order_model(int(n), int(count), int(table), segs, a.ctypes.data,
+                                     J.ctypes.data, beta.ctypes.data, out.ctypes.data)
+    if got < 0:
+        raise OrbgError(int(got), "orbg_query_order_model")
+    return [tuple(int(x) for x in row[1:1 + row[0]]) for row in out[:got]]
+
+
 # ------------------------------------------------------- convenience layer
 
 class Code:
     """Owning wrapper of an orbg_code handle."""
 
-    def __init__(self, mat, kind=ORBG_MAT_H, n=None, k=None, max_query_cap=0, line=None):
-        """line: (J0, beta) for one-line full ORBGRAND, None for basic."""
+    def __init__(self, mat, kind=ORBG_MAT_H, n=None, k=None, max_query_cap=0, line=None,
+                 model=None):
+        """line: (J0, beta) for one-line full ORBGRAND; model: (anchors, J,
+        beta) for m-segment full ORBGRAND; neither for basic."""
         mat = np.asarray(mat, dtype=np.uint8)
         n = mat.shape[1] if n is None else n
         if k is None:
             k = n - mat.shape[0] if kind == ORBG_MAT_H else mat.shape[0]
         self.n, self.k = int(n), int(k)
-        if line is None:
-            self.handle = orbg_load_code(mat, kind, n, k, max_query_cap)
-        else:
+        if line is not None and model is not None:
+            raise ValueError("give a line or a model, not both")
+        if model is not None:
+            self.handle = orbg_load_code_model(mat, kind, n, k, max_query_cap, model)
+        elif line is not None:
             self.handle = orbg_load_code_line(mat, kind, n, k, max_query_cap, *line)
+        else:
+            self.handle = orbg_load_code(mat, kind, n, k, max_query_cap)
 
     def close(self):
         if self.handle is not None and self.handle.value:

@@ -90,6 +90,24 @@ def test_decode_argument_checks_without_gpu(lib):
     for J0, beta in ((-1, 1), (0, 0), (2000, 1), (0, 2000)):
         assert lib.orbg_query_order_line(7, 4, 0, J0, beta, out.ctypes.data) == orbg.ORBG_EINVAL
         assert lib.orbg_load_code_line(None, 0, 7, 4, 0, J0, beta, None) == orbg.ORBG_EINVAL
+    H = np.zeros((3, 7), np.uint8)
+    h = ctypes.c_void_p()
+    # m-segment models out of range: a position weighing below 0, beta 0,
+    # anchors out of order or outside 1..n-1, too many segments
+    for m, anchors, J, beta in ((1, [], [-2], [1]), (1, [], [0], [0]), (2, [4], [0, -3], [1, 2]),
+                                (2, [0], [0, 0], [1, 1]), (2, [7], [0, 0], [1, 1]),
+                                (3, [4, 3], [0, 0, 0], [1, 1, 1]), (9, [1] * 8, [0] * 9, [1] * 9),
+                                (0, [], [0], [1]), (1, [], [1 << 21], [1])):
+        a = np.array(anchors or [0], np.int32)
+        j = np.array(J, np.int32)
+        b = np.array(beta, np.int32)
+        assert lib.orbg_query_order_model(7, 4, 0, m, a.ctypes.data, j.ctypes.data,
+                                          b.ctypes.data, out.ctypes.data) == orbg.ORBG_EINVAL
+        assert lib.orbg_load_code_model(H.ctypes.data, 0, 7, 4, 0, m, a.ctypes.data,
+                                        j.ctypes.data, b.ctypes.data,
+                                        ctypes.byref(h)) == orbg.ORBG_EINVAL
+    assert lib.orbg_query_order_model(7, 4, 0, 1, None, None, None,
+                                      out.ctypes.data) == orbg.ORBG_EINVAL
 
 
 @pytest.mark.parametrize("n,count", [(1, 2), (3, 8), (7, 128), (12, 4096),
@@ -134,3 +152,57 @@ def test_query_order_line_tables_match_oracle(lib, n, count, line):
     flat = orbg.orbg_query_order_line(n, count, 2, *line)
     assert 0 < len(flat) <= 256
     assert flat == want[:len(flat)]
+
+
+def _check_model_tables(n, count, model):
+    want = oracle.enumerate_patterns_mline(n, count, model)
+    assert orbg.orbg_query_order_model(n, count, 0, model) == want
+    assert orbg.orbg_query_order_model(n, count, 1, model) == want
+    flat = orbg.orbg_query_order_model(n, count, 2, model)
+    assert 0 < len(flat) <= 256
+    assert flat == want[:len(flat)]
+
+
+def test_query_order_model_tables_match_oracle(lib):
+    """The m-segment tables (Sec. III-D, Eq. relest_seg) expand to exactly
+    the m-segment oracle's order in all three tables the kernels read: the
+    whole order for n = 10 under models of one to four segments, zero-weight
+    positions included."""
+    import oracle_pins
+    for model in oracle_pins.MODELS10:
+        _check_model_tables(10, 1 << 10, model)
+
+
+@pytest.mark.parametrize("n,k", [(64, 48), (127, 113), (128, 105), (255, 231)])
+def test_query_order_fitted_model_tables_match_oracle(lib, n, k):
+    """Models fitted (Sec. III-E) to AWGN blocks at three SNRs, one to four
+    lines, both quantisations: the tables expand to the oracle's order."""
+    code = workloads.rlc(n, k, seed=n)
+    seen = set()
+    for snr in (2.0, 4.0, 6.0):
+        llr, _ = workloads.awgn_llr(code, 2, snr, seed=int(snr) + n)
+        for b in range(llr.shape[0]):
+            for lines in (1, 2, 3, 4):
+                for div in (False, True):
+                    model = oracle.fit(llr[b], lines, div)
+                    if model not in seen:
+                        seen.add(model)
+                        _check_model_tables(n, 20000, model)
+    assert len(seen) >= 6
+
+
+def test_query_order_one_segment_model_is_the_line(lib):
+    """One segment with J_0 >= 0 is the one-line order; J_0 = 0, beta = 1
+    the basic order (built without triple runs here)."""
+    for n in (12, 64, 128):
+        for J0, beta in ((0, 1), (3, 1), (5, 2)):
+            assert (orbg.orbg_query_order_model(n, 30000, 0, ((), (J0,), (beta,))) ==
+                    orbg.orbg_query_order_line(n, 30000, 0, J0, beta))
+
+
+def test_query_order_model_limit(lib):
+    """A model whose order reaches position 256 among a pattern's leading
+    positions, which a run stores in a byte, is refused with ELIMIT."""
+    with pytest.raises(orbg.OrbgError) as ei:
+        orbg.orbg_query_order_model(256, 8, 0, ((255,), (1000, 0), (1, 1)))
+    assert ei.value.status == orbg.ORBG_ELIMIT
