@@ -69,6 +69,9 @@ def parse_args(argv=None):
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--line", default="",
                    help="J0,beta: decode one-line full ORBGRAND (Sec. III-D) instead of basic")
+    p.add_argument("--model", default="",
+                   help="I_1,..;J_0,..;beta_1,..: decode m-segment full ORBGRAND (Sec. III-D, "
+                        "Eq. relest_seg) under this model instead of basic")
     p.add_argument("--no-graph", action="store_true",
                    help="time direct calls instead of replays of a captured CUDA graph")
     p.add_argument("--ref-sample", type=int, default=8000,
@@ -87,11 +90,23 @@ def parse_args(argv=None):
                         "for the batched launch (orbg_tuning)")
     args = p.parse_args(argv)
     select_workload(args.workload, args.blocks_per_point)
+    global LINE, MODEL, WORKLOAD
+    if args.line and args.model:
+        raise SystemExit("give --line or --model, not both")
     if args.line:
-        global LINE, WORKLOAD
         LINE = tuple(int(x) for x in args.line.split(","))
         WORKLOAD += ", one-line full ORBGRAND J0=%d beta=%d" % LINE
+    if args.model:
+        parts = [tuple(int(x) for x in f.split(",") if x.strip()) for f in args.model.split(";")]
+        if len(parts) != 3 or len(parts[1]) != len(parts[2]) or len(parts[0]) + 1 != len(parts[1]):
+            raise SystemExit("--model wants I_1..I_{m-1};J_0..J_{m-1};beta_1..beta_m")
+        MODEL = tuple(parts)
+        WORKLOAD += ", %d-segment full ORBGRAND %s" % (len(MODEL[1]), describe_model(MODEL))
     return args
+
+
+def describe_model(model):
+    return "I=%s J=%s beta=%s" % tuple(",".join(str(x) for x in f) or "-" for f in model)
 
 
 def select_workload(name, b_per_point):
@@ -107,6 +122,7 @@ def select_workload(name, b_per_point):
 
 WORKLOAD_NAME = "bch"
 LINE = None  # (J0, beta) for one-line full ORBGRAND, None for basic
+MODEL = None  # (anchors, J, beta) for m-segment full ORBGRAND, None for basic
 
 
 CODE_FN = "config2_code"
@@ -160,39 +176,44 @@ def sum_over_ranks(value, world, device=None):
     return float(t.item())
 
 
-def class_weight_prefix(n, max_queries, line=None):
-    """Cumulative Hamming weight over the query order, by class: the order
-    visits classes (W, w) -- the partitions of W into w distinct parts <= n
-    -- in increasing J0 w + beta W, w ascending within it (basic ORBGRAND:
-    J0 = 0, beta = 1, so logistic weights W = 0, 1, ...).  Returns
-    (class_end[], class_w[]) up to max_queries, so sum_{t<=q} w_t follows
-    from q alone."""
+def position_weights(n, line=None, model=None):
+    """rho_j for the sorted positions j = 1..n: j for basic ORBGRAND, J0 + beta j
+    for a line, J_{i-1} + beta_i (j - I_{i-1}) on segment i of a model
+    (Eq. relest_seg)."""
+    if model is not None:
+        anchors, J, beta = model
+        I = [0] + list(anchors) + [n]
+        return [J[i] + beta[i] * (j - I[i]) for i in range(len(J))
+                for j in range(I[i] + 1, I[i + 1] + 1)]
     J0, beta = line if line else (0, 1)
-    # N[w][W]: sets of w distinct parts in [1, n] summing to W (DP over parts)
-    Wmax = 1
+    return [J0 + beta * j for j in range(1, n + 1)]
+
+
+def class_weight_prefix(n, max_queries, line=None, model=None):
+    """Cumulative Hamming weight over the query order, by class: the order
+    visits classes (R, w) -- the w-subsets of the positions whose weights
+    rho_j sum to R -- in increasing R, w ascending within it (basic
+    ORBGRAND: rho_j = j, so R is the logistic weight).  Returns (class_end[],
+    class_w[]) up to max_queries, so sum_{t<=q} w_t follows from q alone."""
+    rho = position_weights(n, line, model)
+    sat = 1 << 61
+    Rmax = 64
     while True:
-        Wmax *= 2
-        N = np.zeros((Wmax + 1, Wmax + 1), dtype=object)  # [w][W]
-        N[0][0] = 1
-        for part in range(1, min(n, Wmax) + 1):
-            for w in range(Wmax, 0, -1):
-                N[w][part:] = N[w][part:] + N[w - 1][:Wmax + 1 - part]
-        # classes of reliability weight <= beta Wmax are all within W <= Wmax
-        classes = sorted((J0 * w + beta * W, w, int(N[w][W]))
-                         for w in range(Wmax + 1) for W in range(Wmax + 1)
-                         if N[w][W] and J0 * w + beta * W <= beta * Wmax)
-        total = sum(c for _, _, c in classes)
-        if total >= max_queries or Wmax > 4096:
+        # N[w][R]: w-subsets of weight R (saturating counts)
+        N = np.zeros((n + 1, Rmax + 1), np.int64)
+        N[0, 0] = 1
+        for r in rho:
+            if r <= Rmax:
+                N[1:, r:] += N[:-1, :Rmax + 1 - r]
+                np.minimum(N, sat, out=N)
+        if N.astype(np.float64).sum() >= max_queries or Rmax >= sum(rho):
             break
-    ends, ws = [], []
-    t = 0
-    for _, w, c in classes:
-        t += c
-        ends.append(t)
-        ws.append(w)
-        if t >= max_queries:
-            break
-    return np.array(ends, np.int64), np.array(ws, np.int64)
+        Rmax *= 2
+    w_idx = np.nonzero(N.T)          # classes in R order, w ascending within R
+    counts = N.T[w_idx]
+    cut = int(np.searchsorted(np.cumsum(counts.astype(np.float64)), max_queries)) + 1
+    ends = np.cumsum(counts[:cut])
+    return ends.astype(np.int64), w_idx[1][:cut].astype(np.int64)
 
 
 def sum_weights(q, class_end, class_w):
@@ -284,10 +305,12 @@ class ClockSampler:
 # ------------------------------------------------------------- CPU side
 
 def _oracle_worker(args):
-    H, llr, cap, line = args
+    H, llr, cap, line, model = args
     import oracle
     t = time.perf_counter()
-    if line:
+    if model:
+        _, q, ab, _ = oracle.decode_batch_mline(H, llr, cap, model)
+    elif line:
         _, q, ab, _ = oracle.decode_batch_1line(H, llr, cap, *line)
     else:
         _, q, ab, _ = oracle.decode_batch(H, llr, cap)
@@ -308,12 +331,12 @@ def cpu_sample(llr, per_point, step):
 def run_oracle(H, llr, cap, procs):
     """Decode llr on `procs` spawned single-threaded oracle processes."""
     if procs <= 1:
-        return _oracle_worker((H, llr, cap, LINE))
+        return _oracle_worker((H, llr, cap, LINE, MODEL))
     import multiprocessing as mp
     chunks = np.array_split(llr, procs)
     ctx = mp.get_context("spawn")
     with ctx.Pool(procs) as pool:
-        res = pool.map(_oracle_worker, [(H, c, cap, LINE) for c in chunks])
+        res = pool.map(_oracle_worker, [(H, c, cap, LINE, MODEL) for c in chunks])
     return max(r[0] for r in res), sum(r[1] for r in res), sum(r[2] for r in res)
 
 
@@ -348,7 +371,7 @@ def bench_reference(args, rank, world):
             sample = cpu_sample(llr, per_point, s)
             chunks = np.array_split(sample, cores)
             t0 = time.perf_counter()
-            res = pool.map(_oracle_worker, [(code.H, c, CAP, LINE) for c in chunks])
+            res = pool.map(_oracle_worker, [(code.H, c, CAP, LINE, MODEL) for c in chunks])
             dt = time.perf_counter() - t0
             if s >= args.warmup:
                 times.append(dt)
@@ -410,7 +433,10 @@ class Job:
             raise SystemExit("--form plain needs a single-code workload")
         self.B = B
         self.n_of_block = np.array([c.n for c in self.codes], np.int64)[self.cid_np]
-        self.objs = [orbg.Code(c.H, max_query_cap=CAP, line=LINE) for c in self.codes]
+        if MODEL is not None and any(MODEL[0] and MODEL[0][-1] >= c.n for c in self.codes):
+            raise SystemExit("--model: every anchor must lie below each code's n")
+        self.objs = [orbg.Code(c.H, max_query_cap=CAP, line=LINE, model=MODEL)
+                     for c in self.codes]
         self.cs = orbg.CodeSet(self.objs)
         self.llr = torch.from_numpy(self.llr_np).to(dev)
         n_total = int(self.n_of_block.sum())
@@ -468,7 +494,7 @@ class Job:
             sel = self.cid_np == j
             if not sel.any():
                 continue
-            ends, ws = class_weight_prefix(code.n, CAP, LINE)
+            ends, ws = class_weight_prefix(code.n, CAP, LINE, MODEL)
             qj = qh[sel]
             w32 = (code.r + 31) // 32
             total += w32 * (sum_weights(qj, ends, ws) + int(qj.sum()))
@@ -581,8 +607,10 @@ def bench_ours(args, rank, world, local):
                              ">" if job.llr_np.nbytes > 129e6 else "<=")),
                    "tuning": orbg.orbg_codeset_get_tuning(job.cs.handle).as_dict(),
                    "tuning_source": tuned, "timed": graph,
-                   "order": ("one-line full ORBGRAND, J0=%d beta=%d" % LINE) if LINE
-                   else "basic ORBGRAND",
+                   "order": (("%d-segment full ORBGRAND, %s"
+                              % (len(MODEL[1]), describe_model(MODEL))) if MODEL
+                             else ("one-line full ORBGRAND, J0=%d beta=%d" % LINE) if LINE
+                             else "basic ORBGRAND"),
                    "parallelism": "replicas x%d (blocks sharded by rank, no collective)" % world},
         "queries_per_s": queries_total / (total_ms / 1000.0),
         "latency_ms": {"step_p50": statistics.median(per_step),

@@ -74,3 +74,17 @@ def test_class_weight_prefix_one_line_matches_oracle(line):
     _, q, _, sw = oracle.decode_batch_1line(code.H, llr, 10 ** 5, *line)
     ends, ws = bench.class_weight_prefix(code.n, 10 ** 5, line)
     assert bench.sum_weights(q, ends, ws) == int(sw.sum())
+
+
+def test_class_weight_prefix_m_segment_matches_oracle():
+    """The same for m-segment orders (Sec. III-D, Eq. relest_seg): a model
+    with a zero-weight position and models fitted (Sec. III-E) to blocks."""
+    import bench
+    import oracle
+    from paper_2202_13951_gb300 import workloads
+    code = workloads.rlc(64, 48, 5)
+    llr, _ = workloads.awgn_llr(code, 150, 3.0, 8)
+    for model in (((8,), (-2, 11), (2, 1)), oracle.fit(llr[0], 3), oracle.fit(llr[1], 2, True)):
+        _, q, _, sw = oracle.decode_batch_mline(code.H, llr, 10 ** 5, model)
+        ends, ws = bench.class_weight_prefix(code.n, 10 ** 5, model=model)
+        assert bench.sum_weights(q, ends, ws) == int(sw.sum()), model
