@@ -46,13 +46,20 @@ WORKLOADS = {
     "mixed": ("mixed rlc(64,51),(128,112),(256,240),(256,232), code uniform per block, "
               "%d blocks at Eb/N0 U[4,7] dB, query cap 1e6, one launch, autotuned",
               None, (), (401,)),
+    "paper256": ("paper-shaped [256,234] family: ca-polar(256,234[K=245]), crc(256,234), "
+                 "rlc(256,234), bch(255,231), code uniform per block, %d blocks at Eb/N0 "
+                 "U[4,7] dB, query cap 5e6, one launch, autotuned",
+                 None, (), (601,)),
 }
+# multi-code workloads: generator of (codes, code_id, llr, llr_offset, codewords, ebn0)
+# and blocks per step as a multiple of --blocks-per-point
+MIXED = {"mixed": ("config4_inputs", 10), "paper256": ("paper256_inputs", 4)}
 POINTS = (4.0, 5.0, 6.0, 7.0)
 SEEDS = (201, 202, 203, 204)
 B_PER_POINT = 100_000
 WORKLOAD = WORKLOADS["bch"][0] % B_PER_POINT
 CAP = 1_000_000
-CAPS = {"rlc64": 100_000}
+CAPS = {"rlc64": 100_000, "paper256": 5_000_000}
 SMS = 152
 SM_MAX_MHZ = 2070.0
 
@@ -117,7 +124,7 @@ def select_workload(name, b_per_point):
     if name == "rlc64" and b_per_point == 100_000:
         b_per_point = 10_000  # the configuration's 2 x 10,000 blocks
     B_PER_POINT = b_per_point
-    WORKLOAD = desc % (b_per_point * 10 if name == "mixed" else b_per_point)
+    WORKLOAD = desc % (b_per_point * MIXED[name][1] if name in MIXED else b_per_point)
 
 
 WORKLOAD_NAME = "bch"
@@ -358,9 +365,35 @@ def bench_reference(args, rank, world):
         return None
     import oracle
     oracle.build_oracle()
-    code, llr = make_inputs(0)
     cores = os.cpu_count() or 1
-    per_point = max(1, args.ref_sample // len(POINTS))
+    if WORKLOAD_NAME in MIXED:
+        from paper_2202_13951_gb300 import workloads
+        gen, mult = MIXED[WORKLOAD_NAME]
+        B = mult * B_PER_POINT
+        codes, cid, llr_flat, off, _, _ = getattr(workloads, gen)(B=B, seed=SEEDS[0])
+        per_point = args.ref_sample
+
+        def step_work(step):
+            """ref_sample blocks in a stride walk, grouped by code, split over
+            the cores."""
+            idx = (np.arange(step * per_point, (step + 1) * per_point) * 9973) % B
+            work = []
+            for j, code in enumerate(codes):
+                sel = idx[cid[idx] == j]
+                if sel.size:
+                    blk = np.stack([llr_flat[off[b]:off[b] + code.n] for b in sel])
+                    work += [(code.H, c, CAP, LINE, MODEL)
+                             for c in np.array_split(blk, max(1, cores // len(codes)))
+                             if c.shape[0]]
+            return work, idx.size
+    else:
+        code, llr = make_inputs(0)
+        per_point = max(1, args.ref_sample // len(POINTS))
+
+        def step_work(step):
+            sample = cpu_sample(llr, per_point, step)
+            return ([(code.H, c, CAP, LINE, MODEL) for c in np.array_split(sample, cores)],
+                    sample.shape[0])
     # the pool is started once, before any timing
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
@@ -368,14 +401,13 @@ def bench_reference(args, rank, world):
     times, blocks, queries = [], 0, 0
     try:
         for s in range(args.warmup + args.steps):
-            sample = cpu_sample(llr, per_point, s)
-            chunks = np.array_split(sample, cores)
+            work, nblk = step_work(s)
             t0 = time.perf_counter()
-            res = pool.map(_oracle_worker, [(code.H, c, CAP, LINE, MODEL) for c in chunks])
+            res = pool.map(_oracle_worker, work)
             dt = time.perf_counter() - t0
             if s >= args.warmup:
                 times.append(dt)
-                blocks += sample.shape[0]
+                blocks += nblk
                 queries += sum(r[1] for r in res)
     finally:
         pool.close()
@@ -389,15 +421,17 @@ def bench_reference(args, rank, world):
         "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32-llr/u32-syndrome",
         "data": "synthetic BPSK/AWGN, seeded",
-        "config": {"workload": WORKLOAD, "sample_blocks_per_step": sample.shape[0],
+        "config": {"workload": WORKLOAD, "sample_blocks_per_step": nblk,
                    "l2": "n/a (CPU)"},
         "queries_per_s": queries / total,
         "cpu_baseline": {"value": value, "unit": "blocks/s", "cores": cores,
                          "kind": "oracle",
-                         "sample": "%d blocks per step (%d per Eb/N0 point), %d timed steps, "
+                         "sample": "%d blocks per step (%s), %d timed steps, "
                                    "%d single-threaded oracle processes (%s)"
-                                   % (sample.shape[0], per_point, args.steps, cores,
-                                      cpu_model())},
+                                   % (nblk, ("a stride walk over the mixed batch"
+                                             if WORKLOAD_NAME in MIXED else
+                                             "%d per Eb/N0 point" % per_point),
+                                      args.steps, cores, cpu_model())},
         "e2e": {"value": value, "unit": "blocks/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -414,10 +448,11 @@ class Job:
         from paper_2202_13951_gb300 import workloads
         self.orbg = orbg
         self.form = args.form
-        if WORKLOAD_NAME == "mixed":
-            B = 10 * B_PER_POINT
-            codes, cid, llr, off, cwt, _ = workloads.config4_inputs(B=B,
-                                                                     seed=SEEDS[0] + 1000 * rank)
+        if WORKLOAD_NAME in MIXED:
+            gen, mult = MIXED[WORKLOAD_NAME]
+            B = mult * B_PER_POINT
+            codes, cid, llr, off, cwt, _ = getattr(workloads, gen)(B=B,
+                                                                   seed=SEEDS[0] + 1000 * rank)
             self.codes = codes
             self.cid_np, self.off_np, self.llr_np = cid, off, llr
             self.sent = cwt

@@ -22,6 +22,11 @@ H, (n-k) x n, with G H^T = 0 over GF(2)):
   * CA-Polar(128, K=105): F^(x)7 in natural order, K positions chosen by the
     Bhattacharyya recursion at a design Eb/N0, 94 message bits followed by an
     11-bit CRC with g(x) = x^11 + x^10 + x^9 + x^5 + 1 (linear dimension 94)
+  * the [256, 234] family of Sec. IV (22 parity bits): CA-Polar[256, 234]
+    (K = 245 positions: 234 message bits and the same 11-bit CRC),
+    CRC[256, 234] (a shortened cyclic code whose degree-22 generator is the
+    smallest primitive polynomial of that degree), RLC[256, 234], and
+    BCH[255, 231], t = 3, over GF(2^8) built on x^8 + x^4 + x^3 + x^2 + 1
 """
 from __future__ import annotations
 
@@ -181,6 +186,73 @@ def _minimal_poly(beta_exp, m, prim):
     return sum(c << i for i, c in enumerate(poly))
 
 
+def _poly_powmod2(e, m):
+    """x^e mod m(x) over GF(2), square and multiply."""
+    result, base = 1, _poly_mod2(0b10, m)
+    while e:
+        if e & 1:
+            result = _poly_mod2(_poly_mul2(result, base), m)
+        base = _poly_mod2(_poly_mul2(base, base), m)
+        e >>= 1
+    return result
+
+
+def _prime_factors(v):
+    out, f = [], 2
+    while f * f <= v:
+        if v % f == 0:
+            out.append(f)
+            while v % f == 0:
+                v //= f
+        f += 1
+    if v > 1:
+        out.append(v)
+    return out
+
+
+def is_primitive_poly(p):
+    """p(x) of degree d over GF(2) is primitive iff x has order 2^d - 1
+    modulo p: x^(2^d - 1) = 1 and x^((2^d - 1)/q) != 1 for every prime q
+    dividing 2^d - 1 (p irreducible follows)."""
+    d = p.bit_length() - 1
+    if d < 1 or not p & 1:
+        return False
+    order = (1 << d) - 1
+    if _poly_powmod2(order, p) != 1:
+        return False
+    return all(_poly_powmod2(order // q, p) != 1 for q in _prime_factors(order))
+
+
+def smallest_primitive_poly(d):
+    """The numerically smallest primitive polynomial of degree d."""
+    for p in range((1 << d) | 1, 1 << (d + 1), 2):
+        if is_primitive_poly(p):
+            return p
+    raise ValueError(d)
+
+
+def cyclic_code(name, n, k, g):
+    """The (shortened) cyclic code of generator g(x), deg g = n - k: the
+    multiples m(x) g(x) of degree < n."""
+    deg = g.bit_length() - 1
+    assert deg == n - k, (deg, n - k)
+    gb = np.array([(g >> i) & 1 for i in range(deg + 1)], np.uint8)
+    G = np.zeros((k, n), np.uint8)
+    for i in range(k):
+        G[i, i:i + deg + 1] = gb
+    H = gf2_nullspace(G)
+    assert H.shape == (n - k, n)
+    _check(G, H)
+    return Code(name, n, k, G, H)
+
+
+def crc_code(n: int = 256, k: int = 234) -> Code:
+    """CRC[n, k]: codewords m(x) x^(n-k) + (m(x) x^(n-k) mod g(x)), i.e. the
+    multiples of g(x); g is the smallest primitive polynomial of degree
+    n - k (the paper does not print its generator)."""
+    return cyclic_code("crc(%d,%d)" % (n, k), n, k, smallest_primitive_poly(n - k))
+
+
 def bch(n: int = 127, k: int = 113, m: int = 7, prim: int = 0b10001001,
         t: int = 2) -> Code:
     """Binary narrow-sense BCH code, g(x) = lcm(m_1, m_3, ..., m_{2t-1})."""
@@ -191,17 +263,8 @@ def bch(n: int = 127, k: int = 113, m: int = 7, prim: int = 0b10001001,
         if mp not in seen:
             seen.append(mp)
             g = _poly_mul2(g, mp)
-    deg = g.bit_length() - 1
-    assert deg == n - k, (deg, n - k)
     assert _poly_mod2((1 << n) | 1, g) == 0  # g divides x^n + 1
-    gb = np.array([(g >> i) & 1 for i in range(deg + 1)], np.uint8)
-    G = np.zeros((k, n), np.uint8)
-    for i in range(k):
-        G[i, i:i + deg + 1] = gb  # shifts of g(x): c(x) = m(x) g(x)
-    H = gf2_nullspace(G)
-    assert H.shape == (n - k, n)
-    _check(G, H)
-    return Code("bch(%d,%d)" % (n, k), n, k, G, H)
+    return cyclic_code("bch(%d,%d)" % (n, k), n, k, g)
 
 
 # ----------------------------------------------------------- CA-Polar ----
@@ -348,10 +411,28 @@ def config4_inputs(B=1_000_000, seed=401):
     """Mixed batch: code id uniform per block, Eb/N0 uniform in [4, 7] dB.
     Returns (codes, code_id[B], llr list per block as a flat float32 array,
     llr_offset[B], codewords flat, ebn0[B])."""
-    codes = config4_codes()
+    return mixed_inputs(config4_codes(), B, seed)
+
+
+def paper256_codes():
+    """The [256, 234]-class codes of Sec. IV's first comparison."""
+    return [ca_polar(256, 245), crc_code(256, 234), rlc(256, 234, seed=61),
+            bch(255, 231, m=8, prim=0b100011101, t=3)]
+
+
+def paper256_inputs(B=400_000, seed=601):
+    """The paper-shaped mixed batch: the four [256, 234]-class codes, code
+    uniform per block, Eb/N0 uniform in [4, 7] dB (as config4_inputs)."""
+    return mixed_inputs(paper256_codes(), B, seed)
+
+
+def mixed_inputs(codes, B, seed, ebn0_lo=4.0, ebn0_hi=7.0):
+    """Blocks of several codes: code id uniform per block, Eb/N0 uniform in
+    [ebn0_lo, ebn0_hi] dB; blocks laid out back to back.  Returns (codes,
+    code_id[B], llr flat float32, llr_offset[B], codewords flat, ebn0[B])."""
     rng = np.random.default_rng(seed)
     cid = rng.integers(0, len(codes), size=B).astype(np.int32)
-    ebn0 = rng.uniform(4.0, 7.0, size=B)
+    ebn0 = rng.uniform(ebn0_lo, ebn0_hi, size=B)
     ns = np.array([c.n for c in codes], np.int64)
     lens = ns[cid]
     off = np.zeros(B, np.int64)

@@ -447,6 +447,33 @@ def test_config3_full_size_sampled(orbg):
     _sampled(orbg, code, llr, 10 ** 6, 120, 3)
 
 
+def test_paper256_full_size_sampled(orbg):
+    """The paper-shaped [256, 234] family of Sec. IV (CA-Polar, CRC, RLC and
+    BCH[255, 231]), 400,000 blocks at Eb/N0 U[4, 7] dB, cap 5e6, one batched
+    launch: 40 seeded random blocks of each code against the oracle, and
+    every decoded block a codeword."""
+    cap = 5 * 10 ** 6
+    codes, cid, llr, off, _, _ = workloads.paper256_inputs()
+    cs = orbg.CodeSet([orbg.Code(cd.H, max_query_cap=cap) for cd in codes])
+    llr_t = torch.from_numpy(llr).cuda()
+    off_t = torch.from_numpy(off).cuda()
+    cid_t = torch.from_numpy(cid).cuda()
+    cw, q, ab = orbg.decode_batched(cs, llr_t, cap, code_id=cid_t, llr_offset=off_t,
+                                    cw_offset=off_t, n_total=llr.shape[0])
+    torch.cuda.synchronize()
+    cw, q, ab = cw.cpu().numpy(), q.cpu().numpy().astype(np.int64), ab.cpu().numpy()
+    rng = np.random.default_rng(8)
+    for j, cd in enumerate(codes):
+        idx = np.nonzero(cid == j)[0]
+        rows = np.stack([cw[off[b]:off[b] + cd.n] for b in idx])
+        ok = ab[idx] == 0
+        assert not ((rows[ok].astype(np.int64) @ cd.H.T.astype(np.int64)) % 2).any()
+        pick = np.sort(rng.choice(idx.shape[0], size=40, replace=False))
+        blocks = np.stack([llr[off[b]:off[b] + cd.n] for b in idx[pick]])
+        want = oracle.decode_batch(cd.H, blocks, cap)[:3]
+        assert_same((rows[pick], q[idx[pick]], ab[idx[pick]]), want)
+
+
 @pytest.mark.parametrize("tuning", [(8, 0, 8, 1, 16), (4, 0, 1, 64, 4), (16, 0, 32, 4096, 1),
                                     (2, 1, 3, 100, 7), (8, 0, 8, 10 ** 6, 16)],
                          ids=lambda t: "wpc%d_cps%d_grab%d_budget%d_hw%d" % t)

@@ -84,3 +84,82 @@ def test_seeded_and_deterministic():
     a, _ = workloads.awgn_llr(code, 50, 5.0, seed=101)
     b, _ = workloads.awgn_llr(code, 50, 5.0, seed=101)
     assert a.dtype == np.float32 and (a == b).all()
+
+
+def test_primitive_polynomials():
+    """Primitivity by the order of x: the textbook primitive polynomials the
+    BCH codes are built on pass; an irreducible non-primitive one
+    (x^4 + x^3 + x^2 + x + 1, order 5) and reducible ones fail; the smallest
+    primitive polynomial of degree 22 is the trinomial x^22 + x + 1."""
+    assert workloads.is_primitive_poly(0b10001001)      # x^7 + x^3 + 1
+    assert workloads.is_primitive_poly(0b100011101)     # x^8 + x^4 + x^3 + x^2 + 1
+    assert workloads.is_primitive_poly(0b10011)         # x^4 + x + 1
+    assert not workloads.is_primitive_poly(0b11111)     # order 5
+    assert not workloads.is_primitive_poly(0b101)       # (x + 1)^2
+    assert not workloads.is_primitive_poly(0b10010)     # divisible by x
+    # brute force for small degrees: x has order 2^d - 1 modulo p
+    for d in range(2, 9):
+        for p in range((1 << d) | 1, 1 << (d + 1), 2):
+            r, order = 1, None
+            for e in range(1, 1 << d):
+                r <<= 1
+                if r >> d:
+                    r ^= p
+                if r == 1:
+                    order = e
+                    break
+            assert workloads.is_primitive_poly(p) == (order == (1 << d) - 1), bin(p)
+    assert workloads.smallest_primitive_poly(22) == (1 << 22) | 0b11
+
+
+def test_paper256_codes():
+    """The [256, 234]-class codes of Sec. IV: sizes, G H^T = 0, full rank;
+    BCH[255, 231] corrects 3 errors (all patterns of weight <= 3 have
+    distinct syndromes), CRC[256, 234] corrects 1 (distinct non-zero
+    columns: a shortened Hamming code), CA-Polar[256, 234] codewords carry
+    frozen zeros and a valid CRC-11 on their 245 positions."""
+    codes = workloads.paper256_codes()
+    assert [(c.n, c.k) for c in codes] == [(256, 234), (256, 234), (256, 234), (255, 231)]
+    for code in codes:
+        G = code.G.astype(np.int64)
+        H = code.H.astype(np.int64)
+        assert not ((G @ H.T) % 2).any()
+        assert workloads.gf2_rank(code.G) == code.k
+        assert workloads.gf2_rank(code.H) == code.r
+    polar, crc, _, bch = codes
+    # BCH: syndromes of weight 0..3 patterns all distinct
+    Hb = bch.H.astype(np.int64)
+    col = (Hb * (1 << np.arange(bch.r))[:, None]).sum(axis=0)
+    i, j = np.triu_indices(bch.n, 1)
+    pair = col[i] ^ col[j]
+    trip = (pair[None, :] ^ col[:, None])[(np.arange(bch.n)[:, None] < i[None, :])]
+    syn = np.concatenate([[0], col, pair, trip])
+    assert np.unique(syn).size == syn.size == 1 + 255 + 32385 + 2731135
+    # CRC: distinct non-zero columns
+    Hc = crc.H.astype(np.int64)
+    colc = (Hc * (1 << np.arange(crc.r))[:, None]).sum(axis=0)
+    assert (colc != 0).all() and np.unique(colc).size == crc.n
+    # CA-Polar: F^(x)8 is its own inverse over GF(2); u = x F has zeros off
+    # the 245 chosen positions, and its message bits end in their CRC-11
+    pos = workloads.bhattacharyya_positions(256, 245, 3.0, 234 / 256)
+    rng = np.random.default_rng(7)
+    msg = rng.integers(0, 2, (5, 234)).astype(np.uint8)
+    x = workloads.encode(polar.G, msg)
+    u = workloads.polar_transform(x)
+    frozen = np.setdiff1d(np.arange(256), pos)
+    assert not u[:, frozen].any()
+    for b in range(5):
+        info = [int(v) for v in u[b, pos]]
+        assert info[234:] == workloads.crc_bits(info[:234])
+
+
+def test_paper256_inputs():
+    """Mixed paper-shaped batch: deterministic, every code present, blocks
+    back to back."""
+    codes, cid, llr, off, cw, eb = workloads.paper256_inputs(B=4000, seed=5)
+    codes2, cid2, llr2, *_ = workloads.paper256_inputs(B=4000, seed=5)
+    assert np.array_equal(cid, cid2) and np.array_equal(llr, llr2)
+    assert set(np.unique(cid)) == {0, 1, 2, 3}
+    ns = np.array([c.n for c in codes])[cid]
+    assert off[0] == 0 and (np.diff(off) == ns[:-1]).all()
+    assert llr.shape[0] == off[-1] + ns[-1] and (eb >= 4.0).all() and (eb <= 7.0).all()
