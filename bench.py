@@ -15,7 +15,11 @@ collective (blocks are independent), and the timing is the max over ranks
 (weak scaling).  ``--impl reference`` times the CPU oracle on the host
 cores instead, on a bounded sample of the same workload.
 
-Prints one JSON line (rank 0).
+Prints one JSON line (rank 0).  At N = 1 on the default workload the line
+also carries ``extra_workloads``: the same workload in the one-line and
+three-segment full ORBGRAND orders (Sec. III-D) and the paper-shaped
+[256,234] workload (``--workload paper256``), each timed on the device in
+its own process after the headline measurement (``--no-extra`` skips them).
 """
 import argparse
 import json
@@ -79,6 +83,9 @@ def parse_args(argv=None):
     p.add_argument("--model", default="",
                    help="I_1,..;J_0,..;beta_1,..: decode m-segment full ORBGRAND (Sec. III-D, "
                         "Eq. relest_seg) under this model instead of basic")
+    p.add_argument("--no-extra", action="store_true",
+                   help="skip the secondary measurements (full ORBGRAND orders, the "
+                        "paper-shaped workload) that follow the headline one")
     p.add_argument("--no-graph", action="store_true",
                    help="time direct calls instead of replays of a captured CUDA graph")
     p.add_argument("--ref-sample", type=int, default=8000,
@@ -130,6 +137,12 @@ def select_workload(name, b_per_point):
 WORKLOAD_NAME = "bch"
 LINE = None  # (J0, beta) for one-line full ORBGRAND, None for basic
 MODEL = None  # (anchors, J, beta) for m-segment full ORBGRAND, None for basic
+# Full ORBGRAND models for the secondary measurements on the BCH workload: the
+# one- and three-line fits (Sec. III-E, Eq. Q, Eq. quant) of the mean ordered
+# |LLR| curve of 10,000 of its blocks at 5.5 dB (seed 7); a CPU test recomputes
+# them with the oracle.
+EXTRA_LINE = (5, 1)
+EXTRA_MODEL = ((7, 17), (3, 37, 58), (5, 2, 1))
 
 
 CODE_FN = "config2_code"
@@ -307,6 +320,46 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(inside), "window": window}
+
+
+def run_extra(shape, steps=20, warmup=3, timeout_s=240):
+    """Secondary measurements, each in its own process after the headline
+    one (same box, same clocks sampling): the BCH workload decoded in the
+    one-line and three-segment full ORBGRAND orders (with the headline's
+    tuning), and the paper-shaped [256,234] workload in basic order.
+    Device-timed values only (no e2e, no CPU baseline); a failure records
+    its message instead of a number."""
+    runs = [("bch, one-line full ORBGRAND J0=%d beta=%d" % EXTRA_LINE,
+             ["--line", "%d,%d" % EXTRA_LINE, "--shape", shape]),
+            ("bch, 3-segment full ORBGRAND %s" % describe_model(EXTRA_MODEL),
+             ["--model", ";".join(",".join(str(x) for x in f) for f in EXTRA_MODEL),
+              "--shape", shape]),
+            ("paper256, basic ORBGRAND", ["--workload", "paper256"])]
+    out = []
+    for label, argv in runs:
+        cmd = [sys.executable, os.path.abspath(__file__), *argv, "--steps", str(steps),
+               "--warmup", str(warmup), "--no-cpu-baseline", "--no-e2e", "--no-extra"]
+        rec = {"label": label, "args": " ".join(argv)}
+        try:
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
+            last = [x for x in r.stdout.splitlines() if x.startswith("{")]
+            if r.returncode != 0 or not last:
+                rec["error"] = ("exit %d: %s" % (r.returncode,
+                                                 (r.stderr.strip().splitlines() or [""])[-1]))[:300]
+            else:
+                d = json.loads(last[-1])
+                rec.update({k: d.get(k) for k in ("value", "unit", "ms_per_step", "steps",
+                                                  "queries_per_s", "mean_queries",
+                                                  "abandon_rate", "bler", "gpu_launches")})
+                rec["workload"] = d["config"]["workload"]
+                rec["tuning_source"] = d["config"].get("tuning_source")
+                rec["roofline"] = {k: d["roofline"].get(k)
+                                   for k in ("bound", "achieved", "peak", "unit", "frac")}
+                rec["clocks"] = d.get("clocks")
+        except subprocess.TimeoutExpired:
+            rec["error"] = "timed out after %d s" % timeout_s
+        out.append(rec)
+    return out
 
 
 # ------------------------------------------------------------- CPU side
@@ -674,6 +727,12 @@ def bench_ours(args, rank, world, local):
         line["e2e"] = e2e
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(job)
+    if (rank == 0 and world == 1 and not args.no_extra and WORKLOAD_NAME == "bch" and
+            LINE is None and MODEL is None and args.form == "batched"):
+        t = orbg.orbg_codeset_get_tuning(job.cs.handle)
+        shape = ",".join(str(x) for x in (t.warps_per_cta, t.ctas_per_sm, t.blocks_per_grab,
+                                          t.warp_budget, t.heavy_warps))
+        line["extra_workloads"] = run_extra(shape)
     if world > 1:
         dist.destroy_process_group()
     return line if rank == 0 else None

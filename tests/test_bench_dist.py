@@ -88,3 +88,38 @@ def test_class_weight_prefix_m_segment_matches_oracle():
         _, q, _, sw = oracle.decode_batch_mline(code.H, llr, 10 ** 5, model)
         ends, ws = bench.class_weight_prefix(code.n, 10 ** 5, model=model)
         assert bench.sum_weights(q, ends, ws) == int(sw.sum()), model
+
+
+def test_extra_models_are_the_fits_of_the_mean_curve():
+    """The bench's secondary full-ORBGRAND orders are the one- and
+    three-line fits (Sec. III-E) of the mean ordered |LLR| curve of 10,000
+    BCH(127,113) blocks at 5.5 dB (seed 7), as its comment states."""
+    import bench
+    import oracle
+    from paper_2202_13951_gb300 import workloads
+    llr, _ = workloads.awgn_llr(workloads.config2_code(), 10000, 5.5, 7)
+    curve = np.sort(np.abs(llr), axis=1).mean(axis=0).astype(np.float32)
+    anchors, J, beta = oracle.fit(curve, 1)
+    assert anchors == () and (J[0], beta[0]) == bench.EXTRA_LINE
+    assert oracle.fit(curve, 3) == bench.EXTRA_MODEL
+
+
+def test_extra_runs_parse_their_arguments():
+    """The secondary runs' command lines parse: the model and the line are
+    taken, the paper-shaped workload is selected."""
+    import bench
+    try:
+        a = bench.parse_args(["--model", ";".join(",".join(str(x) for x in f)
+                                                  for f in bench.EXTRA_MODEL)])
+        assert bench.MODEL == bench.EXTRA_MODEL and bench.LINE is None
+        bench.MODEL = None
+        bench.parse_args(["--line", "%d,%d" % bench.EXTRA_LINE])
+        assert bench.LINE == bench.EXTRA_LINE
+        bench.LINE = None
+        bench.parse_args(["--workload", "paper256"])
+        assert bench.CAP == 5_000_000 and "paper-shaped" in bench.WORKLOAD
+        assert not a.no_extra
+    finally:
+        bench.MODEL = None
+        bench.LINE = None
+        bench.parse_args([])
