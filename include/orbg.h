@@ -395,6 +395,29 @@ ORBG_API int64_t orbg_query_order_model(int n, uint32_t count, int table, int m,
                                         const int32_t *anchors, const int32_t *J,
                                         const int32_t *beta, int32_t *out);
 
+/*
+ * Per-block piece-wise linear fitting and quantisation (Sec. III-E, Eq. Q,
+ * Eq. quant) on the device: for each of B blocks of n LLRs (llr, [B][n]
+ * FP32, device memory) the ordered reliability curve L_1 <= ... <= L_n of
+ * |LLR| is fitted with up to `lines` (1..8) lines and quantised into the
+ * model of orbg_load_code_model.  Anchors start at indices 1 and floor(n/2);
+ * each further anchor splits the first (edge) interval at its largest
+ * vertical gap between chord and curve (the smaller index on equal gaps),
+ * stopping early when there is none; the centre line covers the rest.
+ * Q = the smallest segment slope; beta_i = [s_i / Q], J_0 = [L_1 / Q] -
+ * beta_1, J_i = [L_{I_i} / Q], [x] rounding half away from zero;
+ * divisible != 0 makes each J_{i-1} a multiple of beta_i ([J/beta] beta).
+ * n < 4, a flat stretch (Q <= 0) or a quantised ratio above 2^24 gives the
+ * basic model (m = 1, J_0 = 0, beta_1 = 1).  models: device memory,
+ * [B][ORBG_FIT_STRIDE] int32 per block: m, then the anchors I_1..I_7 (m - 1
+ * used), then J_0..J_7 (m used), then beta_1..beta_8 (m used), unused
+ * entries 0; m = 0 marks a block with a NaN LLR.  Stream-ordered on
+ * cuda_stream.  Errors: EINVAL (sizes, NULL or host pointers), ECUDA.
+ */
+#define ORBG_FIT_STRIDE 24
+ORBG_API int orbg_fit_models(const float *llr, int64_t B, int n, int lines, int divisible,
+                             int32_t *models, void *cuda_stream);
+
 /* Static description of a status code (never NULL). */
 ORBG_API const char *orbg_status_string(int status);
 

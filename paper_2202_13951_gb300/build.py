@@ -15,12 +15,13 @@ CSRC = os.path.join(PKG, "csrc")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "liborbg.so")
 SOURCES = ["orbg_plain.cu", "orbg_batched.cu", "orbg_noalloc.cu",
-           "orbg_probe.cu", "orbg_api.cpp", "orbg_serve.cpp",
+           "orbg_probe.cu", "orbg_fit.cu", "orbg_api.cpp", "orbg_serve.cpp",
            "orbg_tables.cpp"]
 # the batched kernels: one object per (keys per lane, syndrome words) pair
 INST = "orbg_batched_inst.cu"
 INST_KW = [(k, w) for k in (1, 2, 4, 8) for w in (1, 2, 4)]
-HEADERS = ["orbg_internal.h", "orbg_decode_block.cuh", "orbg_batched.cuh", "orbg_heavy.cuh"]
+HEADERS = ["orbg_internal.h", "orbg_decode_block.cuh", "orbg_batched.cuh", "orbg_heavy.cuh",
+           "orbg_fit.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,109 @@
+/*
+ * orbg_fit.cu -- per-block piece-wise linear fitting and quantisation of the
+ * ordered reliability curve on the device (Sec. III-E, Eq. Q, Eq. quant).
+ *
+ * One warp per received block, blocks taken in a grid-stride loop.  The
+ * block's reliabilities |LLR| are staged in the warp's shared memory and
+ * sorted ascending by a bitonic network over 256 slots (unused slots hold
+ * +inf and sort last), which gives the ordered curve L_1 <= ... <= L_n of
+ * Sec. III-A.  Lane 0 then places the anchors and quantises the segments
+ * (orbg_fit.cuh).  The work per block is O(n log^2 n) compares and
+ * O(lines * n) double operations: small beside one decode.
+ */
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "../../include/orbg.h"
+#include "orbg_fit.cuh"
+#include "orbg_internal.h"
+
+namespace {
+
+constexpr int kWarps = 8;           /* warps per CTA */
+constexpr int kSlots = 256;         /* sorted slots per block: n <= 256 */
+static_assert(ORBG_FIT_WORDS == ORBG_FIT_STRIDE, "model record size");
+
+__global__ void __launch_bounds__(kWarps * 32) orbg_fit_kernel(const float *__restrict__ llr,
+                                                              int64_t B, int n, int lines,
+                                                              int divisible,
+                                                              int32_t *__restrict__ models)
+{
+    __shared__ float sm[kWarps][kSlots];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *s = sm[warp];
+    const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+    for (int64_t b = (int64_t)blockIdx.x * kWarps + warp; b < B; b += nwarps) {
+        const float *x = llr + b * (int64_t)n;
+        bool nan = false;
+        for (int i = lane; i < kSlots; i += 32) {
+            const float v = i < n ? x[i] : INFINITY;
+            nan |= isnan(v);
+            s[i] = fabsf(v);
+        }
+        nan = __any_sync(0xFFFFFFFFu, nan);
+        int32_t *out = models + b * (int64_t)ORBG_FIT_STRIDE;
+        if (nan) {
+            for (int i = lane; i < ORBG_FIT_STRIDE; i += 32)
+                out[i] = 0; /* m = 0 marks a NaN block */
+            __syncwarp();
+            continue;
+        }
+        __syncwarp();
+        /* bitonic sort, ascending: stage (k, j) compares i and i + j for the
+         * 128 indices i with bit j clear, in direction (i & k) == 0 */
+        for (int k = 2; k <= kSlots; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int t = lane; t < kSlots / 2; t += 32) {
+                    const int i = (t / j) * 2 * j + (t % j);
+                    const int l = i + j;
+                    const float va = s[i], vb = s[l];
+                    if ((va > vb) == ((i & k) == 0)) {
+                        s[i] = vb;
+                        s[l] = va;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        if (lane == 0) {
+            int32_t res[ORBG_FIT_STRIDE];
+            for (int i = 0; i < ORBG_FIT_STRIDE; i++)
+                res[i] = 0;
+            orbg_fit::fit_sorted(s, n, lines, divisible, res);
+            for (int i = 0; i < ORBG_FIT_STRIDE; i++)
+                out[i] = res[i];
+        }
+        __syncwarp();
+    }
+}
+
+bool device_accessible(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+extern "C" ORBG_API int orbg_fit_models(const float *llr, int64_t B, int n, int lines,
+                                        int divisible, int32_t *models, void *cuda_stream)
+{
+    if (B < 0 || n < 1 || n > ORBG_MAX_N || lines < 1 || lines > ORBG_FIT_SEG)
+        return ORBG_EINVAL;
+    if (B == 0)
+        return ORBG_OK;
+    if (!llr || !models || !device_accessible(llr) || !device_accessible(models))
+        return ORBG_EINVAL;
+    const int64_t ctas = (B + kWarps - 1) / kWarps;
+    const unsigned grid = (unsigned)(ctas < 152 * 16 ? ctas : 152 * 16);
+    orbg_fit_kernel<<<grid, kWarps * 32, 0, (cudaStream_t)cuda_stream>>>(llr, B, n, lines,
+                                                                         divisible ? 1 : 0,
+                                                                         models);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ORBG_OK : orbg_note_cuda_error((int)e);
+}

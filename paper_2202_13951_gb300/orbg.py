@@ -112,6 +112,7 @@ def load_library(path=None):
     lib.orbg_query_order_line.argtypes = [i32, u32, i32, i32, i32, vp]
     lib.orbg_query_order_line.restype = i64
     lib.orbg_query_order_model.argtypes = [i32, u32, i32, i32, vp, vp, vp, vp]
+    lib.orbg_fit_models.argtypes = [vp, i64, i32, i32, i32, vp, vp]
     lib.orbg_query_order_model.restype = i64
     lib.orbg_server_create.argtypes = [vp, ctypes.c_size_t, u32, i32, i64, ctypes.POINTER(vp)]
     lib.orbg_server_submit.argtypes = [vp, ctypes.c_uint64, i32, vp, i64]
@@ -129,7 +130,7 @@ def load_library(path=None):
               "orbg_server_poll", "orbg_server_fetch", "orbg_server_stats_get",
               "orbg_server_destroy", "orbg_server_replay",
               "orbg_codeset_set_tuning", "orbg_codeset_get_tuning", "orbg_probe_int_lanes",
-              "orbg_probe_smem_bytes", "orbg_codeset_autotune",
+              "orbg_probe_smem_bytes", "orbg_codeset_autotune", "orbg_fit_models",
               "orbg_last_cuda_error", "orbg_version"):
         getattr(lib, f).restype = i32
     if path == LIB_PATH:
@@ -420,6 +421,31 @@ def orbg_query_order_model(n, count, table, model):
     if got < 0:
         raise OrbgError(int(got), "orbg_query_order_model")
     return [tuple(int(x) for x in row[1:1 + row[0]]) for row in out[:got]]
+
+
+ORBG_FIT_STRIDE = 24
+
+
+def fit_models(llr, n, lines, divisible=False, stream=None):
+    """orbg_fit_models on a device tensor of B x n FP32 LLRs: the int32
+    [B, ORBG_FIT_STRIDE] model records (Sec. III-E), stream-ordered."""
+    import torch
+    lib = load_library()
+    B = llr.numel() // n
+    out = torch.empty((B, ORBG_FIT_STRIDE), dtype=torch.int32, device=llr.device)
+    st = _stream(stream if stream is not None else torch.cuda.current_stream(llr.device))
+    _check(lib.orbg_fit_models(llr.data_ptr(), B, int(n), int(lines), int(bool(divisible)),
+                               out.data_ptr(), st), "orbg_fit_models")
+    return out
+
+
+def model_of_record(rec):
+    """(anchors, J, beta) of one model record; None for a NaN block (m = 0)."""
+    rec = [int(x) for x in rec]
+    m = rec[0]
+    if m == 0:
+        return None
+    return tuple(rec[1:m]), tuple(rec[8:8 + m]), tuple(rec[16:16 + m])
 
 
 # ------------------------------------------------------- convenience layer
