@@ -332,54 +332,6 @@ def test_one_line_orbgrand(orbg, line):
         assert_same(gpu_batched(orbg, cs, llr, cap), want)
 
 
-def _models(n, llr):
-    """A hand-set model with a zero-weight least reliable position, and
-    models fitted (Sec. III-E) to two of the blocks."""
-    return [((n // 8,), (-2, n // 8 + 3), (2, 1)), oracle.fit(llr[0], 3),
-            oracle.fit(llr[1], 2, True), oracle.fit(llr[2], 4)]
-
-
-def test_m_segment_orbgrand(orbg):
-    """m-segment full ORBGRAND (Sec. III-D, Eq. relest_seg): codes loaded
-    with a model decode, plain, batched and all in the second phase,
-    exactly as the m-segment oracle."""
-    cap = 20000
-    for n, k, seed, ebn0 in ((64, 51, 93, 3.5), (127, 113, 94, 4.0)):
-        code = workloads.rlc(n, k, seed)
-        rng = np.random.default_rng(seed + 1)
-        awgn = workloads.awgn_llr(code, 180, ebn0, seed + 2)[0]
-        llr = np.concatenate([tiny_inputs(n, rng, 20), awgn])
-        for model in _models(n, awgn):
-            want = oracle.decode_batch_mline(code.H, llr, cap, model)[:3]
-            c = orbg.Code(code.H, max_query_cap=cap, model=model)
-            assert_same(gpu_plain(orbg, c, llr, cap), want)
-            cs = orbg.CodeSet([c])
-            assert_same(gpu_batched(orbg, cs, llr, cap), want)
-            orbg.orbg_codeset_set_tuning(cs.handle, orbg.OrbgTuning(8, 0, 1, 64, 8))
-            assert_same(gpu_batched(orbg, cs, llr, cap), want)
-
-
-def test_m_segment_and_basic_codes_in_one_launch(orbg):
-    """Blocks of a basic code and of the same code under an m-segment model
-    in one batched launch decode as each order's oracle."""
-    cap = 20000
-    code = workloads.rlc(64, 51, 95)
-    llr = workloads.awgn_llr(code, 300, 3.5, 96)[0]
-    model = oracle.fit(llr[0], 3)
-    cs = orbg.CodeSet([orbg.Code(code.H, max_query_cap=cap),
-                       orbg.Code(code.H, max_query_cap=cap, model=model)])
-    cid = (np.arange(llr.shape[0]) % 2).astype(np.int32)
-    llr_t = torch.from_numpy(llr).cuda()
-    cid_t = torch.from_numpy(cid).cuda()
-    cw, q, ab = orbg.decode_batched(cs, llr_t, cap, code_id=cid_t)
-    torch.cuda.synchronize()
-    got = (cw.cpu().numpy(), q.cpu().numpy().astype(np.int64), ab.cpu().numpy())
-    basic = oracle.decode_batch(code.H, llr[cid == 0], cap)[:3]
-    seg = oracle.decode_batch_mline(code.H, llr[cid == 1], cap, model)[:3]
-    assert_same(tuple(x[cid == 0] for x in got), basic)
-    assert_same(tuple(x[cid == 1] for x in got), seg)
-
-
 def test_mixed_codes_one_launch_equals_alone(orbg):
     """Blocks of four codes with different n and n-k in one batched launch
     give what each code's blocks give alone, and what the oracle gives."""
@@ -445,33 +397,6 @@ def test_config3_full_size_sampled(orbg):
     syndromes, heavy abandonment); 120 seeded random blocks checked."""
     code, llr, _ = workloads.config3_inputs()
     _sampled(orbg, code, llr, 10 ** 6, 120, 3)
-
-
-def test_paper256_full_size_sampled(orbg):
-    """The paper-shaped [256, 234] family of Sec. IV (CA-Polar, CRC, RLC and
-    BCH[255, 231]), 400,000 blocks at Eb/N0 U[4, 7] dB, cap 5e6, one batched
-    launch: 40 seeded random blocks of each code against the oracle, and
-    every decoded block a codeword."""
-    cap = 5 * 10 ** 6
-    codes, cid, llr, off, _, _ = workloads.paper256_inputs()
-    cs = orbg.CodeSet([orbg.Code(cd.H, max_query_cap=cap) for cd in codes])
-    llr_t = torch.from_numpy(llr).cuda()
-    off_t = torch.from_numpy(off).cuda()
-    cid_t = torch.from_numpy(cid).cuda()
-    cw, q, ab = orbg.decode_batched(cs, llr_t, cap, code_id=cid_t, llr_offset=off_t,
-                                    cw_offset=off_t, n_total=llr.shape[0])
-    torch.cuda.synchronize()
-    cw, q, ab = cw.cpu().numpy(), q.cpu().numpy().astype(np.int64), ab.cpu().numpy()
-    rng = np.random.default_rng(8)
-    for j, cd in enumerate(codes):
-        idx = np.nonzero(cid == j)[0]
-        rows = np.stack([cw[off[b]:off[b] + cd.n] for b in idx])
-        ok = ab[idx] == 0
-        assert not ((rows[ok].astype(np.int64) @ cd.H.T.astype(np.int64)) % 2).any()
-        pick = np.sort(rng.choice(idx.shape[0], size=40, replace=False))
-        blocks = np.stack([llr[off[b]:off[b] + cd.n] for b in idx[pick]])
-        want = oracle.decode_batch(cd.H, blocks, cap)[:3]
-        assert_same((rows[pick], q[idx[pick]], ab[idx[pick]]), want)
 
 
 @pytest.mark.parametrize("tuning", [(8, 0, 8, 1, 16), (4, 0, 1, 64, 4), (16, 0, 32, 4096, 1),
