@@ -418,6 +418,33 @@ ORBG_API int64_t orbg_query_order_model(int n, uint32_t count, int table, int m,
 ORBG_API int orbg_fit_models(const float *llr, int64_t B, int n, int lines, int divisible,
                              int32_t *models, void *cuda_stream);
 
+/*
+ * Full ORBGRAND with one line fitted per block (Sec. III-E with one line,
+ * then the order of Sec. III-D): each block is decoded in the one-line
+ * order of its own fit (beta = 1, J_0 = [L_1 / Q] - 1, Q the slope from
+ * L_1 to L_{floor(n/2)}), the paper's "1-line" variant.  The object keeps,
+ * for the given code (not owned; it must outlive the object), one handle
+ * per J_0 met so far (built on first use with the code's max_query_cap;
+ * J_0 above n(n+1)/2, which orders by Hamming weight first, is held at
+ * n(n+1)/2 + 1), and a code set over them.  divisible != 0 selects the
+ * J-divisible quantisation (the same line when beta = 1).
+ * orbg_fitted_decode: device buffers only -- llr [B][n] FP32, codeword
+ * [B][n], queries [B], abandoned [B] as orbg_decode; models: NULL or a
+ * device buffer [B][ORBG_FIT_STRIDE] that receives each block's fit
+ * (orbg_fit_models).  It fits on cuda_stream, reads the J_0s back
+ * (synchronising cuda_stream), and decodes all blocks in one batched call
+ * with each block's own order; results equal the one-line decoder of each
+ * block's line.  Errors: EINVAL (NULL or host buffers), ELIMIT
+ * (query_cap above the code's max_query_cap, more than 1024 distinct
+ * lines), ENOMEM, ECUDA.  One call at a time per object (serialised).
+ */
+typedef struct orbg_fitted orbg_fitted;
+ORBG_API int orbg_fitted_create(const orbg_code *code, int divisible, orbg_fitted **out);
+ORBG_API int orbg_fitted_decode(orbg_fitted *f, const float *llr, int64_t B,
+                                uint32_t query_cap, uint8_t *codeword, uint32_t *queries,
+                                uint8_t *abandoned, int32_t *models, void *cuda_stream);
+ORBG_API int orbg_fitted_free(orbg_fitted *f);
+
 /* Static description of a status code (never NULL). */
 ORBG_API const char *orbg_status_string(int status);
 

@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -1036,6 +1037,157 @@ int orbg_codeset_autotune(orbg_codeset *set, const int32_t *code_id, const int64
     /* leave the outputs holding the sample's results under the chosen tuning */
     return orbg_decode_batched(set, code_id, llr_offset, llr, B, query_cap, codeword, cw_offset,
                                queries, abandoned, cuda_stream);
+}
+
+}  // extern "C"
+
+/* ------------------------------------------ per-block one-line fitting -- */
+
+/*
+ * Full ORBGRAND with one line fitted per block (Sec. III-E, then the order
+ * of Sec. III-D).  With one line the fit gives beta = 1 and J_0 = [L_1/Q] -
+ * 1 >= -1, so the blocks of a batch fall into few orders (one per J_0).
+ * The object keeps one handle of the code per J_0 met so far, and a code
+ * set over them; a decode fits every block on the device, reads the J_0s
+ * back, and decodes all blocks in one batched launch, each with its own
+ * J_0's handle.  J_0 above n(n+1)/2 orders patterns by Hamming weight
+ * first whatever its value, so it is held at n(n+1)/2 + 1.
+ */
+struct orbg_fitted {
+    const orbg_code *code;         /* not owned */
+    int divisible;
+    std::mutex mu;
+    std::map<int32_t, int> slot;   /* J_0 -> index into handles */
+    std::vector<orbg_code *> handles;
+    orbg_codeset *set = nullptr;   /* over handles; rebuilt when one is added */
+};
+
+namespace {
+
+/* The code in the one-line order of (J_0, beta = 1): line tables when
+ * 0 <= J_0 <= ORBG_MAX_LINE, else the one-segment model tables. */
+int fitted_handle(const orbg_code *code, int32_t J0, orbg_code **out)
+{
+    if (J0 >= 0 && J0 <= ORBG_MAX_LINE)
+        return load_code(code->H.data(), ORBG_MAT_H, code->n, code->k, code->max_cap, nullptr,
+                         J0, 1, out);
+    OrbgModel md;
+    md.m = 1;
+    md.I[0] = 0;
+    md.I[1] = code->n;
+    md.J[0] = J0;
+    md.beta[0] = 1;
+    return load_code(code->H.data(), ORBG_MAT_H, code->n, code->k, code->max_cap, &md, 0, 1,
+                     out);
+}
+
+}  // namespace
+
+extern "C" {
+
+int orbg_fitted_create(const orbg_code *code, int divisible, orbg_fitted **out)
+{
+    if (!out)
+        return ORBG_EINVAL;
+    *out = nullptr;
+    if (!code)
+        return ORBG_EINVAL;
+    orbg_fitted *f = new (std::nothrow) orbg_fitted();
+    if (!f)
+        return ORBG_ENOMEM;
+    f->code = code;
+    f->divisible = divisible ? 1 : 0;
+    *out = f;
+    return ORBG_OK;
+}
+
+int orbg_fitted_free(orbg_fitted *f)
+{
+    if (!f)
+        return ORBG_OK;
+    orbg_codeset_free(f->set);
+    for (orbg_code *c : f->handles)
+        orbg_free_code(c);
+    delete f;
+    return ORBG_OK;
+}
+
+int orbg_fitted_decode(orbg_fitted *f, const float *llr, int64_t B, uint32_t query_cap,
+                       uint8_t *codeword, uint32_t *queries, uint8_t *abandoned,
+                       int32_t *models, void *cuda_stream)
+{
+    if (!f || B < 0 || query_cap < 1)
+        return ORBG_EINVAL;
+    if (query_cap > f->code->max_cap || B >= ((int64_t)1 << 32))
+        return ORBG_ELIMIT;
+    if (B == 0)
+        return ORBG_OK;
+    if (!llr || !codeword || !queries || !abandoned || !is_device_ptr(llr) ||
+        !is_device_ptr(codeword) || !is_device_ptr(queries) || !is_device_ptr(abandoned) ||
+        !is_device_ptr(models))
+        return ORBG_EINVAL;
+    std::lock_guard<std::mutex> lk(f->mu);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int n = f->code->n;
+    const int32_t j0_top = n * (n + 1) / 2 + 1;
+    int32_t *d_models = models;
+    int32_t *d_cid = nullptr;
+    cudaError_t e = cudaSuccess;
+    int rc = ORBG_OK;
+    if (!models && (e = cudaMallocAsync((void **)&d_models,
+                                        (size_t)B * ORBG_FIT_STRIDE * sizeof(int32_t), st)) !=
+                       cudaSuccess)
+        return cuda_fail(e);
+    /* the line of every block, then each block's m and J_0 on the host */
+    std::vector<int32_t> mj((size_t)B * 2);
+    rc = orbg_fit_models(llr, B, n, 1, f->divisible, d_models, cuda_stream);
+    const size_t rec = ORBG_FIT_STRIDE * sizeof(int32_t);
+    if (rc == ORBG_OK &&
+        ((e = cudaMemcpy2DAsync(mj.data(), 8, d_models, rec, 4, (size_t)B,
+                                cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+         (e = cudaMemcpy2DAsync(mj.data() + 1, 8, d_models + 8, rec, 4, (size_t)B,
+                                cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+         (e = cudaStreamSynchronize(st)) != cudaSuccess))
+        rc = cuda_fail(e);
+    /* a handle per J_0 (NaN blocks, m = 0, take any: the decode flags them) */
+    std::vector<int32_t> cid((size_t)B);
+    bool grown = false;
+    for (int64_t b = 0; b < B && rc == ORBG_OK; b++) {
+        const int32_t J0 = mj[2 * b] == 0 ? 0 : std::min(mj[2 * b + 1], j0_top);
+        auto it = f->slot.find(J0);
+        if (it == f->slot.end()) {
+            if (f->handles.size() >= 1024) {
+                rc = ORBG_ELIMIT;
+                break;
+            }
+            orbg_code *h = nullptr;
+            if ((rc = fitted_handle(f->code, J0, &h)) != ORBG_OK)
+                break;
+            f->handles.push_back(h);
+            it = f->slot.emplace(J0, (int)f->handles.size() - 1).first;
+            grown = true;
+        }
+        cid[b] = it->second;
+    }
+    if (rc == ORBG_OK && (grown || !f->set)) {
+        orbg_codeset_free(f->set);
+        f->set = nullptr;
+        rc = orbg_codeset_create(f->handles.data(), (int)f->handles.size(), &f->set);
+    }
+    /* one batched launch, every block in its own line's order */
+    if (rc == ORBG_OK &&
+        ((e = cudaMallocAsync((void **)&d_cid, (size_t)B * sizeof(int32_t), st)) != cudaSuccess ||
+         (e = cudaMemcpyAsync(d_cid, cid.data(), (size_t)B * sizeof(int32_t),
+                              cudaMemcpyHostToDevice, st)) != cudaSuccess))
+        rc = cuda_fail(e);
+    if (rc == ORBG_OK)
+        rc = orbg_decode_batched(f->set, d_cid, nullptr, llr, B, query_cap, codeword, nullptr,
+                                 queries, abandoned, cuda_stream);
+    if (d_cid)
+        cudaFreeAsync(d_cid, st);
+    if (!models)
+        cudaFreeAsync(d_models, st);
+    return rc;
 }
 
 }  // extern "C"

@@ -113,6 +113,9 @@ def load_library(path=None):
     lib.orbg_query_order_line.restype = i64
     lib.orbg_query_order_model.argtypes = [i32, u32, i32, i32, vp, vp, vp, vp]
     lib.orbg_fit_models.argtypes = [vp, i64, i32, i32, i32, vp, vp]
+    lib.orbg_fitted_create.argtypes = [vp, i32, ctypes.POINTER(vp)]
+    lib.orbg_fitted_decode.argtypes = [vp, vp, i64, u32, vp, vp, vp, vp, vp]
+    lib.orbg_fitted_free.argtypes = [vp]
     lib.orbg_query_order_model.restype = i64
     lib.orbg_server_create.argtypes = [vp, ctypes.c_size_t, u32, i32, i64, ctypes.POINTER(vp)]
     lib.orbg_server_submit.argtypes = [vp, ctypes.c_uint64, i32, vp, i64]
@@ -131,6 +134,7 @@ def load_library(path=None):
               "orbg_server_destroy", "orbg_server_replay",
               "orbg_codeset_set_tuning", "orbg_codeset_get_tuning", "orbg_probe_int_lanes",
               "orbg_probe_smem_bytes", "orbg_codeset_autotune", "orbg_fit_models",
+              "orbg_fitted_create", "orbg_fitted_decode", "orbg_fitted_free",
               "orbg_last_cuda_error", "orbg_version"):
         getattr(lib, f).restype = i32
     if path == LIB_PATH:
@@ -437,6 +441,48 @@ def fit_models(llr, n, lines, divisible=False, stream=None):
     _check(lib.orbg_fit_models(llr.data_ptr(), B, int(n), int(lines), int(bool(divisible)),
                                out.data_ptr(), st), "orbg_fit_models")
     return out
+
+
+class Fitted:
+    """Owning wrapper of an orbg_fitted object: one-line full ORBGRAND with
+    each block's own fitted line (Sec. III-E)."""
+
+    def __init__(self, code, divisible=False):
+        lib = load_library()
+        self.code = code  # the handle must outlive the object
+        h = ctypes.c_void_p()
+        _check(lib.orbg_fitted_create(code.handle, int(bool(divisible)), ctypes.byref(h)),
+               "orbg_fitted_create")
+        self.handle = h
+
+    def decode(self, llr, query_cap, stream=None):
+        """llr: CUDA tensor [B][n].  Returns (codeword u8, queries int32,
+        abandoned u8, model records int32 [B][ORBG_FIT_STRIDE])."""
+        import torch
+        lib = load_library()
+        n = self.code.n
+        B = llr.numel() // n
+        dev = llr.device
+        cw = torch.empty((B, n), dtype=torch.uint8, device=dev)
+        q = torch.empty((B,), dtype=torch.int32, device=dev)
+        ab = torch.empty((B,), dtype=torch.uint8, device=dev)
+        rec = torch.empty((B, ORBG_FIT_STRIDE), dtype=torch.int32, device=dev)
+        st = _stream(stream if stream is not None else torch.cuda.current_stream(dev))
+        _check(lib.orbg_fitted_decode(self.handle, llr.data_ptr(), B, int(query_cap),
+                                      cw.data_ptr(), q.data_ptr(), ab.data_ptr(),
+                                      rec.data_ptr(), st), "orbg_fitted_decode")
+        return cw, q, ab, rec
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            load_library().orbg_fitted_free(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def model_of_record(rec):

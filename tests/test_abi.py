@@ -206,3 +206,17 @@ def test_query_order_model_limit(lib):
     with pytest.raises(orbg.OrbgError) as ei:
         orbg.orbg_query_order_model(256, 8, 0, ((255,), (1000, 0), (1, 1)))
     assert ei.value.status == orbg.ORBG_ELIMIT
+
+
+def test_fitted_argument_checks(lib):
+    """The per-block one-line fitted decoder refuses NULL objects and codes
+    without a GPU call."""
+    h = ctypes.c_void_p()
+    assert lib.orbg_fitted_create(None, 0, ctypes.byref(h)) == orbg.ORBG_EINVAL
+    assert lib.orbg_fitted_create(None, 0, None) == orbg.ORBG_EINVAL
+    assert lib.orbg_fitted_free(None) == orbg.ORBG_OK
+    assert lib.orbg_fitted_decode(None, None, 1, 10, None, None, None, None,
+                                  None) == orbg.ORBG_EINVAL
+    assert lib.orbg_fit_models(None, -1, 64, 3, 0, None, None) == orbg.ORBG_EINVAL
+    assert lib.orbg_fit_models(None, 4, 64, 0, 0, None, None) == orbg.ORBG_EINVAL
+    assert lib.orbg_fit_models(None, 4, 64, 9, 0, None, None) == orbg.ORBG_EINVAL

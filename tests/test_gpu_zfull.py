@@ -169,3 +169,33 @@ def test_fitted_model_decodes_as_oracle(orbg):
     torch.cuda.synchronize()
     wc, wq, wab, _ = oracle.decode_batch_fit(code.H, llr[:1], 20000, 3)
     assert (cw.cpu().numpy() == wc).all() and int(q[0]) == int(wq[0]) and int(ab[0]) == int(wab[0])
+
+
+def test_fitted_line_decode_as_oracle(orbg):
+    """One-line full ORBGRAND with each block's own line (Sec. III-E, one
+    line, then Sec. III-D's order), in one call: equal to the oracle's
+    fit-then-decode block by block, over SNRs that give many distinct
+    lines (including J_0 = -1), with a NaN block, both quantisations, and
+    a second call that reuses the cached handles."""
+    cap = 20000
+    for code, seed in ((workloads.rlc(64, 51, 99), 100), (workloads.config2_code(), 101)):
+        llr = np.concatenate([workloads.awgn_llr(code, 120, eb, seed + int(eb))[0]
+                              for eb in (2.0, 4.0, 6.0, 8.0)])
+        llr[7, 3] = np.nan
+        c = orbg.Code(code.H, max_query_cap=cap)
+        for div in (False, True):
+            f = orbg.Fitted(c, divisible=div)
+            d = torch.from_numpy(llr).cuda()
+            for _ in range(2):
+                cw, q, ab, rec = f.decode(d, cap)
+                torch.cuda.synchronize()
+                ok = np.ones(llr.shape[0], bool)
+                ok[7] = False
+                want = oracle.decode_batch_fit(code.H, llr[ok], cap, 1, div)[:3]
+                assert_same((cw.cpu().numpy()[ok], q.cpu().numpy().astype(np.int64)[ok],
+                             ab.cpu().numpy()[ok]), want)
+                assert int(ab[7]) == 2 and int(q[7]) == 0
+                rec = rec.cpu().numpy()
+                for b in np.nonzero(ok)[0][::17]:
+                    assert orbg.model_of_record(rec[b]) == oracle.fit(llr[b], 1, div)
+            f.close()
