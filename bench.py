@@ -83,6 +83,9 @@ def parse_args(argv=None):
     p.add_argument("--model", default="",
                    help="I_1,..;J_0,..;beta_1,..: decode m-segment full ORBGRAND (Sec. III-D, "
                         "Eq. relest_seg) under this model instead of basic")
+    p.add_argument("--fitted", action="store_true",
+                   help="decode one-line full ORBGRAND with a line fitted per block "
+                        "(Sec. III-E; orbg_fitted_decode) instead of basic")
     p.add_argument("--no-extra", action="store_true",
                    help="skip the secondary measurements (full ORBGRAND orders, the "
                         "paper-shaped workload) that follow the headline one")
@@ -104,9 +107,12 @@ def parse_args(argv=None):
                         "for the batched launch (orbg_tuning)")
     args = p.parse_args(argv)
     select_workload(args.workload, args.blocks_per_point)
-    global LINE, MODEL, WORKLOAD
-    if args.line and args.model:
-        raise SystemExit("give --line or --model, not both")
+    global LINE, MODEL, FITTED, WORKLOAD
+    if sum(map(bool, (args.line, args.model, args.fitted))) > 1:
+        raise SystemExit("give one of --line, --model, --fitted")
+    FITTED = bool(args.fitted)
+    if FITTED:
+        WORKLOAD += ", one-line full ORBGRAND with a line fitted per block"
     if args.line:
         LINE = tuple(int(x) for x in args.line.split(","))
         WORKLOAD += ", one-line full ORBGRAND J0=%d beta=%d" % LINE
@@ -137,6 +143,7 @@ def select_workload(name, b_per_point):
 WORKLOAD_NAME = "bch"
 LINE = None  # (J0, beta) for one-line full ORBGRAND, None for basic
 MODEL = None  # (anchors, J, beta) for m-segment full ORBGRAND, None for basic
+FITTED = False  # one-line full ORBGRAND with a line fitted per block
 # Full ORBGRAND models for the secondary measurements on the BCH workload: the
 # one- and three-line fits (Sec. III-E, Eq. Q, Eq. quant) of the mean ordered
 # |LLR| curve of 10,000 of its blocks at 5.5 dB (seed 7); a CPU test recomputes
@@ -334,6 +341,7 @@ def run_extra(shape, steps=20, warmup=3, timeout_s=240):
             ("bch, 3-segment full ORBGRAND %s" % describe_model(EXTRA_MODEL),
              ["--model", ";".join(",".join(str(x) for x in f) for f in EXTRA_MODEL),
               "--shape", shape]),
+            ("bch, one-line full ORBGRAND with a line fitted per block", ["--fitted"]),
             ("paper256, basic ORBGRAND", ["--workload", "paper256"])]
     out = []
     for label, argv in runs:
@@ -365,10 +373,12 @@ def run_extra(shape, steps=20, warmup=3, timeout_s=240):
 # ------------------------------------------------------------- CPU side
 
 def _oracle_worker(args):
-    H, llr, cap, line, model = args
+    H, llr, cap, line, model, fitted = args
     import oracle
     t = time.perf_counter()
-    if model:
+    if fitted:
+        _, q, ab, _ = oracle.decode_batch_fit(H, llr, cap, 1)
+    elif model:
         _, q, ab, _ = oracle.decode_batch_mline(H, llr, cap, model)
     elif line:
         _, q, ab, _ = oracle.decode_batch_1line(H, llr, cap, *line)
@@ -391,12 +401,12 @@ def cpu_sample(llr, per_point, step):
 def run_oracle(H, llr, cap, procs):
     """Decode llr on `procs` spawned single-threaded oracle processes."""
     if procs <= 1:
-        return _oracle_worker((H, llr, cap, LINE, MODEL))
+        return _oracle_worker((H, llr, cap, LINE, MODEL, FITTED))
     import multiprocessing as mp
     chunks = np.array_split(llr, procs)
     ctx = mp.get_context("spawn")
     with ctx.Pool(procs) as pool:
-        res = pool.map(_oracle_worker, [(H, c, cap, LINE, MODEL) for c in chunks])
+        res = pool.map(_oracle_worker, [(H, c, cap, LINE, MODEL, FITTED) for c in chunks])
     return max(r[0] for r in res), sum(r[1] for r in res), sum(r[2] for r in res)
 
 
@@ -435,7 +445,7 @@ def bench_reference(args, rank, world):
                 sel = idx[cid[idx] == j]
                 if sel.size:
                     blk = np.stack([llr_flat[off[b]:off[b] + code.n] for b in sel])
-                    work += [(code.H, c, CAP, LINE, MODEL)
+                    work += [(code.H, c, CAP, LINE, MODEL, FITTED)
                              for c in np.array_split(blk, max(1, cores // len(codes)))
                              if c.shape[0]]
             return work, idx.size
@@ -445,8 +455,8 @@ def bench_reference(args, rank, world):
 
         def step_work(step):
             sample = cpu_sample(llr, per_point, step)
-            return ([(code.H, c, CAP, LINE, MODEL) for c in np.array_split(sample, cores)],
-                    sample.shape[0])
+            return ([(code.H, c, CAP, LINE, MODEL, FITTED)
+                     for c in np.array_split(sample, cores)], sample.shape[0])
     # the pool is started once, before any timing
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
@@ -526,6 +536,12 @@ class Job:
         self.objs = [orbg.Code(c.H, max_query_cap=CAP, line=LINE, model=MODEL)
                      for c in self.codes]
         self.cs = orbg.CodeSet(self.objs)
+        self.fitted = None
+        if FITTED:
+            if len(self.codes) != 1 or self.form != "batched":
+                raise SystemExit("--fitted needs a single-code workload and the batched form")
+            self.fitted = orbg.Fitted(self.objs[0])
+            self.rec = torch.empty((B, orbg.ORBG_FIT_STRIDE), dtype=torch.int32, device=dev)
         self.llr = torch.from_numpy(self.llr_np).to(dev)
         n_total = int(self.n_of_block.sum())
         self.cw = torch.empty((n_total,), dtype=torch.uint8, device=dev)
@@ -554,6 +570,15 @@ class Job:
         self.call(self.stream)
 
     def call(self, stream):
+        if self.fitted is not None:
+            lib = self.orbg.load_library()
+            rc = lib.orbg_fitted_decode(self.fitted.handle, self.llr.data_ptr(), self.B, CAP,
+                                        self.cw.data_ptr(), self.q.data_ptr(),
+                                        self.ab.data_ptr(), self.rec.data_ptr(),
+                                        self.orbg._stream(stream))
+            if rc != 0:
+                raise self.orbg.OrbgError(rc, "orbg_fitted_decode")
+            return
         if self.form == "plain":
             self.orbg.orbg_decode(self.objs[0].handle, self.llr, self.B, CAP, self.cw, self.q,
                                   self.ab, stream)
@@ -582,10 +607,19 @@ class Job:
             sel = self.cid_np == j
             if not sel.any():
                 continue
-            ends, ws = class_weight_prefix(code.n, CAP, LINE, MODEL)
-            qj = qh[sel]
             w32 = (code.r + 31) // 32
-            total += w32 * (sum_weights(qj, ends, ws) + int(qj.sum()))
+            if self.fitted is not None:
+                # each block in its own line's order (beta = 1, J_0 per block)
+                rec = self.rec.cpu().numpy()
+                J0 = np.where(rec[:, 0] == 0, 0, rec[:, 8])
+                for j0 in np.unique(J0):
+                    ends, ws = class_weight_prefix(code.n, CAP, (int(j0), 1))
+                    qj = qh[J0 == j0]
+                    total += w32 * (sum_weights(qj, ends, ws) + int(qj.sum()))
+            else:
+                ends, ws = class_weight_prefix(code.n, CAP, LINE, MODEL)
+                qj = qh[sel]
+                total += w32 * (sum_weights(qj, ends, ws) + int(qj.sum()))
             total += int(sel.sum()) * code.n * math.ceil(math.log2(code.n))
         return total
 
@@ -612,6 +646,8 @@ def bench_ours(args, rank, world, local):
         f = [int(x) for x in args.shape.split(",")]
         orbg.orbg_codeset_set_tuning(job.cs.handle, orbg.OrbgTuning(*f))
         tuned = "given (--shape)"
+    elif FITTED:
+        tuned = "default (the fitted decoder's own code set)"
     elif not args.no_autotune and args.form == "batched":
         job.autotune()  # untimed: scheduling knobs only, results do not change
         tuned = "autotuned on this workload before warm-up"
@@ -620,7 +656,9 @@ def bench_ours(args, rank, world, local):
         job.step()
     torch.cuda.synchronize(dev)
     graph = "direct calls (--no-graph)"
-    if not args.no_graph:
+    if FITTED:
+        graph = "direct calls (the fitted decoder reads each block's line back mid-step)"
+    elif not args.no_graph:
         try:
             job.capture()
             for _ in range(3):  # warm-up replays
@@ -677,7 +715,7 @@ def bench_ours(args, rank, world, local):
 
     # end to end: host (pinned) buffers through the same C call
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not FITTED:
         e2e = bench_e2e(orbg, job, args, world, dev)
 
     line = {
@@ -695,7 +733,9 @@ def bench_ours(args, rank, world, local):
                              ">" if job.llr_np.nbytes > 129e6 else "<=")),
                    "tuning": orbg.orbg_codeset_get_tuning(job.cs.handle).as_dict(),
                    "tuning_source": tuned, "timed": graph,
-                   "order": (("%d-segment full ORBGRAND, %s"
+                   "order": ("one-line full ORBGRAND, a line fitted per block (Sec. III-E)"
+                             if FITTED else
+                             ("%d-segment full ORBGRAND, %s"
                               % (len(MODEL[1]), describe_model(MODEL))) if MODEL
                              else ("one-line full ORBGRAND, J0=%d beta=%d" % LINE) if LINE
                              else "basic ORBGRAND"),
@@ -707,7 +747,7 @@ def bench_ours(args, rank, world, local):
         "abandon_rate": float(abh.mean()),
         "mean_queries": float(qh.mean()),
         "bler": job.bler(),
-        "gpu_launches": (1 if args.form == "plain" else 2) * args.steps,
+        "gpu_launches": (1 if args.form == "plain" else 3 if FITTED else 2) * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "Tops/s", "frac": (achieved / peak) if peak else None,
                      "traffic": None,
@@ -728,7 +768,7 @@ def bench_ours(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(job)
     if (rank == 0 and world == 1 and not args.no_extra and WORKLOAD_NAME == "bch" and
-            LINE is None and MODEL is None and args.form == "batched"):
+            LINE is None and MODEL is None and not FITTED and args.form == "batched"):
         t = orbg.orbg_codeset_get_tuning(job.cs.handle)
         shape = ",".join(str(x) for x in (t.warps_per_cta, t.ctas_per_sm, t.blocks_per_grab,
                                           t.warp_budget, t.heavy_warps))

@@ -123,3 +123,23 @@ def test_extra_runs_parse_their_arguments():
         bench.MODEL = None
         bench.LINE = None
         bench.parse_args([])
+
+
+def test_class_weight_prefix_fitted_lines_match_oracle():
+    """The bench's op count for one line fitted per block (each block's own
+    J_0, beta = 1; J_0 = -1 included) equals the oracle's weight sums of its
+    fit-then-decode."""
+    import bench
+    import oracle
+    from paper_2202_13951_gb300 import workloads
+    code = workloads.rlc(64, 48, 5)
+    llr = np.concatenate([workloads.awgn_llr(code, 60, eb, 9 + int(eb))[0]
+                          for eb in (1.0, 3.0, 6.0)])
+    _, q, _, sw = oracle.decode_batch_fit(code.H, llr, 10 ** 5, 1)
+    J0 = np.array([oracle.fit(x, 1)[1][0] for x in llr])
+    assert (J0 == -1).any() and len(set(J0.tolist())) > 3
+    total = 0
+    for j0 in np.unique(J0):
+        ends, ws = bench.class_weight_prefix(code.n, 10 ** 5, (int(j0), 1))
+        total += bench.sum_weights(q[J0 == j0].astype(np.int64), ends, ws)
+    assert total == int(sw.sum())
