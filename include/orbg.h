@@ -1,5 +1,5 @@
 /*
- * orbg.h -- C ABI of the GB300 basic-ORBGRAND decoder.
+ * orbg.h -- C ABI of the GB300 ORBGRAND decoder.
  *
  * Basic ORBGRAND (Duffy, An, Medard, arXiv 2202.13951): for each received
  * block, sort the bit positions by reliability |LLR| (Sec. III-A), query
@@ -8,6 +8,12 @@
  * that is a code-book member, i.e. whose syndrome H (y (+) z) is zero
  * (Algorithm 1; membership of a linear code by a matrix multiply and
  * compare, Sec. I), or abandon after the query cap (Sec. IV-A).
+ * Full ORBGRAND (Sec. III-D, III-E) replaces the logistic weight by the
+ * reliability weight of a one-line or piece-wise linear model of the
+ * ordered reliabilities: orbg_load_code_line and orbg_load_code_model load
+ * a code for a fixed line or model, orbg_fit_models fits each block's
+ * model on the device, and orbg_fitted_* decodes every block in the order
+ * of its own fitted line.
  *
  * Query order fixed by this library where the paper leaves ties arbitrary:
  *   - bits with equal |LLR| are ordered by their received index;
@@ -22,10 +28,11 @@
  *   - on error, output buffers are unspecified;
  *   - abandonment is a per-block result, not an error;
  *   - buffers are owned by the caller.  Each may be a device pointer or a
- *     host pointer (detected per pointer).  With all buffers on the device
- *     the call is asynchronous on `cuda_stream` (NULL = the legacy default
- *     stream) and the buffers must stay valid until the stream reaches the
- *     call's end.  With any host buffer the library stages the data through
+ *     host pointer (detected per pointer), except where a function asks
+ *     for device memory only (orbg_fit_models, orbg_fitted_decode).  With
+ *     all buffers on the device the call is asynchronous on `cuda_stream`
+ *     (NULL = the legacy default stream) and the buffers must stay valid
+ *     until the stream reaches the call's end.  With any host buffer the library stages the data through
  *     device memory, copies results back and synchronises the stream before
  *     returning.
  */
