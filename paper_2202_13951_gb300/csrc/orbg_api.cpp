@@ -1048,9 +1048,10 @@ int orbg_codeset_autotune(orbg_codeset *set, const int32_t *code_id, const int64
  * of Sec. III-D).  With one line the fit gives beta = 1 and J_0 = [L_1/Q] -
  * 1 >= -1, so the blocks of a batch fall into few orders (one per J_0).
  * The object keeps one handle of the code per J_0 met so far, and a code
- * set over them; a decode fits every block on the device, reads the J_0s
- * back, and decodes all blocks in one batched launch, each with its own
- * J_0's handle.  J_0 above n(n+1)/2 orders patterns by Hamming weight
+ * set over them; a decode fits every block on the device, marks which J_0s
+ * occur (read back: one byte per possible J_0), adds the missing handles,
+ * maps each block to its J_0's code id on the device, and decodes all
+ * blocks in one batched launch.  J_0 above n(n+1)/2 orders patterns by Hamming weight
  * first whatever its value, so it is held at n(n+1)/2 + 1.
  */
 struct orbg_fitted {
@@ -1129,31 +1130,39 @@ int orbg_fitted_decode(orbg_fitted *f, const float *llr, int64_t B, uint32_t que
     std::lock_guard<std::mutex> lk(f->mu);
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const int n = f->code->n;
-    const int32_t j0_top = n * (n + 1) / 2 + 1;
+    const int32_t top = n * (n + 1) / 2 + 1; /* J_0 held at most here */
+    const size_t nj = (size_t)top + 2;       /* J_0 = -1 .. top */
     int32_t *d_models = models;
-    int32_t *d_cid = nullptr;
+    int32_t *d_cid = nullptr, *d_lut = nullptr;
+    uint8_t *d_present = nullptr;
     cudaError_t e = cudaSuccess;
     int rc = ORBG_OK;
-    if (!models && (e = cudaMallocAsync((void **)&d_models,
-                                        (size_t)B * ORBG_FIT_STRIDE * sizeof(int32_t), st)) !=
-                       cudaSuccess)
-        return cuda_fail(e);
-    /* the line of every block, then each block's m and J_0 on the host */
-    std::vector<int32_t> mj((size_t)B * 2);
-    rc = orbg_fit_models(llr, B, n, 1, f->divisible, d_models, cuda_stream);
-    const size_t rec = ORBG_FIT_STRIDE * sizeof(int32_t);
+    if ((!models && (e = cudaMallocAsync((void **)&d_models,
+                                         (size_t)B * ORBG_FIT_STRIDE * sizeof(int32_t), st)) !=
+                        cudaSuccess) ||
+        (e = cudaMallocAsync((void **)&d_cid, (size_t)B * sizeof(int32_t), st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&d_lut, nj * sizeof(int32_t), st)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&d_present, nj, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(d_present, 0, nj, st)) != cudaSuccess)
+        rc = cuda_fail(e);
+    /* every block's line, then which J_0s occur (device), read back */
+    if (rc == ORBG_OK)
+        rc = orbg_fit_models(llr, B, n, 1, f->divisible, d_models, cuda_stream);
+    std::vector<uint8_t> present(nj);
     if (rc == ORBG_OK &&
-        ((e = cudaMemcpy2DAsync(mj.data(), 8, d_models, rec, 4, (size_t)B,
-                                cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
-         (e = cudaMemcpy2DAsync(mj.data() + 1, 8, d_models + 8, rec, 4, (size_t)B,
-                                cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        ((e = (cudaError_t)orbg_fit_mark_lines(d_models, B, top, d_present, cuda_stream)) !=
+             cudaSuccess ||
+         (e = cudaMemcpyAsync(present.data(), d_present, nj, cudaMemcpyDeviceToHost, st)) !=
+             cudaSuccess ||
          (e = cudaStreamSynchronize(st)) != cudaSuccess))
         rc = cuda_fail(e);
-    /* a handle per J_0 (NaN blocks, m = 0, take any: the decode flags them) */
-    std::vector<int32_t> cid((size_t)B);
+    /* a handle per J_0 met (cached across calls), and the J_0 -> code id table */
+    std::vector<int32_t> lut(nj, 0);
     bool grown = false;
-    for (int64_t b = 0; b < B && rc == ORBG_OK; b++) {
-        const int32_t J0 = mj[2 * b] == 0 ? 0 : std::min(mj[2 * b + 1], j0_top);
+    for (size_t i = 0; i < nj && rc == ORBG_OK; i++) {
+        if (!present[i])
+            continue;
+        const int32_t J0 = (int32_t)i - 1;
         auto it = f->slot.find(J0);
         if (it == f->slot.end()) {
             if (f->handles.size() >= 1024) {
@@ -1167,25 +1176,28 @@ int orbg_fitted_decode(orbg_fitted *f, const float *llr, int64_t B, uint32_t que
             it = f->slot.emplace(J0, (int)f->handles.size() - 1).first;
             grown = true;
         }
-        cid[b] = it->second;
+        lut[i] = it->second;
     }
     if (rc == ORBG_OK && (grown || !f->set)) {
         orbg_codeset_free(f->set);
         f->set = nullptr;
         rc = orbg_codeset_create(f->handles.data(), (int)f->handles.size(), &f->set);
     }
-    /* one batched launch, every block in its own line's order */
+    /* code ids on the device, then one batched launch, each block in its
+     * own line's order */
     if (rc == ORBG_OK &&
-        ((e = cudaMallocAsync((void **)&d_cid, (size_t)B * sizeof(int32_t), st)) != cudaSuccess ||
-         (e = cudaMemcpyAsync(d_cid, cid.data(), (size_t)B * sizeof(int32_t),
-                              cudaMemcpyHostToDevice, st)) != cudaSuccess))
+        ((e = cudaMemcpyAsync(d_lut, lut.data(), nj * sizeof(int32_t), cudaMemcpyHostToDevice,
+                              st)) != cudaSuccess ||
+         (e = (cudaError_t)orbg_fit_map_lines(d_models, B, top, d_lut, d_cid, cuda_stream)) !=
+             cudaSuccess))
         rc = cuda_fail(e);
     if (rc == ORBG_OK)
         rc = orbg_decode_batched(f->set, d_cid, nullptr, llr, B, query_cap, codeword, nullptr,
                                  queries, abandoned, cuda_stream);
-    if (d_cid)
-        cudaFreeAsync(d_cid, st);
-    if (!models)
+    for (void *p : {(void *)d_cid, (void *)d_lut, (void *)d_present})
+        if (p)
+            cudaFreeAsync(p, st);
+    if (!models && d_models)
         cudaFreeAsync(d_models, st);
     return rc;
 }

@@ -78,6 +78,36 @@ __global__ void __launch_bounds__(kWarps * 32) orbg_fit_kernel(const float *__re
     }
 }
 
+/* J_0 of a one-line record, as the fitted decoder groups blocks: NaN
+ * blocks (m = 0) join J_0 = 0, and J_0 is held within [-1, top]. */
+__device__ __forceinline__ int32_t line_j0(const int32_t *rec, int32_t top)
+{
+    const int32_t j0 = rec[0] == 0 ? 0 : rec[8];
+    return j0 < -1 ? -1 : j0 > top ? top : j0;
+}
+
+__global__ void orbg_fit_mark_kernel(const int32_t *__restrict__ models, int64_t B, int32_t top,
+                                     uint8_t *__restrict__ present)
+{
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B;
+         b += (int64_t)gridDim.x * blockDim.x)
+        present[line_j0(models + b * (int64_t)ORBG_FIT_STRIDE, top) + 1] = 1;
+}
+
+__global__ void orbg_fit_map_kernel(const int32_t *__restrict__ models, int64_t B, int32_t top,
+                                    const int32_t *__restrict__ lut, int32_t *__restrict__ cid)
+{
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B;
+         b += (int64_t)gridDim.x * blockDim.x)
+        cid[b] = lut[line_j0(models + b * (int64_t)ORBG_FIT_STRIDE, top) + 1];
+}
+
+unsigned grid_for(int64_t B, int threads)
+{
+    const int64_t g = (B + threads - 1) / threads;
+    return (unsigned)(g < 152 * 8 ? (g > 0 ? g : 1) : 152 * 8);
+}
+
 bool device_accessible(const void *p)
 {
     cudaPointerAttributes a;
@@ -106,4 +136,20 @@ extern "C" ORBG_API int orbg_fit_models(const float *llr, int64_t B, int n, int 
                                                                          models);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ORBG_OK : orbg_note_cuda_error((int)e);
+}
+
+int orbg_fit_mark_lines(const int32_t *models, int64_t B, int32_t top, uint8_t *present,
+                        void *stream)
+{
+    orbg_fit_mark_kernel<<<grid_for(B, 256), 256, 0, (cudaStream_t)stream>>>(models, B, top,
+                                                                             present);
+    return (int)cudaGetLastError();
+}
+
+int orbg_fit_map_lines(const int32_t *models, int64_t B, int32_t top, const int32_t *lut,
+                       int32_t *cid, void *stream)
+{
+    orbg_fit_map_kernel<<<grid_for(B, 256), 256, 0, (cudaStream_t)stream>>>(models, B, top, lut,
+                                                                            cid);
+    return (int)cudaGetLastError();
 }

@@ -191,6 +191,14 @@ int orbg_codeset_view(const orbg_codeset *set, OrbgSetView *out);
 int orbg_codeset_lengths(const orbg_codeset *set, std::vector<int> *n_of);
 /* Records a cudaError_t for orbg_last_cuda_error; returns the orbg status. */
 int orbg_note_cuda_error(int cuda_error);
+/* Fitted one-line decoding (orbg_fit.cu): over B one-line model records,
+ * present[J_0 + 1] = 1 for every J_0 met, and cid[b] = lut[J_0 + 1]; NaN
+ * blocks count as J_0 = 0 and J_0 is held within [-1, top].  present and
+ * lut hold top + 2 entries.  Return a cudaError_t. */
+int orbg_fit_mark_lines(const int32_t *models, int64_t B, int32_t top, uint8_t *present,
+                        void *stream);
+int orbg_fit_map_lines(const int32_t *models, int64_t B, int32_t top, const int32_t *lut,
+                       int32_t *cid, void *stream);
 int orbg_launch_int_probe(double *lanes_per_clk_per_sm);
 int orbg_launch_smem_probe(double *bytes_per_clk_per_sm);
 #endif
