@@ -438,7 +438,7 @@ ORBG_API int orbg_fit_models(const float *llr, int64_t B, int n, int lines, int 
  * orbg_fitted_decode: device buffers only -- llr [B][n] FP32, codeword
  * [B][n], queries [B], abandoned [B] as orbg_decode; models: NULL or a
  * device buffer [B][ORBG_FIT_STRIDE] that receives each block's fit
- * (orbg_fit_models).  It fits on cuda_stream, reads the J_0s back
+ * (orbg_fit_models).  It fits on cuda_stream, reads back which J_0s occur
  * (synchronising cuda_stream), and decodes all blocks in one batched call
  * with each block's own order; results equal the one-line decoder of each
  * block's line.  Errors: EINVAL (NULL or host buffers), ELIMIT
