@@ -444,6 +444,9 @@ ORBG_API int orbg_fit_models(const float *llr, int64_t B, int n, int lines, int 
  * block's line.  Errors: EINVAL (NULL or host buffers), ELIMIT
  * (query_cap above the code's max_query_cap, more than 1024 distinct
  * lines), ENOMEM, ECUDA.  One call at a time per object (serialised).
+ * orbg_fitted_free releases the object and its handles (NULL is allowed);
+ * like orbg_free_code it is not stream-ordered: no decode call on the
+ * object may still be in flight.
  */
 typedef struct orbg_fitted orbg_fitted;
 ORBG_API int orbg_fitted_create(const orbg_code *code, int divisible, orbg_fitted **out);
