@@ -366,6 +366,8 @@ def run_extra(shape, steps=20, warmup=3, timeout_s=240):
                 rec["clocks"] = d.get("clocks")
         except subprocess.TimeoutExpired:
             rec["error"] = "timed out after %d s" % timeout_s
+        except Exception as exc:  # never lose the headline line to a secondary run
+            rec["error"] = ("%s: %s" % (type(exc).__name__, exc))[:300]
         out.append(rec)
     return out
 
@@ -772,7 +774,10 @@ def bench_ours(args, rank, world, local):
         t = orbg.orbg_codeset_get_tuning(job.cs.handle)
         shape = ",".join(str(x) for x in (t.warps_per_cta, t.ctas_per_sm, t.blocks_per_grab,
                                           t.warp_budget, t.heavy_warps))
-        line["extra_workloads"] = run_extra(shape)
+        try:
+            line["extra_workloads"] = run_extra(shape)
+        except Exception as exc:
+            line["extra_workloads"] = [{"error": ("%s: %s" % (type(exc).__name__, exc))[:300]}]
     if world > 1:
         dist.destroy_process_group()
     return line if rank == 0 else None
