@@ -17,9 +17,10 @@ cores instead, on a bounded sample of the same workload.
 
 Prints one JSON line (rank 0).  At N = 1 on the default workload the line
 also carries ``extra_workloads``: the same workload in the one-line and
-three-segment full ORBGRAND orders (Sec. III-D) and the paper-shaped
-[256,234] workload (``--workload paper256``), each timed on the device in
-its own process after the headline measurement (``--no-extra`` skips them).
+three-segment full ORBGRAND orders (Sec. III-D) and with a line fitted per
+block (Sec. III-E), and the paper-shaped [256,234] workload (``--workload
+paper256``), each timed on the device in its own process after the
+headline measurement (``--no-extra`` skips them).
 """
 import argparse
 import json
@@ -333,7 +334,8 @@ def run_extra(shape, steps=20, warmup=3, timeout_s=240):
     """Secondary measurements, each in its own process after the headline
     one (same box, same clocks sampling): the BCH workload decoded in the
     one-line and three-segment full ORBGRAND orders (with the headline's
-    tuning), and the paper-shaped [256,234] workload in basic order.
+    tuning) and with a line fitted per block, and the paper-shaped
+    [256,234] workload in basic order.
     Device-timed values only (no e2e, no CPU baseline); a failure records
     its message instead of a number."""
     runs = [("bch, one-line full ORBGRAND J0=%d beta=%d" % EXTRA_LINE,
