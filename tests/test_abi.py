@@ -220,3 +220,16 @@ def test_fitted_argument_checks(lib):
     assert lib.orbg_fit_models(None, -1, 64, 3, 0, None, None) == orbg.ORBG_EINVAL
     assert lib.orbg_fit_models(None, 4, 64, 0, 0, None, None) == orbg.ORBG_EINVAL
     assert lib.orbg_fit_models(None, 4, 64, 9, 0, None, None) == orbg.ORBG_EINVAL
+
+
+def test_query_order_model_deep_n256(lib):
+    """Deeper m-segment tables at n = 256: 100,000 patterns of models fitted
+    (Sec. III-E) to blocks of a [256, 234] code expand to the oracle's order
+    in both run tables."""
+    code = workloads.rlc(256, 234, seed=61)
+    llr, _ = workloads.awgn_llr(code, 2, 5.0, seed=3)
+    for b, lines in ((0, 3), (1, 4)):
+        model = oracle.fit(llr[b], lines)
+        want = oracle.enumerate_patterns_mline(256, 100000, model)
+        assert orbg.orbg_query_order_model(256, 100000, 0, model) == want
+        assert orbg.orbg_query_order_model(256, 100000, 1, model) == want
