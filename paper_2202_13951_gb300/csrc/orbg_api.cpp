@@ -1146,11 +1146,11 @@ int orbg_fitted_decode(orbg_fitted *f, const float *llr, int64_t B, uint32_t que
         (e = cudaMemsetAsync(d_present, 0, nj, st)) != cudaSuccess)
         rc = cuda_fail(e);
     /* every block's line, then which J_0s occur (device), read back */
-    if (rc == ORBG_OK)
-        rc = orbg_fit_models(llr, B, n, 1, f->divisible, d_models, cuda_stream);
     std::vector<uint8_t> present(nj);
     if (rc == ORBG_OK &&
-        ((e = (cudaError_t)orbg_fit_mark_lines(d_models, B, top, d_present, cuda_stream)) !=
+        ((e = (cudaError_t)orbg_fit_launch(llr, B, n, 1, f->divisible, d_models,
+                                           cuda_stream)) != cudaSuccess ||
+         (e = (cudaError_t)orbg_fit_mark_lines(d_models, B, top, d_present, cuda_stream)) !=
              cudaSuccess ||
          (e = cudaMemcpyAsync(present.data(), d_present, nj, cudaMemcpyDeviceToHost, st)) !=
              cudaSuccess ||
@@ -1191,10 +1191,45 @@ int orbg_fitted_decode(orbg_fitted *f, const float *llr, int64_t B, uint32_t que
          (e = (cudaError_t)orbg_fit_map_lines(d_models, B, top, d_lut, d_cid, cuda_stream)) !=
              cudaSuccess))
         rc = cuda_fail(e);
-    if (rc == ORBG_OK)
-        rc = orbg_decode_batched(f->set, d_cid, nullptr, llr, B, query_cap, codeword, nullptr,
-                                 queries, abandoned, cuda_stream);
-    for (void *p : {(void *)d_cid, (void *)d_lut, (void *)d_present})
+    /* the batched launch on device buffers (dense layout: every handle has
+     * the code's n), as orbg_decode_batched makes it */
+    unsigned long long *scratch = nullptr;
+    if (rc == ORBG_OK &&
+        (e = cudaMallocAsync((void **)&scratch, orbg_batched_scratch_bytes(B), st)) !=
+            cudaSuccess)
+        rc = cuda_fail(e);
+    if (rc == ORBG_OK) {
+        const orbg_codeset *set = f->set;
+        const orbg_tuning &t = set->tuning;
+        OrbgBatchedArgs a{};
+        a.d_codes = set->d_codes;
+        a.code0 = &set->code0;
+        a.ncodes = set->ncodes;
+        a.n_max = set->n_max;
+        a.w32_max = set->w32_max;
+        a.code_id = d_cid;
+        a.llr_off = nullptr;
+        a.llr = llr;
+        a.B = B;
+        a.cap = query_cap;
+        a.budget = t.warp_budget < query_cap ? t.warp_budget : query_cap;
+        a.cw = codeword;
+        a.cw_off = nullptr;
+        a.q = queries;
+        a.ab = abandoned;
+        a.scratch = scratch;
+        a.warps_per_cta = t.warps_per_cta;
+        a.ctas_per_sm = t.ctas_per_sm;
+        a.grab = t.blocks_per_grab;
+        a.heavy_warps = t.heavy_warps;
+        a.ntrip_max = set->ntrip_max;
+        a.x3w_max = set->x3w_max;
+        a.stream = st;
+        const int le = orbg_launch_batched(a);
+        if (le != 0)
+            rc = cuda_fail((cudaError_t)le);
+    }
+    for (void *p : {(void *)scratch, (void *)d_cid, (void *)d_lut, (void *)d_present})
         if (p)
             cudaFreeAsync(p, st);
     if (!models && d_models)

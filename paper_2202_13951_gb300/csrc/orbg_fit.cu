@@ -120,6 +120,16 @@ bool device_accessible(const void *p)
 
 }  // namespace
 
+int orbg_fit_launch(const float *llr, int64_t B, int n, int lines, int divisible,
+                    int32_t *models, void *stream)
+{
+    const int64_t ctas = (B + kWarps - 1) / kWarps;
+    const unsigned grid = (unsigned)(ctas < 152 * 16 ? ctas : 152 * 16);
+    orbg_fit_kernel<<<grid, kWarps * 32, 0, (cudaStream_t)stream>>>(llr, B, n, lines,
+                                                                    divisible ? 1 : 0, models);
+    return (int)cudaGetLastError();
+}
+
 extern "C" ORBG_API int orbg_fit_models(const float *llr, int64_t B, int n, int lines,
                                         int divisible, int32_t *models, void *cuda_stream)
 {
@@ -129,13 +139,8 @@ extern "C" ORBG_API int orbg_fit_models(const float *llr, int64_t B, int n, int 
         return ORBG_OK;
     if (!llr || !models || !device_accessible(llr) || !device_accessible(models))
         return ORBG_EINVAL;
-    const int64_t ctas = (B + kWarps - 1) / kWarps;
-    const unsigned grid = (unsigned)(ctas < 152 * 16 ? ctas : 152 * 16);
-    orbg_fit_kernel<<<grid, kWarps * 32, 0, (cudaStream_t)cuda_stream>>>(llr, B, n, lines,
-                                                                         divisible ? 1 : 0,
-                                                                         models);
-    const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? ORBG_OK : orbg_note_cuda_error((int)e);
+    const int e = orbg_fit_launch(llr, B, n, lines, divisible, models, cuda_stream);
+    return e == 0 ? ORBG_OK : orbg_note_cuda_error(e);
 }
 
 int orbg_fit_mark_lines(const int32_t *models, int64_t B, int32_t top, uint8_t *present,

@@ -197,6 +197,10 @@ int orbg_note_cuda_error(int cuda_error);
  * lut hold top + 2 entries.  Return a cudaError_t. */
 int orbg_fit_mark_lines(const int32_t *models, int64_t B, int32_t top, uint8_t *present,
                         void *stream);
+/* orbg_fit_models' launch without its argument checks (B >= 1, 1 <= n <=
+ * 256, 1 <= lines <= 8, device buffers); returns a cudaError_t. */
+int orbg_fit_launch(const float *llr, int64_t B, int n, int lines, int divisible,
+                    int32_t *models, void *stream);
 int orbg_fit_map_lines(const int32_t *models, int64_t B, int32_t top, const int32_t *lut,
                        int32_t *cid, void *stream);
 int orbg_launch_int_probe(double *lanes_per_clk_per_sm);
