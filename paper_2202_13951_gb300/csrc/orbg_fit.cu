@@ -50,19 +50,11 @@ __global__ void __launch_bounds__(kWarps * 32) orbg_fit_kernel(const float *__re
             continue;
         }
         __syncwarp();
-        /* bitonic sort, ascending: stage (k, j) compares i and i + j for the
-         * 128 indices i with bit j clear, in direction (i & k) == 0 */
+        /* bitonic sort, ascending: each stage's 128 pairs, four per lane */
         for (int k = 2; k <= kSlots; k <<= 1) {
             for (int j = k >> 1; j > 0; j >>= 1) {
-                for (int t = lane; t < kSlots / 2; t += 32) {
-                    const int i = (t / j) * 2 * j + (t % j);
-                    const int l = i + j;
-                    const float va = s[i], vb = s[l];
-                    if ((va > vb) == ((i & k) == 0)) {
-                        s[i] = vb;
-                        s[l] = va;
-                    }
-                }
+                for (int t = lane; t < kSlots / 2; t += 32)
+                    orbg_fit::bitonic_step(s, k, j, t);
                 __syncwarp();
             }
         }

@@ -57,6 +57,23 @@ ORBG_FIT_HD inline double dvd(double a, double b)
 #endif
 }
 
+/* One compare-exchange of the ascending bitonic sort over `slots` (a power
+ * of two) values: stage (k, j) compares index i and i + j for the slots / 2
+ * indices i with bit j clear, t = 0 .. slots/2 - 1 numbering them, in
+ * direction (i & k) == 0 (ascending).  Stages run for k = 2, 4, .., slots
+ * and, inside each, j = k/2, k/4, .., 1; every pair of a stage is
+ * independent of the others. */
+ORBG_FIT_HD inline void bitonic_step(float *s, int k, int j, int t)
+{
+    const int i = (t / j) * 2 * j + (t % j);
+    const int l = i + j;
+    const float va = s[i], vb = s[l];
+    if ((va > vb) == ((i & k) == 0)) {
+        s[i] = vb;
+        s[l] = va;
+    }
+}
+
 /* [x]: rounding half away from zero */
 ORBG_FIT_HD inline long long round_half_away(double x)
 {

@@ -77,3 +77,18 @@ def test_fit_steps_parabola_closed_forms(fit_host):
         llr = oracle_pins._disguise([j * j for j in range(1, n + 1)], rng)
         assert fit_host(llr, lines) == plain
         assert fit_host(llr, lines, True) == div
+
+
+def test_bitonic_network_sorts_every_length(fit_host):
+    """The kernel's 256-slot bitonic network (orbg_fit.cuh's step, stages in
+    the kernel's order) sorts |LLR| ascending for every n = 1..256, with
+    ties, zeros and infinities; the host build returns an error otherwise."""
+    rng = np.random.default_rng(47)
+    for n in range(1, 257):
+        x = rng.normal(0.0, 2.0, n).astype(np.float32)
+        if n % 3 == 0:
+            x = np.round(x)
+        if n % 5 == 0:
+            x[rng.integers(0, n, 2)] = np.inf
+            x[rng.integers(0, n, 1)] = -0.0
+        fit_host(x, 1)  # asserts the sort held
