@@ -427,6 +427,13 @@ struct ModelBuilder {
     };
     std::vector<Node> nodes;
 
+    /* one weight's patterns, back to back: pattern q is pos_all[start[q] ..
+     * start[q] + len[q]) ascending */
+    std::vector<int> pos_all;
+    std::vector<uint32_t> start;
+    std::vector<uint16_t> len;
+    std::vector<uint32_t> order;  /* pattern indices in (w, positions) order */
+
     int build(uint64_t cap, std::vector<OrbgRun> *out, uint64_t *patterns) {
         const int n = b.n;
         typedef std::pair<long, int> Item;   /* (weight, node) */
@@ -435,15 +442,18 @@ struct ModelBuilder {
         nodes.push_back(Node{-1, 0});
         heap.push(Item(x[0], 0));
         b.t = 1;
-        std::vector<std::vector<int>> bucket;
         long R = 0;
         bool first = true;
         while (b.t <= cap && (first || !heap.empty())) {
-            bucket.clear();
-            if (first)
-                bucket.push_back(std::vector<int>()); /* the empty pattern, weight 0 */
-            else
+            pos_all.clear();
+            start.clear();
+            len.clear();
+            if (first) {                 /* the empty pattern, weight 0 */
+                start.push_back(0);
+                len.push_back(0);
+            } else {
                 R = heap.top().first;
+            }
             first = false;
             while (!heap.empty() && heap.top().first == R) {
                 const int id = heap.top().second;
@@ -456,42 +466,52 @@ struct ModelBuilder {
                     nodes.push_back(Node{par, k + 1});
                     heap.push(Item(R - x[k] + x[k + 1], (int)nodes.size() - 1));
                 }
-                std::vector<int> v;
+                const size_t s0 = pos_all.size();
                 for (int q = id; q >= 0; q = nodes[q].parent)
-                    v.push_back(pos[nodes[q].rank]);
-                std::sort(v.begin(), v.end());
-                bucket.push_back(v);
+                    pos_all.push_back(pos[nodes[q].rank]);
+                std::sort(pos_all.begin() + (long)s0, pos_all.end());
+                start.push_back((uint32_t)s0);
+                len.push_back((uint16_t)(pos_all.size() - s0));
             }
-            if (nodes.size() > (size_t)1 << 30)
+            if (nodes.size() > (size_t)1 << 30 || pos_all.size() > 0xFFFFFFFFull)
                 return -2;
-            std::sort(bucket.begin(), bucket.end(),
-                      [](const std::vector<int> &p, const std::vector<int> &q) {
-                          return p.size() != q.size() ? p.size() < q.size() : p < q;
-                      });
-            if (emit_bucket(bucket, out))
+            order.resize(start.size());
+            for (size_t q = 0; q < order.size(); q++)
+                order[q] = (uint32_t)q;
+            std::sort(order.begin(), order.end(), [this](uint32_t p, uint32_t q) {
+                if (len[p] != len[q])
+                    return len[p] < len[q];
+                const int *a = pos_all.data() + start[p], *c = pos_all.data() + start[q];
+                return std::lexicographical_compare(a, a + len[p], c, c + len[q]);
+            });
+            if (emit_bucket(out))
                 return -2;
         }
         *patterns = b.t - 1;
         return b.overflow ? -2 : 0;
     }
 
+    const int *pat(size_t i) const { return pos_all.data() + start[order[i]]; }
+    int wof(size_t i) const { return len[order[i]]; }
+
     /* Runs of one weight's patterns, class by class (one class per w). */
-    int emit_bucket(const std::vector<std::vector<int>> &P, std::vector<OrbgRun> *out) {
+    int emit_bucket(std::vector<OrbgRun> *out) {
+        const size_t np = order.size();
         size_t i = 0;
-        while (i < P.size()) {
-            const int w = (int)P[i].size();
+        while (i < np) {
+            const int w = wof(i);
             size_t end = i;
-            while (end < P.size() && (int)P[end].size() == w)
+            while (end < np && wof(end) == w)
                 end++;
             if (w - 2 > ORBG_RUN_MAX_PRE)
                 return -2;
             for (size_t s = i; s < end;) {
-                const std::vector<int> &v = P[s];
+                const int *v = pat(s);
                 size_t e = s + 1;
                 if (w >= 2) {
                     const int a = v[w - 2], bb = v[w - 1];
-                    while (e < end && std::equal(v.begin(), v.end() - 2, P[e].begin()) &&
-                           P[e][w - 2] == a + (int)(e - s) && P[e][w - 1] == bb - (int)(e - s))
+                    while (e < end && std::equal(v, v + w - 2, pat(e)) &&
+                           pat(e)[w - 2] == a + (int)(e - s) && pat(e)[w - 1] == bb - (int)(e - s))
                         e++;
                     if (a + bb <= 255) {
                         for (int q = 0; q < w - 2; q++)
@@ -507,7 +527,7 @@ struct ModelBuilder {
                     return -2;
                 for (size_t q = s; q < e; q++) {
                     for (int z = 0; z < w; z++)
-                        b.pre[z] = P[q][z];
+                        b.pre[z] = pat(q)[z];
                     b.single(w);
                 }
                 s = e;
