@@ -539,6 +539,23 @@ def pin_fit_invariants(orc):
                 assert len(orc.enumerate_patterns_mline(64, 50, model)) == 50
 
 
+def pin_fit_degenerate(orc):
+    """Curves Eq. Q and Eq. quant cannot quantise give the basic model
+    (J_0 = 0, beta_1 = 1): fewer than four positions, a flat curve (Q = 0),
+    infinite reliabilities at the anchors, and a ratio beyond 2^24."""
+    basic = ((), (0,), (1,))
+    for n in (1, 2, 3):
+        assert orc.fit(np.arange(1, n + 1, dtype=np.float32), 3) == basic
+    assert orc.fit(np.full(40, 1.5, np.float32), 3) == basic
+    assert orc.fit(np.full(40, np.inf, np.float32), 2) == basic
+    # slope 1e-20 up to the kink at 5, then 1e20: the second slope is 1e40 Q
+    steep = np.array([1e-20 * j if j <= 5 else 5e-20 + 1e20 * (j - 5) for j in range(1, 41)],
+                     np.float32)
+    for lines in (2, 3):
+        assert orc.fit(steep, lines) == basic
+        assert orc.fit(steep, lines, divisible=True) == basic
+
+
 def pin_fit_brute_decode(orc, blocks=24):
     """Full ORBGRAND with per-block fitting (Sec. III-E, then the m-segment
     order) = brute force under the closed-form model, on blocks whose
@@ -570,7 +587,8 @@ FAST_PINS = [pin_first_queries, pin_fig3, pin_fig5, pin_order_brute,
              pin_1line_is_basic_at_origin, pin_1line_brute_decode, pin_1line_invariants,
              pin_mline_order_brute, pin_mline_generating_function,
              pin_mline_one_segment_is_one_line, pin_mline_brute_decode, pin_fit_parabola,
-             pin_fit_piecewise_exact, pin_fit_invariants, pin_fit_brute_decode]
+             pin_fit_piecewise_exact, pin_fit_invariants, pin_fit_degenerate,
+             pin_fit_brute_decode]
 
 
 def run_all(orc, pins=None):

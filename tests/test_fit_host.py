@@ -53,7 +53,9 @@ def _curves():
     out.append(x)
     out.append(np.full(40, np.inf, np.float32))
     out.append(np.full(40, 1.5, np.float32))
-    out.append(np.array([1e-30, 1e-30, 3e-30] + [1e30] * 37, np.float32))  # out of range
+    out.append(np.array([1e-30, 1e-30, 3e-30] + [1e30] * 37, np.float32))
+    out.append(np.array([1e-20 * j if j <= 5 else 5e-20 + 1e20 * (j - 5)
+                         for j in range(1, 41)], np.float32))  # a ratio beyond 2^24
     return out
 
 

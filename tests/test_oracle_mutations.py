@@ -39,6 +39,8 @@ MUTATIONS = [
      "const int lo = a[na - 2], hi = a[na - 1];"),
     ("fit_centre_rounded_up", "a[1] = n / 2;", "a[1] = (n + 1) / 2;"),
     ("fit_Q_largest_slope", "if (s[i] < Q)", "if (s[i] > Q)"),
+    ("fit_range_guard_dropped",
+     "if (!(s[i] / Q <= ORC_FIT_MAX) || !(L[a[i]] / Q <= ORC_FIT_MAX))", "if (0)"),
     ("fit_first_slope_from_origin", "s[0] = (L[a[1]] - L[1]) / (double)(a[1] - 1);",
      "s[0] = L[a[1]] / (double)a[1];"),
     ("fit_J0_unshifted", "J[0] = orc_round(L[1] / Q) - beta[0];", "J[0] = orc_round(L[1] / Q);"),
