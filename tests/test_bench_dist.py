@@ -143,3 +143,37 @@ def test_class_weight_prefix_fitted_lines_match_oracle():
         ends, ws = bench.class_weight_prefix(code.n, 10 ** 5, (int(j0), 1))
         total += bench.sum_weights(q[J0 == j0].astype(np.int64), ends, ws)
     assert total == int(sw.sum())
+
+
+def test_run_extra_parses_child_lines(monkeypatch):
+    """The secondary runs' results are read from each child's JSON line
+    (here a stand-in line; no GPU), and a failing child records its error
+    instead of raising."""
+    import json
+    import subprocess
+    import types
+    import bench
+    line = {"value": 1.0e6, "unit": "blocks/s", "ms_per_step": 0.4, "steps": 20,
+            "queries_per_s": 2.0e9, "mean_queries": 12.5, "abandon_rate": 0.0, "bler": 0.01,
+            "gpu_launches": 40,
+            "config": {"workload": "w", "tuning_source": "given (--shape)"},
+            "roofline": {"bound": "alu", "achieved": 3.0, "peak": 20.1, "unit": "Tops/s",
+                         "frac": 0.15, "traffic": None, "what": "x"},
+            "clocks": {"sm_mhz": 2070}}
+    calls = []
+
+    def fake_run(cmd, **kw):
+        calls.append(cmd)
+        if "paper256" in cmd:
+            return types.SimpleNamespace(returncode=1, stdout="", stderr="boom\nRuntimeError: x")
+        return types.SimpleNamespace(returncode=0, stdout="log\n" + json.dumps(line) + "\n",
+                                     stderr="")
+    monkeypatch.setattr(subprocess, "run", fake_run)
+    out = bench.run_extra("8,0,4,16384,8")
+    assert len(out) == len(calls) == 4
+    ok = [r for r in out if "error" not in r]
+    assert len(ok) == 3 and all(r["value"] == 1.0e6 and r["roofline"]["frac"] == 0.15 and
+                                r["workload"] == "w" for r in ok)
+    bad = [r for r in out if "error" in r]
+    assert len(bad) == 1 and "RuntimeError" in bad[0]["error"]
+    assert all("--no-extra" in c and "--no-cpu-baseline" in c for c in calls)
