@@ -31,6 +31,7 @@ ORBG_BLOCK_DECODED = 0
 ORBG_BLOCK_ABANDONED = 1
 ORBG_BLOCK_NAN = 2
 ORBG_NOALLOC_MAX_BLOCKS = 1 << 19
+ORBG_FIT_STRIDE = 24
 
 LIB_PATH = _build.LIB
 _lib = None
@@ -425,9 +426,6 @@ def orbg_query_order_model(n, count, table, model):
     if got < 0:
         raise OrbgError(int(got), "orbg_query_order_model")
     return [tuple(int(x) for x in row[1:1 + row[0]]) for row in out[:got]]
-
-
-ORBG_FIT_STRIDE = 24
 
 
 def fit_models(llr, n, lines, divisible=False, stream=None):
