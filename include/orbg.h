@@ -107,7 +107,9 @@ ORBG_API int orbg_load_code(const uint8_t *mat, int kind, int n, int k,
  * weight ascending, then lexicographic).  J0: 0..1024, beta: 1..1024;
  * J0 = 0, beta = 1 is orbg_load_code.  Every decode entry point decodes
  * in the handle's order.  Errors as orbg_load_code; EINVAL for J0 or beta
- * out of range.
+ * out of range; ELIMIT when the order up to max_query_cap reaches a
+ * logistic weight above 255 (a large J0 at a large cap; the same line as a
+ * one-segment orbg_load_code_model has no such limit).
  */
 ORBG_API int orbg_load_code_line(const uint8_t *mat, int kind, int n, int k,
                                  uint32_t max_query_cap, int32_t J0, int32_t beta,
@@ -443,7 +445,8 @@ ORBG_API int orbg_fit_models(const float *llr, int64_t B, int n, int lines, int 
  * with each block's own order; results equal the one-line decoder of each
  * block's line.  Errors: EINVAL (NULL or host buffers), ELIMIT
  * (query_cap above the code's max_query_cap, more than 1024 distinct
- * lines), ENOMEM, ECUDA.  One call at a time per object (serialised).
+ * lines, or a line whose order puts position 256 of an n = 256 code within
+ * the cap), ENOMEM, ECUDA.  One call at a time per object (serialised).
  * orbg_fitted_free releases the object and its handles (NULL is allowed);
  * like orbg_free_code it is not stream-ordered: no decode call on the
  * object may still be in flight.

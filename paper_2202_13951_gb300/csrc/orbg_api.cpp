@@ -1066,12 +1066,17 @@ struct orbg_fitted {
 namespace {
 
 /* The code in the one-line order of (J_0, beta = 1): line tables when
- * 0 <= J_0 <= ORBG_MAX_LINE, else the one-segment model tables. */
+ * 0 <= J_0 <= ORBG_MAX_LINE and they reach the cap (a large J_0 takes them
+ * past logistic weight ORBG_MAX_LOGISTIC), else the one-segment model
+ * tables, which hold any weight. */
 int fitted_handle(const orbg_code *code, int32_t J0, orbg_code **out)
 {
-    if (J0 >= 0 && J0 <= ORBG_MAX_LINE)
-        return load_code(code->H.data(), ORBG_MAT_H, code->n, code->k, code->max_cap, nullptr,
-                         J0, 1, out);
+    if (J0 >= 0 && J0 <= ORBG_MAX_LINE) {
+        const int rc = load_code(code->H.data(), ORBG_MAT_H, code->n, code->k, code->max_cap,
+                                 nullptr, J0, 1, out);
+        if (rc != ORBG_ELIMIT)
+            return rc;
+    }
     OrbgModel md;
     md.m = 1;
     md.I[0] = 0;

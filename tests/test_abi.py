@@ -233,3 +233,15 @@ def test_query_order_model_deep_n256(lib):
         want = oracle.enumerate_patterns_mline(256, 100000, model)
         assert orbg.orbg_query_order_model(256, 100000, 0, model) == want
         assert orbg.orbg_query_order_model(256, 100000, 1, model) == want
+
+
+def test_large_line_intercept_needs_model_tables(lib):
+    """A large J_0 makes the line tables stop at logistic weight 255 before
+    the cap (ELIMIT); the one-segment model tables, which the fitted decoder
+    falls back to, hold the same order to the cap."""
+    with pytest.raises(orbg.OrbgError) as ei:
+        orbg.orbg_query_order_line(255, 20000, 0, 202, 1)
+    assert ei.value.status == orbg.ORBG_ELIMIT
+    model = ((), (202,), (1,))
+    want = oracle.enumerate_patterns_mline(255, 20000, model)
+    assert orbg.orbg_query_order_model(255, 20000, 0, model) == want
