@@ -27,10 +27,11 @@ def orbg():
 # ------------------------------------------- m-segment full ORBGRAND
 
 def _models(n, llr):
-    """A hand-set model with a zero-weight least reliable position, and
-    models fitted (Sec. III-E) to two of the blocks."""
-    return [((n // 8,), (-2, n // 8 + 3), (2, 1)), oracle.fit(llr[0], 3),
-            oracle.fit(llr[1], 2, True), oracle.fit(llr[2], 4)]
+    """Hand-set models — a zero-weight least reliable position; light
+    positions far down the order, which leave the flat table empty — and
+    models fitted (Sec. III-E) to three of the blocks."""
+    return [((n // 8,), (-2, n // 8 + 3), (2, 1)), ((n * 5 // 8,), (-4, 0), (9, 4)),
+            oracle.fit(llr[0], 3), oracle.fit(llr[1], 2, True), oracle.fit(llr[2], 4)]
 
 
 def test_m_segment_orbgrand(orbg):
