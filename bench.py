@@ -330,14 +330,15 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(inside), "window": window}
 
 
-def run_extra(shape, steps=20, warmup=3, timeout_s=240):
+def run_extra(shape, steps=20, warmup=3, timeout_s=240, budget_s=420):
     """Secondary measurements, each in its own process after the headline
     one (same box, same clocks sampling): the BCH workload decoded in the
     one-line and three-segment full ORBGRAND orders (with the headline's
     tuning) and with a line fitted per block, and the paper-shaped
     [256,234] workload in basic order.
     Device-timed values only (no e2e, no CPU baseline); a failure records
-    its message instead of a number."""
+    its message instead of a number; runs that would start after budget_s
+    seconds are skipped, so the whole bench stays within minutes."""
     runs = [("bch, one-line full ORBGRAND J0=%d beta=%d" % EXTRA_LINE,
              ["--line", "%d,%d" % EXTRA_LINE, "--shape", shape]),
             ("bch, 3-segment full ORBGRAND %s" % describe_model(EXTRA_MODEL),
@@ -346,10 +347,15 @@ def run_extra(shape, steps=20, warmup=3, timeout_s=240):
             ("bch, one-line full ORBGRAND with a line fitted per block", ["--fitted"]),
             ("paper256, basic ORBGRAND", ["--workload", "paper256"])]
     out = []
+    t0 = time.time()
     for label, argv in runs:
         cmd = [sys.executable, os.path.abspath(__file__), *argv, "--steps", str(steps),
                "--warmup", str(warmup), "--no-cpu-baseline", "--no-e2e", "--no-extra"]
         rec = {"label": label, "args": " ".join(argv)}
+        if time.time() - t0 > budget_s:
+            rec["error"] = "skipped: the secondary runs' %d s budget was spent" % budget_s
+            out.append(rec)
+            continue
         try:
             r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
             last = [x for x in r.stdout.splitlines() if x.startswith("{")]
