@@ -2,25 +2,29 @@
 """Throughput of the GB300 basic-ORBGRAND decoder.
 
 One step = one batched persistent launch (orbg_decode_batched) over the
-whole BCH(127,113) workload: 4 x 100,000 blocks of FP32 LLRs at Eb/N0 =
-4, 5, 6, 7 dB, query cap 1e6 -- every block sorted, searched and written
-back.  Inputs (203 MB, larger than the 129 MB L2) are resident in HBM when
-the timed region starts; the code tables stay resident.
+whole mixed workload: 1,000,000 blocks, each of a random linear code drawn
+uniformly from (64,51), (128,112), (256,240) and (256,232), at Eb/N0
+uniform in [4, 7] dB, query cap 1e6 -- every block sorted, searched and
+written back.  Inputs (576 MB, larger than the 129 MB L2) are resident in
+HBM when the timed region starts; the code tables stay resident.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 N > 1 runs under torchrun, one rank per GPU: each rank decodes its own
-400,000-block workload (seeds offset by rank), there is no data-path
-collective (blocks are independent), and the timing is the max over ranks
-(weak scaling).  ``--impl reference`` times the CPU oracle on the host
-cores instead, on a bounded sample of the same workload.
+workload (seeds offset by rank), there is no data-path collective (blocks
+are independent), and the timing is the max over ranks (weak scaling).
+``--impl reference`` times the CPU oracle on the host cores instead, on a
+bounded sample of the same workload.
 
-Prints one JSON line (rank 0).  At N = 1 on the default workload the line
-also carries ``extra_workloads``: the same workload in the one-line and
-three-segment full ORBGRAND orders (Sec. III-D) and with a line fitted per
-block (Sec. III-E), and the paper-shaped [256,234] workload (``--workload
-paper256``), each timed on the device in its own process after the
-headline measurement (``--no-extra`` skips them).
+Prints one JSON line (rank 0).  Besides the timing it carries ``parity``:
+the GPU outputs of the timed step compared bit for bit with the oracle on
+a stratified sample of the blocks (the whole workload where that is cheap).
+At N = 1 on the default workload the line also carries ``forms`` (the
+BCH(127,113) workload through the plain single launch and the batched form,
+same inputs, same BLER), ``serving`` (the continuous-batching server on a
+Poisson trace) and ``extra_workloads`` (full ORBGRAND orders, Sec. III-D and
+III-E, and the paper-shaped [256,234] workload), each measured in its own
+process after the headline (``--no-extra`` skips them).
 """
 import argparse
 import json
@@ -65,8 +69,6 @@ B_PER_POINT = 100_000
 WORKLOAD = WORKLOADS["bch"][0] % B_PER_POINT
 CAP = 1_000_000
 CAPS = {"rlc64": 100_000, "paper256": 5_000_000}
-SMS = 152
-SM_MAX_MHZ = 2070.0
 
 
 # ------------------------------------------------------------------ utils
@@ -94,9 +96,20 @@ def parse_args(argv=None):
                    help="time direct calls instead of replays of a captured CUDA graph")
     p.add_argument("--ref-sample", type=int, default=8000,
                    help="blocks per reference step (CPU oracle)")
-    p.add_argument("--workload", choices=sorted(WORKLOADS), default="bch",
-                   help="bch: the headline configuration; capolar: the search-heavy "
-                        "CA-Polar configuration (profiling)")
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default="mixed",
+                   help="mixed: the headline configuration (1,000,000 blocks of four "
+                        "random codes); bch, capolar, rlc64: the single-code "
+                        "configurations; paper256: the paper-shaped [256,234] family")
+    p.add_argument("--no-parity", action="store_true",
+                   help="skip the oracle comparison of the timed step's outputs")
+    p.add_argument("--parity-budget", type=float, default=60.0,
+                   help="seconds of host-core time (wall) the oracle comparison may take")
+    p.add_argument("--parity-per-code", type=int, default=20000,
+                   help="blocks of each code the oracle comparison aims to check")
+    p.add_argument("--no-serving", action="store_true",
+                   help="skip the serving measurement of the default run")
+    p.add_argument("--serving-seconds", type=float, default=10.0,
+                   help="seconds of Poisson arrivals in the serving measurement")
     p.add_argument("--blocks-per-point", type=int, default=B_PER_POINT)
     p.add_argument("--form", choices=("batched", "plain"), default="batched",
                    help="batched: orbg_decode_batched (two persistent launches); plain: "
@@ -330,71 +343,141 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(inside), "window": window}
 
 
-def run_extra(shape, steps=20, warmup=3, timeout_s=240, budget_s=420):
-    """Secondary measurements, each in its own process after the headline
-    one (same box, same clocks sampling): the BCH workload decoded in the
-    one-line and three-segment full ORBGRAND orders (with the headline's
-    tuning) and with a line fitted per block, and the paper-shaped
-    [256,234] workload in basic order.
-    Device-timed values only (no e2e, no CPU baseline); a failure records
-    its message instead of a number; runs that would start after budget_s
-    seconds are skipped, so the whole bench stays within minutes."""
-    runs = [("bch, one-line full ORBGRAND J0=%d beta=%d" % EXTRA_LINE,
-             ["--line", "%d,%d" % EXTRA_LINE, "--shape", shape]),
+def run_child(argv, steps=20, warmup=3, timeout_s=300):
+    """bench.py in its own process with argv (device-timed only: no e2e, no
+    CPU baseline, no secondary runs); its JSON line, or {"error": ...}."""
+    cmd = [sys.executable, os.path.abspath(__file__), *argv, "--steps", str(steps),
+           "--warmup", str(warmup), "--no-cpu-baseline", "--no-e2e", "--no-extra"]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
+        last = [x for x in r.stdout.splitlines() if x.startswith("{")]
+        if r.returncode != 0 or not last:
+            return {"error": ("exit %d: %s" % (r.returncode,
+                                               (r.stderr.strip().splitlines() or [""])[-1]))[:300]}
+        return json.loads(last[-1])
+    except subprocess.TimeoutExpired:
+        return {"error": "timed out after %d s" % timeout_s}
+    except Exception as exc:  # never lose the headline line to a secondary run
+        return {"error": ("%s: %s" % (type(exc).__name__, exc))[:300]}
+
+
+def summarise_child(d):
+    rec = {k: d.get(k) for k in ("value", "unit", "ms_per_step", "steps", "queries_per_s",
+                                 "mean_queries", "abandon_rate", "bler", "gpu_launches")}
+    rec["workload"] = d["config"]["workload"]
+    rec["form"] = d["config"].get("form")
+    rec["tuning_source"] = d["config"].get("tuning_source")
+    rec["timed"] = d["config"].get("timed")
+    rec["roofline"] = {k: d["roofline"].get(k)
+                       for k in ("bound", "achieved", "peak", "unit", "frac", "issued_frac",
+                                 "traffic")}
+    rec["clocks"] = d.get("clocks")
+    if "parity" in d:
+        rec["parity"] = {k: d["parity"].get(k) for k in ("checked", "blocks", "mismatches",
+                                                          "abandoned_checked")}
+    return rec
+
+
+def run_forms():
+    """The plain single launch against the batched form on the same inputs:
+    the BCH(127,113) workload (4 x 100,000 blocks at 4-7 dB, cap 1e6),
+    each form in its own process, each with its own parity check (the whole
+    workload against the oracle).  Identical outputs give identical BLER."""
+    out = {}
+    every = ["--parity-per-code", "400000"]
+    for name, argv in (("batched", ["--workload", "bch"] + every),
+                       ("plain", ["--workload", "bch", "--form", "plain"] + every)):
+        d = run_child(argv)
+        out[name] = d if "error" in d else summarise_child(d)
+    b, p = out["batched"], out["plain"]
+    if "error" not in b and "error" not in p:
+        out["same_bler"] = b["bler"] == p["bler"]
+        out["batched_over_plain"] = b["value"] / p["value"]
+    return out
+
+
+def run_serving(seconds, timeout_s=420):
+    """The serving measurement (paper_2202_13951_gb300.serve --measure) in
+    its own process: capacity, half capacity and 2e6 blocks/s offered."""
+    cmd = [sys.executable, "-m", "paper_2202_13951_gb300.serve", "--measure", "--seconds",
+           str(seconds)]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s, cwd=ROOT)
+        last = [x for x in r.stdout.splitlines() if x.startswith("{")]
+        if r.returncode != 0 or not last:
+            return {"error": ("exit %d: %s" % (r.returncode,
+                                               (r.stderr.strip().splitlines() or [""])[-1]))[:300]}
+        return json.loads(last[-1])
+    except subprocess.TimeoutExpired:
+        return {"error": "timed out after %d s" % timeout_s}
+    except Exception as exc:
+        return {"error": ("%s: %s" % (type(exc).__name__, exc))[:300]}
+
+
+def extra_runs():
+    """(label, argv) of the secondary measurements."""
+    return [("bch, one-line full ORBGRAND J0=%d beta=%d" % EXTRA_LINE,
+             ["--workload", "bch", "--line", "%d,%d" % EXTRA_LINE]),
             ("bch, 3-segment full ORBGRAND %s" % describe_model(EXTRA_MODEL),
-             ["--model", ";".join(",".join(str(x) for x in f) for f in EXTRA_MODEL),
-              "--shape", shape]),
-            ("bch, one-line full ORBGRAND with a line fitted per block", ["--fitted"]),
+             ["--workload", "bch", "--model",
+              ";".join(",".join(str(x) for x in f) for f in EXTRA_MODEL)]),
+            ("bch, one-line full ORBGRAND with a line fitted per block",
+             ["--workload", "bch", "--fitted"]),
             ("paper256, basic ORBGRAND", ["--workload", "paper256"])]
+
+
+def run_extra(steps=20, warmup=3, timeout_s=300, budget_s=420):
+    """Secondary measurements, each in its own process after the headline
+    one (same box): full ORBGRAND orders on the BCH workload and the
+    paper-shaped [256,234] workload.  Device-timed values only (no e2e, no
+    CPU baseline), each with its own parity check; a failure records its
+    message instead of a number; runs that would start after budget_s
+    seconds are skipped, so the whole bench stays within minutes."""
     out = []
     t0 = time.time()
-    for label, argv in runs:
-        cmd = [sys.executable, os.path.abspath(__file__), *argv, "--steps", str(steps),
-               "--warmup", str(warmup), "--no-cpu-baseline", "--no-e2e", "--no-extra"]
+    for label, argv in extra_runs():
         rec = {"label": label, "args": " ".join(argv)}
         if time.time() - t0 > budget_s:
             rec["error"] = "skipped: the secondary runs' %d s budget was spent" % budget_s
             out.append(rec)
             continue
-        try:
-            r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
-            last = [x for x in r.stdout.splitlines() if x.startswith("{")]
-            if r.returncode != 0 or not last:
-                rec["error"] = ("exit %d: %s" % (r.returncode,
-                                                 (r.stderr.strip().splitlines() or [""])[-1]))[:300]
-            else:
-                d = json.loads(last[-1])
-                rec.update({k: d.get(k) for k in ("value", "unit", "ms_per_step", "steps",
-                                                  "queries_per_s", "mean_queries",
-                                                  "abandon_rate", "bler", "gpu_launches")})
-                rec["workload"] = d["config"]["workload"]
-                rec["tuning_source"] = d["config"].get("tuning_source")
-                rec["roofline"] = {k: d["roofline"].get(k)
-                                   for k in ("bound", "achieved", "peak", "unit", "frac")}
-                rec["clocks"] = d.get("clocks")
-        except subprocess.TimeoutExpired:
-            rec["error"] = "timed out after %d s" % timeout_s
-        except Exception as exc:  # never lose the headline line to a secondary run
-            rec["error"] = ("%s: %s" % (type(exc).__name__, exc))[:300]
+        d = run_child(argv, steps, warmup, timeout_s)
+        rec.update(d if "error" in d else summarise_child(d))
         out.append(rec)
     return out
 
 
 # ------------------------------------------------------------- CPU side
 
-def _oracle_worker(args):
-    H, llr, cap, line, model, fitted = args
+def _oracle_decode(H, llr, cap, line, model, fitted):
+    """The oracle's decoding of llr [B][n] in the bench's order: basic, a
+    line, a model, or a model fitted per block (fitted = lines, or (lines,
+    divisible))."""
     import oracle
-    t = time.perf_counter()
     if fitted:
-        _, q, ab, _ = oracle.decode_batch_fit(H, llr, cap, 1)
+        lines, div = fitted if isinstance(fitted, tuple) else (int(fitted), False)
+        cw, q, ab, _ = oracle.decode_batch_fit(H, llr, cap, lines, div)
     elif model:
-        _, q, ab, _ = oracle.decode_batch_mline(H, llr, cap, model)
+        cw, q, ab, _ = oracle.decode_batch_mline(H, llr, cap, model)
     elif line:
-        _, q, ab, _ = oracle.decode_batch_1line(H, llr, cap, *line)
+        cw, q, ab, _ = oracle.decode_batch_1line(H, llr, cap, *line)
     else:
-        _, q, ab, _ = oracle.decode_batch(H, llr, cap)
+        cw, q, ab, _ = oracle.decode_batch(H, llr, cap)
+    return cw, q, ab
+
+
+def _oracle_worker(args):
+    H, llr, cap, line, model, fitted = args[:6]
+    t = time.perf_counter()
+    cw, q, ab = _oracle_decode(H, llr, cap, line, model, fitted)
     return time.perf_counter() - t, int(q.sum()), llr.shape[0]
+
+
+def _oracle_outputs(args):
+    """(block indices, oracle outputs) of one chunk, for the parity check."""
+    idx, H, llr, cap, line, model, fitted = args
+    cw, q, ab = _oracle_decode(H, llr, cap, line, model, fitted)
+    return idx, cw, q, ab
 
 
 def cpu_sample(llr, per_point, step):
@@ -596,13 +679,35 @@ class Job:
         self.orbg.orbg_decode_batched(self.cs.handle, self.cid, self.off, self.llr, self.B, CAP,
                                       self.cw, self.off, self.q, self.ab, stream)
 
-    def bler(self):
+    def block_starts(self):
+        """First codeword byte of each block in the output buffer."""
+        return (np.concatenate([[0], np.cumsum(self.n_of_block)[:-1]])
+                if self.off_np is None else self.off_np)
+
+    def bler(self, cw=None):
         """Fraction of blocks whose decoding differs from the sent codeword."""
-        got = self.cw.cpu().numpy()
+        got = self.cw.cpu().numpy() if cw is None else cw
         diff = got != self.sent
-        starts = (np.concatenate([[0], np.cumsum(self.n_of_block)[:-1]])
-                  if self.off_np is None else self.off_np)
-        return float(np.logical_or.reduceat(diff, starts).mean())
+        return float(np.logical_or.reduceat(diff, self.block_starts()).mean())
+
+    def launches_per_step(self):
+        """Kernels of this library launched by one step."""
+        if self.form == "plain":
+            return 1
+        sort = 2 if (self.off_np is not None and len(self.codes) > 1) else 0
+        if self.fitted is not None:
+            return 3 + 2 + 2  # fit, mark, map; code sort (a set of one handle per line); phases
+        return 2 + sort
+
+    def kernel_names(self):
+        if self.form == "plain":
+            return "orbg_plain_kernel"
+        names = "orbg_batched_kernel + orbg_heavy_kernel"
+        if self.fitted is not None:
+            return "orbg_fit_kernel + line marking + " + names
+        if self.off_np is not None and len(self.codes) > 1:
+            names += " + the two code-sort kernels"
+        return names
 
     def autotune(self):
         return self.orbg.orbg_codeset_autotune(self.cs.handle, self.cid, self.off, self.llr,
@@ -704,8 +809,8 @@ def bench_ours(args, rank, world, local):
     value = blocks_total / (total_ms / 1000.0)
 
     # work done per step, from this rank's last step
-    qh = job.q.cpu().numpy().astype(np.int64)
-    abh = job.ab.cpu().numpy()
+    got = gpu_outputs(job)
+    qh, abh = got[1], got[2]
     q_step = int(qh.sum())
     queries_total = sum_over_ranks(float(q_step * args.steps), world, dev)
     alg_ops = job.alg_ops(qh)
@@ -717,11 +822,16 @@ def bench_ours(args, rank, world, local):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    lanes = measured_int_lanes(orbg)
-    peak = lanes * SMS * SM_MAX_MHZ * 1e6 / 1e12 if lanes else None
-    smem_bpc = measured_smem_bytes(orbg)
-
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
     clocks = sampler.summary(t_wall0, t_wall1)
+    max_mhz = clocks.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    run_mhz = (clocks.get("sm_mhz") if clocks.get("window") == "timed" and clocks.get("sm_mhz")
+               else max_mhz)
+    lanes = measured_int_lanes(orbg)
+    peak = lanes * sms * run_mhz * 1e6 / 1e12 if lanes else None
+    smem_bpc = measured_smem_bytes(orbg)
+    prof = stored_profile(build, job_profile_key(args))
 
     # end to end: host (pinned) buffers through the same C call
     e2e = None
@@ -743,7 +853,8 @@ def bench_ours(args, rank, world, local):
                              ">" if job.llr_np.nbytes > 129e6 else "<=")),
                    "tuning": orbg.orbg_codeset_get_tuning(job.cs.handle).as_dict(),
                    "tuning_source": tuned, "timed": graph,
-                   "order": ("one-line full ORBGRAND, a line fitted per block (Sec. III-E)"
+                   "order": ("full ORBGRAND, a %d-line model fitted per block (Sec. III-E)"
+                             % (FITTED[0] if isinstance(FITTED, tuple) else 1)
                              if FITTED else
                              ("%d-segment full ORBGRAND, %s"
                               % (len(MODEL[1]), describe_model(MODEL))) if MODEL
@@ -753,42 +864,86 @@ def bench_ours(args, rank, world, local):
         "queries_per_s": queries_total / (total_ms / 1000.0),
         "latency_ms": {"step_p50": statistics.median(per_step),
                        "step_p99": float(np.percentile(per_step, 99)),
-                       "what": "one %d-block batch, launch to completion" % B},
+                       "what": "one %d-block batch, launch to completion (request latency "
+                               "under load: see serving)" % B},
         "abandon_rate": float(abh.mean()),
         "mean_queries": float(qh.mean()),
-        "bler": job.bler(),
-        "gpu_launches": (1 if args.form == "plain" else 3 if FITTED else 2) * args.steps,
+        "bler": job.bler(got[0]),
+        "gpu_launches": job.launches_per_step() * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "Tops/s", "frac": (achieved / peak) if peak else None,
-                     "traffic": None,
-                     "what": ("the step's kernels (batched: orbg_batched_kernel + "
-                              "orbg_heavy_kernel; plain: orbg_plain_kernel); algorithmic "
-                              "32-bit integer ops per launch = sum_t W32 (w_t + 1) + "
-                              "B n ceil(log2 n) = %d; peak = measured LOP3 lanes/clk/SM (%s) "
-                              "x 152 SMs x 2070 MHz" % (alg_ops, lanes))},
+                     "traffic": prof.get("traffic_bytes_per_step") if prof else None,
+                     "issued_frac": prof.get("issued_frac") if prof else None,
+                     "what": ("the step's decode kernels together (%s), timed by CUDA events "
+                              "around each step on the launching stream; algorithmic 32-bit "
+                              "integer ops per step = sum_t W32 (w_t + 1) + B n ceil(log2 n) "
+                              "= %d, which charges each column XOR as one op although one "
+                              "3-input lop3 can retire two, and charges every query in full "
+                              "although the triple-range walk tests sixteen queries with "
+                              "about thirty instructions (so frac can exceed 1 on "
+                              "search-heavy work); peak = measured lop3 lanes/clk/SM (%s) x "
+                              "%d SMs x %.0f MHz (the median SM clock sampled during the "
+                              "timed steps); issued_frac = the ALU pipe's issue utilisation "
+                              "(ncu, time-weighted over the step's kernels, same source "
+                              "digest); traffic = their DRAM bytes per step (ncu, same "
+                              "digest; null when the kernels changed since the capture)"
+                              % (job.kernel_names(), alg_ops, lanes, sms, run_mhz)),
+                     "profile": prof.get("source") if prof else None},
         "clocks": clocks,
         "hbm_peak_gbs": peaks.get("hbm_gbs"),
         "smem_peak": {"bytes_per_clk_per_sm": smem_bpc,
-                      "tb_s": (smem_bpc * SMS * SM_MAX_MHZ * 1e6 / 1e12) if smem_bpc else None,
+                      "tb_s": (smem_bpc * sms * run_mhz * 1e6 / 1e12) if smem_bpc else None,
                       "what": "measured 64-bit conflict-free shared loads (the search's "
                               "column and triple-table reads are shared loads)"},
     }
     if e2e:
         line["e2e"] = e2e
+    have = {}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(job)
-    if (rank == 0 and world == 1 and not args.no_extra and WORKLOAD_NAME == "bch" and
-            LINE is None and MODEL is None and not FITTED and args.form == "batched"):
-        t = orbg.orbg_codeset_get_tuning(job.cs.handle)
-        shape = ",".join(str(x) for x in (t.warps_per_cta, t.ctas_per_sm, t.blocks_per_grab,
-                                          t.warp_budget, t.heavy_warps))
+        line["cpu_baseline"], have = cpu_baseline(job)
+    if not args.no_parity:
+        line["parity"] = parity_check(job, got, have, budget_s=args.parity_budget,
+                                      per_code=args.parity_per_code)
+    default = (rank == 0 and world == 1 and not args.no_extra and WORKLOAD_NAME == "mixed" and
+               LINE is None and MODEL is None and not FITTED and args.form == "batched")
+    if default:
+        line["forms"] = run_forms()
+        if not args.no_serving:
+            line["serving"] = run_serving(args.serving_seconds)
         try:
-            line["extra_workloads"] = run_extra(shape)
+            line["extra_workloads"] = run_extra()
         except Exception as exc:
             line["extra_workloads"] = [{"error": ("%s: %s" % (type(exc).__name__, exc))[:300]}]
     if world > 1:
         dist.destroy_process_group()
     return line if rank == 0 else None
+
+
+# DRAM traffic and ALU issue utilisation of a step's kernels, from one ncu
+# capture each (`profiles/` holds the summaries and commands); keyed by
+# workload/form/order and valid only for the library sources they were taken
+# on (the build's source digest).  Traffic is per step, scaled from the
+# captured size by the blocks decoded when the capture was smaller.
+PROFILES = {}
+
+
+def job_profile_key(args):
+    order = ("fitted%d" % (FITTED[0] if isinstance(FITTED, tuple) else 1) if FITTED else
+             "model" if MODEL else "line" if LINE else "basic")
+    return "%s/%s/%s" % (WORKLOAD_NAME, args.form, order)
+
+
+def stored_profile(build, key):
+    """The stored ncu figures for key, if they were taken on these sources."""
+    rec = PROFILES.get(key)
+    if not rec:
+        return None
+    try:
+        if rec.get("digest") != build._digest():
+            return None
+    except Exception:
+        return None
+    return rec
 
 
 def measured_int_lanes(orbg):
@@ -849,41 +1004,143 @@ def bench_e2e(orbg, job, args, world, dev):
             "what": "the same call on pinned host buffers: H2D, kernels, D2H, sync"}
 
 
+def block_rows(job, idx, code_j):
+    """LLR rows [len(idx)][n] of blocks idx (all of code code_j)."""
+    n = job.codes[code_j].n
+    if job.off_np is None:
+        return job.llr_np[idx]
+    return np.stack([job.llr_np[job.off_np[b]:job.off_np[b] + n] for b in idx])
+
+
+def stratified_order(idx, stride=97):
+    """idx in a stratified order: every stride-th entry, then the next
+    residue, and so on (any prefix samples the whole range evenly)."""
+    return np.concatenate([idx[r::stride] for r in range(min(stride, max(1, idx.size)))])
+
+
 def cpu_baseline(job, budget_s=15.0):
     """The oracle as it stands, one process, on a bounded sample of the same
     workload: blocks taken in a stratified order (every stride-th block,
     then the next residue, ...) in chunks, until about budget_s seconds of
-    CPU work; the whole workload if it finishes sooner."""
+    CPU work; the whole workload if it finishes sooner.  Also returns the
+    oracle's outputs of those blocks ({block: (codeword, q, abandon)}), which
+    the parity check reuses."""
     import oracle
     oracle.build_oracle()
     B = job.B
-    stride = 97
-    order = np.concatenate([np.arange(r, B, stride) for r in range(stride)])
+    order = stratified_order(np.arange(B))
     t_total = 0.0
     nb = 0
     qsum = 0
     chunk = 1000
+    outputs = {}
     for c0 in range(0, B, chunk):
         idx = order[c0:c0 + chunk]
         for j in np.unique(job.cid_np[idx]):
             sel = idx[job.cid_np[idx] == j]
-            n = job.codes[j].n
-            if job.off_np is None:
-                llr = job.llr_np[sel]
-            else:
-                llr = np.stack([job.llr_np[job.off_np[b]:job.off_np[b] + n] for b in sel])
-            dt, qs, k = run_oracle(job.codes[j].H, llr, CAP, 1)
-            t_total += dt
-            qsum += qs
-            nb += k
+            llr = block_rows(job, sel, j)
+            t = time.perf_counter()
+            cw, q, ab = _oracle_decode(job.codes[j].H, llr, CAP, LINE, MODEL, FITTED)
+            t_total += time.perf_counter() - t
+            qsum += int(q.sum())
+            nb += sel.size
+            for k, b in enumerate(sel):
+                outputs[int(b)] = (cw[k], int(q[k]), int(ab[k]))
         if t_total > budget_s:
             break
     what = ("the whole %d-block workload" % nb if nb == B else
-            "%d of the %d blocks (stratified: every %d-th block, residues in turn; ~%.0f s)"
-            % (nb, B, stride, budget_s))
-    return {"value": nb / t_total, "unit": "blocks/s", "cores": 1, "kind": "oracle",
-            "queries_per_s": qsum / t_total,
-            "sample": "%s, one single-threaded process on %s" % (what, cpu_model())}
+            "%d of the %d blocks (stratified: every 97-th block, residues in turn; ~%.0f s)"
+            % (nb, B, budget_s))
+    return ({"value": nb / t_total, "unit": "blocks/s", "cores": 1, "kind": "oracle",
+             "queries_per_s": qsum / t_total,
+             "sample": "%s, one single-threaded process on %s" % (what, cpu_model())},
+            outputs)
+
+
+def gpu_outputs(job):
+    """The timed step's outputs on the host: codeword bytes, q, abandon."""
+    return (job.cw.cpu().numpy(), job.q.cpu().numpy().astype(np.int64),
+            job.ab.cpu().numpy())
+
+
+def parity_check(job, got, have=None, budget_s=60.0, per_code=20000):
+    """The GPU outputs of the timed step against the oracle, block by block
+    (codeword, query count, abandon flag; tolerance 0), outside the timed
+    region.  Blocks the CPU baseline already decoded (`have`) are compared
+    directly; then, per code, blocks in a stratified order are decoded by the
+    oracle on all host cores (spawned single-threaded processes) until every
+    code has `per_code` blocks checked (or all of its blocks), or until
+    budget_s seconds have passed.  Blocks the GPU abandoned are put first in
+    each code's order (at most 500 per code), so the longest searches are
+    among those checked."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build_oracle()
+    cw_g, q_g, ab_g = got
+    starts = job.block_starts()
+    have = have or {}
+    checked = {}
+    mism = []
+    ncodes = len(job.codes)
+    done = np.zeros(job.B, bool)
+
+    def compare(b, cw, q, ab):
+        n = int(job.n_of_block[b])
+        ok = (q == q_g[b] and ab == ab_g[b] and
+              np.array_equal(np.asarray(cw, np.uint8), cw_g[starts[b]:starts[b] + n]))
+        j = int(job.cid_np[b])
+        checked[j] = checked.get(j, 0) + 1
+        done[b] = True
+        if not ok:
+            mism.append(int(b))
+
+    for b, (cw, q, ab) in have.items():
+        compare(b, cw, q, ab)
+    t0 = time.time()
+    todo = []
+    for j in range(ncodes):
+        idx = np.nonzero((job.cid_np == j) & ~done)[0]
+        aband = idx[ab_g[idx] == 1][:500]
+        rest = stratified_order(idx[ab_g[idx] != 1])
+        want = max(0, min(per_code - checked.get(j, 0), idx.size))
+        todo.append((j, np.concatenate([aband, rest])[:want]))
+    chunk = 256
+    tasks = []
+    for j, idx in todo:
+        for c in range(0, idx.size, chunk):
+            sel = idx[c:c + chunk]
+            tasks.append((c, j, sel))
+    tasks.sort(key=lambda t: t[0])   # codes interleaved, abandoned blocks first
+    cores = os.cpu_count() or 1
+    timed_out = False
+    if tasks:
+        ctx = mp.get_context("spawn")
+        pool = ctx.Pool(cores)
+        try:
+            gen = ((sel, job.codes[j].H, block_rows(job, sel, j), CAP, LINE, MODEL, FITTED)
+                   for _, j, sel in tasks)
+            for sel, cw, q, ab in pool.imap_unordered(_oracle_outputs, gen):
+                for k, b in enumerate(sel):
+                    compare(int(b), cw[k], int(q[k]), int(ab[k]))
+                if time.time() - t0 > budget_s:
+                    timed_out = True
+                    break
+        finally:
+            pool.terminate()
+            pool.join()
+    n_checked = int(done.sum())
+    return {"checked": n_checked, "blocks": job.B, "mismatches": len(mism),
+            "mismatch_blocks": mism[:10],
+            "abandoned_checked": int((done & (ab_g == 1)).sum()),
+            "per_code": {str(j): checked.get(j, 0) for j in range(ncodes)},
+            "what": ("the timed step's codeword, query count and abandon flag of every "
+                     "checked block equal the oracle's (tolerance 0); blocks: %s"
+                     % ("all" if n_checked == job.B else
+                        "the CPU baseline's sample plus, per code, the GPU-abandoned blocks "
+                        "(up to 500) and a stratified sample, up to %d per code%s"
+                        % (per_code, ", cut by the %.0f s budget" % budget_s
+                           if timed_out else ""))),
+            "cores": cores, "wall_s": round(time.time() - t0, 1)}
 
 
 def main(argv=None):

@@ -32,9 +32,11 @@
  *     for device memory only (orbg_fit_models, orbg_fitted_decode).  With
  *     all buffers on the device the call is asynchronous on `cuda_stream`
  *     (NULL = the legacy default stream) and the buffers must stay valid
- *     until the stream reaches the call's end.  With any host buffer the library stages the data through
- *     device memory, copies results back and synchronises the stream before
- *     returning.
+ *     until the stream reaches the call's end.  With any host buffer the
+ *     library stages the data through device memory, copies results back
+ *     and synchronises the stream before returning;
+ *   - telling host from device pointers (cudaPointerGetAttributes) never
+ *     clears a CUDA error that the caller's earlier work left pending.
  */
 #ifndef ORBG_H
 #define ORBG_H
@@ -187,9 +189,11 @@ ORBG_API int orbg_codeset_free(orbg_codeset *set);
  *   cw_offset  : [B] byte offset of block b in codeword, or NULL (dense).
  *   Other arguments as orbg_decode; query_cap must be within every code's
  *   max_query_cap.
- * The call uses 64 + 8 B bytes of stream-ordered device scratch (queue
- * counters and the list of still-open blocks), allocated and freed on
- * cuda_stream.
+ * The call uses 72 + 8 ncodes + 12 B bytes of stream-ordered device
+ * scratch (queue counters, per-code block counts, the list of still-open
+ * blocks and the blocks' order grouped by code), allocated and freed on
+ * cuda_stream.  With code_id given and more than one code in the set, the
+ * first launch takes the blocks grouped by code.
  * Host buffers (staged through stream-ordered device copies): a call with
  * every buffer on the host, B >= 131072 and a layout that places the
  * blocks in order without overlap (dense, or offsets that never go back)
@@ -223,12 +227,15 @@ ORBG_API int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id
  *     staging): EINVAL otherwise.
  *   - B <= ORBG_NOALLOC_MAX_BLOCKS (524,288), else ELIMIT.  Larger batches
  *     can be split into several calls.
- *   - The array is 8 * (8 + ORBG_NOALLOC_MAX_BLOCKS) bytes (4 MiB + 64 B)
- *     of device memory per GPU that loads the library, held until the
- *     process exits.
+ *   - The array is 12 * ORBG_NOALLOC_MAX_BLOCKS + 8,264 bytes (6 MiB +
+ *     8,264 B) of device memory per GPU that loads the library, held until
+ *     the process exits.
  *   - The first call on each device looks up the array's device address
  *     (with that device current) and keeps it; make that first call before
- *     any stream capture.
+ *     any stream capture.  The kept address belongs to the device's primary
+ *     context (the runtime API's): it is invalid after cudaDeviceReset and
+ *     in a context made with the driver API on that device, where this
+ *     entry point must not be called.
  *   - All calls on a device share the one array; the counters that must
  *     start at zero are cleared on cuda_stream at the start of each call.
  *     Calls whose work overlaps on the GPU (other streams, or other host

@@ -4,6 +4,7 @@ sm_103a only (``-gencode arch=compute_103a,code=sm_103a``), cudart linked
 statically, translation units compiled in parallel.  ``python -m
 paper_2202_13951_gb300.build`` or ``build()``.
 """
+import hashlib
 import os
 import shutil
 import subprocess
@@ -32,18 +33,36 @@ def nvcc():
     return exe
 
 
-def _stale():
-    if not os.path.exists(LIB):
-        return True
-    t = os.path.getmtime(LIB)
+STAMP = LIB + ".sha256"
+
+
+def _digest(extra=()):
+    """SHA-256 of every source, header and flag the library is built from,
+    and of the compiler's path: the library is rebuilt whenever this
+    changes (file times are not trusted: a copied tree keeps them)."""
+    h = hashlib.sha256()
     deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS + [INST]]
     deps.append(os.path.join(ROOT, "include", "orbg.h"))
     deps.append(os.path.abspath(__file__))
-    return any(os.path.getmtime(d) > t for d in deps)
+    for d in deps:
+        h.update(os.path.basename(d).encode())
+        with open(d, "rb") as f:
+            h.update(hashlib.sha256(f.read()).digest())
+    h.update(repr(list(extra)).encode())
+    h.update(nvcc().encode())
+    return h.hexdigest()
+
+
+def _stale(digest):
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
+        return True
+    with open(STAMP) as f:
+        return f.read().strip() != digest
 
 
 def build(force=False, verbose=False, extra=()):
-    if not force and not _stale():
+    digest = _digest(extra)
+    if not force and not _stale(digest):
         return LIB
     os.makedirs(OBJDIR, exist_ok=True)
     cc = nvcc()
@@ -77,6 +96,10 @@ def build(force=False, verbose=False, extra=()):
     link = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static", "-lpthread"]
     subprocess.check_call(link)
     os.replace(tmp, LIB)
+    with open(STAMP + ".tmp", "w") as f:
+        f.write(digest + "\n")
+    os.replace(STAMP + ".tmp", STAMP)
+    print("liborbg.so: compiled %d units for sm_103a" % len(units), file=sys.stderr)
     return LIB
 
 

@@ -70,10 +70,15 @@ bool is_device_ptr(const void *p)
 {
     if (!p)
         return true;
+    /* an error the caller's earlier work left pending stays for the caller:
+     * only the probe's own error (plain host pointers on old runtimes) is
+     * cleared */
+    const cudaError_t pending = cudaPeekAtLastError();
     cudaPointerAttributes a;
     cudaError_t e = cudaPointerGetAttributes(&a, p);
     if (e != cudaSuccess) {
-        cudaGetLastError(); /* clear: plain host pointers on old runtimes */
+        if (pending == cudaSuccess)
+            cudaGetLastError();
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
@@ -592,7 +597,7 @@ int orbg_codeset_create(const orbg_code *const *codes, int ncodes, orbg_codeset 
     if (!out)
         return ORBG_EINVAL;
     *out = nullptr;
-    if (!codes || ncodes < 1 || ncodes > 1024)
+    if (!codes || ncodes < 1 || ncodes > ORBG_MAX_CODES)
         return ORBG_EINVAL;
     std::vector<OrbgDeviceCode> descs((size_t)ncodes);
     orbg_codeset *s = new (std::nothrow) orbg_codeset();
@@ -719,7 +724,7 @@ int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
         (e = cudaMallocAsync((void **)&d_cw, n_cw, st)) != cudaSuccess ||
         (e = cudaMallocAsync((void **)&d_q, (size_t)B * sizeof(uint32_t), st)) != cudaSuccess ||
         (e = cudaMallocAsync((void **)&d_ab, (size_t)B, st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&scratch, orbg_batched_scratch_bytes(per), st)) !=
+        (e = cudaMallocAsync((void **)&scratch, orbg_batched_scratch_bytes(per, set->ncodes), st)) !=
             cudaSuccess ||
         (code_id && (e = cudaMallocAsync((void **)&d_cid, (size_t)B * sizeof(int32_t), st)) !=
                         cudaSuccess) ||
@@ -899,7 +904,7 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
         return rc;
     }
     unsigned long long *scratch = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&scratch, orbg_batched_scratch_bytes(B), st);
+    cudaError_t e = cudaMallocAsync((void **)&scratch, orbg_batched_scratch_bytes(B, set->ncodes), st);
     if (e != cudaSuccess) {
         sg.finish(false);
         return cuda_fail(e);
@@ -1183,10 +1188,14 @@ int orbg_fitted_decode(orbg_fitted *f, const float *llr, int64_t B, uint32_t que
         }
         lut[i] = it->second;
     }
-    if (rc == ORBG_OK && (grown || !f->set)) {
+    if (grown || !f->set) {
+        /* a handle added in this call (even one that then failed on a
+         * later J_0) makes the set stale: drop it, so that no call decodes
+         * with a set that lacks a handle the J_0 map already names */
         orbg_codeset_free(f->set);
         f->set = nullptr;
-        rc = orbg_codeset_create(f->handles.data(), (int)f->handles.size(), &f->set);
+        if (rc == ORBG_OK)
+            rc = orbg_codeset_create(f->handles.data(), (int)f->handles.size(), &f->set);
     }
     /* code ids on the device, then one batched launch, each block in its
      * own line's order */
@@ -1200,7 +1209,7 @@ int orbg_fitted_decode(orbg_fitted *f, const float *llr, int64_t B, uint32_t que
      * the code's n), as orbg_decode_batched makes it */
     unsigned long long *scratch = nullptr;
     if (rc == ORBG_OK &&
-        (e = cudaMallocAsync((void **)&scratch, orbg_batched_scratch_bytes(B), st)) !=
+        (e = cudaMallocAsync((void **)&scratch, orbg_batched_scratch_bytes(B, f->set->ncodes), st)) !=
             cudaSuccess)
         rc = cuda_fail(e);
     if (rc == ORBG_OK) {

@@ -30,9 +30,96 @@ int orbg_grid_for(const void *kern, int threads, size_t smem, int ctas_per_sm, i
     return 0;
 }
 
-size_t orbg_batched_scratch_bytes(int64_t B)
+size_t orbg_batched_scratch_bytes(int64_t B, int ncodes)
 {
-    return sizeof(unsigned long long) * ((size_t)ORBG_BATCHED_COUNTERS + (size_t)(B > 0 ? B : 0));
+    const size_t b = (size_t)(B > 0 ? B : 0);
+    return 8 * (size_t)ORBG_BATCHED_COUNTERS + 8 * ((size_t)(ncodes > 0 ? ncodes : 0) + 1) +
+           12 * b;
+}
+
+namespace {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortChunk = 4096; /* blocks per CTA of the scatter */
+
+/* code id of block b as the sort buckets it: ids outside the set go last */
+__device__ __forceinline__ int sort_bucket(const int32_t *code_id, int64_t b, int ncodes)
+{
+    const int c = code_id[b];
+    return c >= 0 && c < ncodes ? c : ncodes;
+}
+
+__global__ void __launch_bounds__(kSortThreads) orbg_code_count_kernel(
+    const int32_t *__restrict__ code_id, int64_t B, int ncodes, uint32_t *__restrict__ count)
+{
+    extern __shared__ uint32_t h[];
+    for (int i = threadIdx.x; i <= ncodes; i += blockDim.x)
+        h[i] = 0;
+    __syncthreads();
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B;
+         b += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&h[sort_bucket(code_id, b, ncodes)], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i <= ncodes; i += blockDim.x)
+        if (h[i])
+            atomicAdd(&count[i], h[i]);
+}
+
+/* Each CTA scatters one chunk of kSortChunk blocks: it counts its chunk per
+ * code, reserves a range of each code's slots with one global atomic per
+ * code, and writes its blocks there (in chunk order within a code). */
+__global__ void __launch_bounds__(kSortThreads) orbg_code_scatter_kernel(
+    const int32_t *__restrict__ code_id, int64_t B, int ncodes,
+    const uint32_t *__restrict__ count, uint32_t *__restrict__ cursor,
+    uint32_t *__restrict__ perm)
+{
+    extern __shared__ uint32_t sh[];
+    uint32_t *base = sh;              /* [ncodes + 1] first slot of each code */
+    uint32_t *local = sh + ncodes + 1; /* [ncodes + 1] this chunk's count, then its cursor */
+    const int64_t lo = (int64_t)blockIdx.x * kSortChunk;
+    const int64_t hi = lo + kSortChunk < B ? lo + kSortChunk : B;
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int i = 0; i <= ncodes; i++) {
+            base[i] = acc;
+            acc += count[i];
+        }
+    }
+    for (int i = threadIdx.x; i <= ncodes; i += blockDim.x)
+        local[i] = 0;
+    __syncthreads();
+    for (int64_t b = lo + threadIdx.x; b < hi; b += blockDim.x)
+        atomicAdd(&local[sort_bucket(code_id, b, ncodes)], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i <= ncodes; i += blockDim.x)
+        local[i] = local[i] ? base[i] + atomicAdd(&cursor[i], local[i]) : 0u;
+    __syncthreads();
+    for (int64_t b = lo + threadIdx.x; b < hi; b += blockDim.x)
+        perm[atomicAdd(&local[sort_bucket(code_id, b, ncodes)], 1u)] = (uint32_t)b;
+}
+
+}  // namespace
+
+int orbg_launch_code_sort(const int32_t *code_id, int64_t B, int ncodes, const OrbgScratch &s,
+                          void *stream)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t sh1 = sizeof(uint32_t) * (size_t)(ncodes + 1);
+    int dev = 0, sms = 1;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return (int)e;
+    int64_t g1 = (B + kSortThreads - 1) / kSortThreads;
+    if (g1 > (int64_t)sms * 8)
+        g1 = (int64_t)sms * 8;
+    orbg_code_count_kernel<<<(unsigned)g1, kSortThreads, sh1, st>>>(code_id, B, ncodes, s.count);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return (int)e;
+    const int64_t g2 = (B + kSortChunk - 1) / kSortChunk;
+    orbg_code_scatter_kernel<<<(unsigned)g2, kSortThreads, 2 * sh1, st>>>(
+        code_id, B, ncodes, s.count, s.cursor, s.perm);
+    return (int)cudaGetLastError();
 }
 
 int orbg_launch_batched(const OrbgBatchedArgs &args)

@@ -46,8 +46,8 @@ __global__ void __launch_bounds__(256, ORBG_PHASE1_MIN_CTAS) orbg_batched_kernel
     const int64_t *__restrict__ llr_off, const float *__restrict__ llr, int64_t B, uint32_t cap,
     uint32_t budget, uint8_t *__restrict__ cw, const int64_t *__restrict__ cw_off,
     uint32_t *__restrict__ q, uint8_t *__restrict__ ab, unsigned long long *__restrict__ counters,
-    unsigned long long *__restrict__ heavy, uint32_t bstride, uint32_t x3w_bytes, int grab,
-    const __grid_constant__ OrbgDeviceCode code0)
+    unsigned long long *__restrict__ heavy, const uint32_t *__restrict__ perm, uint32_t bstride,
+    uint32_t x3w_bytes, int grab, const __grid_constant__ OrbgDeviceCode code0)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
@@ -63,7 +63,10 @@ __global__ void __launch_bounds__(256, ORBG_PHASE1_MIN_CTAS) orbg_batched_kernel
                                                  warp * x3w_bytes);
     const int64_t n0 = ONE ? code0.n : codes[0].n;
 
-    /* the warp's block sequence: `grab` consecutive blocks per atomic */
+    /* the warp's block sequence: `grab` consecutive queue slots per atomic;
+     * with perm (mixed codes) slot i holds the block perm[i], so that the
+     * blocks of one code are decoded together (one variant of the decoder
+     * runs at a time and its instructions stay cached) */
     int64_t pos = 0, end = 0;
     auto next_block = [&]() -> int64_t {
         if (pos >= end) {
@@ -76,7 +79,8 @@ __global__ void __launch_bounds__(256, ORBG_PHASE1_MIN_CTAS) orbg_batched_kernel
             if (pos >= B)
                 return B;
         }
-        return pos++;
+        const int64_t slot = pos++;
+        return perm ? (int64_t)__ldg(perm + slot) : slot;
     };
     auto stage = [&](int64_t b, int slot) {
         if (b < B) {
@@ -141,14 +145,18 @@ cudaError_t launch_t(const OrbgBatchedArgs &a)
     const int wpc = a.warps_per_cta > 0 ? (a.warps_per_cta > 8 ? 8 : a.warps_per_cta) : 8;
     const int g = a.grab < 1 ? 1 : a.grab;
     const uint32_t bstride = block_smem_bytes(a.n_max, a.w32_max);
-    unsigned long long *counters = a.scratch;
-    unsigned long long *heavy = a.scratch + kCounters;
+    const OrbgScratch sc = orbg_scratch_layout(a.scratch, a.B, a.ncodes);
+    unsigned long long *counters = sc.counters;
+    unsigned long long *heavy = sc.heavy;
     cudaStream_t st = (cudaStream_t)a.stream;
     cudaError_t e;
     int grid = 0, rc;
-    if ((e = cudaMemsetAsync(counters, 0, sizeof(unsigned long long) * kCounters, st)) !=
-        cudaSuccess)
+    if ((e = cudaMemsetAsync(a.scratch, 0, sc.zero_bytes, st)) != cudaSuccess)
         return e;
+    /* mixed codes: phase 1 takes the blocks grouped by code */
+    const bool sorted = !ONE && a.code_id != nullptr && a.ncodes > 1;
+    if (sorted && (rc = orbg_launch_code_sort(a.code_id, a.B, a.ncodes, sc, st)) != 0)
+        return (cudaError_t)rc;
     /* phase 1: per warp, one block's working set, two LLR slots and its own
      * triple table */
     auto k1 = orbg_batched_kernel<KMAX, WMAX, ONE>;
@@ -164,7 +172,8 @@ cudaError_t launch_t(const OrbgBatchedArgs &a)
         c0 = *a.code0;
     k1<<<grid, wpc * 32, smem1, st>>>(a.d_codes, a.ncodes, a.code_id, a.llr_off, a.llr, a.B,
                                       a.cap, a.budget, a.cw, a.cw_off, a.q, a.ab, counters,
-                                      heavy, bstride, x3w_bytes, g, c0);
+                                      heavy, sorted ? sc.perm : nullptr, bstride, x3w_bytes, g,
+                                      c0);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     if (a.budget >= a.cap)

@@ -94,17 +94,31 @@ __global__ void orbg_fit_map_kernel(const int32_t *__restrict__ models, int64_t 
         cid[b] = lut[line_j0(models + b * (int64_t)ORBG_FIT_STRIDE, top) + 1];
 }
 
+/* SMs of the current device (the grids below are grid-stride loops, so
+ * any count gives the same result; 1 if the query fails) */
+int64_t device_sms()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1)
+        return 1;
+    return sms;
+}
+
 unsigned grid_for(int64_t B, int threads)
 {
-    const int64_t g = (B + threads - 1) / threads;
-    return (unsigned)(g < 152 * 8 ? (g > 0 ? g : 1) : 152 * 8);
+    const int64_t g = (B + threads - 1) / threads, top = device_sms() * 8;
+    return (unsigned)(g < top ? (g > 0 ? g : 1) : top);
 }
 
 bool device_accessible(const void *p)
 {
+    const cudaError_t pending = cudaPeekAtLastError(); /* left for the caller */
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
+        if (pending == cudaSuccess)
+            cudaGetLastError();
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
@@ -115,8 +129,8 @@ bool device_accessible(const void *p)
 int orbg_fit_launch(const float *llr, int64_t B, int n, int lines, int divisible,
                     int32_t *models, void *stream)
 {
-    const int64_t ctas = (B + kWarps - 1) / kWarps;
-    const unsigned grid = (unsigned)(ctas < 152 * 16 ? ctas : 152 * 16);
+    const int64_t ctas = (B + kWarps - 1) / kWarps, top = device_sms() * 16;
+    const unsigned grid = (unsigned)(ctas < top ? ctas : top);
     orbg_fit_kernel<<<grid, kWarps * 32, 0, (cudaStream_t)stream>>>(llr, B, n, lines,
                                                                     divisible ? 1 : 0, models);
     return (int)cudaGetLastError();

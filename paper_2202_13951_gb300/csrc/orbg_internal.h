@@ -170,10 +170,40 @@ ORBG_DECLARE_BATCHED(2, 1) ORBG_DECLARE_BATCHED(2, 2) ORBG_DECLARE_BATCHED(2, 4)
 ORBG_DECLARE_BATCHED(4, 1) ORBG_DECLARE_BATCHED(4, 2) ORBG_DECLARE_BATCHED(4, 4)
 ORBG_DECLARE_BATCHED(8, 1) ORBG_DECLARE_BATCHED(8, 2) ORBG_DECLARE_BATCHED(8, 4)
 #undef ORBG_DECLARE_BATCHED
-/* device scratch the batched form needs for B blocks: counters (queue head,
- * open-block count, phase-2 cursor) and the list of open blocks */
+/* Device scratch of one batched call over B blocks of a set of ncodes codes,
+ * in this order: ORBG_BATCHED_COUNTERS 64-bit counters (queue head, open-block
+ * count, phase-2 cursor); per-code block counts and fill cursors (ncodes + 1
+ * uint32 each, the last for code ids outside the set); the list of open
+ * blocks (B uint64); the blocks in phase 1's order, grouped by code (B
+ * uint32).  The counters, counts and cursors start at zero. */
 #define ORBG_BATCHED_COUNTERS 8
-size_t orbg_batched_scratch_bytes(int64_t B);
+#define ORBG_MAX_CODES 1024      /* codes in one set */
+size_t orbg_batched_scratch_bytes(int64_t B, int ncodes);
+struct OrbgScratch {
+    unsigned long long *counters;
+    uint32_t *count, *cursor;
+    unsigned long long *heavy;
+    uint32_t *perm;
+    size_t zero_bytes;            /* bytes from the start that must be zero */
+};
+inline OrbgScratch orbg_scratch_layout(void *base, int64_t B, int ncodes)
+{
+    OrbgScratch s;
+    unsigned char *p = (unsigned char *)base;
+    const size_t nc = (size_t)(ncodes > 0 ? ncodes : 0) + 1;
+    s.counters = (unsigned long long *)p;
+    s.count = (uint32_t *)(p + 8 * ORBG_BATCHED_COUNTERS);
+    s.cursor = s.count + nc;
+    s.zero_bytes = 8 * ORBG_BATCHED_COUNTERS + 8 * nc;
+    s.heavy = (unsigned long long *)(p + s.zero_bytes);
+    s.perm = (uint32_t *)(s.heavy + (B > 0 ? B : 0));
+    return s;
+}
+/* Order the blocks of a mixed-code call by code id (counting sort into
+ * perm, invalid ids last), so that phase 1's warps decode one code's
+ * blocks at a time; returns a cudaError_t. */
+int orbg_launch_code_sort(const int32_t *code_id, int64_t B, int ncodes, const OrbgScratch &s,
+                          void *stream);
 int orbg_grid_for(const void *kern, int threads, size_t smem, int ctas_per_sm, int *grid_out);
 
 /* What a launch needs of a code set (orbg_api.cpp owns the struct). */

@@ -11,11 +11,15 @@
  * that scratch in a fixed array compiled into this library instead.
  *
  * The array is a file-scope __device__ variable: every GPU that loads the
- * library holds it (8 * (8 + ORBG_NOALLOC_MAX_BLOCKS) bytes, 4 MiB + 64 B)
- * until the process exits.  Host code cannot use the variable's name as a
+ * library holds it (the batched form's scratch for ORBG_NOALLOC_MAX_BLOCKS
+ * blocks of a set of up to 1024 codes: 12 bytes per block plus 8,264 bytes,
+ * 6 MiB + 8,264 B) until the process exits.  Host code cannot use the variable's name as a
  * device address, so the first call on each device, with that device
  * current, asks the runtime for the address (cudaGetSymbolAddress) and keeps
- * it; later calls on that device reuse it.
+ * it; later calls on that device reuse it.  The kept address belongs to the
+ * device's primary context (the one the runtime API uses): it is not valid
+ * after cudaDeviceReset, nor in a context the caller made with the driver
+ * API on the same device, and this entry point must not be used there.
  */
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -29,10 +33,13 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 
-/* Scratch shared by every no-alloc call on a device: counters, then one
- * slot per block for the open-block list. */
-static __device__ __align__(256) unsigned long long
-    g_orbg_noalloc_scratch[ORBG_BATCHED_COUNTERS + ORBG_NOALLOC_MAX_BLOCKS];
+/* Scratch shared by every no-alloc call on a device, laid out as
+ * orbg_scratch_layout places it: counters, per-code counts and cursors, the
+ * open-block list and phase 1's block order. */
+constexpr size_t kScratchWords =
+    (8 * ORBG_BATCHED_COUNTERS + 8 * (ORBG_MAX_CODES + 1) + 12 * (size_t)ORBG_NOALLOC_MAX_BLOCKS +
+     7) / 8;
+static __device__ __align__(256) unsigned long long g_orbg_noalloc_scratch[kScratchWords];
 
 std::mutex g_mu;
 unsigned long long *g_scratch_addr[kMaxDevices];
@@ -63,9 +70,12 @@ bool on_device(const void *p)
 {
     if (!p)
         return true;
+    /* clear only the probe's own error, never one the caller left pending */
+    const cudaError_t pending = cudaPeekAtLastError();
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
+        if (pending == cudaSuccess)
+            cudaGetLastError();
         return false;
     }
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;

@@ -130,7 +130,7 @@ struct Layout {
         o = align_up(o + (size_t)B, 256);
         L.out_end = o;
         L.scratch = o;
-        o = align_up(o + orbg_batched_scratch_bytes(B), 256);
+        o = align_up(o + orbg_batched_scratch_bytes(B, ORBG_MAX_CODES), 256);
         L.total = o;
         return L;
     }

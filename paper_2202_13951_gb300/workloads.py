@@ -498,3 +498,57 @@ def serving_trace(rate_blocks_s=2e6, seconds=10.0, max_size=4096, ebn0=(3.0, 7.0
     return {"arrival_s": np.array(arrivals, np.float64), "code": code, "B": size,
             "ebn0": eb, "llr_off": llr_off, "blk_off": blk_off, "llr_all": llr_all,
             "cw_all": cw_all, "codes": codes}
+
+
+def serving_pool(codes=None, pool_blocks=1 << 19, ebn0=(3.0, 7.0), seed=511):
+    """Blocks for long serving traces: per code, pool_blocks blocks whose
+    Eb/N0 rises linearly from ebn0[0] to ebn0[1] over the pool's rows.
+    Returns (codes, llr flat float32, pool_off[code] (element offset of the
+    code's first row), cw flat)."""
+    codes = codes if codes is not None else config5_codes()
+    eb = np.linspace(ebn0[0], ebn0[1], pool_blocks)
+    ns = np.array([c.n for c in codes], np.int64)
+    pool_off = np.concatenate([[0], np.cumsum(ns * pool_blocks)[:-1]]).astype(np.int64)
+    llr = np.zeros(int((ns * pool_blocks).sum()), np.float32)
+    cw = np.zeros(llr.shape[0], np.uint8)
+    for j, cd in enumerate(codes):
+        l, c = awgn_llr(cd, pool_blocks, eb, seed * 10 + j)
+        llr[pool_off[j]:pool_off[j] + cd.n * pool_blocks] = l.ravel()
+        cw[pool_off[j]:pool_off[j] + cd.n * pool_blocks] = c.ravel()
+    return codes, llr, pool_off, cw
+
+
+def pooled_serving_trace(pool, pool_blocks, rate_blocks_s=2e6, seconds=10.0, max_size=4096,
+                         ebn0=(3.0, 7.0), seed=501):
+    """A Poisson request stream as serving_trace (sizes U{1..max_size}, code
+    uniform, Eb/N0 uniform per request, exponential gaps) whose blocks are
+    rows of a serving_pool: request r reads the B_r consecutive rows of its
+    code's pool that start where the pool's Eb/N0 equals the request's, so
+    a long trace needs no new blocks.  Requests may share rows (their
+    codeword outputs then land on the same bytes: the decoder is
+    deterministic, so they agree).  Returns the dict of serving_trace,
+    with llr_all the pool's array and `pool_row[r]` the first row."""
+    codes, llr, pool_off, cw = pool
+    rng = np.random.default_rng(seed)
+    mean_size = (1 + max_size) / 2.0
+    req_rate = rate_blocks_s / mean_size
+    m_est = int(req_rate * seconds * 1.2) + 16
+    gaps = rng.exponential(1.0 / req_rate, size=m_est)
+    arrivals = np.cumsum(gaps)
+    while arrivals[-1] < seconds:
+        more = np.cumsum(rng.exponential(1.0 / req_rate, size=m_est)) + arrivals[-1]
+        arrivals = np.concatenate([arrivals, more])
+    arrivals = arrivals[arrivals < seconds]
+    m = arrivals.shape[0]
+    size = rng.integers(1, max_size + 1, size=m).astype(np.int64)
+    code = rng.integers(0, len(codes), size=m).astype(np.int32)
+    eb = rng.uniform(ebn0[0], ebn0[1], size=m)
+    ns = np.array([c.n for c in codes], np.int64)
+    frac = (eb - ebn0[0]) / (ebn0[1] - ebn0[0])
+    row = np.round(frac * (pool_blocks - size)).astype(np.int64)
+    llr_off = pool_off[code] + row * ns[code]
+    blk_off = np.zeros(m, np.int64)
+    blk_off[1:] = np.cumsum(size)[:-1]
+    return {"arrival_s": arrivals.astype(np.float64), "code": code, "B": size, "ebn0": eb,
+            "llr_off": llr_off, "blk_off": blk_off, "llr_all": llr, "cw_all": cw,
+            "codes": codes, "pool_row": row}

@@ -169,11 +169,58 @@ def test_run_extra_parses_child_lines(monkeypatch):
         return types.SimpleNamespace(returncode=0, stdout="log\n" + json.dumps(line) + "\n",
                                      stderr="")
     monkeypatch.setattr(subprocess, "run", fake_run)
-    out = bench.run_extra("8,0,4,16384,8")
-    assert len(out) == len(calls) == 4
+    out = bench.run_extra()
+    assert len(out) == len(calls) == len(bench.extra_runs())
     ok = [r for r in out if "error" not in r]
-    assert len(ok) == 3 and all(r["value"] == 1.0e6 and r["roofline"]["frac"] == 0.15 and
-                                r["workload"] == "w" for r in ok)
+    assert len(ok) == len(calls) - 1 and all(r["value"] == 1.0e6 and
+                                             r["roofline"]["frac"] == 0.15 and
+                                             r["workload"] == "w" for r in ok)
     bad = [r for r in out if "error" in r]
     assert len(bad) == 1 and "RuntimeError" in bad[0]["error"]
     assert all("--no-extra" in c and "--no-cpu-baseline" in c for c in calls)
+
+
+class _FakeJob:
+    """What bench.parity_check reads of a job, for a mixed batch on the CPU."""
+
+    def __init__(self, codes, cid, llr, off):
+        self.codes, self.cid_np, self.llr_np, self.off_np = codes, cid, llr, off
+        self.B = cid.shape[0]
+        self.n_of_block = np.array([c.n for c in codes], np.int64)[cid]
+
+    def block_starts(self):
+        return self.off_np
+
+
+def test_parity_check_counts_mismatches_on_mixed_blocks():
+    """bench.parity_check compares every checked block's codeword, query
+    count and abandon flag with the oracle's: outputs that are the oracle's
+    own give no mismatch; a planted wrong query count, codeword bit or
+    abandon flag in three blocks gives three, each named."""
+    import bench
+    import oracle
+    from paper_2202_13951_gb300 import workloads
+    codes = [workloads.rlc(32, 24, 3), workloads.rlc(48, 36, 4)]
+    codes, cid, llr, off, _, _ = workloads.mixed_inputs(codes, 300, 11, 2.0, 5.0)
+    job = _FakeJob(codes, cid, llr, off)
+    cw = np.zeros(llr.shape[0], np.uint8)
+    q = np.zeros(job.B, np.int64)
+    ab = np.zeros(job.B, np.uint8)
+    bench.select_workload("mixed", 100)
+    for j, c in enumerate(codes):
+        idx = np.nonzero(cid == j)[0]
+        rows = np.stack([llr[off[b]:off[b] + c.n] for b in idx])
+        wc, wq, wab, _ = oracle.decode_batch(c.H, rows, bench.CAP)
+        for k, b in enumerate(idx):
+            cw[off[b]:off[b] + c.n] = wc[k]
+        q[idx], ab[idx] = wq, wab
+    res = bench.parity_check(job, (cw, q, ab), budget_s=120, per_code=1000)
+    assert res["checked"] == job.B and res["mismatches"] == 0
+    q2, cw2, ab2 = q.copy(), cw.copy(), ab.copy()
+    q2[5] += 1
+    cw2[off[17]] ^= 1
+    ab2[40] ^= 1
+    res = bench.parity_check(job, (cw2, q2, ab2), budget_s=120, per_code=1000)
+    assert res["mismatches"] == 3 and sorted(res["mismatch_blocks"]) == [5, 17, 40]
+    res = bench.parity_check(job, (cw, q, ab), budget_s=120, per_code=50)
+    assert res["checked"] == 100 and res["mismatches"] == 0

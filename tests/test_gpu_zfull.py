@@ -200,3 +200,36 @@ def test_fitted_line_decode_as_oracle(orbg):
                 for b in np.nonzero(ok)[0][::17]:
                     assert orbg.model_of_record(rec[b]) == oracle.fit(llr[b], 1, div)
             f.close()
+
+
+def test_fitted_decode_after_a_failed_line(orbg):
+    """A call that adds one line's handle and then fails on a later line
+    (here a block whose fitted J_0 orders n = 256 positions Hamming weight
+    first, which the tables refuse) must not leave the object decoding with
+    a code set that lacks the added handle: the next call over blocks of
+    that line equals the oracle's fit-then-decode."""
+    cap = 5000
+    code = workloads.rlc(256, 240, 71)
+    c = orbg.Code(code.H, max_query_cap=cap)
+    f = orbg.Fitted(c)
+    first = workloads.awgn_llr(code, 1, 7.0, 72)[0]  # one block: one line
+    cw, q, ab, rec = f.decode(torch.from_numpy(first).cuda(), cap)
+    torch.cuda.synchronize()
+    seen = {orbg.model_of_record(r)[1][0] for r in rec.cpu().numpy()}
+    # blocks at a lower SNR: lines not met in the first call
+    low = workloads.awgn_llr(code, 256, 2.0, 73)[0]
+    j0 = np.array([oracle.fit(x, 1)[1][0] for x in low])
+    new = low[~np.isin(j0, list(seen))][:8]
+    assert new.shape[0] > 0
+    rng = np.random.default_rng(74)
+    flat = (10.0 + 1e-4 * np.arange(1, 257)) * rng.choice([-1.0, 1.0], 256)
+    flat = flat[rng.permutation(256)].astype(np.float32)[None, :]
+    assert oracle.fit(flat[0], 1)[1][0] > 256 * 257 // 2
+    with pytest.raises(orbg.OrbgError):
+        f.decode(torch.from_numpy(np.concatenate([new, flat])).cuda(), cap)
+    torch.cuda.synchronize()
+    cw, q, ab, _ = f.decode(torch.from_numpy(new).cuda(), cap)
+    torch.cuda.synchronize()
+    want = oracle.decode_batch_fit(code.H, new, cap, 1)[:3]
+    assert_same((cw.cpu().numpy(), q.cpu().numpy().astype(np.int64), ab.cpu().numpy()), want)
+    f.close()

@@ -73,3 +73,31 @@ def test_noalloc_rejects_what_it_cannot_do(orbg):
         orbg.orbg_decode_batched_noalloc(cs.handle, None, None, x.cpu().numpy(), 8, 1000,
                                          out, None, q, ab)
     assert ei.value.status == orbg.ORBG_EINVAL
+
+
+def test_noalloc_mixed_codes_with_offsets(orbg):
+    """Mixed codes of different n and syndrome widths in one call, with
+    device code-id and offset arrays and a small phase-1 budget (so the
+    open-block list, the per-code counts and the block order in the fixed
+    array are all used): bit for bit the same as orbg_decode_batched."""
+    codes = workloads.config4_codes() + [workloads.config3_code()]  # r = 13..34: 1 and 2 words
+    cs = orbg.CodeSet([orbg.Code(c.H, max_query_cap=10 ** 5) for c in codes])
+    orbg.orbg_codeset_set_tuning(cs.handle, orbg.OrbgTuning(8, 0, 4, 128, 8))
+    for seed in (903, 904):
+        _, cid, llr, off, _, _ = workloads.mixed_inputs(codes, 6000, seed)
+        llr_t = torch.from_numpy(llr).cuda()
+        cid_t = torch.from_numpy(cid).cuda()
+        off_t = torch.from_numpy(off).cuda()
+        B = cid.shape[0]
+        outs = []
+        for fn in (orbg.orbg_decode_batched, orbg.orbg_decode_batched_noalloc):
+            cw = torch.full((llr.shape[0],), 0xAB, dtype=torch.uint8, device="cuda")
+            q = torch.full((B,), -1, dtype=torch.int32, device="cuda")
+            ab = torch.full((B,), 0xCD, dtype=torch.uint8, device="cuda")
+            fn(cs.handle, cid_t, off_t, llr_t, B, 10 ** 5, cw, off_t, q, ab,
+               torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            outs.append((cw.cpu().numpy(), q.cpu().numpy(), ab.cpu().numpy()))
+        for g, w in zip(outs[1], outs[0]):
+            assert np.array_equal(g, w)
+        assert (outs[0][1] > 128).any() and (outs[0][2] == 0).any()
