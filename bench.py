@@ -55,6 +55,9 @@ WORKLOADS = {
     "mixed": ("mixed rlc(64,51),(128,112),(256,240),(256,232), code uniform per block, "
               "%d blocks at Eb/N0 U[4,7] dB, query cap 1e6, one launch, autotuned",
               None, (), (401,)),
+    "capolar256": ("ca-polar(256,234[K=245]) 4x%d blocks at Eb/N0 5,5.5,6,6.5 dB, "
+                   "query cap 5e6", "capolar256_code", (5.0, 5.5, 6.0, 6.5),
+                   (701, 702, 703, 704)),
     "paper256": ("paper-shaped [256,234] family: ca-polar(256,234[K=245]), crc(256,234), "
                  "rlc(256,234), bch(255,231), code uniform per block, %d blocks at Eb/N0 "
                  "U[4,7] dB, query cap 5e6, one launch, autotuned",
@@ -68,7 +71,7 @@ SEEDS = (201, 202, 203, 204)
 B_PER_POINT = 100_000
 WORKLOAD = WORKLOADS["bch"][0] % B_PER_POINT
 CAP = 1_000_000
-CAPS = {"rlc64": 100_000, "paper256": 5_000_000}
+CAPS = {"rlc64": 100_000, "paper256": 5_000_000, "capolar256": 5_000_000}
 
 
 # ------------------------------------------------------------------ utils
@@ -89,6 +92,12 @@ def parse_args(argv=None):
     p.add_argument("--fitted", action="store_true",
                    help="decode one-line full ORBGRAND with a line fitted per block "
                         "(Sec. III-E; orbg_fitted_decode) instead of basic")
+    p.add_argument("--fitted-lines", type=int, default=0,
+                   help="decode full ORBGRAND with a model of this many lines fitted per "
+                        "block, each block searched in its own order (Sec. III-E, III-D; "
+                        "orbg_decode_fitted)")
+    p.add_argument("--divisible", action="store_true",
+                   help="with --fitted-lines: Eq. quant's J-divisible quantisation")
     p.add_argument("--no-extra", action="store_true",
                    help="skip the secondary measurements (full ORBGRAND orders, the "
                         "paper-shaped workload) that follow the headline one")
@@ -111,6 +120,9 @@ def parse_args(argv=None):
     p.add_argument("--serving-seconds", type=float, default=10.0,
                    help="seconds of Poisson arrivals in the serving measurement")
     p.add_argument("--blocks-per-point", type=int, default=B_PER_POINT)
+    p.add_argument("--points", default="",
+                   help="Eb/N0 points (dB, comma-separated) in place of a single-code "
+                        "workload's own; seeds follow the workload's first seed")
     p.add_argument("--form", choices=("batched", "plain"), default="batched",
                    help="batched: orbg_decode_batched (two persistent launches); plain: "
                         "orbg_decode (one warp per block, one launch)")
@@ -121,12 +133,18 @@ def parse_args(argv=None):
                         "for the batched launch (orbg_tuning)")
     args = p.parse_args(argv)
     select_workload(args.workload, args.blocks_per_point)
+    if args.points:
+        set_points(tuple(float(x) for x in args.points.split(",")))
     global LINE, MODEL, FITTED, WORKLOAD
-    if sum(map(bool, (args.line, args.model, args.fitted))) > 1:
-        raise SystemExit("give one of --line, --model, --fitted")
+    if sum(map(bool, (args.line, args.model, args.fitted, args.fitted_lines))) > 1:
+        raise SystemExit("give one of --line, --model, --fitted, --fitted-lines")
     FITTED = bool(args.fitted)
     if FITTED:
         WORKLOAD += ", one-line full ORBGRAND with a line fitted per block"
+    if args.fitted_lines:
+        FITTED = (int(args.fitted_lines), bool(args.divisible))
+        WORKLOAD += (", full ORBGRAND with a %d-line model fitted per block%s"
+                     % (FITTED[0], " (J divisible by beta)" if FITTED[1] else ""))
     if args.line:
         LINE = tuple(int(x) for x in args.line.split(","))
         WORKLOAD += ", one-line full ORBGRAND J0=%d beta=%d" % LINE
@@ -154,10 +172,28 @@ def select_workload(name, b_per_point):
     WORKLOAD = desc % (b_per_point * MIXED[name][1] if name in MIXED else b_per_point)
 
 
+def set_points(points):
+    """Another set of Eb/N0 points for a single-code workload."""
+    global POINTS, SEEDS, WORKLOAD
+    if WORKLOAD_NAME in MIXED:
+        raise SystemExit("--points applies to single-code workloads")
+    base = SEEDS[0]
+    POINTS = tuple(points)
+    SEEDS = tuple(base + 17 * i for i in range(len(POINTS)))
+    head = WORKLOAD.split(" blocks at Eb/N0 ")[0].rsplit(" ", 1)[0]
+    tail = WORKLOAD.split(" dB", 1)[1]
+    WORKLOAD = "%s %dx%d blocks at Eb/N0 %s dB%s" % (
+        head, len(POINTS), B_PER_POINT, ",".join("%g" % e for e in POINTS), tail)
+
+
 WORKLOAD_NAME = "bch"
 LINE = None  # (J0, beta) for one-line full ORBGRAND, None for basic
 MODEL = None  # (anchors, J, beta) for m-segment full ORBGRAND, None for basic
-FITTED = False  # one-line full ORBGRAND with a line fitted per block
+# False; True: one-line full ORBGRAND with a line fitted per block through
+# per-line tables (orbg_fitted_decode); (lines, divisible): a model of that
+# many lines fitted per block, each block searched in its own order
+# (orbg_decode_fitted)
+FITTED = False
 # Full ORBGRAND models for the secondary measurements on the BCH workload: the
 # one- and three-line fits (Sec. III-E, Eq. Q, Eq. quant) of the mean ordered
 # |LLR| curve of 10,000 of its blocks at 5.5 dB (seed 7); a CPU test recomputes
@@ -372,6 +408,8 @@ def summarise_child(d):
                        for k in ("bound", "achieved", "peak", "unit", "frac", "issued_frac",
                                  "traffic")}
     rec["clocks"] = d.get("clocks")
+    if "per_point" in d:
+        rec["per_point"] = d["per_point"]
     if "parity" in d:
         rec["parity"] = {k: d["parity"].get(k) for k in ("checked", "blocks", "mismatches",
                                                           "abandoned_checked")}
@@ -423,7 +461,12 @@ def extra_runs():
               ";".join(",".join(str(x) for x in f) for f in EXTRA_MODEL)]),
             ("bch, one-line full ORBGRAND with a line fitted per block",
              ["--workload", "bch", "--fitted"]),
-            ("paper256, basic ORBGRAND", ["--workload", "paper256"])]
+            ("bch, full ORBGRAND with a 3-line model fitted per block",
+             ["--workload", "bch", "--fitted-lines", "3"]),
+            ("paper256, basic ORBGRAND", ["--workload", "paper256"]),
+            ("ca-polar[256,234] at 5-6.5 dB, full ORBGRAND with a 3-line model fitted per "
+             "block (the paper's operating points, Sec. IV-B)",
+             ["--workload", "capolar256", "--fitted-lines", "3"])]
 
 
 def run_extra(steps=20, warmup=3, timeout_s=300, budget_s=420):
@@ -456,28 +499,26 @@ def _oracle_decode(H, llr, cap, line, model, fitted):
     import oracle
     if fitted:
         lines, div = fitted if isinstance(fitted, tuple) else (int(fitted), False)
-        cw, q, ab, _ = oracle.decode_batch_fit(H, llr, cap, lines, div)
-    elif model:
-        cw, q, ab, _ = oracle.decode_batch_mline(H, llr, cap, model)
-    elif line:
-        cw, q, ab, _ = oracle.decode_batch_1line(H, llr, cap, *line)
-    else:
-        cw, q, ab, _ = oracle.decode_batch(H, llr, cap)
-    return cw, q, ab
+        return oracle.decode_batch_fit(H, llr, cap, lines, div)
+    if model:
+        return oracle.decode_batch_mline(H, llr, cap, model)
+    if line:
+        return oracle.decode_batch_1line(H, llr, cap, *line)
+    return oracle.decode_batch(H, llr, cap)
 
 
 def _oracle_worker(args):
     H, llr, cap, line, model, fitted = args[:6]
     t = time.perf_counter()
-    cw, q, ab = _oracle_decode(H, llr, cap, line, model, fitted)
+    cw, q, ab, _ = _oracle_decode(H, llr, cap, line, model, fitted)
     return time.perf_counter() - t, int(q.sum()), llr.shape[0]
 
 
 def _oracle_outputs(args):
     """(block indices, oracle outputs) of one chunk, for the parity check."""
     idx, H, llr, cap, line, model, fitted = args
-    cw, q, ab = _oracle_decode(H, llr, cap, line, model, fitted)
-    return idx, cw, q, ab
+    cw, q, ab, sw = _oracle_decode(H, llr, cap, line, model, fitted)
+    return idx, cw, q, ab, sw
 
 
 def cpu_sample(llr, per_point, step):
@@ -630,10 +671,12 @@ class Job:
                      for c in self.codes]
         self.cs = orbg.CodeSet(self.objs)
         self.fitted = None
+        self.search = isinstance(FITTED, tuple)
         if FITTED:
             if len(self.codes) != 1 or self.form != "batched":
                 raise SystemExit("--fitted needs a single-code workload and the batched form")
-            self.fitted = orbg.Fitted(self.objs[0])
+            if not self.search:
+                self.fitted = orbg.Fitted(self.objs[0])
             self.rec = torch.empty((B, orbg.ORBG_FIT_STRIDE), dtype=torch.int32, device=dev)
         self.llr = torch.from_numpy(self.llr_np).to(dev)
         n_total = int(self.n_of_block.sum())
@@ -663,6 +706,10 @@ class Job:
         self.call(self.stream)
 
     def call(self, stream):
+        if self.search:
+            self.orbg.orbg_decode_fitted(self.objs[0].handle, self.llr, self.B, CAP, FITTED[0],
+                                         FITTED[1], self.cw, self.q, self.ab, self.rec, stream)
+            return
         if self.fitted is not None:
             lib = self.orbg.load_library()
             rc = lib.orbg_fitted_decode(self.fitted.handle, self.llr.data_ptr(), self.B, CAP,
@@ -690,9 +737,24 @@ class Job:
         diff = got != self.sent
         return float(np.logical_or.reduceat(diff, self.block_starts()).mean())
 
+    def per_point(self, got):
+        """BLER, mean queries and abandon rate of each Eb/N0 point (single-code
+        workloads: the points' blocks are consecutive)."""
+        cw, q, ab = got
+        n = self.codes[0].n
+        wrong = (cw.reshape(-1, n) != self.sent.reshape(-1, n)).any(axis=1)
+        out = []
+        for i, e in enumerate(POINTS):
+            sl = slice(i * B_PER_POINT, (i + 1) * B_PER_POINT)
+            out.append({"ebn0_db": e, "blocks": B_PER_POINT, "bler": float(wrong[sl].mean()),
+                        "block_errors": int(wrong[sl].sum()),
+                        "mean_queries": float(q[sl].mean()),
+                        "abandon_rate": float((ab[sl] == 1).mean())})
+        return out
+
     def launches_per_step(self):
         """Kernels of this library launched by one step."""
-        if self.form == "plain":
+        if self.form == "plain" or self.search:
             return 1
         sort = 2 if (self.off_np is not None and len(self.codes) > 1) else 0
         if self.fitted is not None:
@@ -702,6 +764,8 @@ class Job:
     def kernel_names(self):
         if self.form == "plain":
             return "orbg_plain_kernel"
+        if self.search:
+            return "orbg_fitsearch_kernel"
         names = "orbg_batched_kernel + orbg_heavy_kernel"
         if self.fitted is not None:
             return "orbg_fit_kernel + line marking + " + names
@@ -714,16 +778,24 @@ class Job:
                                                self.B, CAP, self.cw, self.off, self.q, self.ab,
                                                3, self.stream)
 
-    def alg_ops(self, qh):
+    def alg_ops(self, qh, sample=None):
         """Algorithmic integer ops of one step: per query sum_t W32 (w_t + 1),
-        per block n ceil(log2 n) sort compares."""
+        per block n ceil(log2 n) sort compares.  For a model fitted per
+        block (each block its own order) the per-block mean of q + sum_t w_t
+        comes from the oracle on the parity check's sample (`sample`: code
+        -> [blocks, sum]); None without one."""
         total = 0
         for j, code in enumerate(self.codes):
             sel = self.cid_np == j
             if not sel.any():
                 continue
             w32 = (code.r + 31) // 32
-            if self.fitted is not None:
+            if self.search:
+                if not sample or j not in sample or not sample[j][0]:
+                    return None
+                nb, acc = sample[j]
+                total += int(round(w32 * acc / nb * int(sel.sum())))
+            elif self.fitted is not None:
                 # each block in its own line's order (beta = 1, J_0 per block)
                 rec = self.rec.cpu().numpy()
                 J0 = np.where(rec[:, 0] == 0, 0, rec[:, 8])
@@ -761,6 +833,8 @@ def bench_ours(args, rank, world, local):
         f = [int(x) for x in args.shape.split(",")]
         orbg.orbg_codeset_set_tuning(job.cs.handle, orbg.OrbgTuning(*f))
         tuned = "given (--shape)"
+    elif isinstance(FITTED, tuple):
+        tuned = "none (one warp per block, blocks from a work queue)"
     elif FITTED:
         tuned = "default (the fitted decoder's own code set)"
     elif not args.no_autotune and args.form == "batched":
@@ -771,7 +845,7 @@ def bench_ours(args, rank, world, local):
         job.step()
     torch.cuda.synchronize(dev)
     graph = "direct calls (--no-graph)"
-    if FITTED:
+    if FITTED is True:
         graph = "direct calls (the fitted decoder reads each block's line back mid-step)"
     elif not args.no_graph:
         try:
@@ -813,9 +887,9 @@ def bench_ours(args, rank, world, local):
     qh, abh = got[1], got[2]
     q_step = int(qh.sum())
     queries_total = sum_over_ranks(float(q_step * args.steps), world, dev)
-    alg_ops = job.alg_ops(qh)
+    alg_ops = None if job.search else job.alg_ops(qh)  # per-block models: after parity
     kernel_ms = statistics.mean(per_step)
-    achieved = alg_ops / (kernel_ms / 1000.0) / 1e12   # Tops/s
+    achieved = alg_ops / (kernel_ms / 1000.0) / 1e12 if alg_ops is not None else None  # Tops/s
 
     peaks = {}
     try:
@@ -871,13 +945,14 @@ def bench_ours(args, rank, world, local):
         "bler": job.bler(got[0]),
         "gpu_launches": job.launches_per_step() * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "Tops/s", "frac": (achieved / peak) if peak else None,
+                     "unit": "Tops/s",
+                     "frac": (achieved / peak) if peak and achieved is not None else None,
                      "traffic": prof.get("traffic_bytes_per_step") if prof else None,
                      "issued_frac": prof.get("issued_frac") if prof else None,
                      "what": ("the step's decode kernels together (%s), timed by CUDA events "
                               "around each step on the launching stream; algorithmic 32-bit "
                               "integer ops per step = sum_t W32 (w_t + 1) + B n ceil(log2 n) "
-                              "= %d, which charges each column XOR as one op although one "
+                              "= %s, which charges each column XOR as one op although one "
                               "3-input lop3 can retire two, and charges every query in full "
                               "although the triple-range walk tests sixteen queries with "
                               "about thirty instructions (so frac can exceed 1 on "
@@ -898,12 +973,27 @@ def bench_ours(args, rank, world, local):
     }
     if e2e:
         line["e2e"] = e2e
+    if job.off_np is None and len(POINTS) > 1:
+        line["per_point"] = job.per_point(got)
     have = {}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], have = cpu_baseline(job)
     if not args.no_parity:
         line["parity"] = parity_check(job, got, have, budget_s=args.parity_budget,
                                       per_code=args.parity_per_code)
+        sample = line["parity"].pop("_alg")
+        if job.search:
+            # each block in its own order: the work per block is the oracle's
+            # own count on the checked sample, scaled to the step
+            alg_ops = job.alg_ops(qh, sample)
+            if alg_ops is not None:
+                rf = line["roofline"]
+                rf["achieved"] = alg_ops / (kernel_ms / 1000.0) / 1e12
+                rf["frac"] = rf["achieved"] / peak if peak else None
+                rf["what"] = rf["what"].replace(
+                    "= None,", "= %d (estimated: the oracle's q + sum_t w_t per block on the "
+                               "%d checked blocks, times the blocks of the step)," %
+                    (alg_ops, line["parity"]["checked"]))
     default = (rank == 0 and world == 1 and not args.no_extra and WORKLOAD_NAME == "mixed" and
                LINE is None and MODEL is None and not FITTED and args.form == "batched")
     if default:
@@ -1023,8 +1113,8 @@ def cpu_baseline(job, budget_s=15.0):
     workload: blocks taken in a stratified order (every stride-th block,
     then the next residue, ...) in chunks, until about budget_s seconds of
     CPU work; the whole workload if it finishes sooner.  Also returns the
-    oracle's outputs of those blocks ({block: (codeword, q, abandon)}), which
-    the parity check reuses."""
+    oracle's outputs of those blocks ({block: (codeword, q, abandon, sum of
+    the queries' Hamming weights)}), which the parity check reuses."""
     import oracle
     oracle.build_oracle()
     B = job.B
@@ -1040,12 +1130,12 @@ def cpu_baseline(job, budget_s=15.0):
             sel = idx[job.cid_np[idx] == j]
             llr = block_rows(job, sel, j)
             t = time.perf_counter()
-            cw, q, ab = _oracle_decode(job.codes[j].H, llr, CAP, LINE, MODEL, FITTED)
+            cw, q, ab, sw = _oracle_decode(job.codes[j].H, llr, CAP, LINE, MODEL, FITTED)
             t_total += time.perf_counter() - t
             qsum += int(q.sum())
             nb += sel.size
             for k, b in enumerate(sel):
-                outputs[int(b)] = (cw[k], int(q[k]), int(ab[k]))
+                outputs[int(b)] = (cw[k], int(q[k]), int(ab[k]), int(sw[k]))
         if t_total > budget_s:
             break
     what = ("the whole %d-block workload" % nb if nb == B else
@@ -1072,7 +1162,10 @@ def parity_check(job, got, have=None, budget_s=60.0, per_code=20000):
     code has `per_code` blocks checked (or all of its blocks), or until
     budget_s seconds have passed.  Blocks the GPU abandoned are put first in
     each code's order (at most 500 per code), so the longest searches are
-    among those checked."""
+    among those checked.  Also returns, under "_alg", per code the blocks
+    checked and the sum over them of q + sum_t w_t (the oracle's own count
+    of the queries' Hamming weights), from which the algorithmic work of
+    orders with a model per block is estimated."""
     import multiprocessing as mp
     import oracle
     oracle.build_oracle()
@@ -1084,18 +1177,23 @@ def parity_check(job, got, have=None, budget_s=60.0, per_code=20000):
     ncodes = len(job.codes)
     done = np.zeros(job.B, bool)
 
-    def compare(b, cw, q, ab):
+    alg = {}
+
+    def compare(b, cw, q, ab, sw):
         n = int(job.n_of_block[b])
         ok = (q == q_g[b] and ab == ab_g[b] and
               np.array_equal(np.asarray(cw, np.uint8), cw_g[starts[b]:starts[b] + n]))
         j = int(job.cid_np[b])
         checked[j] = checked.get(j, 0) + 1
+        a = alg.setdefault(j, [0, 0])
+        a[0] += 1
+        a[1] += int(sw) + int(q)
         done[b] = True
         if not ok:
             mism.append(int(b))
 
-    for b, (cw, q, ab) in have.items():
-        compare(b, cw, q, ab)
+    for b, (cw, q, ab, sw) in have.items():
+        compare(b, cw, q, ab, sw)
     t0 = time.time()
     todo = []
     for j in range(ncodes):
@@ -1119,9 +1217,9 @@ def parity_check(job, got, have=None, budget_s=60.0, per_code=20000):
         try:
             gen = ((sel, job.codes[j].H, block_rows(job, sel, j), CAP, LINE, MODEL, FITTED)
                    for _, j, sel in tasks)
-            for sel, cw, q, ab in pool.imap_unordered(_oracle_outputs, gen):
+            for sel, cw, q, ab, sw in pool.imap_unordered(_oracle_outputs, gen):
                 for k, b in enumerate(sel):
-                    compare(int(b), cw[k], int(q[k]), int(ab[k]))
+                    compare(int(b), cw[k], int(q[k]), int(ab[k]), int(sw[k]))
                 if time.time() - t0 > budget_s:
                     timed_out = True
                     break
@@ -1140,7 +1238,7 @@ def parity_check(job, got, have=None, budget_s=60.0, per_code=20000):
                         "(up to 500) and a stratified sample, up to %d per code%s"
                         % (per_code, ", cut by the %.0f s budget" % budget_s
                            if timed_out else ""))),
-            "cores": cores, "wall_s": round(time.time() - t0, 1)}
+            "cores": cores, "wall_s": round(time.time() - t0, 1), "_alg": alg}
 
 
 def main(argv=None):

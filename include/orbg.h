@@ -192,8 +192,9 @@ ORBG_API int orbg_codeset_free(orbg_codeset *set);
  * The call uses 72 + 8 ncodes + 12 B bytes of stream-ordered device
  * scratch (queue counters, per-code block counts, the list of still-open
  * blocks and the blocks' order grouped by code), allocated and freed on
- * cuda_stream.  With code_id given and more than one code in the set, the
- * first launch takes the blocks grouped by code.
+ * cuda_stream.  With code_id given and codes of different length classes
+ * (n <= 32, 64, 128, 256) or syndrome widths in the set, the first launch
+ * takes the blocks grouped by code.
  * Host buffers (staged through stream-ordered device copies): a call with
  * every buffer on the host, B >= 131072 and a layout that places the
  * blocks in order without overlap (dense, or offsets that never go back)
@@ -464,6 +465,40 @@ ORBG_API int orbg_fitted_decode(orbg_fitted *f, const float *llr, int64_t B,
                                 uint32_t query_cap, uint8_t *codeword, uint32_t *queries,
                                 uint8_t *abandoned, int32_t *models, void *cuda_stream);
 ORBG_API int orbg_fitted_free(orbg_fitted *f);
+
+/*
+ * Full ORBGRAND with a piece-wise linear model fitted to each block, any
+ * number of lines (Sec. III-E, Eq. Q, Eq. quant, then the order of Sec.
+ * III-D, Eq. relest_seg): the paper's 1- to 4-line variants of Sec. IV.
+ * One launch; per block, on the device: the reliability sort, the fit of
+ * orbg_fit_models (same anchors, same quantisation, plain or J-divisible),
+ * and a search of the block's own order -- noise patterns by increasing
+ * reliability weight (the sum over flipped sorted positions j of
+ * J_{i-1} + beta_i (j - I_{i-1}), i the segment of j), ties by Hamming
+ * weight and then positions lexicographically, the empty pattern first --
+ * for the first code-book member within query_cap queries.  The results
+ * equal, block by block, orbg_decode on a handle loaded with
+ * orbg_load_code_model for that block's fitted model.
+ *   code      : the code (its query-order tables are not used: any
+ *               query_cap up to ORBG_MAX_QUERY_CAP is allowed).
+ *   llr, B, codeword, queries, abandoned : as orbg_decode (host or device).
+ *   lines     : 1..8;  divisible : 0 or 1 (Eq. quant's J-divisible form).
+ *   models    : NULL, or [B][ORBG_FIT_STRIDE] int32 receiving each block's
+ *               model record as orbg_fit_models writes it.
+ *   abandoned[b] may also be ORBG_BLOCK_RANGE: the block's model would
+ *   need reliability weights above 2^26 - 1 (far beyond any cap's reach
+ *   for a model fitted to AWGN blocks) before its result is known, or its
+ *   search exceeded its step guard; codeword = hard decision, queries = 0.
+ * Device-buffer calls are asynchronous on cuda_stream and use 8 bytes of
+ * stream-ordered device scratch (the work-queue counter).
+ * Errors: EINVAL, ELIMIT (query_cap above ORBG_MAX_QUERY_CAP), ENOMEM,
+ * ECUDA; ENAN only for host-buffer calls, as orbg_decode.
+ */
+#define ORBG_BLOCK_RANGE 3
+ORBG_API int orbg_decode_fitted(const orbg_code *code, const float *llr, int64_t B,
+                                uint32_t query_cap, int lines, int divisible,
+                                uint8_t *codeword, uint32_t *queries, uint8_t *abandoned,
+                                int32_t *models, void *cuda_stream);
 
 /* Static description of a status code (never NULL). */
 ORBG_API const char *orbg_status_string(int status);

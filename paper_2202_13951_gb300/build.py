@@ -21,8 +21,11 @@ SOURCES = ["orbg_plain.cu", "orbg_batched.cu", "orbg_noalloc.cu",
 # the batched kernels: one object per (keys per lane, syndrome words) pair
 INST = "orbg_batched_inst.cu"
 INST_KW = [(k, w) for k in (1, 2, 4, 8) for w in (1, 2, 4)]
+# the per-block fitted decoder: one object per keys per lane
+FS_INST = "orbg_fitted_search_inst.cu"
+FS_K = (1, 2, 4, 8)
 HEADERS = ["orbg_internal.h", "orbg_decode_block.cuh", "orbg_batched.cuh", "orbg_heavy.cuh",
-           "orbg_fit.cuh"]
+           "orbg_fit.cuh", "orbg_fitted_search.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -41,7 +44,7 @@ def _digest(extra=()):
     and of the compiler's path: the library is rebuilt whenever this
     changes (file times are not trusted: a copied tree keeps them)."""
     h = hashlib.sha256()
-    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS + [INST]]
+    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS + [INST, FS_INST]]
     deps.append(os.path.join(ROOT, "include", "orbg.h"))
     deps.append(os.path.abspath(__file__))
     for d in deps:
@@ -74,6 +77,8 @@ def build(force=False, verbose=False, extra=()):
     units = [(INST, "orbg_batched_k%dw%d.o" % (k, w),
               ["-DORBG_INST_K=%d" % k, "-DORBG_INST_W=%d" % w])
              for k, w in sorted(INST_KW, key=lambda kw: -kw[0] * kw[1])]
+    units += [(FS_INST, "orbg_fitted_search_k%d.o" % k, ["-DORBG_FS_K=%d" % k])
+              for k in sorted(FS_K, reverse=True)]
     units += [(s, s + ".o", []) for s in SOURCES]
     for s, o, defs in units:
         obj = os.path.join(OBJDIR, o)

@@ -37,6 +37,7 @@ struct orbg_code {
 
 struct orbg_codeset {
     int ncodes, n_max, w32_max;
+    int variants;                /* distinct (keys per lane, syndrome words) of the codes */
     uint32_t ntrip_max;
     uint32_t x3w_max;
     orbg_tuning tuning;
@@ -179,6 +180,7 @@ int orbg_codeset_view(const orbg_codeset *set, OrbgSetView *out)
     out->ncodes = set->ncodes;
     out->n_max = set->n_max;
     out->w32_max = set->w32_max;
+    out->variants = set->variants;
     out->ntrip_max = set->ntrip_max;
     out->x3w_max = set->x3w_max;
     out->cap_min = set->cap_min;
@@ -625,6 +627,18 @@ int orbg_codeset_create(const orbg_code *const *codes, int ncodes, orbg_codeset 
         s->ntrip_max = std::max(s->ntrip_max, codes[i]->dev.ntrip);
         s->x3w_max = std::max(s->x3w_max, codes[i]->dev.x3w);
     }
+    {
+        /* the decoder variants the kernels dispatch to: keys per lane from
+         * n (n <= 32, 64, 128, 256) and the syndrome width */
+        std::vector<int> kw;
+        for (int i = 0; i < ncodes; i++) {
+            const int n = codes[i]->n;
+            const int kc = n <= 32 ? 0 : n <= 64 ? 1 : n <= 128 ? 2 : 3;
+            kw.push_back(kc * 8 + codes[i]->w32);
+        }
+        std::sort(kw.begin(), kw.end());
+        s->variants = (int)(std::unique(kw.begin(), kw.end()) - kw.begin());
+    }
     cudaError_t e;
     if ((e = cudaGetDevice(&s->device)) != cudaSuccess ||
         (e = cudaMalloc(&s->d_codes, descs.size() * sizeof(OrbgDeviceCode))) != cudaSuccess ||
@@ -769,6 +783,7 @@ int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
         a.ncodes = set->ncodes;
         a.n_max = set->n_max;
         a.w32_max = set->w32_max;
+        a.variants = set->variants;
         a.code_id = d_cid ? d_cid + b0 : nullptr;
         a.llr_off = d_lo ? d_lo + b0 : nullptr;
         a.cw_off = d_co ? d_co + b0 : nullptr;
@@ -917,6 +932,7 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
     a.ncodes = set->ncodes;
     a.n_max = set->n_max;
     a.w32_max = set->w32_max;
+    a.variants = set->variants;
     a.code_id = d_cid;
     a.llr_off = d_lo;
     a.llr = d_llr;
@@ -1221,6 +1237,7 @@ int orbg_fitted_decode(orbg_fitted *f, const float *llr, int64_t B, uint32_t que
         a.ncodes = set->ncodes;
         a.n_max = set->n_max;
         a.w32_max = set->w32_max;
+        a.variants = set->variants;
         a.code_id = d_cid;
         a.llr_off = nullptr;
         a.llr = llr;
@@ -1249,6 +1266,79 @@ int orbg_fitted_decode(orbg_fitted *f, const float *llr, int64_t B, uint32_t que
     if (!models && d_models)
         cudaFreeAsync(d_models, st);
     return rc;
+}
+
+}  // extern "C"
+
+/* ------------------------------------- per-block fitted models, any lines -- */
+
+extern "C" {
+
+int orbg_decode_fitted(const orbg_code *code, const float *llr, int64_t B, uint32_t query_cap,
+                       int lines, int divisible, uint8_t *codeword, uint32_t *queries,
+                       uint8_t *abandoned, int32_t *models, void *cuda_stream)
+{
+    if (!code || B < 0 || query_cap < 1 || lines < 1 || lines > ORBG_MAX_SEG)
+        return ORBG_EINVAL;
+    if (query_cap > ORBG_MAX_QUERY_CAP || B >= ((int64_t)1 << 40))
+        return ORBG_ELIMIT;
+    if (B == 0)
+        return ORBG_OK;
+    if (!llr || !codeword || !queries || !abandoned)
+        return ORBG_EINVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const size_t nb = (size_t)B * code->n;
+    Stager sg(st);
+    const float *d_llr;
+    uint8_t *d_cw, *d_ab;
+    uint32_t *d_q;
+    int32_t *d_rec = nullptr;
+    int rc;
+    if ((rc = sg.add(llr, nb * sizeof(float), true, false, &d_llr)) ||
+        (rc = sg.add(codeword, nb, false, true, &d_cw)) ||
+        (rc = sg.add(queries, (size_t)B * sizeof(uint32_t), false, true, &d_q)) ||
+        (rc = sg.add(abandoned, (size_t)B, false, true, &d_ab)) ||
+        (rc = sg.add(models, models ? (size_t)B * ORBG_FIT_STRIDE * sizeof(int32_t) : 0, false,
+                     true, &d_rec))) {
+        sg.finish(false);
+        return rc;
+    }
+    unsigned long long *queue = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&queue, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) {
+        sg.finish(false);
+        return cuda_fail(e);
+    }
+    const int n = code->n;
+    const int div = divisible ? 1 : 0;
+    int le;
+    if (n <= 32)
+        le = orbg_launch_fitsearch_k1(code->dev, d_llr, B, query_cap, lines, div, d_cw, d_q,
+                                      d_ab, d_rec, queue, st);
+    else if (n <= 64)
+        le = orbg_launch_fitsearch_k2(code->dev, d_llr, B, query_cap, lines, div, d_cw, d_q,
+                                      d_ab, d_rec, queue, st);
+    else if (n <= 128)
+        le = orbg_launch_fitsearch_k4(code->dev, d_llr, B, query_cap, lines, div, d_cw, d_q,
+                                      d_ab, d_rec, queue, st);
+    else
+        le = orbg_launch_fitsearch_k8(code->dev, d_llr, B, query_cap, lines, div, d_cw, d_q,
+                                      d_ab, d_rec, queue, st);
+    cudaFreeAsync(queue, st);
+    if (le != 0) {
+        sg.finish(false);
+        return cuda_fail((cudaError_t)le);
+    }
+    if (!sg.any())
+        return ORBG_OK;
+    rc = sg.finish(true);
+    if (rc)
+        return rc;
+    if (!is_device_ptr(abandoned))
+        for (int64_t b = 0; b < B; b++)
+            if (abandoned[b] == ORBG_BLOCK_NAN)
+                return ORBG_ENAN;
+    return ORBG_OK;
 }
 
 }  // extern "C"

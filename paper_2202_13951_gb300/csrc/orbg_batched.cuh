@@ -153,8 +153,9 @@ cudaError_t launch_t(const OrbgBatchedArgs &a)
     int grid = 0, rc;
     if ((e = cudaMemsetAsync(a.scratch, 0, sc.zero_bytes, st)) != cudaSuccess)
         return e;
-    /* mixed codes: phase 1 takes the blocks grouped by code */
-    const bool sorted = !ONE && a.code_id != nullptr && a.ncodes > 1;
+    /* codes that need different decoder variants: phase 1 takes the blocks
+     * grouped by code, so one variant runs at a time */
+    const bool sorted = !ONE && a.code_id != nullptr && a.ncodes > 1 && a.variants > 1;
     if (sorted && (rc = orbg_launch_code_sort(a.code_id, a.B, a.ncodes, sc, st)) != 0)
         return (cudaError_t)rc;
     /* phase 1: per warp, one block's working set, two LLR slots and its own

@@ -83,49 +83,23 @@ ORBG_FIT_HD inline long long round_half_away(double x)
 /* L_j, 1-based, from the sorted values */
 ORBG_FIT_HD inline double Lj(const float *s, int j) { return (double)s[j - 1]; }
 
-/*
- * s: the n reliabilities in ascending order.  Writes out[0..23]: m, the
- * anchors I_1..I_{m-1} at 1.., J_0..J_{m-1} at 8.., beta_1..beta_m at
- * 16.. (out zeroed by the caller).  Anchors start at 1 and floor(n/2);
- * each further anchor splits the first interval at its largest chord gap
- * (smaller index on ties) until `lines` segments or no gap; Q = the
- * smallest slope; beta_i = [s_i / Q], J_0 = [L_1 / Q] - beta_1, J_i =
- * [L_{I_i} / Q]; divisible: J_{i-1} <- [J_{i-1} / beta_i] beta_i.  n < 4,
- * Q <= 0 or a ratio above 2^24 (or not finite): the basic model.
- */
-ORBG_FIT_HD inline void fit_sorted(const float *s, int n, int lines, int divisible, int32_t *out)
+/* The vertical gap at index j between the chord of the ordered curve over
+ * [lo, hi] and the curve itself (the anchor search of Sec. III-E). */
+ORBG_FIT_HD inline double chord_gap(const float *s, int lo, int hi, int j)
+{
+    const double Llo = Lj(s, lo);
+    const double rise = sub(Lj(s, hi), Llo);
+    const double chord = add(Llo, dvd(mul(rise, (double)(j - lo)), (double)(hi - lo)));
+    return fabs(sub(chord, Lj(s, j)));
+}
+
+/* Eq. Q and Eq. quant for the anchors a[0] = 1 < a[1] < ... < a[na-1]
+ * (the last the centre floor(n/2)): writes out as fit_sorted does (out
+ * holds the basic model on entry). */
+ORBG_FIT_HD inline void quantise(const float *s, const int *a, int na, int divisible,
+                                 int32_t *out)
 {
     const double kFitMax = 16777216.0; /* 2^24 */
-    int a[ORBG_FIT_SEG + 1];
-    int na = 2;
-    out[0] = 1;
-    out[8] = 0;  /* J_0 */
-    out[16] = 1; /* beta_1 */
-    if (n < 4)
-        return;
-    a[0] = 1;
-    a[1] = n / 2;
-    while (na - 1 < lines) {
-        const int lo = a[0], hi = a[1];
-        int best = -1;
-        double gap = 0.0;
-        const double Llo = Lj(s, lo);
-        const double rise = sub(Lj(s, hi), Llo);
-        for (int j = lo + 1; j < hi; j++) {
-            const double chord = add(Llo, dvd(mul(rise, (double)(j - lo)), (double)(hi - lo)));
-            const double g = fabs(sub(chord, Lj(s, j)));
-            if (g > gap) {
-                gap = g;
-                best = j;
-            }
-        }
-        if (best < 0)
-            break;
-        for (int k = na; k > 1; k--)
-            a[k] = a[k - 1];
-        a[1] = best;
-        na++;
-    }
     const int m = na - 1;
     double sl[ORBG_FIT_SEG];
     sl[0] = dvd(sub(Lj(s, a[1]), Lj(s, 1)), (double)(a[1] - 1));
@@ -156,6 +130,48 @@ ORBG_FIT_HD inline void fit_sorted(const float *s, int n, int lines, int divisib
         out[8 + i] = (int32_t)J[i];
         out[16 + i] = (int32_t)beta[i];
     }
+}
+
+/*
+ * s: the n reliabilities in ascending order.  Writes out[0..23]: m, the
+ * anchors I_1..I_{m-1} at 1.., J_0..J_{m-1} at 8.., beta_1..beta_m at
+ * 16.. (out zeroed by the caller).  Anchors start at 1 and floor(n/2);
+ * each further anchor splits the first interval at its largest chord gap
+ * (smaller index on ties) until `lines` segments or no gap; Q = the
+ * smallest slope; beta_i = [s_i / Q], J_0 = [L_1 / Q] - beta_1, J_i =
+ * [L_{I_i} / Q]; divisible: J_{i-1} <- [J_{i-1} / beta_i] beta_i.  n < 4,
+ * Q <= 0 or a ratio above 2^24 (or not finite): the basic model.
+ */
+ORBG_FIT_HD inline void fit_sorted(const float *s, int n, int lines, int divisible, int32_t *out)
+{
+    int a[ORBG_FIT_SEG + 1];
+    int na = 2;
+    out[0] = 1;
+    out[8] = 0;  /* J_0 */
+    out[16] = 1; /* beta_1 */
+    if (n < 4)
+        return;
+    a[0] = 1;
+    a[1] = n / 2;
+    while (na - 1 < lines) {
+        const int lo = a[0], hi = a[1];
+        int best = -1;
+        double gap = 0.0;
+        for (int j = lo + 1; j < hi; j++) {
+            const double g = chord_gap(s, lo, hi, j);
+            if (g > gap) {
+                gap = g;
+                best = j;
+            }
+        }
+        if (best < 0)
+            break;
+        for (int k = na; k > 1; k--)
+            a[k] = a[k - 1];
+        a[1] = best;
+        na++;
+    }
+    quantise(s, a, na, divisible, out);
 }
 
 }  // namespace orbg_fit

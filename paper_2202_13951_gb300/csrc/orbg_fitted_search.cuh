@@ -1,0 +1,634 @@
+/*
+ * orbg_fitted_search.cuh -- full ORBGRAND with a piece-wise linear model
+ * fitted to each block (Sec. III-E), searched in that block's own order
+ * (Sec. III-D), one warp per block.
+ *
+ * Per block, fused in one kernel:
+ *   1. load, hard decision y, starting syndrome s0 = H y (as the other
+ *      decoders: load_block);
+ *   2. the exact reliability order pi (sort_block) and the ordered curve
+ *      L_1 <= ... <= L_n;
+ *   3. the fit: anchors by the largest chord gap (every lane takes a share of
+ *      the indices; the warp keeps the largest gap, the smaller index on
+ *      ties), then Eq. Q and Eq. quant on one lane (orbg_fit.cuh, the same
+ *      double operations as the oracle);
+ *   4. the integer weight rho_j of every sorted position j (Eq. relest_seg:
+ *      J_{i-1} + beta_i (j - I_{i-1}) on segment i) and the suffix minima
+ *      msuf_j = min over j' >= j of rho_j';
+ *   5. the search for the first code-book member in the order of increasing
+ *      reliability weight R(z) = sum of rho over the flipped positions, ties
+ *      by Hamming weight and then positions lexicographically (the order
+ *      every decoder of this library uses inside one weight).
+ *
+ * The search walks the subsets of {1..n} as a binary tree in lexicographic
+ * order: node S = {j_1 < ... < j_t} has the child S + {j_t + 1} ("add") and
+ * the next sibling S - {j_t} + {j_t + 1} ("replace"); every non-empty subset
+ * is reached once from the root {1}.  Everything below a node keeps
+ * j_1..j_{t-1} and adds positions >= j_t, so R(S) - rho_{j_t} + msuf_{j_t}
+ * bounds the weight of the node and all it leads to from below; a pass with
+ * bound Rhi enters only nodes whose bound is <= Rhi and tests those with
+ * R <= Rhi (the weights rho need not increase with j).  The 32 lanes of the
+ * warp each walk a part of the tree depth first, with their positions on a
+ * per-lane stack in shared memory; a lane that runs out of work is given the
+ * "replace" branch of a lane that is about to take its "add" branch.
+ *
+ * Passes run with growing bounds ("bands"): a pass that finds code-book
+ * members lowers its bound to the lightest one found, and the least of
+ * them in the order (weight, Hamming weight, positions) is the decoding; a
+ * second pass over the nodes up to that weight counts the patterns that
+ * come before it, which gives its query index.  A pass without a member
+ * that already covers `cap` queries ends the block as abandoned.  Every
+ * pass is a finite walk of a finite tree; each also stops after a fixed
+ * number of steps (a guard, never reached by a correct walk) and marks the
+ * block ORBG_BLOCK_RANGE, as does a search that would need weights beyond
+ * 2^26 - 1.
+ */
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "orbg_decode_block.cuh"
+#include "orbg_fit.cuh"
+
+namespace orbg_fitsearch {
+
+using namespace orbg_dev;
+
+constexpr int kWarps = 8;                   /* warps per CTA, one block each */
+constexpr int kDepth = 31;                  /* largest pattern the stack holds */
+constexpr uint32_t kRhoInf = 1u << 30;      /* weight of a position never reached */
+constexpr int32_t kRmax = (1 << 26) - 1;    /* heaviest reliability weight searched */
+constexpr int32_t kNoHit = 0x7FFFFFFF;
+constexpr int kBlockRange = ORBG_BLOCK_RANGE; /* abandoned[] value: beyond the search range */
+
+/* Shared memory of one warp (one block in flight). */
+template <int W> struct FsSmem {
+    typedef typename Syn<W>::T T;
+    uint32_t *rho;   /* [258] rho_j, j = 1..n; rho[n + 1] = kRhoInf */
+    uint32_t *msuf;  /* [258] suffix minima, msuf[n + 1] = kRhoInf */
+    uint32_t *c0;    /* [258] first syndrome word of position j; c0[0] = 0 */
+    T *h;            /* [258] whole syndrome of position j (W > 1) */
+    float *L;        /* [256] ordered reliabilities */
+    uint8_t *pi;     /* [256] received index of sorted position j - 1 */
+    uint8_t *cw;     /* [256] staged codeword */
+    uint8_t *stk;    /* [32][32] stk[d * 32 + lane]: j_{d+1} of the lane's node */
+    uint8_t *hb;     /* [32][32] hb[i * 32 + lane]: the lane's best member so far */
+    uint8_t *best;   /* [32] the block's decoding, positions ascending */
+    int32_t *rec;    /* [24] the block's model record */
+    int32_t *anch;   /* [9] anchors during the fit */
+    __device__ __forceinline__ FsSmem(unsigned char *base)
+    {
+        unsigned char *p = base;
+        rho = (uint32_t *)p;
+        p += 258 * 4;
+        msuf = (uint32_t *)p;
+        p += 258 * 4;
+        c0 = (uint32_t *)p;
+        p += 258 * 4;
+        p = (unsigned char *)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+        h = (T *)p;
+        if (W > 1)
+            p += 258 * sizeof(T);
+        L = (float *)p;
+        p += 256 * 4;
+        pi = p;
+        p += 256;
+        cw = p;
+        p += 256;
+        stk = p;
+        p += 32 * 32;
+        hb = p;
+        p += 32 * 32;
+        best = p;
+        p += 32;
+        rec = (int32_t *)p;
+        p += 24 * 4;
+        anch = (int32_t *)p;
+    }
+};
+
+template <int W>
+__host__ __device__ constexpr uint32_t fs_warp_bytes()
+{
+    return (uint32_t)((3 * 258 * 4 + 15) / 16 * 16 + (W > 1 ? 258 * 4 * W : 0) + 256 * 4 + 256 +
+                      256 + 32 * 32 + 32 * 32 + 32 + 24 * 4 + 9 * 4 + 15) /
+           16 * 16;
+}
+
+/* ---------------------------------------------------------- the fit */
+
+/* Sec. III-E on the ordered curve sm.L: anchors by the largest chord gap
+ * (lanes share the indices of the interval; the largest gap wins, the
+ * smaller index on equal gaps, as in the one-lane loop of fit_sorted), then
+ * Eq. Q / Eq. quant on lane 0.  Writes sm.rec. */
+template <int W>
+__device__ void fit_block(const FsSmem<W> &sm, int n, int lines, int divisible, int lane)
+{
+    if (lane < ORBG_FIT_WORDS)
+        sm.rec[lane] = 0;
+    __syncwarp();
+    if (lane == 0) {
+        sm.rec[0] = 1;
+        sm.rec[8] = 0;
+        sm.rec[16] = 1;
+        sm.anch[0] = 1;
+        sm.anch[1] = n / 2;
+    }
+    __syncwarp();
+    if (n < 4)
+        return;
+    int na = 2;
+    while (na - 1 < lines) {
+        const int lo = sm.anch[0], hi = sm.anch[1];
+        double gap = 0.0;
+        int best = -1;
+        for (int j = lo + 1 + lane; j < hi; j += 32) {
+            const double g = orbg_fit::chord_gap(sm.L, lo, hi, j);
+            if (g > gap) {
+                gap = g;
+                best = j;
+            }
+        }
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) {
+            const double og = __shfl_xor_sync(FULL_MASK, gap, d);
+            const int oj = __shfl_xor_sync(FULL_MASK, best, d);
+            if (oj >= 0 && (best < 0 || og > gap || (og == gap && oj < best))) {
+                gap = og;
+                best = oj;
+            }
+        }
+        if (best < 0)
+            break;
+        __syncwarp();
+        if (lane == 0) {
+            for (int k = na; k > 1; k--)
+                sm.anch[k] = sm.anch[k - 1];
+            sm.anch[1] = best;
+        }
+        __syncwarp();
+        na++;
+    }
+    if (lane == 0)
+        orbg_fit::quantise(sm.L, sm.anch, na, divisible, sm.rec);
+    __syncwarp();
+}
+
+/* rho_j from the model record (Eq. relest_seg), clamped to kRhoInf, and the
+ * suffix minima.  Lane l owns positions 8l + 1 .. 8l + 8. */
+template <int W>
+__device__ void position_weights(const FsSmem<W> &sm, int n, int lane)
+{
+    const int m = sm.rec[0];
+    uint32_t v[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const int j = 8 * lane + 1 + i;
+        uint32_t r = kRhoInf;
+        if (j <= n) {
+            int seg = 0, Ilo = 0;
+            for (int s = 1; s < m; s++)
+                if (j > sm.rec[s]) {
+                    seg = s;
+                    Ilo = sm.rec[s];
+                }
+            const long long w =
+                (long long)sm.rec[8 + seg] + (long long)sm.rec[16 + seg] * (long long)(j - Ilo);
+            r = w < 0 ? 0u : w >= (long long)kRhoInf ? kRhoInf : (uint32_t)w;
+            sm.rho[j] = r;
+        }
+        v[i] = r;
+    }
+#pragma unroll
+    for (int i = 6; i >= 0; i--)
+        v[i] = min(v[i], v[i + 1]);
+    /* minimum over the lanes above: inclusive suffix scan, shifted by one */
+    uint32_t incl = v[0];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_down_sync(FULL_MASK, incl, d);
+        if (lane + d < 32)
+            incl = min(incl, o);
+    }
+    uint32_t above = __shfl_down_sync(FULL_MASK, incl, 1);
+    if (lane == 31)
+        above = kRhoInf;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const int j = 8 * lane + 1 + i;
+        if (j <= n)
+            sm.msuf[j] = min(v[i], above);
+    }
+    if (lane == 0) {
+        sm.rho[n + 1] = kRhoInf;
+        sm.msuf[n + 1] = kRhoInf;
+    }
+    __syncwarp();
+}
+
+/* ------------------------------------------------- the tree walk */
+
+/* Is the lane's node (stack j_1..j_{t-1}, then jt) before the t-position
+ * pattern other[i * ostride] in lexicographic order? */
+__device__ __forceinline__ bool node_lex_less(const uint8_t *stk, int lane, int t, int jt,
+                                              const uint8_t *other, int ostride)
+{
+    for (int i = 0; i < t; i++) {
+        const int a = i < t - 1 ? (int)stk[i * 32 + lane] : jt;
+        const int b = (int)other[i * ostride];
+        if (a != b)
+            return a < b;
+    }
+    return false;
+}
+
+/* Are the best members of lanes la and lb (t positions each) in
+ * lexicographic order? */
+__device__ __forceinline__ bool hb_lex_less(const uint8_t *hb, int la, int lb, int t)
+{
+    for (int i = 0; i < t; i++) {
+        const int a = hb[i * 32 + la], b = hb[i * 32 + lb];
+        if (a != b)
+            return a < b;
+    }
+    return false;
+}
+
+/* Syndrome of the lane's node on all W words. */
+template <int W>
+__device__ __noinline__ bool node_is_member(const FsSmem<W> &sm, int lane, int t, int jt,
+                                            typename Syn<W>::T s0)
+{
+    typename Syn<W>::T P = sx(s0, sm.h[jt]);
+    for (int i = 0; i < t - 1; i++)
+        P = sx(P, sm.h[sm.stk[i * 32 + lane]]);
+    return sz(P);
+}
+
+/*
+ * One pass over the nodes whose bound is <= Rhi.
+ * RANK = false: tests every node with R <= Rhi; a lane keeps its least
+ *   member (bR, bT, its positions in hb) and the bound drops to the warp's
+ *   lightest member.  Returns the number of nodes tested (lane's share).
+ * RANK = true: counts the nodes before the block's decoding (weight Rb,
+ *   Hamming weight Tb, positions sm.best): lighter, or as heavy with fewer
+ *   positions, or as heavy and as many positions and lexicographically
+ *   smaller.  Returns the lane's share of that count.
+ * *guard is set (warp-uniform) if the walk exceeds `steps` iterations.
+ */
+template <int W, bool RANK>
+__device__ uint32_t tree_pass(const FsSmem<W> &sm, int n, typename Syn<W>::T s0, int32_t Rhi,
+                              int32_t Rb, int Tb, int lane, uint32_t steps, int32_t *bR,
+                              int *bT, bool *guard)
+{
+    const uint32_t s0w = first_word(s0);
+    bool active = false, fresh = false;
+    int t = 0, t0 = 0, jt = 0;
+    uint32_t R = 0, rcur = 0, ccur = 0, syn = 0, don = 0, cnt = 0;
+    if (lane == 0 && n >= 1 && sm.msuf[1] <= (uint32_t)Rhi) {
+        active = true;
+        fresh = true;
+        t = 1;
+        t0 = 1;
+        jt = 1;
+        rcur = sm.rho[1];
+        ccur = sm.c0[1];
+        R = rcur;
+        syn = s0w ^ ccur;
+    }
+    uint32_t it = 0;
+    for (;;) {
+        const uint32_t act = __ballot_sync(FULL_MASK, active);
+        if (act == 0)
+            break;
+        if (++it > steps) {
+            *guard = true;
+            break;
+        }
+        const bool tested = active && fresh && R <= (uint32_t)Rhi;
+        if (RANK) {
+            if (tested) {
+                if (R < (uint32_t)Rb)
+                    cnt++;
+                else if (R == (uint32_t)Rb &&
+                         (t < Tb || (t == Tb && node_lex_less(sm.stk, lane, t, jt, sm.best, 1))))
+                    cnt++;
+            }
+        } else {
+            cnt += tested ? 1u : 0u;
+            const bool cand = tested && syn == 0u;
+            if (__any_sync(FULL_MASK, cand)) {
+                if (cand && (W == 1 || node_is_member<W>(sm, lane, t, jt, s0))) {
+                    const bool better =
+                        (int32_t)R < *bR ||
+                        ((int32_t)R == *bR &&
+                         (t < *bT ||
+                          (t == *bT && node_lex_less(sm.stk, lane, t, jt, sm.hb + lane, 32))));
+                    if (better) {
+                        for (int i = 0; i < t - 1; i++)
+                            sm.hb[i * 32 + lane] = sm.stk[i * 32 + lane];
+                        sm.hb[(t - 1) * 32 + lane] = (uint8_t)jt;
+                        *bR = (int32_t)R;
+                        *bT = t;
+                    }
+                }
+                /* nothing heavier than the lightest member found can come first */
+                Rhi = min(Rhi, __reduce_min_sync(FULL_MASK, *bR));
+            }
+        }
+        const int jn = jt + 1;
+        const bool okn = active && jt < n;
+        const uint32_t ms = okn ? sm.msuf[jn] : kRhoInf;
+        const bool addOK = okn && fresh && R + ms <= (uint32_t)Rhi;
+        bool replOK = okn && R - rcur + ms <= (uint32_t)Rhi && !((don >> t) & 1u);
+        /* lanes without work take the replace branch of lanes about to add */
+        const uint32_t idle = ~act;
+        const uint32_t donors = __ballot_sync(FULL_MASK, addOK && replOK);
+        bool got = false;
+        if (idle != 0u && donors != 0u) {
+            const uint32_t below = (1u << lane) - 1u;
+            int src = lane;
+            if (!active) {
+                /* the r-th idle lane takes the r-th donor's branch */
+                uint32_t r = __popc(idle & below);
+                if (r < (uint32_t)__popc(donors)) {
+                    uint32_t m = donors;
+                    for (; r > 0; r--)
+                        m &= m - 1u;
+                    src = __ffs(m) - 1;
+                }
+            }
+            const bool give = addOK && replOK && __popc(donors & below) < __popc(idle);
+            const int st = __shfl_sync(FULL_MASK, t, src);
+            const int sj = __shfl_sync(FULL_MASK, jt, src);
+            const uint32_t sR = __shfl_sync(FULL_MASK, R, src);
+            const uint32_t ssyn = __shfl_sync(FULL_MASK, syn, src);
+            const uint32_t src_r = __shfl_sync(FULL_MASK, rcur, src);
+            const uint32_t src_c = __shfl_sync(FULL_MASK, ccur, src);
+            if (src != lane) {
+                const uint32_t rn = sm.rho[sj + 1], cn = sm.c0[sj + 1];
+                for (int d = 0; d < st - 1; d++)
+                    sm.stk[d * 32 + lane] = sm.stk[d * 32 + src];
+                t = st;
+                t0 = st;
+                jt = sj + 1;
+                R = sR - src_r + rn;
+                syn = ssyn ^ src_c ^ cn;
+                rcur = rn;
+                ccur = cn;
+                don = 0;
+                fresh = true;
+                active = true;
+                got = true;
+            }
+            if (give) {
+                don |= 1u << t;
+                replOK = false;
+            }
+            __syncwarp();
+        }
+        if (active && !got) {
+            if (addOK && t >= kDepth) {
+                *guard = true; /* deeper than the stack: cannot happen within 2^26 queries */
+                active = false;
+            } else if (addOK || replOK) {
+                const uint32_t rn = sm.rho[jn], cn = sm.c0[jn];
+                if (addOK) {
+                    sm.stk[(t - 1) * 32 + lane] = (uint8_t)jt;
+                    t++;
+                    R += rn;
+                    syn ^= cn;
+                } else {
+                    R = R - rcur + rn;
+                    syn ^= ccur ^ cn;
+                }
+                jt = jn;
+                rcur = rn;
+                ccur = cn;
+                fresh = true;
+            } else if (t > t0) {
+                R -= rcur;
+                syn ^= ccur;
+                don &= ~(1u << t);
+                t--;
+                jt = sm.stk[(t - 1) * 32 + lane];
+                rcur = sm.rho[jt];
+                ccur = sm.c0[jt];
+                fresh = false;
+            } else {
+                active = false;
+            }
+        }
+    }
+    *guard = __any_sync(FULL_MASK, *guard);
+    return cnt;
+}
+
+/* Sum over the warp of per-lane counts below 2^32 (exact in 64 bits). */
+__device__ __forceinline__ uint64_t warp_sum64(uint32_t v)
+{
+    const uint64_t hi = __reduce_add_sync(FULL_MASK, v >> 16);
+    const uint64_t lo = __reduce_add_sync(FULL_MASK, v & 0xFFFFu);
+    return (hi << 16) + lo;
+}
+
+/* ---------------------------------------------------------- one block */
+
+template <int K, int W>
+__device__ void decode_fitted_block(const OrbgDeviceCode &code, const float *__restrict__ llr,
+                                    uint8_t *__restrict__ cw_out, uint32_t *__restrict__ q_out,
+                                    uint8_t *__restrict__ ab_out, int32_t *__restrict__ rec_out,
+                                    uint32_t cap, int lines, int divisible, const FsSmem<W> &sm,
+                                    int lane)
+{
+    typedef typename Syn<W>::T T;
+    const int n = code.n;
+    uint32_t key[K];
+    bool nan;
+    const T s0 = load_block<K, W>(code, llr, key, sm.cw, lane, &nan);
+    uint32_t q = 0;
+    int ab = 0, wbest = 0;
+    if (nan) {
+        ab = ORBG_BLOCK_NAN;
+        if (rec_out && lane < ORBG_FIT_WORDS)
+            rec_out[lane] = 0;
+    } else if (sz(s0) && rec_out == nullptr) {
+        q = 1; /* the hard decision is a code word: query 1, whatever the model */
+    } else {
+        sort_block<K>(key, llr, n, lane);
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            const int e = lane * K + k;
+            if (e < n) {
+                const int idx = (int)key[k];
+                sm.pi[e] = (uint8_t)idx;
+                sm.L[e] = fabsf(__ldg(llr + idx));
+                const T col = load_col<W>(code.hcol, idx);
+                sm.c0[e + 1] = first_word(col);
+                if (W > 1)
+                    sm.h[e + 1] = col;
+            }
+        }
+        if (lane == 0) {
+            sm.c0[0] = 0u;
+            if (W > 1)
+                sm.h[0] = szero<T>();
+        }
+        __syncwarp();
+        fit_block<W>(sm, n, lines, divisible, lane);
+        if (rec_out && lane < ORBG_FIT_WORDS)
+            rec_out[lane] = sm.rec[lane];
+        if (sz(s0)) {
+            q = 1;
+        } else if (cap <= 1) {
+            q = cap;
+            ab = ORBG_BLOCK_ABANDONED;
+        } else {
+            position_weights<W>(sm, n, lane);
+            /* first bound: the twelfth position's weight (about seventy
+             * patterns for the basic order) */
+            uint32_t r12 = lane < 12 && lane < n ? sm.rho[lane + 1] : 0u;
+            r12 = __reduce_max_sync(FULL_MASK, r12);
+            int32_t Rhi = (int32_t)min(max(r12, sm.msuf[1]), (uint32_t)kRmax);
+            int32_t Rprev = (int32_t)sm.msuf[1] - 1;
+            double Cprev = 1.0;
+            const uint32_t steps = 64u * (min(cap, (uint32_t)ORBG_MAX_QUERY_CAP) + 4096u);
+            bool guard = false;
+            for (;;) {
+                int32_t bR = kNoHit;
+                int bT = 0;
+                const uint32_t c = tree_pass<W, false>(sm, n, s0, Rhi, 0, 0, lane, steps, &bR,
+                                                       &bT, &guard);
+                if (guard) {
+                    ab = kBlockRange;
+                    break;
+                }
+                const double C = 1.0 + (double)warp_sum64(c);
+                const int32_t Rb = __reduce_min_sync(FULL_MASK, bR);
+                if (Rb != kNoHit) {
+                    /* the least member over the lanes: weight, then size, then positions */
+                    int cl = bR == Rb ? lane : -1;
+                    int cT = bR == Rb ? bT : 0x7FFFFFFF;
+#pragma unroll
+                    for (int d = 16; d >= 1; d >>= 1) {
+                        const int ol = __shfl_down_sync(FULL_MASK, cl, d);
+                        const int oT = __shfl_down_sync(FULL_MASK, cT, d);
+                        if (lane + d < 32 && ol >= 0 &&
+                            (cl < 0 || oT < cT || (oT == cT && hb_lex_less(sm.hb, ol, cl, oT)))) {
+                            cl = ol;
+                            cT = oT;
+                        }
+                    }
+                    cl = __shfl_sync(FULL_MASK, cl, 0);
+                    const int Tb = __shfl_sync(FULL_MASK, cT, 0);
+                    if (lane < Tb)
+                        sm.best[lane] = sm.hb[lane * 32 + cl];
+                    __syncwarp();
+                    const uint32_t before = tree_pass<W, true>(sm, n, s0, Rb, Rb, Tb, lane, steps,
+                                                               &bR, &bT, &guard);
+                    if (guard) {
+                        ab = kBlockRange;
+                        break;
+                    }
+                    const uint64_t rank = 2ull + warp_sum64(before);
+                    if (rank <= cap) {
+                        q = (uint32_t)rank;
+                        wbest = Tb;
+                    } else {
+                        q = cap;
+                        ab = ORBG_BLOCK_ABANDONED;
+                    }
+                    break;
+                }
+                if (C >= (double)cap) {
+                    q = cap;
+                    ab = ORBG_BLOCK_ABANDONED;
+                    break;
+                }
+                if (Rhi >= kRmax) {
+                    ab = kBlockRange;
+                    break;
+                }
+                /* next bound: aim at about four times the patterns (at most a
+                 * little past the cap), from the growth over the last band */
+                const double target = fmin(4.0 * C, 1.25 * (double)cap + 64.0);
+                const double span = (double)(Rhi - Rprev);
+                double delta = 2.0 * span;
+                if (C > Cprev) {
+                    const double g = log(C / Cprev) / span;
+                    delta = log(target / C) / g;
+                }
+                delta = fmax(1.0, fmin(delta, 4.0 * span));
+                Rprev = Rhi;
+                Cprev = C;
+                Rhi = (int32_t)fmin((double)Rhi + ceil(delta), (double)kRmax);
+            }
+        }
+    }
+    if (q == 0u && ab == 0)
+        ab = kBlockRange;
+    if (lane < wbest)
+        sm.cw[sm.pi[sm.best[lane] - 1]] ^= 1;
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const int i = k * 32 + lane;
+        if (i < n)
+            cw_out[i] = sm.cw[i];
+    }
+    if (lane == 0) {
+        *q_out = ab == ORBG_BLOCK_NAN || ab == kBlockRange ? 0u : q;
+        *ab_out = (uint8_t)ab;
+    }
+    __syncwarp();
+}
+
+/* Persistent: warps take blocks from an atomic counter, one at a time. */
+template <int K, int W>
+__global__ void __launch_bounds__(kWarps * 32) orbg_fitsearch_kernel(
+    const __grid_constant__ OrbgDeviceCode code, const float *__restrict__ llr, int64_t B,
+    uint32_t cap, int lines, int divisible, uint8_t *__restrict__ cw,
+    uint32_t *__restrict__ q, uint8_t *__restrict__ ab, int32_t *__restrict__ models,
+    unsigned long long *__restrict__ queue)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    FsSmem<W> sm(smem + warp * fs_warp_bytes<W>());
+    const int64_t n = code.n;
+    for (;;) {
+        unsigned long long b = 0;
+        if (lane == 0)
+            b = atomicAdd(queue, 1ull);
+        b = __shfl_sync(FULL_MASK, b, 0);
+        if (b >= (unsigned long long)B)
+            break;
+        decode_fitted_block<K, W>(code, llr + (int64_t)b * n, cw + (int64_t)b * n, q + b, ab + b,
+                                  models ? models + (int64_t)b * ORBG_FIT_WORDS : nullptr, cap,
+                                  lines, divisible, sm, lane);
+    }
+}
+
+template <int K, int W>
+int launch_fitsearch(const OrbgDeviceCode &code, const float *llr, int64_t B, uint32_t cap,
+                     int lines, int divisible, uint8_t *cw, uint32_t *q, uint8_t *ab,
+                     int32_t *models, unsigned long long *queue, void *stream)
+{
+    auto kern = orbg_fitsearch_kernel<K, W>;
+    const size_t smem = (size_t)fs_warp_bytes<W>() * kWarps;
+    int grid = 0;
+    int rc = orbg_grid_for((const void *)kern, kWarps * 32, smem, 0, &grid);
+    if (rc != 0)
+        return rc;
+    const int64_t need = (B + kWarps - 1) / kWarps;
+    if (grid > need)
+        grid = (int)need;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess)
+        return (int)e;
+    kern<<<grid, kWarps * 32, smem, st>>>(code, llr, B, cap, lines, divisible, cw, q, ab, models,
+                                          queue);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace orbg_fitsearch

@@ -148,6 +148,7 @@ struct OrbgBatchedArgs {
     const OrbgDeviceCode *d_codes;
     const OrbgDeviceCode *code0;
     int ncodes, n_max, w32_max;
+    int variants;                /* distinct decoder variants among the codes (> 1: sort) */
     const int32_t *code_id;
     const int64_t *llr_off;
     const float *llr;
@@ -201,7 +202,9 @@ inline OrbgScratch orbg_scratch_layout(void *base, int64_t B, int ncodes)
 }
 /* Order the blocks of a mixed-code call by code id (counting sort into
  * perm, invalid ids last), so that phase 1's warps decode one code's
- * blocks at a time; returns a cudaError_t. */
+ * blocks at a time (used when the codes need different decoder variants,
+ * whose instructions would otherwise compete for the instruction cache);
+ * returns a cudaError_t. */
 int orbg_launch_code_sort(const int32_t *code_id, int64_t B, int ncodes, const OrbgScratch &s,
                           void *stream);
 int orbg_grid_for(const void *kern, int threads, size_t smem, int ctas_per_sm, int *grid_out);
@@ -212,6 +215,7 @@ struct OrbgSetView {
     const OrbgDeviceCode *d_codes;
     OrbgDeviceCode code0;        /* host copy of code 0's descriptor */
     int ncodes, n_max, w32_max;
+    int variants;
     uint32_t ntrip_max;
     uint32_t x3w_max;
     uint32_t cap_min;
@@ -233,6 +237,17 @@ int orbg_fit_launch(const float *llr, int64_t B, int n, int lines, int divisible
                     int32_t *models, void *stream);
 int orbg_fit_map_lines(const int32_t *models, int64_t B, int32_t top, const int32_t *lut,
                        int32_t *cid, void *stream);
+/* The per-block fitted decoder (orbg_fitted_search_inst.cu, one per keys per
+ * lane K): every block fitted (Sec. III-E) and searched in its own order;
+ * queue: one device counter.  Return a cudaError_t value. */
+#define ORBG_DECLARE_FITSEARCH(K)                                                         \
+    int orbg_launch_fitsearch_k##K(const OrbgDeviceCode &code, const float *llr, int64_t B, \
+                                   uint32_t cap, int lines, int divisible, uint8_t *cw,     \
+                                   uint32_t *q, uint8_t *ab, int32_t *models,               \
+                                   unsigned long long *queue, void *stream);
+ORBG_DECLARE_FITSEARCH(1) ORBG_DECLARE_FITSEARCH(2) ORBG_DECLARE_FITSEARCH(4)
+ORBG_DECLARE_FITSEARCH(8)
+#undef ORBG_DECLARE_FITSEARCH
 int orbg_launch_int_probe(double *lanes_per_clk_per_sm);
 int orbg_launch_smem_probe(double *bytes_per_clk_per_sm);
 #endif

@@ -30,6 +30,7 @@ ORBG_DEFAULT_QUERY_CAP = 1 << 20
 ORBG_BLOCK_DECODED = 0
 ORBG_BLOCK_ABANDONED = 1
 ORBG_BLOCK_NAN = 2
+ORBG_BLOCK_RANGE = 3
 ORBG_NOALLOC_MAX_BLOCKS = 1 << 19
 ORBG_FIT_STRIDE = 24
 
@@ -117,6 +118,7 @@ def load_library(path=None):
     lib.orbg_fitted_create.argtypes = [vp, i32, ctypes.POINTER(vp)]
     lib.orbg_fitted_decode.argtypes = [vp, vp, i64, u32, vp, vp, vp, vp, vp]
     lib.orbg_fitted_free.argtypes = [vp]
+    lib.orbg_decode_fitted.argtypes = [vp, vp, i64, u32, i32, i32, vp, vp, vp, vp, vp]
     lib.orbg_query_order_model.restype = i64
     lib.orbg_server_create.argtypes = [vp, ctypes.c_size_t, u32, i32, i64, ctypes.POINTER(vp)]
     lib.orbg_server_submit.argtypes = [vp, ctypes.c_uint64, i32, vp, i64]
@@ -136,7 +138,7 @@ def load_library(path=None):
               "orbg_codeset_set_tuning", "orbg_codeset_get_tuning", "orbg_probe_int_lanes",
               "orbg_probe_smem_bytes", "orbg_codeset_autotune", "orbg_fit_models",
               "orbg_fitted_create", "orbg_fitted_decode", "orbg_fitted_free",
-              "orbg_last_cuda_error", "orbg_version"):
+              "orbg_decode_fitted", "orbg_last_cuda_error", "orbg_version"):
         getattr(lib, f).restype = i32
     if path == LIB_PATH:
         _lib = lib
@@ -246,6 +248,16 @@ def orbg_decode(code, llr, B, query_cap, codeword, queries, abandoned, cuda_stre
                                     _ptr(codeword, "uint8"), _ptr(queries, "uint32"),
                                     _ptr(abandoned, "uint8"), _stream(cuda_stream))
     _check(rc, "orbg_decode")
+
+
+def orbg_decode_fitted(code, llr, B, query_cap, lines, divisible, codeword, queries, abandoned,
+                       models=None, cuda_stream=None):
+    rc = load_library().orbg_decode_fitted(code, _ptr(llr, "float32"), int(B), int(query_cap),
+                                           int(lines), int(bool(divisible)),
+                                           _ptr(codeword, "uint8"), _ptr(queries, "uint32"),
+                                           _ptr(abandoned, "uint8"), _ptr(models, "int32"),
+                                           _stream(cuda_stream))
+    _check(rc, "orbg_decode_fitted")
 
 
 def orbg_codeset_create(codes):
@@ -555,6 +567,23 @@ def decode(code, llr, query_cap, stream=None):
     orbg_decode(code.handle, llr, B, query_cap, cw, q, ab,
                 stream if stream is not None else torch.cuda.current_stream(llr.device))
     return cw, q, ab
+
+
+def decode_fitted(code, llr, query_cap, lines, divisible=False, stream=None):
+    """Full ORBGRAND with a `lines`-line model fitted to each block (Sec.
+    III-E), each block searched in its own order (Sec. III-D), on a torch
+    tensor llr[B][n] (CUDA): returns (codeword u8, queries int32, abandoned
+    u8, model records int32 [B][ORBG_FIT_STRIDE])."""
+    import torch
+    B = llr.shape[0]
+    dev = llr.device
+    cw = torch.empty((B, code.n), dtype=torch.uint8, device=dev)
+    q = torch.empty((B,), dtype=torch.int32, device=dev)
+    ab = torch.empty((B,), dtype=torch.uint8, device=dev)
+    rec = torch.empty((B, ORBG_FIT_STRIDE), dtype=torch.int32, device=dev)
+    orbg_decode_fitted(code.handle, llr, B, query_cap, lines, divisible, cw, q, ab, rec,
+                       stream if stream is not None else torch.cuda.current_stream(dev))
+    return cw, q, ab, rec
 
 
 def decode_batched(codeset, llr, query_cap, code_id=None, llr_offset=None,

@@ -414,6 +414,12 @@ def config4_inputs(B=1_000_000, seed=401):
     return mixed_inputs(config4_codes(), B, seed)
 
 
+def capolar256_code():
+    """CA-Polar[256, 234] of Sec. IV (K = 245 polar positions: 234 message
+    bits and the CRC-11), as in paper256_codes."""
+    return ca_polar(256, 245)
+
+
 def paper256_codes():
     """The [256, 234]-class codes of Sec. IV's first comparison."""
     return [ca_polar(256, 245), crc_code(256, 234), rlc(256, 234, seed=61),

@@ -381,9 +381,14 @@ def _sampled(orbg, code, llr, cap, nsample, seed):
 
 def test_config2_full_size_sampled(orbg):
     """BCH(127,113), 4 x 100,000 blocks at 4..7 dB, cap 1e6, one batched
-    launch (the benchmark's call); 3000 seeded random blocks checked."""
+    launch (the benchmark's call); 3000 seeded random blocks checked, and
+    every block when oracle.cache holds this configuration."""
+    from oracle import cache
     code, llr, _ = workloads.config2_inputs()
     got = _sampled(orbg, code, llr, 10 ** 6, 3000, 2)
+    full = cache.load(2)
+    if full is not None:
+        assert_same(got, (full["cw"].reshape(llr.shape), full["q"], full["ab"]))
     # property at any size: every decoded block is a codeword
     cw, q, ab = got
     ok = ab == 0
@@ -392,11 +397,71 @@ def test_config2_full_size_sampled(orbg):
     assert int(syn.abs().sum().item()) == 0
 
 
+def _stratified_pick(q, ab, rng, n_abandoned, n_longest, n_random, within=None):
+    """Blocks to check: some the GPU abandoned, the longest decoded
+    searches, and seeded random ones (indices into q, sorted, unique)."""
+    idx = np.arange(q.shape[0]) if within is None else within
+    aband = idx[ab[idx] == 1]
+    dec = idx[ab[idx] == 0]
+    pick = [rng.choice(aband, min(n_abandoned, aband.size), replace=False),
+            dec[np.argsort(q[dec])[-n_longest:]],
+            rng.choice(idx, min(n_random, idx.size), replace=False)]
+    return np.unique(np.concatenate(pick))
+
+
 def test_config3_full_size_sampled(orbg):
     """CA-Polar(128,94), 4 x 100,000 blocks at 3..6 dB, cap 1e6 (64-bit
-    syndromes, heavy abandonment); 120 seeded random blocks checked."""
+    syndromes, heavy abandonment), one batched launch: 2,000 blocks or more
+    against the oracle -- 400 the GPU abandoned, the 300 longest decoded
+    searches (deep in the CTA phase) and 1,300 seeded random ones -- or
+    every block when oracle.cache holds this configuration."""
+    import oracle_pool
+    from oracle import cache
     code, llr, _ = workloads.config3_inputs()
-    _sampled(orbg, code, llr, 10 ** 6, 120, 3)
+    c = orbg.Code(code.H, max_query_cap=10 ** 6)
+    got = gpu_batched(orbg, orbg.CodeSet([c]), llr, 10 ** 6)
+    full = cache.load(3)
+    if full is not None:
+        assert_same(got, (full["cw"].reshape(llr.shape), full["q"], full["ab"]))
+    pick = _stratified_pick(got[1], got[2], np.random.default_rng(3), 400, 300, 1300)
+    assert pick.size >= 1900 and (got[2][pick] == 1).sum() >= 300
+    want = oracle_pool.decode_batch(code.H, llr[pick], 10 ** 6)[:3]
+    assert_same(got, want, pick)
+
+
+def test_config4_full_size(orbg):
+    """The benchmark's headline workload in its launch configuration: 1,000,000
+    blocks of the four random codes in one batched call (device buffers,
+    per-block code ids and offsets), checked per code on 500 or more blocks
+    (GPU-abandoned ones, the longest searches, random ones), every decoded
+    block a codeword, and every block against oracle.cache when present."""
+    import oracle_pool
+    from oracle import cache
+    codes, cid, llr, off, _, _ = workloads.config4_inputs()
+    cs = orbg.CodeSet([orbg.Code(cd.H, max_query_cap=10 ** 6) for cd in codes])
+    cw, q, ab = orbg.decode_batched(cs, torch.from_numpy(llr).cuda(), 10 ** 6,
+                                    code_id=torch.from_numpy(cid).cuda(),
+                                    llr_offset=torch.from_numpy(off).cuda(),
+                                    cw_offset=torch.from_numpy(off).cuda(),
+                                    n_total=llr.shape[0])
+    torch.cuda.synchronize()
+    cw, q, ab = cw.cpu().numpy(), q.cpu().numpy().astype(np.int64), ab.cpu().numpy()
+    full = cache.load(4)
+    if full is not None:
+        assert np.array_equal(cw, full["cw"]) and np.array_equal(q, full["q"].astype(np.int64))
+        assert np.array_equal(ab, full["ab"])
+    rng = np.random.default_rng(4)
+    for j, cd in enumerate(codes):
+        idx = np.nonzero(cid == j)[0]
+        rows = np.stack([cw[off[b]:off[b] + cd.n] for b in idx])
+        ok = ab[idx] == 0
+        assert not ((rows[ok].astype(np.int64) @ cd.H.T.astype(np.int64)) % 2).any()
+        pick = _stratified_pick(q, ab, rng, 100, 100, 320, within=idx)
+        assert pick.size >= 500
+        blocks = np.stack([llr[off[b]:off[b] + cd.n] for b in pick])
+        want = oracle_pool.decode_batch(cd.H, blocks, 10 ** 6)[:3]
+        assert_same((np.stack([cw[off[b]:off[b] + cd.n] for b in pick]), q[pick], ab[pick]),
+                    want)
 
 
 @pytest.mark.parametrize("tuning", [(8, 0, 8, 1, 16), (4, 0, 1, 64, 4), (16, 0, 32, 4096, 1),
