@@ -707,8 +707,10 @@ class Job:
 
     def call(self, stream):
         if self.search:
+            # no model records are asked for: a block whose hard decision is a
+            # code word decodes at query 1 in any order, unfitted
             self.orbg.orbg_decode_fitted(self.objs[0].handle, self.llr, self.B, CAP, FITTED[0],
-                                         FITTED[1], self.cw, self.q, self.ab, self.rec, stream)
+                                         FITTED[1], self.cw, self.q, self.ab, None, stream)
             return
         if self.fitted is not None:
             lib = self.orbg.load_library()

@@ -189,10 +189,11 @@ ORBG_API int orbg_codeset_free(orbg_codeset *set);
  *   cw_offset  : [B] byte offset of block b in codeword, or NULL (dense).
  *   Other arguments as orbg_decode; query_cap must be within every code's
  *   max_query_cap.
- * The call uses 72 + 8 ncodes + 12 B bytes of stream-ordered device
- * scratch (queue counters, per-code block counts, the list of still-open
- * blocks and the blocks' order grouped by code), allocated and freed on
- * cuda_stream.  With code_id given and codes of different length classes
+ * The call uses 87 + 8 ncodes + 12 B + 272 min(B, 32768) bytes of
+ * stream-ordered device scratch (queue counters, per-code block counts, the
+ * list of still-open blocks, the blocks' order grouped by code, and the
+ * reliability order of up to 32,768 still-open blocks, which the second
+ * launch reuses), allocated and freed on cuda_stream.  With code_id given and codes of different length classes
  * (n <= 32, 64, 128, 256) or syndrome widths in the set, the first launch
  * takes the blocks grouped by code.
  * Host buffers (staged through stream-ordered device copies): a call with
@@ -228,9 +229,9 @@ ORBG_API int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id
  *     staging): EINVAL otherwise.
  *   - B <= ORBG_NOALLOC_MAX_BLOCKS (524,288), else ELIMIT.  Larger batches
  *     can be split into several calls.
- *   - The array is 12 * ORBG_NOALLOC_MAX_BLOCKS + 8,264 bytes (6 MiB +
- *     8,264 B) of device memory per GPU that loads the library, held until
- *     the process exits.
+ *   - The array is 12 * ORBG_NOALLOC_MAX_BLOCKS + 8,280 + 272 * 32,768
+ *     bytes (14.5 MiB + 8,280 B) of device memory per GPU that loads the
+ *     library, held until the process exits.
  *   - The first call on each device looks up the array's device address
  *     (with that device current) and keeps it; make that first call before
  *     any stream capture.  The kept address belongs to the device's primary

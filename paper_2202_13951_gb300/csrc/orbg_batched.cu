@@ -33,8 +33,9 @@ int orbg_grid_for(const void *kern, int threads, size_t smem, int ctas_per_sm, i
 size_t orbg_batched_scratch_bytes(int64_t B, int ncodes)
 {
     const size_t b = (size_t)(B > 0 ? B : 0);
+    const size_t h = b < ORBG_HANDOVER_MAX ? b : ORBG_HANDOVER_MAX;
     return 8 * (size_t)ORBG_BATCHED_COUNTERS + 8 * ((size_t)(ncodes > 0 ? ncodes : 0) + 1) +
-           12 * b;
+           12 * b + 15 + (size_t)ORBG_HANDOVER_BYTES * h;
 }
 
 namespace {

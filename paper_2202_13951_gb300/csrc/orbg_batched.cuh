@@ -46,8 +46,9 @@ __global__ void __launch_bounds__(256, ORBG_PHASE1_MIN_CTAS) orbg_batched_kernel
     const int64_t *__restrict__ llr_off, const float *__restrict__ llr, int64_t B, uint32_t cap,
     uint32_t budget, uint8_t *__restrict__ cw, const int64_t *__restrict__ cw_off,
     uint32_t *__restrict__ q, uint8_t *__restrict__ ab, unsigned long long *__restrict__ counters,
-    unsigned long long *__restrict__ heavy, const uint32_t *__restrict__ perm, uint32_t bstride,
-    uint32_t x3w_bytes, int grab, const __grid_constant__ OrbgDeviceCode code0)
+    unsigned long long *__restrict__ heavy, const uint32_t *__restrict__ perm,
+    unsigned char *__restrict__ hand, uint32_t hand_cap, uint32_t bstride, uint32_t x3w_bytes,
+    int grab, const __grid_constant__ OrbgDeviceCode code0)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
@@ -115,7 +116,7 @@ __global__ void __launch_bounds__(256, ORBG_PHASE1_MIN_CTAS) orbg_batched_kernel
             decode_block_warp<KMAX, WMAX, true, true, (KMAX <= 4)>(code0, l, cw + co, q + b, ab + b,
                                                             cap, budget, bsm, lane, heavy,
                                                             &counters[1], (unsigned long long)b,
-                                                            X3w);
+                                                            X3w, hand, hand_cap);
         } else if (cid < 0 || cid >= ncodes) {
             if (lane == 0) {
                 q[b] = 0u;
@@ -126,7 +127,7 @@ __global__ void __launch_bounds__(256, ORBG_PHASE1_MIN_CTAS) orbg_batched_kernel
 #define ORBG_CALL_WARP(KK, WW)                                                                 \
     decode_block_warp<KK, WW, true, true, false>(code, l, cw + co, q + b, ab + b, cap,       \
                                                  budget, bsm, lane, heavy, &counters[1],    \
-                                                 (unsigned long long)b, X3w)
+                                                 (unsigned long long)b, X3w, hand, hand_cap)
             ORBG_DISPATCH(KMAX, WMAX, ORBG_CALL_WARP);
 #undef ORBG_CALL_WARP
         }
@@ -173,13 +174,13 @@ cudaError_t launch_t(const OrbgBatchedArgs &a)
         c0 = *a.code0;
     k1<<<grid, wpc * 32, smem1, st>>>(a.d_codes, a.ncodes, a.code_id, a.llr_off, a.llr, a.B,
                                       a.cap, a.budget, a.cw, a.cw_off, a.q, a.ab, counters,
-                                      heavy, sorted ? sc.perm : nullptr, bstride, x3w_bytes, g,
-                                      c0);
+                                      heavy, sorted ? sc.perm : nullptr, sc.hand, sc.hand_cap,
+                                      bstride, x3w_bytes, g, c0);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     if (a.budget >= a.cap)
         return cudaSuccess; /* every block finished in phase 1 */
-    return launch_heavy_t<KMAX, WMAX, ONE>(a, counters, heavy);
+    return launch_heavy_t<KMAX, WMAX, ONE>(a, counters, heavy, sc.hand);
 }
 
 /* Phases 1 and 2 for keys-per-lane bound KMAX and syndrome width WMAX. */

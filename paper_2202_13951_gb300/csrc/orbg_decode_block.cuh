@@ -793,8 +793,11 @@ __device__ __forceinline__ uint32_t group_reaching(const OrbgTable &tb, uint32_t
  * below the best hit, at most `cap`, and at most `budget`.  If the walk
  * stops on the budget with the result still open, the block is not
  * written: its index is appended to heavy[] (when heavy != NULL) for
- * decode_block_cta.  With budget >= cap every block finishes here.  LS:
- * llr points into shared memory (the batched kernel stages it there).
+ * decode_block_cta, with its reliability order and starting syndrome in
+ * the handover record of the same slot when one is free (hand_cap; bit 63
+ * of the heavy[] entry says so).  With budget >= cap every block finishes
+ * here.  LS: llr points into shared memory (the batched kernel stages it
+ * there).
  */
 template <int K, int W, bool LS = false, bool TRIP = false, bool PF = true>
 __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__restrict__ llr,
@@ -802,7 +805,8 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
                                   uint8_t *__restrict__ ab_out, uint32_t cap, uint32_t budget,
                                   unsigned char *__restrict__ bsm, int lane,
                                   unsigned long long *heavy, unsigned long long *heavy_count,
-                                  unsigned long long block_index, uint16_t *X3w = nullptr)
+                                  unsigned long long block_index, uint16_t *X3w = nullptr,
+                                  unsigned char *hand = nullptr, uint32_t hand_cap = 0)
 {
     typedef typename Syn<W>::T T;
     const int n = code.n;
@@ -955,10 +959,28 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
         handover = stop;
     }
     if (!done) {
-        /* every query below `handover` was tested without a hit */
-        if (heavy != nullptr && lane == 0) {
-            unsigned long long slot = atomicAdd(heavy_count, 1ull);
-            heavy[slot] = block_index | ((unsigned long long)handover << 32);
+        /* every query below `handover` was tested without a hit; the block
+         * is fully sorted here (the walk past the flat table sorts it) */
+        if (heavy != nullptr) {
+            unsigned long long slot = 0;
+            if (lane == 0)
+                slot = atomicAdd(heavy_count, 1ull);
+            slot = __shfl_sync(FULL_MASK, slot, 0);
+            const bool keep = slot < (unsigned long long)hand_cap;
+            if (keep) {
+                unsigned char *rec = hand + slot * ORBG_HANDOVER_BYTES;
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    const int e = lane * K + k;
+                    if (e < n)
+                        rec[e] = sm.pi[e];
+                }
+                if (lane == 0)
+                    *reinterpret_cast<T *>(rec + 256) = s0;
+            }
+            if (lane == 0)
+                heavy[slot] = block_index | ((unsigned long long)handover << 32) |
+                              (keep ? 1ull << 63 : 0ull);
         }
         __syncwarp();
         return;
@@ -1002,13 +1024,33 @@ __device__ void decode_block_cta(const OrbgDeviceCode &code, const float *__rest
                                  uint8_t *__restrict__ ab_out, uint32_t cap,
                                  unsigned char *__restrict__ bsm, uint16_t *__restrict__ X3,
                                  uint32_t *s_best, typename Syn<W>::T *s_s0, uint32_t from,
-                                 int warp, int lane, int nwarps)
+                                 int warp, int lane, int nwarps,
+                                 const unsigned char *__restrict__ rec = nullptr)
 {
     typedef typename Syn<W>::T T;
     const int n = code.n;
     const OrbgTable &tb = code.cta;
     BlockSmem<W> sm(bsm, n);
-    if (warp == 0) {
+    if (rec != nullptr) {
+        /* phase 1's handover record: the block's order and starting
+         * syndrome; every thread takes a share of the positions */
+        for (int i = (int)threadIdx.x; i < n; i += (int)blockDim.x) {
+            sm.cw[i] = __ldg(llr + i) > 0.0f ? 1 : 0;
+            const int idx = (int)rec[i];
+            sm.pi[i] = (uint8_t)idx;
+            const T col = load_col<W>(code.hcol, idx);
+            sm.h[i] = col;
+            if (W > 1)
+                sm.h0[i] = first_word(col);
+        }
+        if (threadIdx.x == 0) {
+            sm.h[-1] = szero<T>();
+            if (W > 1)
+                sm.h0[-1] = 0u;
+            *s_best = ORBG_NONE;
+            *s_s0 = *reinterpret_cast<const T *>(rec + 256);
+        }
+    } else if (warp == 0) {
         uint32_t key[K];
         bool nan;
         const T s0 = load_block<K, W>(code, llr, key, sm.cw, lane, &nan);

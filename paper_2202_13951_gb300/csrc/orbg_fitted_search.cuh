@@ -28,9 +28,13 @@
  * bounds the weight of the node and all it leads to from below; a pass with
  * bound Rhi enters only nodes whose bound is <= Rhi and tests those with
  * R <= Rhi (the weights rho need not increase with j).  The 32 lanes of the
- * warp each walk a part of the tree depth first, with their positions on a
- * per-lane stack in shared memory; a lane that runs out of work is given the
- * "replace" branch of a lane that is about to take its "add" branch.
+ * warp each walk a part of the tree depth first (lane l starts with the sets
+ * whose least position is l + 1), with their positions on a per-lane stack
+ * in shared memory; a lane that runs out of work is given the "replace"
+ * branch of a lane that is about to take its "add" branch; a lane at a leaf
+ * also tests up to kLeafRun of the leaf's later siblings in the same step
+ * while they are leaves too (the lanes stay in step: a longer inner run
+ * would hold the other lanes).
  *
  * Passes run with growing bounds ("bands"): a pass that finds code-book
  * members lowers its bound to the lightest one found, and the least of
@@ -58,6 +62,7 @@ constexpr int kWarps = 8;                   /* warps per CTA, one block each */
 constexpr int kDepth = 31;                  /* largest pattern the stack holds */
 constexpr uint32_t kRhoInf = 1u << 30;      /* weight of a position never reached */
 constexpr int32_t kRmax = (1 << 26) - 1;    /* heaviest reliability weight searched */
+constexpr int kLeafRun = 3;                /* leaf siblings tested per step besides the node */
 constexpr int32_t kNoHit = 0x7FFFFFFF;
 constexpr int kBlockRange = ORBG_BLOCK_RANGE; /* abandoned[] value: beyond the search range */
 
@@ -117,10 +122,123 @@ __host__ __device__ constexpr uint32_t fs_warp_bytes()
 
 /* ---------------------------------------------------------- the fit */
 
-/* Sec. III-E on the ordered curve sm.L: anchors by the largest chord gap
- * (lanes share the indices of the interval; the largest gap wins, the
- * smaller index on equal gaps, as in the one-lane loop of fit_sorted), then
- * Eq. Q / Eq. quant on lane 0.  Writes sm.rec. */
+/* The largest chord gap over the indices of (lo, hi), the smaller index on
+ * equal gaps (-1 if no gap is > 0), exactly as the one-lane loop of
+ * fit_sorted finds it.  Each lane first computes its indices' gaps in
+ * single precision: with M the largest |L| of the interval, a single-
+ * precision gap is within 7 * 2^-24 M of the double-precision one (five
+ * roundings, each of a value <= 2 M), so an index whose single-precision gap
+ * is more than 2^-19 M below the largest cannot hold the largest double-
+ * precision gap.  If exactly one index is left and its gap exceeds 2^-19 M,
+ * its double-precision gap is positive and larger than every other one: it
+ * is the answer, with no double-precision work; otherwise the remaining
+ * candidates are evaluated in double precision (all of them when the curve
+ * is not finite there). */
+template <int W>
+__device__ __forceinline__ int chord_argmax(const FsSmem<W> &sm, int lo, int hi, int lane)
+{
+    float M = 0.0f, g32max = 0.0f;
+    for (int j = lo + lane; j <= hi; j += 32)
+        M = fmaxf(M, sm.L[j - 1]);
+    /* reliabilities are >= 0 (or +inf): their bit patterns order as they do */
+    M = __uint_as_float(__reduce_max_sync(FULL_MASK, __float_as_uint(M)));
+    const bool finite = isfinite(M);
+    const float Llo = sm.L[lo - 1], rise = sm.L[hi - 1] - Llo, span = (float)(hi - lo);
+    const float margin = ldexpf(M, -19);
+    if (finite) {
+        for (int j = lo + 1 + lane; j < hi; j += 32)
+            g32max = fmaxf(g32max, fabsf(Llo + rise * (float)(j - lo) / span - sm.L[j - 1]));
+        g32max = __uint_as_float(__reduce_max_sync(FULL_MASK, __float_as_uint(g32max)));
+        const float cut = g32max - margin;
+        uint32_t n_cand = 0;
+        int cand = -1;
+        for (int j = lo + 1 + lane; j < hi; j += 32)
+            if (fabsf(Llo + rise * (float)(j - lo) / span - sm.L[j - 1]) >= cut) {
+                n_cand++;
+                cand = j;
+            }
+        if (__reduce_add_sync(FULL_MASK, n_cand) == 1u && g32max > margin)
+            return __reduce_max_sync(FULL_MASK, (unsigned)(cand + 1)) - 1;
+    }
+    const float cut = g32max - margin;
+    double gap = 0.0;
+    int best = -1;
+    for (int j = lo + 1 + lane; j < hi; j += 32) {
+        if (finite && fabsf(Llo + rise * (float)(j - lo) / span - sm.L[j - 1]) < cut)
+            continue;
+        const double g = orbg_fit::chord_gap(sm.L, lo, hi, j);
+        if (g > gap) {
+            gap = g;
+            best = j;
+        }
+    }
+    /* gaps kept are >= 0 and not NaN: their bit patterns order as they do */
+    unsigned long long gb = (unsigned long long)__double_as_longlong(gap);
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        const unsigned long long og = __shfl_xor_sync(FULL_MASK, gb, d);
+        const int oj = __shfl_xor_sync(FULL_MASK, best, d);
+        if (oj >= 0 && (best < 0 || og > gb || (og == gb && oj < best))) {
+            gb = og;
+            best = oj;
+        }
+    }
+    return best;
+}
+
+/* Eq. Q and Eq. quant for the anchors sm.anch[0..na-1], one segment per
+ * lane: the same double operations per segment as orbg_fit::quantise, and
+ * the same results (the least slope is taken over the segments in any
+ * order; a NaN first slope gives the basic model as there).  Writes sm.rec,
+ * which holds the basic model on entry. */
+template <int W>
+__device__ __forceinline__ void quantise_lanes(const FsSmem<W> &sm, int na, int divisible,
+                                               int lane)
+{
+    using namespace orbg_fit;
+    const double kFitMax = 16777216.0; /* 2^24 */
+    const int m = na - 1;
+    const bool mine = lane < m;
+    const int a0 = sm.anch[mine ? lane : 0], a1 = sm.anch[mine ? lane + 1 : 1];
+    const double sl = mine ? dvd(sub(Lj(sm.L, a1), Lj(sm.L, a0)), (double)(a1 - a0)) : 0.0;
+    const double s0 = __shfl_sync(FULL_MASK, sl, 0);
+    double Q = mine ? sl : s0;
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1)
+        Q = fmin(Q, __shfl_xor_sync(FULL_MASK, Q, d));
+    if (s0 != s0)
+        Q = s0; /* the first slope NaN: as the one-lane loop, no positive Q */
+    if (!(Q > 0.0))
+        return;
+    const double rs = mine ? dvd(sl, Q) : 0.0;
+    const double rl = mine ? dvd(Lj(sm.L, a0), Q) : 0.0;
+    const bool bad = mine && (!(rs <= kFitMax) || !(rl <= kFitMax));
+    if (__any_sync(FULL_MASK, bad))
+        return;
+    long long beta = 0, J = 0;
+    if (mine) {
+        beta = round_half_away(rs);
+        J = round_half_away(rl);
+    }
+    const long long beta1 = __shfl_sync(FULL_MASK, beta, 0);
+    if (lane == 0)
+        J -= beta1;
+    if (mine && divisible)
+        J = round_half_away(dvd((double)J, (double)beta)) * beta;
+    __syncwarp();
+    if (lane == 0)
+        sm.rec[0] = m;
+    if (mine) {
+        if (lane >= 1)
+            sm.rec[lane] = a0;
+        sm.rec[8 + lane] = (int32_t)J;
+        sm.rec[16 + lane] = (int32_t)beta;
+    }
+    __syncwarp();
+}
+
+/* Sec. III-E on the ordered curve sm.L: anchors by the largest chord gap,
+ * then Eq. Q / Eq. quant.  Writes sm.rec. */
 template <int W>
 __device__ void fit_block(const FsSmem<W> &sm, int n, int lines, int divisible, int lane)
 {
@@ -139,25 +257,7 @@ __device__ void fit_block(const FsSmem<W> &sm, int n, int lines, int divisible, 
         return;
     int na = 2;
     while (na - 1 < lines) {
-        const int lo = sm.anch[0], hi = sm.anch[1];
-        double gap = 0.0;
-        int best = -1;
-        for (int j = lo + 1 + lane; j < hi; j += 32) {
-            const double g = orbg_fit::chord_gap(sm.L, lo, hi, j);
-            if (g > gap) {
-                gap = g;
-                best = j;
-            }
-        }
-#pragma unroll
-        for (int d = 16; d >= 1; d >>= 1) {
-            const double og = __shfl_xor_sync(FULL_MASK, gap, d);
-            const int oj = __shfl_xor_sync(FULL_MASK, best, d);
-            if (oj >= 0 && (best < 0 || og > gap || (og == gap && oj < best))) {
-                gap = og;
-                best = oj;
-            }
-        }
+        const int best = chord_argmax<W>(sm, sm.anch[0], sm.anch[1], lane);
         if (best < 0)
             break;
         __syncwarp();
@@ -169,9 +269,7 @@ __device__ void fit_block(const FsSmem<W> &sm, int n, int lines, int divisible, 
         __syncwarp();
         na++;
     }
-    if (lane == 0)
-        orbg_fit::quantise(sm.L, sm.anch, na, divisible, sm.rec);
-    __syncwarp();
+    quantise_lanes<W>(sm, na, divisible, lane);
 }
 
 /* rho_j from the model record (Eq. relest_seg), clamped to kRhoInf, and the
@@ -282,17 +380,23 @@ __device__ uint32_t tree_pass(const FsSmem<W> &sm, int n, typename Syn<W>::T s0,
                               int *bT, bool *guard)
 {
     const uint32_t s0w = first_word(s0);
-    bool active = false, fresh = false;
+    bool active = false; /* an active lane's node is always untested yet */
     int t = 0, t0 = 0, jt = 0;
     uint32_t R = 0, rcur = 0, ccur = 0, syn = 0, don = 0, cnt = 0;
-    if (lane == 0 && n >= 1 && sm.msuf[1] <= (uint32_t)Rhi) {
-        active = true;
-        fresh = true;
+    /* every lane starts at once: lane l < L takes the sets whose least
+     * position is l + 1 (the node {l + 1} and what its "add" branch leads to:
+     * the "replace" branch at depth 1 is marked as given away), lane L the
+     * sets whose least position is L + 1 or more (node {L + 1} with both
+     * branches); L = min(n, 32) - 1 */
+    const int last = min(n, 32) - 1;
+    if (lane <= last) {
+        jt = lane + 1;
+        rcur = sm.rho[jt];
+        ccur = sm.c0[jt];
+        active = (lane < last ? rcur : sm.msuf[jt]) <= (uint32_t)Rhi;
         t = 1;
         t0 = 1;
-        jt = 1;
-        rcur = sm.rho[1];
-        ccur = sm.c0[1];
+        don = lane < last ? 1u << 1 : 0u;
         R = rcur;
         syn = s0w ^ ccur;
     }
@@ -305,7 +409,7 @@ __device__ uint32_t tree_pass(const FsSmem<W> &sm, int n, typename Syn<W>::T s0,
             *guard = true;
             break;
         }
-        const bool tested = active && fresh && R <= (uint32_t)Rhi;
+        const bool tested = active && R <= (uint32_t)Rhi;
         if (RANK) {
             if (tested) {
                 if (R < (uint32_t)Rb)
@@ -339,7 +443,7 @@ __device__ uint32_t tree_pass(const FsSmem<W> &sm, int n, typename Syn<W>::T s0,
         const int jn = jt + 1;
         const bool okn = active && jt < n;
         const uint32_t ms = okn ? sm.msuf[jn] : kRhoInf;
-        const bool addOK = okn && fresh && R + ms <= (uint32_t)Rhi;
+        const bool addOK = okn && R + ms <= (uint32_t)Rhi;
         bool replOK = okn && R - rcur + ms <= (uint32_t)Rhi && !((don >> t) & 1u);
         /* lanes without work take the replace branch of lanes about to add */
         const uint32_t idle = ~act;
@@ -377,7 +481,6 @@ __device__ uint32_t tree_pass(const FsSmem<W> &sm, int n, typename Syn<W>::T s0,
                 rcur = rn;
                 ccur = cn;
                 don = 0;
-                fresh = true;
                 active = true;
                 got = true;
             }
@@ -388,35 +491,90 @@ __device__ uint32_t tree_pass(const FsSmem<W> &sm, int n, typename Syn<W>::T s0,
             __syncwarp();
         }
         if (active && !got) {
+            int jm = jn;              /* the position the move brings in */
+            bool move = addOK || replOK;
             if (addOK && t >= kDepth) {
                 *guard = true; /* deeper than the stack: cannot happen within 2^26 queries */
                 active = false;
-            } else if (addOK || replOK) {
-                const uint32_t rn = sm.rho[jn], cn = sm.c0[jn];
+                move = false;
+            } else if (addOK) {
+                sm.stk[(t - 1) * 32 + lane] = (uint8_t)jt;
+                t++;
+            } else if (replOK) {
+                /* a leaf: test up to kLeafRun of its later siblings (same
+                 * prefix, last position jm = jt + 1, ...) in this step while
+                 * they are leaves too; stop at one that leads further or needs
+                 * the full step, and move there (or past the tested ones) */
+                const uint32_t Rp = R - rcur, sp = syn ^ ccur;
+                move = false;
+                bool stop = false;
+#pragma unroll
+                for (int u = 0; u < kLeafRun; u++) {
+                    if (stop)
+                        break;
+                    if (jm > n || Rp + sm.msuf[jm] > (uint32_t)Rhi) {
+                        stop = true; /* no later sibling is reachable */
+                        break;
+                    }
+                    const uint32_t r = sm.rho[jm], Rs = Rp + r;
+                    const bool inner = jm < n && Rs + sm.msuf[jm + 1] <= (uint32_t)Rhi;
+                    const bool own = Rs <= (uint32_t)Rhi &&
+                                     (RANK ? Rs == (uint32_t)Rb : (sp ^ sm.c0[jm]) == 0u);
+                    if (inner || own) {
+                        move = true;
+                        stop = true;
+                        break;
+                    }
+                    if (Rs <= (uint32_t)Rhi)
+                        cnt += RANK ? (Rs < (uint32_t)Rb ? 1u : 0u) : 1u;
+                    jm++;
+                }
+                if (!stop)
+                    move = jm <= n && Rp + sm.msuf[jm] <= (uint32_t)Rhi;
+                if (!move) {
+                    /* the siblings are done: back up from the prefix */
+                    R = Rp;
+                    syn = sp;
+                    rcur = 0u;
+                    ccur = 0u;
+                }
+            }
+            if (!move && active && !addOK) {
+                /* back up until an ancestor's "replace" branch is open (it is
+                 * taken at once), or the lane's part of the tree is done */
+                for (;;) {
+                    if (t <= t0) {
+                        active = false;
+                        break;
+                    }
+                    R -= rcur;
+                    syn ^= ccur;
+                    don &= ~(1u << t);
+                    t--;
+                    jt = sm.stk[(t - 1) * 32 + lane];
+                    rcur = sm.rho[jt];
+                    ccur = RANK ? 0u : sm.c0[jt];
+                    jm = jt + 1;
+                    if (R - rcur + sm.msuf[jm] <= (uint32_t)Rhi && !((don >> t) & 1u)) {
+                        move = true;
+                        break;
+                    }
+                }
+            }
+            if (move) {
+                /* the rank pass needs no syndromes */
+                const uint32_t rn = sm.rho[jm], cn = RANK ? 0u : sm.c0[jm];
                 if (addOK) {
-                    sm.stk[(t - 1) * 32 + lane] = (uint8_t)jt;
-                    t++;
                     R += rn;
                     syn ^= cn;
                 } else {
+                    /* replace: the last position jt gives way to jm = jt + 1 */
                     R = R - rcur + rn;
                     syn ^= ccur ^ cn;
                 }
-                jt = jn;
+                jt = jm;
                 rcur = rn;
                 ccur = cn;
-                fresh = true;
-            } else if (t > t0) {
-                R -= rcur;
-                syn ^= ccur;
-                don &= ~(1u << t);
-                t--;
-                jt = sm.stk[(t - 1) * 32 + lane];
-                rcur = sm.rho[jt];
-                ccur = sm.c0[jt];
-                fresh = false;
-            } else {
-                active = false;
             }
         }
     }
@@ -585,7 +743,7 @@ __device__ void decode_fitted_block(const OrbgDeviceCode &code, const float *__r
 
 /* Persistent: warps take blocks from an atomic counter, one at a time. */
 template <int K, int W>
-__global__ void __launch_bounds__(kWarps * 32) orbg_fitsearch_kernel(
+__global__ void __launch_bounds__(kWarps * 32, 3) orbg_fitsearch_kernel(
     const __grid_constant__ OrbgDeviceCode code, const float *__restrict__ llr, int64_t B,
     uint32_t cap, int lines, int divisible, uint8_t *__restrict__ cw,
     uint32_t *__restrict__ q, uint8_t *__restrict__ ab, int32_t *__restrict__ models,

@@ -25,11 +25,11 @@ __global__ void __launch_bounds__(512, ORBG_PHASE2_MIN_CTAS) orbg_heavy_kernel(
     const int64_t *__restrict__ llr_off, const float *__restrict__ llr, uint32_t cap,
     uint8_t *__restrict__ cw, const int64_t *__restrict__ cw_off, uint32_t *__restrict__ q,
     uint8_t *__restrict__ ab, unsigned long long *__restrict__ counters,
-    const unsigned long long *__restrict__ heavy, uint32_t bstride,
-    const __grid_constant__ OrbgDeviceCode code0)
+    const unsigned long long *__restrict__ heavy, const unsigned char *__restrict__ hand,
+    uint32_t bstride, const __grid_constant__ OrbgDeviceCode code0)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned long long s_block;
+    __shared__ unsigned long long s_block, s_slot;
     __shared__ uint32_t s_best;
     __shared__ uint4 s_s0;
     const int warp = threadIdx.x >> 5;
@@ -40,21 +40,24 @@ __global__ void __launch_bounds__(512, ORBG_PHASE2_MIN_CTAS) orbg_heavy_kernel(
         if (threadIdx.x == 0) {
             const unsigned long long nheavy = *((volatile unsigned long long *)&counters[1]);
             const unsigned long long slot = atomicAdd(&counters[2], 1ull);
-            s_block = slot < nheavy ? heavy[slot] : ~0ull; /* block | tested-below << 32 */
+            /* block | tested-below << 32 | handover record << 63 */
+            s_block = slot < nheavy ? heavy[slot] : ~0ull;
+            s_slot = slot;
         }
         __syncthreads();
         const unsigned long long bb = s_block;
         if (bb == ~0ull)
             break; /* uniform: every thread read the same s_block */
         const int64_t b = (int64_t)(bb & 0xFFFFFFFFull);
-        const uint32_t from = (uint32_t)(bb >> 32);
+        const uint32_t from = (uint32_t)((bb >> 32) & 0x7FFFFFFFull);
+        const unsigned char *rec = (bb >> 63) ? hand + s_slot * ORBG_HANDOVER_BYTES : nullptr;
         const int64_t lo = llr_off ? llr_off[b] : b * n0;
         const int64_t co = cw_off ? cw_off[b] : b * n0;
         if (ONE) {
             decode_block_cta<KMAX, WMAX>(code0, llr + lo, cw + co, q + b, ab + b, cap, smem,
                                          reinterpret_cast<uint16_t *>(smem + bstride), &s_best,
                                          reinterpret_cast<typename Syn<WMAX>::T *>(&s_s0), from,
-                                         warp, lane, nwarps);
+                                         warp, lane, nwarps, rec);
             continue;
         }
         const int cid = code_id ? code_id[b] : 0; /* checked in phase 1 */
@@ -63,7 +66,7 @@ __global__ void __launch_bounds__(512, ORBG_PHASE2_MIN_CTAS) orbg_heavy_kernel(
     decode_block_cta<KK, WW>(code, llr + lo, cw + co, q + b, ab + b, cap, smem,              \
                              reinterpret_cast<uint16_t *>(smem + bstride), &s_best,          \
                              reinterpret_cast<typename Syn<WW>::T *>(&s_s0), from, warp, lane,  \
-                             nwarps)
+                             nwarps, rec)
         ORBG_DISPATCH(KMAX, WMAX, ORBG_CALL_CTA);
 #undef ORBG_CALL_CTA
     }
@@ -72,7 +75,7 @@ __global__ void __launch_bounds__(512, ORBG_PHASE2_MIN_CTAS) orbg_heavy_kernel(
 
 template <int KMAX, int WMAX, bool ONE>
 cudaError_t launch_heavy_t(const OrbgBatchedArgs &a, unsigned long long *counters,
-                           const unsigned long long *heavy)
+                           const unsigned long long *heavy, const unsigned char *hand)
 {
     auto k2 = orbg_heavy_kernel<KMAX, WMAX, ONE>;
     const int hw = a.heavy_warps > 0 ? a.heavy_warps : 16;
@@ -87,7 +90,8 @@ cudaError_t launch_heavy_t(const OrbgBatchedArgs &a, unsigned long long *counter
         c0 = *a.code0;
     k2<<<grid, hw * 32, smem, (cudaStream_t)a.stream>>>(a.d_codes, a.ncodes, a.code_id,
                                                         a.llr_off, a.llr, a.cap, a.cw, a.cw_off,
-                                                        a.q, a.ab, counters, heavy, bstride, c0);
+                                                        a.q, a.ab, counters, heavy, hand, bstride,
+                                                        c0);
     return cudaGetLastError();
 }
 

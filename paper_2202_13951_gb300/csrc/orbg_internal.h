@@ -180,11 +180,19 @@ ORBG_DECLARE_BATCHED(8, 1) ORBG_DECLARE_BATCHED(8, 2) ORBG_DECLARE_BATCHED(8, 4)
 #define ORBG_BATCHED_COUNTERS 8
 #define ORBG_MAX_CODES 1024      /* codes in one set */
 size_t orbg_batched_scratch_bytes(int64_t B, int ncodes);
+/* Then, 16-byte aligned, up to ORBG_HANDOVER_MAX handover records: for the
+ * i-th block phase 1 leaves open, its reliability order (256 bytes: the
+ * received index of each sorted position) and its starting syndrome (16
+ * bytes), so that phase 2 need not sort the block again. */
+#define ORBG_HANDOVER_MAX 32768
+#define ORBG_HANDOVER_BYTES 272
 struct OrbgScratch {
     unsigned long long *counters;
     uint32_t *count, *cursor;
     unsigned long long *heavy;
     uint32_t *perm;
+    unsigned char *hand;          /* handover records */
+    uint32_t hand_cap;            /* records available */
     size_t zero_bytes;            /* bytes from the start that must be zero */
 };
 inline OrbgScratch orbg_scratch_layout(void *base, int64_t B, int ncodes)
@@ -192,12 +200,16 @@ inline OrbgScratch orbg_scratch_layout(void *base, int64_t B, int ncodes)
     OrbgScratch s;
     unsigned char *p = (unsigned char *)base;
     const size_t nc = (size_t)(ncodes > 0 ? ncodes : 0) + 1;
+    const size_t b = (size_t)(B > 0 ? B : 0);
     s.counters = (unsigned long long *)p;
     s.count = (uint32_t *)(p + 8 * ORBG_BATCHED_COUNTERS);
     s.cursor = s.count + nc;
     s.zero_bytes = 8 * ORBG_BATCHED_COUNTERS + 8 * nc;
     s.heavy = (unsigned long long *)(p + s.zero_bytes);
-    s.perm = (uint32_t *)(s.heavy + (B > 0 ? B : 0));
+    s.perm = (uint32_t *)(s.heavy + b);
+    const size_t hoff = ((size_t)((unsigned char *)(s.perm + b) - p) + 15) & ~(size_t)15;
+    s.hand = p + hoff;
+    s.hand_cap = (uint32_t)(b < ORBG_HANDOVER_MAX ? b : ORBG_HANDOVER_MAX);
     return s;
 }
 /* Order the blocks of a mixed-code call by code id (counting sort into

@@ -403,10 +403,12 @@ def _stratified_pick(q, ab, rng, n_abandoned, n_longest, n_random, within=None):
     idx = np.arange(q.shape[0]) if within is None else within
     aband = idx[ab[idx] == 1]
     dec = idx[ab[idx] == 0]
-    pick = [rng.choice(aband, min(n_abandoned, aband.size), replace=False),
-            dec[np.argsort(q[dec])[-n_longest:]],
-            rng.choice(idx, min(n_random, idx.size), replace=False)]
-    return np.unique(np.concatenate(pick))
+    first = np.unique(np.concatenate([rng.choice(aband, min(n_abandoned, aband.size),
+                                                 replace=False),
+                                      dec[np.argsort(q[dec])[-n_longest:]]]))
+    rest = np.setdiff1d(idx, first)
+    return np.unique(np.concatenate([first,
+                                     rng.choice(rest, min(n_random, rest.size), replace=False)]))
 
 
 def test_config3_full_size_sampled(orbg):
@@ -456,7 +458,7 @@ def test_config4_full_size(orbg):
         rows = np.stack([cw[off[b]:off[b] + cd.n] for b in idx])
         ok = ab[idx] == 0
         assert not ((rows[ok].astype(np.int64) @ cd.H.T.astype(np.int64)) % 2).any()
-        pick = _stratified_pick(q, ab, rng, 100, 100, 320, within=idx)
+        pick = _stratified_pick(q, ab, rng, 100, 100, 400, within=idx)
         assert pick.size >= 500
         blocks = np.stack([llr[off[b]:off[b] + cd.n] for b in pick])
         want = oracle_pool.decode_batch(cd.H, blocks, 10 ** 6)[:3]
