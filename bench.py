@@ -55,8 +55,8 @@ WORKLOADS = {
     "mixed": ("mixed rlc(64,51),(128,112),(256,240),(256,232), code uniform per block, "
               "%d blocks at Eb/N0 U[4,7] dB, query cap 1e6, one launch, autotuned",
               None, (), (401,)),
-    "capolar256": ("ca-polar(256,234[K=245]) 4x%d blocks at Eb/N0 5,5.5,6,6.5 dB, "
-                   "query cap 5e6", "capolar256_code", (5.0, 5.5, 6.0, 6.5),
+    "capolar256": ("ca-polar(256,234[K=245]) 4x%d blocks at Eb/N0 5,5.1,5.2,5.3 dB, "
+                   "query cap 5e6", "capolar256_code", (5.0, 5.1, 5.2, 5.3),
                    (701, 702, 703, 704)),
     "paper256": ("paper-shaped [256,234] family: ca-polar(256,234[K=245]), crc(256,234), "
                  "rlc(256,234), bch(255,231), code uniform per block, %d blocks at Eb/N0 "
@@ -464,8 +464,8 @@ def extra_runs():
             ("bch, full ORBGRAND with a 3-line model fitted per block",
              ["--workload", "bch", "--fitted-lines", "3"]),
             ("paper256, basic ORBGRAND", ["--workload", "paper256"]),
-            ("ca-polar[256,234] at 5-6.5 dB, full ORBGRAND with a 3-line model fitted per "
-             "block (the paper's operating points, Sec. IV-B)",
+            ("ca-polar[256,234] at 5-5.3 dB (BLER about 1e-3), full ORBGRAND with a 3-line "
+             "model fitted per block (the paper's operating point, Sec. IV-B)",
              ["--workload", "capolar256", "--fitted-lines", "3"])]
 
 

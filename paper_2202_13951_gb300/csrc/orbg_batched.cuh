@@ -112,8 +112,11 @@ __global__ void __launch_bounds__(256, ORBG_PHASE1_MIN_CTAS) orbg_batched_kernel
         const int64_t co = cw_off ? cw_off[b] : b * n0;
         const float *l = ring + slot * kSlot;
         if (ONE) {
-            /* one code, read from the kernel's parameters: K and W are exact */
-            decode_block_warp<KMAX, WMAX, true, true, (KMAX <= 4)>(code0, l, cw + co, q + b, ab + b,
+            /* one code, read from the kernel's parameters: K and W are exact;
+             * its sort is unrolled unless it is the 256-key one (for mixed
+             * codes, where several decoder variants share the instruction
+             * cache, the sort's stage loops stay rolled) */
+            decode_block_warp<KMAX, WMAX, true, true, (KMAX <= 4), (KMAX >= 8)>(code0, l, cw + co, q + b, ab + b,
                                                             cap, budget, bsm, lane, heavy,
                                                             &counters[1], (unsigned long long)b,
                                                             X3w, hand, hand_cap);
@@ -125,7 +128,7 @@ __global__ void __launch_bounds__(256, ORBG_PHASE1_MIN_CTAS) orbg_batched_kernel
         } else {
             const OrbgDeviceCode code = codes[cid];
 #define ORBG_CALL_WARP(KK, WW)                                                                 \
-    decode_block_warp<KK, WW, true, true, false>(code, l, cw + co, q + b, ab + b, cap,       \
+    decode_block_warp<KK, WW, true, true, false, true>(code, l, cw + co, q + b, ab + b, cap, \
                                                  budget, bsm, lane, heavy, &counters[1],    \
                                                  (unsigned long long)b, X3w, hand, hand_cap)
             ORBG_DISPATCH(KMAX, WMAX, ORBG_CALL_WARP);

@@ -205,9 +205,92 @@ __device__ __forceinline__ typename Syn<W>::T load_block(const OrbgDeviceCode &c
 /* ------------------------------------------------------- step 2: sort */
 
 /* Bitonic sort of 32*K unique keys held K per lane; afterwards position
- * e = lane*K + k holds the e-th smallest. */
+ * e = lane*K + k holds the e-th smallest.  The network's merge levels and
+ * its strides across lanes are loops (the compare-exchanges of one step,
+ * over the lane's K keys, are unrolled): the code stays small enough to
+ * remain in the instruction cache while the warps of an SM sort block after
+ * block, where the fully unrolled network (about 1,300 instructions for
+ * K = 8) was fetched anew for every block. */
 template <int K>
 __device__ __forceinline__ void sort_keys(uint64_t (&key)[K], int lane)
+{
+#pragma unroll 1
+    for (int size = 2; size <= 32 * K; size <<= 1) {
+#pragma unroll 1
+        for (int stride = size >> 1; stride >= K; stride >>= 1) {
+            const int lm = stride / K;
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const int e = lane * K + k;
+                uint64_t o = shfl_xor_u64(key[k], lm);
+                bool asc = (e & size) == 0;
+                bool lower = (e & stride) == 0;
+                uint64_t mn = key[k] < o ? key[k] : o;
+                uint64_t mx = key[k] < o ? o : key[k];
+                key[k] = (lower == asc) ? mn : mx;
+            }
+        }
+#pragma unroll
+        for (int stride = K / 2; stride > 0; stride >>= 1) {
+            if (stride > (size >> 1))
+                continue;
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                if ((k & stride) == 0) {
+                    const int k2 = k | stride;
+                    const int e = lane * K + k;
+                    bool asc = (e & size) == 0;
+                    uint64_t a = key[k], b = key[k2];
+                    bool sw = asc ? (a > b) : (a < b);
+                    key[k] = sw ? b : a;
+                    key[k2] = sw ? a : b;
+                }
+            }
+        }
+    }
+}
+
+/* Bitonic sort of 32*K unique 32-bit keys held K per lane (loops as
+ * sort_keys). */
+template <int K>
+__device__ __forceinline__ void bitonic32(uint32_t (&key)[K], int lane)
+{
+#pragma unroll 1
+    for (int size = 2; size <= 32 * K; size <<= 1) {
+#pragma unroll 1
+        for (int stride = size >> 1; stride >= K; stride >>= 1) {
+            const int lm = stride / K;
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                const int e = lane * K + k;
+                const uint32_t o = __shfl_xor_sync(FULL_MASK, key[k], lm);
+                const bool takemin = ((e & size) == 0) == ((e & stride) == 0);
+                key[k] = takemin ? min(key[k], o) : max(key[k], o);
+            }
+        }
+#pragma unroll
+        for (int stride = K / 2; stride > 0; stride >>= 1) {
+            if (stride > (size >> 1))
+                continue;
+#pragma unroll
+            for (int k = 0; k < K; k++) {
+                if ((k & stride) == 0) {
+                    const int k2 = k | stride;
+                    const int e = lane * K + k;
+                    const bool asc = (e & size) == 0;
+                    const uint32_t lo = min(key[k], key[k2]), hi = max(key[k], key[k2]);
+                    key[k] = asc ? lo : hi;
+                    key[k2] = asc ? hi : lo;
+                }
+            }
+        }
+    }
+}
+
+/* The same networks fully unrolled (sort_keys, bitonic32): faster where
+ * one kernel sorts for a single code, whose code then stays cached. */
+template <int K>
+__device__ __forceinline__ void sort_keys_unrolled(uint64_t (&key)[K], int lane)
 {
 #pragma unroll
     for (int size = 2; size <= 32 * K; size <<= 1) {
@@ -245,7 +328,7 @@ __device__ __forceinline__ void sort_keys(uint64_t (&key)[K], int lane)
 
 /* Bitonic sort of 32*K unique 32-bit keys held K per lane. */
 template <int K>
-__device__ __forceinline__ void bitonic32(uint32_t (&key)[K], int lane)
+__device__ __forceinline__ void bitonic32_unrolled(uint32_t (&key)[K], int lane)
 {
 #pragma unroll
     for (int size = 2; size <= 32 * K; size <<= 1) {
@@ -283,12 +366,15 @@ __device__ __forceinline__ void bitonic32(uint32_t (&key)[K], int lane)
  * sort exact 64-bit keys (bits << 32 | i) rebuilt from the LLRs instead.
  * Afterwards key[k] holds the received index of sorted position lane*K + k.
  */
-template <int K, bool LS = false>
+template <int K, bool LS = false, bool ROLL = true>
 __device__ __forceinline__ void sort_block(uint32_t (&key)[K], const float *__restrict__ llr,
                                            int n, int lane)
 {
     typedef KeyBits<K> KB;
-    bitonic32<K>(key, lane);
+    if (ROLL)
+        bitonic32<K>(key, lane);
+    else
+        bitonic32_unrolled<K>(key, lane);
     bool bad = false;
     const uint32_t next_first = __shfl_down_sync(FULL_MASK, key[0], 1);
 #pragma unroll
@@ -312,7 +398,10 @@ __device__ __forceinline__ void sort_block(uint32_t (&key)[K], const float *__re
                 i < n ? (__float_as_uint(llr_at<LS>(llr, i)) & 0x7FFFFFFFu) : 0xFFFFFFFFu;
             k64[k] = ((uint64_t)bits << 32) | (uint32_t)i;
         }
-        sort_keys<K>(k64, lane);
+        if (ROLL)
+            sort_keys<K>(k64, lane);
+        else
+            sort_keys_unrolled<K>(k64, lane);
 #pragma unroll
         for (int k = 0; k < K; k++)
             key[k] = (uint32_t)k64[k];
@@ -799,7 +888,7 @@ __device__ __forceinline__ uint32_t group_reaching(const OrbgTable &tb, uint32_t
  * here.  LS: llr points into shared memory (the batched kernel stages it
  * there).
  */
-template <int K, int W, bool LS = false, bool TRIP = false, bool PF = true>
+template <int K, int W, bool LS = false, bool TRIP = false, bool PF = true, bool ROLL = true>
 __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__restrict__ llr,
                                   uint8_t *__restrict__ cw_out, uint32_t *__restrict__ q_out,
                                   uint8_t *__restrict__ ab_out, uint32_t cap, uint32_t budget,
@@ -847,7 +936,7 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
                 if (upto > have) {
                     if (extract_ranks<K>(key, have, upto, &prev, &mine_key, lane)) {
                         make_keys<K, LS>(llr, n, lane, key);
-                        sort_block<K, LS>(key, llr, n, lane);
+                        sort_block<K, LS, ROLL>(key, llr, n, lane);
                         build_perm<K, W>(code, key, sm, lane);
                         sorted = true;
                     } else {
@@ -874,7 +963,7 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
         if (best == ORBG_NONE && !sorted) {
             /* leaving the flat table: every rank is needed */
             make_keys<K, LS>(llr, n, lane, key);
-            sort_block<K, LS>(key, llr, n, lane);
+            sort_block<K, LS, ROLL>(key, llr, n, lane);
             build_perm<K, W>(code, key, sm, lane);
             __syncwarp();
         }

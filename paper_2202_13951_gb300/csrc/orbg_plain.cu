@@ -27,8 +27,9 @@ __global__ void __launch_bounds__(256) orbg_plain_kernel(OrbgDeviceCode code,
     if (b >= B)
         return; /* whole warp */
     const int64_t off = b * (int64_t)code.n;
-    decode_block_warp<K, W>(code, llr + off, cw + off, q + b, ab + b, cap, cap,
-                            smem + warp * wstride, lane, nullptr, nullptr, 0ull);
+    decode_block_warp<K, W, false, false, true, (K >= 8)>(code, llr + off, cw + off, q + b,
+                                                          ab + b, cap, cap, smem + warp * wstride,
+                                                          lane, nullptr, nullptr, 0ull);
 }
 
 template <int K, int W>
