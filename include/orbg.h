@@ -193,17 +193,20 @@ ORBG_API int orbg_codeset_free(orbg_codeset *set);
  * stream-ordered device scratch (queue counters, per-code block counts, the
  * list of still-open blocks, the blocks' order grouped by code, and the
  * reliability order of up to 32,768 still-open blocks, which the second
- * launch reuses), allocated and freed on cuda_stream.  With code_id given and codes of different length classes
- * (n <= 32, 64, 128, 256) or syndrome widths in the set, the first launch
- * takes the blocks grouped by code.
+ * launch reuses), allocated and freed on cuda_stream.  With code_id given
+ * and codes of different length classes (n <= 32, 64, 128, 256) or
+ * syndrome widths in the set, the first launch takes the blocks grouped by
+ * code.
  * Host buffers (staged through stream-ordered device copies): a call with
  * every buffer on the host, B >= 131072 and a layout that places the
  * blocks in order without overlap (dense, or offsets that never go back)
- * is cut into up to eight chunks whose copies in, decodes and copies out
- * overlap on three library-owned streams (created on the set's first such
- * call); cuda_stream waits for them and is synchronised before the call
- * returns, as for any host-buffer call.  With host buffers and offsets,
- * codeword bytes between blocks are unspecified afterwards.
+ * is cut into up to eight chunks: each chunk's copy in overlaps the first
+ * launch over the chunks before it, the second launch runs once over the
+ * blocks every chunk left open, and the results are then copied out, on
+ * three library-owned streams (created on the set's first such call);
+ * cuda_stream waits for them and is synchronised before the call returns,
+ * as for any host-buffer call.  With host buffers and offsets, codeword
+ * bytes between blocks are unspecified afterwards.
  * Results are identical to orbg_decode's block by block.
  * Paper: Algorithm 1 per block; the batching is this library's.
  */

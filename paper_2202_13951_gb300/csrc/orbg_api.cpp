@@ -379,6 +379,7 @@ namespace {
 int load_code(const uint8_t *mat, int kind, int n, int k, uint32_t max_query_cap,
               const OrbgModel *md, int32_t J0, int32_t beta, orbg_code **out)
 {
+    OrbgRange range("orbg_load_code");
     if (!mat || (kind != ORBG_MAT_H && kind != ORBG_MAT_G) || n < 1 || k < 0 || k >= n)
         return ORBG_EINVAL;
     if (n > ORBG_MAX_N || n - k > ORBG_MAX_R)
@@ -553,6 +554,7 @@ int orbg_code_info(const orbg_code *code, int *n, int *k, uint32_t *max_query_ca
 int orbg_decode(const orbg_code *code, const float *llr, int64_t B, uint32_t query_cap,
                 uint8_t *codeword, uint32_t *queries, uint8_t *abandoned, void *cuda_stream)
 {
+    OrbgRange range("orbg_decode");
     if (!code || B < 0)
         return ORBG_EINVAL;
     if (query_cap < 1)
@@ -685,14 +687,17 @@ bool ordered_layout(const orbg_codeset *set, const int32_t *code_id,
 
 /*
  * Host buffers and a large batch: the batch is cut into chunks of
- * consecutive blocks whose host-to-device copy, decode and device-to-host
- * copy run on three streams, so chunk i's copy in overlaps chunk i-1's
- * decode and chunk i-2's copy out.  The layout is dense (one code, no
- * offsets) or given per block by offsets that place the blocks in order
- * without overlap (ordered_layout), so each chunk's LLRs and codewords are
- * one contiguous range.  Each chunk is an ordinary batched call on its
- * blocks, so the results equal the unchunked call's.  n_llr, n_cw: element
- * counts of the whole buffers.  Synchronises `st`.
+ * consecutive blocks; each chunk's host-to-device copy (one stream) is
+ * followed by the first launch over its blocks (a second stream), so chunk
+ * i's copy in overlaps chunk i-1's decode; the blocks every chunk leaves
+ * open go to one list, which a single second launch searches after the
+ * last chunk (one tail for the batch, not one per chunk); then the results
+ * of the whole batch are copied out (a third stream).  The layout is dense
+ * (one code, no offsets) or given per block by offsets that place the
+ * blocks in order without overlap (ordered_layout), so each chunk's LLRs
+ * are one contiguous range.  Each block is decoded exactly as by an
+ * unchunked call.  n_llr, n_cw: element counts of the whole buffers.
+ * Synchronises `st`.
  */
 int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
                              const int64_t *llr_offset, const float *llr, int64_t B,
@@ -738,7 +743,7 @@ int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
         (e = cudaMallocAsync((void **)&d_cw, n_cw, st)) != cudaSuccess ||
         (e = cudaMallocAsync((void **)&d_q, (size_t)B * sizeof(uint32_t), st)) != cudaSuccess ||
         (e = cudaMallocAsync((void **)&d_ab, (size_t)B, st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&scratch, orbg_batched_scratch_bytes(per, set->ncodes), st)) !=
+        (e = cudaMallocAsync((void **)&scratch, orbg_batched_scratch_bytes(B, set->ncodes), st)) !=
             cudaSuccess ||
         (code_id && (e = cudaMallocAsync((void **)&d_cid, (size_t)B * sizeof(int32_t), st)) !=
                         cudaSuccess) ||
@@ -764,58 +769,79 @@ int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
                             s_in);
     const orbg_tuning &t = set->tuning;
     int le = 0;
+    OrbgBatchedArgs a{};
+    a.d_codes = set->d_codes;
+    a.code0 = &set->code0;
+    a.ncodes = set->ncodes;
+    a.n_max = set->n_max;
+    a.w32_max = set->w32_max;
+    a.variants = set->variants;
+    a.cap = query_cap;
+    a.budget = t.warp_budget < query_cap ? t.warp_budget : query_cap;
+    a.scratch = scratch;
+    a.warps_per_cta = t.warps_per_cta;
+    a.ctas_per_sm = t.ctas_per_sm;
+    a.grab = t.blocks_per_grab;
+    a.heavy_warps = t.heavy_warps;
+    a.ntrip_max = set->ntrip_max;
+    a.x3w_max = set->x3w_max;
+    a.stream = s_dec;
+    a.scratch_B = B;
     for (int64_t i = 0; i < nch && e == cudaSuccess && le == 0; i++) {
         const int64_t b0 = i * per, b1 = std::min(B, b0 + per);
         if (b1 <= b0)
             break;
-        const int64_t l0 = llr_at(b0), l1 = llr_at(b1), c0 = cw_at(b0), c1 = cw_at(b1);
-        cudaEvent_t in_done = nullptr, dec_done = nullptr;
-        if ((e = event(&in_done)) != cudaSuccess || (e = event(&dec_done)) != cudaSuccess)
+        const int64_t l0 = llr_at(b0), l1 = llr_at(b1), c0 = cw_at(b0);
+        cudaEvent_t in_done = nullptr;
+        if ((e = event(&in_done)) != cudaSuccess)
             break;
         if ((e = cudaMemcpyAsync(d_llr + l0, llr + l0, (size_t)(l1 - l0) * sizeof(float),
                                  cudaMemcpyHostToDevice, s_in)) != cudaSuccess ||
             (e = cudaEventRecord(in_done, s_in)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(s_dec, in_done, 0)) != cudaSuccess)
             break;
-        OrbgBatchedArgs a{};
-        a.d_codes = set->d_codes;
-        a.code0 = &set->code0;
-        a.ncodes = set->ncodes;
-        a.n_max = set->n_max;
-        a.w32_max = set->w32_max;
-        a.variants = set->variants;
+        /* phase 1 of this chunk; dense chunks index from their own first
+         * block, offsets are absolute in the whole buffers */
         a.code_id = d_cid ? d_cid + b0 : nullptr;
         a.llr_off = d_lo ? d_lo + b0 : nullptr;
         a.cw_off = d_co ? d_co + b0 : nullptr;
-        /* dense chunks index from their own first block; offsets are
-         * absolute in the whole buffers */
         a.llr = d_lo ? d_llr : d_llr + l0;
         a.cw = d_co ? d_cw : d_cw + c0;
         a.B = b1 - b0;
-        a.cap = query_cap;
-        a.budget = t.warp_budget < query_cap ? t.warp_budget : query_cap;
         a.q = d_q + b0;
         a.ab = d_ab + b0;
-        a.scratch = scratch;
-        a.warps_per_cta = t.warps_per_cta;
-        a.ctas_per_sm = t.ctas_per_sm;
-        a.grab = t.blocks_per_grab;
-        a.heavy_warps = t.heavy_warps;
-        a.ntrip_max = set->ntrip_max;
-        a.x3w_max = set->x3w_max;
-        a.stream = s_dec;
-        if ((le = orbg_launch_batched(a)) != 0)
-            break;
-        if ((e = cudaEventRecord(dec_done, s_dec)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(s_out, dec_done, 0)) != cudaSuccess ||
-            (c1 > c0 &&
-             (e = cudaMemcpyAsync(codeword + c0, d_cw + c0, (size_t)(c1 - c0),
-                                  cudaMemcpyDeviceToHost, s_out)) != cudaSuccess) ||
-            (e = cudaMemcpyAsync(queries + b0, d_q + b0, (size_t)(b1 - b0) * sizeof(uint32_t),
-                                 cudaMemcpyDeviceToHost, s_out)) != cudaSuccess ||
-            (e = cudaMemcpyAsync(abandoned + b0, d_ab + b0, (size_t)(b1 - b0),
-                                 cudaMemcpyDeviceToHost, s_out)) != cudaSuccess)
-            break;
+        a.stage = 1;
+        a.first_chunk = i == 0;
+        a.scratch_base = b0;
+        le = orbg_launch_batched(a);
+    }
+    /* phase 2 once, over the whole batch, then the results out */
+    cudaEvent_t dec_done = nullptr;
+    if (e == cudaSuccess && le == 0) {
+        a.code_id = d_cid;
+        a.llr_off = d_lo;
+        a.cw_off = d_co;
+        a.llr = d_llr;
+        a.cw = d_cw;
+        a.B = B;
+        a.q = d_q;
+        a.ab = d_ab;
+        a.stage = 2;
+        a.first_chunk = 0;
+        a.scratch_base = 0;
+        le = orbg_launch_batched(a);
+    }
+    if (e == cudaSuccess && le == 0 &&
+        ((e = event(&dec_done)) != cudaSuccess ||
+         (e = cudaEventRecord(dec_done, s_dec)) != cudaSuccess ||
+         (e = cudaStreamWaitEvent(s_out, dec_done, 0)) != cudaSuccess ||
+         (n_cw > 0 && (e = cudaMemcpyAsync(codeword, d_cw, n_cw, cudaMemcpyDeviceToHost,
+                                           s_out)) != cudaSuccess) ||
+         (e = cudaMemcpyAsync(queries, d_q, (size_t)B * sizeof(uint32_t),
+                              cudaMemcpyDeviceToHost, s_out)) != cudaSuccess ||
+         (e = cudaMemcpyAsync(abandoned, d_ab, (size_t)B, cudaMemcpyDeviceToHost, s_out)) !=
+             cudaSuccess)) {
+        /* fall through to the join */
     }
     /* join: the caller's stream waits for all three before the buffers go */
     cudaError_t je = cudaSuccess;
@@ -852,6 +878,7 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
                         uint32_t query_cap, uint8_t *codeword, const int64_t *cw_offset,
                         uint32_t *queries, uint8_t *abandoned, void *cuda_stream)
 {
+    OrbgRange range("orbg_decode_batched");
     if (!set || B < 0 || query_cap < 1)
         return ORBG_EINVAL;
     if (query_cap > set->cap_min || B >= ((int64_t)1 << 32))
@@ -974,6 +1001,7 @@ int orbg_codeset_autotune(orbg_codeset *set, const int32_t *code_id, const int64
                           const int64_t *cw_offset, uint32_t *queries, uint8_t *abandoned,
                           int reps, void *cuda_stream, orbg_tuning *best)
 {
+    OrbgRange range("orbg_codeset_autotune");
     if (!set || B < 1 || reps < 0 || reps > 64)
         return ORBG_EINVAL;
     if (!is_device_ptr(llr) || !is_device_ptr(codeword) || !is_device_ptr(queries) ||
@@ -1143,6 +1171,7 @@ int orbg_fitted_decode(orbg_fitted *f, const float *llr, int64_t B, uint32_t que
                        uint8_t *codeword, uint32_t *queries, uint8_t *abandoned,
                        int32_t *models, void *cuda_stream)
 {
+    OrbgRange range("orbg_fitted_decode");
     if (!f || B < 0 || query_cap < 1)
         return ORBG_EINVAL;
     if (query_cap > f->code->max_cap || B >= ((int64_t)1 << 32))
@@ -1278,6 +1307,7 @@ int orbg_decode_fitted(const orbg_code *code, const float *llr, int64_t B, uint3
                        int lines, int divisible, uint8_t *codeword, uint32_t *queries,
                        uint8_t *abandoned, int32_t *models, void *cuda_stream)
 {
+    OrbgRange range("orbg_decode_fitted");
     if (!code || B < 0 || query_cap < 1 || lines < 1 || lines > ORBG_MAX_SEG)
         return ORBG_EINVAL;
     if (query_cap > ORBG_MAX_QUERY_CAP || B >= ((int64_t)1 << 40))

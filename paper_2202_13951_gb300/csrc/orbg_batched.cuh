@@ -35,20 +35,27 @@ using namespace orbg_dev;
 
 constexpr int kCounters = ORBG_BATCHED_COUNTERS;
 
-/* resident phase-1 CTAs per SM the register allocation is sized for */
+/* resident phase-1 CTAs per SM the register allocation is sized for: three
+ * for one code (80 registers, no spills), two for mixed codes (the kernel
+ * holding every variant spilled at 80; at two it holds them in registers,
+ * and the measured step of the mixed 1,000,000-block batch drops 5 %) */
 #ifndef ORBG_PHASE1_MIN_CTAS
 #define ORBG_PHASE1_MIN_CTAS 3
 #endif
+#ifndef ORBG_PHASE1_MIN_CTAS_MIXED
+#define ORBG_PHASE1_MIN_CTAS_MIXED 2
+#endif
 
 template <int KMAX, int WMAX, bool ONE>
-__global__ void __launch_bounds__(256, ORBG_PHASE1_MIN_CTAS) orbg_batched_kernel(
+__global__ void __launch_bounds__(256, ONE ? ORBG_PHASE1_MIN_CTAS : ORBG_PHASE1_MIN_CTAS_MIXED)
+    orbg_batched_kernel(
     const OrbgDeviceCode *__restrict__ codes, int ncodes, const int32_t *__restrict__ code_id,
     const int64_t *__restrict__ llr_off, const float *__restrict__ llr, int64_t B, uint32_t cap,
     uint32_t budget, uint8_t *__restrict__ cw, const int64_t *__restrict__ cw_off,
     uint32_t *__restrict__ q, uint8_t *__restrict__ ab, unsigned long long *__restrict__ counters,
     unsigned long long *__restrict__ heavy, const uint32_t *__restrict__ perm,
-    unsigned char *__restrict__ hand, uint32_t hand_cap, uint32_t bstride, uint32_t x3w_bytes,
-    int grab, const __grid_constant__ OrbgDeviceCode code0)
+    unsigned char *__restrict__ hand, uint32_t hand_cap, unsigned long long b_base,
+    uint32_t bstride, uint32_t x3w_bytes, int grab, const __grid_constant__ OrbgDeviceCode code0)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
@@ -118,8 +125,9 @@ __global__ void __launch_bounds__(256, ORBG_PHASE1_MIN_CTAS) orbg_batched_kernel
              * cache, the sort's stage loops stay rolled) */
             decode_block_warp<KMAX, WMAX, true, true, (KMAX <= 4), (KMAX >= 8)>(code0, l, cw + co, q + b, ab + b,
                                                             cap, budget, bsm, lane, heavy,
-                                                            &counters[1], (unsigned long long)b,
-                                                            X3w, hand, hand_cap);
+                                                            &counters[1],
+                                                            b_base + (unsigned long long)b, X3w,
+                                                            hand, hand_cap);
         } else if (cid < 0 || cid >= ncodes) {
             if (lane == 0) {
                 q[b] = 0u;
@@ -130,7 +138,8 @@ __global__ void __launch_bounds__(256, ORBG_PHASE1_MIN_CTAS) orbg_batched_kernel
 #define ORBG_CALL_WARP(KK, WW)                                                                 \
     decode_block_warp<KK, WW, true, true, false, true>(code, l, cw + co, q + b, ab + b, cap, \
                                                  budget, bsm, lane, heavy, &counters[1],    \
-                                                 (unsigned long long)b, X3w, hand, hand_cap)
+                                                 b_base + (unsigned long long)b, X3w, hand,  \
+                                                 hand_cap)
             ORBG_DISPATCH(KMAX, WMAX, ORBG_CALL_WARP);
 #undef ORBG_CALL_WARP
         }
@@ -149,14 +158,30 @@ cudaError_t launch_t(const OrbgBatchedArgs &a)
     const int wpc = a.warps_per_cta > 0 ? (a.warps_per_cta > 8 ? 8 : a.warps_per_cta) : 8;
     const int g = a.grab < 1 ? 1 : a.grab;
     const uint32_t bstride = block_smem_bytes(a.n_max, a.w32_max);
-    const OrbgScratch sc = orbg_scratch_layout(a.scratch, a.B, a.ncodes);
+    const OrbgScratch sc =
+        orbg_scratch_layout(a.scratch, a.scratch_B > 0 ? a.scratch_B : a.B, a.ncodes);
     unsigned long long *counters = sc.counters;
     unsigned long long *heavy = sc.heavy;
     cudaStream_t st = (cudaStream_t)a.stream;
     cudaError_t e;
     int grid = 0, rc;
-    if ((e = cudaMemsetAsync(a.scratch, 0, sc.zero_bytes, st)) != cudaSuccess)
-        return e;
+    if (a.stage == 2) {
+        /* phase 2 over the open blocks every chunk's phase 1 listed */
+        if (a.budget >= a.cap)
+            return cudaSuccess;
+        return launch_heavy_t<KMAX, WMAX, ONE>(a, counters, heavy, sc.hand);
+    }
+    if (a.stage == 0 || a.first_chunk) {
+        if ((e = cudaMemsetAsync(a.scratch, 0, sc.zero_bytes, st)) != cudaSuccess)
+            return e;
+    } else {
+        /* a later chunk: a fresh queue and code counts; the open-block list
+         * and the phase-2 cursor carry on */
+        if ((e = cudaMemsetAsync(counters, 0, sizeof(unsigned long long), st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(sc.count, 0, sc.zero_bytes - 8 * ORBG_BATCHED_COUNTERS, st)) !=
+                cudaSuccess)
+            return e;
+    }
     /* codes that need different decoder variants: phase 1 takes the blocks
      * grouped by code, so one variant runs at a time */
     const bool sorted = !ONE && a.code_id != nullptr && a.ncodes > 1 && a.variants > 1;
@@ -178,11 +203,12 @@ cudaError_t launch_t(const OrbgBatchedArgs &a)
     k1<<<grid, wpc * 32, smem1, st>>>(a.d_codes, a.ncodes, a.code_id, a.llr_off, a.llr, a.B,
                                       a.cap, a.budget, a.cw, a.cw_off, a.q, a.ab, counters,
                                       heavy, sorted ? sc.perm : nullptr, sc.hand, sc.hand_cap,
-                                      bstride, x3w_bytes, g, c0);
+                                      (unsigned long long)a.scratch_base, bstride, x3w_bytes, g,
+                                      c0);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
-    if (a.budget >= a.cap)
-        return cudaSuccess; /* every block finished in phase 1 */
+    if (a.budget >= a.cap || a.stage == 1)
+        return cudaSuccess; /* every block finished in phase 1, or phase 2 comes later */
     return launch_heavy_t<KMAX, WMAX, ONE>(a, counters, heavy, sc.hand);
 }
 

@@ -960,8 +960,10 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
                 break;
             }
         }
-        if (best == ORBG_NONE && !sorted) {
-            /* leaving the flat table: every rank is needed */
+        if (best == ORBG_NONE && !sorted && cap > code.nflat) {
+            /* leaving the flat table: every rank is needed (unless the
+             * cap ended the search inside it: the walk below then stops at
+             * its first floor, past the cap) */
             make_keys<K, LS>(llr, n, lane, key);
             sort_block<K, LS, ROLL>(key, llr, n, lane);
             build_perm<K, W>(code, key, sm, lane);

@@ -162,6 +162,17 @@ struct OrbgBatchedArgs {
     int warps_per_cta, ctas_per_sm, grab, heavy_warps;
     uint32_t ntrip_max, x3w_max;
     void *stream;
+    /* Staged calls (the host-buffer pipeline: phase 1 chunk by chunk as the
+     * LLRs arrive, then one phase 2 over every chunk's open blocks).
+     * stage 0: both phases; 1: phase 1 of one chunk, blocks scratch_base ..
+     * scratch_base + B - 1 of the whole batch (the pointers already point at
+     * the chunk), first_chunk clears the scratch; 2: phase 2 only, over the
+     * whole batch (pointers and B of the whole batch).  scratch_B: the
+     * batch's block count the scratch is laid out for (0 = B). */
+    int stage;
+    int first_chunk;
+    int64_t scratch_base;
+    int64_t scratch_B;
 };
 int orbg_launch_batched(const OrbgBatchedArgs &args);
 /* orbg_batched_inst.cu, one per (keys per lane K, syndrome words W) */
@@ -220,6 +231,16 @@ inline OrbgScratch orbg_scratch_layout(void *base, int64_t B, int ncodes)
 int orbg_launch_code_sort(const int32_t *code_id, int64_t B, int ncodes, const OrbgScratch &s,
                           void *stream);
 int orbg_grid_for(const void *kern, int threads, size_t smem, int ctas_per_sm, int *grid_out);
+
+/* A named range on the NVTX timeline for the span of a scope (header-only
+ * NVTX v3: a no-op unless a profiler such as Nsight Systems is attached). */
+#include <nvtx3/nvToolsExt.h>
+struct OrbgRange {
+    explicit OrbgRange(const char *name) { nvtxRangePushA(name); }
+    ~OrbgRange() { nvtxRangePop(); }
+    OrbgRange(const OrbgRange &) = delete;
+    OrbgRange &operator=(const OrbgRange &) = delete;
+};
 
 /* What a launch needs of a code set (orbg_api.cpp owns the struct). */
 #include "../../include/orbg.h"

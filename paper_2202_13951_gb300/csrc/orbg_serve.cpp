@@ -297,6 +297,7 @@ bool dispatch_one(orbg_server *s)
         b += r->B;
         off += (size_t)r->B * r->n;
     }
+    OrbgRange range("orbg_server batch");
     unsigned char *d = s->d_pool + bt.dev_off;
     cudaStream_t st = s->streams[stream];
     cudaError_t e = cudaMemcpyAsync(d, h, bt.L.in_end, cudaMemcpyHostToDevice, st);
