@@ -1163,7 +1163,8 @@ def parity_check(job, got, have=None, budget_s=60.0, per_code=20000):
     oracle on all host cores (spawned single-threaded processes) until every
     code has `per_code` blocks checked (or all of its blocks), or until
     budget_s seconds have passed.  Blocks the GPU abandoned are put first in
-    each code's order (at most 500 per code), so the longest searches are
+    each code's order, up to 500 per code checked in all (even when the CPU
+    baseline's sample already reaches per_code), so the longest searches are
     among those checked.  Also returns, under "_alg", per code the blocks
     checked and the sum over them of q + sum_t w_t (the oracle's own count
     of the queries' Hamming weights), from which the algorithmic work of
@@ -1200,10 +1201,14 @@ def parity_check(job, got, have=None, budget_s=60.0, per_code=20000):
     todo = []
     for j in range(ncodes):
         idx = np.nonzero((job.cid_np == j) & ~done)[0]
-        aband = idx[ab_g[idx] == 1][:500]
+        # the GPU-abandoned blocks first (up to 500 per code checked in all,
+        # whatever the CPU baseline's sample already covered), then the
+        # stratified rest up to per_code
+        seen = int((done & (ab_g == 1) & (job.cid_np == j)).sum())
+        aband = idx[ab_g[idx] == 1][:max(0, 500 - seen)]
         rest = stratified_order(idx[ab_g[idx] != 1])
-        want = max(0, min(per_code - checked.get(j, 0), idx.size))
-        todo.append((j, np.concatenate([aband, rest])[:want]))
+        want = max(0, min(per_code - checked.get(j, 0) - aband.size, rest.size))
+        todo.append((j, np.concatenate([aband, rest[:want]])))
     chunk = 256
     tasks = []
     for j, idx in todo:

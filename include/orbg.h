@@ -189,7 +189,7 @@ ORBG_API int orbg_codeset_free(orbg_codeset *set);
  *   cw_offset  : [B] byte offset of block b in codeword, or NULL (dense).
  *   Other arguments as orbg_decode; query_cap must be within every code's
  *   max_query_cap.
- * The call uses 87 + 8 ncodes + 12 B + 272 min(B, 32768) bytes of
+ * The call uses 95 + 16 ncodes + 12 B + 272 min(B, 32768) bytes of
  * stream-ordered device scratch (queue counters, per-code block counts, the
  * list of still-open blocks, the blocks' order grouped by code, and the
  * reliability order of up to 32,768 still-open blocks, which the second
@@ -232,8 +232,8 @@ ORBG_API int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id
  *     staging): EINVAL otherwise.
  *   - B <= ORBG_NOALLOC_MAX_BLOCKS (524,288), else ELIMIT.  Larger batches
  *     can be split into several calls.
- *   - The array is 12 * ORBG_NOALLOC_MAX_BLOCKS + 8,280 + 272 * 32,768
- *     bytes (14.5 MiB + 8,280 B) of device memory per GPU that loads the
+ *   - The array is 12 * ORBG_NOALLOC_MAX_BLOCKS + 16,480 + 272 * 32,768
+ *     bytes (14.5 MiB + 16,480 B) of device memory per GPU that loads the
  *     library, held until the process exits.
  *   - The first call on each device looks up the array's device address
  *     (with that device current) and keeps it; make that first call before
@@ -509,6 +509,15 @@ ORBG_API const char *orbg_status_string(int status);
 
 /* The last CUDA error code seen by this thread (0 if none). */
 ORBG_API int orbg_last_cuda_error(void);
+
+/* Device memory of calls that stage host buffers, and their scratch, comes
+ * from a stream-ordered pool the library keeps per device, which holds
+ * freed memory for the next call instead of returning it at every
+ * synchronisation (so a repeated large host-buffer batch does not map and
+ * unmap its buffers each time).  This returns what the current device's
+ * pool holds unused to the driver; memory of calls still in flight stays.
+ * Returns ORBG_OK, or ORBG_ECUDA. */
+ORBG_API int orbg_pool_trim(void);
 
 /* Library version, e.g. 100 for 0.1.0. */
 ORBG_API int orbg_version(void);

@@ -46,10 +46,12 @@ struct orbg_codeset {
     uint32_t cap_min;
     int device;
     OrbgDeviceCode *d_codes = nullptr;
-    /* streams of the pipelined host-buffer path (copy in, decode, copy
-     * out), created on first use */
+    /* streams of the pipelined host-buffer path (copy in, two for decodes,
+     * copy out) and its host-mapped buffer for the outputs of the blocks
+     * phase 2 decodes, created on first use; one pipelined call at a time */
     mutable std::mutex pipe_mu;
-    mutable cudaStream_t pipe[3] = {nullptr, nullptr, nullptr};
+    mutable cudaStream_t pipe[4] = {nullptr, nullptr, nullptr, nullptr};
+    mutable unsigned char *gather = nullptr;
 };
 
 namespace {
@@ -57,6 +59,12 @@ namespace {
 thread_local int g_last_cuda = 0;
 /* smallest chunk of the pipelined host-buffer path (blocks) */
 constexpr int64_t kPipeChunkMin = 65536;
+/* phase-2 blocks whose outputs the pipelined path gathers in one go (more
+ * and it copies every output again) */
+constexpr uint32_t kGatherCap = 65536;
+/* the pipelined path's answer when the layout does not suit it (nothing
+ * written): the caller takes the unchunked path */
+constexpr int kPipeDecline = -1;
 const orbg_tuning kDefaultTuning = {8, 0, 4, 16384u, 8};
 
 int cuda_fail(cudaError_t e)
@@ -85,6 +93,80 @@ bool is_device_ptr(const void *p)
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+/* The library's stream-ordered memory pool on the current device.  Freed
+ * memory stays reserved for the next call (release threshold unlimited):
+ * from the default pool (threshold 0) it goes back to the driver at every
+ * synchronisation, so a large host-buffer batch would map and unmap its
+ * device buffers on every call.  orbg_pool_trim() returns it. */
+std::mutex g_pool_mu;
+std::map<int, cudaMemPool_t> g_pools;
+
+cudaError_t device_pool(cudaMemPool_t *out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    if ((e = cudaMemPoolCreate(&pool, &props)) != cudaSuccess)
+        return e;
+    uint64_t keep = UINT64_MAX;
+    if ((e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep)) !=
+        cudaSuccess) {
+        cudaMemPoolDestroy(pool);
+        return e;
+    }
+    g_pools[dev] = pool;
+    *out = pool;
+    return cudaSuccess;
+}
+
+/* Stream-ordered allocation from that pool; inside a stream capture, the
+ * capture's own allocation node (a graph owns its allocations). */
+cudaError_t alloc_async(void **p, size_t bytes, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess)
+        return e;
+    if (cs != cudaStreamCaptureStatusNone)
+        return cudaMallocAsync(p, bytes, st);
+    cudaMemPool_t pool;
+    if ((e = device_pool(&pool)) != cudaSuccess)
+        return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+}
+template <typename T>
+cudaError_t alloc_async(T **p, size_t bytes, cudaStream_t st)
+{
+    return alloc_async((void **)p, bytes, st);
+}
+
+/* p itself, when it is page-locked host memory the device can write at
+ * the same address (mapped, unified addressing); else NULL. */
+template <typename T>
+T *device_writable_host(T *p)
+{
+    const cudaError_t pending = cudaPeekAtLastError();
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        if (pending == cudaSuccess)
+            cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost && a.devicePointer == (void *)p ? p : nullptr;
+}
+
 /* A device mirror of a caller buffer that lives on the host. */
 struct Staged {
     void *host = nullptr;
@@ -110,7 +192,7 @@ struct Stager {
         s.bytes = bytes;
         s.copy_in = in;
         s.copy_out = out;
-        cudaError_t e = cudaMallocAsync(&s.dev, bytes, st);
+        cudaError_t e = alloc_async(&s.dev, bytes, st);
         if (e != cudaSuccess)
             return cuda_fail(e);
         items.push_back(s);
@@ -219,6 +301,15 @@ const char *orbg_status_string(int status)
 }
 
 int orbg_last_cuda_error(void) { return g_last_cuda; }
+
+int orbg_pool_trim(void)
+{
+    cudaMemPool_t pool;
+    cudaError_t e = device_pool(&pool);
+    if (e == cudaSuccess)
+        e = cudaMemPoolTrimTo(pool, 0);
+    return e == cudaSuccess ? ORBG_OK : cuda_fail(e);
+}
 
 int orbg_version(void) { return 100; }
 
@@ -589,10 +680,8 @@ int orbg_decode(const orbg_code *code, const float *llr, int64_t B, uint32_t que
     rc = sg.finish(true);
     if (rc)
         return rc;
-    if (!is_device_ptr(abandoned))
-        for (int64_t b = 0; b < B; b++)
-            if (abandoned[b] == ORBG_BLOCK_NAN)
-                return ORBG_ENAN;
+    if (!is_device_ptr(abandoned) && std::memchr(abandoned, ORBG_BLOCK_NAN, (size_t)B))
+        return ORBG_ENAN;
     return ORBG_OK;
 }
 
@@ -663,68 +752,101 @@ int orbg_codeset_free(orbg_codeset *set)
     for (cudaStream_t s : set->pipe)
         if (s)
             cudaStreamDestroy(s);
+    if (set->gather)
+        cudaFreeHost(set->gather);
     delete set;
     return ORBG_OK;
 }
 
 namespace {
 
-/* Host layout arrays that place block b + 1 at or after the end of block b
- * (in both buffers), so consecutive blocks occupy one contiguous range.
- * The dense layout (no offsets) qualifies. */
-bool ordered_layout(const orbg_codeset *set, const int32_t *code_id,
-                    const int64_t *llr_offset, const int64_t *cw_offset, int64_t B)
-{
-    if (!llr_offset)
-        return !code_id;
-    for (int64_t b = 0; b + 1 < B; b++) {
-        const int n = set->n_of[code_id ? code_id[b] : 0];
-        if (llr_offset[b + 1] < llr_offset[b] + n || cw_offset[b + 1] < cw_offset[b] + n)
-            return false;
-    }
-    return true;
-}
-
 /*
  * Host buffers and a large batch: the batch is cut into chunks of
- * consecutive blocks; each chunk's host-to-device copy (one stream) is
- * followed by the first launch over its blocks (a second stream), so chunk
- * i's copy in overlaps chunk i-1's decode; the blocks every chunk leaves
- * open go to one list, which a single second launch searches after the
- * last chunk (one tail for the batch, not one per chunk); then the results
- * of the whole batch are copied out (a third stream).  The layout is dense
- * (one code, no offsets) or given per block by offsets that place the
- * blocks in order without overlap (ordered_layout), so each chunk's LLRs
- * are one contiguous range.  Each block is decoded exactly as by an
- * unchunked call.  n_llr, n_cw: element counts of the whole buffers.
- * Synchronises `st`.
+ * consecutive blocks.  Each chunk's host-to-device copy (one stream) is
+ * followed by phase 1 over its blocks, on two decode streams taken in turn
+ * (with a queue slot each in the scratch), so chunk i's copy in overlaps
+ * chunk i-1's decode, and the next chunk's launch fills the SMs that the
+ * end of the previous one leaves idle; each chunk's results go back (a
+ * fourth stream) while later chunks decode.  The blocks every chunk leaves
+ * open go to one list, which a single phase-2 launch searches after the
+ * last chunk (one tail for the batch, not one per chunk).  A gather then
+ * writes their outputs over what the chunk copies brought: straight into
+ * the caller's buffers when they are page-locked and mapped (after those
+ * copies have landed), else into a host-mapped staging buffer that the
+ * host spreads once everything has finished.  Each block is decoded
+ * exactly as by an unchunked call.
+ *
+ * The layout is dense (one code, no offsets) or given by host offsets that
+ * place every block at or after the end of the one before, in both
+ * buffers, so that each chunk is one contiguous range of each.  The host
+ * checks this chunk by chunk, before the chunk's copy and launch, so the
+ * check of chunk i + 1 runs while the device works on chunk i.  When a
+ * chunk fails it (blocks out of order, a code id outside the set) nothing
+ * has been written to the outputs yet, and the call returns kPipeDecline
+ * for the unchunked path (which rejects invalid ids).  Synchronises `st`.
  */
 int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
                              const int64_t *llr_offset, const float *llr, int64_t B,
                              uint32_t query_cap, uint8_t *codeword, const int64_t *cw_offset,
-                             uint32_t *queries, uint8_t *abandoned, size_t n_llr, size_t n_cw,
-                             cudaStream_t st)
+                             uint32_t *queries, uint8_t *abandoned, cudaStream_t st)
 {
-    cudaError_t e = cudaSuccess;
-    {
-        std::lock_guard<std::mutex> lk(set->pipe_mu);
-        for (int i = 0; i < 3 && e == cudaSuccess; i++)
-            if (!set->pipe[i])
-                e = cudaStreamCreateWithFlags(&set->pipe[i], cudaStreamNonBlocking);
-    }
-    if (e != cudaSuccess)
-        return cuda_fail(e);
-    cudaStream_t s_in = set->pipe[0], s_dec = set->pipe[1], s_out = set->pipe[2];
+    if (!llr_offset && code_id)
+        return kPipeDecline; /* a dense layout holds one code */
     const int64_t n0 = set->n_of[0];
-    const int64_t nch = std::min<int64_t>(8, B / kPipeChunkMin);
-    const int64_t per = (B + nch - 1) / nch;
+    /* the buffers' extents if the layout is ordered: the last block ends them */
+    int64_t n_llr = B * n0, n_cw = B * n0;
+    if (llr_offset) {
+        const int32_t c = code_id ? code_id[B - 1] : 0;
+        if (c < 0 || c >= set->ncodes || llr_offset[0] < 0 || cw_offset[0] < 0 ||
+            llr_offset[B - 1] > (INT64_MAX >> 2) || cw_offset[B - 1] > (INT64_MAX >> 2))
+            return kPipeDecline;
+        n_llr = llr_offset[B - 1] + set->n_of[c];
+        n_cw = cw_offset[B - 1] + set->n_of[c];
+    }
     /* first element of block b in each buffer; block B marks the end */
     auto llr_at = [&](int64_t b) -> int64_t {
-        return b >= B ? (int64_t)n_llr : llr_offset ? llr_offset[b] : b * n0;
+        return b >= B ? n_llr : llr_offset ? llr_offset[b] : b * n0;
     };
     auto cw_at = [&](int64_t b) -> int64_t {
-        return b >= B ? (int64_t)n_cw : cw_offset ? cw_offset[b] : b * n0;
+        return b >= B ? n_cw : cw_offset ? cw_offset[b] : b * n0;
     };
+    /* blocks [b0, b1) have codes of the set, and each ends at or before the
+     * start of the next (the first starts at or after 0, checked above) */
+    auto ordered = [&](int64_t b0, int64_t b1) -> bool {
+        if (!llr_offset)
+            return true;
+        for (int64_t b = b0; b < b1; b++) {
+            const int32_t c = code_id ? code_id[b] : 0;
+            if (c < 0 || c >= set->ncodes)
+                return false;
+            const int64_t n = set->n_of[c];
+            if (llr_at(b + 1) < llr_offset[b] + n || cw_at(b + 1) < cw_offset[b] + n)
+                return false;
+        }
+        return true;
+    };
+    std::lock_guard<std::mutex> lk(set->pipe_mu);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 4 && e == cudaSuccess; i++)
+        if (!set->pipe[i])
+            e = cudaStreamCreateWithFlags(&set->pipe[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess && !set->gather)
+        e = cudaHostAlloc((void **)&set->gather, orbg_gather_bytes(kGatherCap, set->n_max),
+                          cudaHostAllocMapped);
+    unsigned char *d_gather = nullptr;
+    if (e == cudaSuccess)
+        e = cudaHostGetDevicePointer((void **)&d_gather, set->gather, 0);
+    if (e != cudaSuccess)
+        return cuda_fail(e);
+    cudaStream_t s_in = set->pipe[0], s_dec = set->pipe[1], s_out = set->pipe[2],
+                 s_dec1 = set->pipe[3];
+    /* the caller's output buffers, when the gather can write them in place */
+    uint8_t *to_cw = device_writable_host(codeword);
+    uint32_t *to_q = device_writable_host(queries);
+    uint8_t *to_ab = device_writable_host(abandoned);
+    const bool in_place = to_cw && to_q && to_ab;
+    const int64_t nch = std::min<int64_t>(8, B / kPipeChunkMin);
+    const int64_t per = (B + nch - 1) / nch;
     float *d_llr = nullptr;
     uint8_t *d_cw = nullptr, *d_ab = nullptr;
     uint32_t *d_q = nullptr;
@@ -738,26 +860,32 @@ int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
             ev.push_back(*out);
         return r;
     };
-    cudaEvent_t start = nullptr, done = nullptr;
-    if ((e = cudaMallocAsync((void **)&d_llr, n_llr * sizeof(float), st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&d_cw, n_cw, st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&d_q, (size_t)B * sizeof(uint32_t), st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&d_ab, (size_t)B, st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&scratch, orbg_batched_scratch_bytes(B, set->ncodes), st)) !=
+    cudaEvent_t start = nullptr;
+    if ((e = alloc_async(&d_llr, (size_t)n_llr * sizeof(float), st)) != cudaSuccess ||
+        (e = alloc_async(&d_cw, (size_t)n_cw, st)) != cudaSuccess ||
+        (e = alloc_async(&d_q, (size_t)B * sizeof(uint32_t), st)) != cudaSuccess ||
+        (e = alloc_async(&d_ab, (size_t)B, st)) != cudaSuccess ||
+        (e = alloc_async(&scratch, orbg_batched_scratch_bytes(B, set->ncodes), st)) !=
             cudaSuccess ||
-        (code_id && (e = cudaMallocAsync((void **)&d_cid, (size_t)B * sizeof(int32_t), st)) !=
+        (code_id && (e = alloc_async(&d_cid, (size_t)B * sizeof(int32_t), st)) !=
                         cudaSuccess) ||
-        (llr_offset && (e = cudaMallocAsync((void **)&d_lo, (size_t)B * sizeof(int64_t), st)) !=
+        (llr_offset && (e = alloc_async(&d_lo, (size_t)B * sizeof(int64_t), st)) !=
                            cudaSuccess) ||
-        (cw_offset && (e = cudaMallocAsync((void **)&d_co, (size_t)B * sizeof(int64_t), st)) !=
+        (cw_offset && (e = alloc_async(&d_co, (size_t)B * sizeof(int64_t), st)) !=
                           cudaSuccess) ||
+        /* the whole scratch cleared once, before either decode stream
+         * starts; each chunk then resets only its own slot */
+        (e = cudaMemsetAsync(scratch, 0, orbg_scratch_layout(scratch, B, set->ncodes).zero_bytes,
+                             st)) != cudaSuccess ||
         (e = event(&start)) != cudaSuccess || (e = cudaEventRecord(start, st)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(s_in, start, 0)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(s_dec, start, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(s_dec1, start, 0)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(s_out, start, 0)) != cudaSuccess) {
         /* fall through to clean-up */
     }
-    /* the per-block layout arrays go first, whole (12 bytes a block) */
+    /* the per-block layout arrays go first, whole (12 bytes a block); the
+     * kernels read a chunk's entries only after the host checked them */
     if (e == cudaSuccess && code_id)
         e = cudaMemcpyAsync(d_cid, code_id, (size_t)B * sizeof(int32_t), cudaMemcpyHostToDevice,
                             s_in);
@@ -785,20 +913,26 @@ int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
     a.heavy_warps = t.heavy_warps;
     a.ntrip_max = set->ntrip_max;
     a.x3w_max = set->x3w_max;
-    a.stream = s_dec;
     a.scratch_B = B;
+    bool declined = false;
+    std::vector<cudaEvent_t> chunk_done;
     for (int64_t i = 0; i < nch && e == cudaSuccess && le == 0; i++) {
         const int64_t b0 = i * per, b1 = std::min(B, b0 + per);
         if (b1 <= b0)
             break;
+        if (!ordered(b0, b1)) {
+            declined = true;
+            break;
+        }
         const int64_t l0 = llr_at(b0), l1 = llr_at(b1), c0 = cw_at(b0);
-        cudaEvent_t in_done = nullptr;
-        if ((e = event(&in_done)) != cudaSuccess)
+        cudaStream_t sd = (i & 1) ? s_dec1 : s_dec;
+        cudaEvent_t in_done = nullptr, dec_done = nullptr;
+        if ((e = event(&in_done)) != cudaSuccess || (e = event(&dec_done)) != cudaSuccess)
             break;
         if ((e = cudaMemcpyAsync(d_llr + l0, llr + l0, (size_t)(l1 - l0) * sizeof(float),
                                  cudaMemcpyHostToDevice, s_in)) != cudaSuccess ||
             (e = cudaEventRecord(in_done, s_in)) != cudaSuccess ||
-            (e = cudaStreamWaitEvent(s_dec, in_done, 0)) != cudaSuccess)
+            (e = cudaStreamWaitEvent(sd, in_done, 0)) != cudaSuccess)
             break;
         /* phase 1 of this chunk; dense chunks index from their own first
          * block, offsets are absolute in the whole buffers */
@@ -811,13 +945,41 @@ int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
         a.q = d_q + b0;
         a.ab = d_ab + b0;
         a.stage = 1;
-        a.first_chunk = i == 0;
+        a.slot = (int)(i & 1);
+        a.first_chunk = 0;
         a.scratch_base = b0;
-        le = orbg_launch_batched(a);
+        a.stream = sd;
+        if ((le = orbg_launch_batched(a)) != 0)
+            break;
+        if ((e = cudaEventRecord(dec_done, sd)) != cudaSuccess)
+            break;
+        chunk_done.push_back(dec_done);
     }
-    /* phase 2 once, over the whole batch, then the results out */
-    cudaEvent_t dec_done = nullptr;
-    if (e == cudaSuccess && le == 0) {
+    const bool go = e == cudaSuccess && le == 0 && !declined;
+    /* every chunk's results out as soon as its phase 1 is done */
+    for (size_t i = 0; go && e == cudaSuccess && i < chunk_done.size(); i++) {
+        const int64_t b0 = (int64_t)i * per, b1 = std::min(B, b0 + per);
+        const int64_t c0 = cw_at(b0), c1 = cw_at(b1);
+        if ((e = cudaStreamWaitEvent(s_out, chunk_done[i], 0)) != cudaSuccess ||
+            (c1 > c0 && (e = cudaMemcpyAsync(codeword + c0, d_cw + c0, (size_t)(c1 - c0),
+                                             cudaMemcpyDeviceToHost, s_out)) != cudaSuccess) ||
+            (e = cudaMemcpyAsync(queries + b0, d_q + b0, (size_t)(b1 - b0) * sizeof(uint32_t),
+                                 cudaMemcpyDeviceToHost, s_out)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(abandoned + b0, d_ab + b0, (size_t)(b1 - b0),
+                                 cudaMemcpyDeviceToHost, s_out)) != cudaSuccess)
+            break;
+    }
+    /* phase 2 once, over the whole batch, after both decode streams; then
+     * its blocks' outputs gathered (in place: after the chunk copies) */
+    cudaEvent_t dec1_done = nullptr, out_done = nullptr;
+    if (go && e == cudaSuccess &&
+        ((e = event(&dec1_done)) != cudaSuccess ||
+         (e = cudaEventRecord(dec1_done, s_dec1)) != cudaSuccess ||
+         (e = cudaStreamWaitEvent(s_dec, dec1_done, 0)) != cudaSuccess)) {
+        /* fall through to the join */
+    }
+    if (go && e == cudaSuccess) {
+        a.stream = s_dec;
         a.code_id = d_cid;
         a.llr_off = d_lo;
         a.cw_off = d_co;
@@ -830,31 +992,50 @@ int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
         a.first_chunk = 0;
         a.scratch_base = 0;
         le = orbg_launch_batched(a);
+        if (le == 0 && in_place &&
+            ((e = event(&out_done)) != cudaSuccess ||
+             (e = cudaEventRecord(out_done, s_out)) != cudaSuccess ||
+             (e = cudaStreamWaitEvent(s_dec, out_done, 0)) != cudaSuccess)) {
+            /* fall through to the join */
+        } else if (le == 0) {
+            le = orbg_launch_heavy_gather(set->d_codes, d_cid, (int)n0, d_co, d_cw, d_q, d_ab,
+                                          orbg_scratch_layout(scratch, B, set->ncodes), d_gather,
+                                          kGatherCap, set->n_max, in_place ? to_cw : nullptr,
+                                          to_q, to_ab, s_dec);
+        }
     }
-    if (e == cudaSuccess && le == 0 &&
-        ((e = event(&dec_done)) != cudaSuccess ||
-         (e = cudaEventRecord(dec_done, s_dec)) != cudaSuccess ||
-         (e = cudaStreamWaitEvent(s_out, dec_done, 0)) != cudaSuccess ||
-         (n_cw > 0 && (e = cudaMemcpyAsync(codeword, d_cw, n_cw, cudaMemcpyDeviceToHost,
-                                           s_out)) != cudaSuccess) ||
-         (e = cudaMemcpyAsync(queries, d_q, (size_t)B * sizeof(uint32_t),
-                              cudaMemcpyDeviceToHost, s_out)) != cudaSuccess ||
-         (e = cudaMemcpyAsync(abandoned, d_ab, (size_t)B, cudaMemcpyDeviceToHost, s_out)) !=
-             cudaSuccess)) {
-        /* fall through to the join */
-    }
-    /* join: the caller's stream waits for all three before the buffers go */
-    cudaError_t je = cudaSuccess;
-    for (cudaStream_t sx : {s_in, s_dec, s_out}) {
-        if (je == cudaSuccess && (je = event(&done)) == cudaSuccess &&
-            (je = cudaEventRecord(done, sx)) == cudaSuccess)
-            je = cudaStreamWaitEvent(st, done, 0);
+    /* join: the caller's stream waits for all four */
+    auto join = [&]() -> cudaError_t {
+        cudaError_t je = cudaSuccess;
+        cudaEvent_t done = nullptr;
+        for (cudaStream_t sx : {s_in, s_dec, s_dec1, s_out}) {
+            if (je == cudaSuccess && (je = event(&done)) == cudaSuccess &&
+                (je = cudaEventRecord(done, sx)) == cudaSuccess)
+                je = cudaStreamWaitEvent(st, done, 0);
+        }
+        if (je == cudaSuccess)
+            je = cudaStreamSynchronize(st);
+        return je;
+    };
+    cudaError_t je = join();
+    /* more phase-2 blocks than the staging buffer holds: copy every output
+     * again */
+    int rc = ORBG_OK;
+    const uint64_t nheavy = *(volatile uint64_t *)set->gather;
+    if (go && le == 0 && e == cudaSuccess && je == cudaSuccess && !in_place &&
+        nheavy > kGatherCap) {
+        if ((e = cudaMemcpyAsync(codeword, d_cw, (size_t)n_cw, cudaMemcpyDeviceToHost, st)) ==
+                cudaSuccess &&
+            (e = cudaMemcpyAsync(queries, d_q, (size_t)B * sizeof(uint32_t),
+                                 cudaMemcpyDeviceToHost, st)) == cudaSuccess &&
+            (e = cudaMemcpyAsync(abandoned, d_ab, (size_t)B, cudaMemcpyDeviceToHost, st)) ==
+                cudaSuccess)
+            e = cudaStreamSynchronize(st);
     }
     for (void *ptr : {(void *)d_llr, (void *)d_cw, (void *)d_q, (void *)d_ab, (void *)scratch,
                       (void *)d_cid, (void *)d_lo, (void *)d_co})
         if (ptr)
             cudaFreeAsync(ptr, st);
-    cudaError_t se = cudaStreamSynchronize(st);
     for (cudaEvent_t x : ev)
         cudaEventDestroy(x);
     if (e != cudaSuccess)
@@ -863,12 +1044,27 @@ int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
         return cuda_fail((cudaError_t)le);
     if (je != cudaSuccess)
         return cuda_fail(je);
-    if (se != cudaSuccess)
-        return cuda_fail(se);
-    for (int64_t b = 0; b < B; b++)
-        if (abandoned[b] == ORBG_BLOCK_NAN)
-            return ORBG_ENAN;
-    return ORBG_OK;
+    if (declined)
+        return kPipeDecline;
+    if (!in_place && nheavy <= kGatherCap) {
+        /* the phase-2 blocks' outputs over what the chunk copies brought */
+        const unsigned char *g = set->gather;
+        const uint32_t *bq = (const uint32_t *)(g + 16);
+        const uint8_t *flag = g + 16 + 8 * (size_t)kGatherCap;
+        const uint8_t *cwg = g + orbg_gather_cw_at(kGatherCap);
+        for (uint64_t h = 0; h < nheavy; h++) {
+            const int64_t b = bq[2 * h];
+            if (b >= B)
+                return cuda_fail(cudaErrorUnknown); /* not a block of this call */
+            std::memcpy(codeword + cw_at(b), cwg + h * (size_t)set->n_max,
+                        (size_t)set->n_of[code_id ? code_id[b] : 0]);
+            queries[b] = bq[2 * h + 1];
+            abandoned[b] = flag[h];
+        }
+    }
+    if (std::memchr(abandoned, ORBG_BLOCK_NAN, (size_t)B))
+        rc = ORBG_ENAN;
+    return rc;
 }
 
 }  // namespace
@@ -890,6 +1086,17 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
     if ((llr_offset == nullptr) != (cw_offset == nullptr))
         return ORBG_EINVAL;
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    /* large batches on host buffers: chunked, copies overlapping decodes,
+     * when every layout array is on the host and places blocks in order */
+    if (B >= 2 * kPipeChunkMin && !is_device_ptr(llr) && !is_device_ptr(codeword) &&
+        !is_device_ptr(queries) && !is_device_ptr(abandoned) &&
+        (!code_id || !is_device_ptr(code_id)) && (!llr_offset || !is_device_ptr(llr_offset)) &&
+        (!cw_offset || !is_device_ptr(cw_offset))) {
+        const int rc = decode_batched_pipelined(set, code_id, llr_offset, llr, B, query_cap,
+                                                codeword, cw_offset, queries, abandoned, st);
+        if (rc != kPipeDecline)
+            return rc;
+    }
     /* element counts: dense layout, or as far as the largest offset reaches */
     size_t n_llr, n_cw;
     if (!llr_offset) {
@@ -917,15 +1124,6 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
             n_llr = n_cw = 0;
         }
     }
-    /* large batches on host buffers: chunked, copies overlapping decodes,
-     * when every layout array is on the host and places blocks in order */
-    if (B >= 2 * kPipeChunkMin && !is_device_ptr(llr) && !is_device_ptr(codeword) &&
-        !is_device_ptr(queries) && !is_device_ptr(abandoned) &&
-        (!code_id || !is_device_ptr(code_id)) && (!llr_offset || !is_device_ptr(llr_offset)) &&
-        (!cw_offset || !is_device_ptr(cw_offset)) &&
-        ordered_layout(set, code_id, llr_offset, cw_offset, B))
-        return decode_batched_pipelined(set, code_id, llr_offset, llr, B, query_cap, codeword,
-                                        cw_offset, queries, abandoned, n_llr, n_cw, st);
     Stager sg(st);
     const float *d_llr;
     uint8_t *d_cw, *d_ab;
@@ -946,7 +1144,7 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
         return rc;
     }
     unsigned long long *scratch = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&scratch, orbg_batched_scratch_bytes(B, set->ncodes), st);
+    cudaError_t e = alloc_async(&scratch, orbg_batched_scratch_bytes(B, set->ncodes), st);
     if (e != cudaSuccess) {
         sg.finish(false);
         return cuda_fail(e);
@@ -989,10 +1187,8 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
     rc = sg.finish(true);
     if (rc)
         return rc;
-    if (!is_device_ptr(abandoned))
-        for (int64_t b = 0; b < B; b++)
-            if (abandoned[b] == ORBG_BLOCK_NAN)
-                return ORBG_ENAN;
+    if (!is_device_ptr(abandoned) && std::memchr(abandoned, ORBG_BLOCK_NAN, (size_t)B))
+        return ORBG_ENAN;
     return ORBG_OK;
 }
 
@@ -1192,12 +1388,12 @@ int orbg_fitted_decode(orbg_fitted *f, const float *llr, int64_t B, uint32_t que
     uint8_t *d_present = nullptr;
     cudaError_t e = cudaSuccess;
     int rc = ORBG_OK;
-    if ((!models && (e = cudaMallocAsync((void **)&d_models,
+    if ((!models && (e = alloc_async(&d_models,
                                          (size_t)B * ORBG_FIT_STRIDE * sizeof(int32_t), st)) !=
                         cudaSuccess) ||
-        (e = cudaMallocAsync((void **)&d_cid, (size_t)B * sizeof(int32_t), st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&d_lut, nj * sizeof(int32_t), st)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&d_present, nj, st)) != cudaSuccess ||
+        (e = alloc_async(&d_cid, (size_t)B * sizeof(int32_t), st)) != cudaSuccess ||
+        (e = alloc_async(&d_lut, nj * sizeof(int32_t), st)) != cudaSuccess ||
+        (e = alloc_async(&d_present, nj, st)) != cudaSuccess ||
         (e = cudaMemsetAsync(d_present, 0, nj, st)) != cudaSuccess)
         rc = cuda_fail(e);
     /* every block's line, then which J_0s occur (device), read back */
@@ -1254,7 +1450,7 @@ int orbg_fitted_decode(orbg_fitted *f, const float *llr, int64_t B, uint32_t que
      * the code's n), as orbg_decode_batched makes it */
     unsigned long long *scratch = nullptr;
     if (rc == ORBG_OK &&
-        (e = cudaMallocAsync((void **)&scratch, orbg_batched_scratch_bytes(B, f->set->ncodes), st)) !=
+        (e = alloc_async(&scratch, orbg_batched_scratch_bytes(B, f->set->ncodes), st)) !=
             cudaSuccess)
         rc = cuda_fail(e);
     if (rc == ORBG_OK) {
@@ -1334,7 +1530,7 @@ int orbg_decode_fitted(const orbg_code *code, const float *llr, int64_t B, uint3
         return rc;
     }
     unsigned long long *queue = nullptr;
-    cudaError_t e = cudaMallocAsync((void **)&queue, sizeof(unsigned long long), st);
+    cudaError_t e = alloc_async(&queue, sizeof(unsigned long long), st);
     if (e != cudaSuccess) {
         sg.finish(false);
         return cuda_fail(e);
@@ -1364,10 +1560,8 @@ int orbg_decode_fitted(const orbg_code *code, const float *llr, int64_t B, uint3
     rc = sg.finish(true);
     if (rc)
         return rc;
-    if (!is_device_ptr(abandoned))
-        for (int64_t b = 0; b < B; b++)
-            if (abandoned[b] == ORBG_BLOCK_NAN)
-                return ORBG_ENAN;
+    if (!is_device_ptr(abandoned) && std::memchr(abandoned, ORBG_BLOCK_NAN, (size_t)B))
+        return ORBG_ENAN;
     return ORBG_OK;
 }
 

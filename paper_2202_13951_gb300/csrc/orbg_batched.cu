@@ -34,7 +34,7 @@ size_t orbg_batched_scratch_bytes(int64_t B, int ncodes)
 {
     const size_t b = (size_t)(B > 0 ? B : 0);
     const size_t h = b < ORBG_HANDOVER_MAX ? b : ORBG_HANDOVER_MAX;
-    return 8 * (size_t)ORBG_BATCHED_COUNTERS + 8 * ((size_t)(ncodes > 0 ? ncodes : 0) + 1) +
+    return 8 * (size_t)ORBG_BATCHED_COUNTERS + 16 * ((size_t)(ncodes > 0 ? ncodes : 0) + 1) +
            12 * b + 15 + (size_t)ORBG_HANDOVER_BYTES * h;
 }
 
@@ -99,7 +99,72 @@ __global__ void __launch_bounds__(kSortThreads) orbg_code_scatter_kernel(
         perm[atomicAdd(&local[sort_bucket(code_id, b, ncodes)], 1u)] = (uint32_t)b;
 }
 
+/* one warp per heavy-list entry; the lanes copy the codeword bytes */
+__global__ void __launch_bounds__(256) orbg_heavy_gather_kernel(
+    const OrbgDeviceCode *__restrict__ codes, const int32_t *__restrict__ code_id, int n0,
+    const int64_t *__restrict__ cw_off, const uint8_t *__restrict__ cw,
+    const uint32_t *__restrict__ q, const uint8_t *__restrict__ ab,
+    const unsigned long long *__restrict__ counters, const unsigned long long *__restrict__ heavy,
+    unsigned char *__restrict__ out, uint32_t cap, int n_max, uint8_t *__restrict__ to_cw,
+    uint32_t *__restrict__ to_q, uint8_t *__restrict__ to_ab)
+{
+    const unsigned long long nheavy = counters[1];
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *(unsigned long long *)out = nheavy;
+    const int lane = threadIdx.x & 31;
+    const uint64_t step = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    if (to_cw) {
+        /* straight into the caller's buffers, at the blocks' own places */
+        for (uint64_t h = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; h < nheavy;
+             h += step) {
+            const uint32_t b = (uint32_t)heavy[h];
+            const int n = code_id ? codes[code_id[b]].n : n0;
+            const int64_t o = cw_off ? cw_off[b] : (int64_t)b * n0;
+            for (int j = lane; j < n; j += 32)
+                to_cw[o + j] = cw[o + j];
+            if (lane == 0) {
+                to_q[b] = q[b];
+                to_ab[b] = ab[b];
+            }
+        }
+        return;
+    }
+    const uint64_t m = nheavy < cap ? nheavy : cap;
+    uint32_t *bq = (uint32_t *)(out + 16);
+    uint8_t *flag = out + 16 + 8 * (size_t)cap;
+    uint8_t *cwo = out + orbg_gather_cw_at(cap);
+    for (uint64_t h = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; h < m; h += step) {
+        const uint32_t b = (uint32_t)heavy[h]; /* low half: the block */
+        const int n = code_id ? codes[code_id[b]].n : n0;
+        const int64_t o = cw_off ? cw_off[b] : (int64_t)b * n0;
+        for (int j = lane; j < n; j += 32)
+            cwo[h * (uint64_t)n_max + j] = cw[o + j];
+        if (lane == 0) {
+            bq[2 * h] = b;
+            bq[2 * h + 1] = q[b];
+            flag[h] = ab[b];
+        }
+    }
+}
+
 }  // namespace
+
+int orbg_launch_heavy_gather(const OrbgDeviceCode *d_codes, const int32_t *code_id, int n0,
+                             const int64_t *cw_off, const uint8_t *cw, const uint32_t *q,
+                             const uint8_t *ab, const OrbgScratch &s, unsigned char *out,
+                             uint32_t cap, int n_max, uint8_t *to_cw, uint32_t *to_q,
+                             uint8_t *to_ab, void *stream)
+{
+    int dev = 0, sms = 1;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return (int)e;
+    orbg_heavy_gather_kernel<<<(unsigned)sms * 2, 256, 0, (cudaStream_t)stream>>>(
+        d_codes, code_id, n0, cw_off, cw, q, ab, s.counters, s.heavy, out, cap, n_max, to_cw, to_q,
+        to_ab);
+    return (int)cudaGetLastError();
+}
 
 int orbg_launch_code_sort(const int32_t *code_id, int64_t B, int ncodes, const OrbgScratch &s,
                           void *stream)

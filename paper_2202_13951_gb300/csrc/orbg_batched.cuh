@@ -53,7 +53,8 @@ __global__ void __launch_bounds__(256, ONE ? ORBG_PHASE1_MIN_CTAS : ORBG_PHASE1_
     const int64_t *__restrict__ llr_off, const float *__restrict__ llr, int64_t B, uint32_t cap,
     uint32_t budget, uint8_t *__restrict__ cw, const int64_t *__restrict__ cw_off,
     uint32_t *__restrict__ q, uint8_t *__restrict__ ab, unsigned long long *__restrict__ counters,
-    unsigned long long *__restrict__ heavy, const uint32_t *__restrict__ perm,
+    unsigned long long *__restrict__ queue, unsigned long long *__restrict__ heavy,
+    const uint32_t *__restrict__ perm,
     unsigned char *__restrict__ hand, uint32_t hand_cap, unsigned long long b_base,
     uint32_t bstride, uint32_t x3w_bytes, int grab, const __grid_constant__ OrbgDeviceCode code0)
 {
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(256, ONE ? ORBG_PHASE1_MIN_CTAS : ORBG_PHASE1_
         if (pos >= end) {
             unsigned long long c = 0;
             if (lane == 0)
-                c = atomicAdd(&counters[0], (unsigned long long)grab);
+                c = atomicAdd(queue, (unsigned long long)grab);
             c = __shfl_sync(FULL_MASK, c, 0);
             pos = (int64_t)c;
             end = min(pos + (int64_t)grab, B);
@@ -171,21 +172,29 @@ cudaError_t launch_t(const OrbgBatchedArgs &a)
             return cudaSuccess;
         return launch_heavy_t<KMAX, WMAX, ONE>(a, counters, heavy, sc.hand);
     }
+    /* this launch's slot: its queue head, code counts and cursors, and its
+     * blocks' part of the order array */
+    const int slot = a.stage == 1 && a.slot == 1 ? 1 : 0;
+    const size_t nc = (size_t)a.ncodes + 1;
+    unsigned long long *queue = counters + (slot ? 3 : 0);
+    OrbgScratch ss = sc;
+    ss.count = sc.count + 2 * nc * slot;
+    ss.cursor = ss.count + nc;
+    ss.perm = sc.perm + (a.stage == 1 ? a.scratch_base : 0);
     if (a.stage == 0 || a.first_chunk) {
         if ((e = cudaMemsetAsync(a.scratch, 0, sc.zero_bytes, st)) != cudaSuccess)
             return e;
     } else {
-        /* a later chunk: a fresh queue and code counts; the open-block list
-         * and the phase-2 cursor carry on */
-        if ((e = cudaMemsetAsync(counters, 0, sizeof(unsigned long long), st)) != cudaSuccess ||
-            (e = cudaMemsetAsync(sc.count, 0, sc.zero_bytes - 8 * ORBG_BATCHED_COUNTERS, st)) !=
-                cudaSuccess)
+        /* a later chunk: a fresh queue and code counts in its slot; the
+         * open-block list and the phase-2 cursor carry on */
+        if ((e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(ss.count, 0, 2 * nc * sizeof(uint32_t), st)) != cudaSuccess)
             return e;
     }
     /* codes that need different decoder variants: phase 1 takes the blocks
      * grouped by code, so one variant runs at a time */
     const bool sorted = !ONE && a.code_id != nullptr && a.ncodes > 1 && a.variants > 1;
-    if (sorted && (rc = orbg_launch_code_sort(a.code_id, a.B, a.ncodes, sc, st)) != 0)
+    if (sorted && (rc = orbg_launch_code_sort(a.code_id, a.B, a.ncodes, ss, st)) != 0)
         return (cudaError_t)rc;
     /* phase 1: per warp, one block's working set, two LLR slots and its own
      * triple table */
@@ -201,8 +210,8 @@ cudaError_t launch_t(const OrbgBatchedArgs &a)
     if (ONE)
         c0 = *a.code0;
     k1<<<grid, wpc * 32, smem1, st>>>(a.d_codes, a.ncodes, a.code_id, a.llr_off, a.llr, a.B,
-                                      a.cap, a.budget, a.cw, a.cw_off, a.q, a.ab, counters,
-                                      heavy, sorted ? sc.perm : nullptr, sc.hand, sc.hand_cap,
+                                      a.cap, a.budget, a.cw, a.cw_off, a.q, a.ab, counters, queue,
+                                      heavy, sorted ? ss.perm : nullptr, sc.hand, sc.hand_cap,
                                       (unsigned long long)a.scratch_base, bstride, x3w_bytes, g,
                                       c0);
     if ((e = cudaGetLastError()) != cudaSuccess)

@@ -168,8 +168,11 @@ struct OrbgBatchedArgs {
      * scratch_base + B - 1 of the whole batch (the pointers already point at
      * the chunk), first_chunk clears the scratch; 2: phase 2 only, over the
      * whole batch (pointers and B of the whole batch).  scratch_B: the
-     * batch's block count the scratch is laid out for (0 = B). */
+     * batch's block count the scratch is laid out for (0 = B).  slot (stage
+     * 1): the queue and code counts this launch uses (0 or 1); a launch
+     * resets its slot's unless it clears the whole scratch. */
     int stage;
+    int slot;
     int first_chunk;
     int64_t scratch_base;
     int64_t scratch_B;
@@ -183,11 +186,15 @@ ORBG_DECLARE_BATCHED(4, 1) ORBG_DECLARE_BATCHED(4, 2) ORBG_DECLARE_BATCHED(4, 4)
 ORBG_DECLARE_BATCHED(8, 1) ORBG_DECLARE_BATCHED(8, 2) ORBG_DECLARE_BATCHED(8, 4)
 #undef ORBG_DECLARE_BATCHED
 /* Device scratch of one batched call over B blocks of a set of ncodes codes,
- * in this order: ORBG_BATCHED_COUNTERS 64-bit counters (queue head, open-block
- * count, phase-2 cursor); per-code block counts and fill cursors (ncodes + 1
+ * in this order: ORBG_BATCHED_COUNTERS 64-bit counters (0: queue head of
+ * slot 0, 1: open-block count, 2: phase-2 cursor, 3: queue head of slot 1);
+ * for each of two slots, per-code block counts and fill cursors (ncodes + 1
  * uint32 each, the last for code ids outside the set); the list of open
  * blocks (B uint64); the blocks in phase 1's order, grouped by code (B
- * uint32).  The counters, counts and cursors start at zero. */
+ * uint32).  The counters, counts and cursors start at zero.  A phase-1
+ * launch uses one slot's queue and counts, so two launches over different
+ * chunks of a batch (the host-buffer pipeline's two decode streams) can run
+ * at the same time. */
 #define ORBG_BATCHED_COUNTERS 8
 #define ORBG_MAX_CODES 1024      /* codes in one set */
 size_t orbg_batched_scratch_bytes(int64_t B, int ncodes);
@@ -199,7 +206,7 @@ size_t orbg_batched_scratch_bytes(int64_t B, int ncodes);
 #define ORBG_HANDOVER_BYTES 272
 struct OrbgScratch {
     unsigned long long *counters;
-    uint32_t *count, *cursor;
+    uint32_t *count, *cursor;     /* slot 0's; slot 1's follow at + 2 (ncodes + 1) */
     unsigned long long *heavy;
     uint32_t *perm;
     unsigned char *hand;          /* handover records */
@@ -215,7 +222,7 @@ inline OrbgScratch orbg_scratch_layout(void *base, int64_t B, int ncodes)
     s.counters = (unsigned long long *)p;
     s.count = (uint32_t *)(p + 8 * ORBG_BATCHED_COUNTERS);
     s.cursor = s.count + nc;
-    s.zero_bytes = 8 * ORBG_BATCHED_COUNTERS + 8 * nc;
+    s.zero_bytes = 8 * ORBG_BATCHED_COUNTERS + 16 * nc;
     s.heavy = (unsigned long long *)(p + s.zero_bytes);
     s.perm = (uint32_t *)(s.heavy + b);
     const size_t hoff = ((size_t)((unsigned char *)(s.perm + b) - p) + 15) & ~(size_t)15;
@@ -230,6 +237,29 @@ inline OrbgScratch orbg_scratch_layout(void *base, int64_t B, int ncodes)
  * returns a cudaError_t. */
 int orbg_launch_code_sort(const int32_t *code_id, int64_t B, int ncodes, const OrbgScratch &s,
                           void *stream);
+/* Outputs of the blocks phase 2 decoded, gathered after the last launch of a
+ * batch whose other results already went to the host.  At `out` (memory the
+ * device writes, here host-mapped) the heavy list's length (uint64).  With
+ * to_cw, to_q, to_ab (the caller's output buffers, device-writable host
+ * memory laid out as cw, q, ab) every listed block's outputs are written
+ * there in place; otherwise `out` also takes, for the list's first `cap`
+ * entries, the block index and query count (uint32 pairs), the flag byte,
+ * and from orbg_gather_cw_at(cap) the codeword bytes at a stride of n_max.
+ * code_id / cw_off NULL: one code of length n0, dense codewords.  Returns a
+ * cudaError_t. */
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline size_t orbg_gather_cw_at(uint32_t cap) { return (16 + 9 * (size_t)cap + 15) & ~(size_t)15; }
+inline size_t orbg_gather_bytes(uint32_t cap, int n_max)
+{
+    return orbg_gather_cw_at(cap) + (size_t)cap * (size_t)n_max;
+}
+int orbg_launch_heavy_gather(const OrbgDeviceCode *d_codes, const int32_t *code_id, int n0,
+                             const int64_t *cw_off, const uint8_t *cw, const uint32_t *q,
+                             const uint8_t *ab, const OrbgScratch &s, unsigned char *out,
+                             uint32_t cap, int n_max, uint8_t *to_cw, uint32_t *to_q,
+                             uint8_t *to_ab, void *stream);
 int orbg_grid_for(const void *kern, int threads, size_t smem, int ctas_per_sm, int *grid_out);
 
 /* A named range on the NVTX timeline for the span of a scope (header-only

@@ -13,7 +13,7 @@
  * The array is a file-scope __device__ variable: every GPU that loads the
  * library holds it (the batched form's scratch for ORBG_NOALLOC_MAX_BLOCKS
  * blocks of a set of up to 1024 codes: 12 bytes per block, 8,264 bytes of
- * counters and 8.5 MiB of handover records, 14.5 MiB + 8,280 B in all) until
+ * counters and 8.5 MiB of handover records, 14.5 MiB + 16,480 B in all) until
  * the process exits.  Host code cannot use the variable's name as a
  * device address, so the first call on each device, with that device
  * current, asks the runtime for the address (cudaGetSymbolAddress) and keeps
@@ -38,7 +38,7 @@ constexpr int kMaxDevices = 64;
  * orbg_scratch_layout places it: counters, per-code counts and cursors, the
  * open-block list and phase 1's block order. */
 constexpr size_t kScratchWords =
-    (8 * ORBG_BATCHED_COUNTERS + 8 * (ORBG_MAX_CODES + 1) + 12 * (size_t)ORBG_NOALLOC_MAX_BLOCKS +
+    (8 * ORBG_BATCHED_COUNTERS + 16 * (ORBG_MAX_CODES + 1) + 12 * (size_t)ORBG_NOALLOC_MAX_BLOCKS +
      15 + (size_t)ORBG_HANDOVER_BYTES * ORBG_HANDOVER_MAX + 7) / 8;
 static __device__ __align__(256) unsigned long long g_orbg_noalloc_scratch[kScratchWords];
 

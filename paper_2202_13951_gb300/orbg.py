@@ -108,6 +108,7 @@ def load_library(path=None):
     lib.orbg_status_string.argtypes = [i32]
     lib.orbg_status_string.restype = ctypes.c_char_p
     lib.orbg_last_cuda_error.argtypes = []
+    lib.orbg_pool_trim.argtypes = []
     lib.orbg_version.argtypes = []
     lib.orbg_query_order.argtypes = [i32, u32, i32, vp]
     lib.orbg_query_order.restype = i64
@@ -138,7 +139,7 @@ def load_library(path=None):
               "orbg_codeset_set_tuning", "orbg_codeset_get_tuning", "orbg_probe_int_lanes",
               "orbg_probe_smem_bytes", "orbg_codeset_autotune", "orbg_fit_models",
               "orbg_fitted_create", "orbg_fitted_decode", "orbg_fitted_free",
-              "orbg_decode_fitted", "orbg_last_cuda_error", "orbg_version"):
+              "orbg_decode_fitted", "orbg_last_cuda_error", "orbg_pool_trim", "orbg_version"):
         getattr(lib, f).restype = i32
     if path == LIB_PATH:
         _lib = lib
@@ -398,6 +399,11 @@ def orbg_status_string(status):
 
 def orbg_last_cuda_error():
     return load_library().orbg_last_cuda_error()
+
+
+def orbg_pool_trim():
+    """Return the device memory the library's pool holds unused."""
+    _check(load_library().orbg_pool_trim(), "orbg_pool_trim")
 
 
 def orbg_version():

@@ -287,6 +287,65 @@ def test_pipelined_host_buffers_mixed_codes(orbg):
     assert np.array_equal(ab, ab_d.cpu().numpy())
 
 
+def test_pipelined_host_buffers_many_phase2_blocks(orbg):
+    """With a phase-1 budget of one query nearly every block goes to phase 2:
+    more than the 65,536 whose outputs the chunked path gathers, so it copies
+    every output again after phase 2; with a budget of 64 fewer go, and the
+    gathered outputs land over the chunk copies.  Both equal the unchunked
+    device-buffer call."""
+    code = workloads.config2_code()
+    llr = workloads.awgn_llr(code, 160_000, 3.5, 4406)[0]
+    B, n = llr.shape
+    cs = orbg.CodeSet([orbg.Code(code.H, max_query_cap=10 ** 4)])
+    for budget in (1, 64):
+        orbg.orbg_codeset_set_tuning(cs.handle, orbg.OrbgTuning(8, 0, 4, budget, 8))
+        dev = gpu_batched(orbg, cs, llr, 10 ** 4)
+        if budget == 1:
+            assert (dev[1] > 1).sum() > 65536
+        cw = np.zeros((B, n), np.uint8)
+        q = np.zeros(B, np.uint32)
+        ab = np.zeros(B, np.uint8)
+        orbg.orbg_decode_batched(cs.handle, None, None, llr, B, 10 ** 4, cw, None, q, ab)
+        assert_same((cw, q.astype(np.int64), ab), dev)
+
+
+def test_pipelined_host_buffers_unordered_and_invalid(orbg):
+    """Host offsets that do not place the blocks in order (here the second
+    half before the first) take the unchunked path with the same results;
+    a code id outside the set in a late chunk is rejected (ORBG_EINVAL)
+    with the outputs untouched."""
+    codes, cid, llr, off, _, _ = workloads.config4_inputs(B=140_000, seed=4405)
+    cs = orbg.CodeSet([orbg.Code(cd.H, max_query_cap=10 ** 4) for cd in codes])
+    B = cid.shape[0]
+    n_total = llr.shape[0]
+    half = B // 2
+    perm = np.concatenate([np.arange(half, B), np.arange(half)])
+    cid2, off2 = cid[perm].copy(), off[perm].copy()
+    cw_d, q_d, ab_d = orbg.decode_batched(cs, torch.from_numpy(llr).cuda(), 10 ** 4,
+                                          code_id=torch.from_numpy(cid2).cuda(),
+                                          llr_offset=torch.from_numpy(off2).cuda(),
+                                          cw_offset=torch.from_numpy(off2).cuda(),
+                                          n_total=n_total)
+    torch.cuda.synchronize()
+    cw = np.zeros(n_total, np.uint8)
+    q = np.zeros(B, np.uint32)
+    ab = np.zeros(B, np.uint8)
+    orbg.orbg_decode_batched(cs.handle, cid2, off2, llr, B, 10 ** 4, cw, off2, q, ab)
+    assert np.array_equal(cw, cw_d.cpu().numpy())
+    assert np.array_equal(q, q_d.cpu().numpy().astype(np.uint32))
+    assert np.array_equal(ab, ab_d.cpu().numpy())
+    bad = cid.copy()
+    bad[B - 3] = len(codes)
+    cw[:] = 0
+    q[:] = 0
+    ab[:] = 0
+    with pytest.raises(orbg.OrbgError) as ei:
+        orbg.orbg_decode_batched(cs.handle, bad, off, llr, B, 10 ** 4, cw, off, q, ab)
+    assert ei.value.status == orbg.ORBG_EINVAL
+    assert not cw.any() and not q.any() and not ab.any()
+    orbg.orbg_pool_trim()
+
+
 def test_batched_call_in_cuda_graph(orbg):
     """A batched call on device buffers (stream-ordered scratch allocation,
     counter reset, both launches) captures into a CUDA graph; every replay
