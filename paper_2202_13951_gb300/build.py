@@ -56,6 +56,19 @@ def _digest(extra=()):
     return h.hexdigest()
 
 
+def kernel_digest():
+    """SHA-256 of the device code alone (the CUDA sources and the headers
+    they include): profiler figures taken on one build stay valid while it
+    is unchanged, whatever happens to the host-only C++ around it."""
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(CSRC)):
+        if name.endswith((".cu", ".cuh")) or name == "orbg_internal.h":
+            h.update(name.encode())
+            with open(os.path.join(CSRC, name), "rb") as f:
+                h.update(hashlib.sha256(f.read()).digest())
+    return h.hexdigest()
+
+
 def _stale(digest):
     if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return True
