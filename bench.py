@@ -754,14 +754,33 @@ class Job:
                         "abandon_rate": float((ab[sl] == 1).mean())})
         return out
 
+    def variants(self):
+        """Decoder variants among the job's codes, as the library counts
+        them: keys per lane from n (<= 32, 64, 128, 256) and syndrome words
+        (1, 2, 3-4)."""
+        kw = set()
+        for c in self.codes:
+            n, r = c.n, c.r
+            w = (r + 31) // 32
+            kw.add((1 if n <= 32 else 2 if n <= 64 else 4 if n <= 128 else 8,
+                    1 if w <= 1 else 2 if w == 2 else 4))
+        return len(kw)
+
     def launches_per_step(self):
-        """Kernels of this library launched by one step."""
+        """Kernels of this library launched by one step: per-block codes
+        (code ids) run phase 1 as one launch per decoder variant, after a
+        two-kernel grouping by variant when there are several; phase 2 is
+        one launch unless the phase-1 budget reaches the cap."""
         if self.form == "plain" or self.search:
             return 1
-        sort = 2 if (self.off_np is not None and len(self.codes) > 1) else 0
+        budget = self.orbg.orbg_codeset_get_tuning(self.cs.handle).warp_budget
+        phase2 = 0 if budget >= CAP else 1
         if self.fitted is not None:
-            return 3 + 2 + 2  # fit, mark, map; code sort (a set of one handle per line); phases
-        return 2 + sort
+            return 3 + 1 + phase2  # fit, mark, map; one variant (handles of one code); phase 2
+        if self.off_np is not None:
+            v = self.variants()
+            return (2 if v > 1 else 0) + v + phase2
+        return 1 + phase2
 
     def kernel_names(self):
         if self.form == "plain":
@@ -771,8 +790,9 @@ class Job:
         names = "orbg_batched_kernel + orbg_heavy_kernel"
         if self.fitted is not None:
             return "orbg_fit_kernel + line marking + " + names
-        if self.off_np is not None and len(self.codes) > 1:
-            names += " + the two code-sort kernels"
+        if self.off_np is not None and self.variants() > 1:
+            names = ("orbg_batched_kernel (one launch per decoder variant) + orbg_heavy_kernel "
+                     "+ the two code-sort kernels")
         return names
 
     def autotune(self):

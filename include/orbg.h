@@ -189,24 +189,33 @@ ORBG_API int orbg_codeset_free(orbg_codeset *set);
  *   cw_offset  : [B] byte offset of block b in codeword, or NULL (dense).
  *   Other arguments as orbg_decode; query_cap must be within every code's
  *   max_query_cap.
- * The call uses 95 + 16 ncodes + 12 B + 272 min(B, 32768) bytes of
+ * The call uses 287 + 16 ncodes + 12 B + 272 min(B, 32768) bytes of
  * stream-ordered device scratch (queue counters, per-code block counts, the
- * list of still-open blocks, the blocks' order grouped by code, and the
- * reliability order of up to 32,768 still-open blocks, which the second
- * launch reuses), allocated and freed on cuda_stream.  With code_id given
- * and codes of different length classes (n <= 32, 64, 128, 256) or
- * syndrome widths in the set, the first launch takes the blocks grouped by
- * code.
+ * list of still-open blocks, the blocks' order grouped by decoder variant,
+ * and the reliability order of up to 32,768 still-open blocks, which the
+ * second launch reuses), allocated on cuda_stream from the library's pool
+ * (orbg_pool_trim).  With code_id given, the first launch is one launch per
+ * decoder variant among the set's codes (length class n <= 32, 64, 128,
+ * 256 and syndrome width 1, 2 or 3-4 words), each of that variant alone;
+ * with several variants the blocks are first grouped by variant on the
+ * device, and each variant's launch may begin while the previous one
+ * finishes (programmatic dependent launch).  A code id outside the set
+ * gives its block queries 0 and flag ORBG_BLOCK_NAN with its codeword
+ * bytes untouched (with host layout arrays and offsets: ORBG_EINVAL).
  * Host buffers (staged through stream-ordered device copies): a call with
  * every buffer on the host, B >= 131072 and a layout that places the
  * blocks in order without overlap (dense, or offsets that never go back)
- * is cut into up to eight chunks: each chunk's copy in overlaps the first
- * launch over the chunks before it, the second launch runs once over the
- * blocks every chunk left open, and the results are then copied out, on
- * three library-owned streams (created on the set's first such call);
- * cuda_stream waits for them and is synchronised before the call returns,
- * as for any host-buffer call.  With host buffers and offsets, codeword
- * bytes between blocks are unspecified afterwards.
+ * is cut into up to eight chunks on four library-owned streams (created
+ * on the set's first such call): each chunk's copy in, then the first
+ * launch over it on one of two decode streams in turn (so a chunk's launch
+ * can fill what the previous one leaves idle), then its results out; the
+ * second launch runs once over the blocks every chunk left open, and their
+ * results are written over the copies (by the device straight into page-
+ * locked output buffers, else through a host-mapped staging buffer).  One
+ * such call runs at a time per set.  cuda_stream waits for the streams and
+ * is synchronised before the call returns, as for any host-buffer call.
+ * With host buffers and offsets, codeword bytes between blocks are
+ * unspecified afterwards.
  * Results are identical to orbg_decode's block by block.
  * Paper: Algorithm 1 per block; the batching is this library's.
  */
@@ -232,8 +241,8 @@ ORBG_API int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id
  *     staging): EINVAL otherwise.
  *   - B <= ORBG_NOALLOC_MAX_BLOCKS (524,288), else ELIMIT.  Larger batches
  *     can be split into several calls.
- *   - The array is 12 * ORBG_NOALLOC_MAX_BLOCKS + 16,480 + 272 * 32,768
- *     bytes (14.5 MiB + 16,480 B) of device memory per GPU that loads the
+ *   - The array is 12 * ORBG_NOALLOC_MAX_BLOCKS + 16,672 + 272 * 32,768
+ *     bytes (14.5 MiB + 16,672 B) of device memory per GPU that loads the
  *     library, held until the process exits.
  *   - The first call on each device looks up the array's device address
  *     (with that device current) and keeps it; make that first call before

@@ -37,7 +37,8 @@ struct orbg_code {
 
 struct orbg_codeset {
     int ncodes, n_max, w32_max;
-    int variants;                /* distinct (keys per lane, syndrome words) of the codes */
+    OrbgVariants var;            /* decoder variants and the codes' sort buckets */
+    int32_t *d_bucket = nullptr; /* [ncodes] sort bucket of each code (var.d_bucket) */
     uint32_t ntrip_max;
     uint32_t x3w_max;
     orbg_tuning tuning;
@@ -262,7 +263,7 @@ int orbg_codeset_view(const orbg_codeset *set, OrbgSetView *out)
     out->ncodes = set->ncodes;
     out->n_max = set->n_max;
     out->w32_max = set->w32_max;
-    out->variants = set->variants;
+    out->var = set->var;
     out->ntrip_max = set->ntrip_max;
     out->x3w_max = set->x3w_max;
     out->cap_min = set->cap_min;
@@ -718,27 +719,48 @@ int orbg_codeset_create(const orbg_code *const *codes, int ncodes, orbg_codeset 
         s->ntrip_max = std::max(s->ntrip_max, codes[i]->dev.ntrip);
         s->x3w_max = std::max(s->x3w_max, codes[i]->dev.x3w);
     }
+    /* the decoder variants the kernels specialise on: keys per lane from n
+     * (n <= 32, 64, 128, 256: 1, 2, 4, 8) and the syndrome words (1, 2, or
+     * 4 for 3-4); the codes in order of (variant, id) number the sort
+     * buckets, so each variant's codes hold consecutive buckets */
+    std::vector<int32_t> bucket((size_t)ncodes);
     {
-        /* the decoder variants the kernels dispatch to: keys per lane from
-         * n (n <= 32, 64, 128, 256) and the syndrome width */
-        std::vector<int> kw;
+        std::vector<int> key((size_t)ncodes), ord((size_t)ncodes);
         for (int i = 0; i < ncodes; i++) {
-            const int n = codes[i]->n;
-            const int kc = n <= 32 ? 0 : n <= 64 ? 1 : n <= 128 ? 2 : 3;
-            kw.push_back(kc * 8 + codes[i]->w32);
+            const int n = codes[i]->n, w = codes[i]->w32;
+            key[i] = (n <= 32 ? 1 : n <= 64 ? 2 : n <= 128 ? 4 : 8) * 8 +
+                     (w <= 1 ? 1 : w == 2 ? 2 : 4);
+            ord[i] = i;
         }
-        std::sort(kw.begin(), kw.end());
-        s->variants = (int)(std::unique(kw.begin(), kw.end()) - kw.begin());
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return key[x] < key[y]; });
+        OrbgVariants &v = s->var;
+        v = OrbgVariants{};
+        for (int j = 0; j < ncodes; j++) {
+            bucket[ord[j]] = j;
+            if (j == 0 || key[ord[j]] != key[ord[j - 1]]) {
+                v.k[v.n] = key[ord[j]] / 8;
+                v.w[v.n] = key[ord[j]] % 8;
+                v.blo[v.n] = j;
+                v.n++;
+            }
+            v.bhi[v.n - 1] = j + 1;
+        }
+        v.bhi[v.n - 1] = ncodes + 1; /* ids outside the set go with the last variant */
     }
     cudaError_t e;
     if ((e = cudaGetDevice(&s->device)) != cudaSuccess ||
         (e = cudaMalloc(&s->d_codes, descs.size() * sizeof(OrbgDeviceCode))) != cudaSuccess ||
         (e = cudaMemcpy(s->d_codes, descs.data(), descs.size() * sizeof(OrbgDeviceCode),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMalloc(&s->d_bucket, bucket.size() * sizeof(int32_t))) != cudaSuccess ||
+        (e = cudaMemcpy(s->d_bucket, bucket.data(), bucket.size() * sizeof(int32_t),
                         cudaMemcpyHostToDevice)) != cudaSuccess) {
         if (s->d_codes) cudaFree(s->d_codes);
+        if (s->d_bucket) cudaFree(s->d_bucket);
         delete s;
         return cuda_fail(e);
     }
+    s->var.d_bucket = s->d_bucket;
     *out = s;
     return ORBG_OK;
 }
@@ -749,6 +771,8 @@ int orbg_codeset_free(orbg_codeset *set)
         return ORBG_OK;
     if (set->d_codes)
         cudaFree(set->d_codes);
+    if (set->d_bucket)
+        cudaFree(set->d_bucket);
     for (cudaStream_t s : set->pipe)
         if (s)
             cudaStreamDestroy(s);
@@ -903,7 +927,7 @@ int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
     a.ncodes = set->ncodes;
     a.n_max = set->n_max;
     a.w32_max = set->w32_max;
-    a.variants = set->variants;
+    a.var = set->var;
     a.cap = query_cap;
     a.budget = t.warp_budget < query_cap ? t.warp_budget : query_cap;
     a.scratch = scratch;
@@ -1157,7 +1181,7 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
     a.ncodes = set->ncodes;
     a.n_max = set->n_max;
     a.w32_max = set->w32_max;
-    a.variants = set->variants;
+    a.var = set->var;
     a.code_id = d_cid;
     a.llr_off = d_lo;
     a.llr = d_llr;
@@ -1462,7 +1486,7 @@ int orbg_fitted_decode(orbg_fitted *f, const float *llr, int64_t B, uint32_t que
         a.ncodes = set->ncodes;
         a.n_max = set->n_max;
         a.w32_max = set->w32_max;
-        a.variants = set->variants;
+        a.var = set->var;
         a.code_id = d_cid;
         a.llr_off = nullptr;
         a.llr = llr;

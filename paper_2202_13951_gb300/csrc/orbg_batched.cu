@@ -43,15 +43,17 @@ namespace {
 constexpr int kSortThreads = 256;
 constexpr int kSortChunk = 4096; /* blocks per CTA of the scatter */
 
-/* code id of block b as the sort buckets it: ids outside the set go last */
-__device__ __forceinline__ int sort_bucket(const int32_t *code_id, int64_t b, int ncodes)
+/* the sort bucket of block b: its code's, ids outside the set last */
+__device__ __forceinline__ int sort_bucket(const int32_t *code_id, const int32_t *bucket,
+                                           int64_t b, int ncodes)
 {
     const int c = code_id[b];
-    return c >= 0 && c < ncodes ? c : ncodes;
+    return c >= 0 && c < ncodes ? bucket[c] : ncodes;
 }
 
 __global__ void __launch_bounds__(kSortThreads) orbg_code_count_kernel(
-    const int32_t *__restrict__ code_id, int64_t B, int ncodes, uint32_t *__restrict__ count)
+    const int32_t *__restrict__ code_id, const int32_t *__restrict__ bucket, int64_t B,
+    int ncodes, uint32_t *__restrict__ count)
 {
     extern __shared__ uint32_t h[];
     for (int i = threadIdx.x; i <= ncodes; i += blockDim.x)
@@ -59,7 +61,7 @@ __global__ void __launch_bounds__(kSortThreads) orbg_code_count_kernel(
     __syncthreads();
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B;
          b += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&h[sort_bucket(code_id, b, ncodes)], 1u);
+        atomicAdd(&h[sort_bucket(code_id, bucket, b, ncodes)], 1u);
     __syncthreads();
     for (int i = threadIdx.x; i <= ncodes; i += blockDim.x)
         if (h[i])
@@ -70,7 +72,7 @@ __global__ void __launch_bounds__(kSortThreads) orbg_code_count_kernel(
  * code, reserves a range of each code's slots with one global atomic per
  * code, and writes its blocks there (in chunk order within a code). */
 __global__ void __launch_bounds__(kSortThreads) orbg_code_scatter_kernel(
-    const int32_t *__restrict__ code_id, int64_t B, int ncodes,
+    const int32_t *__restrict__ code_id, const int32_t *__restrict__ bucket, int64_t B, int ncodes,
     const uint32_t *__restrict__ count, uint32_t *__restrict__ cursor,
     uint32_t *__restrict__ perm)
 {
@@ -90,13 +92,13 @@ __global__ void __launch_bounds__(kSortThreads) orbg_code_scatter_kernel(
         local[i] = 0;
     __syncthreads();
     for (int64_t b = lo + threadIdx.x; b < hi; b += blockDim.x)
-        atomicAdd(&local[sort_bucket(code_id, b, ncodes)], 1u);
+        atomicAdd(&local[sort_bucket(code_id, bucket, b, ncodes)], 1u);
     __syncthreads();
     for (int i = threadIdx.x; i <= ncodes; i += blockDim.x)
         local[i] = local[i] ? base[i] + atomicAdd(&cursor[i], local[i]) : 0u;
     __syncthreads();
     for (int64_t b = lo + threadIdx.x; b < hi; b += blockDim.x)
-        perm[atomicAdd(&local[sort_bucket(code_id, b, ncodes)], 1u)] = (uint32_t)b;
+        perm[atomicAdd(&local[sort_bucket(code_id, bucket, b, ncodes)], 1u)] = (uint32_t)b;
 }
 
 /* one warp per heavy-list entry; the lanes copy the codeword bytes */
@@ -166,8 +168,8 @@ int orbg_launch_heavy_gather(const OrbgDeviceCode *d_codes, const int32_t *code_
     return (int)cudaGetLastError();
 }
 
-int orbg_launch_code_sort(const int32_t *code_id, int64_t B, int ncodes, const OrbgScratch &s,
-                          void *stream)
+int orbg_launch_code_sort(const int32_t *code_id, const int32_t *bucket, int64_t B, int ncodes,
+                          const OrbgScratch &s, void *stream)
 {
     cudaStream_t st = (cudaStream_t)stream;
     const size_t sh1 = sizeof(uint32_t) * (size_t)(ncodes + 1);
@@ -179,13 +181,31 @@ int orbg_launch_code_sort(const int32_t *code_id, int64_t B, int ncodes, const O
     int64_t g1 = (B + kSortThreads - 1) / kSortThreads;
     if (g1 > (int64_t)sms * 8)
         g1 = (int64_t)sms * 8;
-    orbg_code_count_kernel<<<(unsigned)g1, kSortThreads, sh1, st>>>(code_id, B, ncodes, s.count);
+    orbg_code_count_kernel<<<(unsigned)g1, kSortThreads, sh1, st>>>(code_id, bucket, B, ncodes,
+                                                                    s.count);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return (int)e;
     const int64_t g2 = (B + kSortChunk - 1) / kSortChunk;
     orbg_code_scatter_kernel<<<(unsigned)g2, kSortThreads, 2 * sh1, st>>>(
-        code_id, B, ncodes, s.count, s.cursor, s.perm);
+        code_id, bucket, B, ncodes, s.count, s.cursor, s.perm);
     return (int)cudaGetLastError();
+}
+
+int orbg_launch_exact(int K, int W, const OrbgBatchedArgs &a, const OrbgScratch &s,
+                      unsigned long long *queue, int blo, int bhi, int pdl)
+{
+#define ORBG_EX(KK)                                                                         \
+    return W <= 1   ? orbg_launch_exact_k##KK##w1(a, s, queue, blo, bhi, pdl)               \
+           : W == 2 ? orbg_launch_exact_k##KK##w2(a, s, queue, blo, bhi, pdl)               \
+                    : orbg_launch_exact_k##KK##w4(a, s, queue, blo, bhi, pdl);
+    if (K <= 1)
+        ORBG_EX(1)
+    if (K == 2)
+        ORBG_EX(2)
+    if (K == 4)
+        ORBG_EX(4)
+    ORBG_EX(8)
+#undef ORBG_EX
 }
 
 int orbg_launch_batched(const OrbgBatchedArgs &args)

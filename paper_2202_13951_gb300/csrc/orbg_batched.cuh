@@ -36,9 +36,9 @@ using namespace orbg_dev;
 constexpr int kCounters = ORBG_BATCHED_COUNTERS;
 
 /* resident phase-1 CTAs per SM the register allocation is sized for: three
- * for one code (80 registers, no spills), two for mixed codes (the kernel
- * holding every variant spilled at 80; at two it holds them in registers,
- * and the measured step of the mixed 1,000,000-block batch drops 5 %) */
+ * for one code or one decoder variant (80 registers, no spills), two for
+ * the kernel that dispatches per block (holding every variant it spilled at
+ * 80; at two it holds them in registers) */
 #ifndef ORBG_PHASE1_MIN_CTAS
 #define ORBG_PHASE1_MIN_CTAS 3
 #endif
@@ -46,8 +46,16 @@ constexpr int kCounters = ORBG_BATCHED_COUNTERS;
 #define ORBG_PHASE1_MIN_CTAS_MIXED 2
 #endif
 
-template <int KMAX, int WMAX, bool ONE>
-__global__ void __launch_bounds__(256, ONE ? ORBG_PHASE1_MIN_CTAS : ORBG_PHASE1_MIN_CTAS_MIXED)
+/* How a phase-1 kernel finds each block's decoder: P1_ONE every block is
+ * the code in the kernel's parameters; P1_GENERIC each block's code from the
+ * device array, dispatched to K <= KMAX, W <= WMAX; P1_EXACT each block's
+ * code from the device array, all of keys per lane KMAX and width WMAX (one
+ * decoder variant per launch, the blocks taken from their sort buckets). */
+enum { P1_ONE = 0, P1_GENERIC = 1, P1_EXACT = 2 };
+
+template <int KMAX, int WMAX, int MODE>
+__global__ void __launch_bounds__(256, MODE == P1_GENERIC ? ORBG_PHASE1_MIN_CTAS_MIXED
+                                                          : ORBG_PHASE1_MIN_CTAS)
     orbg_batched_kernel(
     const OrbgDeviceCode *__restrict__ codes, int ncodes, const int32_t *__restrict__ code_id,
     const int64_t *__restrict__ llr_off, const float *__restrict__ llr, int64_t B, uint32_t cap,
@@ -56,8 +64,10 @@ __global__ void __launch_bounds__(256, ONE ? ORBG_PHASE1_MIN_CTAS : ORBG_PHASE1_
     unsigned long long *__restrict__ queue, unsigned long long *__restrict__ heavy,
     const uint32_t *__restrict__ perm,
     unsigned char *__restrict__ hand, uint32_t hand_cap, unsigned long long b_base,
-    uint32_t bstride, uint32_t x3w_bytes, int grab, const __grid_constant__ OrbgDeviceCode code0)
+    uint32_t bstride, uint32_t x3w_bytes, int grab, const uint32_t *__restrict__ range_count,
+    int blo, int bhi, const __grid_constant__ OrbgDeviceCode code0)
 {
+    constexpr bool ONE = MODE == P1_ONE;
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -72,10 +82,31 @@ __global__ void __launch_bounds__(256, ONE ? ORBG_PHASE1_MIN_CTAS : ORBG_PHASE1_
                                                  warp * x3w_bytes);
     const int64_t n0 = ONE ? code0.n : codes[0].n;
 
+    /* the queue's slots: all B, or (range_count: the per-bucket counts of
+     * the sort into perm) the slots of buckets [blo, bhi) */
+    int64_t slot_lo = 0, slot_hi = B;
+    if (range_count) {
+        uint32_t before = 0, inside = 0;
+        for (int i = lane; i < bhi; i += 32) {
+            const uint32_t c = range_count[i];
+            if (i < blo)
+                before += c;
+            else
+                inside += c;
+        }
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) {
+            before += __shfl_xor_sync(FULL_MASK, before, m);
+            inside += __shfl_xor_sync(FULL_MASK, inside, m);
+        }
+        slot_lo = before;
+        slot_hi = (int64_t)before + inside;
+    }
     /* the warp's block sequence: `grab` consecutive queue slots per atomic;
      * with perm (mixed codes) slot i holds the block perm[i], so that the
-     * blocks of one code are decoded together (one variant of the decoder
-     * runs at a time and its instructions stay cached) */
+     * blocks of one decoder variant are decoded together.  A warp that finds
+     * the queue empty lets a programmatically dependent launch (the next
+     * variant's) start on the SMs this one's last blocks leave idle. */
     int64_t pos = 0, end = 0;
     auto next_block = [&]() -> int64_t {
         if (pos >= end) {
@@ -83,10 +114,12 @@ __global__ void __launch_bounds__(256, ONE ? ORBG_PHASE1_MIN_CTAS : ORBG_PHASE1_
             if (lane == 0)
                 c = atomicAdd(queue, (unsigned long long)grab);
             c = __shfl_sync(FULL_MASK, c, 0);
-            pos = (int64_t)c;
-            end = min(pos + (int64_t)grab, B);
-            if (pos >= B)
+            pos = slot_lo + (int64_t)c;
+            end = min(pos + (int64_t)grab, slot_hi);
+            if (pos >= slot_hi) {
+                asm volatile("griddepcontrol.launch_dependents;");
                 return B;
+            }
         }
         const int64_t slot = pos++;
         return perm ? (int64_t)__ldg(perm + slot) : slot;
@@ -134,6 +167,12 @@ __global__ void __launch_bounds__(256, ONE ? ORBG_PHASE1_MIN_CTAS : ORBG_PHASE1_
                 q[b] = 0u;
                 ab[b] = 2;
             }
+        } else if (MODE == P1_EXACT) {
+            /* one decoder variant: K and W exact; the block's descriptor is
+             * read where it is used (a register copy of it spilled) */
+            decode_block_warp<KMAX, WMAX, true, true, (KMAX <= 4), (KMAX >= 8)>(
+                codes[cid], l, cw + co, q + b, ab + b, cap, budget, bsm, lane, heavy, &counters[1],
+                b_base + (unsigned long long)b, X3w, hand, hand_cap);
         } else {
             const OrbgDeviceCode code = codes[cid];
 #define ORBG_CALL_WARP(KK, WW)                                                                 \
@@ -150,8 +189,56 @@ __global__ void __launch_bounds__(256, ONE ? ORBG_PHASE1_MIN_CTAS : ORBG_PHASE1_
         slot ^= 1;
     }
     __pipeline_wait_prior(0);
+    /* a launch that may have started before the previous one in its stream
+     * ended completes only after it (a no-op for any other launch), so the
+     * next ordinary launch sees every phase-1 block finished */
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
+
+/* Phase 1 of one decoder variant (K, W): the blocks of sort buckets
+ * [blo, bhi) of ss.perm (blo < 0: every block, in order), on its own queue.
+ * pdl: the launch may begin while the previous launch in the stream (the
+ * previous variant's) finishes its last blocks. */
+template <int K, int W>
+int launch_exact_t(const OrbgBatchedArgs &a, const OrbgScratch &ss, unsigned long long *queue,
+                   int blo, int bhi, int pdl)
+{
+    const int wpc = a.warps_per_cta > 0 ? (a.warps_per_cta > 8 ? 8 : a.warps_per_cta) : 8;
+    const int g = a.grab < 1 ? 1 : a.grab;
+    const int nk = a.n_max < 32 * K ? a.n_max : 32 * K;
+    const uint32_t bstride = block_smem_bytes(nk, W);
+    auto k1 = orbg_batched_kernel<K, W, P1_EXACT>;
+    const uint32_t x3w_bytes = triple_table_bytes(a.x3w_max);
+    const size_t smem1 = ((size_t)bstride + 2u * 32u * K * sizeof(float) + x3w_bytes) * wpc;
+    int grid = 0;
+    int rc = orbg_grid_for((const void *)k1, wpc * 32, smem1, a.ctas_per_sm, &grid);
+    if (rc != 0)
+        return rc;
+    if (blo < 0) {
+        const int64_t need = ((a.B + g - 1) / g + wpc - 1) / wpc;
+        if (grid > need)
+            grid = (int)(need > 0 ? need : 1);
+    }
+    const bool sorted = blo >= 0;
+    OrbgDeviceCode c0{};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)(wpc * 32));
+    cfg.dynamicSmemBytes = smem1;
+    cfg.stream = (cudaStream_t)a.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return (int)cudaLaunchKernelEx(
+        &cfg, k1, a.d_codes, a.ncodes, a.code_id, a.llr_off, a.llr, a.B, a.cap, a.budget, a.cw,
+        a.cw_off, a.q, a.ab, ss.counters, queue, ss.heavy,
+        sorted ? (const uint32_t *)ss.perm : (const uint32_t *)nullptr, ss.hand, ss.hand_cap,
+        (unsigned long long)a.scratch_base, bstride, x3w_bytes, g,
+        sorted ? (const uint32_t *)ss.count : (const uint32_t *)nullptr, blo, bhi, c0);
+}
 
 template <int KMAX, int WMAX, bool ONE>
 cudaError_t launch_t(const OrbgBatchedArgs &a)
@@ -172,11 +259,12 @@ cudaError_t launch_t(const OrbgBatchedArgs &a)
             return cudaSuccess;
         return launch_heavy_t<KMAX, WMAX, ONE>(a, counters, heavy, sc.hand);
     }
-    /* this launch's slot: its queue head, code counts and cursors, and its
-     * blocks' part of the order array */
+    /* this launch's slot: its queue heads, bucket counts and cursors, and
+     * its blocks' part of the order array */
     const int slot = a.stage == 1 && a.slot == 1 ? 1 : 0;
     const size_t nc = (size_t)a.ncodes + 1;
     unsigned long long *queue = counters + (slot ? 3 : 0);
+    unsigned long long *vqueue = counters + 8 + ORBG_MAX_VARIANTS * slot;
     OrbgScratch ss = sc;
     ss.count = sc.count + 2 * nc * slot;
     ss.cursor = ss.count + nc;
@@ -185,37 +273,52 @@ cudaError_t launch_t(const OrbgBatchedArgs &a)
         if ((e = cudaMemsetAsync(a.scratch, 0, sc.zero_bytes, st)) != cudaSuccess)
             return e;
     } else {
-        /* a later chunk: a fresh queue and code counts in its slot; the
+        /* a later chunk: fresh queues and bucket counts in its slot; the
          * open-block list and the phase-2 cursor carry on */
         if ((e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(vqueue, 0, ORBG_MAX_VARIANTS * sizeof(unsigned long long),
+                                 st)) != cudaSuccess ||
             (e = cudaMemsetAsync(ss.count, 0, 2 * nc * sizeof(uint32_t), st)) != cudaSuccess)
             return e;
     }
-    /* codes that need different decoder variants: phase 1 takes the blocks
-     * grouped by code, so one variant runs at a time */
-    const bool sorted = !ONE && a.code_id != nullptr && a.ncodes > 1 && a.variants > 1;
-    if (sorted && (rc = orbg_launch_code_sort(a.code_id, a.B, a.ncodes, ss, st)) != 0)
-        return (cudaError_t)rc;
-    /* phase 1: per warp, one block's working set, two LLR slots and its own
-     * triple table */
-    auto k1 = orbg_batched_kernel<KMAX, WMAX, ONE>;
-    const uint32_t x3w_bytes = triple_table_bytes(a.x3w_max);
-    size_t smem1 = ((size_t)bstride + 2u * 32u * KMAX * sizeof(float) + x3w_bytes) * wpc;
-    if ((rc = orbg_grid_for((const void *)k1, wpc * 32, smem1, a.ctas_per_sm, &grid)) != 0)
-        return (cudaError_t)rc;
-    int64_t units = (a.B + g - 1) / g;
-    int64_t need = (units + wpc - 1) / wpc;
-    if (grid > need) grid = (int)(need > 0 ? need : 1);
-    OrbgDeviceCode c0{};
-    if (ONE)
-        c0 = *a.code0;
-    k1<<<grid, wpc * 32, smem1, st>>>(a.d_codes, a.ncodes, a.code_id, a.llr_off, a.llr, a.B,
-                                      a.cap, a.budget, a.cw, a.cw_off, a.q, a.ab, counters, queue,
-                                      heavy, sorted ? ss.perm : nullptr, sc.hand, sc.hand_cap,
-                                      (unsigned long long)a.scratch_base, bstride, x3w_bytes, g,
-                                      c0);
-    if ((e = cudaGetLastError()) != cudaSuccess)
-        return e;
+    if (!ONE && a.code_id != nullptr && a.var.n >= 1 && a.var.n <= ORBG_MAX_VARIANTS &&
+        a.var.d_bucket != nullptr) {
+        /* per-block codes: one launch per decoder variant, each a kernel of
+         * that variant alone; with several variants the blocks are first
+         * grouped by variant (a counting sort by bucket), and each launch
+         * after the first may start while the one before finishes */
+        const bool sorted = a.var.n > 1;
+        if (sorted && (rc = orbg_launch_code_sort(a.code_id, a.var.d_bucket, a.B, a.ncodes, ss,
+                                                  st)) != 0)
+            return (cudaError_t)rc;
+        for (int v = 0; v < a.var.n; v++) {
+            rc = orbg_launch_exact(a.var.k[v], a.var.w[v], a, ss, vqueue + v,
+                                   sorted ? a.var.blo[v] : -1, a.var.bhi[v], v > 0);
+            if (rc != 0)
+                return (cudaError_t)rc;
+        }
+    } else {
+        /* phase 1: per warp, one block's working set, two LLR slots and its
+         * own triple table */
+        auto k1 = orbg_batched_kernel<KMAX, WMAX, ONE ? P1_ONE : P1_GENERIC>;
+        const uint32_t x3w_bytes = triple_table_bytes(a.x3w_max);
+        size_t smem1 = ((size_t)bstride + 2u * 32u * KMAX * sizeof(float) + x3w_bytes) * wpc;
+        if ((rc = orbg_grid_for((const void *)k1, wpc * 32, smem1, a.ctas_per_sm, &grid)) != 0)
+            return (cudaError_t)rc;
+        int64_t units = (a.B + g - 1) / g;
+        int64_t need = (units + wpc - 1) / wpc;
+        if (grid > need) grid = (int)(need > 0 ? need : 1);
+        OrbgDeviceCode c0{};
+        if (ONE)
+            c0 = *a.code0;
+        k1<<<grid, wpc * 32, smem1, st>>>(a.d_codes, a.ncodes, a.code_id, a.llr_off, a.llr, a.B,
+                                          a.cap, a.budget, a.cw, a.cw_off, a.q, a.ab, counters,
+                                          queue, heavy, nullptr, sc.hand, sc.hand_cap,
+                                          (unsigned long long)a.scratch_base, bstride, x3w_bytes,
+                                          g, nullptr, 0, 0, c0);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return e;
+    }
     if (a.budget >= a.cap || a.stage == 1)
         return cudaSuccess; /* every block finished in phase 1, or phase 2 comes later */
     return launch_heavy_t<KMAX, WMAX, ONE>(a, counters, heavy, sc.hand);

@@ -144,11 +144,24 @@ int orbg_launch_plain(const OrbgDeviceCode &code, const float *llr, int64_t B,
 /* One batched call (orbg_batched.cu); buffers on the device.  code0: host
  * copy of code 0's descriptor, or NULL; with code_id == NULL every block is
  * code 0 and the kernels take it from their parameters. */
+/* The decoder variants of a code set: keys per lane K (n <= 32, 64, 128,
+ * 256: 1, 2, 4, 8) and syndrome words W (1, 2, or 4 for 3-4 words), in the
+ * order a mixed-code call's phase 1 takes them.  The device table d_bucket
+ * gives each code its sort bucket, numbered so that the codes of one
+ * variant hold consecutive buckets [blo, bhi); bucket ncodes collects ids
+ * outside the set and belongs to the last variant. */
+#define ORBG_MAX_VARIANTS 12
+struct OrbgVariants {
+    int n;
+    int k[ORBG_MAX_VARIANTS], w[ORBG_MAX_VARIANTS];
+    int blo[ORBG_MAX_VARIANTS], bhi[ORBG_MAX_VARIANTS];
+    const int32_t *d_bucket; /* [ncodes] */
+};
 struct OrbgBatchedArgs {
     const OrbgDeviceCode *d_codes;
     const OrbgDeviceCode *code0;
     int ncodes, n_max, w32_max;
-    int variants;                /* distinct decoder variants among the codes (> 1: sort) */
+    OrbgVariants var;            /* the set's decoder variants (mixed-code calls) */
     const int32_t *code_id;
     const int64_t *llr_off;
     const float *llr;
@@ -178,8 +191,15 @@ struct OrbgBatchedArgs {
     int64_t scratch_B;
 };
 int orbg_launch_batched(const OrbgBatchedArgs &args);
-/* orbg_batched_inst.cu, one per (keys per lane K, syndrome words W) */
-#define ORBG_DECLARE_BATCHED(K, W) int orbg_launch_batched_k##K##w##W(const OrbgBatchedArgs &a);
+/* orbg_batched_inst.cu, one per (keys per lane K, syndrome words W): both
+ * phases, and phase 1 of that decoder variant alone over sort buckets
+ * [blo, bhi) (blo < 0: every block) on `queue` (pdl: the launch may begin
+ * while the previous one in the stream finishes). */
+struct OrbgScratch;
+#define ORBG_DECLARE_BATCHED(K, W)                                                   \
+    int orbg_launch_batched_k##K##w##W(const OrbgBatchedArgs &a);                    \
+    int orbg_launch_exact_k##K##w##W(const OrbgBatchedArgs &a, const OrbgScratch &s, \
+                                     unsigned long long *queue, int blo, int bhi, int pdl);
 ORBG_DECLARE_BATCHED(1, 1) ORBG_DECLARE_BATCHED(1, 2) ORBG_DECLARE_BATCHED(1, 4)
 ORBG_DECLARE_BATCHED(2, 1) ORBG_DECLARE_BATCHED(2, 2) ORBG_DECLARE_BATCHED(2, 4)
 ORBG_DECLARE_BATCHED(4, 1) ORBG_DECLARE_BATCHED(4, 2) ORBG_DECLARE_BATCHED(4, 4)
@@ -187,15 +207,16 @@ ORBG_DECLARE_BATCHED(8, 1) ORBG_DECLARE_BATCHED(8, 2) ORBG_DECLARE_BATCHED(8, 4)
 #undef ORBG_DECLARE_BATCHED
 /* Device scratch of one batched call over B blocks of a set of ncodes codes,
  * in this order: ORBG_BATCHED_COUNTERS 64-bit counters (0: queue head of
- * slot 0, 1: open-block count, 2: phase-2 cursor, 3: queue head of slot 1);
- * for each of two slots, per-code block counts and fill cursors (ncodes + 1
+ * slot 0, 1: open-block count, 2: phase-2 cursor, 3: queue head of slot 1,
+ * 8 + ORBG_MAX_VARIANTS s + v: the queue head of variant v in slot s); for
+ * each of two slots, per-bucket block counts and fill cursors (ncodes + 1
  * uint32 each, the last for code ids outside the set); the list of open
- * blocks (B uint64); the blocks in phase 1's order, grouped by code (B
- * uint32).  The counters, counts and cursors start at zero.  A phase-1
- * launch uses one slot's queue and counts, so two launches over different
- * chunks of a batch (the host-buffer pipeline's two decode streams) can run
- * at the same time. */
-#define ORBG_BATCHED_COUNTERS 8
+ * blocks (B uint64); the blocks in phase 1's order, grouped by decoder
+ * variant (B uint32).  The counters, counts and cursors start at zero.  A
+ * phase-1 launch uses one slot's queues and counts, so two launches over
+ * different chunks of a batch (the host-buffer pipeline's two decode
+ * streams) can run at the same time. */
+#define ORBG_BATCHED_COUNTERS (8 + 2 * ORBG_MAX_VARIANTS)
 #define ORBG_MAX_CODES 1024      /* codes in one set */
 size_t orbg_batched_scratch_bytes(int64_t B, int ncodes);
 /* Then, 16-byte aligned, up to ORBG_HANDOVER_MAX handover records: for the
@@ -230,13 +251,15 @@ inline OrbgScratch orbg_scratch_layout(void *base, int64_t B, int ncodes)
     s.hand_cap = (uint32_t)(b < ORBG_HANDOVER_MAX ? b : ORBG_HANDOVER_MAX);
     return s;
 }
-/* Order the blocks of a mixed-code call by code id (counting sort into
- * perm, invalid ids last), so that phase 1's warps decode one code's
- * blocks at a time (used when the codes need different decoder variants,
- * whose instructions would otherwise compete for the instruction cache);
- * returns a cudaError_t. */
-int orbg_launch_code_sort(const int32_t *code_id, int64_t B, int ncodes, const OrbgScratch &s,
-                          void *stream);
+/* Order the blocks of a mixed-code call by the bucket of their code
+ * (bucket[code id]; ids outside the set go to bucket ncodes): a counting
+ * sort into perm, so that each decoder variant's blocks hold consecutive
+ * slots and one launch per variant decodes them; returns a cudaError_t. */
+int orbg_launch_code_sort(const int32_t *code_id, const int32_t *bucket, int64_t B, int ncodes,
+                          const OrbgScratch &s, void *stream);
+/* orbg_launch_exact_k*w* for keys per lane K and syndrome words W. */
+int orbg_launch_exact(int K, int W, const OrbgBatchedArgs &a, const OrbgScratch &s,
+                      unsigned long long *queue, int blo, int bhi, int pdl);
 /* Outputs of the blocks phase 2 decoded, gathered after the last launch of a
  * batch whose other results already went to the host.  At `out` (memory the
  * device writes, here host-mapped) the heavy list's length (uint64).  With
@@ -278,7 +301,7 @@ struct OrbgSetView {
     const OrbgDeviceCode *d_codes;
     OrbgDeviceCode code0;        /* host copy of code 0's descriptor */
     int ncodes, n_max, w32_max;
-    int variants;
+    OrbgVariants var;
     uint32_t ntrip_max;
     uint32_t x3w_max;
     uint32_t cap_min;

@@ -310,7 +310,7 @@ bool dispatch_one(orbg_server *s)
         a.code0 = nullptr; /* requests mix codes: per-block code ids */
         a.ncodes = s->view.ncodes;
         a.n_max = s->view.n_max;
-        a.variants = s->view.variants;
+        a.var = s->view.var;
         a.w32_max = s->view.w32_max;
         a.code_id = reinterpret_cast<const int32_t *>(d + bt.L.code_id);
         a.llr_off = reinterpret_cast<const int64_t *>(d + bt.L.llr_off);

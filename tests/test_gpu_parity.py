@@ -416,6 +416,47 @@ def test_mixed_codes_one_launch_equals_alone(orbg):
         assert_same(alone, want, pick)
 
 
+def test_code_ids_outside_the_set_and_one_variant_sets(orbg):
+    """Device code ids outside the set give queries 0 and flag 2, in a set
+    of several decoder variants (blocks grouped by variant, ids outside the
+    set with the last) and in a set of two codes of one variant (one launch,
+    no grouping); every other block equals its code's plain decode."""
+    small = workloads.rlc(64, 51, 71)
+    other = workloads.rlc(60, 45, 72)      # same variant as `small` (n <= 64, one word)
+    big = workloads.rlc(200, 180, 73)
+    rng = np.random.default_rng(74)
+    for codes in ([small, other], [big, small, other]):
+        B = 3000
+        cid = rng.integers(0, len(codes), B).astype(np.int32)
+        bad = rng.choice(B, 25, replace=False)
+        cid[bad[:12]] = len(codes)
+        cid[bad[12:]] = -1
+        n_of = np.array([c.n for c in codes] + [codes[0].n], np.int64)
+        n_blk = n_of[np.where(cid >= 0, np.minimum(cid, len(codes)), len(codes))]
+        off = np.concatenate([[0], np.cumsum(n_blk)[:-1]]).astype(np.int64)
+        llr = (rng.standard_normal(int(n_blk.sum())) * 2.0 + 3.0).astype(np.float32)
+        objs = [orbg.Code(c.H, max_query_cap=10 ** 5) for c in codes]
+        cs = orbg.CodeSet(objs)
+        cw = torch.full((llr.shape[0],), 7, dtype=torch.uint8, device="cuda")
+        q = torch.empty(B, dtype=torch.int32, device="cuda")
+        ab = torch.empty(B, dtype=torch.uint8, device="cuda")
+        off_t = torch.from_numpy(off).cuda()
+        orbg.orbg_decode_batched(cs.handle, torch.from_numpy(cid).cuda(), off_t,
+                                 torch.from_numpy(llr).cuda(), B, 10 ** 5, cw, off_t, q, ab,
+                                 torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        cw, q, ab = cw.cpu().numpy(), q.cpu().numpy().astype(np.int64), ab.cpu().numpy()
+        assert (q[bad] == 0).all() and (ab[bad] == orbg.ORBG_BLOCK_NAN).all()
+        for b in bad:
+            assert (cw[off[b]:off[b] + n_blk[b]] == 7).all()
+        for j, cd in enumerate(codes):
+            idx = np.nonzero(cid == j)[0]
+            blocks = np.stack([llr[off[b]:off[b] + cd.n] for b in idx])
+            alone = gpu_plain(orbg, objs[j], blocks, 10 ** 5)
+            assert_same((np.stack([cw[off[b]:off[b] + cd.n] for b in idx]), q[idx], ab[idx]),
+                        alone)
+
+
 # ------------------------------------------------ benchmark configurations
 
 def test_config1_full_parity(orbg):
