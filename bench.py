@@ -771,8 +771,10 @@ class Job:
         (code ids) run phase 1 as one launch per decoder variant, after a
         two-kernel grouping by variant when there are several; phase 2 is
         one launch unless the phase-1 budget reaches the cap."""
-        if self.form == "plain" or self.search:
+        if self.form == "plain":
             return 1
+        if self.search:
+            return 2  # fit (stage 1), search of the blocks left open (stage 2)
         budget = self.orbg.orbg_codeset_get_tuning(self.cs.handle).warp_budget
         phase2 = 0 if budget >= CAP else 1
         if self.fitted is not None:
@@ -786,7 +788,7 @@ class Job:
         if self.form == "plain":
             return "orbg_plain_kernel"
         if self.search:
-            return "orbg_fitsearch_kernel"
+            return "orbg_fitprep_kernel + orbg_fitsearch_kernel"
         names = "orbg_batched_kernel + orbg_heavy_kernel"
         if self.fitted is not None:
             return "orbg_fit_kernel + line marking + " + names

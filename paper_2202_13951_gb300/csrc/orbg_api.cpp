@@ -1553,8 +1553,8 @@ int orbg_decode_fitted(const orbg_code *code, const float *llr, int64_t B, uint3
         sg.finish(false);
         return rc;
     }
-    unsigned long long *queue = nullptr;
-    cudaError_t e = alloc_async(&queue, sizeof(unsigned long long), st);
+    unsigned char *queue = nullptr; /* the decoder's scratch */
+    cudaError_t e = alloc_async(&queue, orbg_fitsearch_scratch_bytes(B), st);
     if (e != cudaSuccess) {
         sg.finish(false);
         return cuda_fail(e);

@@ -3,7 +3,12 @@
  * fitted to each block (Sec. III-E), searched in that block's own order
  * (Sec. III-D), one warp per block.
  *
- * Per block, fused in one kernel:
+ * Per block, in two launches (each kernel's code stays small enough for the
+ * instruction cache: in one fused kernel the fit's double-precision code and
+ * the search's tree walk, run by different warps of an SM at once, made
+ * instruction fetch the largest stall).  The first launch does steps 1-3
+ * and finishes the blocks that need no search; the second takes the others
+ * from an open list, with their order and model in a handover record:
  *   1. load, hard decision y, starting syndrome s0 = H y (as the other
  *      decoders: load_block);
  *   2. the exact reliability order pi (sort_block) and the ordered curve
@@ -592,12 +597,26 @@ __device__ __forceinline__ uint64_t warp_sum64(uint32_t v)
 
 /* ---------------------------------------------------------- one block */
 
+/* Handover record of a block left to the search launch (ORBG_FIT_HAND_BYTES
+ * bytes): its reliability order pi (n bytes), its model record (24 int32)
+ * and its starting syndrome s0. */
+constexpr int kHandRec = 256;
+constexpr int kHandS0 = 352;
+static_assert(kHandS0 + 16 <= ORBG_FIT_HAND_BYTES, "handover record too small");
+
+/* Stage 1 of a block (the preparing launch): load, hard decision, s0; the
+ * exact reliability order and the fit (steps 1-3).  A block that needs no
+ * search (NaN, a hard decision that is a code word, cap 1) is finished and
+ * written here; any other is appended to the open list with its handover
+ * record. */
 template <int K, int W>
-__device__ void decode_fitted_block(const OrbgDeviceCode &code, const float *__restrict__ llr,
-                                    uint8_t *__restrict__ cw_out, uint32_t *__restrict__ q_out,
-                                    uint8_t *__restrict__ ab_out, int32_t *__restrict__ rec_out,
-                                    uint32_t cap, int lines, int divisible, const FsSmem<W> &sm,
-                                    int lane)
+__device__ void prepare_fitted_block(const OrbgDeviceCode &code, const float *__restrict__ llr,
+                                     uint8_t *__restrict__ cw_out, uint32_t *__restrict__ q_out,
+                                     uint8_t *__restrict__ ab_out, int32_t *__restrict__ rec_out,
+                                     uint32_t cap, int lines, int divisible, const FsSmem<W> &sm,
+                                     int lane, uint32_t b, uint32_t *__restrict__ open,
+                                     unsigned long long *__restrict__ nopen,
+                                     unsigned char *__restrict__ hand)
 {
     typedef typename Syn<W>::T T;
     const int n = code.n;
@@ -605,7 +624,7 @@ __device__ void decode_fitted_block(const OrbgDeviceCode &code, const float *__r
     bool nan;
     const T s0 = load_block<K, W>(code, llr, key, sm.cw, lane, &nan);
     uint32_t q = 0;
-    int ab = 0, wbest = 0;
+    int ab = 0;
     if (nan) {
         ab = ORBG_BLOCK_NAN;
         if (rec_out && lane < ORBG_FIT_WORDS)
@@ -621,16 +640,7 @@ __device__ void decode_fitted_block(const OrbgDeviceCode &code, const float *__r
                 const int idx = (int)key[k];
                 sm.pi[e] = (uint8_t)idx;
                 sm.L[e] = fabsf(__ldg(llr + idx));
-                const T col = load_col<W>(code.hcol, idx);
-                sm.c0[e + 1] = first_word(col);
-                if (W > 1)
-                    sm.h[e + 1] = col;
             }
-        }
-        if (lane == 0) {
-            sm.c0[0] = 0u;
-            if (W > 1)
-                sm.h[0] = szero<T>();
         }
         __syncwarp();
         fit_block<W>(sm, n, lines, divisible, lane);
@@ -642,89 +652,150 @@ __device__ void decode_fitted_block(const OrbgDeviceCode &code, const float *__r
             q = cap;
             ab = ORBG_BLOCK_ABANDONED;
         } else {
-            position_weights<W>(sm, n, lane);
-            /* first bound: the twelfth position's weight (about seventy
-             * patterns for the basic order) */
-            uint32_t r12 = lane < 12 && lane < n ? sm.rho[lane + 1] : 0u;
-            r12 = __reduce_max_sync(FULL_MASK, r12);
-            int32_t Rhi = (int32_t)min(max(r12, sm.msuf[1]), (uint32_t)kRmax);
-            int32_t Rprev = (int32_t)sm.msuf[1] - 1;
-            double Cprev = 1.0;
-            const uint32_t steps = 64u * (min(cap, (uint32_t)ORBG_MAX_QUERY_CAP) + 4096u);
-            bool guard = false;
-            for (;;) {
-                int32_t bR = kNoHit;
-                int bT = 0;
-                const uint32_t c = tree_pass<W, false>(sm, n, s0, Rhi, 0, 0, lane, steps, &bR,
-                                                       &bT, &guard);
-                if (guard) {
-                    ab = kBlockRange;
-                    break;
-                }
-                const double C = 1.0 + (double)warp_sum64(c);
-                const int32_t Rb = __reduce_min_sync(FULL_MASK, bR);
-                if (Rb != kNoHit) {
-                    /* the least member over the lanes: weight, then size, then positions */
-                    int cl = bR == Rb ? lane : -1;
-                    int cT = bR == Rb ? bT : 0x7FFFFFFF;
-#pragma unroll
-                    for (int d = 16; d >= 1; d >>= 1) {
-                        const int ol = __shfl_down_sync(FULL_MASK, cl, d);
-                        const int oT = __shfl_down_sync(FULL_MASK, cT, d);
-                        if (lane + d < 32 && ol >= 0 &&
-                            (cl < 0 || oT < cT || (oT == cT && hb_lex_less(sm.hb, ol, cl, oT)))) {
-                            cl = ol;
-                            cT = oT;
-                        }
-                    }
-                    cl = __shfl_sync(FULL_MASK, cl, 0);
-                    const int Tb = __shfl_sync(FULL_MASK, cT, 0);
-                    if (lane < Tb)
-                        sm.best[lane] = sm.hb[lane * 32 + cl];
-                    __syncwarp();
-                    const uint32_t before = tree_pass<W, true>(sm, n, s0, Rb, Rb, Tb, lane, steps,
-                                                               &bR, &bT, &guard);
-                    if (guard) {
-                        ab = kBlockRange;
-                        break;
-                    }
-                    const uint64_t rank = 2ull + warp_sum64(before);
-                    if (rank <= cap) {
-                        q = (uint32_t)rank;
-                        wbest = Tb;
-                    } else {
-                        q = cap;
-                        ab = ORBG_BLOCK_ABANDONED;
-                    }
-                    break;
-                }
-                if (C >= (double)cap) {
-                    q = cap;
-                    ab = ORBG_BLOCK_ABANDONED;
-                    break;
-                }
-                if (Rhi >= kRmax) {
-                    ab = kBlockRange;
-                    break;
-                }
-                /* next bound: aim at about four times the patterns (at most a
-                 * little past the cap), from the growth over the last band */
-                const double target = fmin(4.0 * C, 1.25 * (double)cap + 64.0);
-                const double span = (double)(Rhi - Rprev);
-                double delta = 2.0 * span;
-                if (C > Cprev) {
-                    const double g = log(C / Cprev) / span;
-                    delta = log(target / C) / g;
-                }
-                delta = fmax(1.0, fmin(delta, 4.0 * span));
-                Rprev = Rhi;
-                Cprev = C;
-                Rhi = (int32_t)fmin((double)Rhi + ceil(delta), (double)kRmax);
+            /* to the search launch */
+            unsigned long long slot = 0;
+            if (lane == 0)
+                slot = atomicAdd(nopen, 1ull);
+            slot = __shfl_sync(FULL_MASK, slot, 0);
+            unsigned char *r = hand + slot * ORBG_FIT_HAND_BYTES;
+            for (int e = lane; e < n; e += 32)
+                r[e] = sm.pi[e];
+            if (lane < ORBG_FIT_WORDS)
+                reinterpret_cast<int32_t *>(r + kHandRec)[lane] = sm.rec[lane];
+            if (lane == 0) {
+                *reinterpret_cast<T *>(r + kHandS0) = s0;
+                open[slot] = b;
             }
+            __syncwarp();
+            return;
         }
+    }
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        const int i = k * 32 + lane;
+        if (i < n)
+            cw_out[i] = sm.cw[i];
+    }
+    if (lane == 0) {
+        *q_out = q;
+        *ab_out = (uint8_t)ab;
+    }
+    __syncwarp();
+}
+/* Stage 2 of a block (the search launch): the block's order, columns, hard
+ * decision and model from its handover record and LLRs, then the weights
+ * and the banded search (steps 4-5), and the outputs. */
+template <int K, int W>
+__device__ void search_fitted_block(const OrbgDeviceCode &code, const float *__restrict__ llr,
+                                    uint8_t *__restrict__ cw_out, uint32_t *__restrict__ q_out,
+                                    uint8_t *__restrict__ ab_out, uint32_t cap,
+                                    const FsSmem<W> &sm, int lane,
+                                    const unsigned char *__restrict__ r)
+{
+    typedef typename Syn<W>::T T;
+    const int n = code.n;
+    for (int e = lane; e < n; e += 32) {
+        const int idx = (int)r[e];
+        sm.pi[e] = (uint8_t)idx;
+        const T col = load_col<W>(code.hcol, idx);
+        sm.c0[e + 1] = first_word(col);
+        if (W > 1)
+            sm.h[e + 1] = col;
+        sm.cw[e] = __ldg(llr + e) > 0.0f ? 1 : 0;
+    }
+    if (lane == 0) {
+        sm.c0[0] = 0u;
+        if (W > 1)
+            sm.h[0] = szero<T>();
+    }
+    if (lane < ORBG_FIT_WORDS)
+        sm.rec[lane] = reinterpret_cast<const int32_t *>(r + kHandRec)[lane];
+    const T s0 = *reinterpret_cast<const T *>(r + kHandS0);
+    __syncwarp();
+    uint32_t q = 0;
+    int ab = 0, wbest = 0;
+    position_weights<W>(sm, n, lane);
+    /* first bound: the twelfth position's weight (about seventy patterns
+     * for the basic order) */
+    uint32_t r12 = lane < 12 && lane < n ? sm.rho[lane + 1] : 0u;
+    r12 = __reduce_max_sync(FULL_MASK, r12);
+    int32_t Rhi = (int32_t)min(max(r12, sm.msuf[1]), (uint32_t)kRmax);
+    int32_t Rprev = (int32_t)sm.msuf[1] - 1;
+    double Cprev = 1.0;
+    const uint32_t steps = 64u * (min(cap, (uint32_t)ORBG_MAX_QUERY_CAP) + 4096u);
+    bool guard = false;
+    for (;;) {
+        int32_t bR = kNoHit;
+        int bT = 0;
+        const uint32_t c =
+            tree_pass<W, false>(sm, n, s0, Rhi, 0, 0, lane, steps, &bR, &bT, &guard);
+        if (guard) {
+            ab = kBlockRange;
+            break;
+        }
+        const double C = 1.0 + (double)warp_sum64(c);
+        const int32_t Rb = __reduce_min_sync(FULL_MASK, bR);
+        if (Rb != kNoHit) {
+            /* the least member over the lanes: weight, then size, then positions */
+            int cl = bR == Rb ? lane : -1;
+            int cT = bR == Rb ? bT : 0x7FFFFFFF;
+#pragma unroll
+            for (int d = 16; d >= 1; d >>= 1) {
+                const int ol = __shfl_down_sync(FULL_MASK, cl, d);
+                const int oT = __shfl_down_sync(FULL_MASK, cT, d);
+                if (lane + d < 32 && ol >= 0 &&
+                    (cl < 0 || oT < cT || (oT == cT && hb_lex_less(sm.hb, ol, cl, oT)))) {
+                    cl = ol;
+                    cT = oT;
+                }
+            }
+            cl = __shfl_sync(FULL_MASK, cl, 0);
+            const int Tb = __shfl_sync(FULL_MASK, cT, 0);
+            if (lane < Tb)
+                sm.best[lane] = sm.hb[lane * 32 + cl];
+            __syncwarp();
+            const uint32_t before =
+                tree_pass<W, true>(sm, n, s0, Rb, Rb, Tb, lane, steps, &bR, &bT, &guard);
+            if (guard) {
+                ab = kBlockRange;
+                break;
+            }
+            const uint64_t rank = 2ull + warp_sum64(before);
+            if (rank <= cap) {
+                q = (uint32_t)rank;
+                wbest = Tb;
+            } else {
+                q = cap;
+                ab = ORBG_BLOCK_ABANDONED;
+            }
+            break;
+        }
+        if (C >= (double)cap) {
+            q = cap;
+            ab = ORBG_BLOCK_ABANDONED;
+            break;
+        }
+        if (Rhi >= kRmax) {
+            ab = kBlockRange;
+            break;
+        }
+        /* next bound: aim at about four times the patterns (at most a little
+         * past the cap), from the growth over the last band */
+        const double target = fmin(4.0 * C, 1.25 * (double)cap + 64.0);
+        const double span = (double)(Rhi - Rprev);
+        double delta = 2.0 * span;
+        if (C > Cprev) {
+            const double g = log(C / Cprev) / span;
+            delta = log(target / C) / g;
+        }
+        delta = fmax(1.0, fmin(delta, 4.0 * span));
+        Rprev = Rhi;
+        Cprev = C;
+        Rhi = (int32_t)fmin((double)Rhi + ceil(delta), (double)kRmax);
     }
     if (q == 0u && ab == 0)
         ab = kBlockRange;
+    __syncwarp();
     if (lane < wbest)
         sm.cw[sm.pi[sm.best[lane] - 1]] ^= 1;
     __syncwarp();
@@ -735,57 +806,107 @@ __device__ void decode_fitted_block(const OrbgDeviceCode &code, const float *__r
             cw_out[i] = sm.cw[i];
     }
     if (lane == 0) {
-        *q_out = ab == ORBG_BLOCK_NAN || ab == kBlockRange ? 0u : q;
+        *q_out = ab == kBlockRange ? 0u : q;
         *ab_out = (uint8_t)ab;
     }
     __syncwarp();
 }
 
-/* Persistent: warps take blocks from an atomic counter, one at a time. */
+/* The scratch of one call (orbg_fitsearch_scratch_bytes): counters, the
+ * open list, the handover records. */
+struct FsScratch {
+    unsigned long long *cnt; /* [0] stage-1 queue, [1] open blocks, [2] stage-2 queue */
+    uint32_t *open;
+    unsigned char *hand;
+    __host__ __device__ FsScratch(unsigned char *base, int64_t B)
+    {
+        cnt = reinterpret_cast<unsigned long long *>(base);
+        open = reinterpret_cast<uint32_t *>(base + 32);
+        hand = base + 32 + ((4 * (size_t)B + 15) & ~(size_t)15);
+    }
+};
+
+/* Stage 1, persistent: warps take blocks from an atomic counter. */
 template <int K, int W>
-__global__ void __launch_bounds__(kWarps * 32, 3) orbg_fitsearch_kernel(
+__global__ void __launch_bounds__(kWarps * 32, 3) orbg_fitprep_kernel(
     const __grid_constant__ OrbgDeviceCode code, const float *__restrict__ llr, int64_t B,
     uint32_t cap, int lines, int divisible, uint8_t *__restrict__ cw,
     uint32_t *__restrict__ q, uint8_t *__restrict__ ab, int32_t *__restrict__ models,
-    unsigned long long *__restrict__ queue)
+    unsigned char *__restrict__ scratch)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     FsSmem<W> sm(smem + warp * fs_warp_bytes<W>());
+    const FsScratch sc(scratch, B);
     const int64_t n = code.n;
     for (;;) {
         unsigned long long b = 0;
         if (lane == 0)
-            b = atomicAdd(queue, 1ull);
+            b = atomicAdd(&sc.cnt[0], 1ull);
         b = __shfl_sync(FULL_MASK, b, 0);
         if (b >= (unsigned long long)B)
             break;
-        decode_fitted_block<K, W>(code, llr + (int64_t)b * n, cw + (int64_t)b * n, q + b, ab + b,
-                                  models ? models + (int64_t)b * ORBG_FIT_WORDS : nullptr, cap,
-                                  lines, divisible, sm, lane);
+        prepare_fitted_block<K, W>(code, llr + (int64_t)b * n, cw + (int64_t)b * n, q + b, ab + b,
+                                   models ? models + (int64_t)b * ORBG_FIT_WORDS : nullptr, cap,
+                                   lines, divisible, sm, lane, (uint32_t)b, sc.open, &sc.cnt[1],
+                                   sc.hand);
+    }
+}
+
+/* Stage 2, persistent over the open list that stage 1 filled. */
+template <int K, int W>
+__global__ void __launch_bounds__(kWarps * 32, 3) orbg_fitsearch_kernel(
+    const __grid_constant__ OrbgDeviceCode code, const float *__restrict__ llr, int64_t B,
+    uint32_t cap, uint8_t *__restrict__ cw, uint32_t *__restrict__ q,
+    uint8_t *__restrict__ ab, unsigned char *__restrict__ scratch)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    FsSmem<W> sm(smem + warp * fs_warp_bytes<W>());
+    const FsScratch sc(scratch, B);
+    const unsigned long long nopen = sc.cnt[1];
+    const int64_t n = code.n;
+    for (;;) {
+        unsigned long long i = 0;
+        if (lane == 0)
+            i = atomicAdd(&sc.cnt[2], 1ull);
+        i = __shfl_sync(FULL_MASK, i, 0);
+        if (i >= nopen)
+            break;
+        const int64_t b = sc.open[i];
+        search_fitted_block<K, W>(code, llr + b * n, cw + b * n, q + b, ab + b, cap, sm, lane,
+                                  sc.hand + i * ORBG_FIT_HAND_BYTES);
     }
 }
 
 template <int K, int W>
 int launch_fitsearch(const OrbgDeviceCode &code, const float *llr, int64_t B, uint32_t cap,
                      int lines, int divisible, uint8_t *cw, uint32_t *q, uint8_t *ab,
-                     int32_t *models, unsigned long long *queue, void *stream)
+                     int32_t *models, unsigned char *scratch, void *stream)
 {
-    auto kern = orbg_fitsearch_kernel<K, W>;
+    auto k1 = orbg_fitprep_kernel<K, W>;
+    auto k2 = orbg_fitsearch_kernel<K, W>;
     const size_t smem = (size_t)fs_warp_bytes<W>() * kWarps;
-    int grid = 0;
-    int rc = orbg_grid_for((const void *)kern, kWarps * 32, smem, 0, &grid);
+    int g1 = 0, g2 = 0;
+    int rc = orbg_grid_for((const void *)k1, kWarps * 32, smem, 0, &g1);
+    if (rc == 0)
+        rc = orbg_grid_for((const void *)k2, kWarps * 32, smem, 0, &g2);
     if (rc != 0)
         return rc;
     const int64_t need = (B + kWarps - 1) / kWarps;
-    if (grid > need)
-        grid = (int)need;
+    if (g1 > need)
+        g1 = (int)need;
+    if (g2 > need)
+        g2 = (int)need;
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 32, st);
     if (e != cudaSuccess)
         return (int)e;
-    kern<<<grid, kWarps * 32, smem, st>>>(code, llr, B, cap, lines, divisible, cw, q, ab, models,
-                                          queue);
+    k1<<<g1, kWarps * 32, smem, st>>>(code, llr, B, cap, lines, divisible, cw, q, ab, models,
+                                      scratch);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return (int)e;
+    k2<<<g2, kWarps * 32, smem, st>>>(code, llr, B, cap, cw, q, ab, scratch);
     return (int)cudaGetLastError();
 }
 

@@ -14,16 +14,16 @@
 
 int ORBG_FS_NAME(ORBG_FS_K)(const OrbgDeviceCode &code, const float *llr, int64_t B,
                             uint32_t cap, int lines, int divisible, uint8_t *cw, uint32_t *q,
-                            uint8_t *ab, int32_t *models, unsigned long long *queue,
+                            uint8_t *ab, int32_t *models, unsigned char *scratch,
                             void *stream)
 {
     using namespace orbg_fitsearch;
     if (code.w32 <= 1)
         return launch_fitsearch<ORBG_FS_K, 1>(code, llr, B, cap, lines, divisible, cw, q, ab,
-                                              models, queue, stream);
+                                              models, scratch, stream);
     if (code.w32 == 2)
         return launch_fitsearch<ORBG_FS_K, 2>(code, llr, B, cap, lines, divisible, cw, q, ab,
-                                              models, queue, stream);
+                                              models, scratch, stream);
     return launch_fitsearch<ORBG_FS_K, 4>(code, llr, B, cap, lines, divisible, cw, q, ab, models,
-                                          queue, stream);
+                                          scratch, stream);
 }

@@ -324,13 +324,22 @@ int orbg_fit_launch(const float *llr, int64_t B, int n, int lines, int divisible
 int orbg_fit_map_lines(const int32_t *models, int64_t B, int32_t top, const int32_t *lut,
                        int32_t *cid, void *stream);
 /* The per-block fitted decoder (orbg_fitted_search_inst.cu, one per keys per
- * lane K): every block fitted (Sec. III-E) and searched in its own order;
- * queue: one device counter.  Return a cudaError_t value. */
+ * lane K): every block fitted (Sec. III-E) and searched in its own order, in
+ * two launches; scratch: orbg_fitsearch_scratch_bytes(B) device bytes (three
+ * counters, the list of blocks the second launch searches, and for each a
+ * handover record of ORBG_FIT_HAND_BYTES: order, model, starting syndrome).
+ * Return a cudaError_t value. */
+#define ORBG_FIT_HAND_BYTES 384
+inline size_t orbg_fitsearch_scratch_bytes(int64_t B)
+{
+    const size_t b = (size_t)(B > 0 ? B : 0);
+    return 32 + ((4 * b + 15) & ~(size_t)15) + (size_t)ORBG_FIT_HAND_BYTES * b;
+}
 #define ORBG_DECLARE_FITSEARCH(K)                                                         \
     int orbg_launch_fitsearch_k##K(const OrbgDeviceCode &code, const float *llr, int64_t B, \
                                    uint32_t cap, int lines, int divisible, uint8_t *cw,     \
                                    uint32_t *q, uint8_t *ab, int32_t *models,               \
-                                   unsigned long long *queue, void *stream);
+                                   unsigned char *scratch, void *stream);
 ORBG_DECLARE_FITSEARCH(1) ORBG_DECLARE_FITSEARCH(2) ORBG_DECLARE_FITSEARCH(4)
 ORBG_DECLARE_FITSEARCH(8)
 #undef ORBG_DECLARE_FITSEARCH
