@@ -1040,21 +1040,64 @@ def bench_ours(args, rank, world, local):
 # captured size by the blocks decoded when the capture was smaller.
 PROFILES = {
     "mixed/batched/basic": {
-        "digest": "cfcf0a6485b8b5f82b641248171fa70bc56ffc107e307d2065b293114e5eb7d6",
-        # phase 1 + phase 2 DRAM bytes on 250,000 blocks (228.4 MB), x 4
-        "traffic_bytes_per_step": 913.6e6,
-        # ALU pipe issue utilisation, phase 1 35.7 % and phase 2 61.1 %, weighted
-        # by their shares of the full-size step (3.44 and 3.60 ms)
-        "issued_frac": 0.487,
+        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
+        # the step's kernels' DRAM bytes on 250,000 blocks (222.5 MB), x 4
+        "traffic_bytes_per_step": 890.0e6,
+        # ALU pipe issue share per kernel, weighted by the full-size step's
+        # time shares (phase 2 61.0 % x 0.548, phase 1 n = 256 42.7 % x 0.362,
+        # n = 128 36.3 % x 0.056, n = 64 32.6 % x 0.032)
+        "issued_frac": 0.52,
         "source": "profiles/orbg_batched_mixed_250k_full.md, "
                   "profiles/orbg_batched_mixed_1m_launches.md",
     },
     "bch/batched/fitted3": {
-        "digest": "cfcf0a6485b8b5f82b641248171fa70bc56ffc107e307d2065b293114e5eb7d6",
-        # 164.8 MB on 280,000 blocks, x 400,000 / 280,000
-        "traffic_bytes_per_step": 235.4e6,
-        "issued_frac": 0.255,
+        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
+        # 346.6 MB on 280,000 blocks, x 400,000 / 280,000
+        "traffic_bytes_per_step": 495.1e6,
+        "issued_frac": 0.326,
         "source": "profiles/orbg_fitsearch_bch127_3line_280k_full.md",
+    },
+    "bch/batched/basic": {
+        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
+        "traffic_bytes_per_step": 237.7e6,  # 166.4 MB on the captured case, x 1.4286
+        "issued_frac": 0.541,
+        "source": "profiles/bench_workloads_traffic_alu.md",
+    },
+    "bch/plain/basic": {
+        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
+        "traffic_bytes_per_step": 235.3e6,  # 164.7 MB on the captured case, x 1.4286
+        "issued_frac": 0.334,
+        "source": "profiles/bench_workloads_traffic_alu.md",
+    },
+    "bch/batched/line": {
+        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
+        "traffic_bytes_per_step": 241.4e6,  # 169.0 MB on the captured case, x 1.4286
+        "issued_frac": 0.554,
+        "source": "profiles/bench_workloads_traffic_alu.md",
+    },
+    "bch/batched/model": {
+        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
+        "traffic_bytes_per_step": 239.9e6,  # 167.9 MB on the captured case, x 1.4286
+        "issued_frac": 0.553,
+        "source": "profiles/bench_workloads_traffic_alu.md",
+    },
+    "bch/batched/fitted1": {
+        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
+        "traffic_bytes_per_step": 571.2e6,  # 399.8 MB on the captured case, x 1.4286
+        "issued_frac": 0.414,
+        "source": "profiles/bench_workloads_traffic_alu.md",
+    },
+    "paper256/batched/basic": {
+        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
+        "traffic_bytes_per_step": 591.7e6,  # 207.1 MB on the captured case, x 2.8571
+        "issued_frac": 0.602,
+        "source": "profiles/bench_workloads_traffic_alu.md",
+    },
+    "capolar256/batched/fitted3": {
+        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
+        "traffic_bytes_per_step": 1037.4e6,  # 363.1 MB on the captured case, x 2.8571
+        "issued_frac": 0.096,
+        "source": "profiles/bench_workloads_traffic_alu.md",
     },
 }
 
