@@ -774,7 +774,7 @@ class Job:
         if self.form == "plain":
             return 1
         if self.search:
-            return 2  # fit (stage 1), search of the blocks left open (stage 2)
+            return 3  # fit, one-warp search of the open blocks, CTA search of the long ones
         budget = self.orbg.orbg_codeset_get_tuning(self.cs.handle).warp_budget
         phase2 = 0 if budget >= CAP else 1
         if self.fitted is not None:
@@ -788,7 +788,7 @@ class Job:
         if self.form == "plain":
             return "orbg_plain_kernel"
         if self.search:
-            return "orbg_fitprep_kernel + orbg_fitsearch_kernel"
+            return "orbg_fitprep_kernel + orbg_fitsearch_kernel + orbg_fitsearch_cta_kernel"
         names = "orbg_batched_kernel + orbg_heavy_kernel"
         if self.fitted is not None:
             return "orbg_fit_kernel + line marking + " + names
@@ -1035,12 +1035,14 @@ def bench_ours(args, rank, world, local):
 
 # DRAM traffic and ALU issue utilisation of a step's kernels, from one ncu
 # capture each (`profiles/` holds the summaries and commands); keyed by
-# workload/form/order and valid only for the library sources they were taken
-# on (the build's source digest).  Traffic is per step, scaled from the
-# captured size by the blocks decoded when the capture was smaller.
+# workload/form/order and valid only while the device code of the kernels
+# they cover is the code they were taken on (its digest: PROFILE_SOURCES).
+# Traffic is per step, scaled from the captured size by the blocks decoded
+# when the capture was smaller.
 PROFILES = {
     "mixed/batched/basic": {
-        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
+        "kernels": "batched",
+        "digest": "3dab41982de60f1d484523e7550267e529327c0e6ee87a6f4121cdd183f03d12",
         # the step's kernels' DRAM bytes on 250,000 blocks (222.5 MB), x 4
         "traffic_bytes_per_step": 890.0e6,
         # ALU pipe issue share per kernel, weighted by the full-size step's
@@ -1051,6 +1053,7 @@ PROFILES = {
                   "profiles/orbg_batched_mixed_1m_launches.md",
     },
     "bch/batched/fitted3": {
+        "kernels": "fitsearch",
         "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
         # 346.6 MB on 280,000 blocks, x 400,000 / 280,000
         "traffic_bytes_per_step": 495.1e6,
@@ -1058,42 +1061,49 @@ PROFILES = {
         "source": "profiles/orbg_fitsearch_bch127_3line_280k_full.md",
     },
     "bch/batched/basic": {
-        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
+        "kernels": "batched",
+        "digest": "3dab41982de60f1d484523e7550267e529327c0e6ee87a6f4121cdd183f03d12",
         "traffic_bytes_per_step": 237.7e6,  # 166.4 MB on the captured case, x 1.4286
         "issued_frac": 0.541,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
     "bch/plain/basic": {
-        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
+        "kernels": "plain",
+        "digest": "4bb2477bbb5c0c7c08601ad4e162f98436e3c905be021d7ff3bf54897b069467",
         "traffic_bytes_per_step": 235.3e6,  # 164.7 MB on the captured case, x 1.4286
         "issued_frac": 0.334,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
     "bch/batched/line": {
-        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
+        "kernels": "batched",
+        "digest": "3dab41982de60f1d484523e7550267e529327c0e6ee87a6f4121cdd183f03d12",
         "traffic_bytes_per_step": 241.4e6,  # 169.0 MB on the captured case, x 1.4286
         "issued_frac": 0.554,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
     "bch/batched/model": {
-        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
+        "kernels": "batched",
+        "digest": "3dab41982de60f1d484523e7550267e529327c0e6ee87a6f4121cdd183f03d12",
         "traffic_bytes_per_step": 239.9e6,  # 167.9 MB on the captured case, x 1.4286
         "issued_frac": 0.553,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
     "bch/batched/fitted1": {
-        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
+        "kernels": "fitline",
+        "digest": "395ffcf7447f124ba3838b9edac798dfc2f5cf4407ffa05e7744e675ee7b8aa9",
         "traffic_bytes_per_step": 571.2e6,  # 399.8 MB on the captured case, x 1.4286
         "issued_frac": 0.414,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
     "paper256/batched/basic": {
-        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
+        "kernels": "batched",
+        "digest": "3dab41982de60f1d484523e7550267e529327c0e6ee87a6f4121cdd183f03d12",
         "traffic_bytes_per_step": 591.7e6,  # 207.1 MB on the captured case, x 2.8571
         "issued_frac": 0.602,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
     "capolar256/batched/fitted3": {
+        "kernels": "fitsearch",
         "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
         "traffic_bytes_per_step": 1037.4e6,  # 363.1 MB on the captured case, x 2.8571
         "issued_frac": 0.096,
@@ -1108,13 +1118,26 @@ def job_profile_key(args):
     return "%s/%s/%s" % (WORKLOAD_NAME, args.form, order)
 
 
+# the device-code files each kernel family is built from (a stored profile
+# is valid while their digest is unchanged)
+PROFILE_SOURCES = {
+    "batched": ["orbg_batched.cuh", "orbg_heavy.cuh", "orbg_decode_block.cuh", "orbg_batched.cu",
+                "orbg_batched_inst.cu", "orbg_internal.h"],
+    "plain": ["orbg_plain.cu", "orbg_decode_block.cuh", "orbg_internal.h"],
+    "fitline": ["orbg_batched.cuh", "orbg_heavy.cuh", "orbg_decode_block.cuh", "orbg_batched.cu",
+                "orbg_batched_inst.cu", "orbg_internal.h", "orbg_fit.cu", "orbg_fit.cuh"],
+    "fitsearch": ["orbg_fitted_search.cuh", "orbg_fitted_search_inst.cu", "orbg_fit.cuh",
+                  "orbg_decode_block.cuh", "orbg_internal.h"],
+}
+
+
 def stored_profile(build, key):
     """The stored ncu figures for key, if they were taken on these sources."""
     rec = PROFILES.get(key)
     if not rec:
         return None
     try:
-        if rec.get("digest") != build.kernel_digest():
+        if rec.get("digest") != build.kernel_digest(PROFILE_SOURCES[rec["kernels"]]):
             return None
     except Exception:
         return None

@@ -56,12 +56,15 @@ def _digest(extra=()):
     return h.hexdigest()
 
 
-def kernel_digest():
-    """SHA-256 of the device code alone (the CUDA sources and the headers
-    they include): profiler figures taken on one build stay valid while it
-    is unchanged, whatever happens to the host-only C++ around it."""
+def kernel_digest(names=None):
+    """SHA-256 of device code (the CUDA sources and the headers they
+    include): all of it, or the files `names` of the source directory.
+    Profiler figures taken on one build stay valid while the kernels they
+    cover are unchanged, whatever happens to the host-only C++ around them."""
     h = hashlib.sha256()
     for name in sorted(os.listdir(CSRC)):
+        if names is not None and name not in names:
+            continue
         if name.endswith((".cu", ".cuh")) or name == "orbg_internal.h":
             h.update(name.encode())
             with open(os.path.join(CSRC, name), "rb") as f:

@@ -3,12 +3,15 @@
  * fitted to each block (Sec. III-E), searched in that block's own order
  * (Sec. III-D), one warp per block.
  *
- * Per block, in two launches (each kernel's code stays small enough for the
- * instruction cache: in one fused kernel the fit's double-precision code and
- * the search's tree walk, run by different warps of an SM at once, made
+ * Per block, in three launches (each kernel's code stays small enough for
+ * the instruction cache: in one fused kernel the fit's double-precision code
+ * and the search's tree walk, run by different warps of an SM at once, made
  * instruction fetch the largest stall).  The first launch does steps 1-3
  * and finishes the blocks that need no search; the second takes the others
- * from an open list, with their order and model in a handover record:
+ * from an open list, with their order and model in a handover record, one
+ * warp per block; a block whose search grows long there goes to the third,
+ * where all warps of a CTA search it (so the few longest blocks, which one
+ * warp each would finish long after the rest, end sooner):
  *   1. load, hard decision y, starting syndrome s0 = H y (as the other
  *      decoders: load_block);
  *   2. the exact reliability order pi (sort_block) and the ordered curve
@@ -39,7 +42,11 @@
  * branch of a lane that is about to take its "add" branch; a lane at a leaf
  * also tests up to kLeafRun of the leaf's later siblings in the same step
  * while they are leaves too (the lanes stay in step: a longer inner run
- * would hold the other lanes).
+ * would hold the other lanes).  When the warps of a CTA share a block, warp
+ * w walks the sets whose least position is w + 1 modulo the warps (its
+ * lanes start on w + 1, w + 1 + P, ...; its depth-1 "replace" steps go P
+ * positions on), and each pass's node counts and least member are combined
+ * over the warps.
  *
  * Passes run with growing bounds ("bands"): a pass that finds code-book
  * members lowers its bound to the lightest one found, and the least of
@@ -68,6 +75,11 @@ constexpr int kDepth = 31;                  /* largest pattern the stack holds *
 constexpr uint32_t kRhoInf = 1u << 30;      /* weight of a position never reached */
 constexpr int32_t kRmax = (1 << 26) - 1;    /* heaviest reliability weight searched */
 constexpr int kLeafRun = 3;                /* leaf siblings tested per step besides the node */
+/* nodes a one-warp pass may test before a CTA takes over (a quarter of the
+ * cap if less): measured on BCH(127,113) and CA-Polar[256,234], 2^16 sent so
+ * many BCH blocks to the CTA search (each restarting there) that its step
+ * grew by a third, 2^18 costs BCH nothing and still cuts the CA-Polar tail */
+constexpr uint32_t kSplit = 1u << 18;
 constexpr int32_t kNoHit = 0x7FFFFFFF;
 constexpr int kBlockRange = ORBG_BLOCK_RANGE; /* abandoned[] value: beyond the search range */
 
@@ -378,11 +390,17 @@ __device__ __noinline__ bool node_is_member(const FsSmem<W> &sm, int lane, int t
  *   positions, or as heavy and as many positions and lexicographically
  *   smaller.  Returns the lane's share of that count.
  * *guard is set (warp-uniform) if the walk exceeds `steps` iterations.
+ * P, w: P warps share one block (P = 1, w = 0: the whole tree); warp w tests
+ * the sets {j} with j = w + 1 modulo P and the larger sets whose second
+ * position is w + 1 modulo P: every warp walks the depth-1 nodes, and its
+ * steps to depth 2 go to the next such position ("add") or P positions on
+ * ("replace"), so the big subtrees of the least reliable positions are
+ * shared out evenly.
  */
-template <int W, bool RANK>
+template <int W, bool RANK, int P>
 __device__ uint32_t tree_pass(const FsSmem<W> &sm, int n, typename Syn<W>::T s0, int32_t Rhi,
                               int32_t Rb, int Tb, int lane, uint32_t steps, int32_t *bR,
-                              int *bT, bool *guard)
+                              int *bT, bool *guard, int w)
 {
     const uint32_t s0w = first_word(s0);
     bool active = false; /* an active lane's node is always untested yet */
@@ -414,7 +432,8 @@ __device__ uint32_t tree_pass(const FsSmem<W> &sm, int n, typename Syn<W>::T s0,
             *guard = true;
             break;
         }
-        const bool tested = active && R <= (uint32_t)Rhi;
+        const bool tested =
+            active && R <= (uint32_t)Rhi && (P == 1 || t != 1 || (jt - 1) % P == w);
         if (RANK) {
             if (tested) {
                 if (R < (uint32_t)Rb)
@@ -445,11 +464,18 @@ __device__ uint32_t tree_pass(const FsSmem<W> &sm, int n, typename Syn<W>::T s0,
                 Rhi = min(Rhi, __reduce_min_sync(FULL_MASK, *bR));
             }
         }
-        const int jn = jt + 1;
-        const bool okn = active && jt < n;
+        /* the "add" child's new position: one on (at depth 1, on to the
+         * warp's class) */
+        const int jn = P == 1 || t != 1 ? jt + 1 : jt + 1 + ((w - jt) % P + P) % P;
+        const bool okn = active && jn <= n;
         const uint32_t ms = okn ? sm.msuf[jn] : kRhoInf;
         const bool addOK = okn && R + ms <= (uint32_t)Rhi;
-        bool replOK = okn && R - rcur + ms <= (uint32_t)Rhi && !((don >> t) & 1u);
+        /* the "replace" branch's position: one on, or P on at depth 2 */
+        const int rs = t == 2 ? P : 1;
+        const int jr = jt + rs;
+        const bool okr = active && jr <= n;
+        const uint32_t msr = P == 1 ? ms : okr ? sm.msuf[jr] : kRhoInf;
+        bool replOK = okr && R - rcur + msr <= (uint32_t)Rhi && !((don >> t) & 1u);
         /* lanes without work take the replace branch of lanes about to add */
         const uint32_t idle = ~act;
         const uint32_t donors = __ballot_sync(FULL_MASK, addOK && replOK);
@@ -475,12 +501,13 @@ __device__ uint32_t tree_pass(const FsSmem<W> &sm, int n, typename Syn<W>::T s0,
             const uint32_t src_r = __shfl_sync(FULL_MASK, rcur, src);
             const uint32_t src_c = __shfl_sync(FULL_MASK, ccur, src);
             if (src != lane) {
-                const uint32_t rn = sm.rho[sj + 1], cn = sm.c0[sj + 1];
+                const int sjr = sj + (st == 2 ? P : 1); /* the donor's replace position */
+                const uint32_t rn = sm.rho[sjr], cn = sm.c0[sjr];
                 for (int d = 0; d < st - 1; d++)
                     sm.stk[d * 32 + lane] = sm.stk[d * 32 + src];
                 t = st;
                 t0 = st;
-                jt = sj + 1;
+                jt = sjr;
                 R = sR - src_r + rn;
                 syn = ssyn ^ src_c ^ cn;
                 rcur = rn;
@@ -496,7 +523,7 @@ __device__ uint32_t tree_pass(const FsSmem<W> &sm, int n, typename Syn<W>::T s0,
             __syncwarp();
         }
         if (active && !got) {
-            int jm = jn;              /* the position the move brings in */
+            int jm = addOK ? jn : jr; /* the position the move brings in */
             bool move = addOK || replOK;
             if (addOK && t >= kDepth) {
                 *guard = true; /* deeper than the stack: cannot happen within 2^26 queries */
@@ -505,7 +532,7 @@ __device__ uint32_t tree_pass(const FsSmem<W> &sm, int n, typename Syn<W>::T s0,
             } else if (addOK) {
                 sm.stk[(t - 1) * 32 + lane] = (uint8_t)jt;
                 t++;
-            } else if (replOK) {
+            } else if (replOK && (P == 1 || t != 1)) {
                 /* a leaf: test up to kLeafRun of its later siblings (same
                  * prefix, last position jm = jt + 1, ...) in this step while
                  * they are leaves too; stop at one that leads further or needs
@@ -532,7 +559,7 @@ __device__ uint32_t tree_pass(const FsSmem<W> &sm, int n, typename Syn<W>::T s0,
                     }
                     if (Rs <= (uint32_t)Rhi)
                         cnt += RANK ? (Rs < (uint32_t)Rb ? 1u : 0u) : 1u;
-                    jm++;
+                    jm += rs;
                 }
                 if (!stop)
                     move = jm <= n && Rp + sm.msuf[jm] <= (uint32_t)Rhi;
@@ -559,8 +586,9 @@ __device__ uint32_t tree_pass(const FsSmem<W> &sm, int n, typename Syn<W>::T s0,
                     jt = sm.stk[(t - 1) * 32 + lane];
                     rcur = sm.rho[jt];
                     ccur = RANK ? 0u : sm.c0[jt];
-                    jm = jt + 1;
-                    if (R - rcur + sm.msuf[jm] <= (uint32_t)Rhi && !((don >> t) & 1u)) {
+                    jm = jt + (t == 2 ? P : 1);
+                    if (jm <= n + 1 && R - rcur + sm.msuf[jm] <= (uint32_t)Rhi &&
+                        !((don >> t) & 1u)) {
                         move = true;
                         break;
                     }
@@ -682,15 +710,13 @@ __device__ void prepare_fitted_block(const OrbgDeviceCode &code, const float *__
     }
     __syncwarp();
 }
-/* Stage 2 of a block (the search launch): the block's order, columns, hard
- * decision and model from its handover record and LLRs, then the weights
- * and the banded search (steps 4-5), and the outputs. */
-template <int K, int W>
-__device__ void search_fitted_block(const OrbgDeviceCode &code, const float *__restrict__ llr,
-                                    uint8_t *__restrict__ cw_out, uint32_t *__restrict__ q_out,
-                                    uint8_t *__restrict__ ab_out, uint32_t cap,
-                                    const FsSmem<W> &sm, int lane,
-                                    const unsigned char *__restrict__ r)
+/* A block's state for the search, from its handover record and LLRs: the
+ * order, the permuted columns, the hard decision and the model, then the
+ * position weights.  Returns s0. */
+template <int W>
+__device__ typename Syn<W>::T load_record(const OrbgDeviceCode &code,
+                                          const float *__restrict__ llr, const FsSmem<W> &sm,
+                                          int lane, const unsigned char *__restrict__ r)
 {
     typedef typename Syn<W>::T T;
     const int n = code.n;
@@ -710,11 +736,66 @@ __device__ void search_fitted_block(const OrbgDeviceCode &code, const float *__r
     }
     if (lane < ORBG_FIT_WORDS)
         sm.rec[lane] = reinterpret_cast<const int32_t *>(r + kHandRec)[lane];
-    const T s0 = *reinterpret_cast<const T *>(r + kHandS0);
     __syncwarp();
+    position_weights<W>(sm, n, lane);
+    return *reinterpret_cast<const T *>(r + kHandS0);
+}
+
+/* Exchange area of the warps of a CTA that search one block together. */
+struct FsTeam {
+    unsigned long long c[kWarps];   /* a pass's tested nodes, per warp */
+    int32_t rb[kWarps];             /* its lightest member's weight (kNoHit: none) */
+    int32_t tb[kWarps];             /* that member's size */
+    int32_t guard[kWarps];
+    uint8_t pos[kWarps][32];        /* that member's positions */
+};
+
+/* The warp's least member of a pass (weight Rb over the warp): its size,
+ * and (lanes < size) its positions in *pos_out. */
+template <int W>
+__device__ __forceinline__ int warp_least_member(const FsSmem<W> &sm, int lane, int32_t bR,
+                                                 int bT, int32_t Rb, uint8_t *pos_out)
+{
+    int cl = bR == Rb ? lane : -1;
+    int cT = bR == Rb ? bT : 0x7FFFFFFF;
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        const int ol = __shfl_down_sync(FULL_MASK, cl, d);
+        const int oT = __shfl_down_sync(FULL_MASK, cT, d);
+        if (lane + d < 32 && ol >= 0 &&
+            (cl < 0 || oT < cT || (oT == cT && hb_lex_less(sm.hb, ol, cl, oT)))) {
+            cl = ol;
+            cT = oT;
+        }
+    }
+    cl = __shfl_sync(FULL_MASK, cl, 0);
+    const int Tb = __shfl_sync(FULL_MASK, cT, 0);
+    if (lane < Tb)
+        pos_out[lane] = sm.hb[lane * 32 + cl];
+    __syncwarp();
+    return Tb;
+}
+
+/*
+ * The banded search of one block (steps 5): by one warp (CTA = false), or
+ * by the kWarps warps of a CTA (CTA = true), warp w walking the sets whose
+ * least position is w + 1 modulo kWarps, each pass's counts, members and
+ * guard combined through `team` (every warp takes the same decisions).
+ * split > 0 (one warp): a pass without a member that tests more than
+ * `split` nodes (and has not reached the cap) ends the walk with *handover
+ * set, for the CTA search.  Sets *q, *ab, and *wbest (the decoding's size;
+ * its positions in sm.best).
+ */
+template <int W, bool CTA>
+__device__ void band_search(const FsSmem<W> &sm, int n, typename Syn<W>::T s0, uint32_t cap,
+                            int lane, int warp, FsTeam *team, uint32_t split, uint32_t *q_out,
+                            int *ab_out, int *wbest_out, bool *handover)
+{
+    constexpr int P = CTA ? kWarps : 1;
+    const int w = CTA ? warp : 0;
     uint32_t q = 0;
     int ab = 0, wbest = 0;
-    position_weights<W>(sm, n, lane);
+    *handover = false;
     /* first bound: the twelfth position's weight (about seventy patterns
      * for the basic order) */
     uint32_t r12 = lane < 12 && lane < n ? sm.rho[lane + 1] : 0u;
@@ -723,44 +804,91 @@ __device__ void search_fitted_block(const OrbgDeviceCode &code, const float *__r
     int32_t Rprev = (int32_t)sm.msuf[1] - 1;
     double Cprev = 1.0;
     const uint32_t steps = 64u * (min(cap, (uint32_t)ORBG_MAX_QUERY_CAP) + 4096u);
-    bool guard = false;
     for (;;) {
         int32_t bR = kNoHit;
         int bT = 0;
+        bool guard = false;
         const uint32_t c =
-            tree_pass<W, false>(sm, n, s0, Rhi, 0, 0, lane, steps, &bR, &bT, &guard);
+            tree_pass<W, false, P>(sm, n, s0, Rhi, 0, 0, lane, steps, &bR, &bT, &guard, w);
+        uint64_t tested = warp_sum64(c);
+        int32_t Rb = __reduce_min_sync(FULL_MASK, bR);
+        int Tb = 0;
+        if (!CTA) {
+            if (Rb != kNoHit && !guard)
+                Tb = warp_least_member<W>(sm, lane, bR, bT, Rb, sm.best);
+        } else {
+            if (Rb != kNoHit && !guard)
+                Tb = warp_least_member<W>(sm, lane, bR, bT, Rb, team->pos[warp]);
+            if (lane == 0) {
+                team->c[warp] = tested;
+                team->rb[warp] = Rb;
+                team->tb[warp] = Tb;
+                team->guard[warp] = guard ? 1 : 0;
+            }
+            __syncthreads();
+            /* the team's totals and least member: weight, size, positions */
+            tested = 0;
+            guard = false;
+            Rb = kNoHit;
+            int win = -1;
+            for (int v = 0; v < kWarps; v++) {
+                tested += team->c[v];
+                guard |= team->guard[v] != 0;
+                const int32_t r = team->rb[v];
+                if (r == kNoHit)
+                    continue;
+                bool better = win < 0 || r < Rb;
+                if (!better && r == Rb) {
+                    const int t = team->tb[v], tw = team->tb[win];
+                    better = t < tw;
+                    if (t == tw)
+                        for (int i = 0; i < t; i++)
+                            if (team->pos[v][i] != team->pos[win][i]) {
+                                better = team->pos[v][i] < team->pos[win][i];
+                                break;
+                            }
+                }
+                if (better) {
+                    win = v;
+                    Rb = r;
+                }
+            }
+            if (win >= 0) {
+                Tb = team->tb[win];
+                if (lane < Tb)
+                    sm.best[lane] = team->pos[win][lane];
+            }
+            __syncthreads(); /* every warp has read the team's entries */
+        }
         if (guard) {
             ab = kBlockRange;
             break;
         }
-        const double C = 1.0 + (double)warp_sum64(c);
-        const int32_t Rb = __reduce_min_sync(FULL_MASK, bR);
+        const double C = 1.0 + (double)tested;
         if (Rb != kNoHit) {
-            /* the least member over the lanes: weight, then size, then positions */
-            int cl = bR == Rb ? lane : -1;
-            int cT = bR == Rb ? bT : 0x7FFFFFFF;
-#pragma unroll
-            for (int d = 16; d >= 1; d >>= 1) {
-                const int ol = __shfl_down_sync(FULL_MASK, cl, d);
-                const int oT = __shfl_down_sync(FULL_MASK, cT, d);
-                if (lane + d < 32 && ol >= 0 &&
-                    (cl < 0 || oT < cT || (oT == cT && hb_lex_less(sm.hb, ol, cl, oT)))) {
-                    cl = ol;
-                    cT = oT;
-                }
-            }
-            cl = __shfl_sync(FULL_MASK, cl, 0);
-            const int Tb = __shfl_sync(FULL_MASK, cT, 0);
-            if (lane < Tb)
-                sm.best[lane] = sm.hb[lane * 32 + cl];
             __syncwarp();
-            const uint32_t before =
-                tree_pass<W, true>(sm, n, s0, Rb, Rb, Tb, lane, steps, &bR, &bT, &guard);
+            const uint32_t b = tree_pass<W, true, P>(sm, n, s0, Rb, Rb, Tb, lane, steps, &bR,
+                                                     &bT, &guard, w);
+            uint64_t before = warp_sum64(b);
+            if (CTA) {
+                if (lane == 0) {
+                    team->c[warp] = before;
+                    team->guard[warp] = guard ? 1 : 0;
+                }
+                __syncthreads();
+                before = 0;
+                guard = false;
+                for (int v = 0; v < kWarps; v++) {
+                    before += team->c[v];
+                    guard |= team->guard[v] != 0;
+                }
+                __syncthreads();
+            }
             if (guard) {
                 ab = kBlockRange;
                 break;
             }
-            const uint64_t rank = 2ull + warp_sum64(before);
+            const uint64_t rank = 2ull + before;
             if (rank <= cap) {
                 q = (uint32_t)rank;
                 wbest = Tb;
@@ -773,6 +901,10 @@ __device__ void search_fitted_block(const OrbgDeviceCode &code, const float *__r
         if (C >= (double)cap) {
             q = cap;
             ab = ORBG_BLOCK_ABANDONED;
+            break;
+        }
+        if (!CTA && split > 0 && C > (double)split) {
+            *handover = true;
             break;
         }
         if (Rhi >= kRmax) {
@@ -795,6 +927,19 @@ __device__ void search_fitted_block(const OrbgDeviceCode &code, const float *__r
     }
     if (q == 0u && ab == 0)
         ab = kBlockRange;
+    *q_out = q;
+    *ab_out = ab;
+    *wbest_out = wbest;
+}
+
+/* The outputs of a searched block: the decoding's flips on the hard
+ * decision, the query count and the flag. */
+template <int K, int W>
+__device__ __forceinline__ void write_fitted(const FsSmem<W> &sm, int n, int lane, uint32_t q,
+                                             int ab, int wbest, uint8_t *__restrict__ cw_out,
+                                             uint32_t *__restrict__ q_out,
+                                             uint8_t *__restrict__ ab_out)
+{
     __syncwarp();
     if (lane < wbest)
         sm.cw[sm.pi[sm.best[lane] - 1]] ^= 1;
@@ -813,16 +958,20 @@ __device__ void search_fitted_block(const OrbgDeviceCode &code, const float *__r
 }
 
 /* The scratch of one call (orbg_fitsearch_scratch_bytes): counters, the
- * open list, the handover records. */
+ * open list, the list of blocks for the CTA search, the handover records. */
 struct FsScratch {
-    unsigned long long *cnt; /* [0] stage-1 queue, [1] open blocks, [2] stage-2 queue */
-    uint32_t *open;
+    unsigned long long *cnt; /* [0] stage-1 queue, [1] open blocks, [2] stage-2 queue,
+                              * [3] stage-3 queue, [4] blocks for stage 3 */
+    uint32_t *open;          /* block of each open slot */
+    uint32_t *wide;          /* open slots left to stage 3 */
     unsigned char *hand;
     __host__ __device__ FsScratch(unsigned char *base, int64_t B)
     {
+        const size_t list = (4 * (size_t)B + 15) & ~(size_t)15;
         cnt = reinterpret_cast<unsigned long long *>(base);
-        open = reinterpret_cast<uint32_t *>(base + 32);
-        hand = base + 32 + ((4 * (size_t)B + 15) & ~(size_t)15);
+        open = reinterpret_cast<uint32_t *>(base + 64);
+        wide = reinterpret_cast<uint32_t *>(base + 64 + list);
+        hand = base + 64 + 2 * list;
     }
 };
 
@@ -853,7 +1002,9 @@ __global__ void __launch_bounds__(kWarps * 32, 3) orbg_fitprep_kernel(
     }
 }
 
-/* Stage 2, persistent over the open list that stage 1 filled. */
+/* Stage 2, persistent over the open list that stage 1 filled, one warp per
+ * block; a block whose search grows past min(kSplit, cap / 4) nodes without
+ * a member is left to stage 3. */
 template <int K, int W>
 __global__ void __launch_bounds__(kWarps * 32, 3) orbg_fitsearch_kernel(
     const __grid_constant__ OrbgDeviceCode code, const float *__restrict__ llr, int64_t B,
@@ -865,7 +1016,8 @@ __global__ void __launch_bounds__(kWarps * 32, 3) orbg_fitsearch_kernel(
     FsSmem<W> sm(smem + warp * fs_warp_bytes<W>());
     const FsScratch sc(scratch, B);
     const unsigned long long nopen = sc.cnt[1];
-    const int64_t n = code.n;
+    const int n = code.n;
+    const uint32_t split = min(kSplit, cap / 4u);
     for (;;) {
         unsigned long long i = 0;
         if (lane == 0)
@@ -874,8 +1026,58 @@ __global__ void __launch_bounds__(kWarps * 32, 3) orbg_fitsearch_kernel(
         if (i >= nopen)
             break;
         const int64_t b = sc.open[i];
-        search_fitted_block<K, W>(code, llr + b * n, cw + b * n, q + b, ab + b, cap, sm, lane,
-                                  sc.hand + i * ORBG_FIT_HAND_BYTES);
+        const auto s0 = load_record<W>(code, llr + b * n, sm, lane,
+                                       sc.hand + i * ORBG_FIT_HAND_BYTES);
+        uint32_t qb = 0;
+        int abb = 0, wbest = 0;
+        bool handover = false;
+        band_search<W, false>(sm, n, s0, cap, lane, warp, nullptr, split, &qb, &abb, &wbest,
+                              &handover);
+        if (handover) {
+            if (lane == 0)
+                sc.wide[atomicAdd(&sc.cnt[4], 1ull)] = (uint32_t)i;
+            __syncwarp();
+            continue;
+        }
+        write_fitted<K, W>(sm, n, lane, qb, abb, wbest, cw + b * n, q + b, ab + b);
+    }
+}
+
+/* Stage 3, persistent over the blocks stage 2 left: all warps of a CTA
+ * search one block, each its own class of least positions. */
+template <int K, int W>
+__global__ void __launch_bounds__(kWarps * 32, 3) orbg_fitsearch_cta_kernel(
+    const __grid_constant__ OrbgDeviceCode code, const float *__restrict__ llr, int64_t B,
+    uint32_t cap, uint8_t *__restrict__ cw, uint32_t *__restrict__ q,
+    uint8_t *__restrict__ ab, unsigned char *__restrict__ scratch)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ FsTeam team;
+    __shared__ unsigned long long s_i;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    FsSmem<W> sm(smem + warp * fs_warp_bytes<W>());
+    const FsScratch sc(scratch, B);
+    const unsigned long long nwide = sc.cnt[4];
+    const int n = code.n;
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_i = atomicAdd(&sc.cnt[3], 1ull);
+        __syncthreads();
+        const unsigned long long k = s_i;
+        __syncthreads(); /* everyone has read s_i before it changes */
+        if (k >= nwide)
+            break; /* uniform */
+        const uint32_t i = sc.wide[k];
+        const int64_t b = sc.open[i];
+        const auto s0 = load_record<W>(code, llr + b * n, sm, lane,
+                                       sc.hand + (size_t)i * ORBG_FIT_HAND_BYTES);
+        uint32_t qb = 0;
+        int abb = 0, wbest = 0;
+        bool handover = false;
+        band_search<W, true>(sm, n, s0, cap, lane, warp, &team, 0u, &qb, &abb, &wbest,
+                             &handover);
+        if (warp == 0)
+            write_fitted<K, W>(sm, n, lane, qb, abb, wbest, cw + b * n, q + b, ab + b);
     }
 }
 
@@ -886,11 +1088,14 @@ int launch_fitsearch(const OrbgDeviceCode &code, const float *llr, int64_t B, ui
 {
     auto k1 = orbg_fitprep_kernel<K, W>;
     auto k2 = orbg_fitsearch_kernel<K, W>;
+    auto k3 = orbg_fitsearch_cta_kernel<K, W>;
     const size_t smem = (size_t)fs_warp_bytes<W>() * kWarps;
-    int g1 = 0, g2 = 0;
+    int g1 = 0, g2 = 0, g3 = 0;
     int rc = orbg_grid_for((const void *)k1, kWarps * 32, smem, 0, &g1);
     if (rc == 0)
         rc = orbg_grid_for((const void *)k2, kWarps * 32, smem, 0, &g2);
+    if (rc == 0)
+        rc = orbg_grid_for((const void *)k3, kWarps * 32, smem, 0, &g3);
     if (rc != 0)
         return rc;
     const int64_t need = (B + kWarps - 1) / kWarps;
@@ -898,8 +1103,10 @@ int launch_fitsearch(const OrbgDeviceCode &code, const float *llr, int64_t B, ui
         g1 = (int)need;
     if (g2 > need)
         g2 = (int)need;
+    if (g3 > B)
+        g3 = (int)B;
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemsetAsync(scratch, 0, 32, st);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 64, st);
     if (e != cudaSuccess)
         return (int)e;
     k1<<<g1, kWarps * 32, smem, st>>>(code, llr, B, cap, lines, divisible, cw, q, ab, models,
@@ -907,6 +1114,9 @@ int launch_fitsearch(const OrbgDeviceCode &code, const float *llr, int64_t B, ui
     if ((e = cudaGetLastError()) != cudaSuccess)
         return (int)e;
     k2<<<g2, kWarps * 32, smem, st>>>(code, llr, B, cap, cw, q, ab, scratch);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return (int)e;
+    k3<<<g3, kWarps * 32, smem, st>>>(code, llr, B, cap, cw, q, ab, scratch);
     return (int)cudaGetLastError();
 }
 

@@ -325,15 +325,16 @@ int orbg_fit_map_lines(const int32_t *models, int64_t B, int32_t top, const int3
                        int32_t *cid, void *stream);
 /* The per-block fitted decoder (orbg_fitted_search_inst.cu, one per keys per
  * lane K): every block fitted (Sec. III-E) and searched in its own order, in
- * two launches; scratch: orbg_fitsearch_scratch_bytes(B) device bytes (three
- * counters, the list of blocks the second launch searches, and for each a
- * handover record of ORBG_FIT_HAND_BYTES: order, model, starting syndrome).
+ * three launches; scratch: orbg_fitsearch_scratch_bytes(B) device bytes
+ * (counters, the list of blocks the second launch searches, the list of
+ * those it leaves to the third, and for each open block a handover record
+ * of ORBG_FIT_HAND_BYTES: order, model, starting syndrome).
  * Return a cudaError_t value. */
 #define ORBG_FIT_HAND_BYTES 384
 inline size_t orbg_fitsearch_scratch_bytes(int64_t B)
 {
     const size_t b = (size_t)(B > 0 ? B : 0);
-    return 32 + ((4 * b + 15) & ~(size_t)15) + (size_t)ORBG_FIT_HAND_BYTES * b;
+    return 64 + 2 * ((4 * b + 15) & ~(size_t)15) + (size_t)ORBG_FIT_HAND_BYTES * b;
 }
 #define ORBG_DECLARE_FITSEARCH(K)                                                         \
     int orbg_launch_fitsearch_k##K(const OrbgDeviceCode &code, const float *llr, int64_t B, \
