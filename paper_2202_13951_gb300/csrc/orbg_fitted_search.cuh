@@ -76,9 +76,10 @@ constexpr uint32_t kRhoInf = 1u << 30;      /* weight of a position never reache
 constexpr int32_t kRmax = (1 << 26) - 1;    /* heaviest reliability weight searched */
 constexpr int kLeafRun = 3;                /* leaf siblings tested per step besides the node */
 /* nodes a one-warp pass may test before a CTA takes over (a quarter of the
- * cap if less): measured on BCH(127,113) and CA-Polar[256,234], 2^16 sent so
- * many BCH blocks to the CTA search (each restarting there) that its step
- * grew by a third, 2^18 costs BCH nothing and still cuts the CA-Polar tail */
+ * cap if less): measured on BCH(127,113) and CA-Polar[256,234] (3 lines),
+ * 2^16 sends so many BCH blocks to the CTA search (each restarting there)
+ * that its step grows by a fifth; 2^18 costs BCH nothing and still takes
+ * the long CA-Polar blocks off single warps */
 constexpr uint32_t kSplit = 1u << 18;
 constexpr int32_t kNoHit = 0x7FFFFFFF;
 constexpr int kBlockRange = ORBG_BLOCK_RANGE; /* abandoned[] value: beyond the search range */

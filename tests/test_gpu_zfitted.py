@@ -4,7 +4,9 @@ order (Sec. III-D, Eq. relest_seg): orbg_decode_fitted through the C ABI,
 bit for bit (codeword, query count, abandon flag and model record) against
 the oracle's fit-then-decode, for 1 to 4 lines, both quantisations, codes
 of every keys-per-lane class and syndrome width, edge inputs, caps at the
-hit, host buffers, and the BCH(127,113) workload at full size."""
+hit, host buffers, and the BCH(127,113) workload at full size.  A block
+whose one-warp search passes a quarter of the cap goes to the search where
+all warps of a CTA share it, so these caps exercise both."""
 import numpy as np
 import pytest
 
