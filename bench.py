@@ -1054,10 +1054,10 @@ PROFILES = {
     },
     "bch/batched/fitted3": {
         "kernels": "fitsearch",
-        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
-        # 346.6 MB on 280,000 blocks, x 400,000 / 280,000
-        "traffic_bytes_per_step": 495.1e6,
-        "issued_frac": 0.326,
+        "digest": "5792a477c39eb8afdce9c72fe081f27fa9205879ae70401e9ff7931b8c2554db",
+        # 346.2 MB on 280,000 blocks, x 400,000 / 280,000
+        "traffic_bytes_per_step": 494.6e6,
+        "issued_frac": 0.320,
         "source": "profiles/orbg_fitsearch_bch127_3line_280k_full.md",
     },
     "bch/batched/basic": {
@@ -1104,9 +1104,9 @@ PROFILES = {
     },
     "capolar256/batched/fitted3": {
         "kernels": "fitsearch",
-        "digest": "35173ecdd3910a3c02ac0312e86507c5ceda0e1d5009688c34ecffbb79c39cb9",
-        "traffic_bytes_per_step": 1037.4e6,  # 363.1 MB on the captured case, x 2.8571
-        "issued_frac": 0.096,
+        "digest": "5792a477c39eb8afdce9c72fe081f27fa9205879ae70401e9ff7931b8c2554db",
+        "traffic_bytes_per_step": 1039.7e6,  # 363.9 MB on the captured case, x 2.8571
+        "issued_frac": 0.234,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
 }
