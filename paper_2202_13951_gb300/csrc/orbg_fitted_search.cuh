@@ -42,11 +42,11 @@
  * branch of a lane that is about to take its "add" branch; a lane at a leaf
  * also tests up to kLeafRun of the leaf's later siblings in the same step
  * while they are leaves too (the lanes stay in step: a longer inner run
- * would hold the other lanes).  When the warps of a CTA share a block, warp
- * w walks the sets whose least position is w + 1 modulo the warps (its
- * lanes start on w + 1, w + 1 + P, ...; its depth-1 "replace" steps go P
- * positions on), and each pass's node counts and least member are combined
- * over the warps.
+ * would hold the other lanes).  When the warps of a CTA share a block, the
+ * tree is cut into kClasses classes by the sets' second positions (modulo
+ * kClasses; the singletons by their position), the warps take classes from
+ * a counter, and each pass's node counts and least member are combined over
+ * the warps.
  *
  * Passes run with growing bounds ("bands"): a pass that finds code-book
  * members lowers its bound to the lightest one found, and the least of
@@ -391,12 +391,11 @@ __device__ __noinline__ bool node_is_member(const FsSmem<W> &sm, int lane, int t
  *   positions, or as heavy and as many positions and lexicographically
  *   smaller.  Returns the lane's share of that count.
  * *guard is set (warp-uniform) if the walk exceeds `steps` iterations.
- * P, w: P warps share one block (P = 1, w = 0: the whole tree); warp w tests
- * the sets {j} with j = w + 1 modulo P and the larger sets whose second
- * position is w + 1 modulo P: every warp walks the depth-1 nodes, and its
- * steps to depth 2 go to the next such position ("add") or P positions on
- * ("replace"), so the big subtrees of the least reliable positions are
- * shared out evenly.
+ * P, w: the walk covers class w of P (P = 1, w = 0: the whole tree): the
+ * sets {j} with j = w + 1 modulo P and the larger sets whose second position
+ * is w + 1 modulo P.  It walks all the depth-1 nodes, and its steps to depth
+ * 2 go to the next such position ("add") or P positions on ("replace"), so
+ * the big subtrees of the least reliable positions are shared out evenly.
  */
 template <int W, bool RANK, int P>
 __device__ uint32_t tree_pass(const FsSmem<W> &sm, int n, typename Syn<W>::T s0, int32_t Rhi,
@@ -742,8 +741,15 @@ __device__ typename Syn<W>::T load_record(const OrbgDeviceCode &code,
     return *reinterpret_cast<const T *>(r + kHandS0);
 }
 
+/* Classes of the tree a CTA's warps share out, pass by pass, from a counter:
+ * class k holds the sets {j} with j = k + 1 and the larger sets whose second
+ * position is k + 1 modulo kClasses (many more classes than warps, so the
+ * warps end a pass close together). */
+constexpr int kClasses = 32;
+
 /* Exchange area of the warps of a CTA that search one block together. */
 struct FsTeam {
+    unsigned int next[2];           /* the next class of a search pass, of a rank pass */
     unsigned long long c[kWarps];   /* a pass's tested nodes, per warp */
     int32_t rb[kWarps];             /* its lightest member's weight (kNoHit: none) */
     int32_t tb[kWarps];             /* that member's size */
@@ -779,9 +785,9 @@ __device__ __forceinline__ int warp_least_member(const FsSmem<W> &sm, int lane, 
 
 /*
  * The banded search of one block (steps 5): by one warp (CTA = false), or
- * by the kWarps warps of a CTA (CTA = true), warp w walking the sets whose
- * least position is w + 1 modulo kWarps, each pass's counts, members and
- * guard combined through `team` (every warp takes the same decisions).
+ * by the kWarps warps of a CTA (CTA = true), each taking classes of the
+ * tree (kClasses) from a counter, each pass's counts, members and guard
+ * combined through `team` (every warp takes the same decisions).
  * split > 0 (one warp): a pass without a member that tests more than
  * `split` nodes (and has not reached the cap) ends the walk with *handover
  * set, for the CTA search.  Sets *q, *ab, and *wbest (the decoding's size;
@@ -792,8 +798,7 @@ __device__ void band_search(const FsSmem<W> &sm, int n, typename Syn<W>::T s0, u
                             int lane, int warp, FsTeam *team, uint32_t split, uint32_t *q_out,
                             int *ab_out, int *wbest_out, bool *handover)
 {
-    constexpr int P = CTA ? kWarps : 1;
-    const int w = CTA ? warp : 0;
+    constexpr int P = CTA ? kClasses : 1;
     uint32_t q = 0;
     int ab = 0, wbest = 0;
     *handover = false;
@@ -809,8 +814,22 @@ __device__ void band_search(const FsSmem<W> &sm, int n, typename Syn<W>::T s0, u
         int32_t bR = kNoHit;
         int bT = 0;
         bool guard = false;
-        const uint32_t c =
-            tree_pass<W, false, P>(sm, n, s0, Rhi, 0, 0, lane, steps, &bR, &bT, &guard, w);
+        uint32_t c = 0;
+        if (!CTA) {
+            c = tree_pass<W, false, 1>(sm, n, s0, Rhi, 0, 0, lane, steps, &bR, &bT, &guard, 0);
+        } else {
+            for (;;) {
+                unsigned int k = 0;
+                if (lane == 0)
+                    k = atomicAdd(&team->next[0], 1u);
+                k = __shfl_sync(FULL_MASK, k, 0);
+                if (k >= (unsigned)kClasses)
+                    break;
+                const int32_t Rk = min(Rhi, __reduce_min_sync(FULL_MASK, bR));
+                c += tree_pass<W, false, P>(sm, n, s0, Rk, 0, 0, lane, steps, &bR, &bT, &guard,
+                                            (int)k);
+            }
+        }
         uint64_t tested = warp_sum64(c);
         int32_t Rb = __reduce_min_sync(FULL_MASK, bR);
         int Tb = 0;
@@ -827,6 +846,8 @@ __device__ void band_search(const FsSmem<W> &sm, int n, typename Syn<W>::T s0, u
                 team->guard[warp] = guard ? 1 : 0;
             }
             __syncthreads();
+            if (threadIdx.x == 0)
+                team->next[0] = 0u; /* no warp takes a class again before the sync below */
             /* the team's totals and least member: weight, size, positions */
             tested = 0;
             guard = false;
@@ -868,8 +889,22 @@ __device__ void band_search(const FsSmem<W> &sm, int n, typename Syn<W>::T s0, u
         const double C = 1.0 + (double)tested;
         if (Rb != kNoHit) {
             __syncwarp();
-            const uint32_t b = tree_pass<W, true, P>(sm, n, s0, Rb, Rb, Tb, lane, steps, &bR,
-                                                     &bT, &guard, w);
+            uint32_t b = 0;
+            if (!CTA) {
+                b = tree_pass<W, true, 1>(sm, n, s0, Rb, Rb, Tb, lane, steps, &bR, &bT, &guard,
+                                          0);
+            } else {
+                for (;;) {
+                    unsigned int k = 0;
+                    if (lane == 0)
+                        k = atomicAdd(&team->next[1], 1u);
+                    k = __shfl_sync(FULL_MASK, k, 0);
+                    if (k >= (unsigned)kClasses)
+                        break;
+                    b += tree_pass<W, true, P>(sm, n, s0, Rb, Rb, Tb, lane, steps, &bR, &bT,
+                                               &guard, (int)k);
+                }
+            }
             uint64_t before = warp_sum64(b);
             if (CTA) {
                 if (lane == 0) {
@@ -877,6 +912,8 @@ __device__ void band_search(const FsSmem<W> &sm, int n, typename Syn<W>::T s0, u
                     team->guard[warp] = guard ? 1 : 0;
                 }
                 __syncthreads();
+                if (threadIdx.x == 0)
+                    team->next[1] = 0u;
                 before = 0;
                 guard = false;
                 for (int v = 0; v < kWarps; v++) {
@@ -1061,8 +1098,11 @@ __global__ void __launch_bounds__(kWarps * 32, 3) orbg_fitsearch_cta_kernel(
     const unsigned long long nwide = sc.cnt[4];
     const int n = code.n;
     for (;;) {
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             s_i = atomicAdd(&sc.cnt[3], 1ull);
+            team.next[0] = 0u;
+            team.next[1] = 0u;
+        }
         __syncthreads();
         const unsigned long long k = s_i;
         __syncthreads(); /* everyone has read s_i before it changes */
