@@ -18,6 +18,7 @@
 
 struct orbg_code {
     int n, k, r, w32;
+    bool has_stride = false;     /* its tables hold strided pair runs (m-segment orders) */
     uint32_t max_cap;
     int device;
     std::vector<uint8_t> H;      /* r x n as used */
@@ -38,6 +39,7 @@ struct orbg_code {
 struct orbg_codeset {
     int ncodes, n_max, w32_max;
     OrbgVariants var;            /* decoder variants and the codes' sort buckets */
+    int has_stride = 0;          /* a code's tables hold strided pair runs */
     int32_t *d_bucket = nullptr; /* [ncodes] sort bucket of each code (var.d_bucket) */
     uint32_t ntrip_max;
     uint32_t x3w_max;
@@ -264,6 +266,7 @@ int orbg_codeset_view(const orbg_codeset *set, OrbgSetView *out)
     out->n_max = set->n_max;
     out->w32_max = set->w32_max;
     out->var = set->var;
+    out->has_stride = set->has_stride;
     out->ntrip_max = set->ntrip_max;
     out->x3w_max = set->x3w_max;
     out->cap_min = set->cap_min;
@@ -531,6 +534,10 @@ int load_code(const uint8_t *mat, int kind, int n, int k, uint32_t max_query_cap
         delete c;
         return ORBG_ELIMIT;
     }
+    for (const OrbgRun &run : tb.runs)
+        c->has_stride |= run.kind == ORBG_RUN_STRIDE;
+    for (const OrbgRun &run : tb.runs_cta)
+        c->has_stride |= run.kind == ORBG_RUN_STRIDE;
     cudaError_t e;
     if ((e = cudaGetDevice(&c->device)) != cudaSuccess) {
         delete c;
@@ -718,6 +725,7 @@ int orbg_codeset_create(const orbg_code *const *codes, int ncodes, orbg_codeset 
         s->cap_min = std::min(s->cap_min, codes[i]->max_cap);
         s->ntrip_max = std::max(s->ntrip_max, codes[i]->dev.ntrip);
         s->x3w_max = std::max(s->x3w_max, codes[i]->dev.x3w);
+        s->has_stride |= codes[i]->has_stride ? 1 : 0;
     }
     /* the decoder variants the kernels specialise on: keys per lane from n
      * (n <= 32, 64, 128, 256: 1, 2, 4, 8) and the syndrome words (1, 2, or
@@ -928,6 +936,7 @@ int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
     a.n_max = set->n_max;
     a.w32_max = set->w32_max;
     a.var = set->var;
+    a.has_stride = set->has_stride;
     a.cap = query_cap;
     a.budget = t.warp_budget < query_cap ? t.warp_budget : query_cap;
     a.scratch = scratch;
@@ -1182,6 +1191,7 @@ int orbg_decode_batched(const orbg_codeset *set, const int32_t *code_id,
     a.n_max = set->n_max;
     a.w32_max = set->w32_max;
     a.var = set->var;
+    a.has_stride = set->has_stride;
     a.code_id = d_cid;
     a.llr_off = d_lo;
     a.llr = d_llr;
@@ -1487,6 +1497,7 @@ int orbg_fitted_decode(orbg_fitted *f, const float *llr, int64_t B, uint32_t que
         a.n_max = set->n_max;
         a.w32_max = set->w32_max;
         a.var = set->var;
+        a.has_stride = set->has_stride;
         a.code_id = d_cid;
         a.llr_off = nullptr;
         a.llr = llr;

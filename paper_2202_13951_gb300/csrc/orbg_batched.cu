@@ -192,12 +192,12 @@ int orbg_launch_code_sort(const int32_t *code_id, const int32_t *bucket, int64_t
 }
 
 int orbg_launch_exact(int K, int W, const OrbgBatchedArgs &a, const OrbgScratch &s,
-                      unsigned long long *queue, int blo, int bhi, int pdl)
+                      unsigned long long *queue, int blo, int bhi, int pdl, int stride)
 {
 #define ORBG_EX(KK)                                                                         \
-    return W <= 1   ? orbg_launch_exact_k##KK##w1(a, s, queue, blo, bhi, pdl)               \
-           : W == 2 ? orbg_launch_exact_k##KK##w2(a, s, queue, blo, bhi, pdl)               \
-                    : orbg_launch_exact_k##KK##w4(a, s, queue, blo, bhi, pdl);
+    return W <= 1   ? orbg_launch_exact_k##KK##w1(a, s, queue, blo, bhi, pdl, stride)       \
+           : W == 2 ? orbg_launch_exact_k##KK##w2(a, s, queue, blo, bhi, pdl, stride)       \
+                    : orbg_launch_exact_k##KK##w4(a, s, queue, blo, bhi, pdl, stride);
     if (K <= 1)
         ORBG_EX(1)
     if (K == 2)

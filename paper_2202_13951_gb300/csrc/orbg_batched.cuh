@@ -53,7 +53,7 @@ constexpr int kCounters = ORBG_BATCHED_COUNTERS;
  * decoder variant per launch, the blocks taken from their sort buckets). */
 enum { P1_ONE = 0, P1_GENERIC = 1, P1_EXACT = 2 };
 
-template <int KMAX, int WMAX, int MODE>
+template <int KMAX, int WMAX, int MODE, bool STRIDE = true>
 __global__ void __launch_bounds__(256, MODE == P1_GENERIC ? ORBG_PHASE1_MIN_CTAS_MIXED
                                                           : ORBG_PHASE1_MIN_CTAS)
     orbg_batched_kernel(
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(256, MODE == P1_GENERIC ? ORBG_PHASE1_MIN_CTAS
         } else if (MODE == P1_EXACT) {
             /* one decoder variant: K and W exact; the block's descriptor is
              * read where it is used (a register copy of it spilled) */
-            decode_block_warp<KMAX, WMAX, true, true, (KMAX <= 4), (KMAX >= 8)>(
+            decode_block_warp<KMAX, WMAX, true, true, (KMAX <= 4), (KMAX >= 8), STRIDE>(
                 codes[cid], l, cw + co, q + b, ab + b, cap, budget, bsm, lane, heavy, &counters[1],
                 b_base + (unsigned long long)b, X3w, hand, hand_cap);
         } else {
@@ -199,8 +199,9 @@ __global__ void __launch_bounds__(256, MODE == P1_GENERIC ? ORBG_PHASE1_MIN_CTAS
 /* Phase 1 of one decoder variant (K, W): the blocks of sort buckets
  * [blo, bhi) of ss.perm (blo < 0: every block, in order), on its own queue.
  * pdl: the launch may begin while the previous launch in the stream (the
- * previous variant's) finishes its last blocks. */
-template <int K, int W>
+ * previous variant's) finishes its last blocks.  STRIDE: the set holds
+ * codes with strided pair runs. */
+template <int K, int W, bool STRIDE>
 int launch_exact_t(const OrbgBatchedArgs &a, const OrbgScratch &ss, unsigned long long *queue,
                    int blo, int bhi, int pdl)
 {
@@ -208,7 +209,7 @@ int launch_exact_t(const OrbgBatchedArgs &a, const OrbgScratch &ss, unsigned lon
     const int g = a.grab < 1 ? 1 : a.grab;
     const int nk = a.n_max < 32 * K ? a.n_max : 32 * K;
     const uint32_t bstride = block_smem_bytes(nk, W);
-    auto k1 = orbg_batched_kernel<K, W, P1_EXACT>;
+    auto k1 = orbg_batched_kernel<K, W, P1_EXACT, STRIDE>;
     const uint32_t x3w_bytes = triple_table_bytes(a.x3w_max);
     const size_t smem1 = ((size_t)bstride + 2u * 32u * K * sizeof(float) + x3w_bytes) * wpc;
     int grid = 0;
@@ -293,7 +294,8 @@ cudaError_t launch_t(const OrbgBatchedArgs &a)
             return (cudaError_t)rc;
         for (int v = 0; v < a.var.n; v++) {
             rc = orbg_launch_exact(a.var.k[v], a.var.w[v], a, ss, vqueue + v,
-                                   sorted ? a.var.blo[v] : -1, a.var.bhi[v], v > 0);
+                                   sorted ? a.var.blo[v] : -1, a.var.bhi[v], v > 0,
+                                   a.has_stride);
             if (rc != 0)
                 return (cudaError_t)rc;
         }

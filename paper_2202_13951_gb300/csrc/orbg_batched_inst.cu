@@ -27,8 +27,10 @@ int ORBG_INST_NAME(ORBG_INST_K, ORBG_INST_W)(const OrbgBatchedArgs &a)
 
 int ORBG_INST_NAME_EX(ORBG_INST_K, ORBG_INST_W)(const OrbgBatchedArgs &a, const OrbgScratch &s,
                                                 unsigned long long *queue, int blo, int bhi,
-                                                int pdl)
+                                                int pdl, int stride)
 {
-    return orbg_batched_impl::launch_exact_t<ORBG_INST_K, ORBG_INST_W>(a, s, queue, blo, bhi,
-                                                                        pdl);
+    return stride ? orbg_batched_impl::launch_exact_t<ORBG_INST_K, ORBG_INST_W, true>(
+                        a, s, queue, blo, bhi, pdl)
+                  : orbg_batched_impl::launch_exact_t<ORBG_INST_K, ORBG_INST_W, false>(
+                        a, s, queue, blo, bhi, pdl);
 }

@@ -558,8 +558,10 @@ __device__ __forceinline__ T prefix_syndrome(const uint4 &v0, const uint4 &v1,
 }
 
 /* Positions (0-based) a query flips besides the prefix: kind 1 hit value
- * is a (1-based), the pair (a, S - a); kind 3 hit value is the triple
- * index.  Writes up to three positions, returns how many. */
+ * is a (1-based), the pair (a, S - a); kind 2 hit value is the pattern's
+ * offset j in the run, the pair (a_0 + j da, b_0 - j db); kind 3 hit value
+ * is the triple index.  Writes up to three positions, returns how many. */
+template <bool STRIDE = true>
 __device__ __forceinline__ int query_tail(const uint4 &v0, uint32_t hit, const uint32_t *trip,
                                           int *pos)
 {
@@ -568,6 +570,12 @@ __device__ __forceinline__ int query_tail(const uint4 &v0, uint32_t hit, const u
         const int S = (int)(v0.z & 0xFFu), a = (int)hit;
         pos[0] = a - 1;
         pos[1] = S - a - 1;
+        return 2;
+    }
+    if (STRIDE && kind == ORBG_RUN_STRIDE) {
+        const int j = (int)hit;
+        pos[0] = (int)(v0.z & 0xFFu) + j * (int)((v0.z >> 16) & 0xFFu) - 1;
+        pos[1] = (int)((v0.z >> 8) & 0xFFu) - j * (int)(v0.z >> 24) - 1;
         return 2;
     }
     if (kind == ORBG_RUN_TRIPLES) {
@@ -597,12 +605,15 @@ __device__ __noinline__ bool verify_query(const uint4 &v0, const uint4 &v1,
     return sz(P);
 }
 
-/* Pair run (kind 1): queries (a, S - a) for a = a_lo, a_lo + 1, ...; two
- * queries per step, first words from h0; a first-word match is checked on
- * all W words outside the scan loop (a false match, probability 2^-32 per
- * query, resumes it).  Returns the offset of the first hit or -1, and the
- * hit's a in *hit. */
-template <int W>
+/* Pair run: queries (a, b) = (a_0 + j da, b_0 - j db), j = 0, 1, ... (kind
+ * 1: a_0 = a_lo, b_0 = S - a_lo, da = db = 1; kind 2, only where STRIDE: as
+ * stored); two queries per step, first words from h0; a first-word match is
+ * checked on all W words outside the scan loop (a false match, probability
+ * 2^-32 per query, resumes it).  Returns the offset of the first hit or -1,
+ * and the hit value for query_tail in *hit (kind 1: a; kind 2: the offset).
+ * STRIDE = false (kernels of code sets without strided runs) compiles the
+ * kind-1 walk alone: the extra registers cost the mixed-code kernels. */
+template <int W, bool STRIDE>
 __device__ __forceinline__ int walk_pairs(const uint4 &v0, const uint4 &v1,
                                           const typename Syn<W>::T *__restrict__ h,
                                           const uint32_t *__restrict__ h0,
@@ -610,16 +621,47 @@ __device__ __forceinline__ int walk_pairs(const uint4 &v0, const uint4 &v1,
                                           uint32_t *hit)
 {
     const int len = run_count(v0);
-    const int S = (int)(v0.z & 0xFFu);
-    const int a_first = (int)((v0.z >> 8) & 0xFFu);
+    if constexpr (!STRIDE) {
+        const int S = (int)(v0.z & 0xFFu);
+        const int a_first = (int)((v0.z >> 8) & 0xFFu);
+        int j = 0;
+        for (;;) {
+            int cand = -1;
+            for (; j < len; j += 2) {
+                const int a = a_first + j;
+                const int b = S - a;
+                /* the second slot is clamped into the table and masked past the run */
+                const int a1 = min(a + 1, n), b1 = max(b - 1, 1);
+                const bool m0 = (h0[a - 1] ^ h0[b - 1]) == P0;
+                const bool m1 = ((h0[a1 - 1] ^ h0[b1 - 1]) == P0) && (j + 1 < len);
+                if (m0 || m1) {
+                    cand = j + (m0 ? 0 : 1);
+                    break;
+                }
+            }
+            if (cand < 0)
+                return -1;
+            if (W == 1 ||
+                verify_query<W>(v0, v1, h, s0, n, (uint32_t)(a_first + cand), nullptr)) {
+                *hit = (uint32_t)(a_first + cand);
+                return cand;
+            }
+            j = cand + 1;
+        }
+    }
+    const bool stride = run_kind(v0) == ORBG_RUN_STRIDE;
+    const int a_first = stride ? (int)(v0.z & 0xFFu) : (int)((v0.z >> 8) & 0xFFu);
+    const int b_first =
+        stride ? (int)((v0.z >> 8) & 0xFFu) : (int)(v0.z & 0xFFu) - a_first;
+    const int da = stride ? (int)((v0.z >> 16) & 0xFFu) : 1;
+    const int db = stride ? (int)(v0.z >> 24) : 1;
     int j = 0;
     for (;;) {
         int cand = -1;
-        for (; j < len; j += 2) {
-            const int a = a_first + j;
-            const int b = S - a;
+        int a = a_first + j * da, b = b_first - j * db;
+        for (; j < len; j += 2, a += 2 * da, b -= 2 * db) {
             /* the second slot is clamped into the table and masked past the run */
-            const int a1 = min(a + 1, n), b1 = max(b - 1, 1);
+            const int a1 = min(a + da, n), b1 = max(b - db, 1);
             const bool m0 = (h0[a - 1] ^ h0[b - 1]) == P0;
             const bool m1 = ((h0[a1 - 1] ^ h0[b1 - 1]) == P0) && (j + 1 < len);
             if (m0 || m1) {
@@ -629,8 +671,9 @@ __device__ __forceinline__ int walk_pairs(const uint4 &v0, const uint4 &v1,
         }
         if (cand < 0)
             return -1;
-        if (W == 1 || verify_query<W>(v0, v1, h, s0, n, (uint32_t)(a_first + cand), nullptr)) {
-            *hit = (uint32_t)(a_first + cand);
+        const uint32_t hv = stride ? (uint32_t)cand : (uint32_t)(a_first + cand);
+        if (W == 1 || verify_query<W>(v0, v1, h, s0, n, hv, nullptr)) {
+            *hit = hv;
             return cand;
         }
         j = cand + 1;
@@ -639,7 +682,7 @@ __device__ __forceinline__ int walk_pairs(const uint4 &v0, const uint4 &v1,
 
 /* Walk one run of the warp table unless it cannot beat `best`.  Returns the
  * run's first hit index (or ORBG_NONE) and the hit value for the flips. */
-template <int W>
+template <int W, bool STRIDE = true>
 __device__ __forceinline__ uint32_t search_run_warp(const uint4 &v0, const uint4 &v1,
                                                     const typename Syn<W>::T *__restrict__ h,
                                                     const uint32_t *__restrict__ h0,
@@ -657,7 +700,7 @@ __device__ __forceinline__ uint32_t search_run_warp(const uint4 &v0, const uint4
         }
         return ORBG_NONE;
     }
-    const int j = walk_pairs<W>(v0, v1, h, h0, s0, P0, n, hit);
+    const int j = walk_pairs<W, STRIDE>(v0, v1, h, h0, s0, P0, n, hit);
     return j < 0 ? ORBG_NONE : tstart + (uint32_t)j;
 }
 
@@ -673,7 +716,7 @@ __device__ __forceinline__ uint32_t zero16(uint32_t t)
  * step.  Entries at or past x3lim are not built: those queries are formed
  * from the triple list instead (slower, used only near the end of a warp's
  * own table). */
-template <int W>
+template <int W, bool STRIDE = true>
 __device__ __forceinline__ uint32_t search_run_cta(const uint4 &v0, const uint4 &v1,
                                                    const typename Syn<W>::T *__restrict__ h,
                                                    const uint32_t *__restrict__ h0,
@@ -742,7 +785,7 @@ __device__ __forceinline__ uint32_t search_run_cta(const uint4 &v0, const uint4 
         }
         return ORBG_NONE;
     }
-    const int j = walk_pairs<W>(v0, v1, h, h0, s0, P0, n, hit);
+    const int j = walk_pairs<W, STRIDE>(v0, v1, h, h0, s0, P0, n, hit);
     return j < 0 ? ORBG_NONE : tstart + (uint32_t)j;
 }
 
@@ -761,6 +804,7 @@ __device__ __forceinline__ void load_run(const OrbgTable &tb, uint32_t e, uint4 
 /* ----------------------------------------------------- step 5: output */
 
 /* The owner of the winning run applies its flips to the staged codeword. */
+template <bool STRIDE = true>
 __device__ __forceinline__ void apply_flips(const OrbgTable &tb, uint32_t run, uint32_t hit,
                                             const uint32_t *trip, const uint8_t *pi,
                                             uint8_t *cw)
@@ -773,7 +817,7 @@ __device__ __forceinline__ void apply_flips(const OrbgTable &tb, uint32_t run, u
         cw[pi[(int)((wd >> (8 * (i & 3))) & 0xFFu) - 1]] ^= 1;
     }
     int pos[3];
-    const int k = query_tail(v0, hit, trip, pos);
+    const int k = query_tail<STRIDE>(v0, hit, trip, pos);
     for (int i = 0; i < k; i++)
         cw[pi[pos[i]]] ^= 1;
 }
@@ -888,7 +932,8 @@ __device__ __forceinline__ uint32_t group_reaching(const OrbgTable &tb, uint32_t
  * here.  LS: llr points into shared memory (the batched kernel stages it
  * there).
  */
-template <int K, int W, bool LS = false, bool TRIP = false, bool PF = true, bool ROLL = true>
+template <int K, int W, bool LS = false, bool TRIP = false, bool PF = true, bool ROLL = true,
+          bool STRIDE = true>
 __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__restrict__ llr,
                                   uint8_t *__restrict__ cw_out, uint32_t *__restrict__ q_out,
                                   uint8_t *__restrict__ ab_out, uint32_t cap, uint32_t budget,
@@ -1031,10 +1076,10 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
                 uint32_t hv = 0;
                 uint32_t mine;
                 if (TRIP)
-                    mine = search_run_cta<W>(v0, v1, sm.h, sm.h0, X3w, x3lim, code.trip, s0,
+                    mine = search_run_cta<W, STRIDE>(v0, v1, sm.h, sm.h0, X3w, x3lim, code.trip, s0,
                                              best, cap, n, code.exact16 != 0, &hv);
                 else
-                    mine = search_run_warp<W>(v0, v1, sm.h, sm.h0, s0, best, cap, n, &hv);
+                    mine = search_run_warp<W, STRIDE>(v0, v1, sm.h, sm.h0, s0, best, cap, n, &hv);
                 const uint32_t gbest = __reduce_min_sync(FULL_MASK, mine);
                 if (gbest < best) {
                     best = gbest;
@@ -1082,7 +1127,7 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
         if (my_run == ORBG_NONE)
             apply_flat_flips(code, my_t, sm.pi, sm.cw);
         else
-            apply_flips(tb, my_run, my_hit, code.trip, sm.pi, sm.cw);
+            apply_flips<STRIDE>(tb, my_run, my_hit, code.trip, sm.pi, sm.cw);
     }
     __syncwarp();
 #pragma unroll
@@ -1109,7 +1154,7 @@ __device__ void decode_block_warp(const OrbgDeviceCode &code, const float *__res
  * the best never increases, so no group that could hold the final best is
  * skipped.
  */
-template <int K, int W>
+template <int K, int W, bool STRIDE = true>
 __device__ void decode_block_cta(const OrbgDeviceCode &code, const float *__restrict__ llr,
                                  uint8_t *__restrict__ cw_out, uint32_t *__restrict__ q_out,
                                  uint8_t *__restrict__ ab_out, uint32_t cap,
@@ -1211,7 +1256,7 @@ __device__ void decode_block_cta(const OrbgDeviceCode &code, const float *__rest
                 nfloor = gn < tb.ngroups ? __ldg(tb.group_floor + gn) : ORBG_NONE;
                 uint32_t hv = 0;
                 const uint32_t mine =
-                    search_run_cta<W>(v0, v1, sm.h, sm.h0, X3, code.ntrip, code.trip, s0, best,
+                    search_run_cta<W, STRIDE>(v0, v1, sm.h, sm.h0, X3, code.ntrip, code.trip, s0, best,
                                       cap, n, code.exact16 != 0, &hv);
                 const uint32_t gbest = __reduce_min_sync(FULL_MASK, mine);
                 if (gbest != ORBG_NONE) {
@@ -1233,7 +1278,7 @@ __device__ void decode_block_cta(const OrbgDeviceCode &code, const float *__rest
         if (my_run == ORBG_NONE)
             apply_flat_flips(code, my_t, sm.pi, sm.cw);
         else
-            apply_flips(tb, my_run, my_hit, code.trip, sm.pi, sm.cw);
+            apply_flips<STRIDE>(tb, my_run, my_hit, code.trip, sm.pi, sm.cw);
     }
     __syncthreads();
     for (int i = warp * 32 + lane; i < n; i += nwarps * 32)

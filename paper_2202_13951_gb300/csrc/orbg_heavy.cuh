@@ -19,7 +19,7 @@ using namespace orbg_dev;
 #define ORBG_PHASE2_MIN_CTAS 2
 #endif
 
-template <int KMAX, int WMAX, bool ONE>
+template <int KMAX, int WMAX, bool ONE, bool STRIDE>
 __global__ void __launch_bounds__(512, ORBG_PHASE2_MIN_CTAS) orbg_heavy_kernel(
     const OrbgDeviceCode *__restrict__ codes, int ncodes, const int32_t *__restrict__ code_id,
     const int64_t *__restrict__ llr_off, const float *__restrict__ llr, uint32_t cap,
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(512, ORBG_PHASE2_MIN_CTAS) orbg_heavy_kernel(
         const int64_t lo = llr_off ? llr_off[b] : b * n0;
         const int64_t co = cw_off ? cw_off[b] : b * n0;
         if (ONE) {
-            decode_block_cta<KMAX, WMAX>(code0, llr + lo, cw + co, q + b, ab + b, cap, smem,
+            decode_block_cta<KMAX, WMAX, STRIDE>(code0, llr + lo, cw + co, q + b, ab + b, cap, smem,
                                          reinterpret_cast<uint16_t *>(smem + bstride), &s_best,
                                          reinterpret_cast<typename Syn<WMAX>::T *>(&s_s0), from,
                                          warp, lane, nwarps, rec);
@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(512, ORBG_PHASE2_MIN_CTAS) orbg_heavy_kernel(
         const int cid = code_id ? code_id[b] : 0; /* checked in phase 1 */
         const OrbgDeviceCode code = codes[cid];
 #define ORBG_CALL_CTA(KK, WW)                                                               \
-    decode_block_cta<KK, WW>(code, llr + lo, cw + co, q + b, ab + b, cap, smem,              \
+    decode_block_cta<KK, WW, STRIDE>(code, llr + lo, cw + co, q + b, ab + b, cap, smem,              \
                              reinterpret_cast<uint16_t *>(smem + bstride), &s_best,          \
                              reinterpret_cast<typename Syn<WW>::T *>(&s_s0), from, warp, lane,  \
                              nwarps, rec)
@@ -73,11 +73,11 @@ __global__ void __launch_bounds__(512, ORBG_PHASE2_MIN_CTAS) orbg_heavy_kernel(
     (void)ncodes;
 }
 
-template <int KMAX, int WMAX, bool ONE>
-cudaError_t launch_heavy_t(const OrbgBatchedArgs &a, unsigned long long *counters,
+template <int KMAX, int WMAX, bool ONE, bool STRIDE>
+cudaError_t launch_heavy_k(const OrbgBatchedArgs &a, unsigned long long *counters,
                            const unsigned long long *heavy, const unsigned char *hand)
 {
-    auto k2 = orbg_heavy_kernel<KMAX, WMAX, ONE>;
+    auto k2 = orbg_heavy_kernel<KMAX, WMAX, ONE, STRIDE>;
     const int hw = a.heavy_warps > 0 ? a.heavy_warps : 16;
     const uint32_t bstride = block_smem_bytes(a.n_max, a.w32_max);
     const size_t smem = (size_t)bstride + triple_table_bytes(a.ntrip_max);
@@ -93,6 +93,19 @@ cudaError_t launch_heavy_t(const OrbgBatchedArgs &a, unsigned long long *counter
                                                         a.q, a.ab, counters, heavy, hand, bstride,
                                                         c0);
     return cudaGetLastError();
+}
+
+/* One code: strided runs always handled (no cost measured there); code
+ * sets: the kernel with them only where a code has them. */
+template <int KMAX, int WMAX, bool ONE>
+cudaError_t launch_heavy_t(const OrbgBatchedArgs &a, unsigned long long *counters,
+                           const unsigned long long *heavy, const unsigned char *hand)
+{
+    if constexpr (ONE)
+        return launch_heavy_k<KMAX, WMAX, true, true>(a, counters, heavy, hand);
+    else
+        return a.has_stride ? launch_heavy_k<KMAX, WMAX, false, true>(a, counters, heavy, hand)
+                            : launch_heavy_k<KMAX, WMAX, false, false>(a, counters, heavy, hand);
 }
 
 }  // namespace orbg_batched_impl

@@ -10,7 +10,10 @@
  * Warp table (one warp decodes a block):
  *   kind 0  one pattern of weight 0 or 1 (the prefix is the pattern);
  *   kind 1  a prefix v_1 < ... < v_{w-2} and every pair a < b <= n after it
- *           with a + b = S, a ascending from a_lo.
+ *           with a + b = S, a ascending from a_lo;
+ *   kind 2  (m-segment orders) a prefix and the pairs (a_0 + j da, b_0 - j db),
+ *           j = 0, 1, ...: a pair whose positions lie in two segments of
+ *           slopes beta, beta' with beta da = beta' db keeps its weight.
  * CTA table (a CTA decodes a block and first builds the block's triple
  * table X3: the first syndrome word of every triple c < a < b <= n with
  * c + a + b <= S3max, ordered by that sum, then c, then a):
@@ -39,7 +42,7 @@
 #define ORBG_X3_MAX 16384      /* triple-table entries (32 KiB of shared memory, 16 bits each) */
 #define ORBG_X3_WARP_S3 44     /* triple sums a phase-1 warp keeps in its own table */
 
-enum { ORBG_RUN_SINGLE = 0, ORBG_RUN_PAIRS = 1, ORBG_RUN_TRIPLES = 3 };
+enum { ORBG_RUN_SINGLE = 0, ORBG_RUN_PAIRS = 1, ORBG_RUN_STRIDE = 2, ORBG_RUN_TRIPLES = 3 };
 
 /* One run: 32 bytes, read by a lane as two 16-byte loads. */
 struct OrbgRun {
@@ -47,7 +50,9 @@ struct OrbgRun {
     uint16_t count;     /* patterns in the run, >= 1 */
     uint8_t npre;       /* prefix positions used */
     uint8_t kind;       /* ORBG_RUN_* */
-    uint32_t aux;       /* kind 1: S | a_lo << 8 (1-based); kind 3: first X3 index */
+    uint32_t aux;       /* kind 1: S | a_lo << 8 (1-based); kind 2: a_0 | b_0 << 8 | da << 16 |
+                         * db << 24 (pattern j's pair is a_0 + j da, b_0 - j db); kind 3:
+                         * first X3 index */
     uint8_t pre[ORBG_RUN_MAX_PRE]; /* 1-based prefix positions, ascending; 0 = unused */
 };
 
@@ -128,7 +133,8 @@ struct OrbgModel {
     long beta[ORBG_MAX_SEG];
 };
 /* The tables for the m-segment order (reliability weight, then Hamming
- * weight, then positions lexicographically), single and pair runs only. */
+ * weight, then positions lexicographically): single, pair and strided pair
+ * runs. */
 int orbg_build_tables_model(int n, uint64_t cap, const OrbgModel &md, OrbgTables *out);
 int orbg_run_pattern(const OrbgRun &r, int j, const uint32_t *trip, int *v);
 
@@ -162,6 +168,7 @@ struct OrbgBatchedArgs {
     const OrbgDeviceCode *code0;
     int ncodes, n_max, w32_max;
     OrbgVariants var;            /* the set's decoder variants (mixed-code calls) */
+    int has_stride;              /* a code of the set has strided pair runs (kind 2) */
     const int32_t *code_id;
     const int64_t *llr_off;
     const float *llr;
@@ -199,7 +206,8 @@ struct OrbgScratch;
 #define ORBG_DECLARE_BATCHED(K, W)                                                   \
     int orbg_launch_batched_k##K##w##W(const OrbgBatchedArgs &a);                    \
     int orbg_launch_exact_k##K##w##W(const OrbgBatchedArgs &a, const OrbgScratch &s, \
-                                     unsigned long long *queue, int blo, int bhi, int pdl);
+                                     unsigned long long *queue, int blo, int bhi, int pdl, \
+                                     int stride);
 ORBG_DECLARE_BATCHED(1, 1) ORBG_DECLARE_BATCHED(1, 2) ORBG_DECLARE_BATCHED(1, 4)
 ORBG_DECLARE_BATCHED(2, 1) ORBG_DECLARE_BATCHED(2, 2) ORBG_DECLARE_BATCHED(2, 4)
 ORBG_DECLARE_BATCHED(4, 1) ORBG_DECLARE_BATCHED(4, 2) ORBG_DECLARE_BATCHED(4, 4)
@@ -259,7 +267,7 @@ int orbg_launch_code_sort(const int32_t *code_id, const int32_t *bucket, int64_t
                           const OrbgScratch &s, void *stream);
 /* orbg_launch_exact_k*w* for keys per lane K and syndrome words W. */
 int orbg_launch_exact(int K, int W, const OrbgBatchedArgs &a, const OrbgScratch &s,
-                      unsigned long long *queue, int blo, int bhi, int pdl);
+                      unsigned long long *queue, int blo, int bhi, int pdl, int stride);
 /* Outputs of the blocks phase 2 decoded, gathered after the last launch of a
  * batch whose other results already went to the host.  At `out` (memory the
  * device writes, here host-mapped) the heavy list's length (uint64).  With
@@ -302,6 +310,7 @@ struct OrbgSetView {
     OrbgDeviceCode code0;        /* host copy of code 0's descriptor */
     int ncodes, n_max, w32_max;
     OrbgVariants var;
+    int has_stride;
     uint32_t ntrip_max;
     uint32_t x3w_max;
     uint32_t cap_min;

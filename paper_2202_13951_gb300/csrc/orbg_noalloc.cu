@@ -117,6 +117,7 @@ extern "C" int orbg_decode_batched_noalloc(const orbg_codeset *set, const int32_
     a.ncodes = v.ncodes;
     a.n_max = v.n_max;
     a.var = v.var;
+    a.has_stride = v.has_stride;
     a.w32_max = v.w32_max;
     a.code_id = code_id;
     a.llr_off = llr_offset;

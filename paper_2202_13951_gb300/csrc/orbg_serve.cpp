@@ -311,6 +311,7 @@ bool dispatch_one(orbg_server *s)
         a.ncodes = s->view.ncodes;
         a.n_max = s->view.n_max;
         a.var = s->view.var;
+        a.has_stride = s->view.has_stride;
         a.w32_max = s->view.w32_max;
         a.code_id = reinterpret_cast<const int32_t *>(d + bt.L.code_id);
         a.llr_off = reinterpret_cast<const int64_t *>(d + bt.L.llr_off);

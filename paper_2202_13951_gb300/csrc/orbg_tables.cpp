@@ -415,6 +415,8 @@ namespace {
  * from, so a min-heap pops weights in order.  All subsets of one weight R
  * are collected, ordered by (w, positions) and cut into runs: consecutive
  * patterns (p, a, b), (p, a + 1, b - 1), ... with one prefix p become one
+ * pair run, and consecutive (p, a, b), (p, a + da, b - db), ... (a pair
+ * across two segments whose slopes balance, beta da = beta' db) one strided
  * pair run; the rest are single runs.
  */
 struct ModelBuilder {
@@ -510,14 +512,33 @@ struct ModelBuilder {
                 size_t e = s + 1;
                 if (w >= 2) {
                     const int a = v[w - 2], bb = v[w - 1];
+                    /* the step from this pattern to the next, if it keeps the prefix */
+                    int da = 1, db = 1;
+                    if (e < end && std::equal(v, v + w - 2, pat(e))) {
+                        da = pat(e)[w - 2] - a;
+                        db = bb - pat(e)[w - 1];
+                    }
+                    if (da < 1 || db < 1 || da > 255 || db > 255)
+                        da = db = 1;
                     while (e < end && std::equal(v, v + w - 2, pat(e)) &&
-                           pat(e)[w - 2] == a + (int)(e - s) && pat(e)[w - 1] == bb - (int)(e - s))
+                           pat(e)[w - 2] == a + da * (int)(e - s) &&
+                           pat(e)[w - 1] == bb - db * (int)(e - s))
                         e++;
-                    if (a + bb <= 255) {
+                    if (da == 1 && db == 1 && a + bb <= 255) {
                         for (int q = 0; q < w - 2; q++)
                             b.pre[q] = v[q];
                         OrbgRun r = b.blank(ORBG_RUN_PAIRS, w - 2);
                         r.aux = (uint32_t)(a + bb) | ((uint32_t)a << 8);
+                        b.emit(r, (uint64_t)(e - s));
+                        s = e;
+                        continue;
+                    }
+                    if (e - s >= 2 && bb <= 255) {
+                        for (int q = 0; q < w - 2; q++)
+                            b.pre[q] = v[q];
+                        OrbgRun r = b.blank(ORBG_RUN_STRIDE, w - 2);
+                        r.aux = (uint32_t)a | ((uint32_t)bb << 8) | ((uint32_t)da << 16) |
+                                ((uint32_t)db << 24);
                         b.emit(r, (uint64_t)(e - s));
                         s = e;
                         continue;
@@ -591,6 +612,9 @@ int orbg_run_pattern(const OrbgRun &r, int j, const uint32_t *trip, int *v)
         const int S = (int)(r.aux & 0xFFu), a = (int)(r.aux >> 8) + j;
         v[w++] = a;
         v[w++] = S - a;
+    } else if (r.kind == ORBG_RUN_STRIDE) {
+        v[w++] = (int)(r.aux & 0xFFu) + j * (int)((r.aux >> 16) & 0xFFu);
+        v[w++] = (int)((r.aux >> 8) & 0xFFu) - j * (int)(r.aux >> 24);
     } else if (r.kind == ORBG_RUN_TRIPLES) {
         const uint32_t t = trip[r.aux + (uint32_t)j];
         v[w++] = (int)(t & 0xFFu) + 1;
