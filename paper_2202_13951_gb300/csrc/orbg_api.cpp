@@ -842,8 +842,10 @@ int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
     auto cw_at = [&](int64_t b) -> int64_t {
         return b >= B ? n_cw : cw_offset ? cw_offset[b] : b * n0;
     };
-    /* blocks [b0, b1) have codes of the set, and each ends at or before the
-     * start of the next (the first starts at or after 0, checked above) */
+    /* blocks [b0, b1) have codes of the set, each ends at or before the
+     * start of the next (the first starts at or after 0, checked above) and
+     * within the extents taken from the last block (a chunk whose copy would
+     * reach past them is refused before it is made) */
     auto ordered = [&](int64_t b0, int64_t b1) -> bool {
         if (!llr_offset)
             return true;
@@ -852,7 +854,8 @@ int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
             if (c < 0 || c >= set->ncodes)
                 return false;
             const int64_t n = set->n_of[c];
-            if (llr_at(b + 1) < llr_offset[b] + n || cw_at(b + 1) < cw_offset[b] + n)
+            if (llr_at(b + 1) < llr_offset[b] + n || cw_at(b + 1) < cw_offset[b] + n ||
+                llr_at(b + 1) > n_llr || cw_at(b + 1) > n_cw)
                 return false;
         }
         return true;
@@ -877,8 +880,24 @@ int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
     uint32_t *to_q = device_writable_host(queries);
     uint8_t *to_ab = device_writable_host(abandoned);
     const bool in_place = to_cw && to_q && to_ab;
-    const int64_t nch = std::min<int64_t>(8, B / kPipeChunkMin);
-    const int64_t per = (B + nch - 1) / nch;
+    /* chunk bounds: up to eight equal chunks, the first of them cut into a
+     * quarter and three quarters when it is large enough, so that decoding
+     * starts after a shorter first copy */
+    std::vector<int64_t> cut;
+    {
+        const int64_t nch = std::min<int64_t>(8, B / kPipeChunkMin);
+        const int64_t per = (B + nch - 1) / nch;
+        cut.push_back(0);
+        for (int64_t i = 0; i < nch; i++) {
+            const int64_t b0 = i * per, b1 = std::min(B, b0 + per);
+            if (b1 <= b0)
+                break;
+            if (i == 0 && per / 4 >= kPipeChunkMin / 4)
+                cut.push_back(b0 + per / 4);
+            cut.push_back(b1);
+        }
+    }
+    const int64_t nch = (int64_t)cut.size() - 1;
     float *d_llr = nullptr;
     uint8_t *d_cw = nullptr, *d_ab = nullptr;
     uint32_t *d_q = nullptr;
@@ -950,7 +969,7 @@ int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
     bool declined = false;
     std::vector<cudaEvent_t> chunk_done;
     for (int64_t i = 0; i < nch && e == cudaSuccess && le == 0; i++) {
-        const int64_t b0 = i * per, b1 = std::min(B, b0 + per);
+        const int64_t b0 = cut[(size_t)i], b1 = cut[(size_t)i + 1];
         if (b1 <= b0)
             break;
         if (!ordered(b0, b1)) {
@@ -991,7 +1010,7 @@ int decode_batched_pipelined(const orbg_codeset *set, const int32_t *code_id,
     const bool go = e == cudaSuccess && le == 0 && !declined;
     /* every chunk's results out as soon as its phase 1 is done */
     for (size_t i = 0; go && e == cudaSuccess && i < chunk_done.size(); i++) {
-        const int64_t b0 = (int64_t)i * per, b1 = std::min(B, b0 + per);
+        const int64_t b0 = cut[i], b1 = cut[i + 1];
         const int64_t c0 = cw_at(b0), c1 = cw_at(b1);
         if ((e = cudaStreamWaitEvent(s_out, chunk_done[i], 0)) != cudaSuccess ||
             (c1 > c0 && (e = cudaMemcpyAsync(codeword + c0, d_cw + c0, (size_t)(c1 - c0),
