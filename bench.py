@@ -1042,71 +1042,78 @@ def bench_ours(args, rank, world, local):
 PROFILES = {
     "mixed/batched/basic": {
         "kernels": "batched",
-        "digest": "3dab41982de60f1d484523e7550267e529327c0e6ee87a6f4121cdd183f03d12",
+        "digest": "7b03928670c372699143d03d03463cfee560f6f11ab9ea5ef97af34a5324c00b",
         # the step's kernels' DRAM bytes on 250,000 blocks (222.5 MB), x 4
-        "traffic_bytes_per_step": 890.0e6,
         # ALU pipe issue share per kernel, weighted by the full-size step's
-        # time shares (phase 2 61.0 % x 0.548, phase 1 n = 256 42.7 % x 0.362,
-        # n = 128 36.3 % x 0.056, n = 64 32.6 % x 0.032)
-        "issued_frac": 0.52,
+        # time shares (phase 2 61.0 % x 0.547, phase 1 n = 256 42.7 % x 0.363,
+        # n = 128 37.0 % x 0.055, n = 64 33.0 % x 0.032)
+        "traffic_bytes_per_step": 890.0e6,
+        "issued_frac": 0.520,
         "source": "profiles/orbg_batched_mixed_250k_full.md, "
                   "profiles/orbg_batched_mixed_1m_launches.md",
     },
     "bch/batched/fitted3": {
         "kernels": "fitsearch",
-        "digest": "5792a477c39eb8afdce9c72fe081f27fa9205879ae70401e9ff7931b8c2554db",
-        # 346.2 MB on 280,000 blocks, x 400,000 / 280,000
-        "traffic_bytes_per_step": 494.6e6,
-        "issued_frac": 0.320,
+        "digest": "707d54cfc5f5c3e493a94eb96cf08dd3160a23a2342f6fb118a5e41e390b44f7",
+        # 346.1 MB on 280,000 blocks, x 400,000 / 280,000
+        "traffic_bytes_per_step": 494.4e6,
+        "issued_frac": 0.323,
         "source": "profiles/orbg_fitsearch_bch127_3line_280k_full.md",
     },
     "bch/batched/basic": {
         "kernels": "batched",
-        "digest": "3dab41982de60f1d484523e7550267e529327c0e6ee87a6f4121cdd183f03d12",
-        "traffic_bytes_per_step": 237.7e6,  # 166.4 MB on the captured case, x 1.4286
-        "issued_frac": 0.541,
+        "digest": "7b03928670c372699143d03d03463cfee560f6f11ab9ea5ef97af34a5324c00b",
+        # 166.9 MB on the captured case, x 1.4286
+        "traffic_bytes_per_step": 238.4e6,
+        "issued_frac": 0.547,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
     "bch/plain/basic": {
         "kernels": "plain",
-        "digest": "4bb2477bbb5c0c7c08601ad4e162f98436e3c905be021d7ff3bf54897b069467",
-        "traffic_bytes_per_step": 235.3e6,  # 164.7 MB on the captured case, x 1.4286
-        "issued_frac": 0.334,
+        "digest": "2b3529069139a27367233b7ad4e8f57258122caf53cf9a476efde684f6b3b757",
+        # 165.0 MB on the captured case, x 1.4286
+        "traffic_bytes_per_step": 235.7e6,
+        "issued_frac": 0.344,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
     "bch/batched/line": {
         "kernels": "batched",
-        "digest": "3dab41982de60f1d484523e7550267e529327c0e6ee87a6f4121cdd183f03d12",
-        "traffic_bytes_per_step": 241.4e6,  # 169.0 MB on the captured case, x 1.4286
-        "issued_frac": 0.554,
+        "digest": "7b03928670c372699143d03d03463cfee560f6f11ab9ea5ef97af34a5324c00b",
+        # 169.0 MB on the captured case, x 1.4286
+        "traffic_bytes_per_step": 241.4e6,
+        "issued_frac": 0.557,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
     "bch/batched/model": {
         "kernels": "batched",
-        "digest": "3dab41982de60f1d484523e7550267e529327c0e6ee87a6f4121cdd183f03d12",
-        "traffic_bytes_per_step": 239.9e6,  # 167.9 MB on the captured case, x 1.4286
-        "issued_frac": 0.553,
+        "digest": "7b03928670c372699143d03d03463cfee560f6f11ab9ea5ef97af34a5324c00b",
+        # 166.5 MB on the captured case, x 1.4286
+        "traffic_bytes_per_step": 237.9e6,
+        "issued_frac": 0.615,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
     "bch/batched/fitted1": {
         "kernels": "fitline",
-        "digest": "395ffcf7447f124ba3838b9edac798dfc2f5cf4407ffa05e7744e675ee7b8aa9",
-        "traffic_bytes_per_step": 571.2e6,  # 399.8 MB on the captured case, x 1.4286
+        "digest": "7bd931ca690c0430105ccc897302cb8be01efdceb828cbdb210989cb79e7cb4d",
+        # 399.9 MB on the captured case, x 1.4286
+        "traffic_bytes_per_step": 571.2e6,
         "issued_frac": 0.414,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
     "paper256/batched/basic": {
         "kernels": "batched",
-        "digest": "3dab41982de60f1d484523e7550267e529327c0e6ee87a6f4121cdd183f03d12",
-        "traffic_bytes_per_step": 591.7e6,  # 207.1 MB on the captured case, x 2.8571
+        "digest": "7b03928670c372699143d03d03463cfee560f6f11ab9ea5ef97af34a5324c00b",
+        # 207.0 MB on the captured case, x 2.8571
+        "traffic_bytes_per_step": 591.4e6,
         "issued_frac": 0.602,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
     "capolar256/batched/fitted3": {
         "kernels": "fitsearch",
-        "digest": "5792a477c39eb8afdce9c72fe081f27fa9205879ae70401e9ff7931b8c2554db",
-        "traffic_bytes_per_step": 1039.7e6,  # 363.9 MB on the captured case, x 2.8571
-        "issued_frac": 0.234,
+        "digest": "707d54cfc5f5c3e493a94eb96cf08dd3160a23a2342f6fb118a5e41e390b44f7",
+        # 363.5 MB on the captured case, x 2.8571
+        "traffic_bytes_per_step": 1038.4e6,
+        "issued_frac": 0.264,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
 }
