@@ -1197,12 +1197,17 @@ def bench_e2e(orbg, job, args, world, dev):
     steps = max(3, min(args.steps, 20))
     torch.cuda.synchronize(dev)
     per = []
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        ts = time.perf_counter()
-        step()  # host-buffer calls synchronise before returning
-        per.append((time.perf_counter() - ts) * 1e3)
-    dt = time.perf_counter() - t0
+    import gc
+    gc.disable()  # no collector pause inside a timed call
+    try:
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            ts = time.perf_counter()
+            step()  # host-buffer calls synchronise before returning
+            per.append((time.perf_counter() - ts) * 1e3)
+        dt = time.perf_counter() - t0
+    finally:
+        gc.enable()
     dt = max_over_ranks(dt, world, dev)
     blocks = sum_over_ranks(float(B * steps), world, dev)
     return {"value": blocks / dt, "unit": "blocks/s",
