@@ -1054,10 +1054,10 @@ PROFILES = {
     },
     "bch/batched/fitted3": {
         "kernels": "fitsearch",
-        "digest": "707d54cfc5f5c3e493a94eb96cf08dd3160a23a2342f6fb118a5e41e390b44f7",
-        # 346.1 MB on 280,000 blocks, x 400,000 / 280,000
-        "traffic_bytes_per_step": 494.4e6,
-        "issued_frac": 0.323,
+        "digest": "94a00e1d2821a075a805ff0efe814d28bb876986614d7c0631684702ce7a0397",
+        # 346.4 MB on 280,000 blocks, x 400,000 / 280,000
+        "traffic_bytes_per_step": 494.9e6,
+        "issued_frac": 0.317,
         "source": "profiles/orbg_fitsearch_bch127_3line_280k_full.md",
     },
     "bch/batched/basic": {
@@ -1110,10 +1110,10 @@ PROFILES = {
     },
     "capolar256/batched/fitted3": {
         "kernels": "fitsearch",
-        "digest": "707d54cfc5f5c3e493a94eb96cf08dd3160a23a2342f6fb118a5e41e390b44f7",
-        # 363.5 MB on the captured case, x 2.8571
-        "traffic_bytes_per_step": 1038.4e6,
-        "issued_frac": 0.264,
+        "digest": "94a00e1d2821a075a805ff0efe814d28bb876986614d7c0631684702ce7a0397",
+        # 363.9 MB on the captured case, x 2.8571
+        "traffic_bytes_per_step": 1039.7e6,
+        "issued_frac": 0.305,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
 }

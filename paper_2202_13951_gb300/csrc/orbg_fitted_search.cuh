@@ -745,7 +745,7 @@ __device__ typename Syn<W>::T load_record(const OrbgDeviceCode &code,
  * class k holds the sets {j} with j = k + 1 and the larger sets whose second
  * position is k + 1 modulo kClasses (many more classes than warps, so the
  * warps end a pass close together). */
-constexpr int kClasses = 32;
+constexpr int kClasses = 64; /* measured on CA-Polar[256,234]: 32 95 ms, 64 87, 128 88 */
 
 /* Exchange area of the warps of a CTA that search one block together. */
 struct FsTeam {
