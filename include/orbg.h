@@ -178,9 +178,10 @@ ORBG_API int orbg_codeset_create(const orbg_code *const *codes, int ncodes,
 ORBG_API int orbg_codeset_free(orbg_codeset *set);
 
 /*
- * Batched form: two persistent launches.  In the first, warps pull blocks
- * from an atomic work queue and decode each alone up to a query budget; in
- * the second, every CTA takes one still-open block at a time and searches it
+ * Batched form: two persistent phases.  In the first (one launch, or one per
+ * decoder variant of a code set), warps pull blocks from an atomic work
+ * queue and decode each alone up to a query budget; in the second (one
+ * launch), every CTA takes one still-open block at a time and searches it
  * with all its warps.  Blocks with very different query counts, and blocks
  * of different codes, balance across the GPU.
  *   code_id    : [B] index into the set per block, or NULL (all code 0).
