@@ -80,7 +80,7 @@ def gaussian_binomial(m, k):
 
 def pin_first_queries(orc):
     """Sec. III-B: queries 1..3 are {}, {1}, {2}; queries 4-5 are {3} and
-    {1,2} (tie arbitrary in the paper; this build's reading puts the lower
+    {1,2} (tie arbitrary in the paper; this library's reading puts the lower
     Hamming weight first)."""
     g = _golden("sec3b_first_queries.txt")
     for n in (3, 8, 64, 256):

@@ -44,7 +44,7 @@ def test_nan_rejected(orc):
 
 
 def test_sort_ties_and_zero(orc):
-    """Sec. III-A sort, with this build's tie reading: equal |LLR| keep the
+    """Sec. III-A sort, with this library's tie reading: equal |LLR| keep the
     received order, -0 and +0 are equal, +inf is most reliable."""
     llr = np.array([2.0, -0.0, 1.0, -2.0, 0.0, np.inf, -1.0, -np.inf],
                    np.float32)
