@@ -1042,13 +1042,13 @@ def bench_ours(args, rank, world, local):
 PROFILES = {
     "mixed/batched/basic": {
         "kernels": "batched",
-        "digest": "7b03928670c372699143d03d03463cfee560f6f11ab9ea5ef97af34a5324c00b",
-        # the step's kernels' DRAM bytes on 250,000 blocks (222.5 MB), x 4
+        "digest": "3494b48828cb5608a40b74bd8e80af37af1166bf8e2f0c560cc7a46ece5d2c62",
+        # the step's kernels' DRAM bytes on 250,000 blocks (222.4 MB), x 4
         # ALU pipe issue share per kernel, weighted by the full-size step's
-        # time shares (phase 2 61.0 % x 0.547, phase 1 n = 256 42.7 % x 0.363,
-        # n = 128 37.0 % x 0.055, n = 64 33.0 % x 0.032)
-        "traffic_bytes_per_step": 890.0e6,
-        "issued_frac": 0.520,
+        # time shares (phase 2 62.6 % x 0.542, phase 1 n = 256 42.7 % x 0.367,
+        # n = 128 36.5 % x 0.056, n = 64 32.9 % x 0.033)
+        "traffic_bytes_per_step": 889.6e6,
+        "issued_frac": 0.527,
         "source": "profiles/orbg_batched_mixed_250k_full.md, "
                   "profiles/orbg_batched_mixed_1m_launches.md",
     },
@@ -1062,10 +1062,10 @@ PROFILES = {
     },
     "bch/batched/basic": {
         "kernels": "batched",
-        "digest": "7b03928670c372699143d03d03463cfee560f6f11ab9ea5ef97af34a5324c00b",
-        # 166.9 MB on the captured case, x 1.4286
-        "traffic_bytes_per_step": 238.4e6,
-        "issued_frac": 0.547,
+        "digest": "3494b48828cb5608a40b74bd8e80af37af1166bf8e2f0c560cc7a46ece5d2c62",
+        # 166.8 MB on the captured case, x 1.4286
+        "traffic_bytes_per_step": 238.3e6,
+        "issued_frac": 0.554,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
     "bch/plain/basic": {
@@ -1078,34 +1078,34 @@ PROFILES = {
     },
     "bch/batched/line": {
         "kernels": "batched",
-        "digest": "7b03928670c372699143d03d03463cfee560f6f11ab9ea5ef97af34a5324c00b",
-        # 169.0 MB on the captured case, x 1.4286
-        "traffic_bytes_per_step": 241.4e6,
+        "digest": "3494b48828cb5608a40b74bd8e80af37af1166bf8e2f0c560cc7a46ece5d2c62",
+        # 169.1 MB on the captured case, x 1.4286
+        "traffic_bytes_per_step": 241.6e6,
         "issued_frac": 0.557,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
     "bch/batched/model": {
         "kernels": "batched",
-        "digest": "7b03928670c372699143d03d03463cfee560f6f11ab9ea5ef97af34a5324c00b",
-        # 166.5 MB on the captured case, x 1.4286
-        "traffic_bytes_per_step": 237.9e6,
-        "issued_frac": 0.615,
+        "digest": "3494b48828cb5608a40b74bd8e80af37af1166bf8e2f0c560cc7a46ece5d2c62",
+        # 166.4 MB on the captured case, x 1.4286
+        "traffic_bytes_per_step": 237.7e6,
+        "issued_frac": 0.614,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
     "bch/batched/fitted1": {
         "kernels": "fitline",
-        "digest": "7bd931ca690c0430105ccc897302cb8be01efdceb828cbdb210989cb79e7cb4d",
+        "digest": "ee11a040ab090829cf01f10d52aa461b22040add88f62841460595287814a94c",
         # 399.9 MB on the captured case, x 1.4286
-        "traffic_bytes_per_step": 571.2e6,
+        "traffic_bytes_per_step": 571.3e6,
         "issued_frac": 0.414,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
     "paper256/batched/basic": {
         "kernels": "batched",
-        "digest": "7b03928670c372699143d03d03463cfee560f6f11ab9ea5ef97af34a5324c00b",
+        "digest": "3494b48828cb5608a40b74bd8e80af37af1166bf8e2f0c560cc7a46ece5d2c62",
         # 207.0 MB on the captured case, x 2.8571
         "traffic_bytes_per_step": 591.4e6,
-        "issued_frac": 0.602,
+        "issued_frac": 0.598,
         "source": "profiles/bench_workloads_traffic_alu.md",
     },
     "capolar256/batched/fitted3": {

@@ -41,8 +41,12 @@ __global__ void __launch_bounds__(512, ORBG_PHASE2_MIN_CTAS) orbg_heavy_kernel(
             const unsigned long long nheavy = *((volatile unsigned long long *)&counters[1]);
             const unsigned long long slot = atomicAdd(&counters[2], 1ull);
             /* block | tested-below << 32 | handover record << 63 */
-            s_block = slot < nheavy ? heavy[slot] : ~0ull;
-            s_slot = slot;
+            /* code sets take the list from its end: its phase-1 launches run
+             * by decoder variant, shortest codes first, so the longest codes'
+             * blocks, which search longest, list last and start first here */
+            const unsigned long long r = ONE ? slot : nheavy - 1ull - slot;
+            s_block = slot < nheavy ? heavy[r] : ~0ull;
+            s_slot = r;
         }
         __syncthreads();
         const unsigned long long bb = s_block;
