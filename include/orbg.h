@@ -273,8 +273,11 @@ ORBG_API int orbg_decode_batched_noalloc(const orbg_codeset *set,
  *   blocks_per_grab phase 1: blocks a warp takes per work-queue atomic
  *                   (1..1024; 0 = 4)
  *   warp_budget     phase 1: queries of a block's order a single warp walks
- *                   before handing the block to phase 2 (0 = 16384; a value
- *                   >= the call's query cap disables phase 2)
+ *                   before handing the block to phase 2 (0 = 16384).  A warp
+ *                   also hands a block on, whatever the budget, where its
+ *                   walk first needs triple sums past its own triple table
+ *                   (query 14,798 of basic ORBGRAND), so budgets above that
+ *                   act alike; phase 2 runs in every call
  *   heavy_warps     phase 2: warps per CTA sharing one block (1..16; 0 = 8)
  * None of these change any result.
  */

@@ -256,8 +256,6 @@ cudaError_t launch_t(const OrbgBatchedArgs &a)
     int grid = 0, rc;
     if (a.stage == 2) {
         /* phase 2 over the open blocks every chunk's phase 1 listed */
-        if (a.budget >= a.cap)
-            return cudaSuccess;
         return launch_heavy_t<KMAX, WMAX, ONE>(a, counters, heavy, sc.hand);
     }
     /* this launch's slot: its queue heads, bucket counts and cursors, and
@@ -321,8 +319,13 @@ cudaError_t launch_t(const OrbgBatchedArgs &a)
         if ((e = cudaGetLastError()) != cudaSuccess)
             return e;
     }
-    if (a.budget >= a.cap || a.stage == 1)
-        return cudaSuccess; /* every block finished in phase 1, or phase 2 comes later */
+    /* phase 2 runs whatever the budget: a phase-1 walk on the CTA table also
+     * stops, open, where it needs triple sums past the warp's own table
+     * (decode_block_warp), so the list can hold blocks with a budget at or
+     * above the cap too (with an empty list the launch only reads its
+     * length) */
+    if (a.stage == 1)
+        return cudaSuccess; /* phase 2 comes later, over every chunk's list */
     return launch_heavy_t<KMAX, WMAX, ONE>(a, counters, heavy, sc.hand);
 }
 

@@ -928,9 +928,12 @@ __device__ __forceinline__ uint32_t group_reaching(const OrbgTable &tb, uint32_t
  * written: its index is appended to heavy[] (when heavy != NULL) for
  * decode_block_cta, with its reliability order and starting syndrome in
  * the handover record of the same slot when one is free (hand_cap; bit 63
- * of the heavy[] entry says so).  With budget >= cap every block finishes
- * here.  LS: llr points into shared memory (the batched kernel stages it
- * there).
+ * of the heavy[] entry says so).  On the CTA table (TRIP) a walk that
+ * reaches groups needing triple sums past the warp's own table
+ * (ORBG_X3_WARP_S3) with no hit stops there and is listed the same way,
+ * whatever the budget; on the warp table, with budget >= cap every block
+ * finishes here.  LS: llr points into shared memory (the batched kernel
+ * stages it there).
  */
 template <int K, int W, bool LS = false, bool TRIP = false, bool PF = true, bool ROLL = true,
           bool STRIDE = true>

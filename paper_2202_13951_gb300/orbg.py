@@ -446,13 +446,26 @@ def orbg_query_order_model(n, count, table, model):
     return [tuple(int(x) for x in row[1:1 + row[0]]) for row in out[:got]]
 
 
+
+def _out(shape, dtype, device):
+    """An output tensor for a decode helper: torch.empty, or, when the
+    environment sets ORBG_POISON_OUTPUTS=1 (the test suite does), filled
+    with all-ones bits (codeword byte 255, q 2^32 - 1, flag 255), which no
+    decode writes, so an output a call leaves unwritten cannot pass for a
+    result left in recycled memory by an earlier call."""
+    import torch
+    t = torch.empty(shape, dtype=dtype, device=device)
+    if os.environ.get("ORBG_POISON_OUTPUTS") == "1":
+        t.fill_(-1 if dtype == torch.int32 else 0xFF)
+    return t
+
 def fit_models(llr, n, lines, divisible=False, stream=None):
     """orbg_fit_models on a device tensor of B x n FP32 LLRs: the int32
     [B, ORBG_FIT_STRIDE] model records (Sec. III-E), stream-ordered."""
     import torch
     lib = load_library()
     B = llr.numel() // n
-    out = torch.empty((B, ORBG_FIT_STRIDE), dtype=torch.int32, device=llr.device)
+    out = _out((B, ORBG_FIT_STRIDE), torch.int32, llr.device)
     st = _stream(stream if stream is not None else torch.cuda.current_stream(llr.device))
     _check(lib.orbg_fit_models(llr.data_ptr(), B, int(n), int(lines), int(bool(divisible)),
                                out.data_ptr(), st), "orbg_fit_models")
@@ -479,10 +492,10 @@ class Fitted:
         n = self.code.n
         B = llr.numel() // n
         dev = llr.device
-        cw = torch.empty((B, n), dtype=torch.uint8, device=dev)
-        q = torch.empty((B,), dtype=torch.int32, device=dev)
-        ab = torch.empty((B,), dtype=torch.uint8, device=dev)
-        rec = torch.empty((B, ORBG_FIT_STRIDE), dtype=torch.int32, device=dev)
+        cw = _out((B, n), torch.uint8, dev)
+        q = _out((B,), torch.int32, dev)
+        ab = _out((B,), torch.uint8, dev)
+        rec = _out((B, ORBG_FIT_STRIDE), torch.int32, dev)
         st = _stream(stream if stream is not None else torch.cuda.current_stream(dev))
         _check(lib.orbg_fitted_decode(self.handle, llr.data_ptr(), B, int(query_cap),
                                       cw.data_ptr(), q.data_ptr(), ab.data_ptr(),
@@ -567,9 +580,9 @@ def decode(code, llr, query_cap, stream=None):
     queries int32, abandoned u8) tensors on the same device."""
     import torch
     B = llr.shape[0]
-    cw = torch.empty((B, code.n), dtype=torch.uint8, device=llr.device)
-    q = torch.empty((B,), dtype=torch.int32, device=llr.device)
-    ab = torch.empty((B,), dtype=torch.uint8, device=llr.device)
+    cw = _out((B, code.n), torch.uint8, llr.device)
+    q = _out((B,), torch.int32, llr.device)
+    ab = _out((B,), torch.uint8, llr.device)
     orbg_decode(code.handle, llr, B, query_cap, cw, q, ab,
                 stream if stream is not None else torch.cuda.current_stream(llr.device))
     return cw, q, ab
@@ -583,10 +596,10 @@ def decode_fitted(code, llr, query_cap, lines, divisible=False, stream=None):
     import torch
     B = llr.shape[0]
     dev = llr.device
-    cw = torch.empty((B, code.n), dtype=torch.uint8, device=dev)
-    q = torch.empty((B,), dtype=torch.int32, device=dev)
-    ab = torch.empty((B,), dtype=torch.uint8, device=dev)
-    rec = torch.empty((B, ORBG_FIT_STRIDE), dtype=torch.int32, device=dev)
+    cw = _out((B, code.n), torch.uint8, dev)
+    q = _out((B,), torch.int32, dev)
+    ab = _out((B,), torch.uint8, dev)
+    rec = _out((B, ORBG_FIT_STRIDE), torch.int32, dev)
     orbg_decode_fitted(code.handle, llr, B, query_cap, lines, divisible, cw, q, ab, rec,
                        stream if stream is not None else torch.cuda.current_stream(dev))
     return cw, q, ab, rec
@@ -601,12 +614,12 @@ def decode_batched(codeset, llr, query_cap, code_id=None, llr_offset=None,
     if llr_offset is None:
         n = codeset.codes[0].n
         B = llr.numel() // n
-        cw = torch.empty((B, n), dtype=torch.uint8, device=dev)
+        cw = _out((B, n), torch.uint8, dev)
     else:
         B = llr_offset.shape[0]
-        cw = torch.empty((n_total,), dtype=torch.uint8, device=dev)
-    q = torch.empty((B,), dtype=torch.int32, device=dev)
-    ab = torch.empty((B,), dtype=torch.uint8, device=dev)
+        cw = _out((n_total,), torch.uint8, dev)
+    q = _out((B,), torch.int32, dev)
+    ab = _out((B,), torch.uint8, dev)
     orbg_decode_batched(codeset.handle, code_id, llr_offset, llr, B, query_cap, cw,
                         cw_offset, q, ab,
                         stream if stream is not None else torch.cuda.current_stream(dev))

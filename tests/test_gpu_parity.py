@@ -364,8 +364,9 @@ def test_batched_call_in_cuda_graph(orbg):
         orbg.orbg_decode_batched(cs.handle, None, None, x, B, 10 ** 6, cw, None, q, ab,
                                  torch.cuda.current_stream())
     for _ in range(2):
-        cw.zero_()
-        q.zero_()
+        cw.fill_(0xFF)
+        q.fill_(-1)
+        ab.fill_(0xFF)
         g.replay()
         torch.cuda.synchronize()
         assert_same((cw.cpu().numpy(), q.cpu().numpy().astype(np.int64), ab.cpu().numpy()),
@@ -438,8 +439,8 @@ def test_code_ids_outside_the_set_and_one_variant_sets(orbg):
         objs = [orbg.Code(c.H, max_query_cap=10 ** 5) for c in codes]
         cs = orbg.CodeSet(objs)
         cw = torch.full((llr.shape[0],), 7, dtype=torch.uint8, device="cuda")
-        q = torch.empty(B, dtype=torch.int32, device="cuda")
-        ab = torch.empty(B, dtype=torch.uint8, device="cuda")
+        q = torch.full((B,), -1, dtype=torch.int32, device="cuda")
+        ab = torch.full((B,), 0xFF, dtype=torch.uint8, device="cuda")
         off_t = torch.from_numpy(off).cuda()
         orbg.orbg_decode_batched(cs.handle, torch.from_numpy(cid).cuda(), off_t,
                                  torch.from_numpy(llr).cuda(), B, 10 ** 5, cw, off_t, q, ab,
@@ -582,6 +583,56 @@ def test_batched_tuning_does_not_change_results(orbg, tuning):
     cs = orbg.CodeSet([c])
     orbg.orbg_codeset_set_tuning(cs.handle, orbg.OrbgTuning(*tuning))
     assert_same(gpu_batched(orbg, cs, llr, cap), want)
+
+
+
+# In basic ORBGRAND's CTA table, phase 1's walk reaches its first group
+# needing triple sums past the warp's own table at this query index, whatever
+# the code's length (the run layout depends on the order alone).
+WARP_TRIPLES_END = 14798
+
+
+def test_budget_at_or_above_cap_still_runs_phase_2(orbg):
+    """A phase-1 walk on the CTA table stops, open, where it needs triple sums
+    past the warp's own table, whatever the budget.  With the default budget
+    (16384) and a cap between that point and the budget, and with a budget
+    far above the cap, the open blocks still reach phase 2: outputs start
+    poisoned and equal the oracle's, on device buffers."""
+    code = workloads.rlc(64, 44, 61)
+    llr, _ = workloads.awgn_llr(code, 4000, 2.5, 63)
+    cap = 16000
+    want = oracle.decode_batch(code.H, llr, cap)[:3]
+    assert (want[1].astype(np.int64) > WARP_TRIPLES_END).sum() >= 10
+    c = orbg.Code(code.H, max_query_cap=10 ** 5)
+    for tuning in (None, (8, 0, 4, 16384, 8), (8, 0, 4, 10 ** 6, 4)):
+        cs = orbg.CodeSet([c])
+        if tuning is not None:
+            orbg.orbg_codeset_set_tuning(cs.handle, orbg.OrbgTuning(*tuning))
+        assert_same(gpu_batched(orbg, cs, llr, cap), want)
+
+
+def test_budget_above_cap_host_buffers(orbg):
+    """The chunked host-buffer path with a budget above the cap: its phase 2
+    over every chunk's open blocks still runs.  Host outputs start poisoned;
+    they equal the device-buffer call, and the oracle on every block past the
+    warp's own triple table."""
+    code = workloads.rlc(64, 44, 61)
+    llr, _ = workloads.awgn_llr(code, 140000, 3.5, 64)
+    B, n = llr.shape
+    cap = 16000
+    c = orbg.Code(code.H, max_query_cap=10 ** 5)
+    cs = orbg.CodeSet([c])
+    orbg.orbg_codeset_set_tuning(cs.handle, orbg.OrbgTuning(8, 0, 4, 10 ** 6, 4))
+    dev = gpu_batched(orbg, cs, llr, cap)
+    cw = np.full((B, n), 0xFF, np.uint8)
+    q = np.full(B, 0xFFFFFFFF, np.uint32)
+    ab = np.full(B, 0xFF, np.uint8)
+    orbg.orbg_decode_batched(cs.handle, None, None, llr, B, cap, cw, None, q, ab)
+    assert_same((cw, q.astype(np.int64), ab), dev)
+    far = np.nonzero(dev[1] > WARP_TRIPLES_END)[0]
+    assert far.size >= 10
+    want = oracle.decode_batch(code.H, llr[far], cap)[:3]
+    assert_same((cw[far], q[far].astype(np.int64), ab[far]), want)
 
 
 def test_mixed_codes_phase2(orbg):
