@@ -131,11 +131,22 @@ def parse_args(argv=None):
     p.add_argument("--shape", default="",
                    help="warps_per_cta,ctas_per_sm,blocks_per_grab,warp_budget,heavy_warps "
                         "for the batched launch (orbg_tuning)")
+    p.add_argument("--cap", type=int, default=0,
+                   help="query cap of the codes and calls (0 = the workload's own); a low "
+                        "cap stops every search there, which times the fixed work a block "
+                        "costs (loading, query 1, writing)")
     args = p.parse_args(argv)
     select_workload(args.workload, args.blocks_per_point)
     if args.points:
         set_points(tuple(float(x) for x in args.points.split(",")))
-    global LINE, MODEL, FITTED, WORKLOAD
+    global LINE, MODEL, FITTED, WORKLOAD, CAP
+    if args.cap < 0:
+        raise SystemExit("--cap must be positive")
+    if args.cap:
+        CAP = int(args.cap)
+        head, tail = WORKLOAD.split("query cap ", 1)
+        rest = tail.split(",", 1)
+        WORKLOAD = head + "query cap %d" % CAP + ("," + rest[1] if len(rest) > 1 else "")
     if sum(map(bool, (args.line, args.model, args.fitted, args.fitted_lines))) > 1:
         raise SystemExit("give one of --line, --model, --fitted, --fitted-lines")
     FITTED = bool(args.fitted)

@@ -119,6 +119,10 @@ def test_extra_runs_parse_their_arguments():
         bench.parse_args(["--workload", "paper256"])
         assert bench.CAP == 5_000_000 and "paper-shaped" in bench.WORKLOAD
         assert not a.no_extra
+        bench.parse_args(["--workload", "bch", "--cap", "33"])
+        assert bench.CAP == 33 and bench.WORKLOAD.endswith("query cap 33")
+        bench.parse_args(["--workload", "mixed", "--cap", "1"])
+        assert bench.CAP == 1 and "query cap 1, one launch, autotuned" in bench.WORKLOAD
     finally:
         bench.MODEL = None
         bench.LINE = None
