@@ -323,6 +323,14 @@ ORBG_API int orbg_codeset_get_tuning(const orbg_codeset *set, orbg_tuning *t);
  *                      [B], abandoned [B] (any pointer may be NULL) to host
  *                      memory, with its latency from submit to completion
  *                      in seconds, and forgets the request.
+ *   cancel           : withdraws a request: it is never reported by poll
+ *                      and fetch no longer finds it.  One still waiting is
+ *                      removed; one already in a batch still runs on the
+ *                      device (its blocks share the batch's launch) and its
+ *                      results are dropped when the batch finishes; one
+ *                      finished but not yet fetched is discarded.  EINVAL
+ *                      if the server knows no such id (never submitted,
+ *                      already fetched or cancelled).
  *   destroy          : waits for submitted work, then frees everything.
  * The server's own extension, not the paper's (the paper decodes one block
  * at a time, Algorithm 1).
@@ -333,6 +341,7 @@ typedef struct orbg_server_stats {
     uint64_t blocks_submitted, blocks_done;
     uint64_t batches, max_batch_blocks, max_inflight_batches;
     uint64_t pending, inflight_batches;
+    uint64_t cancelled;  /* requests withdrawn by orbg_server_cancel */
 } orbg_server_stats;
 
 ORBG_API int orbg_server_create(const orbg_codeset *set, size_t mem_budget_bytes,
@@ -345,6 +354,7 @@ ORBG_API int orbg_server_poll(orbg_server *srv, uint64_t *ids, int max_ids,
 ORBG_API int orbg_server_fetch(orbg_server *srv, uint64_t request_id,
                                uint8_t *codeword, uint32_t *queries,
                                uint8_t *abandoned, double *latency_s);
+ORBG_API int orbg_server_cancel(orbg_server *srv, uint64_t request_id);
 ORBG_API int orbg_server_stats_get(orbg_server *srv, orbg_server_stats *out);
 ORBG_API int orbg_server_destroy(orbg_server *srv);
 

@@ -102,6 +102,7 @@ struct Request {
     std::vector<uint32_t> q;
     std::vector<uint8_t> ab;
     double t_submit = 0, t_done = 0;
+    bool cancelled = false; /* in a batch when cancelled: dropped when it retires */
 };
 
 /* Byte layout of one batch; identical in the device and the pinned pool. */
@@ -200,6 +201,12 @@ void retire(orbg_server *s)
         const double t = now_s();
         for (Request *r : it->reqs) {
             const size_t nb = (size_t)r->B * r->n;
+            if (r->cancelled) {
+                b += r->B;
+                off += nb;
+                delete r;
+                continue;
+            }
             r->cw.assign(cw + off, cw + off + nb);
             r->q.assign(q + b, q + b + r->B);
             r->ab.assign(ab + b, ab + b + r->B);
@@ -520,6 +527,41 @@ int orbg_server_fetch(orbg_server *s, uint64_t request_id, uint8_t *codeword, ui
     if (latency_s) *latency_s = r->t_done - r->t_submit;
     delete r;
     return ORBG_OK;
+}
+
+int orbg_server_cancel(orbg_server *s, uint64_t request_id)
+{
+    if (!s)
+        return ORBG_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (auto it = s->pending.begin(); it != s->pending.end(); ++it) {
+        if ((*it)->id == request_id) {
+            delete *it;
+            s->pending.erase(it);
+            s->stats.cancelled += 1;
+            return ORBG_OK;
+        }
+    }
+    for (Batch &bt : s->inflight) {
+        for (Request *r : bt.reqs) {
+            if (r->id == request_id && !r->cancelled) {
+                r->cancelled = true;
+                s->stats.cancelled += 1;
+                return ORBG_OK;
+            }
+        }
+    }
+    auto d = s->done.find(request_id);
+    if (d != s->done.end()) {
+        delete d->second;
+        s->done.erase(d);
+        auto o = std::find(s->done_order.begin(), s->done_order.end(), request_id);
+        if (o != s->done_order.end())
+            s->done_order.erase(o);
+        s->stats.cancelled += 1;
+        return ORBG_OK;
+    }
+    return ORBG_EINVAL;
 }
 
 int orbg_server_stats_get(orbg_server *s, orbg_server_stats *out)

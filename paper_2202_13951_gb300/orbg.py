@@ -52,7 +52,8 @@ class OrbgServerStats(ctypes.Structure):
     """struct orbg_server_stats of include/orbg.h."""
     _fields_ = [(f, ctypes.c_uint64) for f in (
         "submitted", "completed", "blocks_submitted", "blocks_done", "batches",
-        "max_batch_blocks", "max_inflight_batches", "pending", "inflight_batches")]
+        "max_batch_blocks", "max_inflight_batches", "pending", "inflight_batches",
+        "cancelled")]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -126,6 +127,7 @@ def load_library(path=None):
     lib.orbg_server_poll.argtypes = [vp, vp, i32, i32]
     lib.orbg_server_fetch.argtypes = [vp, ctypes.c_uint64, vp, vp, vp,
                                       ctypes.POINTER(ctypes.c_double)]
+    lib.orbg_server_cancel.argtypes = [vp, ctypes.c_uint64]
     lib.orbg_server_stats_get.argtypes = [vp, ctypes.POINTER(OrbgServerStats)]
     lib.orbg_server_destroy.argtypes = [vp]
     lib.orbg_server_replay.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp,
@@ -134,7 +136,8 @@ def load_library(path=None):
               "orbg_free_code", "orbg_code_info", "orbg_decode",
               "orbg_codeset_create", "orbg_codeset_free", "orbg_decode_batched",
               "orbg_decode_batched_noalloc", "orbg_server_create", "orbg_server_submit",
-              "orbg_server_poll", "orbg_server_fetch", "orbg_server_stats_get",
+              "orbg_server_poll", "orbg_server_fetch", "orbg_server_cancel",
+              "orbg_server_stats_get",
               "orbg_server_destroy", "orbg_server_replay",
               "orbg_codeset_set_tuning", "orbg_codeset_get_tuning", "orbg_probe_int_lanes",
               "orbg_probe_smem_bytes", "orbg_codeset_autotune", "orbg_fit_models",
@@ -324,6 +327,10 @@ def orbg_server_fetch(srv, request_id, codeword=None, queries=None, abandoned=No
                                             _ptr(queries, "uint32"), _ptr(abandoned, "uint8"),
                                             ctypes.byref(lat)), "orbg_server_fetch")
     return lat.value
+
+
+def orbg_server_cancel(srv, request_id):
+    _check(load_library().orbg_server_cancel(srv, int(request_id)), "orbg_server_cancel")
 
 
 def orbg_server_stats_get(srv):

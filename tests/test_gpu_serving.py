@@ -102,3 +102,68 @@ def test_overlapping_batches_and_admission(orbg):
         assert ei.value.status == orbg.ORBG_ELIMIT
     finally:
         orbg.orbg_server_destroy(srv)
+
+
+def test_cancel_waiting_running_and_finished_requests(orbg):
+    """orbg_server_cancel withdraws a request wherever it is: still waiting
+    (removed), in a batch (it runs, its results are dropped), or finished
+    and not yet fetched (discarded).  A cancelled id is never reported by
+    poll and cannot be fetched; every other request completes as usual and
+    decodes as it does alone.  Which of the three cases a cancel meets
+    depends on timing; each outcome is checked the same way."""
+    import time
+    cap = 10 ** 6
+    codes_w = workloads.config5_codes()
+    codes = [orbg.Code(c.H, max_query_cap=cap) for c in codes_w]
+    cs = orbg.CodeSet(codes)
+    srv = orbg.orbg_server_create(cs.handle, 64 << 20, cap, 2, 2048)
+    try:
+        reqs = [workloads.awgn_llr(codes_w[1], 1500, 2.5, 2000 + i)[0] for i in range(8)]
+        for i, llr in enumerate(reqs):  # one request a batch, two batches at a time
+            orbg.orbg_server_submit(srv, i, 1, llr, llr.shape[0])
+        cancel = [0, 6, 7]
+        for i in cancel:
+            orbg.orbg_server_cancel(srv, i)
+        for bad in (6, 12345):  # already withdrawn; never submitted
+            with pytest.raises(orbg.OrbgError) as ei:
+                orbg.orbg_server_cancel(srv, bad)
+            assert ei.value.status == orbg.ORBG_EINVAL
+        want = set(range(len(reqs))) - set(cancel)
+        got = set()
+        t0 = time.time()
+        while got != want:
+            ids = orbg.orbg_server_poll(srv, 64, 100000)
+            assert not set(ids) & set(cancel)
+            got.update(ids)
+            assert time.time() - t0 < 120
+        # a request that finishes and is neither polled nor fetched
+        small = workloads.awgn_llr(codes_w[0], 8, 6.0, 2100)[0]
+        orbg.orbg_server_submit(srv, 50, 0, small, small.shape[0])
+        while True:
+            st = orbg.orbg_server_stats_get(srv)
+            if st["pending"] == 0 and st["inflight_batches"] == 0:
+                break
+            assert time.time() - t0 < 120
+            time.sleep(0.001)
+        orbg.orbg_server_cancel(srv, 50)
+        assert 50 not in orbg.orbg_server_poll(srv, 64, 1000)
+        for i in cancel + [50]:
+            with pytest.raises(orbg.OrbgError):
+                orbg.orbg_server_fetch(srv, i)
+        cd = codes_w[1]
+        for i in sorted(want):
+            B = reqs[i].shape[0]
+            cw = np.zeros(B * cd.n, np.uint8)
+            q = np.zeros(B, np.uint32)
+            ab = np.zeros(B, np.uint8)
+            orbg.orbg_server_fetch(srv, i, cw, q, ab)
+            if i in (1, 5):
+                alone = _alone(orbg, cs, cd, reqs[i], cap, 1, len(codes))
+                assert np.array_equal(cw.reshape(B, cd.n), alone[0])
+                assert np.array_equal(q.astype(np.int64), alone[1])
+                assert np.array_equal(ab, alone[2])
+        st = orbg.orbg_server_stats_get(srv)
+        assert st["cancelled"] == len(cancel) + 1
+        assert st["submitted"] == len(reqs) + 1
+    finally:
+        orbg.orbg_server_destroy(srv)
