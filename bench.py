@@ -1058,7 +1058,7 @@ def bench_ours(args, rank, world, local):
 PROFILES = {
     "mixed/batched/basic": {
         "kernels": "batched",
-        "digest": "3494b48828cb5608a40b74bd8e80af37af1166bf8e2f0c560cc7a46ece5d2c62",
+        "digest": "2c12445a5d48257a47c952b322d3bff627fe866c08f362acfe76301aa124f4ac",
         # the step's kernels' DRAM bytes on 250,000 blocks (222.4 MB), x 4
         # ALU pipe issue share per kernel, weighted by the full-size step's
         # time shares (phase 2 62.6 % x 0.542, phase 1 n = 256 42.7 % x 0.367,
@@ -1070,7 +1070,7 @@ PROFILES = {
     },
     "bch/batched/fitted3": {
         "kernels": "fitsearch",
-        "digest": "94a00e1d2821a075a805ff0efe814d28bb876986614d7c0631684702ce7a0397",
+        "digest": "de5fe7c9402f8746661f22207cfd249604b74f2bced388ba6bcd2e522d9358f9",
         # 346.4 MB on 280,000 blocks, x 400,000 / 280,000
         "traffic_bytes_per_step": 494.9e6,
         "issued_frac": 0.317,
@@ -1078,7 +1078,7 @@ PROFILES = {
     },
     "bch/batched/basic": {
         "kernels": "batched",
-        "digest": "3494b48828cb5608a40b74bd8e80af37af1166bf8e2f0c560cc7a46ece5d2c62",
+        "digest": "2c12445a5d48257a47c952b322d3bff627fe866c08f362acfe76301aa124f4ac",
         # 166.8 MB on the captured case, x 1.4286
         "traffic_bytes_per_step": 238.3e6,
         "issued_frac": 0.554,
@@ -1086,7 +1086,7 @@ PROFILES = {
     },
     "bch/plain/basic": {
         "kernels": "plain",
-        "digest": "2b3529069139a27367233b7ad4e8f57258122caf53cf9a476efde684f6b3b757",
+        "digest": "c529c1ef75f6f3ff68d8e84ae7a9ed48dd5b78b9e935a6f10120dd8354ec41b8",
         # 165.0 MB on the captured case, x 1.4286
         "traffic_bytes_per_step": 235.7e6,
         "issued_frac": 0.344,
@@ -1094,7 +1094,7 @@ PROFILES = {
     },
     "bch/batched/line": {
         "kernels": "batched",
-        "digest": "3494b48828cb5608a40b74bd8e80af37af1166bf8e2f0c560cc7a46ece5d2c62",
+        "digest": "2c12445a5d48257a47c952b322d3bff627fe866c08f362acfe76301aa124f4ac",
         # 169.1 MB on the captured case, x 1.4286
         "traffic_bytes_per_step": 241.6e6,
         "issued_frac": 0.557,
@@ -1102,7 +1102,7 @@ PROFILES = {
     },
     "bch/batched/model": {
         "kernels": "batched",
-        "digest": "3494b48828cb5608a40b74bd8e80af37af1166bf8e2f0c560cc7a46ece5d2c62",
+        "digest": "2c12445a5d48257a47c952b322d3bff627fe866c08f362acfe76301aa124f4ac",
         # 166.4 MB on the captured case, x 1.4286
         "traffic_bytes_per_step": 237.7e6,
         "issued_frac": 0.614,
@@ -1110,7 +1110,7 @@ PROFILES = {
     },
     "bch/batched/fitted1": {
         "kernels": "fitline",
-        "digest": "ee11a040ab090829cf01f10d52aa461b22040add88f62841460595287814a94c",
+        "digest": "97ba7642ce2a3a88e76f54600d1b4350c6c75f61b0d9d555182f9b108aa4bd8b",
         # 399.9 MB on the captured case, x 1.4286
         "traffic_bytes_per_step": 571.3e6,
         "issued_frac": 0.414,
@@ -1118,7 +1118,7 @@ PROFILES = {
     },
     "paper256/batched/basic": {
         "kernels": "batched",
-        "digest": "3494b48828cb5608a40b74bd8e80af37af1166bf8e2f0c560cc7a46ece5d2c62",
+        "digest": "2c12445a5d48257a47c952b322d3bff627fe866c08f362acfe76301aa124f4ac",
         # 207.0 MB on the captured case, x 2.8571
         "traffic_bytes_per_step": 591.4e6,
         "issued_frac": 0.598,
@@ -1126,7 +1126,7 @@ PROFILES = {
     },
     "capolar256/batched/fitted3": {
         "kernels": "fitsearch",
-        "digest": "94a00e1d2821a075a805ff0efe814d28bb876986614d7c0631684702ce7a0397",
+        "digest": "de5fe7c9402f8746661f22207cfd249604b74f2bced388ba6bcd2e522d9358f9",
         # 363.9 MB on the captured case, x 2.8571
         "traffic_bytes_per_step": 1039.7e6,
         "issued_frac": 0.305,

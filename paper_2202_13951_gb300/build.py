@@ -6,6 +6,7 @@ paper_2202_13951_gb300.build`` or ``build()``.
 """
 import hashlib
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -56,11 +57,15 @@ def _digest(extra=()):
     return h.hexdigest()
 
 
+_COMMENT = re.compile(rb"/\*.*?\*/|//[^\n]*", re.S)
+
+
 def kernel_digest(names=None):
     """SHA-256 of device code (the CUDA sources and the headers they
-    include): all of it, or the files `names` of the source directory.
-    Profiler figures taken on one build stay valid while the kernels they
-    cover are unchanged, whatever happens to the host-only C++ around them."""
+    include, with their comments removed): all of it, or the files `names`
+    of the source directory.  Profiler figures taken on one build stay
+    valid while the kernels they cover are unchanged, whatever happens to
+    the host-only C++ around them or to the comments."""
     h = hashlib.sha256()
     for name in sorted(os.listdir(CSRC)):
         if names is not None and name not in names:
@@ -68,7 +73,7 @@ def kernel_digest(names=None):
         if name.endswith((".cu", ".cuh")) or name == "orbg_internal.h":
             h.update(name.encode())
             with open(os.path.join(CSRC, name), "rb") as f:
-                h.update(hashlib.sha256(f.read()).digest())
+                h.update(hashlib.sha256(_COMMENT.sub(b"", f.read())).digest())
     return h.hexdigest()
 
 
