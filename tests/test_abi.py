@@ -272,3 +272,18 @@ def test_model_with_empty_flat_table(lib):
         model = ((n * 5 // 8,), (-4, 0), (9, 4))
         assert orbg.orbg_query_order_model(n, 5000, 2, model) == []
         _check_model_tables(n, 5000, model)
+
+
+def test_output_poisoning_of_the_decode_helpers(monkeypatch):
+    """The binding's decode helpers allocate their outputs through _out:
+    with ORBG_POISON_OUTPUTS=1 (which this suite sets) every byte of a fresh
+    output holds all-ones bits, a value no decode writes (codeword bytes are
+    0 or 1, q >= 1 or 0 for NaN blocks, flags 0-2); without it the tensor is
+    only allocated."""
+    torch = pytest.importorskip("torch")
+    monkeypatch.setenv("ORBG_POISON_OUTPUTS", "1")
+    cw = orbg._out((3, 5), torch.uint8, "cpu")
+    q = orbg._out((3,), torch.int32, "cpu")
+    assert (cw == 255).all() and (q.view(torch.uint8) == 255).all()
+    monkeypatch.setenv("ORBG_POISON_OUTPUTS", "0")
+    assert orbg._out((2,), torch.uint8, "cpu").shape == (2,)
