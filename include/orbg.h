@@ -542,7 +542,8 @@ ORBG_API int orbg_last_cuda_error(void);
  * Returns ORBG_OK, or ORBG_ECUDA. */
 ORBG_API int orbg_pool_trim(void);
 
-/* Library version, e.g. 100 for 0.1.0. */
+/* Library version, major * 10000 + minor * 100 + patch: 200 for 0.2.0 (0.2 added
+ * orbg_server_cancel and the cancelled count at the end of orbg_server_stats). */
 ORBG_API int orbg_version(void);
 
 #ifdef __cplusplus

@@ -315,7 +315,7 @@ int orbg_pool_trim(void)
     return e == cudaSuccess ? ORBG_OK : cuda_fail(e);
 }
 
-int orbg_version(void) { return 100; }
+int orbg_version(void) { return 200; }
 
 int64_t orbg_query_order(int n, uint32_t count, int table, int32_t *out)
 {

@@ -44,7 +44,7 @@ def test_status_strings_and_version(lib):
     for s in range(-7, 1):
         assert orbg.orbg_status_string(s) not in ("", "unknown status")
     assert orbg.orbg_status_string(-99) == "unknown status"
-    assert orbg.orbg_version() == 100
+    assert orbg.orbg_version() == 200
 
 
 def test_tuning_argument_checks(lib):
