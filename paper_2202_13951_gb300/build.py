@@ -26,7 +26,7 @@ INST_KW = [(k, w) for k in (1, 2, 4, 8) for w in (1, 2, 4)]
 FS_INST = "orbg_fitted_search_inst.cu"
 FS_K = (1, 2, 4, 8)
 HEADERS = ["orbg_internal.h", "orbg_decode_block.cuh", "orbg_batched.cuh", "orbg_heavy.cuh",
-           "orbg_fit.cuh", "orbg_fitted_search.cuh"]
+           "orbg_fit.cuh", "orbg_fitted_search.cuh", "orbg_regions.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

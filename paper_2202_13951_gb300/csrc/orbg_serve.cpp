@@ -38,6 +38,7 @@
 
 #include "../../include/orbg.h"
 #include "orbg_internal.h"
+#include "orbg_regions.h"
 
 namespace {
 
@@ -49,48 +50,6 @@ double now_s()
 }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
-
-/* First-fit allocator over [0, size) with 256-byte granules. */
-class Regions {
-  public:
-    explicit Regions(size_t size) { free_[0] = size; }
-    bool alloc(size_t bytes, size_t *off)
-    {
-        bytes = align_up(bytes, 256);
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= bytes) {
-                *off = it->first;
-                size_t rest = it->second - bytes;
-                size_t start = it->first + bytes;
-                free_.erase(it);
-                if (rest)
-                    free_[start] = rest;
-                return true;
-            }
-        }
-        return false;
-    }
-    void release(size_t off, size_t bytes)
-    {
-        bytes = align_up(bytes, 256);
-        auto it = free_.emplace(off, bytes).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-
-  private:
-    std::map<size_t, size_t> free_;
-};
 
 struct Request {
     uint64_t id;
@@ -159,7 +118,7 @@ struct orbg_server {
     int64_t max_batch_blocks = 0;
     unsigned char *d_pool = nullptr;
     unsigned char *h_pool = nullptr;
-    Regions *dreg = nullptr, *hreg = nullptr;
+    orbg_host::Regions *dreg = nullptr, *hreg = nullptr;
     std::vector<cudaStream_t> streams;
     std::vector<char> stream_busy;
     std::deque<Request *> pending;
@@ -440,8 +399,8 @@ int orbg_server_create(const orbg_codeset *set, size_t mem_budget_bytes, uint32_
         return rc;
     }
     s->stream_busy.assign(s->streams.size(), 0);
-    s->dreg = new Regions(s->budget);
-    s->hreg = new Regions(s->budget);
+    s->dreg = new orbg_host::Regions(s->budget);
+    s->hreg = new orbg_host::Regions(s->budget);
     s->th = std::thread(dispatcher, s);
     *out = s;
     return ORBG_OK;
